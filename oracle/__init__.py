@@ -1,0 +1,261 @@
+"""CPU oracle for polynomial-preconditioned GMRES (test infrastructure only).
+
+A thin ctypes wrapper around ``ppg_oracle.c``: plain serial float64 C code
+that the CUDA library is checked against.  Only the tests, the smoke check
+and the benchmark's CPU-baseline leg import this package; the library never
+does, and the two share no code.
+
+The C source states, routine by routine, which part of the paper (Loe,
+Thornquist, Boman, arXiv 1907.00072) it follows: Eq. 1 (power basis and
+normal equations), Eq. 2 (the polynomial's power form), Section IV (the
+POTRF-based degree limit) and Sections I/III (right-preconditioned GMRES(m)
+with a relative-residual stopping test).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ppg_oracle.c")
+_LIB = os.path.join(_HERE, "libppg_oracle.so")
+
+POLY_NONE, POLY_POWER, POLY_ARNOLDI = 0, 1, 2
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, strict IEEE: no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB)
+        d = ctypes.c_double
+        i64 = ctypes.c_int64
+        ci = ctypes.c_int
+        p = ctypes.c_void_p
+        _lib.orc_spmv.argtypes = [i64, p, p, p, p, p]
+        _lib.orc_spmv_rows.argtypes = [i64, p, p, p, p, i64, p, p]
+        _lib.orc_transpose.argtypes = [i64, p, p, p, p, p, p]
+        _lib.orc_poly_apply.argtypes = [i64, p, p, p, ci, ci, p, p, p, d, p, p]
+        _lib.orc_poly_eval_zp.argtypes = [ci, ci, p, p, p, d, d]
+        _lib.orc_poly_eval_zp.restype = d
+        _lib.orc_cholesky.argtypes = [ci, p, ci]
+        _lib.orc_cholesky.restype = ci
+        _lib.orc_poly_normal_eq.argtypes = [i64, p, p, p, p, ci, p, p, p, p]
+        _lib.orc_poly_normal_eq.restype = ci
+        _lib.orc_arnoldi.argtypes = [i64, p, p, p, ci, ci, p, p, p, d, p, ci, p, p, p]
+        _lib.orc_arnoldi.restype = ci
+        _lib.orc_poly_gmres.argtypes = [i64, p, p, p, p, ci, p, p, p, p]
+        _lib.orc_poly_gmres.restype = ci
+        _lib.orc_poly_arnoldi_to_power.argtypes = [ci, p, p, d, p]
+        _lib.orc_gmres.argtypes = [i64, p, p, p, ci, ci, p, p, p, d, p, p, d, ci, ci, p, p, ci]
+        _lib.orc_gmres.restype = ci
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _csr(a):
+    return a.n, _i32(a.rowptr), _i32(a.colidx), _f64(a.vals)
+
+
+@dataclass
+class Poly:
+    """The GMRES minimum-residual polynomial in one of the oracle's representations."""
+
+    kind: int
+    deg: int
+    coef: np.ndarray | None = None  # POWER: coef[i] multiplies A^i
+    H: np.ndarray | None = None  # ARNOLDI: (deg+2) x (deg+1) column-major
+    y: np.ndarray | None = None
+    beta: float = 1.0
+    info: int = 0  # POTRF info of the normal-equations route
+    resid: float = float("nan")  # ||v0 - A p(A) v0|| where known
+
+    def args(self):
+        return (
+            self.kind,
+            self.deg,
+            _ptr(self.coef),
+            _ptr(self.H),
+            _ptr(self.y),
+            float(self.beta),
+        )
+
+    def _keep(self):
+        return (self.coef, self.H, self.y)
+
+
+IDENTITY = Poly(POLY_NONE, 0)
+
+
+def spmv(a, x):
+    lib = _load()
+    n, rp, ci, va = _csr(a)
+    x = _f64(x)
+    y = np.empty(n)
+    lib.orc_spmv(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(x), _ptr(y))
+    return y
+
+
+def spmv_rows(a, x, rows):
+    lib = _load()
+    n, rp, ci, va = _csr(a)
+    x = _f64(x)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    y = np.empty(len(rows))
+    lib.orc_spmv_rows(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(x), len(rows), _ptr(rows), _ptr(y))
+    return y
+
+
+def transpose(a):
+    import workloads
+
+    lib = _load()
+    n, rp, ci, va = _csr(a)
+    nnz = int(rp[-1])
+    rpt = np.empty(n + 1, np.int32)
+    cit = np.empty(nnz, np.int32)
+    vat = np.empty(nnz)
+    lib.orc_transpose(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(rpt), _ptr(cit), _ptr(vat))
+    return workloads.CSR(n, rpt, cit, vat, a.name + "^T")
+
+
+def cholesky(G):
+    """Returns (L, info) with POTRF semantics (info = 1-based failing order, 0 if none)."""
+    lib = _load()
+    k = G.shape[0]
+    a = np.asfortranarray(G, dtype=np.float64).copy(order="F")
+    info = lib.orc_cholesky(k, _ptr(a), k)
+    return np.tril(a), info
+
+
+def poly_normal_eq(a, v0, deg):
+    """The paper's construction (Eq. 1 + Cholesky); degree clamped per Section IV."""
+    lib = _load()
+    n, rp, ci, va = _csr(a)
+    v0 = _f64(v0)
+    coef = np.zeros(deg + 1)
+    info = ctypes.c_int(0)
+    gram = np.zeros((deg + 1) * (deg + 1))
+    rhs = np.zeros(deg + 1)
+    used = lib.orc_poly_normal_eq(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(v0), deg, _ptr(coef), ctypes.byref(info),
+                                  _ptr(gram), _ptr(rhs))
+    if used == -2:
+        raise MemoryError("oracle allocation failed")
+    p = Poly(POLY_POWER, max(used, 0), coef[: max(used, 0) + 1].copy(), info=info.value)
+    p.gram = gram.reshape(deg + 1, deg + 1, order="F")
+    p.rhs = rhs
+    p.used = used
+    return p
+
+
+def poly_gmres(a, v0, deg):
+    """Minimum-residual polynomial from deg+1 MGS Arnoldi steps (Arnoldi form)."""
+    lib = _load()
+    n, rp, ci, va = _csr(a)
+    v0 = _f64(v0)
+    H = np.zeros((deg + 2) * (deg + 1))
+    y = np.zeros(deg + 1)
+    beta = ctypes.c_double(0)
+    resid = ctypes.c_double(0)
+    built = lib.orc_poly_gmres(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(v0), deg, _ptr(H), _ptr(y),
+                               ctypes.byref(beta), ctypes.byref(resid))
+    if built == -2:
+        raise MemoryError("oracle allocation failed")
+    if built < deg:  # breakdown: keep the exact lower-degree polynomial
+        Hc = H.reshape(deg + 2, deg + 1, order="F")[: built + 2, : built + 1].copy(order="F").ravel(order="F")
+        return Poly(POLY_ARNOLDI, built, None, Hc, y[: built + 1].copy(), beta.value, resid=resid.value)
+    return Poly(POLY_ARNOLDI, deg, None, H, y, beta.value, resid=resid.value)
+
+
+def arnoldi_to_power(p: Poly) -> np.ndarray:
+    lib = _load()
+    coef = np.zeros(p.deg + 1)
+    lib.orc_poly_arnoldi_to_power(p.deg, _ptr(p.H), _ptr(p.y), float(p.beta), _ptr(coef))
+    return coef
+
+
+def poly_apply(a, p: Poly, x):
+    lib = _load()
+    n, rp, ci, va = _csr(a)
+    x = _f64(x)
+    out = np.empty(n)
+    keep = p._keep()  # noqa: F841 (arrays must outlive the call)
+    lib.orc_poly_apply(n, _ptr(rp), _ptr(ci), _ptr(va), *p.args(), _ptr(x), _ptr(out))
+    return out
+
+
+def poly_eval_zp(p: Poly, z):
+    """alpha p(alpha) at real points (Section V's plots)."""
+    lib = _load()
+    keep = p._keep()  # noqa: F841
+    return np.array([lib.orc_poly_eval_zp(*p.args(), float(t)) for t in np.atleast_1d(z)])
+
+
+def arnoldi(a, p: Poly, v, k):
+    """k MGS Arnoldi steps of A p(A) from v: returns (V n x (k+1), Hbar (k+1) x k, beta, steps)."""
+    lib = _load()
+    n, rp, ci, va = _csr(a)
+    v = _f64(v)
+    V = np.zeros((k + 1) * n)
+    H = np.zeros((k + 1) * k)
+    beta = ctypes.c_double(0)
+    keep = p._keep()  # noqa: F841
+    done = lib.orc_arnoldi(n, _ptr(rp), _ptr(ci), _ptr(va), *p.args(), _ptr(v), k, _ptr(V), _ptr(H),
+                           ctypes.byref(beta))
+    return V.reshape(k + 1, n).T, H.reshape(k, k + 1).T, beta.value, done
+
+
+@dataclass
+class SolveResult:
+    x: np.ndarray
+    converged: bool
+    iters: int
+    restarts: int
+    spmvs: int
+    dots: int
+    relres: float
+    est: float
+    hist: np.ndarray
+
+
+def gmres(a, b, p: Poly = IDENTITY, tol=1e-8, m=50, maxit=10000, x0=None):
+    """Right-preconditioned restarted GMRES(m) with MGS Arnoldi."""
+    lib = _load()
+    n, rp, ci, va = _csr(a)
+    b = _f64(b)
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    stats = np.zeros(8)
+    hist = np.zeros(maxit)
+    keep = p._keep()  # noqa: F841
+    st = lib.orc_gmres(n, _ptr(rp), _ptr(ci), _ptr(va), *p.args(), _ptr(b), _ptr(x), float(tol), int(m), int(maxit),
+                       _ptr(stats), _ptr(hist), int(maxit))
+    if st == -2:
+        raise MemoryError("oracle allocation failed")
+    it = int(stats[0])
+    return SolveResult(x, bool(stats[4]), it, int(stats[1]), int(stats[2]), int(stats[3]), float(stats[5]),
+                       float(stats[6]), hist[:it].copy())
