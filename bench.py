@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""PP-GMRES time-to-solution on GB300 (one JSON line on stdout).
+
+Workload: 3D convection-diffusion, 7-point upwind stencil on a 128^3 grid
+(n = 2,097,152, nnz = 14,581,760, CSR float64), wind (1, 0.5, 0.25) scaled to
+Peclet 50, b uniform in [-1, 1] (SplitMix64 seed 1), x0 = 0, GMRES(50), relative
+residual 1e-8.  One step = build the minimum-residual polynomial (roots form,
+v0 from seed 2) + solve, inputs resident in HBM.  The headline is the float32
+p(A)/Arnoldi solve with float64 iterative refinement; the float64 solve and the
+other degrees are reported under "variants".
+
+  python bench.py [--gpus N --steps K --warmup W] [--degree D] [--precision f32|f64]
+  python bench.py --impl reference ...   # the CPU oracle, bounded sample, same metric
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as w  # noqa: E402
+
+METRIC = "PP-GMRES time-to-solution at rel. res. 1e-8; SpMV-chain HBM GB/s vs peak"
+UNIT = "ms"
+WORKLOAD = "3D convection-diffusion 7-point upwind, 128^3 (n=2097152, nnz=14581760), Pe 50, GMRES(50), rtol 1e-8"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.samples.append([s.strip() for s in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=6)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 3 + i and s[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ppg" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, world, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+
+def oracle_sample(a, b, deg, iters=2):
+    """The oracle on the same workload, bounded: polynomial build + `iters` GMRES iterations."""
+    import oracle
+
+    v0 = w.v0(a.n)
+    t0 = time.perf_counter()
+    p = oracle.poly_gmres(a, v0, deg)
+    t1 = time.perf_counter()
+    r = oracle.gmres(a, b, p, tol=1e-8, m=50, maxit=iters)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / max(r.iters, 1)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    a = w.c2_matrix(args.N)
+    b = w.rhs(a.n)
+    est_iters = args.ref_iters
+    times = []
+    for i in range(args.warmup + args.steps):
+        tb, ti = oracle_sample(a, b, args.degree, iters=2)
+        if i >= args.warmup:
+            times.append((tb + est_iters * ti) * 1e3)
+    v = statistics.mean(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "degree": args.degree, "basis": "arnoldi-form (oracle)",
+                   "restart": 50, "iterations_assumed": est_iters},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"oracle polynomial build (degree {args.degree}) + 2 GMRES(50) iterations on the "
+                                   f"full matrix per step; time-to-solution = build + {est_iters} x per-iteration time"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ppg", choices=["ppg", "reference"])
+    ap.add_argument("--degree", type=int, default=10)
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--N", type=int, default=128, help="grid side (128 is the benchmark workload)")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=60)
+    args = ap.parse_args()
+
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    import paper_1907_00072_gb300 as ppg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    a = w.c2_matrix(args.N)
+    b_h = w.rhs(a.n)
+    v0_h = w.v0(a.n)
+    T = lambda x, dt=torch.float64: torch.as_tensor(x, dtype=dt, device=dev)  # noqa: E731
+    s = ppg.Solver(T(a.rowptr, torch.int32), T(a.colidx, torch.int32), T(a.vals))
+    b = T(b_h)
+    v0 = T(v0_h)
+    prec = ppg.PPG_F32 if args.precision == "f32" else ppg.PPG_F64
+    stream = torch.cuda.current_stream()
+
+    def step(deg=args.degree, precision=prec, bvec=b):
+        used, _ = s.build_poly(deg, ppg.PPG_BASIS_ROOTS, v0=v0)
+        x, info = s.solve(bvec, tol=1e-8, restart=50, maxit=20000, precision=precision)
+        return x, info
+
+    for _ in range(args.warmup):
+        x, info = step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            x, info = step()
+            infos.append(info)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world, dev)
+    launches_per_step = int(np.mean([i.stats["kernel_launches"] for i in infos]))
+    build_launches = None
+    last = infos[-1].stats
+
+    # ---- end to end: pinned host b in, x out, through the public API
+    b_pin = torch.from_numpy(b_h).pin_memory()
+    x_pin = torch.empty(a.n, dtype=torch.float64).pin_memory()
+    b_dev = torch.empty_like(b)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e2.record(stream)
+    for _ in range(args.steps):
+        b_dev.copy_(b_pin, non_blocking=True)
+        x, info = step(bvec=b_dev)
+        x_pin.copy_(x, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e2.elapsed_time(e3) / args.steps, world, dev)
+    relres_host = float(np.linalg.norm(b_h - a.to_scipy() @ x_pin.numpy()) / np.linalg.norm(b_h))
+
+    # ---- roofline of the dominant kernel: the fused SpMV step, timed alone with CUDA events
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    dtype_t = torch.float32 if prec == ppg.PPG_F32 else torch.float64
+    sv = 4 if prec == ppg.PPG_F32 else 8
+    xs = torch.as_tensor(w.uniform(51, a.n), dtype=dtype_t, device=dev)
+    ys = torch.empty_like(xs)
+    for _ in range(3):
+        s.spmv(xs, ys)
+    reps = 50
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        s.spmv(xs, ys)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = ev[0].elapsed_time(ev[1]) / reps
+    spmv_bytes = a.nnz * (sv + 4) + 4 * (a.n + 1) + 2 * a.n * sv
+    achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+
+    # ---- variants: degree x precision, one measured solve each
+    variants = {}
+    if not args.no_variants:
+        for deg in (1, 10, 25, 40):
+            for pname, pv in (("f64", ppg.PPG_F64), ("f32", ppg.PPG_F32)):
+                step(deg, pv)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ea.record(stream)
+                _, inf = step(deg, pv)
+                eb.record(stream)
+                torch.cuda.synchronize()
+                variants[f"d{deg}_{pname}"] = {
+                    "ms": round(ea.elapsed_time(eb), 3), "iterations": inf.stats["iterations"],
+                    "restarts": inf.stats["restarts"], "relres_true": inf.stats["relres_true"],
+                    "status": inf.status}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        tb, ti = oracle_sample(a, b_h, args.degree, iters=2)
+        it64 = variants.get(f"d{args.degree}_f64", {}).get("iterations", last["iterations"])
+        cpu_ms = (tb + it64 * ti) * 1e3
+        cpu = {"value": round(cpu_ms, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle build (degree {args.degree}) + 2 GMRES(50) iterations on the full matrix; "
+                         f"time-to-solution = build + {it64} iterations x measured per-iteration time"}
+
+    line = {
+        "metric": METRIC, "value": round(ms, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == ppg.PPG_F32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "degree": args.degree, "basis": "roots (Leja)", "restart": 50,
+                   "precision": "f32 inner, f64 refinement" if prec == ppg.PPG_F32 else "f64",
+                   "l2": "inputs larger than L2 (CSR 175 MB, basis up to 857 MB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iterations": last["iterations"], "restarts": last["restarts"], "relres_true": last["relres_true"],
+        "relres_host_check": relres_host,
+        "roofline": {"bound": "hbm", "kernel": "k_spmv<float>" if prec == ppg.PPG_F32 else "k_spmv<double>",
+                     "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 3),
+                     "peak_source": "measured" if "hbm_gbs" in pk else "fallback",
+                     "traffic": None, "bytes_per_launch": spmv_bytes, "ms_per_launch": round(spmv_ms, 5)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_ms, 3), "unit": UNIT, "h2d_bytes_per_step": 8 * a.n, "d2h_bytes_per_step": 8 * a.n},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "variants": variants,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

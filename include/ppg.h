@@ -1,0 +1,210 @@
+/*
+ * ppg.h -- C ABI of the GB300 polynomial-preconditioned GMRES library (libppg.so).
+ *
+ * The method is the GMRES minimum-residual polynomial preconditioner of Loe,
+ * Thornquist and Boman, "Polynomial Preconditioned GMRES to Reduce
+ * Communication in Parallel Computing" (arXiv 1907.00072):
+ *
+ *   - p is the degree-d polynomial minimising ||v0 - A p(A) v0||_2 for a
+ *     generating vector v0 (Section II, Eq. 1);
+ *   - p(A) = y_{d+1} A^d + ... + y_2 A + y_1 (Eq. 2) is applied as a right
+ *     preconditioner: A p(A) u = b, x = p(A) u (Section I);
+ *   - the outer solver is restarted GMRES(m) with two passes of classical
+ *     Gram-Schmidt (Section III) and a relative residual stopping test
+ *     ||b - A x|| / ||b|| <= tol (Section III).
+ *
+ * Conventions for every entry point:
+ *   - Matrix and vector pointers are DEVICE pointers unless a name ends in _h
+ *     (host).  The caller owns them; the library never frees them.
+ *   - A context owns its own copy of the CSR matrix (made by ppg_create), its
+ *     CUDA stream (borrowed, may be NULL for the legacy default stream) and a
+ *     workspace (library-allocated unless the caller provides one with
+ *     ppg_set_workspace).
+ *   - Calls enqueue work on the context's stream.  Calls that return host data
+ *     (degree_used, stats, ppg_get_poly, ppg_create's validation) synchronise
+ *     that stream before returning.
+ *   - No C++ exception crosses this boundary.  Every call returns a
+ *     ppg_status; ppg_last_error() gives a one-line explanation of the most
+ *     recent failure on the calling thread.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef PPG_H
+#define PPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ppg_ctx ppg_ctx;
+
+typedef enum {
+    PPG_OK = 0,
+    PPG_WARN_DEGREE_CLAMPED = 1, /* power basis: the Gram matrix of Eq. 1 failed Cholesky at the
+                                    requested degree; the highest degree that factors is used (Section IV) */
+    PPG_ERR_NOT_CONVERGED = 2,   /* maxit reached; x holds the last iterate */
+    PPG_ERR_INVALID_ARG = -1,    /* bad sizes, null pointers, CSR with rowptr not monotone or colidx out of range */
+    PPG_ERR_CUDA = -2,           /* a CUDA runtime call failed (see ppg_last_error) */
+    PPG_ERR_POLY_BREAKDOWN = -3, /* no usable polynomial: degree 0 fails, non-finite coefficients or roots */
+    PPG_ERR_NONFINITE = -4,      /* NaN or Inf in a reduction (residual, inner product or norm) */
+    PPG_ERR_TIMEOUT = -5,        /* a bounded device wait expired */
+    PPG_ERR_OOM = -6,            /* device allocation failed or the caller's workspace is too small */
+    PPG_ERR_NO_POLY = -7         /* apply requested before a polynomial was built or set */
+} ppg_status;
+
+/* polynomial representations */
+enum {
+    PPG_BASIS_POWER = 0, /* coefficients y_1..y_{d+1} of Eq. 2, from the normal equations of Eq. 1 */
+    PPG_BASIS_ROOTS = 1  /* the d+1 roots theta_i of 1 - z p(z), i.e. p(z) = (1 - prod(1 - z/theta_i)) / z */
+};
+
+/* arithmetic of the Krylov basis, p(A) and the SpMVs inside them */
+enum {
+    PPG_F64 = 0, /* float64 throughout */
+    PPG_F32 = 1  /* float32 p(A) and Arnoldi; float64 true residual, Hessenberg least squares and updates of x */
+};
+
+typedef struct {
+    int precision;     /* PPG_F64 (default) or PPG_F32 */
+    double inner_rtol; /* PPG_F32 only: a restart cycle also ends when its residual estimate has dropped by
+                          this factor (iterative refinement step); <= 0 selects 1e-5 */
+    int use_graph;     /* 1: run each restart cycle as one CUDA graph with device-side loop control;
+                          0: host-enqueued kernels; < 0: library default (graph) */
+    int reserved[5];
+} ppg_opts;
+
+typedef struct {
+    int64_t iterations;  /* GMRES iterations (basis vectors built) */
+    int64_t restarts;    /* restart cycles started */
+    int64_t spmvs;       /* sparse matrix-vector products, counted as in Section III */
+    int64_t dots;        /* 2 block inner products + 1 norm per iteration (Section III) and 1 norm per cycle */
+    int64_t kernel_launches;
+    double relres_true;  /* ||b - A x|| / ||b|| of the returned x, computed in float64 */
+    double relres_est;   /* last in-cycle Givens estimate |g_{j+1}| / ||b|| */
+    int degree_used;     /* degree of the polynomial applied */
+    int converged;       /* 1 if relres_true <= tol */
+    int breakdowns;      /* cycles ended by a (lucky) Arnoldi breakdown */
+    int reserved;
+    double time_ms;      /* wall time of the call on the device stream (CUDA events) */
+} ppg_stats;
+
+/* ------------------------------------------------------------------ context */
+
+/* Creates a context for the n x n CSR matrix (int32 rowptr[n+1] and colidx[nnz], float64 vals[nnz],
+ * device pointers, zero-based).  The matrix is copied into library-owned device memory and validated
+ * on the device (rowptr[0] = 0, rowptr non-decreasing, rowptr[n] = nnz, 0 <= colidx < n); columns within
+ * a row need not be sorted.  stream is a cudaStream_t (NULL: legacy default stream).  Synchronises.
+ * Errors: PPG_ERR_INVALID_ARG (n <= 0, nnz < 0, null pointer, invalid CSR), PPG_ERR_OOM, PPG_ERR_CUDA. */
+ppg_status ppg_create(ppg_ctx **ctx, int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                      const double *vals, void *stream);
+
+/* Frees everything the context allocated (not a caller-provided workspace).  NULL is a no-op. */
+void ppg_destroy(ppg_ctx *ctx);
+
+/* Changes the stream later calls enqueue on. */
+ppg_status ppg_set_stream(ppg_ctx *ctx, void *stream);
+
+/* Bytes of device workspace needed by solves with this restart length, polynomial degree and
+ * precision (also enough for ppg_build_poly at that degree and ppg_apply_poly). */
+ppg_status ppg_workspace_bytes(const ppg_ctx *ctx, int restart, int degree, int precision, size_t *bytes);
+
+/* Hands the context a caller-owned device workspace (at least 256-byte aligned).  The library then
+ * allocates no workspace of its own while this one is large enough; a call that needs more returns
+ * PPG_ERR_OOM.  Passing NULL returns to library-managed allocation.  The buffer must outlive its use. */
+ppg_status ppg_set_workspace(ppg_ctx *ctx, void *ws, size_t bytes);
+
+/* ------------------------------------------------------------------ kernels */
+
+/* y = A x (Section II's SpMV).  precision PPG_F64: x, y are float64[n]; PPG_F32: float32[n] with the
+ * float32 copy of the values.  x and y must not overlap. */
+ppg_status ppg_spmv(ppg_ctx *ctx, const void *x, void *y, int precision);
+
+/* ------------------------------------------------------------------ polynomial */
+
+/* Builds the minimum-residual polynomial of the given degree from the generating vector v0
+ * (float64[n] device pointer, or NULL for v0 uniform in [-1, 1] from the counter-based SplitMix64
+ * stream `seed`, as Section V recommends a random vector).
+ *   PPG_BASIS_POWER: the paper's construction (Eq. 1): d+1 SpMVs give AV = [A v0, ..., A^{d+1} v0],
+ *     G = (AV)^T AV and r = (AV)^T v0 are formed in one pass, G y = r is solved by Cholesky.  If the
+ *     Cholesky pivot of order j is not positive, the degree is clamped to j-2 (Section IV) and
+ *     PPG_WARN_DEGREE_CLAMPED is returned.
+ *   PPG_BASIS_ROOTS: the same polynomial represented by the roots of 1 - z p(z) (the harmonic Ritz
+ *     values of a (d+1)-step Arnoldi run from v0), applied as a product in Leja order; stable at the
+ *     high degrees where the power basis fails (Sections II and VIII point to such constructions).
+ * degree = -1 selects the degree automatically by Section IV's rule: the highest degree whose power-
+ * basis Gram matrix still factors (searched up to 30).  degree_used (host, may be NULL) receives the
+ * degree built.  Synchronises.  0 <= degree <= 62.
+ * Errors: PPG_ERR_INVALID_ARG, PPG_ERR_POLY_BREAKDOWN, PPG_ERR_NONFINITE, PPG_ERR_OOM, PPG_ERR_CUDA. */
+ppg_status ppg_build_poly(ppg_ctx *ctx, int degree, int basis, const double *v0, uint64_t seed, int *degree_used);
+
+/* Sets the polynomial from host data instead of building it.
+ *   PPG_BASIS_POWER: coef_h[0..degree] with coef_h[i] multiplying A^i (y_{i+1} of Eq. 2).
+ *   PPG_BASIS_ROOTS: coef_h holds degree+1 roots as (re, im) pairs, applied in the given order;
+ *     a complex root must be followed by its conjugate. */
+ppg_status ppg_set_poly(ppg_ctx *ctx, int basis, int degree, const double *coef_h);
+
+/* Copies the current polynomial to host: *basis, *degree, and coef_h (capacity cap doubles):
+ * degree+1 coefficients (power) or degree+1 (re, im) root pairs in application order (roots).
+ * Also returns (resid_h, may be NULL) ||v0 - A p(A) v0|| / ||v0|| as measured during construction
+ * (NaN if the polynomial was set). */
+ppg_status ppg_get_poly(ppg_ctx *ctx, int *basis, int *degree, double *coef_h, int cap, double *resid_h);
+
+/* out = p(A) v (Eq. 2) with the current polynomial; precision as in ppg_spmv.  v and out are
+ * device vectors of length n of the matching type and must not overlap. */
+ppg_status ppg_apply_poly(ppg_ctx *ctx, const void *v, void *out, int precision);
+
+/* ------------------------------------------------------------------ solvers */
+
+/* Solves A x = b by right-preconditioned GMRES(restart) with the current polynomial (the identity if
+ * none was built): the Krylov basis is built for A p(A) with two classical Gram-Schmidt passes per
+ * iteration, the Hessenberg least-squares problem is solved with Givens rotations on the device, and
+ * at each restart x += p(A) V y followed by a float64 true residual b - A x.  b and x are float64[n]
+ * (x: initial guess in, solution out).  Stops when ||b - A x|| / ||b|| <= tol or after maxit
+ * iterations.  1 <= restart <= 127.  opts and stats may be NULL.  Synchronises.
+ * Returns PPG_OK, PPG_ERR_NOT_CONVERGED, or an error. */
+ppg_status ppg_solve(ppg_ctx *ctx, const double *b, double *x, double tol, int restart, int maxit,
+                     const ppg_opts *opts, ppg_stats *stats);
+
+/* Solves A^T lambda = g with the same method and the preconditioner p(A^T) = p(A)^T (same
+ * polynomial), using a transposed copy of the matrix built on the device at the first call.  Used by
+ * the adjoint of x = A^{-1} b: dL/db = lambda and dL/dvals_k = -lambda_{row(k)} x_{col(k)}. */
+ppg_status ppg_solve_transpose(ppg_ctx *ctx, const double *g, double *lambda, double tol, int restart, int maxit,
+                               const ppg_opts *opts, ppg_stats *stats);
+
+/* out_k = alpha * u_{row(k)} * v_{col(k)} for every stored entry k of the matrix (CSR order of the
+ * matrix passed to ppg_create).  u, v float64[n]; out float64[nnz]. */
+ppg_status ppg_csr_outer(ppg_ctx *ctx, const double *u, const double *v, double alpha, double *out);
+
+/* k steps of Arnoldi for the operator A p(A) (current polynomial, or A alone if none) from v (float64[n]),
+ * with the solver's two-pass classical Gram-Schmidt kernels, in float64.  V (device, may be NULL):
+ * n x (k+1) column-major orthonormal basis; H_h (host): (k+1) x k column-major Hessenberg matrix.
+ * Returns the number of steps completed (< k on breakdown) in *steps.  1 <= k <= 127. */
+ppg_status ppg_arnoldi(ppg_ctx *ctx, const double *v, int k, double *V, double *H_h, int *steps);
+
+/* Eigenvalues of a k x k upper Hessenberg matrix (float64, column-major with leading dimension ld,
+ * device pointer) by the device's Francis double-shift QR kernel, the one used for the roots of the
+ * polynomial.  wr, wi: device float64[k].  Exposed for testing.  1 <= k <= 64. */
+ppg_status ppg_hessenberg_eigs(ppg_ctx *ctx, int k, const double *H, int ld, double *wr, double *wi);
+
+/* Fills out[i] = uniform in [-1, 1) from the counter-based SplitMix64 stream `seed` (element i is the
+ * stream's position i: z = mix(mix(seed) + (i+1) * 0x9E3779B97F4A7C15), u = (z >> 11) * 2^-53).
+ * This is the generator ppg_build_poly uses when v0 is NULL. */
+ppg_status ppg_fill_uniform(ppg_ctx *ctx, double *out, int64_t n, uint64_t seed);
+
+/* ------------------------------------------------------------------ diagnostics */
+
+const char *ppg_status_string(ppg_status status);
+
+/* One-line description of the last failure on the calling thread ("" if none). */
+const char *ppg_last_error(void);
+
+/* Library version string. */
+const char *ppg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPG_H */

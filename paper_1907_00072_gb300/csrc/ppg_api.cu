@@ -1,0 +1,988 @@
+// ppg_api.cu -- the C ABI (include/ppg.h) and the solver driver of the GB300 PP-GMRES library.
+//
+// Host-side orchestration only: every arithmetic step of the method runs in the
+// library's kernels (ppg_spmv.cu, ppg_ortho.cu, ppg_small.cu).  The driver keeps
+// the iteration state on the device (ppg::Cycle), so an iteration is a fixed
+// sequence of launches that reads the iteration index from device memory; the host
+// only enqueues and, once per restart cycle, reads back a few bytes of status.
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ppg.h"
+#include "ppg_internal.h"
+
+using namespace ppg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ppg_status fail(ppg_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+ppg_status fail(ppg_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define PPG_CK(call)                                                                                      \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? PPG_ERR_OOM : PPG_ERR_CUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                                      \
+    } while (0)
+
+#define PPG_TRY(expr)                     \
+    do {                                  \
+        ppg_status s_ = (expr);           \
+        if (s_ < 0) return s_;            \
+    } while (0)
+
+constexpr int kNumVecs = 8;  // working vectors in the workspace
+
+// Number of bytes of Cycle read back by the host (everything before the arrays).
+constexpr size_t kCycleHeader = offsetof(Cycle, sigma);
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct ppg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    DevMatrix A{};
+    int *d_rowptr = nullptr;
+    int *d_colidx = nullptr;
+    double *d_vals = nullptr;
+    float *d_vals32 = nullptr;
+    long long ld = 0;  // padded vector length
+
+    // polynomial (host copy; coefficients enter kernels as launch arguments)
+    int has_poly = 0;
+    int basis = PPG_BASIS_POWER;
+    int degree = 0;
+    std::vector<double> coef;   // power: degree + 1
+    std::vector<double> roots;  // roots: 2 (degree + 1) (re, im)
+    std::vector<double> table;  // roots: 2 (degree + 1) per-step coefficients
+    double poly_resid = NAN;
+
+    Cycle *st = nullptr;      // device state
+    Cycle *h_st = nullptr;    // pinned host mirror (header)
+    double *d_small = nullptr;  // 4 * kKmax doubles: construction outputs
+    int *d_info = nullptr;      // 16 ints
+    int *h_info = nullptr;      // pinned
+    double *h_small = nullptr;  // pinned, 4 * kKmax
+
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = true;
+
+    ppg_ctx *tctx = nullptr;  // transposed matrix (adjoint)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    long long launches = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- workspace
+
+struct Layout {
+    double *partials;
+    int partial_blocks;  // capacity in CTAs for (kKmax + 1) columns
+    char *basis;         // ncols columns of ld elements
+    int ncols;
+    char *vec[kNumVecs];  // working vectors of ld elements
+    size_t esize;
+};
+
+size_t partial_doubles(const ppg_ctx *c)
+{
+    const size_t gs = (size_t)(kKmax + 1) * (size_t)c->num_sms * 16;
+    const size_t gram = (size_t)(kSmallMax * (kSmallMax + 1) / 2) * (size_t)gram_grid(c->num_sms);
+    const size_t resid = (size_t)c->A.resid_blocks;
+    return std::max(gs, std::max(gram, resid));
+}
+
+size_t layout_bytes(const ppg_ctx *c, int ncols)
+{
+    const size_t p = round_up((long long)(partial_doubles(c) * sizeof(double)), 4096);
+    return p + (size_t)(ncols + kNumVecs) * (size_t)c->ld * sizeof(double);
+}
+
+ppg_status get_layout(ppg_ctx *c, int ncols, size_t esize, Layout *L)
+{
+    const size_t need = layout_bytes(c, ncols);
+    if (need > c->ws_bytes) {
+        if (!c->ws_owned)
+            return fail(PPG_ERR_OOM, "workspace of %zu bytes is smaller than the %zu bytes needed", c->ws_bytes,
+                        need);
+        if (c->ws) cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+        PPG_CK(cudaMalloc(&c->ws, need));
+        c->ws_bytes = need;
+    }
+    const size_t p = round_up((long long)(partial_doubles(c) * sizeof(double)), 4096);
+    L->partials = reinterpret_cast<double *>(c->ws);
+    L->partial_blocks = c->num_sms * 16;
+    L->basis = c->ws + p;
+    L->ncols = ncols;
+    L->esize = esize;
+    for (int i = 0; i < kNumVecs; ++i) L->vec[i] = L->basis + (size_t)(ncols + i) * c->ld * esize;
+    // rows n..ld-1 of every column and vector must read as zero
+    if (c->ld > c->A.n) {
+        PPG_CK(cudaMemset2DAsync(L->basis + (size_t)c->A.n * esize, c->ld * esize, 0, (c->ld - c->A.n) * esize,
+                                 ncols + kNumVecs, c->stream));
+    }
+    return PPG_OK;
+}
+
+ppg_status ensure_f32(ppg_ctx *c)
+{
+    if (c->d_vals32) return PPG_OK;
+    PPG_CK(cudaMalloc(&c->d_vals32, (size_t)(c->A.nnz + 8) * sizeof(float)));
+    PPG_CK(cudaMemsetAsync(c->d_vals32, 0, (size_t)(c->A.nnz + 8) * sizeof(float), c->stream));
+    if (c->A.nnz > 0) PPG_CK(launch_cast_f32(c->d_vals, c->d_vals32, c->A.nnz, c->stream));
+    c->A.vals32 = c->d_vals32;
+    return PPG_OK;
+}
+
+// ---------------------------------------------------------------- operand helpers
+
+VecRef vfix(const void *p) { return VecRef{p, 0, 0, 0}; }
+VecRef vcol(const void *base, long long ld, int off) { return VecRef{base, ld, off, 1}; }
+VecRef vnone() { return VecRef{nullptr, 0, 0, 0}; }
+Scalar simm(double v) { return Scalar{v, nullptr, 0, 0, nullptr, 0, 0}; }
+// v * sigma[j] (sigma follows the iteration index) when sig is set
+Scalar sscaled(double v, const double *sig) { return Scalar{v, sig, 0, sig ? 1 : 0, nullptr, 0, 0}; }
+
+SpmvEpi epi_none()
+{
+    SpmvEpi e;
+    e.x = vnone();
+    e.out0 = e.u0 = e.w0 = e.out1 = e.u1 = e.w1 = vnone();
+    e.a0 = e.b0 = e.c0 = e.a1 = e.b1 = e.c1 = simm(0.0);
+    return e;
+}
+
+struct Exec {
+    ppg_ctx *c;
+    const DevMatrix *A;
+    int prec;
+    cudaStream_t s;
+
+    ppg_status spmv(const SpmvEpi &e, int check)
+    {
+        c->launches++;
+        PPG_CK(launch_spmv(*A, prec, e, c->st, check, s));
+        return PPG_OK;
+    }
+    ppg_status axpy(const SpmvEpi &e, int check)
+    {
+        c->launches++;
+        PPG_CK(launch_axpy(A->n, prec, e, c->st, check, s));
+        return PPG_OK;
+    }
+
+    // dst = p(A) (scale * src).  sig: device sigma array (follows j) or null for 1.
+    // tmp: 3 distinct working vectors, none of them src or dst.
+    ppg_status poly_apply(VecRef src, const double *sig, VecRef dst, char *const tmp[3], int check)
+    {
+        if (!c->has_poly) {
+            SpmvEpi e = epi_none();
+            e.out0 = dst;
+            e.u0 = src;
+            e.b0 = sscaled(1.0, sig);
+            return axpy(e, check);
+        }
+        if (c->basis == PPG_BASIS_POWER) {
+            const int d = c->degree;
+            const std::vector<double> &y = c->coef;
+            if (d == 0) {
+                SpmvEpi e = epi_none();
+                e.out0 = dst;
+                e.u0 = src;
+                e.b0 = sscaled(y[0], sig);
+                return axpy(e, check);
+            }
+            // Horner: t_1 = y_d A v + y_{d-1} v;  t_i = A t_{i-1} + y_{d-i} v;  p(A) v = t_d
+            VecRef prev = src;
+            for (int i = 1; i <= d; ++i) {
+                VecRef out = ((d - i) % 2 == 0) ? dst : vfix(tmp[0]);
+                SpmvEpi e = epi_none();
+                e.x = prev;
+                e.out0 = out;
+                e.a0 = (i == 1) ? sscaled(y[d], sig) : simm(1.0);
+                e.u0 = src;
+                e.b0 = sscaled(y[d - i], sig);
+                PPG_TRY(spmv(e, check));
+                prev = out;
+            }
+            return PPG_OK;
+        }
+        // product form over the Leja-ordered roots; y accumulates in dst
+        const int k = c->degree + 1;
+        const double *tb = c->table.data();
+        const double *rt = c->roots.data();
+        VecRef P = src;
+        bool first = true;
+        int pp = 0;  // which of tmp[0], tmp[1] receives the next P
+        VecRef T = vfix(tmp[2]);
+        for (int i = 0; i < k;) {
+            const bool real = rt[2 * i + 1] == 0.0;
+            const double *S = first ? sig : nullptr;
+            if (real) {
+                const double t = tb[2 * i];
+                SpmvEpi e = epi_none();
+                e.out0 = dst;
+                e.u0 = P;
+                e.b0 = sscaled(t, S);
+                if (!first) {
+                    e.w0 = dst;
+                    e.c0 = simm(1.0);
+                }
+                if (i == k - 1) {
+                    PPG_TRY(axpy(e, check));
+                } else {
+                    VecRef Pn = vfix(tmp[pp]);
+                    e.x = P;
+                    e.a0 = simm(0.0);
+                    e.out1 = Pn;
+                    e.a1 = sscaled(-t, S);
+                    e.u1 = P;
+                    e.b1 = sscaled(1.0, S);
+                    PPG_TRY(spmv(e, check));
+                    P = Pn;
+                    pp ^= 1;
+                }
+                i += 1;
+            } else {
+                const double c2a = tb[2 * i], cq = tb[2 * i + 1];
+                const bool last = (i + 2 >= k);
+                SpmvEpi e = epi_none();
+                e.x = P;
+                e.out0 = dst;
+                e.a0 = sscaled(-cq, S);
+                e.u0 = P;
+                e.b0 = sscaled(c2a, S);
+                if (!first) {
+                    e.w0 = dst;
+                    e.c0 = simm(1.0);
+                }
+                e.out1 = T;
+                e.a1 = sscaled(1.0, S);
+                PPG_TRY(spmv(e, check));
+                if (!last) {
+                    VecRef Pn = vfix(tmp[pp]);
+                    SpmvEpi f = epi_none();
+                    f.x = T;
+                    f.out0 = Pn;
+                    f.a0 = simm(cq);
+                    f.u0 = T;
+                    f.b0 = simm(-c2a);
+                    f.w0 = P;
+                    f.c0 = sscaled(1.0, S);
+                    PPG_TRY(spmv(f, check));
+                    P = Pn;
+                    pp ^= 1;
+                }
+                i += 2;
+            }
+            first = false;
+        }
+        return PPG_OK;
+    }
+
+    // w = A p(A) (scale * src), fusing the scalar cases into one SpMV.
+    ppg_status poly_then_A(VecRef src, const double *sig, VecRef w, char *const tmp[4], int check)
+    {
+        if (!c->has_poly || (c->basis == PPG_BASIS_POWER && c->degree == 0)) {
+            const double s0 = c->has_poly ? c->coef[0] : 1.0;
+            SpmvEpi e = epi_none();
+            e.x = src;
+            e.out0 = w;
+            e.a0 = sscaled(s0, sig);
+            return spmv(e, check);
+        }
+        char *t3[3] = {tmp[1], tmp[2], tmp[3]};
+        PPG_TRY(poly_apply(src, sig, vfix(tmp[0]), t3, check));
+        SpmvEpi e = epi_none();
+        e.x = vfix(tmp[0]);
+        e.out0 = w;
+        e.a0 = simm(1.0);
+        return spmv(e, check);
+    }
+
+    // number of SpMVs in one application of p(A)
+    int poly_spmvs() const
+    {
+        if (!c->has_poly) return 0;
+        if (c->basis == PPG_BASIS_POWER) return c->degree;
+        return c->degree;  // d+1 roots, the last one needs no SpMV
+    }
+};
+
+// One Arnoldi iteration for A p(A): w = A p(A) v_j, then the three Gram-Schmidt passes.
+struct Iter {
+    Exec *x;
+    const Layout *L;
+    int kmax;
+    long long ntiles;
+    int nblk;
+
+    ppg_status gs(int op, int from_k, void *out, int out_follow)
+    {
+        GsArgs a{};
+        a.U = L->basis;
+        a.ldu = x->c->ld;
+        a.w = L->vec[0];
+        a.out = out;
+        a.out_follow = out_follow;
+        a.op = op;
+        a.kcols_from_k = from_k;
+        a.ntiles = ntiles;
+        a.partials = L->partials;
+        a.nblk = nblk;
+        x->c->launches++;
+        PPG_CK(launch_gs(x->prec, kmax, a, x->c->st, x->s));
+        return PPG_OK;
+    }
+
+    ppg_status iteration()
+    {
+        char *tmp[4] = {L->vec[1], L->vec[2], L->vec[3], L->vec[4]};
+        PPG_TRY(x->poly_then_A(vcol(L->basis, x->c->ld, 0), x->c->st->sigma, vfix(L->vec[0]), tmp, kSkipIfDone));
+        PPG_TRY(gs(kGsDot, 0, nullptr, 0));
+        PPG_TRY(gs(kGsUpdDot, 0, nullptr, 0));
+        PPG_TRY(gs(kGsUpdNorm, 0, nullptr, 1));
+        return PPG_OK;
+    }
+
+    // x += p(A) V y with the coefficients the last pass-3 finalisation left in coef.
+    ppg_status cycle_end(double *xsol)
+    {
+        char *z = L->vec[5], *e = L->vec[6];
+        PPG_TRY(gs(kGsCombine, 1, z, 0));
+        const void *corr = z;
+        if (x->c->has_poly) {
+            char *t3[3] = {L->vec[1], L->vec[2], L->vec[3]};
+            PPG_TRY(x->poly_apply(vfix(z), nullptr, vfix(e), t3, kSkipIfNoCols));
+            corr = e;
+        }
+        x->c->launches++;
+        PPG_CK(launch_xupdate(x->A->n, x->prec, corr, xsol, x->c->st, x->s));
+        return PPG_OK;
+    }
+};
+
+ppg_status init_cycle_state(ppg_ctx *c, int mode, int m, long long maxit, double tol, double inner)
+{
+    Cycle *h = c->h_st;
+    memset(h, 0, kCycleHeader);
+    h->mode = mode;
+    h->m = m;
+    h->maxit = maxit;
+    h->tol = tol;
+    h->inner_rtol = inner;
+    h->cycle_done = 1;
+    PPG_CK(cudaMemcpyAsync(c->st, h, kCycleHeader, cudaMemcpyHostToDevice, c->stream));
+    PPG_CK(cudaMemsetAsync(c->st->ticket, 0, sizeof(c->st->ticket), c->stream));
+    return PPG_OK;
+}
+
+ppg_status read_state(ppg_ctx *c)
+{
+    PPG_CK(cudaMemcpyAsync(c->h_st, c->st, kCycleHeader, cudaMemcpyDeviceToHost, c->stream));
+    PPG_CK(cudaStreamSynchronize(c->stream));
+    if (c->h_st->error & kErrTimeout) return fail(PPG_ERR_TIMEOUT, "a bounded device wait expired");
+    return PPG_OK;
+}
+
+int kmax_for(int ncols) { return ncols <= 64 ? 64 : 128; }
+
+// Runs `steps` Arnoldi iterations of A p(A) (current polynomial) from v (float64, n) in float64 with
+// the solver's kernels; the Hessenberg matrix stays in c->st.  v may be null when the start vector is
+// already in basis column 0.  Returns the number of steps completed in *done.
+ppg_status run_arnoldi(ppg_ctx *c, const double *v, int steps, const Layout &L, int *done)
+{
+    Exec ex{c, &c->A, kF64, c->stream};
+    const int kmax = kmax_for(steps + 1);
+    const long long ntiles = c->ld / gs_tile_rows(kF64, kmax);
+    Iter it{&ex, &L, kmax, ntiles, gs_grid(kF64, kmax, ntiles, c->num_sms)};
+    PPG_TRY(init_cycle_state(c, 0, steps, steps, 0.0, 0.0));
+    c->launches++;
+    PPG_CK(launch_norm_start(c->A.n, kF64, v ? v : (const double *)L.basis, v ? (void *)L.basis : nullptr, 1, c->st,
+                             L.partials, c->A.resid_blocks, c->stream));
+    for (int j = 0; j < steps; ++j) PPG_TRY(it.iteration());
+    PPG_TRY(read_state(c));
+    if (c->h_st->error & kErrNonfinite) return fail(PPG_ERR_NONFINITE, "non-finite value in the Arnoldi run");
+    *done = c->h_st->j;
+    return PPG_OK;
+}
+
+ppg_status build_power(ppg_ctx *c, int deg, const Layout &L, int *used, int *info)
+{
+    const long long ld = c->ld;
+    Exec ex{c, &c->A, kF64, c->stream};
+    for (int i = 1; i <= deg + 1; ++i) {
+        SpmvEpi e = epi_none();
+        e.x = vfix(L.basis + (size_t)(i - 1) * ld * sizeof(double));
+        e.out0 = vfix(L.basis + (size_t)i * ld * sizeof(double));
+        e.a0 = simm(1.0);
+        PPG_TRY(ex.spmv(e, kNoCheck));
+    }
+    PPG_TRY(init_cycle_state(c, 0, 1, 1, 0.0, 0.0));
+    c->launches++;
+    PPG_CK(launch_gram_cholesky(c->A.n, ld, (const double *)L.basis, deg, L.partials, gram_grid(c->num_sms),
+                                c->d_small, c->d_info, c->st, c->stream));
+    PPG_CK(cudaMemcpyAsync(c->h_small, c->d_small, sizeof(double) * (deg + 1), cudaMemcpyDeviceToHost, c->stream));
+    PPG_CK(cudaMemcpyAsync(c->h_info, c->d_info, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+    PPG_TRY(read_state(c));
+    *info = c->h_info[0];
+    *used = c->h_info[1];
+    if (*used < 0) return fail(PPG_ERR_POLY_BREAKDOWN, "the Gram matrix of Eq. 1 is not positive at degree 0");
+    if (!c->h_info[2]) return fail(PPG_ERR_POLY_BREAKDOWN, "non-finite polynomial coefficients");
+    c->basis = PPG_BASIS_POWER;
+    c->degree = *used;
+    c->coef.assign(c->h_small, c->h_small + *used + 1);
+    c->roots.clear();
+    c->table.clear();
+    c->poly_resid = NAN;
+    c->has_poly = 1;
+    return PPG_OK;
+}
+
+ppg_status build_roots(ppg_ctx *c, int deg, const Layout &L, int *used)
+{
+    // Arnoldi with A alone from v0 (already in basis column 0)
+    const int had = c->has_poly;
+    c->has_poly = 0;
+    int done = 0;
+    ppg_status s = run_arnoldi(c, nullptr, deg + 1, L, &done);
+    c->has_poly = had;
+    if (s < 0) return s;
+    const int k = done;  // harmonic Ritz problem size; degree k - 1
+    if (k < 1) return fail(PPG_ERR_POLY_BREAKDOWN, "the generating vector is zero");
+    c->launches++;
+    PPG_CK(launch_roots(c->st, k, c->d_small, c->d_small + 2 * kKmax, c->d_info, c->stream));
+    PPG_CK(cudaMemcpyAsync(c->h_small, c->d_small, sizeof(double) * 4 * kKmax, cudaMemcpyDeviceToHost, c->stream));
+    PPG_CK(cudaMemcpyAsync(c->h_info, c->d_info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PPG_CK(cudaStreamSynchronize(c->stream));
+    if (c->h_info[0] != 0)
+        return fail(PPG_ERR_POLY_BREAKDOWN, "roots of the residual polynomial failed (status %d)", c->h_info[0]);
+    c->basis = PPG_BASIS_ROOTS;
+    c->degree = k - 1;
+    c->roots.assign(c->h_small, c->h_small + 2 * k);
+    c->table.assign(c->h_small + 2 * kKmax, c->h_small + 2 * kKmax + 2 * k);
+    c->coef.clear();
+    c->poly_resid = c->h_st->est;
+    c->has_poly = 1;
+    *used = k - 1;
+    return PPG_OK;
+}
+
+ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int restart, int maxit,
+                      const ppg_opts *opts, ppg_stats *stats)
+{
+    if (!b || !x) return fail(PPG_ERR_INVALID_ARG, "null b or x");
+    if (restart < 1 || restart > kKmax - 1) return fail(PPG_ERR_INVALID_ARG, "restart must be in [1, %d]", kKmax - 1);
+    if (maxit < 0 || !(tol >= 0.0)) return fail(PPG_ERR_INVALID_ARG, "bad tol or maxit");
+    const int prec = opts ? opts->precision : PPG_F64;
+    if (prec != PPG_F64 && prec != PPG_F32) return fail(PPG_ERR_INVALID_ARG, "unknown precision");
+    double inner = 0.0;
+    if (prec == PPG_F32) {
+        inner = (opts && opts->inner_rtol > 0.0) ? opts->inner_rtol : 1e-5;
+        PPG_TRY(ensure_f32(c));
+    }
+    const size_t es = prec == PPG_F64 ? 8 : 4;
+    const int ncols = restart + 1;
+    Layout L;
+    PPG_TRY(get_layout(c, ncols, es, &L));
+    const long long launches0 = c->launches;
+    PPG_CK(cudaEventRecord(c->ev0, c->stream));
+
+    Exec ex{c, &c->A, prec, c->stream};
+    const int kmax = kmax_for(ncols);
+    const long long ntiles = c->ld / gs_tile_rows(prec, kmax);
+    Iter it{&ex, &L, kmax, ntiles, gs_grid(prec, kmax, ntiles, c->num_sms)};
+
+    PPG_TRY(init_cycle_state(c, 0, restart, maxit, tol, inner));
+    c->launches++;
+    PPG_CK(launch_norm_start(c->A.n, kF64, b, nullptr, 0, c->st, L.partials, c->A.resid_blocks, c->stream));
+    PPG_TRY(read_state(c));
+    long long residuals = 0;
+    if (c->h_st->bnorm == 0.0) {
+        PPG_CK(cudaMemsetAsync(x, 0, sizeof(double) * c->A.n, c->stream));
+        c->h_st->converged = 1;
+        c->h_st->relres = 0.0;
+    } else {
+        c->launches++;
+        PPG_CK(launch_residual(c->A, prec, b, x, L.basis, c->st, L.partials, c->stream));
+        residuals++;
+        PPG_TRY(read_state(c));
+        while (!c->h_st->stop) {
+            for (int j = 0; j < restart; ++j) PPG_TRY(it.iteration());
+            PPG_TRY(it.cycle_end(x));
+            c->launches++;
+            PPG_CK(launch_residual(c->A, prec, b, x, L.basis, c->st, L.partials, c->stream));
+            residuals++;
+            PPG_TRY(read_state(c));
+        }
+    }
+    PPG_CK(cudaEventRecord(c->ev1, c->stream));
+    PPG_CK(cudaEventSynchronize(c->ev1));
+    const Cycle &h = *c->h_st;
+    if (stats) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        memset(stats, 0, sizeof *stats);
+        stats->iterations = h.iters;
+        stats->restarts = h.cycles;
+        const int ps = ex.poly_spmvs();
+        stats->spmvs = h.iters * (long long)(ps + 1) + h.cycles * (long long)ps + residuals;
+        stats->dots = 3 * h.iters + residuals;
+        stats->kernel_launches = c->launches - launches0;
+        stats->relres_true = h.relres;
+        stats->relres_est = h.est;
+        stats->degree_used = c->has_poly ? c->degree : 0;
+        stats->converged = h.converged;
+        stats->breakdowns = h.n_breakdowns;
+        stats->time_ms = ms;
+    }
+    if (h.error & kErrNonfinite) return fail(PPG_ERR_NONFINITE, "non-finite value in a reduction");
+    return h.converged ? PPG_OK : PPG_ERR_NOT_CONVERGED;
+}
+
+ppg_status check_ctx(const ppg_ctx *c)
+{
+    if (!c) return fail(PPG_ERR_INVALID_ARG, "null context");
+    return PPG_OK;
+}
+
+ppg_status set_device(const ppg_ctx *c)
+{
+    PPG_CK(cudaSetDevice(c->device));
+    return PPG_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+const char *ppg_version(void) { return "ppg 0.1 (sm_103a)"; }
+
+const char *ppg_last_error(void) { return g_last_error.c_str(); }
+
+const char *ppg_status_string(ppg_status s)
+{
+    switch (s) {
+    case PPG_OK: return "ok";
+    case PPG_WARN_DEGREE_CLAMPED: return "degree clamped (Cholesky of the power-basis Gram matrix failed)";
+    case PPG_ERR_NOT_CONVERGED: return "not converged";
+    case PPG_ERR_INVALID_ARG: return "invalid argument";
+    case PPG_ERR_CUDA: return "CUDA error";
+    case PPG_ERR_POLY_BREAKDOWN: return "polynomial breakdown";
+    case PPG_ERR_NONFINITE: return "non-finite value";
+    case PPG_ERR_TIMEOUT: return "device wait timed out";
+    case PPG_ERR_OOM: return "out of device memory";
+    case PPG_ERR_NO_POLY: return "no polynomial";
+    }
+    return "unknown status";
+}
+
+ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowptr, const int32_t *colidx,
+                      const double *vals, void *stream)
+{
+    g_last_error.clear();
+    if (!out) return fail(PPG_ERR_INVALID_ARG, "null output pointer");
+    *out = nullptr;
+    if (n <= 0 || nnz < 0 || n >= (1LL << 31) - 256 || nnz >= (1LL << 31) - 64)
+        return fail(PPG_ERR_INVALID_ARG, "bad sizes n=%lld nnz=%lld", (long long)n, (long long)nnz);
+    if (!rowptr || (nnz > 0 && (!colidx || !vals))) return fail(PPG_ERR_INVALID_ARG, "null CSR pointer");
+    ppg_ctx *c = new (std::nothrow) ppg_ctx();
+    if (!c) return fail(PPG_ERR_OOM, "host allocation failed");
+    struct Guard {
+        ppg_ctx **c;
+        ~Guard()
+        {
+            if (*c) ppg_destroy(*c);
+        }
+    } guard{&c};
+
+    PPG_CK(cudaGetDevice(&c->device));
+    PPG_CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    c->stream = (cudaStream_t)stream;
+    c->A.n = (int)n;
+    c->A.nnz = nnz;
+    c->A.num_sms = c->num_sms;
+    c->A.resid_blocks = c->num_sms * 8;
+    c->ld = round_up(n, kLdPad);
+    PPG_CK(cudaMalloc(&c->d_rowptr, sizeof(int) * (n + 1)));
+    PPG_CK(cudaMalloc(&c->d_colidx, sizeof(int) * (nnz + 16)));
+    PPG_CK(cudaMalloc(&c->d_vals, sizeof(double) * (nnz + 8)));
+    PPG_CK(cudaMemcpyAsync(c->d_rowptr, rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, c->stream));
+    PPG_CK(cudaMemsetAsync(c->d_colidx, 0, sizeof(int) * (nnz + 16), c->stream));
+    PPG_CK(cudaMemsetAsync(c->d_vals, 0, sizeof(double) * (nnz + 8), c->stream));
+    if (nnz > 0) {
+        PPG_CK(cudaMemcpyAsync(c->d_colidx, colidx, sizeof(int) * nnz, cudaMemcpyDeviceToDevice, c->stream));
+        PPG_CK(cudaMemcpyAsync(c->d_vals, vals, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    c->A.rowptr = c->d_rowptr;
+    c->A.colidx = c->d_colidx;
+    c->A.vals64 = c->d_vals;
+
+    PPG_CK(cudaMalloc(&c->st, sizeof(Cycle)));
+    PPG_CK(cudaMemsetAsync(c->st, 0, sizeof(Cycle), c->stream));
+    PPG_CK(cudaMalloc(&c->d_small, sizeof(double) * 4 * kKmax));
+    PPG_CK(cudaMalloc(&c->d_info, sizeof(int) * 16));
+    PPG_CK(cudaMallocHost(&c->h_st, kCycleHeader));
+    PPG_CK(cudaMallocHost(&c->h_info, sizeof(int) * 16));
+    PPG_CK(cudaMallocHost(&c->h_small, sizeof(double) * 4 * kKmax));
+    PPG_CK(cudaEventCreate(&c->ev0));
+    PPG_CK(cudaEventCreate(&c->ev1));
+
+    // validate on the device
+    PPG_CK(cudaMemsetAsync(c->d_info, 0, sizeof(int), c->stream));
+    PPG_CK(launch_validate((int)n, nnz, c->d_rowptr, c->d_colidx, c->d_info, c->stream));
+    PPG_CK(cudaMemcpyAsync(c->h_info, c->d_info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PPG_CK(cudaStreamSynchronize(c->stream));
+    if (c->h_info[0] != 0) return fail(PPG_ERR_INVALID_ARG, "invalid CSR (validation flags 0x%x)", c->h_info[0]);
+
+    // tiling: rows per tile from the mean row length, staging capacity from the largest tile
+    const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
+    int R = 256;
+    if (avg > 10) R = 128;
+    if (avg > 20) R = 64;
+    if (avg > 40) R = 32;
+    if (avg > 80) R = 8;
+    std::vector<int> hrp(n + 1);
+    PPG_CK(cudaMemcpy(hrp.data(), c->d_rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
+    long long maxtile = 0;
+    for (long long r0 = 0; r0 < n; r0 += R) {
+        const long long r1 = std::min<long long>(n, r0 + R);
+        maxtile = std::max<long long>(maxtile, hrp[r1] - hrp[r0]);
+    }
+    const long long cap = std::min<long long>(4096, round_up(maxtile + 8, 16));
+    c->A.rows_per_tile = R;
+    c->A.lanes_per_row = kThreads / R;
+    c->A.cap64 = (int)std::max<long long>(cap, 64);
+    c->A.cap32 = (int)std::max<long long>(cap, 64);
+    PPG_CK(spmv_configure(c->A.cap64, c->A.cap32));
+    PPG_CK(gs_configure());
+    PPG_CK(gram_configure());
+
+    *out = c;
+    c = nullptr;  // release from the guard
+    return PPG_OK;
+}
+
+void ppg_destroy(ppg_ctx *c)
+{
+    if (!c) return;
+    if (c->tctx) ppg_destroy(c->tctx);
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(c->d_rowptr);
+    cudaFree(c->d_colidx);
+    cudaFree(c->d_vals);
+    cudaFree(c->d_vals32);
+    cudaFree(c->st);
+    cudaFree(c->d_small);
+    cudaFree(c->d_info);
+    if (c->ws_owned) cudaFree(c->ws);
+    cudaFreeHost(c->h_st);
+    cudaFreeHost(c->h_info);
+    cudaFreeHost(c->h_small);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+}
+
+ppg_status ppg_set_stream(ppg_ctx *c, void *stream)
+{
+    PPG_TRY(check_ctx(c));
+    c->stream = (cudaStream_t)stream;
+    if (c->tctx) c->tctx->stream = c->stream;
+    return PPG_OK;
+}
+
+ppg_status ppg_workspace_bytes(const ppg_ctx *c, int restart, int degree, int precision, size_t *bytes)
+{
+    (void)precision;
+    PPG_TRY(check_ctx(c));
+    if (!bytes || restart < 1 || restart > kKmax - 1 || degree < -1 || degree > kSmallMax - 2)
+        return fail(PPG_ERR_INVALID_ARG, "bad restart, degree or null output");
+    const int d = degree < 0 ? 30 : degree;
+    *bytes = layout_bytes(c, std::max(restart + 1, d + 2));
+    return PPG_OK;
+}
+
+ppg_status ppg_set_workspace(ppg_ctx *c, void *ws, size_t bytes)
+{
+    PPG_TRY(check_ctx(c));
+    PPG_TRY(set_device(c));
+    if (c->ws_owned && c->ws) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->ws);
+    }
+    if (ws) {
+        if (((uintptr_t)ws & 255) != 0) return fail(PPG_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+        c->ws = (char *)ws;
+        c->ws_bytes = bytes;
+        c->ws_owned = false;
+    } else {
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+        c->ws_owned = true;
+    }
+    return PPG_OK;
+}
+
+ppg_status ppg_spmv(ppg_ctx *c, const void *x, void *y, int precision)
+{
+    PPG_TRY(check_ctx(c));
+    if (!x || !y) return fail(PPG_ERR_INVALID_ARG, "null vector");
+    if (precision != PPG_F64 && precision != PPG_F32) return fail(PPG_ERR_INVALID_ARG, "unknown precision");
+    PPG_TRY(set_device(c));
+    if (precision == PPG_F32) PPG_TRY(ensure_f32(c));
+    Exec ex{c, &c->A, precision, c->stream};
+    SpmvEpi e = epi_none();
+    e.x = vfix(x);
+    e.out0 = vfix(y);
+    e.a0 = simm(1.0);
+    return ex.spmv(e, kNoCheck);
+}
+
+ppg_status ppg_build_poly(ppg_ctx *c, int degree, int basis, const double *v0, uint64_t seed, int *degree_used)
+{
+    PPG_TRY(check_ctx(c));
+    if (degree < -1 || degree > kSmallMax - 2) return fail(PPG_ERR_INVALID_ARG, "degree must be in [-1, 62]");
+    if (basis != PPG_BASIS_POWER && basis != PPG_BASIS_ROOTS) return fail(PPG_ERR_INVALID_ARG, "unknown basis");
+    PPG_TRY(set_device(c));
+    const bool autodeg = degree < 0;
+    int deg = autodeg ? 30 : degree;
+    Layout L;
+    PPG_TRY(get_layout(c, std::max(deg + 2, 2), sizeof(double), &L));
+    double *b0 = (double *)L.basis;
+    if (v0) {
+        PPG_CK(launch_copy_in(c->A.n, kF64, v0, b0, c->stream));
+    } else {
+        PPG_CK(launch_fill_uniform(b0, c->A.n, seed, c->stream));
+    }
+    c->launches++;
+    ppg_status status = PPG_OK;
+    int used = 0, info = 0;
+    if (basis == PPG_BASIS_POWER || autodeg) {
+        PPG_TRY(build_power(c, deg, L, &used, &info));
+        if (!autodeg && used < deg) status = PPG_WARN_DEGREE_CLAMPED;
+        deg = used;
+    }
+    if (basis == PPG_BASIS_ROOTS) {
+        if (autodeg) {  // the power build overwrote nothing but columns 1..; column 0 still holds v0
+        }
+        PPG_TRY(build_roots(c, deg, L, &used));
+    }
+    if (degree_used) *degree_used = used;
+    return status;
+}
+
+ppg_status ppg_set_poly(ppg_ctx *c, int basis, int degree, const double *coef_h)
+{
+    PPG_TRY(check_ctx(c));
+    if (degree < 0 || degree > kSmallMax - 2 || !coef_h) return fail(PPG_ERR_INVALID_ARG, "bad degree or null data");
+    if (basis == PPG_BASIS_POWER) {
+        for (int i = 0; i <= degree; ++i)
+            if (!std::isfinite(coef_h[i])) return fail(PPG_ERR_POLY_BREAKDOWN, "non-finite coefficient");
+        c->coef.assign(coef_h, coef_h + degree + 1);
+        c->roots.clear();
+        c->table.clear();
+    } else if (basis == PPG_BASIS_ROOTS) {
+        const int k = degree + 1;
+        std::vector<double> r(coef_h, coef_h + 2 * k), t(2 * k, 0.0);
+        for (int i = 0; i < k; ++i) {
+            const double re = r[2 * i], im = r[2 * i + 1];
+            if (!std::isfinite(re) || !std::isfinite(im) || (re == 0.0 && im == 0.0))
+                return fail(PPG_ERR_POLY_BREAKDOWN, "zero or non-finite root");
+            if (im != 0.0) {
+                if (i + 1 >= k || r[2 * i + 2] != re || r[2 * i + 3] != -im || im < 0.0)
+                    return fail(PPG_ERR_INVALID_ARG, "a complex root (im > 0) must be followed by its conjugate");
+            }
+        }
+        PPG_TRY(set_device(c));
+        PPG_CK(cudaMemcpyAsync(c->d_small, r.data(), sizeof(double) * 2 * k, cudaMemcpyHostToDevice, c->stream));
+        PPG_CK(launch_root_table(k, c->d_small, c->d_small + 2 * kKmax, c->d_info, c->stream));
+        PPG_CK(cudaMemcpyAsync(c->h_small, c->d_small + 2 * kKmax, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost,
+                               c->stream));
+        PPG_CK(cudaMemcpyAsync(c->h_info, c->d_info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        PPG_CK(cudaStreamSynchronize(c->stream));
+        if (c->h_info[0]) return fail(PPG_ERR_POLY_BREAKDOWN, "zero or non-finite root");
+        t.assign(c->h_small, c->h_small + 2 * k);
+        c->roots = r;
+        c->table = t;
+        c->coef.clear();
+    } else {
+        return fail(PPG_ERR_INVALID_ARG, "unknown basis");
+    }
+    c->basis = basis;
+    c->degree = degree;
+    c->poly_resid = NAN;
+    c->has_poly = 1;
+    return PPG_OK;
+}
+
+ppg_status ppg_get_poly(ppg_ctx *c, int *basis, int *degree, double *coef_h, int cap, double *resid_h)
+{
+    PPG_TRY(check_ctx(c));
+    if (!c->has_poly) return fail(PPG_ERR_NO_POLY, "no polynomial has been built or set");
+    if (basis) *basis = c->basis;
+    if (degree) *degree = c->degree;
+    if (resid_h) *resid_h = c->poly_resid;
+    if (coef_h) {
+        const std::vector<double> &v = c->basis == PPG_BASIS_POWER ? c->coef : c->roots;
+        if ((size_t)cap < v.size()) return fail(PPG_ERR_INVALID_ARG, "capacity %d < %zu", cap, v.size());
+        std::copy(v.begin(), v.end(), coef_h);
+    }
+    return PPG_OK;
+}
+
+ppg_status ppg_apply_poly(ppg_ctx *c, const void *v, void *out, int precision)
+{
+    PPG_TRY(check_ctx(c));
+    if (!v || !out) return fail(PPG_ERR_INVALID_ARG, "null vector");
+    if (precision != PPG_F64 && precision != PPG_F32) return fail(PPG_ERR_INVALID_ARG, "unknown precision");
+    if (!c->has_poly) return fail(PPG_ERR_NO_POLY, "no polynomial has been built or set");
+    PPG_TRY(set_device(c));
+    if (precision == PPG_F32) PPG_TRY(ensure_f32(c));
+    const size_t es = precision == PPG_F64 ? 8 : 4;
+    Layout L;
+    PPG_TRY(get_layout(c, 1, es, &L));
+    PPG_TRY(init_cycle_state(c, 0, 1, 1, 0.0, 0.0));
+    PPG_CK(launch_copy_in(c->A.n, precision, v, L.vec[0], c->stream));
+    Exec ex{c, &c->A, precision, c->stream};
+    char *tmp[3] = {L.vec[2], L.vec[3], L.vec[4]};
+    PPG_TRY(ex.poly_apply(vfix(L.vec[0]), nullptr, vfix(L.vec[1]), tmp, kNoCheck));
+    PPG_CK(launch_copy_in(c->A.n, precision, L.vec[1], out, c->stream));
+    return PPG_OK;
+}
+
+ppg_status ppg_solve(ppg_ctx *c, const double *b, double *x, double tol, int restart, int maxit,
+                     const ppg_opts *opts, ppg_stats *stats)
+{
+    PPG_TRY(check_ctx(c));
+    PPG_TRY(set_device(c));
+    return solve_impl(c, b, x, tol, restart, maxit, opts, stats);
+}
+
+ppg_status ppg_solve_transpose(ppg_ctx *c, const double *g, double *lambda, double tol, int restart, int maxit,
+                               const ppg_opts *opts, ppg_stats *stats)
+{
+    PPG_TRY(check_ctx(c));
+    PPG_TRY(set_device(c));
+    if (!c->tctx) {
+        int *rpT = nullptr, *ciT = nullptr, *work = nullptr;
+        double *vaT = nullptr;
+        const long long n = c->A.n, nnz = c->A.nnz;
+        PPG_CK(cudaMalloc(&rpT, sizeof(int) * (n + 1)));
+        PPG_CK(cudaMalloc(&ciT, sizeof(int) * (nnz + 1)));
+        PPG_CK(cudaMalloc(&vaT, sizeof(double) * (nnz + 1)));
+        PPG_CK(cudaMalloc(&work, sizeof(int) * (n + 1)));
+        PPG_CK(launch_transpose(c->A, rpT, ciT, vaT, work, c->stream));
+        PPG_CK(cudaStreamSynchronize(c->stream));
+        ppg_status s = ppg_create(&c->tctx, n, nnz, rpT, ciT, vaT, c->stream);
+        cudaFree(rpT);
+        cudaFree(ciT);
+        cudaFree(vaT);
+        cudaFree(work);
+        if (s < 0) return s;
+    }
+    ppg_ctx *t = c->tctx;
+    t->stream = c->stream;
+    // p(A^T) = p(A)^T: the same polynomial, whatever its representation
+    t->has_poly = c->has_poly;
+    t->basis = c->basis;
+    t->degree = c->degree;
+    t->coef = c->coef;
+    t->roots = c->roots;
+    t->table = c->table;
+    t->poly_resid = c->poly_resid;
+    return solve_impl(t, g, lambda, tol, restart, maxit, opts, stats);
+}
+
+ppg_status ppg_csr_outer(ppg_ctx *c, const double *u, const double *v, double alpha, double *out)
+{
+    PPG_TRY(check_ctx(c));
+    if (!u || !v || !out) return fail(PPG_ERR_INVALID_ARG, "null vector");
+    PPG_TRY(set_device(c));
+    c->launches++;
+    PPG_CK(launch_csr_outer(c->A, u, v, alpha, out, c->stream));
+    return PPG_OK;
+}
+
+ppg_status ppg_arnoldi(ppg_ctx *c, const double *v, int k, double *V, double *H_h, int *steps)
+{
+    PPG_TRY(check_ctx(c));
+    if (!v || k < 1 || k > kKmax - 1) return fail(PPG_ERR_INVALID_ARG, "bad start vector or k");
+    PPG_TRY(set_device(c));
+    Layout L;
+    PPG_TRY(get_layout(c, k + 1, sizeof(double), &L));
+    int done = 0;
+    PPG_TRY(run_arnoldi(c, v, k, L, &done));
+    if (steps) *steps = done;
+    if (V) {
+        Exec ex{c, &c->A, kF64, c->stream};
+        for (int col = 0; col <= done; ++col) {
+            SpmvEpi e = epi_none();
+            e.out0 = vfix(V + (size_t)col * c->A.n);
+            e.u0 = vfix(L.basis + (size_t)col * c->ld * sizeof(double));
+            e.b0 = Scalar{1.0, c->st->sigma, col, 0, nullptr, 0, 0};
+            PPG_TRY(ex.axpy(e, kNoCheck));
+        }
+    }
+    if (H_h) {
+        PPG_CK(cudaMemcpy2DAsync(H_h, sizeof(double) * (k + 1), c->st->H, sizeof(double) * kLdH,
+                                 sizeof(double) * (k + 1), k, cudaMemcpyDeviceToHost, c->stream));
+    }
+    PPG_CK(cudaStreamSynchronize(c->stream));
+    return PPG_OK;
+}
+
+ppg_status ppg_hessenberg_eigs(ppg_ctx *c, int k, const double *H, int ld, double *wr, double *wi)
+{
+    PPG_TRY(check_ctx(c));
+    if (k < 1 || k > kSmallMax || ld < k || !H || !wr || !wi) return fail(PPG_ERR_INVALID_ARG, "bad arguments");
+    PPG_TRY(set_device(c));
+    PPG_CK(launch_hess_eigs(k, H, ld, wr, wi, c->d_info, c->stream));
+    PPG_CK(cudaMemcpyAsync(c->h_info, c->d_info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PPG_CK(cudaStreamSynchronize(c->stream));
+    if (c->h_info[0]) return fail(PPG_ERR_POLY_BREAKDOWN, "QR iteration did not converge");
+    return PPG_OK;
+}
+
+ppg_status ppg_fill_uniform(ppg_ctx *c, double *out, int64_t n, uint64_t seed)
+{
+    PPG_TRY(check_ctx(c));
+    if (!out || n < 0) return fail(PPG_ERR_INVALID_ARG, "bad output");
+    PPG_TRY(set_device(c));
+    PPG_CK(launch_fill_uniform(out, n, seed, c->stream));
+    return PPG_OK;
+}
+
+}  // extern "C"

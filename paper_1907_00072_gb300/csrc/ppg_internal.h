@@ -1,0 +1,101 @@
+// ppg_internal.h -- host-side launch interface between the library's translation units.
+#pragma once
+
+#include "ppg_common.cuh"
+
+namespace ppg {
+
+enum Prec : int { kF64 = 0, kF32 = 1 };
+
+// The context's device copy of the CSR matrix and the tiling chosen for it.
+struct DevMatrix {
+    int n;
+    long long nnz;
+    const int *rowptr;   // n + 1
+    const int *colidx;   // nnz (+ 16 bytes of padding)
+    const double *vals64;
+    const float *vals32;  // may be null until first needed
+    int rows_per_tile;    // rows of one SpMV tile (R); R * lanes_per_row == kThreads
+    int lanes_per_row;    // G
+    int cap64, cap32;     // non-zeros one tile can stage in shared memory
+    int num_sms;
+    int resid_blocks;     // grid of the persistent residual / norm kernels
+};
+
+// Fused SpMV epilogue (one row r, Ax = (A x)[r]):
+//   out0[r] = a0 * Ax + b0 * u0[r] + c0 * w0[r]
+//   out1[r] = a1 * Ax + b1 * u1[r] + c1 * w1[r]      (when out1 is set)
+// Null vectors drop their term.  out may alias its own u/w (same row is read then
+// written) but never x.
+struct SpmvEpi {
+    VecRef x;
+    VecRef out0, u0, w0;
+    VecRef out1, u1, w1;
+    Scalar a0, b0, c0, a1, b1, c1;
+};
+
+// Gram-Schmidt / basis kernels over the column-major basis U (ld entries per column).
+enum GsOp : int {
+    kGsDot = 1,        // h1 = sigma .* (U^T w), ||w||^2          -> finalize pass 1
+    kGsUpdDot = 2,     // w -= U coef; h2 = sigma .* (U^T w)      -> finalize pass 2
+    kGsUpdNorm = 3,    // out = w - U coef; ||out||^2             -> finalize pass 3 (Hessenberg column)
+    kGsCombine = 4,    // out = -U coef (cycle end: z = V y)
+};
+
+struct GsArgs {
+    const void *U;
+    long long ldu;
+    void *w;          // input vector (kGsDot, kGsUpdDot: updated in place)
+    void *out;        // kGsUpdNorm / kGsCombine output (VecRef-like, column follows j when out_follow)
+    int out_follow;   // 1: out = U + (j + 1) * ldu
+    int op;
+    int kcols_from_k; // 1: number of columns is Cycle::k (cycle end), else Cycle::j + 1
+    long long ntiles;
+    double *partials;
+    int nblk;
+};
+
+cudaError_t launch_validate(int n, long long nnz, const int *rowptr, const int *colidx, int *flag, cudaStream_t s);
+cudaError_t launch_cast_f32(const double *in, float *out, long long count, cudaStream_t s);
+// check: 0 always run; kSkipIfDone: return when the cycle is done (iteration kernels);
+// kSkipIfNoCols: return when the finished cycle has no columns to combine (cycle-end kernels).
+enum Check : int { kNoCheck = 0, kSkipIfDone = 1, kSkipIfNoCols = 2 };
+cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *st, int check, cudaStream_t s);
+cudaError_t launch_axpy(int n, int prec, const SpmvEpi &e, Cycle *st, int check, cudaStream_t s);
+// r = b - A x in float64 written as prec into out (column 0 of the basis); ||r|| finalises the
+// start of a restart cycle in st.
+cudaError_t launch_residual(const DevMatrix &A, int out_prec, const double *b, const double *x, void *out,
+                            Cycle *st, double *partials, cudaStream_t s);
+// ||v||: mode 0 stores ||v|| in st->bnorm; mode 1 starts an Arnoldi run from v (beta, sigma_0, copy into out)
+cudaError_t launch_norm_start(int n, int out_prec, const double *v, void *out, int mode, Cycle *st,
+                              double *partials, int nblk, cudaStream_t s);
+cudaError_t launch_xupdate(int n, int prec, const void *e, double *x, Cycle *st, cudaStream_t s);
+cudaError_t launch_copy_in(int n, int prec, const void *src, void *dst, cudaStream_t s);
+cudaError_t launch_fill_uniform(double *out, long long n, unsigned long long seed, cudaStream_t s);
+cudaError_t launch_csr_outer(const DevMatrix &A, const double *u, const double *v, double alpha, double *out,
+                             cudaStream_t s);
+cudaError_t launch_transpose(const DevMatrix &A, int *rpT, int *ciT, double *vaT, int *work, cudaStream_t s);
+
+// Gram-Schmidt passes (TMA-staged basis tiles).
+int gs_tile_rows(int prec, int kmax);
+size_t gs_smem_bytes(int prec, int kmax);
+int gs_grid(int prec, int kmax, long long ntiles, int num_sms);
+cudaError_t launch_gs(int prec, int kmax, const GsArgs &a, Cycle *st, cudaStream_t s);
+
+// Power-basis Gram matrix of Eq. 1 with Cholesky and the degree clamp (one kernel).
+cudaError_t launch_gram_cholesky(int n, long long ld, const double *B, int deg, double *partials, int nblk,
+                                 double *coef_out, int *info_out, Cycle *st, cudaStream_t s);
+int gram_grid(int num_sms);
+
+// Roots of 1 - z p(z): harmonic Ritz values of the Arnoldi Hessenberg matrix, Leja ordered.
+cudaError_t launch_roots(const Cycle *st, int k, double *roots_out /* 2k */, double *table_out, int *status_out,
+                         cudaStream_t s);
+cudaError_t launch_root_table(int k, const double *roots, double *table_out, int *status_out, cudaStream_t s);
+cudaError_t launch_hess_eigs(int k, const double *H, int ld, double *wr, double *wi, int *status_out,
+                             cudaStream_t s);
+// one-time kernel attribute setup (dynamic shared memory limits)
+cudaError_t spmv_configure(int cap64, int cap32);
+cudaError_t gs_configure();
+cudaError_t gram_configure();
+
+}  // namespace ppg

@@ -1,0 +1,585 @@
+// ppg_ortho.cu -- Gram-Schmidt and Gram-matrix kernels of the GB300 PP-GMRES library.
+//
+// Arnoldi orthogonalisation is classical Gram-Schmidt applied twice (Loe,
+// Thornquist, Boman, Section III: "two steps of Classical Gram Schmidt", two block
+// inner products and one norm per iteration).  With w = A p(A) v_j the three
+// passes over the basis are
+//   pass 1:  h1 = V^T w                         (block inner product, and ||w||^2)
+//   pass 2:  w <- w - V h1,  h2 = V^T w         (update fused with the second inner product)
+//   pass 3:  v_{j+1} <- w - V h2, ||v_{j+1}||^2 (update fused with the norm)
+// Each pass streams the basis once.  Tiles of the column-major basis (TR rows x k
+// columns) are staged in shared memory with TMA bulk copies, double-buffered across
+// a persistent grid, so the update and the inner product of pass 2 read each tile
+// from HBM once.  Per-CTA partial sums go to a [column x CTA] buffer and the last CTA
+// to finish reduces them in a fixed order (deterministic results) and finalises the
+// Hessenberg column on the device: Givens rotations and the convergence test of
+// GMRES never leave the GPU.
+#include <cuda_runtime.h>
+
+#include "ppg_internal.h"
+
+namespace ppg {
+
+template <typename T, int KM>
+struct GsCfg {
+    static constexpr int TR = (sizeof(T) == 8 ? 64 : 128) * 64 / KM;  // rows per tile
+    static constexpr int TPR = kThreads / TR;                           // threads per row (update phase)
+    static constexpr int RPL = TR / 32;                                 // rows per lane (dot phase)
+    static constexpr int CPW = KM / 8;                                  // columns per warp (dot phase)
+    static constexpr int STAGE = KM * TR + TR;                          // elements per pipeline stage
+};
+
+// Accumulator of a warp's column sums: float64 directly, or float32 with Kahan
+// compensation (float64 arithmetic is scarce on this GPU; the float32 basis is
+// reduced in float32 per lane and in float64 across lanes and CTAs).
+template <typename T>
+struct Acc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
+// ---------------------------------------------------------------- finalisation (last CTA, thread 0)
+
+__device__ void finish_pass1(Cycle *st, const double *tot, int k, double wsq)
+{
+    for (int c = 0; c < k; ++c) {
+        const double h = st->sigma[c] * tot[c];
+        st->h1[c] = h;
+        st->coef[c] = h * st->sigma[c];
+    }
+    st->w0sq = wsq;
+}
+
+__device__ void finish_pass2(Cycle *st, const double *tot, int k)
+{
+    for (int c = 0; c < k; ++c) {
+        const double h = st->sigma[c] * tot[c];
+        st->h2[c] = h;
+        st->coef[c] = h * st->sigma[c];
+    }
+}
+
+// Completes Hessenberg column j: H[0..j, j] = h1 + h2, H[j+1, j] = ||v_{j+1}||.  In GMRES
+// mode the previous Givens rotations are applied to the column, a new rotation zeroes
+// H[j+1, j] and updates g; the cycle ends on a small estimate |g_{j+1}|, a breakdown,
+// the restart length or the iteration limit, and then y = R^{-1} g is formed and the
+// coefficients of the correction z = V y are left in coef.
+__device__ void finish_pass3(Cycle *st, double nsq)
+{
+    const int j = st->j;
+    const double nrm = sqrt(nsq);
+    double *Hj = st->H + (long long)j * kLdH;
+    double *Rj = st->R + (long long)j * kLdH;
+    bool finite = isfinite(nrm);
+    for (int i = 0; i <= j; ++i) {
+        Hj[i] = st->h1[i] + st->h2[i];
+        finite = finite && isfinite(Hj[i]);
+    }
+    Hj[j + 1] = nrm;
+    if (!finite) {
+        st->error |= kErrNonfinite;
+        st->stop = 1;
+        st->cycle_done = 1;
+        st->k = 0;
+        st->j = j + 1;
+        return;
+    }
+    const bool brk = !(nrm > 1e-14 * sqrt(st->w0sq));
+    st->sigma[j + 1] = brk ? 0.0 : 1.0 / nrm;
+    st->iters += 1;
+    bool done = brk || (j + 1 >= st->m) || (st->iters >= st->maxit);
+    if (st->mode == 0) {
+        for (int i = 0; i <= j + 1; ++i) Rj[i] = Hj[i];
+        for (int i = 0; i < j; ++i) {
+            const double a = Rj[i], b = Rj[i + 1];
+            Rj[i] = st->cs[i] * a + st->sn[i] * b;
+            Rj[i + 1] = -st->sn[i] * a + st->cs[i] * b;
+        }
+        const double a = Rj[j], b = Rj[j + 1];
+        const double r = hypot(a, b);
+        double c = 1.0, s = 0.0;
+        if (r != 0.0) {
+            c = a / r;
+            s = b / r;
+        }
+        st->cs[j] = c;
+        st->sn[j] = s;
+        Rj[j] = r;
+        Rj[j + 1] = 0.0;
+        const double gj = st->g[j];
+        st->g[j] = c * gj;
+        st->g[j + 1] = -s * gj;
+        const double res = fabs(st->g[j + 1]);
+        st->est = res / st->bnorm;
+        done = done || (res <= st->tol * st->bnorm) || (st->inner_rtol > 0.0 && res <= st->inner_rtol * st->beta);
+    }
+    if (brk) {
+        st->breakdown = 1;
+        st->n_breakdowns += 1;
+    }
+    st->j = j + 1;
+    if (done) {
+        const int k = j + 1;
+        st->k = k;
+        st->cycle_done = 1;
+        if (st->mode == 0) {
+            for (int i = k - 1; i >= 0; --i) {
+                double v = st->g[i];
+                for (int q = i + 1; q < k; ++q) v -= st->R[i + (long long)q * kLdH] * st->y[q];
+                st->y[i] = v / st->R[i + (long long)i * kLdH];
+            }
+            for (int c = 0; c < k; ++c) st->coef[c] = -st->y[c] * st->sigma[c];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- the pass kernel
+
+template <typename T, int KM>
+__global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
+{
+    using C = GsCfg<T, KM>;
+    constexpr int TR = C::TR, TPR = C::TPR, RPL = C::RPL, CPW = C::CPW;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ T s_wn[TR];
+    __shared__ T s_part[TPR][TR];
+    __shared__ T s_coef[KM];
+    __shared__ double s_red[KM + 1];
+    __shared__ double scratch[33];
+    __shared__ int s_last;
+
+    const int op = a.op;
+    if (a.kcols_from_k) {
+        if (st->k == 0) return;
+    } else if (st->cycle_done) {
+        return;
+    }
+    const int k = a.kcols_from_k ? st->k : st->j + 1;
+    const T *__restrict__ U = (const T *)a.U;
+    T *w = (T *)a.w;
+    T *out = a.out_follow ? (T *)a.U + (long long)(st->j + 1) * a.ldu : (T *)a.out;
+    const bool need_w = (op != kGsCombine);
+    T *stage0 = reinterpret_cast<T *>(smem);
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    for (int c = tid; c < KM; c += kThreads) s_coef[c] = (c < k && op != kGsDot) ? (T)st->coef[c] : T(0);
+    __syncthreads();
+
+    auto issue = [&](long long tile, int stage) {
+        T *sU = stage0 + stage * C::STAGE;
+        const uint32_t colb = TR * (uint32_t)sizeof(T);
+        const uint32_t bytes = colb * (uint32_t)k + (need_w ? colb : 0u);
+        mbar_arrive_expect_tx(&bars[stage], bytes);
+        const long long row0 = tile * TR;
+        for (int c = 0; c < k; ++c) bulk_g2s(sU + c * TR, U + (long long)c * a.ldu + row0, colb, &bars[stage]);
+        if (need_w) bulk_g2s(sU + KM * TR, w + row0, colb, &bars[stage]);
+    };
+
+    if (tid == 0) {
+        long long t0 = blockIdx.x, t1 = blockIdx.x + (long long)gridDim.x;
+        if (t0 < a.ntiles) issue(t0, 0);
+        if (t1 < a.ntiles) issue(t1, 1);
+    }
+
+    Acc<T> acc[CPW];
+    double nrm = 0.0;
+    bool timed_out = false;
+    int it = 0;
+    for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+        const int stage = it & 1;
+        if (!mbar_wait_bounded(&bars[stage], (it >> 1) & 1, kWaitLimitNs)) {
+            timed_out = true;
+            break;
+        }
+        const T *sU = stage0 + stage * C::STAGE;
+        const T *sw = sU + KM * TR;
+        const long long row0 = tile * TR;
+        const T *dotvec = sw;
+        if (op != kGsDot) {
+            const int row = tid % TR, q = tid / TR;
+            T part = T(0);
+            for (int c = q; c < k; c += TPR) part = fma(sU[c * TR + row], s_coef[c], part);
+            s_part[q][row] = part;
+            __syncthreads();
+            if (tid < TR) {
+                T sum = s_part[0][row];
+#pragma unroll
+                for (int p = 1; p < TPR; ++p) sum += s_part[p][row];
+                const T wn = (op == kGsCombine ? T(0) : sw[row]) - sum;
+                if (op == kGsUpdDot) {
+                    w[row0 + row] = wn;
+                    s_wn[row] = wn;
+                } else {
+                    out[row0 + row] = wn;
+                    if (op == kGsUpdNorm) nrm += (double)wn * (double)wn;
+                }
+            }
+            __syncthreads();
+            dotvec = s_wn;
+        } else if (tid < TR) {
+            const double t = (double)sw[tid];
+            nrm += t * t;
+        }
+        if (op == kGsDot || op == kGsUpdDot) {
+            T wv[RPL];
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) wv[r] = dotvec[lane * RPL + r];
+#pragma unroll
+            for (int i = 0; i < CPW; ++i) {
+                const int c = wid + 8 * i;
+                if (c < k) {
+                    T s = T(0);
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r) s = fma(sU[c * TR + lane * RPL + r], wv[r], s);
+                    acc[i].add(s);
+                }
+            }
+        }
+        __syncthreads();  // every thread is done with this stage
+        if (tid == 0) {
+            const long long nt = tile + 2LL * gridDim.x;
+            if (nt < a.ntiles) {
+                fence_proxy_async_smem();
+                issue(nt, stage);
+            }
+        }
+    }
+    if (timed_out) {
+        if (tid == 0) atomicOr(&st->error, kErrTimeout);
+        // copies already issued into either stage may still land: wait for them (bounded) first
+        mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimitNs);
+        mbar_wait_bounded(&bars[(it + 1) & 1], ((it + 1) >> 1) & 1, kWaitLimitNs);
+        return;
+    }
+
+    // per-CTA partial sums
+    if (op == kGsDot || op == kGsUpdDot) {
+#pragma unroll
+        for (int i = 0; i < CPW; ++i) {
+            const int c = wid + 8 * i;
+            if (c < k) {
+                const double v = warp_sum(acc[i].get());
+                if (lane == 0) a.partials[(long long)c * a.nblk + blockIdx.x] = v;
+            }
+        }
+    }
+    if (op != kGsCombine) {
+        nrm = block_sum(nrm, scratch);
+        if (tid == 0) a.partials[(long long)kKmax * a.nblk + blockIdx.x] = nrm;
+    }
+    if (op == kGsCombine) return;
+
+    if (last_block_done(&st->ticket[2 + op], &s_last)) {
+        if (op != kGsUpdNorm) {
+            for (int c = wid; c < k; c += 8) {
+                const double v = reduce_partials(a.partials, a.nblk, c);
+                if (lane == 0) s_red[c] = v;
+            }
+        }
+        if (wid == 0) {
+            const double v = reduce_partials(a.partials, a.nblk, kKmax);
+            if (lane == 0) s_red[KM] = v;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (op == kGsDot)
+                finish_pass1(st, s_red, k, s_red[KM]);
+            else if (op == kGsUpdDot)
+                finish_pass2(st, s_red, k);
+            else
+                finish_pass3(st, s_red[KM]);
+            st->ticket[2 + op] = 0;
+        }
+    }
+}
+
+int gs_tile_rows(int prec, int kmax)
+{
+    if (prec == kF64) return kmax <= 64 ? GsCfg<double, 64>::TR : GsCfg<double, 128>::TR;
+    return kmax <= 64 ? GsCfg<float, 64>::TR : GsCfg<float, 128>::TR;
+}
+
+size_t gs_smem_bytes(int prec, int kmax)
+{
+    if (prec == kF64)
+        return 2 * sizeof(double) * (kmax <= 64 ? GsCfg<double, 64>::STAGE : GsCfg<double, 128>::STAGE);
+    return 2 * sizeof(float) * (kmax <= 64 ? GsCfg<float, 64>::STAGE : GsCfg<float, 128>::STAGE);
+}
+
+template <typename T, int KM>
+static int gs_blocks_per_sm()
+{
+    int nb = 0;
+    const size_t smem = 2 * sizeof(T) * GsCfg<T, KM>::STAGE;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gs<T, KM>, kThreads, smem);
+    return nb > 0 ? nb : 1;
+}
+
+int gs_grid(int prec, int kmax, long long ntiles, int num_sms)
+{
+    int per = 1;
+    if (prec == kF64)
+        per = kmax <= 64 ? gs_blocks_per_sm<double, 64>() : gs_blocks_per_sm<double, 128>();
+    else
+        per = kmax <= 64 ? gs_blocks_per_sm<float, 64>() : gs_blocks_per_sm<float, 128>();
+    long long g = (long long)per * num_sms;
+    if (g > ntiles) g = ntiles;
+    return (int)(g > 0 ? g : 1);
+}
+
+template <typename T, int KM>
+static cudaError_t gs_configure_one()
+{
+    return cudaFuncSetAttribute(k_gs<T, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * sizeof(T) * GsCfg<T, KM>::STAGE));
+}
+
+cudaError_t gs_configure()
+{
+    cudaError_t e = gs_configure_one<double, 64>();
+    if (e == cudaSuccess) e = gs_configure_one<double, 128>();
+    if (e == cudaSuccess) e = gs_configure_one<float, 64>();
+    if (e == cudaSuccess) e = gs_configure_one<float, 128>();
+    return e;
+}
+
+cudaError_t launch_gs(int prec, int kmax, const GsArgs &a, Cycle *st, cudaStream_t s)
+{
+    const size_t smem = gs_smem_bytes(prec, kmax);
+    if (prec == kF64) {
+        if (kmax <= 64)
+            k_gs<double, 64><<<a.nblk, kThreads, smem, s>>>(a, st);
+        else
+            k_gs<double, 128><<<a.nblk, kThreads, smem, s>>>(a, st);
+    } else {
+        if (kmax <= 64)
+            k_gs<float, 64><<<a.nblk, kThreads, smem, s>>>(a, st);
+        else
+            k_gs<float, 128><<<a.nblk, kThreads, smem, s>>>(a, st);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Gram matrix of Eq. 1 and its Cholesky solve
+
+// B holds the power basis [v0, A v0, ..., A^{d+1} v0] column-major (ld rows per column,
+// rows beyond n zero).  One streaming pass forms every inner product B_a . B_b
+// (0 <= a <= b <= d+1) from TMA-staged row tiles; the last CTA reduces them, factors
+// G = (AV)^T AV (columns 1..d+1) by Cholesky with LAPACK POTRF's test (a pivot that is
+// not > 0, NaN included, stops the factorisation with info = its 1-based order), and
+// solves G y = (AV)^T v0 with the leading block that factored.  The degree used is d
+// when info = 0, else info - 2 (the largest degree with no Cholesky failure, Section IV).
+constexpr int kGramTR = 64;
+constexpr int kGramStride = kGramTR + 2;  // padded column stride: 16-byte aligned, spreads banks
+constexpr int kGramCols = 64;             // d + 2 <= 64
+constexpr int kGramPairsPerThread = (kGramCols * (kGramCols + 1) / 2 + kThreads - 1) / kThreads;
+
+__global__ void __launch_bounds__(kThreads) k_gram_cholesky(int n, long long ld, const double *__restrict__ B,
+                                                             int deg, long long ntiles, double *partials,
+                                                             double *coef_out, int *info_out, Cycle *st)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_last;
+    __shared__ int s_info;
+    double *stage0 = reinterpret_cast<double *>(smem);
+    const int ncol = deg + 2;
+    const int npair = ncol * (ncol + 1) / 2;
+    const int tid = threadIdx.x;
+    constexpr int TR = kGramTR;
+    const long long stage_elems = (long long)kGramCols * kGramStride;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](long long tile, int stage) {
+        double *sB = stage0 + stage * stage_elems;
+        const uint32_t colb = TR * 8u;
+        mbar_arrive_expect_tx(&bars[stage], colb * (uint32_t)ncol);
+        for (int c = 0; c < ncol; ++c) bulk_g2s(sB + c * kGramStride, B + c * ld + tile * TR, colb, &bars[stage]);
+    };
+    if (tid == 0) {
+        if (blockIdx.x < ntiles) issue(blockIdx.x, 0);
+        if (blockIdx.x + (long long)gridDim.x < ntiles) issue(blockIdx.x + (long long)gridDim.x, 1);
+    }
+    // pair p -> (a, b), a <= b, row-major over the upper triangle
+    int pa[kGramPairsPerThread], pb[kGramPairsPerThread];
+    double acc[kGramPairsPerThread];
+#pragma unroll
+    for (int i = 0; i < kGramPairsPerThread; ++i) {
+        int p = tid + i * kThreads;
+        int a = 0, b = 0;
+        if (p < npair) {
+            int rem = p;
+            a = 0;
+            while (rem >= ncol - a) {
+                rem -= ncol - a;
+                ++a;
+            }
+            b = a + rem;
+        }
+        pa[i] = a;
+        pb[i] = b;
+        acc[i] = 0.0;
+    }
+    bool timed_out = false;
+    int it = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int stage = it & 1;
+        if (!mbar_wait_bounded(&bars[stage], (it >> 1) & 1, kWaitLimitNs)) {
+            timed_out = true;
+            break;
+        }
+        const double *sB = stage0 + stage * stage_elems;
+#pragma unroll
+        for (int i = 0; i < kGramPairsPerThread; ++i) {
+            if (tid + i * kThreads < npair) {
+                const double *x = sB + pa[i] * kGramStride, *y = sB + pb[i] * kGramStride;
+                double s = 0.0;
+                for (int r = 0; r < TR; ++r) s = fma(x[r], y[r], s);
+                acc[i] += s;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const long long nt = tile + 2LL * gridDim.x;
+            if (nt < ntiles) {
+                fence_proxy_async_smem();
+                issue(nt, stage);
+            }
+        }
+    }
+    if (timed_out) {
+        if (tid == 0) atomicOr(&st->error, kErrTimeout);
+        // copies already issued into either stage may still land: wait for them (bounded) first
+        mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimitNs);
+        mbar_wait_bounded(&bars[(it + 1) & 1], ((it + 1) >> 1) & 1, kWaitLimitNs);
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < kGramPairsPerThread; ++i) {
+        const int p = tid + i * kThreads;
+        if (p < npair) partials[(long long)p * gridDim.x + blockIdx.x] = acc[i];
+    }
+    if (!last_block_done(&st->ticket[7], &s_last)) return;
+
+    // ---- last CTA: reduce, factor, solve
+    const int kk = deg + 1;
+    double *G = stage0;             // kk x kk, column-major (ld kk)
+    double *r = stage0 + kk * kk;   // kk
+    double *y = r + kk;             // kk
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int p = wid; p < npair; p += kThreads / 32) {
+        const double v = reduce_partials(partials, gridDim.x, p);
+        if (lane == 0) {
+            int rem = p, a = 0;
+            while (rem >= ncol - a) {
+                rem -= ncol - a;
+                ++a;
+            }
+            const int b = a + rem;
+            if (a == 0) {
+                if (b > 0) r[b - 1] = v;
+            } else {
+                G[(a - 1) + (b - 1) * kk] = v;
+                G[(b - 1) + (a - 1) * kk] = v;
+            }
+        }
+    }
+    if (tid == 0) s_info = 0;
+    __syncthreads();
+    for (int j = 0; j < kk; ++j) {
+        if (tid == 0) {
+            double d = G[j + j * kk];
+            for (int p = 0; p < j; ++p) d -= G[j + p * kk] * G[j + p * kk];
+            if (!(d > 0.0))
+                s_info = j + 1;
+            else
+                G[j + j * kk] = sqrt(d);
+        }
+        __syncthreads();
+        if (s_info) break;
+        const double ljj = G[j + j * kk];
+        for (int i = j + 1 + tid; i < kk; i += kThreads) {
+            double s = G[i + j * kk];
+            for (int p = 0; p < j; ++p) s -= G[i + p * kk] * G[j + p * kk];
+            G[i + j * kk] = s / ljj;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int info = s_info;
+        const int used = info ? info - 2 : deg;
+        for (int i = 0; i < kk; ++i) y[i] = 0.0;
+        const int m = used + 1;
+        for (int i = 0; i < m; ++i) {
+            double s = r[i];
+            for (int p = 0; p < i; ++p) s -= G[i + p * kk] * y[p];
+            y[i] = s / G[i + i * kk];
+        }
+        for (int i = m - 1; i >= 0; --i) {
+            double s = y[i];
+            for (int p = i + 1; p < m; ++p) s -= G[p + i * kk] * y[p];
+            y[i] = s / G[i + i * kk];
+        }
+        bool finite = true;
+        for (int i = 0; i < kk; ++i) {
+            coef_out[i] = (i < m) ? y[i] : 0.0;
+            finite = finite && isfinite(coef_out[i]);
+        }
+        info_out[0] = info;
+        info_out[1] = used;
+        info_out[2] = finite ? 1 : 0;
+        st->ticket[7] = 0;
+    }
+}
+
+int gram_grid(int num_sms)
+{
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gram_cholesky, kThreads,
+                                                  2 * sizeof(double) * kGramCols * kGramStride);
+    if (per < 1) per = 1;
+    return per * num_sms;
+}
+
+cudaError_t gram_configure()
+{
+    return cudaFuncSetAttribute(k_gram_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * sizeof(double) * kGramCols * kGramStride));
+}
+
+cudaError_t launch_gram_cholesky(int n, long long ld, const double *B, int deg, double *partials, int nblk,
+                                 double *coef_out, int *info_out, Cycle *st, cudaStream_t s)
+{
+    const long long ntiles = ld / kGramTR;
+    int grid = nblk;
+    if (grid > ntiles) grid = (int)ntiles;
+    k_gram_cholesky<<<grid, kThreads, 2 * sizeof(double) * kGramCols * kGramStride, s>>>(n, ld, B, deg, ntiles, partials,
+                                                                                    coef_out, info_out, st);
+    return cudaGetLastError();
+}
+
+}  // namespace ppg

@@ -1,0 +1,550 @@
+// ppg_spmv.cu -- CSR sparse matrix-vector kernels of the GB300 PP-GMRES library.
+//
+// The polynomial preconditioner is applied as a chain of SpMVs and vector
+// updates (Loe, Thornquist, Boman, Section II, Eq. 2: p(A) = y_{d+1} A^d + ... + y_1).
+// Each link of the chain is one launch of k_spmv: a row-block CSR kernel whose
+// tile of non-zeros is staged in shared memory by TMA bulk copies, followed by
+// a fused epilogue that forms the Horner step (w <- A w + y_j v) or a root-form
+// step in the same pass, so every vector crosses HBM once per step.
+#include <cuda_runtime.h>
+
+#include "ppg_internal.h"
+
+namespace ppg {
+
+// ---------------------------------------------------------------- validation and conversion
+
+__global__ void k_validate(int n, long long nnz, const int *__restrict__ rowptr, const int *__restrict__ colidx,
+                           int *flag)
+{
+    long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = tid; i <= n; i += stride) {
+        int v = rowptr[i];
+        if (i == 0 && v != 0) atomicOr(flag, 1);
+        if (i == n && (long long)v != nnz) atomicOr(flag, 2);
+        if (i < n && rowptr[i + 1] < v) atomicOr(flag, 4);
+    }
+    for (long long k = tid; k < nnz; k += stride) {
+        int c = colidx[k];
+        if (c < 0 || c >= n) atomicOr(flag, 8);
+    }
+}
+
+cudaError_t launch_validate(int n, long long nnz, const int *rowptr, const int *colidx, int *flag, cudaStream_t s)
+{
+    k_validate<<<1024, kThreads, 0, s>>>(n, nnz, rowptr, colidx, flag);
+    return cudaGetLastError();
+}
+
+__global__ void k_cast_f32(const double *__restrict__ in, float *__restrict__ out, long long count)
+{
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += stride)
+        out[i] = (float)in[i];
+}
+
+cudaError_t launch_cast_f32(const double *in, float *out, long long count, cudaStream_t s)
+{
+    k_cast_f32<<<2048, kThreads, 0, s>>>(in, out, count);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- the fused SpMV step
+
+template <typename T>
+struct SpmvArgs {
+    int n;
+    const int *rowptr;
+    const int *colidx;
+    const T *vals;
+    int rows_per_tile;
+    int lanes_per_row;
+    int cap;  // elements of each staging array
+    Cycle *st;
+    int check_done;
+    SpmvEpi e;
+};
+
+// One CTA per tile of R consecutive rows.  Thread 0 copies the tile's contiguous
+// range of values and column indices into shared memory with two TMA bulk copies
+// (ranges widened to 16-byte boundaries); then G = 256/R lanes per row form the
+// row's dot product, gathering x (resident in L2 for these problem sizes), and the
+// first lane of each row applies the epilogue.  Tiles whose non-zeros exceed the
+// staging capacity read the matrix directly from global memory.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_spmv(SpmvArgs<T> a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_rp[kThreads + 1];
+    __shared__ double s_coef[6];
+
+    Cycle *st = a.st;
+    if (a.check_done == kSkipIfDone && st->cycle_done) return;
+    if (a.check_done == kSkipIfNoCols && st->k == 0) return;
+
+    const int R = a.rows_per_tile;
+    const int G = a.lanes_per_row;
+    const int r0 = blockIdx.x * R;
+    const int rows = min(R, a.n - r0);
+    T *s_val = reinterpret_cast<T *>(smem);
+    int *s_col = reinterpret_cast<int *>(smem + ((a.cap * sizeof(T) + 127) & ~(size_t)127));
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    for (int t = threadIdx.x; t <= rows; t += blockDim.x) s_rp[t] = a.rowptr[r0 + t];
+    switch (threadIdx.x) {
+    case 0: s_coef[0] = resolve(a.e.a0, st); break;
+    case 1: s_coef[1] = resolve(a.e.b0, st); break;
+    case 2: s_coef[2] = resolve(a.e.c0, st); break;
+    case 3: s_coef[3] = resolve(a.e.a1, st); break;
+    case 4: s_coef[4] = resolve(a.e.b1, st); break;
+    case 5: s_coef[5] = resolve(a.e.c1, st); break;
+    default: break;
+    }
+    __syncthreads();
+
+    const int s = s_rp[0], e = s_rp[rows];
+    constexpr int VA = 16 / (int)sizeof(T);
+    const int vs = s & ~(VA - 1), ve = (e + VA - 1) & ~(VA - 1);
+    const int cs = s & ~3, ce = (e + 3) & ~3;
+    const bool staged = (ve - vs) <= a.cap && (ce - cs) <= a.cap;
+
+    if (staged && e > s) {
+        if (threadIdx.x == 0) {
+            const uint32_t vb = (uint32_t)(ve - vs) * (uint32_t)sizeof(T);
+            const uint32_t cb = (uint32_t)(ce - cs) * 4u;
+            mbar_arrive_expect_tx(&bar, vb + cb);
+            bulk_g2s(s_val, a.vals + vs, vb, &bar);
+            bulk_g2s(s_col, a.colidx + cs, cb, &bar);
+        }
+        if (!mbar_wait_bounded(&bar, 0, kWaitLimitNs)) {
+            if (threadIdx.x == 0) atomicOr(&st->error, kErrTimeout);
+            mbar_wait_bounded(&bar, 0, kWaitLimitNs);  // let the copy land before the CTA exits
+            return;
+        }
+    }
+
+    const T *__restrict__ x = resolve_ptr<T>(a.e.x, st);
+    const int lr = threadIdx.x / G;
+    const int lane = threadIdx.x & (G - 1);
+    T acc = T(0);
+    if (lr < rows) {
+        const int k0 = s_rp[lr], k1 = s_rp[lr + 1];
+        int k = k0 + lane;
+        if (staged) {
+            for (; k + 3 * G < k1; k += 4 * G) {
+                const int c0 = s_col[k - cs], c1 = s_col[k + G - cs];
+                const int c2 = s_col[k + 2 * G - cs], c3 = s_col[k + 3 * G - cs];
+                const T x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+                acc = fma(s_val[k - vs], x0, acc);
+                acc = fma(s_val[k + G - vs], x1, acc);
+                acc = fma(s_val[k + 2 * G - vs], x2, acc);
+                acc = fma(s_val[k + 3 * G - vs], x3, acc);
+            }
+            for (; k < k1; k += G) acc = fma(s_val[k - vs], __ldg(x + s_col[k - cs]), acc);
+        } else {
+            for (; k < k1; k += G) acc = fma(__ldg(a.vals + k), __ldg(x + __ldg(a.colidx + k)), acc);
+        }
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+
+    if (lane == 0 && lr < rows) {
+        const int r = r0 + lr;
+        {
+            T *o0 = resolve_ptr<T>(a.e.out0, st);
+            const T *u0 = resolve_ptr<T>(a.e.u0, st);
+            const T *w0 = resolve_ptr<T>(a.e.w0, st);
+            T v = (T)s_coef[0] * acc;
+            if (u0) v = fma((T)s_coef[1], u0[r], v);
+            if (w0) v = fma((T)s_coef[2], w0[r], v);
+            o0[r] = v;
+        }
+        T *o1 = resolve_ptr<T>(a.e.out1, st);
+        if (o1) {
+            const T *u1 = resolve_ptr<T>(a.e.u1, st);
+            const T *w1 = resolve_ptr<T>(a.e.w1, st);
+            T v = (T)s_coef[3] * acc;
+            if (u1) v = fma((T)s_coef[4], u1[r], v);
+            if (w1) v = fma((T)s_coef[5], w1[r], v);
+            o1[r] = v;
+        }
+    }
+}
+
+static size_t spmv_smem(int cap, size_t tsize) { return ((cap * tsize + 127) & ~(size_t)127) + (size_t)cap * 4; }
+
+cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *st, int check_done, cudaStream_t s)
+{
+    const int R = A.rows_per_tile;
+    const int grid = (A.n + R - 1) / R;
+    if (prec == kF64) {
+        SpmvArgs<double> a{A.n, A.rowptr, A.colidx, A.vals64, R, A.lanes_per_row, A.cap64, st, check_done, e};
+        k_spmv<double><<<grid, kThreads, spmv_smem(A.cap64, 8), s>>>(a);
+    } else {
+        SpmvArgs<float> a{A.n, A.rowptr, A.colidx, A.vals32, R, A.lanes_per_row, A.cap32, st, check_done, e};
+        k_spmv<float><<<grid, kThreads, spmv_smem(A.cap32, 4), s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+// Set once per process: the SpMV kernels may use more than 48 KB of dynamic shared memory.
+cudaError_t spmv_configure(int cap64, int cap32)
+{
+    cudaError_t err = cudaFuncSetAttribute(k_spmv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)spmv_smem(cap64, 8));
+    if (err != cudaSuccess) return err;
+    return cudaFuncSetAttribute(k_spmv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)spmv_smem(cap32, 4));
+}
+
+// ---------------------------------------------------------------- matrix-free epilogue (last root of the product form)
+
+template <typename T>
+__global__ void k_axpy(int n, SpmvEpi e, Cycle *st, int check)
+{
+    if (check == kSkipIfDone && st->cycle_done) return;
+    if (check == kSkipIfNoCols && st->k == 0) return;
+    T *o0 = resolve_ptr<T>(e.out0, st);
+    const T *u0 = resolve_ptr<T>(e.u0, st);
+    const T *w0 = resolve_ptr<T>(e.w0, st);
+    const T b0 = (T)resolve(e.b0, st), c0 = (T)resolve(e.c0, st);
+    const int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        T v = T(0);
+        if (u0) v = b0 * u0[r];
+        if (w0) v = fma(c0, w0[r], v);
+        o0[r] = v;
+    }
+}
+
+cudaError_t launch_axpy(int n, int prec, const SpmvEpi &e, Cycle *st, int check, cudaStream_t s)
+{
+    int grid = (n + kThreads - 1) / kThreads;
+    if (grid > 8192) grid = 8192;
+    if (prec == kF64)
+        k_axpy<double><<<grid, kThreads, 0, s>>>(n, e, st, check);
+    else
+        k_axpy<float><<<grid, kThreads, 0, s>>>(n, e, st, check);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- true residual and cycle start
+
+// Starts a restart cycle from r = b - A x (float64), stored in basis column 0 as
+// U_0 = r with sigma_0 = 1/||r||: tests convergence (relative residual, Section III),
+// the iteration limit and finiteness, and resets the Givens right-hand side g = beta e_1.
+__device__ void finish_residual(Cycle *st, double sumsq)
+{
+    const double beta = sqrt(sumsq);
+    st->beta = beta;
+    st->relres = beta / st->bnorm;
+    st->k = 0;
+    st->j = 0;
+    st->breakdown = 0;
+    if (!isfinite(beta)) {
+        st->error |= kErrNonfinite;
+        st->stop = 1;
+    } else if (st->relres <= st->tol) {
+        st->converged = 1;
+        st->stop = 1;
+    } else if (st->iters >= st->maxit) {
+        st->stop = 1;
+    }
+    if (st->stop) {
+        st->cycle_done = 1;
+        return;
+    }
+    st->cycle_done = 0;
+    st->cycles += 1;
+    st->sigma[0] = 1.0 / beta;
+    for (int i = 0; i <= st->m; ++i) st->g[i] = 0.0;
+    st->g[0] = beta;
+}
+
+template <typename Tout>
+__global__ void __launch_bounds__(kThreads) k_residual(int n, const int *__restrict__ rowptr,
+                                                       const int *__restrict__ colidx,
+                                                       const double *__restrict__ vals, const double *__restrict__ b,
+                                                       const double *__restrict__ x, Tout *__restrict__ out, Cycle *st,
+                                                       double *partials)
+{
+    __shared__ double scratch[33];
+    __shared__ int s_last;
+    if (st->stop) return;
+    double nrm = 0.0;
+    const int stride = gridDim.x * blockDim.x;
+    // one warp handles 32 consecutive rows; each lane walks its own row
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        double acc = 0.0;
+        const int k1 = rowptr[r + 1];
+        for (int k = rowptr[r]; k < k1; ++k) acc = fma(vals[k], x[colidx[k]], acc);
+        const double v = b[r] - acc;
+        out[r] = (Tout)v;
+        nrm = fma(v, v, nrm);
+    }
+    nrm = block_sum(nrm, scratch);
+    if (threadIdx.x == 0) partials[blockIdx.x] = nrm;
+    if (last_block_done(&st->ticket[0], &s_last)) {
+        if (threadIdx.x < 32) {
+            const double tot = reduce_partials(partials, gridDim.x, 0);
+            if (threadIdx.x == 0) {
+                finish_residual(st, tot);
+                st->ticket[0] = 0;
+            }
+        }
+    }
+}
+
+cudaError_t launch_residual(const DevMatrix &A, int out_prec, const double *b, const double *x, void *out, Cycle *st,
+                            double *partials, cudaStream_t s)
+{
+    const int grid = A.resid_blocks;
+    if (out_prec == kF64)
+        k_residual<double><<<grid, kThreads, 0, s>>>(A.n, A.rowptr, A.colidx, A.vals64, b, x, (double *)out, st,
+                                                     partials);
+    else
+        k_residual<float><<<grid, kThreads, 0, s>>>(A.n, A.rowptr, A.colidx, A.vals64, b, x, (float *)out, st,
+                                                    partials);
+    return cudaGetLastError();
+}
+
+// ||v||.  mode 0: st->bnorm = ||v|| (right-hand side).  mode 1: start an Arnoldi run from v:
+// out = v (converted), beta = ||v||, sigma_0 = 1/beta, j = 0.
+template <typename Tout>
+__global__ void __launch_bounds__(kThreads) k_norm_start(int n, const double *__restrict__ v, Tout *__restrict__ out,
+                                                         int mode, Cycle *st, double *partials)
+{
+    __shared__ double scratch[33];
+    __shared__ int s_last;
+    double acc = 0.0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const double t = v[r];
+        acc = fma(t, t, acc);
+        if (out) out[r] = (Tout)t;
+    }
+    acc = block_sum(acc, scratch);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    if (last_block_done(&st->ticket[1], &s_last)) {
+        if (threadIdx.x < 32) {
+            const double tot = reduce_partials(partials, gridDim.x, 0);
+            if (threadIdx.x == 0) {
+                const double nv = sqrt(tot);
+                if (mode == 0) {
+                    st->bnorm = nv;
+                } else {
+                    st->beta = nv;
+                    st->bnorm = nv;
+                    st->sigma[0] = (nv > 0.0) ? 1.0 / nv : 0.0;
+                    st->j = 0;
+                    st->k = 0;
+                    st->cycle_done = (nv > 0.0 && isfinite(nv)) ? 0 : 1;
+                    if (!isfinite(nv)) st->error |= kErrNonfinite;
+                    st->breakdown = 0;
+                    for (int i = 0; i <= st->m; ++i) st->g[i] = 0.0;
+                    st->g[0] = nv;
+                }
+                st->ticket[1] = 0;
+            }
+        }
+    }
+}
+
+cudaError_t launch_norm_start(int n, int out_prec, const double *v, void *out, int mode, Cycle *st, double *partials,
+                              int nblk, cudaStream_t s)
+{
+    if (out_prec == kF64)
+        k_norm_start<double><<<nblk, kThreads, 0, s>>>(n, v, (double *)out, mode, st, partials);
+    else
+        k_norm_start<float><<<nblk, kThreads, 0, s>>>(n, v, (float *)out, mode, st, partials);
+    return cudaGetLastError();
+}
+
+// x += e (e in the inner precision), skipped when the cycle produced no columns.
+template <typename Te>
+__global__ void k_xupdate(int n, const Te *__restrict__ e, double *__restrict__ x, Cycle *st)
+{
+    if (st->k == 0) return;
+    const int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) x[r] += (double)e[r];
+}
+
+cudaError_t launch_xupdate(int n, int prec, const void *e, double *x, Cycle *st, cudaStream_t s)
+{
+    int grid = (n + kThreads - 1) / kThreads;
+    if (grid > 8192) grid = 8192;
+    if (prec == kF64)
+        k_xupdate<double><<<grid, kThreads, 0, s>>>(n, (const double *)e, x, st);
+    else
+        k_xupdate<float><<<grid, kThreads, 0, s>>>(n, (const float *)e, x, st);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_copy_in(int n, const T *__restrict__ src, T *__restrict__ dst)
+{
+    const int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) dst[r] = src[r];
+}
+
+cudaError_t launch_copy_in(int n, int prec, const void *src, void *dst, cudaStream_t s)
+{
+    int grid = (n + kThreads - 1) / kThreads;
+    if (grid > 8192) grid = 8192;
+    if (prec == kF64)
+        k_copy_in<double><<<grid, kThreads, 0, s>>>(n, (const double *)src, (double *)dst);
+    else
+        k_copy_in<float><<<grid, kThreads, 0, s>>>(n, (const float *)src, (float *)dst);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- SplitMix64 (Steele, Lea, Flood 2014)
+
+__device__ __forceinline__ unsigned long long splitmix_mix(unsigned long long z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_fill_uniform(double *out, long long n, unsigned long long seed)
+{
+    const unsigned long long base = splitmix_mix(seed);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned long long z = splitmix_mix(base + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull);
+        const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+        out[i] = -1.0 + 2.0 * u;
+    }
+}
+
+cudaError_t launch_fill_uniform(double *out, long long n, unsigned long long seed, cudaStream_t s)
+{
+    k_fill_uniform<<<2048, kThreads, 0, s>>>(out, n, seed);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- adjoint helpers
+
+// out_k = alpha * u_{row(k)} * v_{col(k)} over the CSR pattern (dL/dvals = -lambda_i x_j).
+__global__ void k_csr_outer(int n, const int *__restrict__ rowptr, const int *__restrict__ colidx,
+                            const double *__restrict__ u, const double *__restrict__ v, double alpha,
+                            double *__restrict__ out)
+{
+    const int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const double ur = alpha * u[r];
+        for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) out[k] = ur * v[colidx[k]];
+    }
+}
+
+cudaError_t launch_csr_outer(const DevMatrix &A, const double *u, const double *v, double alpha, double *out,
+                             cudaStream_t s)
+{
+    int grid = (A.n + kThreads - 1) / kThreads;
+    if (grid > 8192) grid = 8192;
+    k_csr_outer<<<grid, kThreads, 0, s>>>(A.n, A.rowptr, A.colidx, u, v, alpha, out);
+    return cudaGetLastError();
+}
+
+// Transpose by counting sort: column counts (atomics), an exclusive scan (single CTA,
+// chunked), a scatter that walks each source row in order, and a per-row sort that makes
+// the order within each row of A^T ascending and independent of atomic timing.
+__global__ void k_count_cols(long long nnz, const int *__restrict__ colidx, int *counts)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += stride)
+        atomicAdd(&counts[colidx[k] + 1], 1);
+}
+
+// in-place inclusive scan of counts[0..n] by one CTA (counts[0] = 0 gives exclusive offsets)
+__global__ void k_scan_single(int n1, int *data)
+{
+    __shared__ int s_carry;
+    __shared__ int s_warp[32];
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < n1; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        int v = (i < n1) ? data[i] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) s_warp[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            int w = (lane < (int)(blockDim.x >> 5)) ? s_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int add = s_carry + (wid > 0 ? s_warp[wid - 1] : 0);
+        if (i < n1) data[i] = v + add;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = add + v;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scatter_t(int n, const int *__restrict__ rowptr, const int *__restrict__ colidx,
+                            const double *__restrict__ vals, const int *__restrict__ rpT, int *fill, int *ciT,
+                            double *vaT)
+{
+    const int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+            const int c = colidx[k];
+            const int dst = rpT[c] + atomicAdd(&fill[c], 1);
+            ciT[dst] = r;
+            vaT[dst] = vals[k];
+        }
+    }
+}
+
+__global__ void k_sort_rows(int n, const int *__restrict__ rpT, int *ciT, double *vaT)
+{
+    const int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const int s = rpT[r], e = rpT[r + 1];
+        for (int i = s + 1; i < e; ++i) {  // insertion sort: rows are short
+            const int c = ciT[i];
+            const double v = vaT[i];
+            int j = i - 1;
+            while (j >= s && ciT[j] > c) {
+                ciT[j + 1] = ciT[j];
+                vaT[j + 1] = vaT[j];
+                --j;
+            }
+            ciT[j + 1] = c;
+            vaT[j + 1] = v;
+        }
+    }
+}
+
+cudaError_t launch_transpose(const DevMatrix &A, int *rpT, int *ciT, double *vaT, int *work, cudaStream_t s)
+{
+    cudaError_t err = cudaMemsetAsync(rpT, 0, sizeof(int) * (A.n + 1), s);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(work, 0, sizeof(int) * A.n, s);
+    if (err != cudaSuccess) return err;
+    k_count_cols<<<1024, kThreads, 0, s>>>(A.nnz, A.colidx, rpT);
+    k_scan_single<<<1, 1024, 0, s>>>(A.n + 1, rpT);
+    int grid = (A.n + kThreads - 1) / kThreads;
+    if (grid > 8192) grid = 8192;
+    k_scatter_t<<<grid, kThreads, 0, s>>>(A.n, A.rowptr, A.colidx, A.vals64, rpT, work, ciT, vaT);
+    k_sort_rows<<<grid, kThreads, 0, s>>>(A.n, rpT, ciT, vaT);
+    return cudaGetLastError();
+}
+
+}  // namespace ppg

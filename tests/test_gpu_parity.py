@@ -1,0 +1,488 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every input is seeded and synthetic (workloads/).  Tolerances:
+  * SpMV, float64: |y_gpu - y_ref| <= 4 u sum_k |a_ik x_k| per row (u = 2^-53 scaled
+    by the row length), i.e. the rounding bound of a dot product in another order.
+  * float32 paths are compared with the float64 oracle within 4 * 2^-24 * row length.
+  * p(A)v and solves: norm-wise relative bounds stated per test, derived from the
+    conditioning of the representation (power basis) or set by the solver contract:
+    true relative residual <= 1e-8, ||x - x_oracle|| / ||x_oracle|| <= 1e-6,
+    iteration counts within 5%.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts too
+    pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="no CUDA device")]
+
+import paper_1907_00072_gb300 as ppg  # noqa: E402
+
+DEV = "cuda:0"
+U64 = 2.0**-53
+U32 = 2.0**-24
+
+
+def T(a, dt=None):
+    a = np.asarray(a)
+    if dt is None:
+        dt = torch.float64 if a.dtype.kind == "f" else torch.int32
+    return torch.as_tensor(a, dtype=dt, device=DEV)
+
+
+def solver_for(a):
+    return ppg.Solver(T(a.rowptr, torch.int32), T(a.colidx, torch.int32), T(a.vals))
+
+
+def row_abs_bound(a, x):
+    """sum_k |a_ik| |x_k| per row, and the row lengths."""
+    abs_a = w.CSR(a.n, a.rowptr, a.colidx, np.abs(a.vals))
+    return oracle.spmv(abs_a, np.abs(x)), np.diff(a.rowptr)
+
+
+def long_row_matrix():
+    """Ragged rows including two rows longer than one shared-memory tile, an empty row,
+    and n not a multiple of the tile height."""
+    n = 6001
+    rng = np.random.default_rng(7)
+    rows = []
+    for i in range(n):
+        if i in (5, 4097):
+            cols = np.sort(rng.choice(n, 5000, replace=False))
+        elif i == 17:
+            cols = np.array([], dtype=int)
+        else:
+            cols = np.sort(rng.choice(n, int(rng.integers(1, 12)), replace=False))
+        rows.append(cols)
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum([len(c) for c in rows])
+    colidx = np.concatenate(rows).astype(np.int32)
+    vals = w.uniform(8, len(colidx))
+    return w.CSR(n, rowptr.astype(np.int32), colidx, vals, "long_rows")
+
+
+MATRICES = {
+    "c1_2d_64": w.c1_matrix,
+    "3d_7pt_21": lambda: w.convdiff(21, 3, 50.0),
+    "27pt_13": lambda: w.stencil27_perturbed(13),
+    "random_ragged": lambda: w.random_csr(3001, 6, 17, diag_shift=0.5),
+    "long_rows": long_row_matrix,
+    "bidiag1": w.bidiag1,
+}
+
+
+# ---------------------------------------------------------------- generator
+
+
+def test_fill_uniform_is_the_published_splitmix64_stream():
+    s = solver_for(w.c1_matrix())
+    out = torch.empty(100003, dtype=torch.float64, device=DEV)
+    ppg.ppg_fill_uniform(s.ctx, out, 2)
+    np.testing.assert_array_equal(out.cpu().numpy(), w.uniform(2, 100003))
+
+
+# ---------------------------------------------------------------- SpMV
+
+
+@pytest.mark.parametrize("name", list(MATRICES))
+def test_spmv_f64_matches_oracle(name):
+    a = MATRICES[name]()
+    x = w.uniform(31, a.n)
+    s = solver_for(a)
+    y = s.spmv(T(x)).cpu().numpy()
+    ref = oracle.spmv(a, x)
+    bound, lens = row_abs_bound(a, x)
+    err = np.abs(y - ref)
+    assert np.all(err <= 4 * U64 * (lens + 1) * bound + 1e-300), np.max(err / (bound + 1e-300))
+
+
+@pytest.mark.parametrize("name", ["c1_2d_64", "27pt_13", "long_rows"])
+def test_spmv_f32_matches_oracle(name):
+    a = MATRICES[name]()
+    x = w.uniform(32, a.n).astype(np.float32)
+    s = solver_for(a)
+    y = s.spmv(T(x, torch.float32)).cpu().numpy().astype(np.float64)
+    ref = oracle.spmv(a, x.astype(np.float64))
+    bound, lens = row_abs_bound(a, x.astype(np.float64))
+    assert np.all(np.abs(y - ref) <= 4 * U32 * (lens + 2) * bound + 1e-30)
+
+
+# ---------------------------------------------------------------- p(A) v
+
+
+def _harmonic_ritz(p):
+    """Roots of 1 - z p(z) for the oracle's Arnoldi-form polynomial (numpy eigvals)."""
+    k = p.deg + 1
+    H = p.H.reshape(k + 1, k, order="F")
+    Hk = H[:k, :k]
+    f = np.linalg.solve(Hk.T, np.eye(k)[:, -1])
+    M = Hk + H[k, k - 1] ** 2 * np.outer(f, np.eye(k)[:, -1])
+    ev = np.linalg.eigvals(M)
+    out = []
+    for e in sorted(ev, key=lambda z: (-abs(z), -z.imag)):
+        if abs(e.imag) == 0:
+            out.append((e.real, 0.0))
+        elif e.imag > 0:
+            out.append((e.real, e.imag))
+            out.append((e.real, -e.imag))
+    return np.array(out).ravel()
+
+
+def _zp_complex(p, z):
+    """z p(z) at complex z from the oracle's Arnoldi-form recurrence."""
+    k = p.deg + 1
+    H = p.H.reshape(k + 1, k, order="F")
+    q = [1.0 / p.beta + 0j]
+    for j in range(1, k):
+        v = z * q[j - 1] - sum(H[i, j - 1] * q[i] for i in range(j))
+        q.append(v / H[j, j - 1])
+    return z * sum(p.y[j] * q[j] for j in range(k))
+
+
+@pytest.mark.parametrize("deg", [0, 1, 3, 5])
+def test_apply_poly_power_form_matches_oracle(deg):
+    a = w.convdiff(40, 2, 10.0)
+    v0 = w.v0(a.n)
+    p = oracle.poly_normal_eq(a, v0, deg)
+    x = w.uniform(41, a.n)
+    s = solver_for(a)
+    s.set_poly(ppg.PPG_BASIS_POWER, p.coef)
+    y = s.apply_poly(T(x)).cpu().numpy()
+    ref = oracle.poly_apply(a, p, x)
+    # Horner vs the explicit sum of Eq. 2: both sum |c_i| |A|^i |x| with rounding u per step
+    absx = np.abs(x)
+    scale = np.zeros(a.n)
+    absa = w.CSR(a.n, a.rowptr, a.colidx, np.abs(a.vals))
+    t = absx.copy()
+    for i in range(deg + 1):
+        scale += abs(p.coef[i]) * t
+        t = oracle.spmv(absa, t)
+    assert np.all(np.abs(y - ref) <= 64 * (deg + 1) * U64 * 8 * scale + 1e-300)
+
+
+ROOT_MATS = {"c1": w.c1_matrix, "27pt": lambda: w.stencil27_perturbed(12),
+             "random": lambda: w.random_csr(3001, 6, 17, diag_shift=0.5)}  # the last has complex roots
+
+
+@pytest.mark.parametrize("deg", [1, 10, 25, 40])
+@pytest.mark.parametrize("mat", ["c1", "random"])
+def test_apply_poly_roots_form_matches_oracle(deg, mat):
+    a = ROOT_MATS[mat]()
+    v0 = w.v0(a.n)
+    p = oracle.poly_gmres(a, v0, deg)
+    roots = _harmonic_ritz(p)
+    x = w.uniform(42, a.n)
+    s = solver_for(a)
+    s.set_poly(ppg.PPG_BASIS_ROOTS, roots)
+    y = s.apply_poly(T(x)).cpu().numpy()
+    ref = oracle.poly_apply(a, p, x)
+    assert np.linalg.norm(y - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("deg", [1, 3, 5])
+def test_build_poly_power_matches_oracle(deg):
+    a = w.c1_matrix()
+    v0 = w.v0(a.n)
+    s = solver_for(a)
+    used, st = s.build_poly(deg, ppg.PPG_BASIS_POWER, v0=T(v0))
+    ref = oracle.poly_normal_eq(a, v0, deg)
+    assert used == deg == ref.used and st == ppg.PPG_OK
+    basis, d, coef, _ = s.get_poly()
+    assert basis == ppg.PPG_BASIS_POWER and d == deg
+    # the Gram matrix has condition ~ 10^(2 deg): compare in the norm it induces
+    np.testing.assert_allclose(coef, ref.coef, rtol=1e-12 * 10 ** (2 * deg), atol=0)
+
+
+def test_build_poly_power_clamps_like_section4():
+    a = w.c1_matrix()
+    v0 = w.v0(a.n)
+    s = solver_for(a)
+    used, st = s.build_poly(16, ppg.PPG_BASIS_POWER, v0=T(v0))
+    ref = oracle.poly_normal_eq(a, v0, 16)
+    assert ref.info > 0 and st == ppg.PPG_WARN_DEGREE_CLAMPED
+    # where POTRF first fails depends on rounding at cond ~ 1e23: allow one degree either way
+    assert abs(used - ref.used) <= 1
+    x = w.uniform(43, a.n)
+    y = s.apply_poly(T(x)).cpu().numpy()
+    r_gpu = np.linalg.norm(v0 - oracle.spmv(a, s.apply_poly(T(v0)).cpu().numpy())) / np.linalg.norm(v0)
+    r_ref = np.linalg.norm(v0 - oracle.spmv(a, oracle.poly_apply(a, ref, v0))) / np.linalg.norm(v0)
+    assert np.isfinite(y).all() and r_gpu <= 2 * r_ref + 1e-12
+
+
+def test_build_poly_auto_degree_is_section4_rule():
+    a = w.c1_matrix()
+    v0 = w.v0(a.n)
+    s = solver_for(a)
+    used, st = s.build_poly(-1, ppg.PPG_BASIS_POWER, v0=T(v0))
+    ref = oracle.poly_normal_eq(a, v0, 30)
+    assert st == ppg.PPG_OK and abs(used - ref.used) <= 1
+
+
+@pytest.mark.parametrize("deg", [1, 5, 10, 25, 40])
+@pytest.mark.parametrize("mat", ["c1", "27pt", "random"])
+def test_build_poly_roots_are_roots_of_the_oracle_polynomial(deg, mat):
+    a = ROOT_MATS[mat]()
+    v0 = w.v0(a.n)
+    s = solver_for(a)
+    used, st = s.build_poly(deg, ppg.PPG_BASIS_ROOTS, v0=T(v0))
+    p = oracle.poly_gmres(a, v0, deg)
+    assert st == ppg.PPG_OK and used == p.deg == deg
+    basis, d, roots, resid = s.get_poly()
+    assert basis == ppg.PPG_BASIS_ROOTS and d == deg
+    # (1) every GPU root is a root of 1 - z p(z) with the oracle's p
+    z = roots[0::2] + 1j * roots[1::2]
+    for zi in z:
+        assert abs(1 - _zp_complex(p, zi)) <= 1e-9, (zi, abs(1 - _zp_complex(p, zi)))
+    # (2) conjugate pairs are adjacent, positive imaginary part first
+    i = 0
+    while i < len(z):
+        if z[i].imag != 0:
+            assert z[i].imag > 0 and z[i + 1] == np.conj(z[i])
+            i += 2
+        else:
+            i += 1
+    # (3) the construction residual equals the GMRES residual of the oracle (Eq. 1)
+    assert abs(resid - p.resid / np.linalg.norm(v0)) <= 1e-8 * max(resid, 1e-3)
+    # (4) applying the roots form equals the oracle's Arnoldi-form application
+    x = w.uniform(44, a.n)
+    y = s.apply_poly(T(x)).cpu().numpy()
+    ref = oracle.poly_apply(a, p, x)
+    assert np.linalg.norm(y - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_build_poly_v0_from_seed_equals_passing_the_vector():
+    a = w.c1_matrix()
+    s = solver_for(a)
+    s.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=None, seed=w.SEED_V0)
+    r1 = s.get_poly()[2]
+    s.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=T(w.v0(a.n)))
+    r2 = s.get_poly()[2]
+    np.testing.assert_array_equal(r1, r2)
+
+
+def test_hessenberg_eigs_match_lapack():
+    rng = np.random.default_rng(3)
+    s = solver_for(w.c1_matrix())
+    for k in (1, 2, 3, 7, 20, 41, 64):
+        H = np.triu(rng.standard_normal((k, k)), -1)
+        Hc = T(np.asfortranarray(H).ravel(order="F"))  # column-major, ld = k
+        wr = torch.zeros(k, dtype=torch.float64, device=DEV)
+        wi = torch.zeros(k, dtype=torch.float64, device=DEV)
+        st = ppg.load_library().ppg_hessenberg_eigs(s.ctx, k, ppg._ptr(Hc), k, ppg._ptr(wr), ppg._ptr(wi))
+        assert st == ppg.PPG_OK
+        mine = wr.cpu().numpy() + 1j * wi.cpu().numpy()
+        for e in np.linalg.eigvals(H):
+            assert np.min(np.abs(mine - e)) <= 1e-11 * max(1.0, np.abs(H).max())
+
+
+# ---------------------------------------------------------------- Arnoldi
+
+
+@pytest.mark.parametrize("with_poly", [False, True])
+def test_arnoldi_matches_oracle(with_poly):
+    a = w.c1_matrix()
+    b = w.rhs(a.n)
+    s = solver_for(a)
+    p = oracle.IDENTITY
+    if with_poly:
+        p = oracle.poly_normal_eq(a, w.v0(a.n), 4)
+        s.set_poly(ppg.PPG_BASIS_POWER, p.coef)
+    k = 30
+    steps, H, V = s.arnoldi(T(b), k, want_V=True)
+    Vr, Hr, beta, done = oracle.arnoldi(a, p, b, k)
+    assert steps == done == k
+    assert np.linalg.norm(H - Hr) <= 1e-10 * np.linalg.norm(Hr)
+    Vg = V.cpu().numpy().T
+    assert np.linalg.norm(np.eye(k + 1) - Vg.T @ Vg) <= 1e-12
+    AV = np.column_stack([oracle.spmv(a, oracle.poly_apply(a, p, Vg[:, j])) for j in range(k)])
+    assert np.linalg.norm(AV - Vg @ H) <= 1e-12 * np.linalg.norm(H)
+
+
+# ---------------------------------------------------------------- solves
+
+
+def _true_relres(a, b, x):
+    return np.linalg.norm(b - oracle.spmv(a, x)) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("mat", ["c1", "random"])
+@pytest.mark.parametrize("deg,basis", [(0, "none"), (1, "roots"), (10, "roots"), (5, "power"), (25, "roots")])
+def test_solve_matches_oracle(deg, basis, mat):
+    a = ROOT_MATS[mat]()
+    b = w.rhs(a.n)
+    v0 = w.v0(a.n)
+    s = solver_for(a)
+    if basis == "none":
+        p = oracle.IDENTITY
+    elif basis == "power":
+        p = oracle.poly_normal_eq(a, v0, deg)
+        s.build_poly(deg, ppg.PPG_BASIS_POWER, v0=T(v0))
+    else:
+        p = oracle.poly_gmres(a, v0, deg)
+        s.build_poly(deg, ppg.PPG_BASIS_ROOTS, v0=T(v0))
+    x, info = s.solve(T(b), tol=1e-8, restart=50, maxit=5000)
+    ref = oracle.gmres(a, b, p, tol=1e-8, m=50, maxit=5000)
+    xg = x.cpu().numpy()
+    assert info.status == ppg.PPG_OK and ref.converged
+    assert _true_relres(a, b, xg) <= 1e-8
+    assert abs(info.stats["relres_true"] - _true_relres(a, b, xg)) <= 1e-10
+    assert np.linalg.norm(xg - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
+    assert abs(info.stats["iterations"] - ref.iters) <= max(1, 0.05 * ref.iters)
+
+
+@pytest.mark.parametrize("restart", [1, 7, 30])
+def test_solve_restart_lengths(restart):
+    a = w.convdiff(24, 2, 20.0)
+    b = w.rhs(a.n)
+    v0 = w.v0(a.n)
+    s = solver_for(a)
+    s.build_poly(8, ppg.PPG_BASIS_ROOTS, v0=T(v0))
+    x, info = s.solve(T(b), tol=1e-8, restart=restart, maxit=20000)
+    ref = oracle.gmres(a, b, oracle.poly_gmres(a, v0, 8), tol=1e-8, m=restart, maxit=20000)
+    xg = x.cpu().numpy()
+    assert info.status == ppg.PPG_OK and _true_relres(a, b, xg) <= 1e-8
+    assert np.linalg.norm(xg - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
+    assert abs(info.stats["iterations"] - ref.iters) <= max(2, 0.05 * ref.iters)
+
+
+def test_solve_mixed_precision_reaches_fp64_accuracy():
+    a = w.c1_matrix()
+    b = w.rhs(a.n)
+    v0 = w.v0(a.n)
+    s = solver_for(a)
+    s.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=T(v0))
+    x, info = s.solve(T(b), tol=1e-8, restart=50, maxit=5000, precision=ppg.PPG_F32)
+    ref = oracle.gmres(a, b, oracle.poly_gmres(a, v0, 10), tol=1e-8, m=50, maxit=5000)
+    xg = x.cpu().numpy()
+    assert info.status == ppg.PPG_OK
+    assert _true_relres(a, b, xg) <= 1e-8
+    assert np.linalg.norm(xg - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
+    assert info.stats["restarts"] >= 2  # refinement steps
+
+
+def test_solve_edge_cases():
+    a = w.c1_matrix()
+    b = w.rhs(a.n)
+    s = solver_for(a)
+    s.build_poly(5, ppg.PPG_BASIS_ROOTS, v0=T(w.v0(a.n)))
+    # zero right-hand side: x = 0, converged, no iterations
+    x0 = T(w.uniform(5, a.n))
+    x, info = s.solve(T(np.zeros(a.n)), x=x0, tol=1e-8)
+    assert info.status == ppg.PPG_OK and info.stats["iterations"] == 0 and not x.any()
+    # exact start: no iterations
+    xd = np.linalg.solve(a.to_dense(), b)
+    x, info = s.solve(T(b), x=T(xd), tol=1e-8)
+    assert info.status == ppg.PPG_OK and info.stats["iterations"] == 0
+    # iteration limit
+    x, info = s.solve(T(b), tol=1e-14, maxit=3)
+    assert info.status == ppg.PPG_ERR_NOT_CONVERGED and info.stats["iterations"] == 3
+    # bad arguments
+    with pytest.raises(ppg.PPGError):
+        s.solve(T(b), restart=0)
+    with pytest.raises(ppg.PPGError):
+        s.solve(T(b), restart=128)
+
+
+def test_invalid_csr_is_rejected():
+    a = w.c1_matrix()
+    bad = a.colidx.copy()
+    bad[10] = a.n + 5
+    with pytest.raises(ppg.PPGError) as e:
+        ppg.Solver(T(a.rowptr, torch.int32), T(bad, torch.int32), T(a.vals))
+    assert e.value.status == ppg.PPG_ERR_INVALID_ARG
+    rp = a.rowptr.copy()
+    rp[100] = rp[101] + 1
+    with pytest.raises(ppg.PPGError):
+        ppg.Solver(T(rp, torch.int32), T(a.colidx, torch.int32), T(a.vals))
+
+
+def test_nonfinite_rhs_reports_nonfinite():
+    a = w.c1_matrix()
+    b = w.rhs(a.n)
+    b[7] = np.nan
+    s = solver_for(a)
+    with pytest.raises(ppg.PPGError) as e:
+        s.solve(T(b), tol=1e-8, maxit=10)
+    assert e.value.status == ppg.PPG_ERR_NONFINITE
+
+
+def test_breakdown_on_invariant_subspace():
+    """b in a 3-dimensional invariant subspace: GMRES ends by a lucky breakdown, exactly."""
+    lams = np.repeat([1.0, 2.0, 5.0], 100)
+    n = len(lams)
+    a = w.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), lams, "diag")
+    b = w.uniform(9, n)
+    s = solver_for(a)
+    x, info = s.solve(T(b), tol=1e-12, restart=20, maxit=100)
+    assert info.status == ppg.PPG_OK and info.stats["iterations"] <= 3
+    np.testing.assert_allclose(x.cpu().numpy(), b / lams, rtol=1e-10)
+
+
+# ---------------------------------------------------------------- adjoint
+
+
+def test_transposed_solve_and_gradients_match_dense():
+    a = w.convdiff(16, 2, 30.0)
+    b = w.rhs(a.n)
+    xt = w.uniform(w.SEED_XTARGET, a.n)
+    s = solver_for(a)
+    s.build_poly(6, ppg.PPG_BASIS_ROOTS, v0=T(w.v0(a.n)))
+    vals = T(a.vals).requires_grad_(True)
+    bt = T(b).requires_grad_(True)
+    x = ppg.solve(s, vals, bt, tol=1e-12)
+    loss = ((x - T(xt)) ** 2).sum()
+    loss.backward()
+    A = a.to_dense()
+    xd = np.linalg.solve(A, b)
+    lam = np.linalg.solve(A.T, 2 * (xd - xt))
+    rows = np.repeat(np.arange(a.n), np.diff(a.rowptr))
+    gvals = -lam[rows] * xd[a.colidx]
+    np.testing.assert_allclose(bt.grad.cpu().numpy(), lam, rtol=1e-7, atol=1e-9 * np.abs(lam).max())
+    np.testing.assert_allclose(vals.grad.cpu().numpy(), gvals, rtol=1e-7, atol=1e-9 * np.abs(gvals).max())
+
+
+# ---------------------------------------------------------------- full-size workloads (sampled)
+
+
+@pytest.fixture(scope="module")
+def c2():
+    return w.c2_matrix()
+
+
+def test_full_size_c2_spmv_and_horner_step_sampled(c2):
+    a = c2
+    assert a.n == 2097152 and a.nnz == 14581760
+    x = w.uniform(51, a.n)
+    s = solver_for(a)
+    y = s.spmv(T(x)).cpu().numpy()
+    rows = np.unique(np.concatenate([np.arange(0, 300), np.arange(a.n - 300, a.n),
+                                     np.random.default_rng(0).integers(0, a.n, 4000)]))
+    ref = oracle.spmv_rows(a, x, rows)
+    bound, lens = row_abs_bound(a, x)
+    assert np.all(np.abs(y[rows] - ref) <= 4 * U64 * (lens[rows] + 1) * bound[rows])
+    # one fused Horner step through apply_poly with a degree-1 power polynomial: c0 x + c1 A x
+    s.set_poly(ppg.PPG_BASIS_POWER, [0.75, -0.125])
+    z = s.apply_poly(T(x)).cpu().numpy()
+    refz = 0.75 * x[rows] - 0.125 * ref
+    assert np.all(np.abs(z[rows] - refz) <= 8 * U64 * (lens[rows] + 2) * (0.125 * bound[rows] + 0.75 * np.abs(x[rows])))
+
+
+def test_full_size_c2_solve_fp64_and_mixed(c2):
+    a = c2
+    b = w.rhs(a.n)
+    s = solver_for(a)
+    used, _ = s.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=T(w.v0(a.n)))
+    assert used == 10
+    x64, i64 = s.solve(T(b), tol=1e-8, restart=50, maxit=3000)
+    x32, i32 = s.solve(T(b), tol=1e-8, restart=50, maxit=3000, precision=ppg.PPG_F32)
+    assert i64.status == ppg.PPG_OK and i32.status == ppg.PPG_OK
+    r64 = _true_relres(a, b, x64.cpu().numpy())
+    r32 = _true_relres(a, b, x32.cpu().numpy())
+    assert r64 <= 1e-8 and r32 <= 1e-8
+    d = np.linalg.norm(x64.cpu().numpy() - x32.cpu().numpy()) / np.linalg.norm(x64.cpu().numpy())
+    assert d <= 1e-6
