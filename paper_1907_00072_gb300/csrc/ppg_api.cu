@@ -112,7 +112,7 @@ struct Layout {
 
 size_t partial_doubles(const ppg_ctx *c)
 {
-    const size_t gs = (size_t)(kKmax + 1) * (size_t)c->num_sms * 16;
+    const size_t gs = (size_t)(kKmax + 1) * (size_t)gs_max_blocks(c->num_sms);
     const size_t gram = (size_t)(kSmallMax * (kSmallMax + 1) / 2) * (size_t)gram_grid(c->num_sms);
     const size_t resid = (size_t)c->A.resid_blocks;
     return std::max(gs, std::max(gram, resid));
@@ -139,7 +139,7 @@ ppg_status get_layout(ppg_ctx *c, int ncols, size_t esize, Layout *L)
     }
     const size_t p = round_up((long long)(partial_doubles(c) * sizeof(double)), 4096);
     L->partials = reinterpret_cast<double *>(c->ws);
-    L->partial_blocks = c->num_sms * 16;
+    L->partial_blocks = gs_max_blocks(c->num_sms);
     L->basis = c->ws + p;
     L->ncols = ncols;
     L->esize = esize;
@@ -174,9 +174,9 @@ Scalar sscaled(double v, const double *sig) { return Scalar{v, sig, 0, sig ? 1 :
 SpmvEpi epi_none()
 {
     SpmvEpi e;
-    e.x = vnone();
+    e.x = e.x2 = vnone();
     e.out0 = e.u0 = e.w0 = e.out1 = e.u1 = e.w1 = vnone();
-    e.a0 = e.b0 = e.c0 = e.a1 = e.b1 = e.c1 = simm(0.0);
+    e.a0 = e.b0 = e.c0 = e.a1 = e.b1 = e.c1 = e.s2 = simm(0.0);
     return e;
 }
 
@@ -201,7 +201,16 @@ struct Exec {
 
     // dst = p(A) (scale * src).  sig: device sigma array (follows j) or null for 1.
     // tmp: 3 distinct working vectors, none of them src or dst.
-    ppg_status poly_apply(VecRef src, const double *sig, VecRef dst, char *const tmp[3], int check)
+    // When defer is given and the product form ends with a real root, the last update
+    // dst += t P is not performed: *defer receives P and t so that the caller can fold it
+    // into the SpMV that consumes dst (A (dst + t P)).
+    struct Deferred {
+        bool active = false;
+        VecRef P;
+        Scalar t;
+    };
+    ppg_status poly_apply(VecRef src, const double *sig, VecRef dst, char *const tmp[3], int check,
+                          Deferred *defer = nullptr)
     {
         if (!c->has_poly) {
             SpmvEpi e = epi_none();
@@ -257,7 +266,13 @@ struct Exec {
                     e.c0 = simm(1.0);
                 }
                 if (i == k - 1) {
-                    PPG_TRY(axpy(e, check));
+                    if (defer && !first) {
+                        defer->active = true;
+                        defer->P = P;
+                        defer->t = e.b0;
+                    } else {
+                        PPG_TRY(axpy(e, check));
+                    }
                 } else {
                     VecRef Pn = vfix(tmp[pp]);
                     e.x = P;
@@ -320,9 +335,14 @@ struct Exec {
             return spmv(e, check);
         }
         char *t3[3] = {tmp[1], tmp[2], tmp[3]};
-        PPG_TRY(poly_apply(src, sig, vfix(tmp[0]), t3, check));
+        Deferred d;
+        PPG_TRY(poly_apply(src, sig, vfix(tmp[0]), t3, check, &d));
         SpmvEpi e = epi_none();
         e.x = vfix(tmp[0]);
+        if (d.active) {  // w = A (y + t P): the last root step rides on this SpMV's gather
+            e.x2 = d.P;
+            e.s2 = d.t;
+        }
         e.out0 = w;
         e.a0 = simm(1.0);
         return spmv(e, check);
@@ -341,11 +361,9 @@ struct Exec {
 struct Iter {
     Exec *x;
     const Layout *L;
-    int kmax;
-    long long ntiles;
-    int nblk;
+    int maxcols;  // restart + 1: bound on the columns a cycle-end combination uses
 
-    ppg_status gs(int op, int from_k, void *out, int out_follow)
+    ppg_status gs(int op, int from_k, void *out, int out_follow, int kcols)
     {
         GsArgs a{};
         a.U = L->basis;
@@ -355,21 +373,21 @@ struct Iter {
         a.out_follow = out_follow;
         a.op = op;
         a.kcols_from_k = from_k;
-        a.ntiles = ntiles;
         a.partials = L->partials;
-        a.nblk = nblk;
         x->c->launches++;
-        PPG_CK(launch_gs(x->prec, kmax, a, x->c->st, x->s));
+        PPG_CK(launch_gs(x->prec, kcols, x->c->ld, x->c->num_sms, a, x->c->st, x->s));
         return PPG_OK;
     }
 
-    ppg_status iteration()
+    // iteration j of the cycle (the device state carries the same j; kernels of a cycle
+    // that ended early return at once)
+    ppg_status iteration(int j)
     {
         char *tmp[4] = {L->vec[1], L->vec[2], L->vec[3], L->vec[4]};
         PPG_TRY(x->poly_then_A(vcol(L->basis, x->c->ld, 0), x->c->st->sigma, vfix(L->vec[0]), tmp, kSkipIfDone));
-        PPG_TRY(gs(kGsDot, 0, nullptr, 0));
-        PPG_TRY(gs(kGsUpdDot, 0, nullptr, 0));
-        PPG_TRY(gs(kGsUpdNorm, 0, nullptr, 1));
+        PPG_TRY(gs(kGsDot, 0, nullptr, 0, j + 1));
+        PPG_TRY(gs(kGsUpdDot, 0, nullptr, 0, j + 1));
+        PPG_TRY(gs(kGsUpdNorm, 0, nullptr, 1, j + 1));
         return PPG_OK;
     }
 
@@ -377,7 +395,7 @@ struct Iter {
     ppg_status cycle_end(double *xsol)
     {
         char *z = L->vec[5], *e = L->vec[6];
-        PPG_TRY(gs(kGsCombine, 1, z, 0));
+        PPG_TRY(gs(kGsCombine, 1, z, 0, maxcols));
         const void *corr = z;
         if (x->c->has_poly) {
             char *t3[3] = {L->vec[1], L->vec[2], L->vec[3]};
@@ -413,22 +431,18 @@ ppg_status read_state(ppg_ctx *c)
     return PPG_OK;
 }
 
-int kmax_for(int ncols) { return ncols <= 64 ? 64 : 128; }
-
 // Runs `steps` Arnoldi iterations of A p(A) (current polynomial) from v (float64, n) in float64 with
 // the solver's kernels; the Hessenberg matrix stays in c->st.  v may be null when the start vector is
 // already in basis column 0.  Returns the number of steps completed in *done.
 ppg_status run_arnoldi(ppg_ctx *c, const double *v, int steps, const Layout &L, int *done)
 {
     Exec ex{c, &c->A, kF64, c->stream};
-    const int kmax = kmax_for(steps + 1);
-    const long long ntiles = c->ld / gs_tile_rows(kF64, kmax);
-    Iter it{&ex, &L, kmax, ntiles, gs_grid(kF64, kmax, ntiles, c->num_sms)};
+    Iter it{&ex, &L, steps + 1};
     PPG_TRY(init_cycle_state(c, 0, steps, steps, 0.0, 0.0));
     c->launches++;
     PPG_CK(launch_norm_start(c->A.n, kF64, v ? v : (const double *)L.basis, v ? (void *)L.basis : nullptr, 1, c->st,
                              L.partials, c->A.resid_blocks, c->stream));
-    for (int j = 0; j < steps; ++j) PPG_TRY(it.iteration());
+    for (int j = 0; j < steps; ++j) PPG_TRY(it.iteration(j));
     PPG_TRY(read_state(c));
     if (c->h_st->error & kErrNonfinite) return fail(PPG_ERR_NONFINITE, "non-finite value in the Arnoldi run");
     *done = c->h_st->j;
@@ -517,9 +531,7 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
     PPG_CK(cudaEventRecord(c->ev0, c->stream));
 
     Exec ex{c, &c->A, prec, c->stream};
-    const int kmax = kmax_for(ncols);
-    const long long ntiles = c->ld / gs_tile_rows(prec, kmax);
-    Iter it{&ex, &L, kmax, ntiles, gs_grid(prec, kmax, ntiles, c->num_sms)};
+    Iter it{&ex, &L, ncols};
 
     PPG_TRY(init_cycle_state(c, 0, restart, maxit, tol, inner));
     c->launches++;
@@ -536,7 +548,7 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
         residuals++;
         PPG_TRY(read_state(c));
         while (!c->h_st->stop) {
-            for (int j = 0; j < restart; ++j) PPG_TRY(it.iteration());
+            for (int j = 0; j < restart; ++j) PPG_TRY(it.iteration(j));
             PPG_TRY(it.cycle_end(x));
             c->launches++;
             PPG_CK(launch_residual(c->A, prec, b, x, L.basis, c->st, L.partials, c->stream));
@@ -634,7 +646,8 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
     c->A.num_sms = c->num_sms;
     c->A.resid_blocks = c->num_sms * 8;
     c->ld = round_up(n, kLdPad);
-    PPG_CK(cudaMalloc(&c->d_rowptr, sizeof(int) * (n + 1)));
+    PPG_CK(cudaMalloc(&c->d_rowptr, sizeof(int) * (n + 1 + 16)));
+    PPG_CK(cudaMemsetAsync(c->d_rowptr, 0, sizeof(int) * (n + 1 + 16), c->stream));
     PPG_CK(cudaMalloc(&c->d_colidx, sizeof(int) * (nnz + 16)));
     PPG_CK(cudaMalloc(&c->d_vals, sizeof(double) * (nnz + 8)));
     PPG_CK(cudaMemcpyAsync(c->d_rowptr, rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, c->stream));
@@ -679,12 +692,12 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
         const long long r1 = std::min<long long>(n, r0 + R);
         maxtile = std::max<long long>(maxtile, hrp[r1] - hrp[r0]);
     }
-    const long long cap = std::min<long long>(4096, round_up(maxtile + 8, 16));
+    const long long cap = std::min<long long>(spmv_cap_max(), round_up(maxtile + 8, 16));
     c->A.rows_per_tile = R;
     c->A.lanes_per_row = kThreads / R;
     c->A.cap64 = (int)std::max<long long>(cap, 64);
     c->A.cap32 = (int)std::max<long long>(cap, 64);
-    PPG_CK(spmv_configure(c->A.cap64, c->A.cap32));
+    PPG_CK(spmv_configure(&c->A));
     PPG_CK(gs_configure());
     PPG_CK(gram_configure());
 
@@ -824,6 +837,7 @@ ppg_status ppg_set_poly(ppg_ctx *c, int basis, int degree, const double *coef_h)
             if (im != 0.0) {
                 if (i + 1 >= k || r[2 * i + 2] != re || r[2 * i + 3] != -im || im < 0.0)
                     return fail(PPG_ERR_INVALID_ARG, "a complex root (im > 0) must be followed by its conjugate");
+                ++i;  // the conjugate partner was checked with it
             }
         }
         PPG_TRY(set_device(c));

@@ -13,7 +13,7 @@ namespace ppg {
 constexpr int kThreads = 256;      // threads per CTA of every streaming kernel
 constexpr int kKmax = 128;         // largest Krylov basis (restart + 1)
 constexpr int kSmallMax = 64;      // largest dense eigen/Cholesky problem (degree + 1 + 1)
-constexpr int kLdPad = 256;        // internal vectors are padded to a multiple of this many entries
+constexpr int kLdPad = 1024;       // internal vectors are padded to a multiple of this many entries
 
 // error bits kept in Cycle::error
 enum : int {
@@ -160,11 +160,11 @@ __device__ __forceinline__ unsigned long long global_timer_ns()
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned long long limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
-    unsigned long long t0 = global_timer_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_timer_ns() - t0 > limit_ns) return false;
+    const unsigned long long t0 = global_timer_ns();
+    for (unsigned int spins = 1;; ++spins) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((spins & 63u) == 0 && global_timer_ns() - t0 > limit_ns) return false;
     }
-    return true;
 }
 
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s

@@ -20,18 +20,20 @@ struct DevMatrix {
     int cap64, cap32;     // non-zeros one tile can stage in shared memory
     int num_sms;
     int resid_blocks;     // grid of the persistent residual / norm kernels
+    int spmv_blocks64;    // persistent SpMV grids
+    int spmv_blocks32;
 };
 
-// Fused SpMV epilogue (one row r, Ax = (A x)[r]):
+// Fused SpMV epilogue (one row r, Ax = (A (x + s2 x2))[r], x2 optional):
 //   out0[r] = a0 * Ax + b0 * u0[r] + c0 * w0[r]
 //   out1[r] = a1 * Ax + b1 * u1[r] + c1 * w1[r]      (when out1 is set)
 // Null vectors drop their term.  out may alias its own u/w (same row is read then
-// written) but never x.
+// written) but never x or x2.
 struct SpmvEpi {
-    VecRef x;
+    VecRef x, x2;
     VecRef out0, u0, w0;
     VecRef out1, u1, w1;
-    Scalar a0, b0, c0, a1, b1, c1;
+    Scalar a0, b0, c0, a1, b1, c1, s2;
 };
 
 // Gram-Schmidt / basis kernels over the column-major basis U (ld entries per column).
@@ -76,11 +78,10 @@ cudaError_t launch_csr_outer(const DevMatrix &A, const double *u, const double *
                              cudaStream_t s);
 cudaError_t launch_transpose(const DevMatrix &A, int *rpT, int *ciT, double *vaT, int *work, cudaStream_t s);
 
-// Gram-Schmidt passes (TMA-staged basis tiles).
-int gs_tile_rows(int prec, int kmax);
-size_t gs_smem_bytes(int prec, int kmax);
-int gs_grid(int prec, int kmax, long long ntiles, int num_sms);
-cudaError_t launch_gs(int prec, int kmax, const GsArgs &a, Cycle *st, cudaStream_t s);
+// Gram-Schmidt passes (TMA-staged basis tiles).  kcols: an upper bound on the number of basis
+// columns the launch will combine (it selects the tile-shape bucket); ld a multiple of 1024.
+cudaError_t launch_gs(int prec, int kcols, long long ld, int num_sms, GsArgs a, Cycle *st, cudaStream_t s);
+int gs_max_blocks(int num_sms);
 
 // Power-basis Gram matrix of Eq. 1 with Cholesky and the degree clamp (one kernel).
 cudaError_t launch_gram_cholesky(int n, long long ld, const double *B, int deg, double *partials, int nblk,
@@ -94,7 +95,8 @@ cudaError_t launch_root_table(int k, const double *roots, double *table_out, int
 cudaError_t launch_hess_eigs(int k, const double *H, int ld, double *wr, double *wi, int *status_out,
                              cudaStream_t s);
 // one-time kernel attribute setup (dynamic shared memory limits)
-cudaError_t spmv_configure(int cap64, int cap32);
+cudaError_t spmv_configure(DevMatrix *A);
+int spmv_cap_max();
 cudaError_t gs_configure();
 cudaError_t gram_configure();
 

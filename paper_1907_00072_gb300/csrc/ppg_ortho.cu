@@ -20,13 +20,16 @@
 
 namespace ppg {
 
+// Tile shape by basis-width bucket KM (k <= KM columns): every pipeline stage carries
+// about 32 KB of basis whatever k is, so the copy pipeline stays deep at small k.
 template <typename T, int KM>
 struct GsCfg {
-    static constexpr int TR = (sizeof(T) == 8 ? 64 : 128) * 64 / KM;  // rows per tile
-    static constexpr int TPR = kThreads / TR;                           // threads per row (update phase)
-    static constexpr int RPL = TR / 32;                                 // rows per lane (dot phase)
-    static constexpr int CPW = KM / 8;                                  // columns per warp (dot phase)
-    static constexpr int STAGE = KM * TR + TR;                          // elements per pipeline stage
+    static constexpr int TR = 32768 / (KM * (int)sizeof(T));             // rows per tile
+    static constexpr int RPT = TR >= kThreads ? TR / kThreads : 1;       // rows per thread (update phase)
+    static constexpr int TPR = TR >= kThreads ? 1 : kThreads / TR;       // threads per row (update phase)
+    static constexpr int RPL = TR / 32;                                  // rows per lane (dot phase)
+    static constexpr int CPW = (KM + 7) / 8;                             // columns per warp (dot phase)
+    static constexpr int STAGE = KM * TR + TR;                           // elements per pipeline stage
 };
 
 // Accumulator of a warp's column sums: float64 directly, or float32 with Kahan
@@ -152,11 +155,11 @@ template <typename T, int KM>
 __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
 {
     using C = GsCfg<T, KM>;
-    constexpr int TR = C::TR, TPR = C::TPR, RPL = C::RPL, CPW = C::CPW;
+    constexpr int TR = C::TR, TPR = C::TPR, RPT = C::RPT, RPL = C::RPL, CPW = C::CPW;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ T s_wn[TR];
-    __shared__ T s_part[TPR][TR];
+    __shared__ T s_part[TPR > 1 ? TPR : 1][TPR > 1 ? TR : 1];
     __shared__ T s_coef[KM];
     __shared__ double s_red[KM + 1];
     __shared__ double scratch[33];
@@ -169,6 +172,10 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
         return;
     }
     const int k = a.kcols_from_k ? st->k : st->j + 1;
+    if (k > KM) {  // the host picked too small a bucket: refuse rather than read past the stage
+        if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&st->error, kErrTimeout);
+        return;
+    }
     const T *__restrict__ U = (const T *)a.U;
     T *w = (T *)a.w;
     T *out = a.out_follow ? (T *)a.U + (long long)(st->j + 1) * a.ldu : (T *)a.out;
@@ -215,41 +222,69 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
         const long long row0 = tile * TR;
         const T *dotvec = sw;
         if (op != kGsDot) {
-            const int row = tid % TR, q = tid / TR;
-            T part = T(0);
-            for (int c = q; c < k; c += TPR) part = fma(sU[c * TR + row], s_coef[c], part);
-            s_part[q][row] = part;
-            __syncthreads();
-            if (tid < TR) {
-                T sum = s_part[0][row];
+            // update: wn = w - sum_c U[:, c] coef[c] on this tile
+            if constexpr (TPR == 1) {
+                T part[RPT];
 #pragma unroll
-                for (int p = 1; p < TPR; ++p) sum += s_part[p][row];
-                const T wn = (op == kGsCombine ? T(0) : sw[row]) - sum;
-                if (op == kGsUpdDot) {
-                    w[row0 + row] = wn;
-                    s_wn[row] = wn;
-                } else {
-                    out[row0 + row] = wn;
-                    if (op == kGsUpdNorm) nrm += (double)wn * (double)wn;
+                for (int r = 0; r < RPT; ++r) part[r] = T(0);
+                for (int c = 0; c < k; ++c) {
+                    const T cc = s_coef[c];
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) part[r] = fma(sU[c * TR + tid + r * kThreads], cc, part[r]);
+                }
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const int row = tid + r * kThreads;
+                    const T wn = (op == kGsCombine ? T(0) : sw[row]) - part[r];
+                    if (op == kGsUpdDot) {
+                        w[row0 + row] = wn;
+                        s_wn[row] = wn;
+                    } else {
+                        out[row0 + row] = wn;
+                        if (op == kGsUpdNorm) nrm += (double)wn * (double)wn;
+                    }
+                }
+                __syncthreads();
+            } else {
+                const int row = tid % TR, q = tid / TR;
+                T part = T(0);
+                for (int c = q; c < k; c += TPR) part = fma(sU[c * TR + row], s_coef[c], part);
+                s_part[q][row] = part;
+                __syncthreads();
+                if (tid < TR) {
+                    T sum = s_part[0][row];
+#pragma unroll
+                    for (int p = 1; p < TPR; ++p) sum += s_part[p][row];
+                    const T wn = (op == kGsCombine ? T(0) : sw[row]) - sum;
+                    if (op == kGsUpdDot) {
+                        w[row0 + row] = wn;
+                        s_wn[row] = wn;
+                    } else {
+                        out[row0 + row] = wn;
+                        if (op == kGsUpdNorm) nrm += (double)wn * (double)wn;
+                    }
+                }
+                __syncthreads();
+            }
+            dotvec = s_wn;
+        } else {
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const int row = tid + r * kThreads;
+                if (row < TR) {
+                    const double t = (double)sw[row];
+                    nrm += t * t;
                 }
             }
-            __syncthreads();
-            dotvec = s_wn;
-        } else if (tid < TR) {
-            const double t = (double)sw[tid];
-            nrm += t * t;
         }
         if (op == kGsDot || op == kGsUpdDot) {
-            T wv[RPL];
-#pragma unroll
-            for (int r = 0; r < RPL; ++r) wv[r] = dotvec[lane * RPL + r];
 #pragma unroll
             for (int i = 0; i < CPW; ++i) {
                 const int c = wid + 8 * i;
                 if (c < k) {
                     T s = T(0);
 #pragma unroll
-                    for (int r = 0; r < RPL; ++r) s = fma(sU[c * TR + lane * RPL + r], wv[r], s);
+                    for (int r = 0; r < RPL; ++r) s = fma(sU[c * TR + lane * RPL + r], dotvec[lane * RPL + r], s);
                     acc[i].add(s);
                 }
             }
@@ -312,71 +347,75 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     }
 }
 
-int gs_tile_rows(int prec, int kmax)
-{
-    if (prec == kF64) return kmax <= 64 ? GsCfg<double, 64>::TR : GsCfg<double, 128>::TR;
-    return kmax <= 64 ? GsCfg<float, 64>::TR : GsCfg<float, 128>::TR;
-}
+// ---- host side: bucket selection, occupancy (cached per instantiation), launch
 
-size_t gs_smem_bytes(int prec, int kmax)
-{
-    if (prec == kF64)
-        return 2 * sizeof(double) * (kmax <= 64 ? GsCfg<double, 64>::STAGE : GsCfg<double, 128>::STAGE);
-    return 2 * sizeof(float) * (kmax <= 64 ? GsCfg<float, 64>::STAGE : GsCfg<float, 128>::STAGE);
-}
+namespace {
 
 template <typename T, int KM>
-static int gs_blocks_per_sm()
+struct GsInst {
+    static constexpr size_t smem() { return 2 * sizeof(T) * (size_t)GsCfg<T, KM>::STAGE; }
+    static int per_sm()
+    {
+        static int cached = 0;
+        if (!cached) {
+            int nb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gs<T, KM>, kThreads, smem());
+            cached = nb > 0 ? nb : 1;
+        }
+        return cached;
+    }
+    static cudaError_t configure()
+    {
+        return cudaFuncSetAttribute(k_gs<T, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
+    }
+    static cudaError_t launch(GsArgs a, long long ld, int num_sms, Cycle *st, cudaStream_t s)
+    {
+        a.ntiles = ld / GsCfg<T, KM>::TR;
+        long long g = (long long)per_sm() * num_sms;
+        if (g > a.ntiles) g = a.ntiles;
+        a.nblk = (int)(g > 0 ? g : 1);
+        k_gs<T, KM><<<a.nblk, kThreads, smem(), s>>>(a, st);
+        return cudaGetLastError();
+    }
+};
+
+template <typename T>
+cudaError_t gs_launch_t(int kcols, GsArgs a, long long ld, int num_sms, Cycle *st, cudaStream_t s)
 {
-    int nb = 0;
-    const size_t smem = 2 * sizeof(T) * GsCfg<T, KM>::STAGE;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gs<T, KM>, kThreads, smem);
-    return nb > 0 ? nb : 1;
+    if (kcols <= 8) return GsInst<T, 8>::launch(a, ld, num_sms, st, s);
+    if (kcols <= 16) return GsInst<T, 16>::launch(a, ld, num_sms, st, s);
+    if (kcols <= 32) return GsInst<T, 32>::launch(a, ld, num_sms, st, s);
+    if (kcols <= 64) return GsInst<T, 64>::launch(a, ld, num_sms, st, s);
+    return GsInst<T, 128>::launch(a, ld, num_sms, st, s);
 }
 
-int gs_grid(int prec, int kmax, long long ntiles, int num_sms)
+template <typename T>
+cudaError_t gs_configure_t()
 {
-    int per = 1;
-    if (prec == kF64)
-        per = kmax <= 64 ? gs_blocks_per_sm<double, 64>() : gs_blocks_per_sm<double, 128>();
-    else
-        per = kmax <= 64 ? gs_blocks_per_sm<float, 64>() : gs_blocks_per_sm<float, 128>();
-    long long g = (long long)per * num_sms;
-    if (g > ntiles) g = ntiles;
-    return (int)(g > 0 ? g : 1);
-}
-
-template <typename T, int KM>
-static cudaError_t gs_configure_one()
-{
-    return cudaFuncSetAttribute(k_gs<T, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(2 * sizeof(T) * GsCfg<T, KM>::STAGE));
-}
-
-cudaError_t gs_configure()
-{
-    cudaError_t e = gs_configure_one<double, 64>();
-    if (e == cudaSuccess) e = gs_configure_one<double, 128>();
-    if (e == cudaSuccess) e = gs_configure_one<float, 64>();
-    if (e == cudaSuccess) e = gs_configure_one<float, 128>();
+    cudaError_t e = GsInst<T, 8>::configure();
+    if (e == cudaSuccess) e = GsInst<T, 16>::configure();
+    if (e == cudaSuccess) e = GsInst<T, 32>::configure();
+    if (e == cudaSuccess) e = GsInst<T, 64>::configure();
+    if (e == cudaSuccess) e = GsInst<T, 128>::configure();
     return e;
 }
 
-cudaError_t launch_gs(int prec, int kmax, const GsArgs &a, Cycle *st, cudaStream_t s)
+}  // namespace
+
+cudaError_t gs_configure()
 {
-    const size_t smem = gs_smem_bytes(prec, kmax);
-    if (prec == kF64) {
-        if (kmax <= 64)
-            k_gs<double, 64><<<a.nblk, kThreads, smem, s>>>(a, st);
-        else
-            k_gs<double, 128><<<a.nblk, kThreads, smem, s>>>(a, st);
-    } else {
-        if (kmax <= 64)
-            k_gs<float, 64><<<a.nblk, kThreads, smem, s>>>(a, st);
-        else
-            k_gs<float, 128><<<a.nblk, kThreads, smem, s>>>(a, st);
-    }
-    return cudaGetLastError();
+    cudaError_t e = gs_configure_t<double>();
+    if (e == cudaSuccess) e = gs_configure_t<float>();
+    return e;
+}
+
+int gs_max_blocks(int num_sms) { return 16 * num_sms; }
+
+cudaError_t launch_gs(int prec, int kcols, long long ld, int num_sms, GsArgs a, Cycle *st, cudaStream_t s)
+{
+    if (kcols < 1 || kcols > kKmax) return cudaErrorInvalidValue;
+    if (prec == kF64) return gs_launch_t<double>(kcols, a, ld, num_sms, st, s);
+    return gs_launch_t<float>(kcols, a, ld, num_sms, st, s);
 }
 
 // ---------------------------------------------------------------- Gram matrix of Eq. 1 and its Cholesky solve

@@ -66,19 +66,41 @@ struct SpmvArgs {
     SpmvEpi e;
 };
 
-// One CTA per tile of R consecutive rows.  Thread 0 copies the tile's contiguous
-// range of values and column indices into shared memory with two TMA bulk copies
-// (ranges widened to 16-byte boundaries); then G = 256/R lanes per row form the
-// row's dot product, gathering x (resident in L2 for these problem sizes), and the
-// first lane of each row applies the epilogue.  Tiles whose non-zeros exceed the
-// staging capacity read the matrix directly from global memory.
+constexpr int kSpmvConsumerWarps = 8;
+constexpr int kSpmvThreads = (kSpmvConsumerWarps + 1) * 32;  // + one producer warp
+constexpr int kSpmvStages = 3;
+constexpr int kSpmvRpBytes = 1152;  // (256 + 1) row pointers, rounded up to 128 bytes
+constexpr int kSpmvCapMax = 4096;
+
+__host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_spmv(SpmvArgs<T> a)
+__host__ __device__ constexpr size_t spmv_stage_bytes(int cap)
+{
+    return kSpmvRpBytes + round128((size_t)cap * sizeof(T)) + round128((size_t)cap * 4);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Persistent, warp-specialised row-block CSR SpMV.  Tiles of R consecutive rows are
+// dealt round-robin to the CTAs.  The producer warp keeps up to three tiles in flight:
+// for each it reads the tile's non-zero range from the row pointers and issues TMA bulk
+// copies of the row-pointer segment, the values and the column indices (ranges widened
+// to 16-byte boundaries) into a shared-memory stage.  Eight consumer warps take the
+// stages in order: G = 256/R lanes per row form the row's dot product from shared
+// memory, gathering x (x + s2 x2 when a second input is given), then the row's first
+// lane applies the fused epilogue and the warp releases the stage.  Tiles whose
+// non-zeros exceed the stage read values and columns from global memory instead.
+template <typename T>
+__global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int s_rp[kThreads + 1];
-    __shared__ double s_coef[6];
+    __shared__ __align__(8) uint64_t full[kSpmvStages];
+    __shared__ __align__(8) uint64_t empty[kSpmvStages];
+    __shared__ double s_coef[7];
 
     Cycle *st = a.st;
     if (a.check_done == kSkipIfDone && st->cycle_done) return;
@@ -86,120 +108,191 @@ __global__ void __launch_bounds__(kThreads) k_spmv(SpmvArgs<T> a)
 
     const int R = a.rows_per_tile;
     const int G = a.lanes_per_row;
-    const int r0 = blockIdx.x * R;
-    const int rows = min(R, a.n - r0);
-    T *s_val = reinterpret_cast<T *>(smem);
-    int *s_col = reinterpret_cast<int *>(smem + ((a.cap * sizeof(T) + 127) & ~(size_t)127));
+    const long long ntiles = ((long long)a.n + R - 1) / R;
+    const size_t stage_bytes = spmv_stage_bytes<T>(a.cap);
+    const size_t val_off = kSpmvRpBytes;
+    const size_t col_off = kSpmvRpBytes + round128((size_t)a.cap * sizeof(T));
+    constexpr int VA = 16 / (int)sizeof(T);
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
 
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
+    if (tid == 0) {
+        for (int s = 0; s < kSpmvStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kSpmvConsumerWarps);
+        }
         fence_mbar_init();
     }
-    for (int t = threadIdx.x; t <= rows; t += blockDim.x) s_rp[t] = a.rowptr[r0 + t];
-    switch (threadIdx.x) {
+    switch (tid) {
     case 0: s_coef[0] = resolve(a.e.a0, st); break;
     case 1: s_coef[1] = resolve(a.e.b0, st); break;
     case 2: s_coef[2] = resolve(a.e.c0, st); break;
     case 3: s_coef[3] = resolve(a.e.a1, st); break;
     case 4: s_coef[4] = resolve(a.e.b1, st); break;
     case 5: s_coef[5] = resolve(a.e.c1, st); break;
+    case 6: s_coef[6] = resolve(a.e.s2, st); break;
     default: break;
     }
     __syncthreads();
 
-    const int s = s_rp[0], e = s_rp[rows];
-    constexpr int VA = 16 / (int)sizeof(T);
-    const int vs = s & ~(VA - 1), ve = (e + VA - 1) & ~(VA - 1);
-    const int cs = s & ~3, ce = (e + 3) & ~3;
-    const bool staged = (ve - vs) <= a.cap && (ce - cs) <= a.cap;
-
-    if (staged && e > s) {
-        if (threadIdx.x == 0) {
-            const uint32_t vb = (uint32_t)(ve - vs) * (uint32_t)sizeof(T);
-            const uint32_t cb = (uint32_t)(ce - cs) * 4u;
-            mbar_arrive_expect_tx(&bar, vb + cb);
-            bulk_g2s(s_val, a.vals + vs, vb, &bar);
-            bulk_g2s(s_col, a.colidx + cs, cb, &bar);
+    if (wid == kSpmvConsumerWarps) {
+        // ---------------- producer
+        if (lane == 0) {
+            int i = 0;
+            for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+                const int s = i % kSpmvStages, round = i / kSpmvStages;
+                if (round > 0 && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitLimitNs)) {
+                    atomicOr(&st->error, kErrTimeout);
+                    break;
+                }
+                const int r0 = (int)(tile * R);
+                const int rows = min(R, a.n - r0);
+                const int e0 = __ldg(a.rowptr + r0), e1 = __ldg(a.rowptr + r0 + rows);
+                const int vs = e0 & ~(VA - 1), ve = (e1 + VA - 1) & ~(VA - 1);
+                const int cs = e0 & ~3, ce = (e1 + 3) & ~3;
+                const bool staged = (ve - vs) <= a.cap && (ce - cs) <= a.cap && e1 > e0;
+                unsigned char *base = smem + s * stage_bytes;
+                const uint32_t rpb = ((uint32_t)(rows + 1) * 4u + 15u) & ~15u;
+                const uint32_t vb = staged ? (uint32_t)(ve - vs) * (uint32_t)sizeof(T) : 0u;
+                const uint32_t cb = staged ? (uint32_t)(ce - cs) * 4u : 0u;
+                mbar_arrive_expect_tx(&full[s], rpb + vb + cb);
+                bulk_g2s(base, a.rowptr + r0, rpb, &full[s]);
+                if (staged) {
+                    bulk_g2s(base + val_off, a.vals + vs, vb, &full[s]);
+                    bulk_g2s(base + col_off, a.colidx + cs, cb, &full[s]);
+                }
+            }
         }
-        if (!mbar_wait_bounded(&bar, 0, kWaitLimitNs)) {
-            if (threadIdx.x == 0) atomicOr(&st->error, kErrTimeout);
-            mbar_wait_bounded(&bar, 0, kWaitLimitNs);  // let the copy land before the CTA exits
+        return;
+    }
+
+    // ---------------- consumers
+    const T *__restrict__ x = resolve_ptr<T>(a.e.x, st);
+    const T *__restrict__ x2 = resolve_ptr<T>(a.e.x2, st);
+    T *o0 = resolve_ptr<T>(a.e.out0, st);
+    const T *u0 = resolve_ptr<T>(a.e.u0, st);
+    const T *w0 = resolve_ptr<T>(a.e.w0, st);
+    T *o1 = resolve_ptr<T>(a.e.out1, st);
+    const T *u1 = resolve_ptr<T>(a.e.u1, st);
+    const T *w1 = resolve_ptr<T>(a.e.w1, st);
+    const T ca0 = (T)s_coef[0], cb0 = (T)s_coef[1], cc0 = (T)s_coef[2];
+    const T ca1 = (T)s_coef[3], cb1 = (T)s_coef[4], cc1 = (T)s_coef[5], c2 = (T)s_coef[6];
+    const int lr = tid / G;
+    const int lg = tid & (G - 1);
+    int i = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+        const int s = i % kSpmvStages;
+        if (!mbar_wait_bounded(&full[s], (i / kSpmvStages) & 1, kWaitLimitNs)) {
+            if (lane == 0) atomicOr(&st->error, kErrTimeout);
+            mbar_wait_bounded(&full[s], (i / kSpmvStages) & 1, kWaitLimitNs);
             return;
         }
-    }
-
-    const T *__restrict__ x = resolve_ptr<T>(a.e.x, st);
-    const int lr = threadIdx.x / G;
-    const int lane = threadIdx.x & (G - 1);
-    T acc = T(0);
-    if (lr < rows) {
-        const int k0 = s_rp[lr], k1 = s_rp[lr + 1];
-        int k = k0 + lane;
-        if (staged) {
-            for (; k + 3 * G < k1; k += 4 * G) {
-                const int c0 = s_col[k - cs], c1 = s_col[k + G - cs];
-                const int c2 = s_col[k + 2 * G - cs], c3 = s_col[k + 3 * G - cs];
-                const T x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
-                acc = fma(s_val[k - vs], x0, acc);
-                acc = fma(s_val[k + G - vs], x1, acc);
-                acc = fma(s_val[k + 2 * G - vs], x2, acc);
-                acc = fma(s_val[k + 3 * G - vs], x3, acc);
+        const unsigned char *base = smem + s * stage_bytes;
+        const int *s_rp = reinterpret_cast<const int *>(base);
+        const T *s_val = reinterpret_cast<const T *>(base + val_off);
+        const int *s_col = reinterpret_cast<const int *>(base + col_off);
+        const int r0 = (int)(tile * R);
+        const int rows = min(R, a.n - r0);
+        const int e0 = s_rp[0], e1 = s_rp[rows];
+        const int vs = e0 & ~(VA - 1), ve = (e1 + VA - 1) & ~(VA - 1);
+        const int cs = e0 & ~3, ce = (e1 + 3) & ~3;
+        const bool staged = (ve - vs) <= a.cap && (ce - cs) <= a.cap && e1 > e0;
+        T acc = T(0);
+        if (lr < rows) {
+            const int k0 = s_rp[lr], k1 = s_rp[lr + 1];
+            int k = k0 + lg;
+            if (staged) {
+                if (x2 == nullptr) {
+                    for (; k + 3 * G < k1; k += 4 * G) {
+                        const int q0 = s_col[k - cs], q1 = s_col[k + G - cs];
+                        const int q2 = s_col[k + 2 * G - cs], q3 = s_col[k + 3 * G - cs];
+                        const T y0 = __ldg(x + q0), y1 = __ldg(x + q1), y2 = __ldg(x + q2), y3 = __ldg(x + q3);
+                        acc = fma(s_val[k - vs], y0, acc);
+                        acc = fma(s_val[k + G - vs], y1, acc);
+                        acc = fma(s_val[k + 2 * G - vs], y2, acc);
+                        acc = fma(s_val[k + 3 * G - vs], y3, acc);
+                    }
+                    for (; k < k1; k += G) acc = fma(s_val[k - vs], __ldg(x + s_col[k - cs]), acc);
+                } else {
+                    for (; k < k1; k += G) {
+                        const int q = s_col[k - cs];
+                        acc = fma(s_val[k - vs], fma(c2, __ldg(x2 + q), __ldg(x + q)), acc);
+                    }
+                }
+            } else {
+                for (; k < k1; k += G) {
+                    const int q = __ldg(a.colidx + k);
+                    const T xv = x2 ? fma(c2, __ldg(x2 + q), __ldg(x + q)) : __ldg(x + q);
+                    acc = fma(__ldg(a.vals + k), xv, acc);
+                }
             }
-            for (; k < k1; k += G) acc = fma(s_val[k - vs], __ldg(x + s_col[k - cs]), acc);
-        } else {
-            for (; k < k1; k += G) acc = fma(__ldg(a.vals + k), __ldg(x + __ldg(a.colidx + k)), acc);
         }
-    }
-    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-
-    if (lane == 0 && lr < rows) {
-        const int r = r0 + lr;
-        {
-            T *o0 = resolve_ptr<T>(a.e.out0, st);
-            const T *u0 = resolve_ptr<T>(a.e.u0, st);
-            const T *w0 = resolve_ptr<T>(a.e.w0, st);
-            T v = (T)s_coef[0] * acc;
-            if (u0) v = fma((T)s_coef[1], u0[r], v);
-            if (w0) v = fma((T)s_coef[2], w0[r], v);
+        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lg == 0 && lr < rows) {
+            const int r = r0 + lr;
+            T v = ca0 * acc;
+            if (u0) v = fma(cb0, u0[r], v);
+            if (w0) v = fma(cc0, w0[r], v);
             o0[r] = v;
+            if (o1) {
+                T v1 = ca1 * acc;
+                if (u1) v1 = fma(cb1, u1[r], v1);
+                if (w1) v1 = fma(cc1, w1[r], v1);
+                o1[r] = v1;
+            }
         }
-        T *o1 = resolve_ptr<T>(a.e.out1, st);
-        if (o1) {
-            const T *u1 = resolve_ptr<T>(a.e.u1, st);
-            const T *w1 = resolve_ptr<T>(a.e.w1, st);
-            T v = (T)s_coef[3] * acc;
-            if (u1) v = fma((T)s_coef[4], u1[r], v);
-            if (w1) v = fma((T)s_coef[5], w1[r], v);
-            o1[r] = v;
-        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
     }
 }
 
-static size_t spmv_smem(int cap, size_t tsize) { return ((cap * tsize + 127) & ~(size_t)127) + (size_t)cap * 4; }
+namespace {
+template <typename T>
+int spmv_per_sm(int cap)
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<T>, kSpmvThreads, kSpmvStages * spmv_stage_bytes<T>(cap));
+    return nb > 0 ? nb : 1;
+}
+}  // namespace
 
 cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *st, int check_done, cudaStream_t s)
 {
     const int R = A.rows_per_tile;
-    const int grid = (A.n + R - 1) / R;
+    const long long ntiles = ((long long)A.n + R - 1) / R;
     if (prec == kF64) {
         SpmvArgs<double> a{A.n, A.rowptr, A.colidx, A.vals64, R, A.lanes_per_row, A.cap64, st, check_done, e};
-        k_spmv<double><<<grid, kThreads, spmv_smem(A.cap64, 8), s>>>(a);
+        long long g = (long long)A.spmv_blocks64;
+        if (g > ntiles) g = ntiles;
+        k_spmv<double><<<(int)g, kSpmvThreads, kSpmvStages * spmv_stage_bytes<double>(A.cap64), s>>>(a);
     } else {
         SpmvArgs<float> a{A.n, A.rowptr, A.colidx, A.vals32, R, A.lanes_per_row, A.cap32, st, check_done, e};
-        k_spmv<float><<<grid, kThreads, spmv_smem(A.cap32, 4), s>>>(a);
+        long long g = (long long)A.spmv_blocks32;
+        if (g > ntiles) g = ntiles;
+        k_spmv<float><<<(int)g, kSpmvThreads, kSpmvStages * spmv_stage_bytes<float>(A.cap32), s>>>(a);
     }
     return cudaGetLastError();
 }
 
-// Set once per process: the SpMV kernels may use more than 48 KB of dynamic shared memory.
-cudaError_t spmv_configure(int cap64, int cap32)
+// Sets the dynamic shared memory limit (for the largest staging capacity, once) and returns
+// the persistent grid sizes for this matrix's capacities.
+cudaError_t spmv_configure(DevMatrix *A)
 {
-    cudaError_t err = cudaFuncSetAttribute(k_spmv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)spmv_smem(cap64, 8));
-    if (err != cudaSuccess) return err;
-    return cudaFuncSetAttribute(k_spmv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)spmv_smem(cap32, 4));
+    static bool done = false;
+    if (!done) {
+        cudaError_t err = cudaFuncSetAttribute(k_spmv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(kSpmvStages * spmv_stage_bytes<double>(kSpmvCapMax)));
+        if (err != cudaSuccess) return err;
+        err = cudaFuncSetAttribute(k_spmv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(kSpmvStages * spmv_stage_bytes<float>(kSpmvCapMax)));
+        if (err != cudaSuccess) return err;
+        done = true;
+    }
+    A->spmv_blocks64 = spmv_per_sm<double>(A->cap64) * A->num_sms;
+    A->spmv_blocks32 = spmv_per_sm<float>(A->cap32) * A->num_sms;
+    return cudaSuccess;
 }
+
+int spmv_cap_max() { return kSpmvCapMax; }
 
 // ---------------------------------------------------------------- matrix-free epilogue (last root of the product form)
 
