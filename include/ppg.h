@@ -72,7 +72,9 @@ typedef struct {
                           this factor (iterative refinement step); <= 0 selects 1e-5 */
     int use_graph;     /* 1: run each restart cycle as one CUDA graph with device-side loop control;
                           0: host-enqueued kernels; < 0: library default (graph) */
-    int reserved[5];
+    int profile;       /* 1: time every SpMV and Gram-Schmidt launch with CUDA events and report their
+                          device time and algorithmic bytes in ppg_stats (adds a sync per cycle) */
+    int reserved[4];
 } ppg_opts;
 
 typedef struct {
@@ -88,6 +90,14 @@ typedef struct {
     int breakdowns;      /* cycles ended by a (lucky) Arnoldi breakdown */
     int reserved;
     double time_ms;      /* wall time of the call on the device stream (CUDA events) */
+    /* filled when ppg_opts.profile = 1 (launches that did work only):
+       the SpMV chain (p(A) steps and the SpMV that applies A) and the Gram-Schmidt passes
+       (block inner products, updates, norms, cycle-end combination).  Bytes are algorithmic:
+       matrix values and indices once, every vector read or written once per launch. */
+    double spmv_ms, spmv_bytes;
+    int64_t spmv_launches;
+    double gs_ms, gs_bytes;
+    int64_t gs_launches;
 } ppg_stats;
 
 /* ------------------------------------------------------------------ context */

@@ -40,7 +40,8 @@ PPG_F32 = 1
 # every symbol include/ppg.h declares
 EXPORTED = (
     "ppg_create", "ppg_destroy", "ppg_set_stream", "ppg_workspace_bytes", "ppg_set_workspace", "ppg_spmv",
-    "ppg_build_poly", "ppg_set_poly", "ppg_get_poly", "ppg_apply_poly", "ppg_solve", "ppg_solve_transpose",
+    "ppg_build_poly", "ppg_set_poly", "ppg_get_poly", "ppg_apply_poly", "ppg_solve",
+    "ppg_solve_transpose",
     "ppg_csr_outer", "ppg_arnoldi", "ppg_hessenberg_eigs", "ppg_fill_uniform", "ppg_status_string",
     "ppg_last_error", "ppg_version",
 )
@@ -48,14 +49,16 @@ EXPORTED = (
 
 class ppg_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class ppg_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("restarts", ctypes.c_int64), ("spmvs", ctypes.c_int64),
                 ("dots", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("relres_true", ctypes.c_double),
                 ("relres_est", ctypes.c_double), ("degree_used", ctypes.c_int), ("converged", ctypes.c_int),
-                ("breakdowns", ctypes.c_int), ("reserved", ctypes.c_int), ("time_ms", ctypes.c_double)]
+                ("breakdowns", ctypes.c_int), ("reserved", ctypes.c_int), ("time_ms", ctypes.c_double),
+                ("spmv_ms", ctypes.c_double), ("spmv_bytes", ctypes.c_double), ("spmv_launches", ctypes.c_int64),
+                ("gs_ms", ctypes.c_double), ("gs_bytes", ctypes.c_double), ("gs_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -208,18 +211,20 @@ def ppg_apply_poly(ctx, v, out):
     return _check(load_library().ppg_apply_poly(ctx, _ptr(v), _ptr(out), _prec_of(v)), "ppg_apply_poly")
 
 
-def _opts(precision=PPG_F64, inner_rtol=0.0, use_graph=-1):
+def _opts(precision=PPG_F64, inner_rtol=0.0, use_graph=-1, profile=0):
     o = ppg_opts()
     o.precision = precision
     o.inner_rtol = inner_rtol
     o.use_graph = use_graph
+    o.profile = profile
     return o
 
 
-def ppg_solve(ctx, b, x, tol=1e-8, restart=50, maxit=10000, precision=PPG_F64, inner_rtol=0.0, use_graph=-1):
+def ppg_solve(ctx, b, x, tol=1e-8, restart=50, maxit=10000, precision=PPG_F64, inner_rtol=0.0, use_graph=-1,
+              profile=0):
     """Solves A x = b in place (x holds x0).  Returns (status, stats dict)."""
     st = ppg_stats()
-    o = _opts(precision, inner_rtol, use_graph)
+    o = _opts(precision, inner_rtol, use_graph, profile)
     s = _check(load_library().ppg_solve(ctx, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit),
                                         ctypes.byref(o), ctypes.byref(st)), "ppg_solve")
     return s, st.as_dict()
@@ -336,10 +341,11 @@ class Solver:
         ppg_apply_poly(self.ctx, v, out)
         return out
 
-    def solve(self, b, x=None, tol=1e-8, restart=50, maxit=10000, precision=PPG_F64, inner_rtol=0.0, use_graph=-1):
+    def solve(self, b, x=None, tol=1e-8, restart=50, maxit=10000, precision=PPG_F64, inner_rtol=0.0, use_graph=-1,
+              profile=0):
         self._workspace(restart, 0, precision)
         x = self._torch.zeros_like(b) if x is None else x
-        status, stats = ppg_solve(self.ctx, b, x, tol, restart, maxit, precision, inner_rtol, use_graph)
+        status, stats = ppg_solve(self.ctx, b, x, tol, restart, maxit, precision, inner_rtol, use_graph, profile)
         return x, SolveInfo(status, stats)
 
     def solve_transpose(self, g, lam=None, tol=1e-8, restart=50, maxit=10000, precision=PPG_F64, inner_rtol=0.0):

@@ -95,6 +95,22 @@ struct ppg_ctx {
     ppg_ctx *tctx = nullptr;  // transposed matrix (adjoint)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long launches = 0;
+
+    // profiling (ppg_opts.profile): an event pair around every SpMV / Gram-Schmidt launch
+    struct ProfRec {
+        int cls;  // 0 SpMV, 1 Gram-Schmidt
+        cudaEvent_t a, b;
+        double bytes;    // algorithmic bytes (Gram-Schmidt: per basis column in kcol_bytes)
+        double kcol_bytes;
+        int j;           // iteration index of the launch within its cycle, -2 at the cycle end
+        int valid;
+    };
+    bool prof = false;
+    int prof_j = -1;
+    std::vector<ProfRec> recs;
+    size_t rec_first = 0;  // first record of the current cycle
+    std::vector<cudaEvent_t> evpool;
+    size_t evnext = 0;
 };
 
 namespace {
@@ -180,6 +196,59 @@ SpmvEpi epi_none()
     return e;
 }
 
+// ---------------------------------------------------------------- profiling helpers
+
+cudaEvent_t prof_event(ppg_ctx *c)
+{
+    if (c->evnext == c->evpool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->evpool.push_back(e);
+    }
+    return c->evpool[c->evnext++];
+}
+
+// Records the start event of a profiled launch (null when profiling is off or events ran out).
+cudaEvent_t prof_begin(ppg_ctx *c, cudaStream_t s)
+{
+    if (!c->prof) return nullptr;
+    cudaEvent_t a = prof_event(c);
+    if (a) cudaEventRecord(a, s);
+    return a;
+}
+
+void prof_end(ppg_ctx *c, cudaStream_t s, cudaEvent_t a, int cls, double bytes, double kcol_bytes)
+{
+    if (!a) return;
+    cudaEvent_t b = prof_event(c);
+    if (!b) return;
+    cudaEventRecord(b, s);
+    c->recs.push_back(ppg_ctx::ProfRec{cls, a, b, bytes, kcol_bytes, c->prof_j, 1});
+}
+
+bool same_vec(const VecRef &u, const VecRef &v)
+{
+    return u.base == v.base && u.ld == v.ld && u.col == v.col && u.follow == v.follow;
+}
+
+// Algorithmic bytes of one SpMV launch: values and column indices once, row pointers once,
+// each distinct vector read once and each output written once.
+double spmv_bytes(const DevMatrix &A, int prec, const SpmvEpi &e)
+{
+    const double es = prec == kF64 ? 8.0 : 4.0;
+    double b = (double)A.nnz * (es + 4.0) + 4.0 * (A.n + 1.0);
+    const VecRef *reads[6] = {&e.x, &e.x2, &e.u0, &e.w0, &e.u1, &e.w1};
+    int distinct = 0;
+    for (int i = 0; i < 6; ++i) {
+        if (!reads[i]->base) continue;
+        bool seen = false;
+        for (int q = 0; q < i; ++q) seen = seen || (reads[q]->base && same_vec(*reads[q], *reads[i]));
+        if (!seen) ++distinct;
+    }
+    const int writes = (e.out0.base ? 1 : 0) + (e.out1.base ? 1 : 0);
+    return b + (double)A.n * es * (distinct + writes);
+}
+
 struct Exec {
     ppg_ctx *c;
     const DevMatrix *A;
@@ -189,7 +258,9 @@ struct Exec {
     ppg_status spmv(const SpmvEpi &e, int check)
     {
         c->launches++;
+        cudaEvent_t ev = prof_begin(c, s);
         PPG_CK(launch_spmv(*A, prec, e, c->st, check, s));
+        prof_end(c, s, ev, 0, spmv_bytes(*A, prec, e), 0.0);
         return PPG_OK;
     }
     ppg_status axpy(const SpmvEpi &e, int check)
@@ -375,7 +446,13 @@ struct Iter {
         a.kcols_from_k = from_k;
         a.partials = L->partials;
         x->c->launches++;
+        cudaEvent_t ev = prof_begin(x->c, x->s);
         PPG_CK(launch_gs(x->prec, kcols, x->c->ld, x->c->num_sms, a, x->c->st, x->s));
+        // bytes: k columns read, w read (except when combining), one vector written (passes 2-4)
+        const double col = (double)x->A->n * (x->prec == kF64 ? 8.0 : 4.0);
+        const double fixed = col * ((op != kGsCombine ? 1.0 : 0.0) + (op != kGsDot ? 1.0 : 0.0));
+        prof_end(x->c, x->s, ev, 1, fixed, col);
+        if (from_k == 0 && x->c->prof && !x->c->recs.empty()) x->c->recs.back().bytes += col * kcols;
         return PPG_OK;
     }
 
@@ -383,6 +460,7 @@ struct Iter {
     // that ended early return at once)
     ppg_status iteration(int j)
     {
+        x->c->prof_j = j;
         char *tmp[4] = {L->vec[1], L->vec[2], L->vec[3], L->vec[4]};
         PPG_TRY(x->poly_then_A(vcol(L->basis, x->c->ld, 0), x->c->st->sigma, vfix(L->vec[0]), tmp, kSkipIfDone));
         PPG_TRY(gs(kGsDot, 0, nullptr, 0, j + 1));
@@ -394,6 +472,7 @@ struct Iter {
     // x += p(A) V y with the coefficients the last pass-3 finalisation left in coef.
     ppg_status cycle_end(double *xsol)
     {
+        x->c->prof_j = -2;
         char *z = L->vec[5], *e = L->vec[6];
         PPG_TRY(gs(kGsCombine, 1, z, 0, maxcols));
         const void *corr = z;
@@ -510,6 +589,43 @@ ppg_status build_roots(ppg_ctx *c, int deg, const Layout &L, int *used)
     return PPG_OK;
 }
 
+// Profiling: after a cycle's launches, read how many iterations really ran (later launches of
+// the cycle returned at once) and how many columns the cycle end combined, and mark records.
+ppg_status prof_close_cycle(ppg_ctx *c)
+{
+    PPG_TRY(read_state(c));
+    const int done = c->h_st->j, k = c->h_st->k;
+    for (size_t i = c->rec_first; i < c->recs.size(); ++i) {
+        ppg_ctx::ProfRec &r = c->recs[i];
+        if (r.j >= 0) {
+            r.valid = r.j < done;
+        } else {
+            r.valid = k > 0;
+            if (r.cls == 1) r.bytes += r.kcol_bytes * k;
+        }
+    }
+    c->rec_first = c->recs.size();
+    return PPG_OK;
+}
+
+void prof_collect(ppg_ctx *c, ppg_stats *st)
+{
+    for (const ppg_ctx::ProfRec &r : c->recs) {
+        if (!r.valid) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) continue;
+        if (r.cls == 0) {
+            st->spmv_ms += ms;
+            st->spmv_bytes += r.bytes;
+            st->spmv_launches += 1;
+        } else {
+            st->gs_ms += ms;
+            st->gs_bytes += r.bytes;
+            st->gs_launches += 1;
+        }
+    }
+}
+
 ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int restart, int maxit,
                       const ppg_opts *opts, ppg_stats *stats)
 {
@@ -532,6 +648,11 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
 
     Exec ex{c, &c->A, prec, c->stream};
     Iter it{&ex, &L, ncols};
+    c->prof = opts && opts->profile;
+    c->recs.clear();
+    c->rec_first = 0;
+    c->evnext = 0;
+    c->prof_j = -1;
 
     PPG_TRY(init_cycle_state(c, 0, restart, maxit, tol, inner));
     c->launches++;
@@ -550,6 +671,7 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
         while (!c->h_st->stop) {
             for (int j = 0; j < restart; ++j) PPG_TRY(it.iteration(j));
             PPG_TRY(it.cycle_end(x));
+            if (c->prof) PPG_TRY(prof_close_cycle(c));
             c->launches++;
             PPG_CK(launch_residual(c->A, prec, b, x, L.basis, c->st, L.partials, c->stream));
             residuals++;
@@ -575,7 +697,9 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
         stats->converged = h.converged;
         stats->breakdowns = h.n_breakdowns;
         stats->time_ms = ms;
+        if (c->prof) prof_collect(c, stats);
     }
+    c->prof = false;
     if (h.error & kErrNonfinite) return fail(PPG_ERR_NONFINITE, "non-finite value in a reduction");
     return h.converged ? PPG_OK : PPG_ERR_NOT_CONVERGED;
 }
@@ -726,6 +850,7 @@ void ppg_destroy(ppg_ctx *c)
     cudaFreeHost(c->h_small);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
     delete c;
 }
 

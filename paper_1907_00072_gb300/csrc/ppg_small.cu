@@ -19,15 +19,18 @@ namespace ppg {
 // roots_out: 2k doubles (re, im) in application order.  table_out: 2k doubles, per root
 // position: real -> (1/theta, 0); first of a pair -> (2a/q, 1/q); second of a pair -> (0, 0).
 // status_out[0]: 0 ok, 1 QR did not converge, 2 singular H_k, 3 zero or non-finite root.
-__global__ void k_roots(const Cycle *st, int k, double *roots_out, double *table_out, int *status_out)
+__global__ void __launch_bounds__(32) k_roots(const Cycle *st, int k, double *roots_out, double *table_out,
+                                              int *status_out)
 {
     __shared__ double work[kSmallMax * kSmallMax + kSmallMax];
-    __shared__ double wr[kSmallMax], wi[kSmallMax];
+    __shared__ double wr[kSmallMax], wi[kSmallMax], score[kSmallMax];
     __shared__ int order[kSmallMax], used[kSmallMax];
-    if (threadIdx.x != 0) return;
-    int status = harmonic_ritz(k, st->H, kLdH, wr, wi, work);
+    const int lane = threadIdx.x;
+    int status = harmonic_ritz(k, st->H, kLdH, wr, wi, work, lane, 32);
+    if (status == 0) leja_order(k, wr, wi, order, used, score, lane, 32);
+    __syncwarp();
+    if (lane != 0) return;
     if (status == 0) {
-        leja_order(k, wr, wi, order, used);
         for (int p = 0; p < k; ++p) {
             const double re = wr[order[p]], im = wi[order[p]];
             roots_out[2 * p] = re;
@@ -88,19 +91,24 @@ cudaError_t launch_roots(const Cycle *st, int k, double *roots_out, double *tabl
     return cudaGetLastError();
 }
 
-__global__ void k_hess_eigs(int k, const double *H, int ld, double *wr, double *wi, int *status_out)
+__global__ void __launch_bounds__(32) k_hess_eigs(int k, const double *H, int ld, double *wr, double *wi,
+                                                  int *status_out)
 {
     __shared__ double m[kSmallMax * kSmallMax];
     __shared__ double r[kSmallMax], im[kSmallMax];
-    if (threadIdx.x != 0) return;
-    for (int j = 0; j < k; ++j)
-        for (int i = 0; i < k; ++i) m[i + j * k] = (i <= j + 1) ? H[i + (long)j * ld] : 0.0;
-    const int st = hess_eigs(k, m, k, r, im);
-    for (int i = 0; i < k; ++i) {
+    const int lane = threadIdx.x;
+    for (int t = lane; t < k * k; t += 32) {
+        const int i = t % k, j = t / k;
+        m[i + j * k] = (i <= j + 1) ? H[i + (long)j * ld] : 0.0;
+    }
+    __syncwarp();
+    const int st = hess_eigs(k, m, k, r, im, lane, 32);
+    __syncwarp();
+    for (int i = lane; i < k; i += 32) {
         wr[i] = r[i];
         wi[i] = im[i];
     }
-    status_out[0] = st;
+    if (lane == 0) status_out[0] = st;
 }
 
 cudaError_t launch_hess_eigs(int k, const double *H, int ld, double *wr, double *wi, int *status_out, cudaStream_t s)
