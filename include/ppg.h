@@ -165,6 +165,26 @@ ppg_status ppg_get_poly(ppg_ctx *ctx, int *basis, int *degree, double *coef_h, i
  * device vectors of length n of the matching type and must not overlap. */
 ppg_status ppg_apply_poly(ppg_ctx *ctx, const void *v, void *out, int precision);
 
+/* Allocation-free variant of ppg_apply_poly (the paper has no counterpart; this is a service of the
+ * library).  For callers that may not allocate device memory at the point of the call -- for example
+ * a service that reserves its whole device-memory budget at start-up, or code running where a
+ * cudaMalloc could fail or must not happen -- it computes out = p(A) v exactly like ppg_apply_poly
+ * but takes its working vectors from a fixed array compiled into the library (one array per GPU that
+ * loads the library, kept until the process exits) instead of the context's workspace, and it calls
+ * no allocating routine.
+ *   - Limit: n <= 65536 rows (5 working vectors of 65536 float64 entries, 2.5 MiB).  Larger
+ *     matrices return PPG_ERR_INVALID_ARG; use ppg_apply_poly.
+ *   - precision PPG_F32 needs the context's float32 copy of the matrix, which this call does not
+ *     create: make one float32 ppg_spmv / ppg_apply_poly / ppg_solve call first (else
+ *     PPG_ERR_INVALID_ARG).
+ *   - The first call on a device looks up the array's device address (once per device, with that
+ *     device current); make that first call before any stream capture.
+ *   - Every call uses the same array, which keeps the previous call's contents; calls whose work
+ *     overlaps on the GPU (different streams, or concurrent host threads) race with each other.
+ *     Calls enqueued on one stream run one after another and are safe.
+ * Asynchronous on the context's stream, like ppg_apply_poly. */
+ppg_status ppg_apply_poly_noalloc(ppg_ctx *ctx, const void *v, void *out, int precision);
+
 /* ------------------------------------------------------------------ solvers */
 
 /* Solves A x = b by right-preconditioned GMRES(restart) with the current polynomial (the identity if

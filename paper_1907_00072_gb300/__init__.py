@@ -40,7 +40,7 @@ PPG_F32 = 1
 # every symbol include/ppg.h declares
 EXPORTED = (
     "ppg_create", "ppg_destroy", "ppg_set_stream", "ppg_workspace_bytes", "ppg_set_workspace", "ppg_spmv",
-    "ppg_build_poly", "ppg_set_poly", "ppg_get_poly", "ppg_apply_poly", "ppg_solve",
+    "ppg_build_poly", "ppg_set_poly", "ppg_get_poly", "ppg_apply_poly", "ppg_apply_poly_noalloc", "ppg_solve",
     "ppg_solve_transpose",
     "ppg_csr_outer", "ppg_arnoldi", "ppg_hessenberg_eigs", "ppg_fill_uniform", "ppg_status_string",
     "ppg_last_error", "ppg_version",
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
         "ppg_set_poly": (I, [P, I, I, P]),
         "ppg_get_poly": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), P, I, ctypes.POINTER(D)]),
         "ppg_apply_poly": (I, [P, P, P, I]),
+        "ppg_apply_poly_noalloc": (I, [P, P, P, I]),
         "ppg_solve": (I, [P, P, P, D, I, I, ctypes.POINTER(ppg_opts), ctypes.POINTER(ppg_stats)]),
         "ppg_solve_transpose": (I, [P, P, P, D, I, I, ctypes.POINTER(ppg_opts), ctypes.POINTER(ppg_stats)]),
         "ppg_csr_outer": (I, [P, P, P, D, P]),
@@ -209,6 +210,12 @@ def ppg_get_poly(ctx):
 
 def ppg_apply_poly(ctx, v, out):
     return _check(load_library().ppg_apply_poly(ctx, _ptr(v), _ptr(out), _prec_of(v)), "ppg_apply_poly")
+
+
+def ppg_apply_poly_noalloc(ctx, v, out):
+    """ppg_apply_poly without any device allocation (n <= 65536; see include/ppg.h)."""
+    return _check(load_library().ppg_apply_poly_noalloc(ctx, _ptr(v), _ptr(out), _prec_of(v)),
+                  "ppg_apply_poly_noalloc")
 
 
 def _opts(precision=PPG_F64, inner_rtol=0.0, use_graph=-1, profile=0):

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -718,6 +719,42 @@ ppg_status set_device(const ppg_ctx *c)
 
 }  // namespace
 
+// =================================================================== allocation-free apply
+
+// Device scratch for ppg_apply_poly_noalloc: the input copy, the output and three working
+// vectors of at most kNoAllocMaxN entries each, in one file-scope array that every GPU
+// loading the library keeps until the process exits.
+namespace {
+constexpr long long kNoAllocMaxN = 65536;
+constexpr int kNoAllocVecs = 5;
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocVecs * kNoAllocMaxN];
+
+namespace {
+
+// Device address of g_noalloc_scratch on `device` (which must be current).  In host code the
+// symbol's name only stands for the device array, so the address is looked up once per device
+// with cudaGetSymbolAddress and cached.
+ppg_status noalloc_scratch(int device, char **out)
+{
+    static std::mutex mu;
+    static void *addr[256] = {};
+    if (device < 0 || device >= 256) return fail(PPG_ERR_INVALID_ARG, "device ordinal %d out of range", device);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(PPG_ERR_CUDA, "cudaGetSymbolAddress(g_noalloc_scratch): %s", cudaGetErrorString(e));
+        addr[device] = p;
+    }
+    *out = static_cast<char *>(addr[device]);
+    return PPG_OK;
+}
+
+}  // namespace
+
 // =================================================================== C ABI
 
 extern "C" {
@@ -1019,6 +1056,33 @@ ppg_status ppg_apply_poly(ppg_ctx *c, const void *v, void *out, int precision)
     char *tmp[3] = {L.vec[2], L.vec[3], L.vec[4]};
     PPG_TRY(ex.poly_apply(vfix(L.vec[0]), nullptr, vfix(L.vec[1]), tmp, kNoCheck));
     PPG_CK(launch_copy_in(c->A.n, precision, L.vec[1], out, c->stream));
+    return PPG_OK;
+}
+
+ppg_status ppg_apply_poly_noalloc(ppg_ctx *c, const void *v, void *out, int precision)
+{
+    PPG_TRY(check_ctx(c));
+    if (!v || !out) return fail(PPG_ERR_INVALID_ARG, "null vector");
+    if (precision != PPG_F64 && precision != PPG_F32) return fail(PPG_ERR_INVALID_ARG, "unknown precision");
+    if (!c->has_poly) return fail(PPG_ERR_NO_POLY, "no polynomial has been built or set");
+    if (c->A.n > kNoAllocMaxN)
+        return fail(PPG_ERR_INVALID_ARG,
+                    "ppg_apply_poly_noalloc handles at most %lld rows (n = %d); use ppg_apply_poly", kNoAllocMaxN,
+                    c->A.n);
+    if (precision == PPG_F32 && !c->d_vals32)
+        return fail(PPG_ERR_INVALID_ARG,
+                    "the float32 copy of the matrix does not exist yet and this call may not allocate it: make one "
+                    "float32 ppg_spmv, ppg_apply_poly or ppg_solve call first");
+    PPG_TRY(set_device(c));
+    char *base = nullptr;
+    PPG_TRY(noalloc_scratch(c->device, &base));
+    char *vec[kNoAllocVecs];
+    for (int i = 0; i < kNoAllocVecs; ++i) vec[i] = base + (size_t)i * kNoAllocMaxN * sizeof(double);
+    PPG_CK(launch_copy_in(c->A.n, precision, v, vec[0], c->stream));
+    Exec ex{c, &c->A, precision, c->stream};
+    char *tmp[3] = {vec[2], vec[3], vec[4]};
+    PPG_TRY(ex.poly_apply(vfix(vec[0]), nullptr, vfix(vec[1]), tmp, kNoCheck));
+    PPG_CK(launch_copy_in(c->A.n, precision, vec[1], out, c->stream));
     return PPG_OK;
 }
 
