@@ -173,6 +173,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=60)
+    ap.add_argument("--profile-harness", action="store_true",
+                    help="for ncu: build the polynomial and run 20 iterations of one solve, print no benchmark line")
     args = ap.parse_args()
 
     world, rank, local = dist_init(args)
@@ -195,6 +197,15 @@ def main():
     v0 = T(v0_h)
     prec = ppg.PPG_F32 if args.precision == "f32" else ppg.PPG_F64
     stream = torch.cuda.current_stream()
+
+    if args.profile_harness:
+        s.build_poly(args.degree, ppg.PPG_BASIS_ROOTS, v0=v0)
+        _, info = s.solve(b, tol=1e-8, restart=50, maxit=20, precision=prec)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_harness": True, "iterations": info.stats["iterations"],
+                          "launches": info.stats["kernel_launches"]}))
+        s.close()
+        return
 
     def step(deg=args.degree, precision=prec, bvec=b):
         used, _ = s.build_poly(deg, ppg.PPG_BASIS_ROOTS, v0=v0)

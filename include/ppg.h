@@ -69,7 +69,7 @@ enum {
 typedef struct {
     int precision;     /* PPG_F64 (default) or PPG_F32 */
     double inner_rtol; /* PPG_F32 only: a restart cycle also ends when its residual estimate has dropped by
-                          this factor (iterative refinement step); <= 0 selects 1e-5 */
+                          this factor (iterative refinement step); <= 0 selects 1e-6 */
     int use_graph;     /* 1: run each restart cycle as one CUDA graph with device-side loop control;
                           0: host-enqueued kernels; < 0: library default (graph) */
     int profile;       /* 1: time every SpMV and Gram-Schmidt launch with CUDA events and report their

@@ -637,7 +637,7 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
     if (prec != PPG_F64 && prec != PPG_F32) return fail(PPG_ERR_INVALID_ARG, "unknown precision");
     double inner = 0.0;
     if (prec == PPG_F32) {
-        inner = (opts && opts->inner_rtol > 0.0) ? opts->inner_rtol : 1e-5;
+        inner = (opts && opts->inner_rtol > 0.0) ? opts->inner_rtol : 1e-6;
         PPG_TRY(ensure_f32(c));
     }
     const size_t es = prec == PPG_F64 ? 8 : 4;

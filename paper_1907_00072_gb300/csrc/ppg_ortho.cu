@@ -27,7 +27,7 @@ struct GsCfg {
     static constexpr int TR = 32768 / (KM * (int)sizeof(T));             // rows per tile
     static constexpr int RPT = TR >= kThreads ? TR / kThreads : 1;       // rows per thread (update phase)
     static constexpr int TPR = TR >= kThreads ? 1 : kThreads / TR;       // threads per row (update phase)
-    static constexpr int RPL = TR / 32;                                  // rows per lane (dot phase)
+    static constexpr int RPL = TR / 32;                                  // rows per lane (dot phase, stride 32)
     static constexpr int CPW = (KM + 7) / 8;                             // columns per warp (dot phase)
     static constexpr int STAGE = KM * TR + TR;                           // elements per pipeline stage
 };
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
                 if (c < k) {
                     T s = T(0);
 #pragma unroll
-                    for (int r = 0; r < RPL; ++r) s = fma(sU[c * TR + lane * RPL + r], dotvec[lane * RPL + r], s);
+                    for (int r = 0; r < RPL; ++r) s = fma(sU[c * TR + r * 32 + lane], dotvec[r * 32 + lane], s);
                     acc[i].add(s);
                 }
             }

@@ -95,7 +95,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 // lane applies the fused epilogue and the warp releases the stage.  Tiles whose
 // non-zeros exceed the stage read values and columns from global memory instead.
 template <typename T>
-__global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a)
+__global__ void __launch_bounds__(kSpmvThreads, 3) k_spmv(SpmvArgs<T> a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[kSpmvStages];
@@ -137,8 +137,19 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a)
     if (wid == kSpmvConsumerWarps) {
         // ---------------- producer
         if (lane == 0) {
+            // the next tile's non-zero range is loaded one tile ahead, so that its latency
+            // overlaps the wait for a free stage
+            auto bounds = [&](long long t, int &e0, int &e1) {
+                const int r0 = (int)(t * R);
+                e0 = __ldg(a.rowptr + r0);
+                e1 = __ldg(a.rowptr + min(r0 + R, a.n));
+            };
+            int ne0 = 0, ne1 = 0;
+            if (blockIdx.x < ntiles) bounds(blockIdx.x, ne0, ne1);
             int i = 0;
             for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+                const int e0 = ne0, e1 = ne1;
+                if (tile + gridDim.x < ntiles) bounds(tile + gridDim.x, ne0, ne1);
                 const int s = i % kSpmvStages, round = i / kSpmvStages;
                 if (round > 0 && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitLimitNs)) {
                     atomicOr(&st->error, kErrTimeout);
@@ -146,7 +157,6 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a)
                 }
                 const int r0 = (int)(tile * R);
                 const int rows = min(R, a.n - r0);
-                const int e0 = __ldg(a.rowptr + r0), e1 = __ldg(a.rowptr + r0 + rows);
                 const int vs = e0 & ~(VA - 1), ve = (e1 + VA - 1) & ~(VA - 1);
                 const int cs = e0 & ~3, ce = (e1 + 3) & ~3;
                 const bool staged = (ve - vs) <= a.cap && (ce - cs) <= a.cap && e1 > e0;
@@ -197,29 +207,43 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a)
         const int cs = e0 & ~3, ce = (e1 + 3) & ~3;
         const bool staged = (ve - vs) <= a.cap && (ce - cs) <= a.cap && e1 > e0;
         T acc = T(0);
+        const int r = r0 + lr;
+        // epilogue operands first: their loads overlap the gathers below
+        T pu0 = T(0), pw0 = T(0), pu1 = T(0), pw1 = T(0);
+        if (lg == 0 && lr < rows) {
+            if (u0) pu0 = u0[r];
+            if (w0) pw0 = w0[r];
+            if (o1) {
+                if (u1) pu1 = u1[r];
+                if (w1) pw1 = w1[r];
+            }
+        }
         if (lr < rows) {
             const int k0 = s_rp[lr], k1 = s_rp[lr + 1];
-            int k = k0 + lg;
             if (staged) {
-                if (x2 == nullptr) {
-                    for (; k + 3 * G < k1; k += 4 * G) {
-                        const int q0 = s_col[k - cs], q1 = s_col[k + G - cs];
-                        const int q2 = s_col[k + 2 * G - cs], q3 = s_col[k + 3 * G - cs];
-                        const T y0 = __ldg(x + q0), y1 = __ldg(x + q1), y2 = __ldg(x + q2), y3 = __ldg(x + q3);
-                        acc = fma(s_val[k - vs], y0, acc);
-                        acc = fma(s_val[k + G - vs], y1, acc);
-                        acc = fma(s_val[k + 2 * G - vs], y2, acc);
-                        acc = fma(s_val[k + 3 * G - vs], y3, acc);
+                // all of a lane's gathers (up to 8 per batch) are issued before the first FMA
+                for (int k = k0 + lg; k < k1; k += 8 * G) {
+                    int q[8];
+                    T xv[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int kk = k + t * G;
+                        q[t] = kk < k1 ? s_col[kk - cs] : -1;
                     }
-                    for (; k < k1; k += G) acc = fma(s_val[k - vs], __ldg(x + s_col[k - cs]), acc);
-                } else {
-                    for (; k < k1; k += G) {
-                        const int q = s_col[k - cs];
-                        acc = fma(s_val[k - vs], fma(c2, __ldg(x2 + q), __ldg(x + q)), acc);
+                    if (x2 == nullptr) {
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) xv[t] = q[t] >= 0 ? __ldg(x + q[t]) : T(0);
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 8; ++t)
+                            xv[t] = q[t] >= 0 ? fma(c2, __ldg(x2 + q[t]), __ldg(x + q[t])) : T(0);
                     }
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        if (q[t] >= 0) acc = fma(s_val[k + t * G - vs], xv[t], acc);
                 }
             } else {
-                for (; k < k1; k += G) {
+                for (int k = k0 + lg; k < k1; k += G) {
                     const int q = __ldg(a.colidx + k);
                     const T xv = x2 ? fma(c2, __ldg(x2 + q), __ldg(x + q)) : __ldg(x + q);
                     acc = fma(__ldg(a.vals + k), xv, acc);
@@ -228,15 +252,14 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs<T> a)
         }
         for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lg == 0 && lr < rows) {
-            const int r = r0 + lr;
             T v = ca0 * acc;
-            if (u0) v = fma(cb0, u0[r], v);
-            if (w0) v = fma(cc0, w0[r], v);
+            if (u0) v = fma(cb0, pu0, v);
+            if (w0) v = fma(cc0, pw0, v);
             o0[r] = v;
             if (o1) {
                 T v1 = ca1 * acc;
-                if (u1) v1 = fma(cb1, u1[r], v1);
-                if (w1) v1 = fma(cc1, w1[r], v1);
+                if (u1) v1 = fma(cb1, pu1, v1);
+                if (w1) v1 = fma(cc1, pw1, v1);
                 o1[r] = v1;
             }
         }
