@@ -317,11 +317,12 @@ def main():
                                + " (SpMV chain: fused Horner / root steps of p(A) and the SpMV with A)",
                      "achieved": round(spmv_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(spmv_gbs / hbm, 3),
                      "peak_source": "measured" if "hbm_gbs" in pk else "fallback", "traffic": None,
-                     "launches": ps["spmv_launches"], "bytes_per_launch": round(ps["spmv_bytes"] / max(ps["spmv_launches"], 1)),
-                     "ms_per_launch": round(ps["spmv_ms"] / max(ps["spmv_launches"], 1), 5)},
+                     "timed_segments": ps["spmv_segments"], "ms_total": round(ps["spmv_ms"], 3),
+                     "bytes_total": ps["spmv_bytes"]},
         "roofline_ortho": {"bound": "hbm", "kernel": "k_gs (two-pass classical Gram-Schmidt)",
                            "achieved": round(gs_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gs_gbs / hbm, 3),
-                           "launches": ps["gs_launches"], "ms_total": round(ps["gs_ms"], 3)},
+                           "timed_segments": ps["gs_segments"], "ms_total": round(ps["gs_ms"], 3),
+                           "bytes_total": ps["gs_bytes"]},
         "spmv_plain": {"achieved": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
                        "ms_per_launch": round(spmv_ms, 5), "bytes_per_launch": spmv_bytes},
         "cpu_baseline": cpu,

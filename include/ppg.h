@@ -90,14 +90,16 @@ typedef struct {
     int breakdowns;      /* cycles ended by a (lucky) Arnoldi breakdown */
     int reserved;
     double time_ms;      /* wall time of the call on the device stream (CUDA events) */
-    /* filled when ppg_opts.profile = 1 (launches that did work only):
-       the SpMV chain (p(A) steps and the SpMV that applies A) and the Gram-Schmidt passes
-       (block inner products, updates, norms, cycle-end combination).  Bytes are algorithmic:
+    /* filled when ppg_opts.profile = 1, for launches that did work: device time and algorithmic
+       bytes of the SpMV chain (p(A) steps and the SpMV that applies A) and of the Gram-Schmidt
+       passes (block inner products, updates, norms, cycle-end combination).  Each run of
+       consecutive launches of one kind (one iteration's SpMV chain, its three passes, ...) is
+       timed by one pair of CUDA events; *_segments counts those runs.  Bytes are algorithmic:
        matrix values and indices once, every vector read or written once per launch. */
     double spmv_ms, spmv_bytes;
-    int64_t spmv_launches;
+    int64_t spmv_segments;
     double gs_ms, gs_bytes;
-    int64_t gs_launches;
+    int64_t gs_segments;
 } ppg_stats;
 
 /* ------------------------------------------------------------------ context */

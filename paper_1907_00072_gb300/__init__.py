@@ -57,8 +57,8 @@ class ppg_stats(ctypes.Structure):
                 ("dots", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("relres_true", ctypes.c_double),
                 ("relres_est", ctypes.c_double), ("degree_used", ctypes.c_int), ("converged", ctypes.c_int),
                 ("breakdowns", ctypes.c_int), ("reserved", ctypes.c_int), ("time_ms", ctypes.c_double),
-                ("spmv_ms", ctypes.c_double), ("spmv_bytes", ctypes.c_double), ("spmv_launches", ctypes.c_int64),
-                ("gs_ms", ctypes.c_double), ("gs_bytes", ctypes.c_double), ("gs_launches", ctypes.c_int64)]
+                ("spmv_ms", ctypes.c_double), ("spmv_bytes", ctypes.c_double), ("spmv_segments", ctypes.c_int64),
+                ("gs_ms", ctypes.c_double), ("gs_bytes", ctypes.c_double), ("gs_segments", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -107,6 +107,7 @@ struct ppg_ctx {
         int valid;
     };
     bool prof = false;
+    bool prof_open = false;
     int prof_j = -1;
     std::vector<ProfRec> recs;
     size_t rec_first = 0;  // first record of the current cycle
@@ -209,22 +210,38 @@ cudaEvent_t prof_event(ppg_ctx *c)
     return c->evpool[c->evnext++];
 }
 
-// Records the start event of a profiled launch (null when profiling is off or events ran out).
-cudaEvent_t prof_begin(ppg_ctx *c, cudaStream_t s)
+// Profiling works on segments: runs of consecutive launches of one class (the SpMV chain of an
+// iteration, its three Gram-Schmidt passes, ...) enqueued back to back.  One event pair brackets
+// each segment, so the measured time is the device time of those launches without per-launch
+// event overhead; each launch adds its algorithmic bytes to the open segment.
+void prof_open(ppg_ctx *c, cudaStream_t s, int cls)
 {
-    if (!c->prof) return nullptr;
+    if (!c->prof) return;
     cudaEvent_t a = prof_event(c);
-    if (a) cudaEventRecord(a, s);
-    return a;
+    if (!a) return;
+    cudaEventRecord(a, s);
+    c->recs.push_back(ppg_ctx::ProfRec{cls, a, nullptr, 0.0, 0.0, c->prof_j, 1});
+    c->prof_open = true;
 }
 
-void prof_end(ppg_ctx *c, cudaStream_t s, cudaEvent_t a, int cls, double bytes, double kcol_bytes)
+void prof_close(ppg_ctx *c, cudaStream_t s)
 {
-    if (!a) return;
+    if (!c->prof || !c->prof_open) return;
+    c->prof_open = false;
     cudaEvent_t b = prof_event(c);
-    if (!b) return;
+    if (!b) {
+        c->recs.pop_back();
+        return;
+    }
     cudaEventRecord(b, s);
-    c->recs.push_back(ppg_ctx::ProfRec{cls, a, b, bytes, kcol_bytes, c->prof_j, 1});
+    c->recs.back().b = b;
+}
+
+void prof_add(ppg_ctx *c, double bytes, double kcol_bytes)
+{
+    if (!c->prof || !c->prof_open) return;
+    c->recs.back().bytes += bytes;
+    c->recs.back().kcol_bytes += kcol_bytes;
 }
 
 bool same_vec(const VecRef &u, const VecRef &v)
@@ -259,9 +276,8 @@ struct Exec {
     ppg_status spmv(const SpmvEpi &e, int check)
     {
         c->launches++;
-        cudaEvent_t ev = prof_begin(c, s);
         PPG_CK(launch_spmv(*A, prec, e, c->st, check, s));
-        prof_end(c, s, ev, 0, spmv_bytes(*A, prec, e), 0.0);
+        prof_add(c, spmv_bytes(*A, prec, e), 0.0);
         return PPG_OK;
     }
     ppg_status axpy(const SpmvEpi &e, int check)
@@ -447,13 +463,15 @@ struct Iter {
         a.kcols_from_k = from_k;
         a.partials = L->partials;
         x->c->launches++;
-        cudaEvent_t ev = prof_begin(x->c, x->s);
         PPG_CK(launch_gs(x->prec, kcols, x->c->ld, x->c->num_sms, a, x->c->st, x->s));
-        // bytes: k columns read, w read (except when combining), one vector written (passes 2-4)
+        // bytes: k columns read, w read (except when combining), one vector written (passes 2-4);
+        // at the cycle end k is known only after the cycle (kcol_bytes is scaled by it then)
         const double col = (double)x->A->n * (x->prec == kF64 ? 8.0 : 4.0);
         const double fixed = col * ((op != kGsCombine ? 1.0 : 0.0) + (op != kGsDot ? 1.0 : 0.0));
-        prof_end(x->c, x->s, ev, 1, fixed, col);
-        if (from_k == 0 && x->c->prof && !x->c->recs.empty()) x->c->recs.back().bytes += col * kcols;
+        if (from_k)
+            prof_add(x->c, fixed, col);
+        else
+            prof_add(x->c, fixed + col * kcols, 0.0);
         return PPG_OK;
     }
 
@@ -461,12 +479,17 @@ struct Iter {
     // that ended early return at once)
     ppg_status iteration(int j)
     {
-        x->c->prof_j = j;
+        ppg_ctx *c = x->c;
+        c->prof_j = j;
         char *tmp[4] = {L->vec[1], L->vec[2], L->vec[3], L->vec[4]};
-        PPG_TRY(x->poly_then_A(vcol(L->basis, x->c->ld, 0), x->c->st->sigma, vfix(L->vec[0]), tmp, kSkipIfDone));
+        prof_open(c, x->s, 0);
+        PPG_TRY(x->poly_then_A(vcol(L->basis, c->ld, 0), c->st->sigma, vfix(L->vec[0]), tmp, kSkipIfDone));
+        prof_close(c, x->s);
+        prof_open(c, x->s, 1);
         PPG_TRY(gs(kGsDot, 0, nullptr, 0, j + 1));
         PPG_TRY(gs(kGsUpdDot, 0, nullptr, 0, j + 1));
         PPG_TRY(gs(kGsUpdNorm, 0, nullptr, 1, j + 1));
+        prof_close(c, x->s);
         return PPG_OK;
     }
 
@@ -475,11 +498,15 @@ struct Iter {
     {
         x->c->prof_j = -2;
         char *z = L->vec[5], *e = L->vec[6];
+        prof_open(x->c, x->s, 1);
         PPG_TRY(gs(kGsCombine, 1, z, 0, maxcols));
+        prof_close(x->c, x->s);
         const void *corr = z;
         if (x->c->has_poly) {
             char *t3[3] = {L->vec[1], L->vec[2], L->vec[3]};
+            prof_open(x->c, x->s, 0);
             PPG_TRY(x->poly_apply(vfix(z), nullptr, vfix(e), t3, kSkipIfNoCols));
+            prof_close(x->c, x->s);
             corr = e;
         }
         x->c->launches++;
@@ -612,17 +639,17 @@ ppg_status prof_close_cycle(ppg_ctx *c)
 void prof_collect(ppg_ctx *c, ppg_stats *st)
 {
     for (const ppg_ctx::ProfRec &r : c->recs) {
-        if (!r.valid) continue;
+        if (!r.valid || !r.b) continue;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) continue;
         if (r.cls == 0) {
             st->spmv_ms += ms;
             st->spmv_bytes += r.bytes;
-            st->spmv_launches += 1;
+            st->spmv_segments += 1;
         } else {
             st->gs_ms += ms;
             st->gs_bytes += r.bytes;
-            st->gs_launches += 1;
+            st->gs_segments += 1;
         }
     }
 }
@@ -650,6 +677,7 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
     Exec ex{c, &c->A, prec, c->stream};
     Iter it{&ex, &L, ncols};
     c->prof = opts && opts->profile;
+    c->prof_open = false;
     c->recs.clear();
     c->rec_first = 0;
     c->evnext = 0;

@@ -169,6 +169,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 
+// Programmatic dependent launch.  Kernels of the solve path are launched so that they may
+// start while the previous kernel of the stream drains: each lets its own dependents start
+// (pdl_trigger) and waits for its predecessor's completion and memory (pdl_wait) before it
+// reads anything the predecessor may have written.  Both are no-ops for ordinary launches.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // ---------------------------------------------------------------- reductions
 
 __device__ __forceinline__ double warp_sum(double v)

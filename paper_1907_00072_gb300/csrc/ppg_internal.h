@@ -3,9 +3,34 @@
 
 #include "ppg_common.cuh"
 
+#include <utility>
+
 namespace ppg {
 
 enum Prec : int { kF64 = 0, kF32 = 1 };
+
+// Whether solve-path kernels are launched with programmatic stream serialization (on by
+// default; PPG_NO_PDL=1 in the environment turns it off, for comparisons).
+bool pdl_enabled();
+
+// Launches kernel<<<grid, block, smem, s>>>(args...) with programmatic stream serialization
+// allowed when pdl_enabled().
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // The context's device copy of the CSR matrix and the tiling chosen for it.
 struct DevMatrix {
@@ -55,6 +80,8 @@ struct GsArgs {
     long long ntiles;
     double *partials;
     int nblk;
+    int kstage;   // columns one pipeline stage holds (>= the columns used); set by launch_gs
+    int nstages;  // pipeline depth; set by launch_gs
 };
 
 cudaError_t launch_validate(int n, long long nnz, const int *rowptr, const int *colidx, int *flag, cudaStream_t s);

@@ -20,16 +20,22 @@
 
 namespace ppg {
 
-// Tile shape by basis-width bucket KM (k <= KM columns): every pipeline stage carries
-// about 32 KB of basis whatever k is, so the copy pipeline stays deep at small k.
+// Tile height by basis-width bucket KM (k <= KM columns): a tile of all KM columns would be
+// 32 KB.  At run time a stage holds exactly the launch's column bound kst (<= KM) plus w, and
+// as many stages as fit the shared-memory budget are used, so that small k still keeps many
+// bytes in flight.
+constexpr int kGsMaxStages = 8;
+constexpr int kGsSmemBudget = 72 * 1024;  // dynamic shared memory per CTA: three CTAs per SM
+
+constexpr int pow2_floor(int v) { return v < 2 ? 1 : 2 * pow2_floor(v / 2); }
+
 template <typename T, int KM>
 struct GsCfg {
-    static constexpr int TR = 32768 / (KM * (int)sizeof(T));             // rows per tile
+    static constexpr int TR = pow2_floor(32768 / (KM * (int)sizeof(T)));  // rows per tile (divides 1024)
     static constexpr int RPT = TR >= kThreads ? TR / kThreads : 1;       // rows per thread (update phase)
     static constexpr int TPR = TR >= kThreads ? 1 : kThreads / TR;       // threads per row (update phase)
     static constexpr int RPL = TR / 32;                                  // rows per lane (dot phase, stride 32)
     static constexpr int CPW = (KM + 7) / 8;                             // columns per warp (dot phase)
-    static constexpr int STAGE = KM * TR + TR;                           // elements per pipeline stage
 };
 
 // Accumulator of a warp's column sums: float64 directly, or float32 with Kahan
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     using C = GsCfg<T, KM>;
     constexpr int TR = C::TR, TPR = C::TPR, RPT = C::RPT, RPL = C::RPL, CPW = C::CPW;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t bars[kGsMaxStages];
     __shared__ T s_wn[TR];
     __shared__ T s_part[TPR > 1 ? TPR : 1][TPR > 1 ? TR : 1];
     __shared__ T s_coef[KM];
@@ -165,6 +171,8 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     __shared__ double scratch[33];
     __shared__ int s_last;
 
+    pdl_trigger();
+    pdl_wait();
     const int op = a.op;
     if (a.kcols_from_k) {
         if (st->k == 0) return;
@@ -172,7 +180,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
         return;
     }
     const int k = a.kcols_from_k ? st->k : st->j + 1;
-    if (k > KM) {  // the host picked too small a bucket: refuse rather than read past the stage
+    if (k > KM || k > a.kstage) {  // the host's bound is too small: refuse rather than overrun a stage
         if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&st->error, kErrTimeout);
         return;
     }
@@ -181,44 +189,55 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     T *out = a.out_follow ? (T *)a.U + (long long)(st->j + 1) * a.ldu : (T *)a.out;
     const bool need_w = (op != kGsCombine);
     T *stage0 = reinterpret_cast<T *>(smem);
+    const int nst = a.nstages;                      // pipeline depth (2..kGsMaxStages)
+    const long long SS = (long long)(a.kstage + 1) * TR;  // elements per stage: kst columns + w
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int q = 0; q < nst; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
     }
     for (int c = tid; c < KM; c += kThreads) s_coef[c] = (c < k && op != kGsDot) ? (T)st->coef[c] : T(0);
     __syncthreads();
 
     auto issue = [&](long long tile, int stage) {
-        T *sU = stage0 + stage * C::STAGE;
+        T *sU = stage0 + stage * SS;
         const uint32_t colb = TR * (uint32_t)sizeof(T);
         const uint32_t bytes = colb * (uint32_t)k + (need_w ? colb : 0u);
         mbar_arrive_expect_tx(&bars[stage], bytes);
         const long long row0 = tile * TR;
         for (int c = 0; c < k; ++c) bulk_g2s(sU + c * TR, U + (long long)c * a.ldu + row0, colb, &bars[stage]);
-        if (need_w) bulk_g2s(sU + KM * TR, w + row0, colb, &bars[stage]);
+        if (need_w) bulk_g2s(sU + (long long)a.kstage * TR, w + row0, colb, &bars[stage]);
     };
 
+    // prologue: the first nst - 1 tiles; tile it + nst - 1 is issued at the start of iteration it
+    // into the stage freed by iteration it - 1
     if (tid == 0) {
-        long long t0 = blockIdx.x, t1 = blockIdx.x + (long long)gridDim.x;
-        if (t0 < a.ntiles) issue(t0, 0);
-        if (t1 < a.ntiles) issue(t1, 1);
+        for (int q = 0; q < nst - 1; ++q) {
+            const long long t = blockIdx.x + (long long)q * gridDim.x;
+            if (t < a.ntiles) issue(t, q);
+        }
     }
 
     Acc<T> acc[CPW];
-    double nrm = 0.0;
+    Acc<T> nrm;  // float32 path: float32 Kahan sum per thread, float64 across threads
     bool timed_out = false;
     int it = 0;
     for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
-        const int stage = it & 1;
-        if (!mbar_wait_bounded(&bars[stage], (it >> 1) & 1, kWaitLimitNs)) {
+        const int stage = it % nst;
+        if (tid == 0) {
+            const long long nt = tile + (long long)(nst - 1) * gridDim.x;
+            if (nt < a.ntiles) {
+                fence_proxy_async_smem();
+                issue(nt, (it + nst - 1) % nst);
+            }
+        }
+        if (!mbar_wait_bounded(&bars[stage], (it / nst) & 1, kWaitLimitNs)) {
             timed_out = true;
             break;
         }
-        const T *sU = stage0 + stage * C::STAGE;
-        const T *sw = sU + KM * TR;
+        const T *sU = stage0 + stage * SS;
+        const T *sw = sU + (long long)a.kstage * TR;
         const long long row0 = tile * TR;
         const T *dotvec = sw;
         if (op != kGsDot) {
@@ -241,7 +260,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
                         s_wn[row] = wn;
                     } else {
                         out[row0 + row] = wn;
-                        if (op == kGsUpdNorm) nrm += (double)wn * (double)wn;
+                        if (op == kGsUpdNorm) nrm.add(wn * wn);
                     }
                 }
                 __syncthreads();
@@ -261,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
                         s_wn[row] = wn;
                     } else {
                         out[row0 + row] = wn;
-                        if (op == kGsUpdNorm) nrm += (double)wn * (double)wn;
+                        if (op == kGsUpdNorm) nrm.add(wn * wn);
                     }
                 }
                 __syncthreads();
@@ -272,8 +291,8 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
             for (int r = 0; r < RPT; ++r) {
                 const int row = tid + r * kThreads;
                 if (row < TR) {
-                    const double t = (double)sw[row];
-                    nrm += t * t;
+                    const T t = sw[row];
+                    nrm.add(t * t);
                 }
             }
         }
@@ -289,20 +308,12 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
                 }
             }
         }
-        __syncthreads();  // every thread is done with this stage
-        if (tid == 0) {
-            const long long nt = tile + 2LL * gridDim.x;
-            if (nt < a.ntiles) {
-                fence_proxy_async_smem();
-                issue(nt, stage);
-            }
-        }
+        __syncthreads();  // every thread is done with this stage before it is refilled
     }
     if (timed_out) {
         if (tid == 0) atomicOr(&st->error, kErrTimeout);
-        // copies already issued into either stage may still land: wait for them (bounded) first
-        mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimitNs);
-        mbar_wait_bounded(&bars[(it + 1) & 1], ((it + 1) >> 1) & 1, kWaitLimitNs);
+        // copies already issued into the stages may still land: wait for them (bounded) first
+        for (int q = 0; q < nst - 1; ++q) mbar_wait_bounded(&bars[(it + q) % nst], ((it + q) / nst) & 1, kWaitLimitNs);
         return;
     }
 
@@ -318,8 +329,8 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
         }
     }
     if (op != kGsCombine) {
-        nrm = block_sum(nrm, scratch);
-        if (tid == 0) a.partials[(long long)kKmax * a.nblk + blockIdx.x] = nrm;
+        const double nsum = block_sum(nrm.get(), scratch);
+        if (tid == 0) a.partials[(long long)kKmax * a.nblk + blockIdx.x] = nsum;
     }
     if (op == kGsCombine) return;
 
@@ -353,40 +364,39 @@ namespace {
 
 template <typename T, int KM>
 struct GsInst {
-    static constexpr size_t smem() { return 2 * sizeof(T) * (size_t)GsCfg<T, KM>::STAGE; }
-    static int per_sm()
-    {
-        static int cached = 0;
-        if (!cached) {
-            int nb = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gs<T, KM>, kThreads, smem());
-            cached = nb > 0 ? nb : 1;
-        }
-        return cached;
-    }
     static cudaError_t configure()
     {
-        return cudaFuncSetAttribute(k_gs<T, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem());
+        return cudaFuncSetAttribute(k_gs<T, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGsSmemBudget);
     }
-    static cudaError_t launch(GsArgs a, long long ld, int num_sms, Cycle *st, cudaStream_t s)
+    static cudaError_t launch(GsArgs a, int kcols, long long ld, int num_sms, Cycle *st, cudaStream_t s)
     {
-        a.ntiles = ld / GsCfg<T, KM>::TR;
-        long long g = (long long)per_sm() * num_sms;
+        constexpr int TR = GsCfg<T, KM>::TR;
+        const size_t stage_bytes = (size_t)(kcols + 1) * TR * sizeof(T);
+        int nst = (int)(kGsSmemBudget / stage_bytes);
+        if (nst > kGsMaxStages) nst = kGsMaxStages;
+        if (nst < 2) return cudaErrorInvalidValue;
+        a.kstage = kcols;
+        a.nstages = nst;
+        const size_t smem = (size_t)nst * stage_bytes;
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gs<T, KM>, kThreads, smem);
+        if (per < 1) per = 1;
+        a.ntiles = ld / TR;
+        long long g = (long long)per * num_sms;
         if (g > a.ntiles) g = a.ntiles;
         a.nblk = (int)(g > 0 ? g : 1);
-        k_gs<T, KM><<<a.nblk, kThreads, smem(), s>>>(a, st);
-        return cudaGetLastError();
+        return launch_pdl(k_gs<T, KM>, dim3(a.nblk), dim3(kThreads), smem, s, a, st);
     }
 };
 
 template <typename T>
 cudaError_t gs_launch_t(int kcols, GsArgs a, long long ld, int num_sms, Cycle *st, cudaStream_t s)
 {
-    if (kcols <= 8) return GsInst<T, 8>::launch(a, ld, num_sms, st, s);
-    if (kcols <= 16) return GsInst<T, 16>::launch(a, ld, num_sms, st, s);
-    if (kcols <= 32) return GsInst<T, 32>::launch(a, ld, num_sms, st, s);
-    if (kcols <= 64) return GsInst<T, 64>::launch(a, ld, num_sms, st, s);
-    return GsInst<T, 128>::launch(a, ld, num_sms, st, s);
+    if (kcols <= 8) return GsInst<T, 8>::launch(a, kcols, ld, num_sms, st, s);
+    if (kcols <= 16) return GsInst<T, 16>::launch(a, kcols, ld, num_sms, st, s);
+    if (kcols <= 32) return GsInst<T, 32>::launch(a, kcols, ld, num_sms, st, s);
+    if (kcols <= 64) return GsInst<T, 64>::launch(a, kcols, ld, num_sms, st, s);
+    return GsInst<T, 128>::launch(a, kcols, ld, num_sms, st, s);
 }
 
 template <typename T>
@@ -409,7 +419,7 @@ cudaError_t gs_configure()
     return e;
 }
 
-int gs_max_blocks(int num_sms) { return 16 * num_sms; }
+int gs_max_blocks(int num_sms) { return 16 * num_sms; }  // 3 CTAs per SM in practice
 
 cudaError_t launch_gs(int prec, int kcols, long long ld, int num_sms, GsArgs a, Cycle *st, cudaStream_t s)
 {

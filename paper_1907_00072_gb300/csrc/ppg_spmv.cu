@@ -10,7 +10,18 @@
 
 #include "ppg_internal.h"
 
+#include <stdlib.h>
+
 namespace ppg {
+
+bool pdl_enabled()
+{
+    static const bool on = [] {
+        const char *v = getenv("PPG_NO_PDL");
+        return !(v && v[0] == '1');
+    }();
+    return on;
+}
 
 // ---------------------------------------------------------------- validation and conversion
 
@@ -103,9 +114,6 @@ __global__ void __launch_bounds__(kSpmvThreads, 3) k_spmv(SpmvArgs<T> a)
     __shared__ double s_coef[7];
 
     Cycle *st = a.st;
-    if (a.check_done == kSkipIfDone && st->cycle_done) return;
-    if (a.check_done == kSkipIfNoCols && st->k == 0) return;
-
     const int R = a.rows_per_tile;
     const int G = a.lanes_per_row;
     const long long ntiles = ((long long)a.n + R - 1) / R;
@@ -114,6 +122,9 @@ __global__ void __launch_bounds__(kSpmvThreads, 3) k_spmv(SpmvArgs<T> a)
     const size_t col_off = kSpmvRpBytes + round128((size_t)a.cap * sizeof(T));
     constexpr int VA = 16 / (int)sizeof(T);
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    // tiles of this CTA whose matrix data is fetched before the predecessor kernel finishes
+    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int prefetched = (int)min((long long)kSpmvStages, my_tiles);
 
     if (tid == 0) {
         for (int s = 0; s < kSpmvStages; ++s) {
@@ -122,17 +133,8 @@ __global__ void __launch_bounds__(kSpmvThreads, 3) k_spmv(SpmvArgs<T> a)
         }
         fence_mbar_init();
     }
-    switch (tid) {
-    case 0: s_coef[0] = resolve(a.e.a0, st); break;
-    case 1: s_coef[1] = resolve(a.e.b0, st); break;
-    case 2: s_coef[2] = resolve(a.e.c0, st); break;
-    case 3: s_coef[3] = resolve(a.e.a1, st); break;
-    case 4: s_coef[4] = resolve(a.e.b1, st); break;
-    case 5: s_coef[5] = resolve(a.e.c1, st); break;
-    case 6: s_coef[6] = resolve(a.e.s2, st); break;
-    default: break;
-    }
     __syncthreads();
+    pdl_trigger();
 
     if (wid == kSpmvConsumerWarps) {
         // ---------------- producer
@@ -148,6 +150,14 @@ __global__ void __launch_bounds__(kSpmvThreads, 3) k_spmv(SpmvArgs<T> a)
             if (blockIdx.x < ntiles) bounds(blockIdx.x, ne0, ne1);
             int i = 0;
             for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+                if (i == prefetched) {
+                    // the first stages hold matrix data only (constant): from here on the
+                    // predecessor must be complete, and this launch may have nothing to do
+                    pdl_wait();
+                    if ((a.check_done == kSkipIfDone && st->cycle_done) ||
+                        (a.check_done == kSkipIfNoCols && st->k == 0))
+                        break;
+                }
                 const int e0 = ne0, e1 = ne1;
                 if (tile + gridDim.x < ntiles) bounds(tile + gridDim.x, ne0, ne1);
                 const int s = i % kSpmvStages, round = i / kSpmvStages;
@@ -175,7 +185,27 @@ __global__ void __launch_bounds__(kSpmvThreads, 3) k_spmv(SpmvArgs<T> a)
         return;
     }
 
-    // ---------------- consumers
+    // consumers: nothing a predecessor wrote is read before this point
+    pdl_wait();
+    if ((a.check_done == kSkipIfDone && st->cycle_done) || (a.check_done == kSkipIfNoCols && st->k == 0)) {
+        // nothing to do: let the prefetched matrix tiles land before the CTA exits
+        for (int q = 0; q < prefetched; ++q) mbar_wait_bounded(&full[q], 0, kWaitLimitNs);
+        return;
+    }
+    if (tid < 7) {
+        switch (tid) {
+        case 0: s_coef[0] = resolve(a.e.a0, st); break;
+        case 1: s_coef[1] = resolve(a.e.b0, st); break;
+        case 2: s_coef[2] = resolve(a.e.c0, st); break;
+        case 3: s_coef[3] = resolve(a.e.a1, st); break;
+        case 4: s_coef[4] = resolve(a.e.b1, st); break;
+        case 5: s_coef[5] = resolve(a.e.c1, st); break;
+        default: s_coef[6] = resolve(a.e.s2, st); break;
+        }
+    }
+    // consumer-only barrier (named barrier 1, the eight consumer warps)
+    asm volatile("bar.sync 1, %0;" ::"n"(kSpmvConsumerWarps * 32) : "memory");
+
     const T *__restrict__ x = resolve_ptr<T>(a.e.x, st);
     const T *__restrict__ x2 = resolve_ptr<T>(a.e.x2, st);
     T *o0 = resolve_ptr<T>(a.e.out0, st);
@@ -286,14 +316,15 @@ cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *s
         SpmvArgs<double> a{A.n, A.rowptr, A.colidx, A.vals64, R, A.lanes_per_row, A.cap64, st, check_done, e};
         long long g = (long long)A.spmv_blocks64;
         if (g > ntiles) g = ntiles;
-        k_spmv<double><<<(int)g, kSpmvThreads, kSpmvStages * spmv_stage_bytes<double>(A.cap64), s>>>(a);
+        return launch_pdl(k_spmv<double>, dim3((unsigned)g), dim3(kSpmvThreads),
+                          kSpmvStages * spmv_stage_bytes<double>(A.cap64), s, a);
     } else {
         SpmvArgs<float> a{A.n, A.rowptr, A.colidx, A.vals32, R, A.lanes_per_row, A.cap32, st, check_done, e};
         long long g = (long long)A.spmv_blocks32;
         if (g > ntiles) g = ntiles;
-        k_spmv<float><<<(int)g, kSpmvThreads, kSpmvStages * spmv_stage_bytes<float>(A.cap32), s>>>(a);
+        return launch_pdl(k_spmv<float>, dim3((unsigned)g), dim3(kSpmvThreads),
+                          kSpmvStages * spmv_stage_bytes<float>(A.cap32), s, a);
     }
-    return cudaGetLastError();
 }
 
 // Sets the dynamic shared memory limit (for the largest staging capacity, once) and returns
@@ -322,6 +353,8 @@ int spmv_cap_max() { return kSpmvCapMax; }
 template <typename T>
 __global__ void k_axpy(int n, SpmvEpi e, Cycle *st, int check)
 {
+    pdl_trigger();
+    pdl_wait();
     if (check == kSkipIfDone && st->cycle_done) return;
     if (check == kSkipIfNoCols && st->k == 0) return;
     T *o0 = resolve_ptr<T>(e.out0, st);
@@ -341,11 +374,8 @@ cudaError_t launch_axpy(int n, int prec, const SpmvEpi &e, Cycle *st, int check,
 {
     int grid = (n + kThreads - 1) / kThreads;
     if (grid > 8192) grid = 8192;
-    if (prec == kF64)
-        k_axpy<double><<<grid, kThreads, 0, s>>>(n, e, st, check);
-    else
-        k_axpy<float><<<grid, kThreads, 0, s>>>(n, e, st, check);
-    return cudaGetLastError();
+    if (prec == kF64) return launch_pdl(k_axpy<double>, dim3(grid), dim3(kThreads), 0, s, n, e, st, check);
+    return launch_pdl(k_axpy<float>, dim3(grid), dim3(kThreads), 0, s, n, e, st, check);
 }
 
 // ---------------------------------------------------------------- true residual and cycle start
@@ -390,6 +420,8 @@ __global__ void __launch_bounds__(kThreads) k_residual(int n, const int *__restr
 {
     __shared__ double scratch[33];
     __shared__ int s_last;
+    pdl_trigger();
+    pdl_wait();
     if (st->stop) return;
     double nrm = 0.0;
     const int stride = gridDim.x * blockDim.x;
@@ -420,12 +452,10 @@ cudaError_t launch_residual(const DevMatrix &A, int out_prec, const double *b, c
 {
     const int grid = A.resid_blocks;
     if (out_prec == kF64)
-        k_residual<double><<<grid, kThreads, 0, s>>>(A.n, A.rowptr, A.colidx, A.vals64, b, x, (double *)out, st,
-                                                     partials);
-    else
-        k_residual<float><<<grid, kThreads, 0, s>>>(A.n, A.rowptr, A.colidx, A.vals64, b, x, (float *)out, st,
-                                                    partials);
-    return cudaGetLastError();
+        return launch_pdl(k_residual<double>, dim3(grid), dim3(kThreads), 0, s, A.n, A.rowptr, A.colidx, A.vals64, b,
+                          x, (double *)out, st, partials);
+    return launch_pdl(k_residual<float>, dim3(grid), dim3(kThreads), 0, s, A.n, A.rowptr, A.colidx, A.vals64, b, x,
+                      (float *)out, st, partials);
 }
 
 // ||v||.  mode 0: st->bnorm = ||v|| (right-hand side).  mode 1: start an Arnoldi run from v:
@@ -436,6 +466,8 @@ __global__ void __launch_bounds__(kThreads) k_norm_start(int n, const double *__
 {
     __shared__ double scratch[33];
     __shared__ int s_last;
+    pdl_trigger();
+    pdl_wait();
     double acc = 0.0;
     const int stride = gridDim.x * blockDim.x;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
@@ -474,16 +506,17 @@ cudaError_t launch_norm_start(int n, int out_prec, const double *v, void *out, i
                               int nblk, cudaStream_t s)
 {
     if (out_prec == kF64)
-        k_norm_start<double><<<nblk, kThreads, 0, s>>>(n, v, (double *)out, mode, st, partials);
-    else
-        k_norm_start<float><<<nblk, kThreads, 0, s>>>(n, v, (float *)out, mode, st, partials);
-    return cudaGetLastError();
+        return launch_pdl(k_norm_start<double>, dim3(nblk), dim3(kThreads), 0, s, n, v, (double *)out, mode, st,
+                          partials);
+    return launch_pdl(k_norm_start<float>, dim3(nblk), dim3(kThreads), 0, s, n, v, (float *)out, mode, st, partials);
 }
 
 // x += e (e in the inner precision), skipped when the cycle produced no columns.
 template <typename Te>
 __global__ void k_xupdate(int n, const Te *__restrict__ e, double *__restrict__ x, Cycle *st)
 {
+    pdl_trigger();
+    pdl_wait();
     if (st->k == 0) return;
     const int stride = gridDim.x * blockDim.x;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) x[r] += (double)e[r];
@@ -493,16 +526,15 @@ cudaError_t launch_xupdate(int n, int prec, const void *e, double *x, Cycle *st,
 {
     int grid = (n + kThreads - 1) / kThreads;
     if (grid > 8192) grid = 8192;
-    if (prec == kF64)
-        k_xupdate<double><<<grid, kThreads, 0, s>>>(n, (const double *)e, x, st);
-    else
-        k_xupdate<float><<<grid, kThreads, 0, s>>>(n, (const float *)e, x, st);
-    return cudaGetLastError();
+    if (prec == kF64) return launch_pdl(k_xupdate<double>, dim3(grid), dim3(kThreads), 0, s, n, (const double *)e, x, st);
+    return launch_pdl(k_xupdate<float>, dim3(grid), dim3(kThreads), 0, s, n, (const float *)e, x, st);
 }
 
 template <typename T>
 __global__ void k_copy_in(int n, const T *__restrict__ src, T *__restrict__ dst)
 {
+    pdl_trigger();
+    pdl_wait();
     const int stride = gridDim.x * blockDim.x;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) dst[r] = src[r];
 }
@@ -512,10 +544,8 @@ cudaError_t launch_copy_in(int n, int prec, const void *src, void *dst, cudaStre
     int grid = (n + kThreads - 1) / kThreads;
     if (grid > 8192) grid = 8192;
     if (prec == kF64)
-        k_copy_in<double><<<grid, kThreads, 0, s>>>(n, (const double *)src, (double *)dst);
-    else
-        k_copy_in<float><<<grid, kThreads, 0, s>>>(n, (const float *)src, (float *)dst);
-    return cudaGetLastError();
+        return launch_pdl(k_copy_in<double>, dim3(grid), dim3(kThreads), 0, s, n, (const double *)src, (double *)dst);
+    return launch_pdl(k_copy_in<float>, dim3(grid), dim3(kThreads), 0, s, n, (const float *)src, (float *)dst);
 }
 
 // ---------------------------------------------------------------- SplitMix64 (Steele, Lea, Flood 2014)
