@@ -175,11 +175,18 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=60)
     ap.add_argument("--profile-harness", action="store_true",
                     help="for ncu: build the polynomial and run 20 iterations of one solve, print no benchmark line")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"],
+                    help="c2 (default): the benchmark line; c1/c3/c4/c5: the other configurations, one JSON line each")
     args = ap.parse_args()
 
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload != "c2":
+        import other_workloads  # noqa: F401  (kept beside bench.py)
+
+        other_workloads.run(args)
         return
 
     import torch

@@ -88,7 +88,7 @@ typedef struct {
     int degree_used;     /* degree of the polynomial applied */
     int converged;       /* 1 if relres_true <= tol */
     int breakdowns;      /* cycles ended by a (lucky) Arnoldi breakdown */
-    int reserved;
+    int ctas_per_system; /* ppg_solve_batched: CTAs (cluster size) per system; 0 otherwise */
     double time_ms;      /* wall time of the call on the device stream (CUDA events) */
     /* filled when ppg_opts.profile = 1, for launches that did work: device time and algorithmic
        bytes of the SpMV chain (p(A) steps and the SpMV that applies A) and of the Gram-Schmidt
@@ -224,6 +224,33 @@ ppg_status ppg_hessenberg_eigs(ppg_ctx *ctx, int k, const double *H, int ld, dou
  * stream's position i: z = mix(mix(seed) + (i+1) * 0x9E3779B97F4A7C15), u = (z >> 11) * 2^-53).
  * This is the generator ppg_build_poly uses when v0 is NULL. */
 ppg_status ppg_fill_uniform(ppg_ctx *ctx, double *out, int64_t n, uint64_t seed);
+
+/* ------------------------------------------------------------------ batched */
+
+/* One system of a batch: a CSR matrix (int32 rowptr[n+1], colidx[nnz], float64 vals[nnz]) and its
+ * vectors, all device pointers owned by the caller. */
+typedef struct {
+    int64_t n, nnz;
+    const int32_t *rowptr, *colidx;
+    const double *vals;
+    const double *b;
+    double *x; /* initial guess in, solution out */
+} ppg_batch_system;
+
+/* Solves nsys independent systems in one persistent launch (replayed from a CUDA graph).  Each
+ * system is owned by one thread-block cluster, which builds the system's minimum-residual polynomial
+ * (roots form, the given degree, v0 uniform in [-1, 1] from the SplitMix64 stream seed + i, float64
+ * construction) and runs float32 PP-GMRES(restart) cycles, each ending with a float64 residual and
+ * update of x (iterative refinement; a cycle stops early once its residual estimate drops by 1e-6),
+ * until ||b - A x|| <= tol ||b|| or maxit iterations.  Systems start largest first.  The number of
+ * CTAs per system is chosen by timing the construction phase of the batch for 4, 8 and 16 CTAs on the
+ * first call with a new batch (cached afterwards).  per_sys (host, nsys entries, may be NULL) receives
+ * each system's statistics (time_ms: the whole batch).  restart <= 40,
+ * degree <= 31.  stream as in ppg_create.  Synchronises.  The library keeps one workspace per device
+ * for batched calls (not thread-safe across host threads on one device).
+ * Returns PPG_OK, PPG_ERR_NOT_CONVERGED if any system missed the tolerance, or an error. */
+ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree, double tol, int restart, int maxit,
+                             uint64_t seed, void *stream, ppg_stats *per_sys);
 
 /* ------------------------------------------------------------------ diagnostics */
 

@@ -42,8 +42,8 @@ EXPORTED = (
     "ppg_create", "ppg_destroy", "ppg_set_stream", "ppg_workspace_bytes", "ppg_set_workspace", "ppg_spmv",
     "ppg_build_poly", "ppg_set_poly", "ppg_get_poly", "ppg_apply_poly", "ppg_apply_poly_noalloc", "ppg_solve",
     "ppg_solve_transpose",
-    "ppg_csr_outer", "ppg_arnoldi", "ppg_hessenberg_eigs", "ppg_fill_uniform", "ppg_status_string",
-    "ppg_last_error", "ppg_version",
+    "ppg_csr_outer", "ppg_arnoldi", "ppg_hessenberg_eigs", "ppg_fill_uniform", "ppg_solve_batched",
+    "ppg_status_string", "ppg_last_error", "ppg_version",
 )
 
 
@@ -56,12 +56,18 @@ class ppg_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("restarts", ctypes.c_int64), ("spmvs", ctypes.c_int64),
                 ("dots", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("relres_true", ctypes.c_double),
                 ("relres_est", ctypes.c_double), ("degree_used", ctypes.c_int), ("converged", ctypes.c_int),
-                ("breakdowns", ctypes.c_int), ("reserved", ctypes.c_int), ("time_ms", ctypes.c_double),
+                ("breakdowns", ctypes.c_int), ("ctas_per_system", ctypes.c_int), ("time_ms", ctypes.c_double),
                 ("spmv_ms", ctypes.c_double), ("spmv_bytes", ctypes.c_double), ("spmv_segments", ctypes.c_int64),
                 ("gs_ms", ctypes.c_double), ("gs_bytes", ctypes.c_double), ("gs_segments", ctypes.c_int64)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ppg_batch_system(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("colidx", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("x", ctypes.c_void_p)]
 
 
 class PPGError(RuntimeError):
@@ -100,6 +106,8 @@ def load_library(path: str = LIB_PATH):
         "ppg_arnoldi": (I, [P, P, I, P, P, ctypes.POINTER(I)]),
         "ppg_hessenberg_eigs": (I, [P, I, P, I, P, P]),
         "ppg_fill_uniform": (I, [P, P, I64, U64]),
+        "ppg_solve_batched": (I, [I, ctypes.POINTER(ppg_batch_system), I, D, I, I, U64, P,
+                                  ctypes.POINTER(ppg_stats)]),
         "ppg_status_string": (ctypes.c_char_p, [I]),
         "ppg_last_error": (ctypes.c_char_p, []),
         "ppg_version": (ctypes.c_char_p, []),
@@ -269,6 +277,25 @@ def ppg_hessenberg_eigs(ctx, H, wr, wi):
 
 def ppg_fill_uniform(ctx, out, seed):
     return _check(load_library().ppg_fill_uniform(ctx, _ptr(out), out.numel(), int(seed)), "ppg_fill_uniform")
+
+
+def ppg_solve_batched(systems, degree=15, tol=1e-8, restart=30, maxit=10000, seed=2, stream=None):
+    """systems: list of (rowptr, colidx, vals, b, x) CUDA tensors (x: initial guess, overwritten).
+    Returns (status, list of per-system stats dicts)."""
+    n = len(systems)
+    arr = (ppg_batch_system * n)()
+    for i, (rp, ci, va, b, x) in enumerate(systems):
+        arr[i].n = rp.numel() - 1
+        arr[i].nnz = va.numel()
+        arr[i].rowptr = rp.data_ptr()
+        arr[i].colidx = ci.data_ptr()
+        arr[i].vals = va.data_ptr()
+        arr[i].b = b.data_ptr()
+        arr[i].x = x.data_ptr()
+    stats = (ppg_stats * n)()
+    st = _check(load_library().ppg_solve_batched(n, arr, int(degree), float(tol), int(restart), int(maxit),
+                                                 int(seed), _stream_ptr(stream), stats), "ppg_solve_batched")
+    return st, [stats[i].as_dict() for i in range(n)]
 
 
 def ppg_status_string(status):

@@ -747,6 +747,64 @@ ppg_status set_device(const ppg_ctx *c)
 
 }  // namespace
 
+// =================================================================== batched solves
+
+namespace {
+
+// Per-device state of ppg_solve_batched: workspace, descriptors, the tuned cluster size and the
+// captured launch, kept between calls.
+struct BatchCache {
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    BatchSys *sys_d = nullptr;
+    int *order_d = nullptr;
+    BatchOut *out_d = nullptr;
+    int cap_sys = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+    // autotuner
+    long long tune_key = -1;
+    int cluster = 0;
+    // captured launch
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> exec_key;
+    bool configured = false;
+};
+
+BatchCache g_batch[64];
+std::mutex g_batch_mu;
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+ppg_status batch_setup(BatchCache &bc, int nsys)
+{
+    if (!bc.configured) {
+        PPG_CK(batch_configure());
+        PPG_CK(cudaStreamCreateWithFlags(&bc.stream, cudaStreamNonBlocking));
+        PPG_CK(cudaEventCreateWithFlags(&bc.ev_in, cudaEventDisableTiming));
+        PPG_CK(cudaEventCreateWithFlags(&bc.ev_out, cudaEventDisableTiming));
+        PPG_CK(cudaEventCreate(&bc.t0));
+        PPG_CK(cudaEventCreate(&bc.t1));
+        bc.configured = true;
+    }
+    if (nsys > bc.cap_sys) {
+        cudaFree(bc.sys_d);
+        cudaFree(bc.order_d);
+        cudaFree(bc.out_d);
+        bc.sys_d = nullptr;
+        bc.order_d = nullptr;
+        bc.out_d = nullptr;
+        bc.cap_sys = 0;
+        PPG_CK(cudaMalloc(&bc.sys_d, sizeof(BatchSys) * nsys));
+        PPG_CK(cudaMalloc(&bc.order_d, sizeof(int) * nsys));
+        PPG_CK(cudaMalloc(&bc.out_d, sizeof(BatchOut) * nsys));
+        bc.cap_sys = nsys;
+    }
+    return PPG_OK;
+}
+
+}  // namespace
+
 // =================================================================== allocation-free apply
 
 // Device scratch for ppg_apply_poly_noalloc: the input copy, the output and three working
@@ -1112,6 +1170,174 @@ ppg_status ppg_apply_poly_noalloc(ppg_ctx *c, const void *v, void *out, int prec
     PPG_TRY(ex.poly_apply(vfix(vec[0]), nullptr, vfix(vec[1]), tmp, kNoCheck));
     PPG_CK(launch_copy_in(c->A.n, precision, vec[1], out, c->stream));
     return PPG_OK;
+}
+
+ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree, double tol, int restart,
+                             int maxit, uint64_t seed, void *stream, ppg_stats *per_sys)
+{
+    g_last_error.clear();
+    if (nsys < 1 || !sys_h) return fail(PPG_ERR_INVALID_ARG, "need at least one system");
+    if (restart < 1 || restart > kBatchMaxRestart)
+        return fail(PPG_ERR_INVALID_ARG, "batched restart must be in [1, %d]", kBatchMaxRestart);
+    if (degree < 0 || degree > kBatchMaxDegree)
+        return fail(PPG_ERR_INVALID_ARG, "batched degree must be in [0, %d]", kBatchMaxDegree);
+    if (maxit < 0 || !(tol >= 0.0)) return fail(PPG_ERR_INVALID_ARG, "bad tol or maxit");
+    for (int i = 0; i < nsys; ++i) {
+        const ppg_batch_system &q = sys_h[i];
+        if (q.n < 1 || q.n >= (1LL << 31) - 256 || q.nnz < 0 || !q.rowptr || !q.b || !q.x ||
+            (q.nnz > 0 && (!q.colidx || !q.vals)))
+            return fail(PPG_ERR_INVALID_ARG, "system %d: bad sizes or null pointers", i);
+    }
+    int dev = 0;
+    PPG_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(PPG_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    BatchCache &bc = g_batch[dev];
+    PPG_TRY(batch_setup(bc, nsys));
+    cudaStream_t us = (cudaStream_t)stream;
+
+    // workspace: float32 values, float32 basis and work vectors, float64 construction basis
+    std::vector<size_t> off(nsys);
+    size_t total = 0;
+    long long total_nnz = 0, total_n = 0;
+    for (int i = 0; i < nsys; ++i) {
+        const long long n = sys_h[i].n, nnz = sys_h[i].nnz;
+        off[i] = total;
+        total += align256(sizeof(float) * (nnz + 8)) + align256(sizeof(float) * n * (restart + 1)) +
+                 align256(sizeof(float) * n * 6) + align256(sizeof(double) * n * (degree + 2)) +
+                 align256(sizeof(double) * n);
+        total_nnz += nnz;
+        total_n += n;
+    }
+    if (total > bc.ws_bytes) {
+        cudaFree(bc.ws);
+        bc.ws = nullptr;
+        bc.ws_bytes = 0;
+        PPG_CK(cudaMalloc(&bc.ws, total));
+        bc.ws_bytes = total;
+    }
+    std::vector<BatchSys> hs(nsys);
+    for (int i = 0; i < nsys; ++i) {
+        const ppg_batch_system &q = sys_h[i];
+        BatchSys &d = hs[i];
+        char *p = bc.ws + off[i];
+        d.n = (int)q.n;
+        d.nnz = (int)q.nnz;
+        d.rowptr = q.rowptr;
+        d.colidx = q.colidx;
+        d.vals64 = q.vals;
+        d.b = q.b;
+        d.x = q.x;
+        d.vals32 = reinterpret_cast<float *>(p);
+        p += align256(sizeof(float) * (q.nnz + 8));
+        d.V = reinterpret_cast<float *>(p);
+        p += align256(sizeof(float) * q.n * (restart + 1));
+        d.fw = reinterpret_cast<float *>(p);
+        p += align256(sizeof(float) * q.n * 6);
+        d.V64 = reinterpret_cast<double *>(p);
+        p += align256(sizeof(double) * q.n * (degree + 2));
+        d.dw = reinterpret_cast<double *>(p);
+    }
+    // largest systems first: the hardware then fills idle SMs with the smaller ones
+    std::vector<int> order(nsys);
+    for (int i = 0; i < nsys; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sys_h[a].nnz > sys_h[b].nnz; });
+
+    PPG_CK(cudaEventRecord(bc.ev_in, us));
+    PPG_CK(cudaStreamWaitEvent(bc.stream, bc.ev_in, 0));
+    PPG_CK(cudaMemcpyAsync(bc.sys_d, hs.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice, bc.stream));
+    PPG_CK(cudaMemcpyAsync(bc.order_d, order.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, bc.stream));
+    PPG_CK(launch_batch_cast(bc.sys_d, nsys, bc.stream));
+
+    BatchParams prm{degree, restart, (long long)maxit, tol, 1e-6, (unsigned long long)seed};
+
+    // autotuner: CTAs per system (the row tile of each CTA) is chosen by timing the polynomial
+    // construction of this very batch (maxit = 0 leaves x untouched) for each launchable size
+    const long long tune_key = total_nnz * 131 + nsys * 7 + degree;
+    if (bc.tune_key != tune_key || bc.cluster == 0) {
+        int best = 0;
+        float best_ms = 0.f;
+        const int cands[3] = {4, 8, 16};
+        for (int ci = 0; ci < 3; ++ci) {
+            const int cl = cands[ci];
+            if (batch_max_clusters(cl) < 1) continue;
+            BatchParams tp = prm;
+            tp.maxit = 0;
+            for (int rep = 0; rep < 2; ++rep) {  // the first run also warms caches
+                PPG_CK(cudaEventRecord(bc.t0, bc.stream));
+                PPG_CK(launch_batch(bc.sys_d, bc.order_d, nsys, cl, tp, bc.out_d, bc.stream));
+                PPG_CK(cudaEventRecord(bc.t1, bc.stream));
+            }
+            PPG_CK(cudaEventSynchronize(bc.t1));
+            float ms = 0.f;
+            PPG_CK(cudaEventElapsedTime(&ms, bc.t0, bc.t1));
+            if (!best || ms < best_ms) {
+                best = cl;
+                best_ms = ms;
+            }
+        }
+        if (!best) return fail(PPG_ERR_CUDA, "no cluster size is launchable for the batched solver");
+        bc.cluster = best;
+        bc.tune_key = tune_key;
+    }
+
+    // the solve itself: one launch, captured once as a graph and replayed
+    std::vector<long long> key = {(long long)(uintptr_t)bc.sys_d, nsys, bc.cluster, degree, restart, maxit,
+                                  (long long)seed};
+    double tolbits;
+    memcpy(&tolbits, &tol, sizeof tol);
+    key.push_back((long long)tolbits);
+    if (!bc.exec || key != bc.exec_key) {
+        if (bc.exec) cudaGraphExecDestroy(bc.exec);
+        bc.exec = nullptr;
+        cudaGraph_t graph = nullptr;
+        PPG_CK(cudaStreamBeginCapture(bc.stream, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t le = launch_batch(bc.sys_d, bc.order_d, nsys, bc.cluster, prm, bc.out_d, bc.stream);
+        const cudaError_t ce = cudaStreamEndCapture(bc.stream, &graph);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(PPG_ERR_CUDA, "capturing the batched launch: %s / %s", cudaGetErrorString(le),
+                        cudaGetErrorString(ce));
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&bc.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return fail(PPG_ERR_CUDA, "instantiating the batched graph: %s", cudaGetErrorString(ie));
+        bc.exec_key = key;
+    }
+    PPG_CK(cudaEventRecord(bc.t0, bc.stream));
+    PPG_CK(cudaGraphLaunch(bc.exec, bc.stream));
+    PPG_CK(cudaEventRecord(bc.t1, bc.stream));
+    PPG_CK(cudaEventRecord(bc.ev_out, bc.stream));
+    PPG_CK(cudaStreamWaitEvent(us, bc.ev_out, 0));
+    std::vector<BatchOut> ho(nsys);
+    PPG_CK(cudaMemcpyAsync(ho.data(), bc.out_d, sizeof(BatchOut) * nsys, cudaMemcpyDeviceToHost, bc.stream));
+    PPG_CK(cudaStreamSynchronize(bc.stream));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, bc.t0, bc.t1);
+    ppg_status worst = PPG_OK;
+    for (int i = 0; i < nsys; ++i) {
+        const BatchOut &o = ho[i];
+        if (per_sys) {
+            ppg_stats &st = per_sys[i];
+            memset(&st, 0, sizeof st);
+            st.iterations = o.iters;
+            st.restarts = o.cycles;
+            st.spmvs = o.spmvs;
+            st.dots = 3 * o.iters + o.cycles + 1;
+            st.kernel_launches = (i == 0) ? 1 : 0;
+            st.relres_true = o.relres;
+            st.relres_est = o.est;
+            st.degree_used = o.degree;
+            st.converged = o.converged;
+            st.breakdowns = o.breakdowns;
+            st.ctas_per_system = bc.cluster;
+            st.time_ms = ms;
+        }
+        if (o.status == 2 && worst >= 0) worst = fail(PPG_ERR_NONFINITE, "system %d: non-finite value", i);
+        if (o.status == 3 && worst >= 0) worst = fail(PPG_ERR_POLY_BREAKDOWN, "system %d: no usable polynomial", i);
+        if (o.status == 0 && !o.converged && worst == PPG_OK) worst = PPG_ERR_NOT_CONVERGED;
+    }
+    return worst;
 }
 
 ppg_status ppg_solve(ppg_ctx *c, const double *b, double *x, double tol, int restart, int maxit,

@@ -121,6 +121,38 @@ cudaError_t launch_roots(const Cycle *st, int k, double *roots_out /* 2k */, dou
 cudaError_t launch_root_table(int k, const double *roots, double *table_out, int *status_out, cudaStream_t s);
 cudaError_t launch_hess_eigs(int k, const double *H, int ld, double *wr, double *wi, int *status_out,
                              cudaStream_t s);
+// ---- batched solver (one thread-block cluster per system)
+struct BatchSys {
+    int n, nnz;
+    const int *rowptr, *colidx;
+    const double *vals64;
+    const float *vals32;  // library-made float32 copy of vals64
+    const double *b;
+    double *x;
+    float *V;     // (restart + 1) columns of n entries
+    float *fw;    // 6 vectors of n entries
+    double *V64;  // (degree + 2) columns of n entries
+    double *dw;   // 1 vector of n entries
+};
+struct BatchParams {
+    int degree, m;
+    long long maxit;
+    double tol, inner_rtol;
+    unsigned long long seed;
+};
+struct BatchOut {
+    long long iters, cycles, spmvs;
+    double relres, est;
+    int status, degree, converged, breakdowns;
+};
+constexpr int kBatchMaxRestart = 40;
+constexpr int kBatchMaxDegree = 31;
+cudaError_t launch_batch_cast(const BatchSys *sys_d, int nsys, cudaStream_t s);
+cudaError_t launch_batch(const BatchSys *sys_d, const int *order_d, int nsys, int cluster, const BatchParams &p,
+                         BatchOut *out_d, cudaStream_t s);
+int batch_max_clusters(int cluster);
+cudaError_t batch_configure();
+
 // one-time kernel attribute setup (dynamic shared memory limits)
 cudaError_t spmv_configure(DevMatrix *A);
 int spmv_cap_max();

@@ -1,0 +1,95 @@
+"""The batched persistent solver: every system matches an independent single-system solve.
+
+Each system of the batch builds its polynomial from the SplitMix64 stream seed + i; the single
+solve is given the same stream, so both build the same minimum-residual polynomial and run the
+same float32 PP-GMRES with float64 refinement.  Solutions must agree to 1e-6 relative, both must
+reach a true relative residual of 1e-8 (checked on the host with the oracle's SpMV), and their
+iteration counts must agree within 5%.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="no CUDA device")]
+
+import paper_1907_00072_gb300 as ppg  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def _T(a, dt):
+    return torch.as_tensor(np.asarray(a), dtype=dt, device=DEV)
+
+
+def _relres(a, b, x):
+    return np.linalg.norm(b - oracle.spmv(a, x)) / np.linalg.norm(b)
+
+
+def _batch(specs):
+    mats, systems = [], []
+    for i, (side, pe) in enumerate(specs):
+        a, b = w.batch_system(i, side, pe)
+        mats.append((a, b))
+        systems.append((_T(a.rowptr, torch.int32), _T(a.colidx, torch.int32), _T(a.vals, torch.float64),
+                        _T(b, torch.float64), torch.zeros(a.n, dtype=torch.float64, device=DEV)))
+    return mats, systems
+
+
+@pytest.mark.parametrize("degree,restart", [(15, 30), (5, 20), (0, 30)])
+def test_batched_matches_single_solves(degree, restart):
+    specs = [(32, 6.4), (48, 57.9), (40, 97.6), (100, 5.1), (71, 33.3), (64, 80.0)]
+    mats, systems = _batch(specs)
+    seed = 11
+    status, stats = ppg.ppg_solve_batched(systems, degree=degree, tol=1e-8, restart=restart, maxit=20000, seed=seed)
+    assert status == ppg.PPG_OK
+    for i, ((a, b), sysi, st) in enumerate(zip(mats, systems, stats)):
+        xb = sysi[4].cpu().numpy()
+        assert st["converged"] == 1 and st["degree_used"] == degree
+        assert _relres(a, b, xb) <= 1e-8
+        s = ppg.Solver(sysi[0], sysi[1], sysi[2])
+        s.build_poly(degree, ppg.PPG_BASIS_ROOTS, v0=None, seed=seed + i)
+        xs, info = s.solve(sysi[3], tol=1e-8, restart=restart, maxit=20000, precision=ppg.PPG_F32)
+        xs = xs.cpu().numpy()
+        assert info.status == ppg.PPG_OK and _relres(a, b, xs) <= 1e-8
+        assert np.linalg.norm(xb - xs) <= 1e-6 * np.linalg.norm(xs)
+        assert abs(st["iterations"] - info.stats["iterations"]) <= max(2, 0.05 * info.stats["iterations"])
+        s.close()
+
+
+def test_batched_matches_oracle_on_a_small_system():
+    specs = [(24, 40.0)]
+    mats, systems = _batch(specs)
+    status, stats = ppg.ppg_solve_batched(systems, degree=10, tol=1e-10, restart=30, maxit=5000, seed=3)
+    (a, b), = mats
+    v0 = w.uniform(3, a.n)  # the SplitMix64 stream the batch uses for system 0
+    ref = oracle.gmres(a, b, oracle.poly_gmres(a, v0, 10), tol=1e-10, m=30, maxit=5000)
+    xb = systems[0][4].cpu().numpy()
+    assert status == ppg.PPG_OK and ref.converged
+    assert np.linalg.norm(xb - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+
+
+def test_batched_zero_rhs_and_initial_guess():
+    specs = [(32, 10.0), (36, 20.0)]
+    mats, systems = _batch(specs)
+    systems[0][3].zero_()  # b = 0: x must come back 0
+    systems[0][4].fill_(1.0)
+    a1, b1 = mats[1]
+    systems[1][4].copy_(_T(np.linalg.solve(a1.to_dense(), b1), torch.float64))  # exact start
+    status, stats = ppg.ppg_solve_batched(systems, degree=8, tol=1e-8, restart=30, seed=4)
+    assert status == ppg.PPG_OK
+    assert stats[1]["iterations"] == 0
+    assert stats[0]["converged"] == 1
+
+
+def test_batched_rejects_bad_arguments():
+    specs = [(32, 10.0)]
+    _, systems = _batch(specs)
+    with pytest.raises(ppg.PPGError):
+        ppg.ppg_solve_batched(systems, degree=40)
+    with pytest.raises(ppg.PPGError):
+        ppg.ppg_solve_batched(systems, restart=41)
