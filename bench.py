@@ -279,7 +279,9 @@ def main():
         eb.record(stream)
     torch.cuda.synchronize()
     spmv_ms = statistics.mean(ea.elapsed_time(eb) for ea, eb in pairs)
-    spmv_bytes = a.nnz * (sv + 4) + 4 * (a.n + 1) + 2 * a.n * sv
+    rows = np.repeat(np.arange(a.n), np.diff(a.rowptr))
+    idx_bytes = 2 if np.abs(a.colidx.astype(np.int64) - rows).max() <= 32767 else 4  # stored index format
+    spmv_bytes = a.nnz * (sv + idx_bytes) + 4 * (a.n + 1) + 2 * a.n * sv
 
     # ---- variants: degree x precision, one measured solve each
     variants = {}

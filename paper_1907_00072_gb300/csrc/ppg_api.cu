@@ -69,6 +69,7 @@ struct ppg_ctx {
     DevMatrix A{};
     int *d_rowptr = nullptr;
     int *d_colidx = nullptr;
+    short *d_coloff = nullptr;
     double *d_vals = nullptr;
     float *d_vals32 = nullptr;
     long long ld = 0;  // padded vector length
@@ -249,12 +250,14 @@ bool same_vec(const VecRef &u, const VecRef &v)
     return u.base == v.base && u.ld == v.ld && u.col == v.col && u.follow == v.follow;
 }
 
-// Algorithmic bytes of one SpMV launch: values and column indices once, row pointers once,
-// each distinct vector read once and each output written once.
+// Algorithmic bytes of one SpMV launch: values and column indices (in the stored format: int16
+// offsets or int32 indices) once, row pointers once, each distinct vector read once and each
+// output written once.
 double spmv_bytes(const DevMatrix &A, int prec, const SpmvEpi &e)
 {
     const double es = prec == kF64 ? 8.0 : 4.0;
-    double b = (double)A.nnz * (es + 4.0) + 4.0 * (A.n + 1.0);
+    const double is = A.coloff ? 2.0 : 4.0;
+    double b = (double)A.nnz * (es + is) + 4.0 * (A.n + 1.0);
     const VecRef *reads[6] = {&e.x, &e.x2, &e.u0, &e.w0, &e.u1, &e.w1};
     int distinct = 0;
     for (int i = 0; i < 6; ++i) {
@@ -925,6 +928,20 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
     PPG_CK(cudaStreamSynchronize(c->stream));
     if (c->h_info[0] != 0) return fail(PPG_ERR_INVALID_ARG, "invalid CSR (validation flags 0x%x)", c->h_info[0]);
 
+    // int16 column offsets halve the index traffic of the SpMV where every entry lies within 32767
+    // of its row (all banded / stencil matrices of moderate bandwidth)
+    PPG_CK(cudaMalloc(&c->d_coloff, sizeof(short) * (nnz + 16)));
+    PPG_CK(cudaMemsetAsync(c->d_coloff, 0, sizeof(short) * (nnz + 16), c->stream));
+    PPG_CK(cudaMemsetAsync(c->d_info, 0, sizeof(int), c->stream));
+    if (nnz > 0) PPG_CK(launch_make_coloff((int)n, c->d_rowptr, c->d_colidx, c->d_coloff, c->d_info, c->stream));
+    PPG_CK(cudaMemcpyAsync(c->h_info, c->d_info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PPG_CK(cudaStreamSynchronize(c->stream));
+    if (c->h_info[0] != 0) {
+        cudaFree(c->d_coloff);
+        c->d_coloff = nullptr;
+    }
+    c->A.coloff = c->d_coloff;
+
     // tiling: rows per tile from the mean row length, staging capacity from the largest tile
     const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
     int R = 256;
@@ -932,6 +949,8 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
     if (avg > 20) R = 64;
     if (avg > 40) R = 32;
     if (avg > 80) R = 8;
+    const int G = kThreads / R;  // lanes per row
+    R *= spmv_rows_per_thread();
     std::vector<int> hrp(n + 1);
     PPG_CK(cudaMemcpy(hrp.data(), c->d_rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
     long long maxtile = 0;
@@ -941,7 +960,7 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
     }
     const long long cap = std::min<long long>(spmv_cap_max(), round_up(maxtile + 8, 16));
     c->A.rows_per_tile = R;
-    c->A.lanes_per_row = kThreads / R;
+    c->A.lanes_per_row = G;
     c->A.cap64 = (int)std::max<long long>(cap, 64);
     c->A.cap32 = (int)std::max<long long>(cap, 64);
     PPG_CK(spmv_configure(&c->A));
@@ -962,6 +981,7 @@ void ppg_destroy(ppg_ctx *c)
     else cudaDeviceSynchronize();
     cudaFree(c->d_rowptr);
     cudaFree(c->d_colidx);
+    cudaFree(c->d_coloff);
     cudaFree(c->d_vals);
     cudaFree(c->d_vals32);
     cudaFree(c->st);

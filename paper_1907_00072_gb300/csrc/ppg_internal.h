@@ -38,9 +38,10 @@ struct DevMatrix {
     long long nnz;
     const int *rowptr;   // n + 1
     const int *colidx;   // nnz (+ 16 bytes of padding)
+    const short *coloff; // int16 column offsets col - row (+ padding), or null when some |col - row| > 32767
     const double *vals64;
     const float *vals32;  // may be null until first needed
-    int rows_per_tile;    // rows of one SpMV tile (R); R * lanes_per_row == kThreads
+    int rows_per_tile;    // rows of one SpMV tile (R); R * lanes_per_row == kThreads * rows per thread
     int lanes_per_row;    // G
     int cap64, cap32;     // non-zeros one tile can stage in shared memory
     int num_sms;
@@ -155,7 +156,9 @@ cudaError_t batch_configure();
 
 // one-time kernel attribute setup (dynamic shared memory limits)
 cudaError_t spmv_configure(DevMatrix *A);
+cudaError_t launch_make_coloff(int n, const int *rowptr, const int *colidx, short *out, int *flag, cudaStream_t s);
 int spmv_cap_max();
+int spmv_rows_per_thread();
 cudaError_t gs_configure();
 cudaError_t gram_configure();
 

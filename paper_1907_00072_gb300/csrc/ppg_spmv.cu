@@ -63,11 +63,11 @@ cudaError_t launch_cast_f32(const double *in, float *out, long long count, cudaS
 
 // ---------------------------------------------------------------- the fused SpMV step
 
-template <typename T>
+template <typename T, typename IDX>
 struct SpmvArgs {
     int n;
     const int *rowptr;
-    const int *colidx;
+    const IDX *cols;  // int32 column indices, or int16 offsets col - row
     const T *vals;
     int rows_per_tile;
     int lanes_per_row;
@@ -77,18 +77,37 @@ struct SpmvArgs {
     SpmvEpi e;
 };
 
+#ifndef PPG_SPMV_MIN_BLOCKS
+#define PPG_SPMV_MIN_BLOCKS 3  // CTAs per SM the register allocation is sized for
+#endif
+
+#ifndef PPG_SPMV_RPT
+#define PPG_SPMV_RPT 1  // rows per consumer thread when rows are short (gathers of all issued together)
+#endif
+
 constexpr int kSpmvConsumerWarps = 8;
+constexpr int kSpmvRpt = PPG_SPMV_RPT;
 constexpr int kSpmvThreads = (kSpmvConsumerWarps + 1) * 32;  // + one producer warp
 constexpr int kSpmvStages = 3;
-constexpr int kSpmvRpBytes = 1152;  // (256 + 1) row pointers, rounded up to 128 bytes
+constexpr int kSpmvRpBytes = (((256 * kSpmvRpt + 1) * 4 + 15) / 16 * 16 + 127) / 128 * 128;  // row pointers
 constexpr int kSpmvCapMax = 4096;
 
 __host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
 
-template <typename T>
+template <typename T, typename IDX>
 __host__ __device__ constexpr size_t spmv_stage_bytes(int cap)
 {
-    return kSpmvRpBytes + round128((size_t)cap * sizeof(T)) + round128((size_t)cap * 4);
+    return kSpmvRpBytes + round128((size_t)cap * sizeof(T)) + round128((size_t)cap * sizeof(IDX));
+}
+
+// column of entry k in row r: int32 indices as stored, int16 entries are offsets from the row
+template <typename IDX>
+__device__ __forceinline__ int col_of(IDX c, int r)
+{
+    if constexpr (sizeof(IDX) == 2)
+        return r + (int)c;
+    else
+        return (int)c;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -105,8 +124,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 // memory, gathering x (x + s2 x2 when a second input is given), then the row's first
 // lane applies the fused epilogue and the warp releases the stage.  Tiles whose
 // non-zeros exceed the stage read values and columns from global memory instead.
-template <typename T>
-__global__ void __launch_bounds__(kSpmvThreads, 3) k_spmv(SpmvArgs<T> a)
+template <typename T, typename IDX>
+__global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv(SpmvArgs<T, IDX> a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[kSpmvStages];
@@ -117,10 +136,11 @@ __global__ void __launch_bounds__(kSpmvThreads, 3) k_spmv(SpmvArgs<T> a)
     const int R = a.rows_per_tile;
     const int G = a.lanes_per_row;
     const long long ntiles = ((long long)a.n + R - 1) / R;
-    const size_t stage_bytes = spmv_stage_bytes<T>(a.cap);
+    const size_t stage_bytes = spmv_stage_bytes<T, IDX>(a.cap);
     const size_t val_off = kSpmvRpBytes;
     const size_t col_off = kSpmvRpBytes + round128((size_t)a.cap * sizeof(T));
     constexpr int VA = 16 / (int)sizeof(T);
+    constexpr int CA = 16 / (int)sizeof(IDX);
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     // tiles of this CTA whose matrix data is fetched before the predecessor kernel finishes
     const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -168,17 +188,17 @@ __global__ void __launch_bounds__(kSpmvThreads, 3) k_spmv(SpmvArgs<T> a)
                 const int r0 = (int)(tile * R);
                 const int rows = min(R, a.n - r0);
                 const int vs = e0 & ~(VA - 1), ve = (e1 + VA - 1) & ~(VA - 1);
-                const int cs = e0 & ~3, ce = (e1 + 3) & ~3;
+                const int cs = e0 & ~(CA - 1), ce = (e1 + CA - 1) & ~(CA - 1);
                 const bool staged = (ve - vs) <= a.cap && (ce - cs) <= a.cap && e1 > e0;
                 unsigned char *base = smem + s * stage_bytes;
                 const uint32_t rpb = ((uint32_t)(rows + 1) * 4u + 15u) & ~15u;
                 const uint32_t vb = staged ? (uint32_t)(ve - vs) * (uint32_t)sizeof(T) : 0u;
-                const uint32_t cb = staged ? (uint32_t)(ce - cs) * 4u : 0u;
+                const uint32_t cb = staged ? (uint32_t)(ce - cs) * (uint32_t)sizeof(IDX) : 0u;
                 mbar_arrive_expect_tx(&full[s], rpb + vb + cb);
                 bulk_g2s(base, a.rowptr + r0, rpb, &full[s]);
                 if (staged) {
                     bulk_g2s(base + val_off, a.vals + vs, vb, &full[s]);
-                    bulk_g2s(base + col_off, a.colidx + cs, cb, &full[s]);
+                    bulk_g2s(base + col_off, a.cols + cs, cb, &full[s]);
                 }
             }
         }
@@ -216,8 +236,10 @@ __global__ void __launch_bounds__(kSpmvThreads, 3) k_spmv(SpmvArgs<T> a)
     const T *w1 = resolve_ptr<T>(a.e.w1, st);
     const T ca0 = (T)s_coef[0], cb0 = (T)s_coef[1], cc0 = (T)s_coef[2];
     const T ca1 = (T)s_coef[3], cb1 = (T)s_coef[4], cc1 = (T)s_coef[5], c2 = (T)s_coef[6];
-    const int lr = tid / G;
+    const int lr = tid / G;  // first row of this lane group; rows lr + q * (256 / G), q < kSpmvRpt
     const int lg = tid & (G - 1);
+    constexpr int RP = kSpmvRpt;
+    const int rstep = kThreads / G;
     int i = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
         const int s = i % kSpmvStages;
@@ -229,68 +251,92 @@ __global__ void __launch_bounds__(kSpmvThreads, 3) k_spmv(SpmvArgs<T> a)
         const unsigned char *base = smem + s * stage_bytes;
         const int *s_rp = reinterpret_cast<const int *>(base);
         const T *s_val = reinterpret_cast<const T *>(base + val_off);
-        const int *s_col = reinterpret_cast<const int *>(base + col_off);
+        const IDX *s_col = reinterpret_cast<const IDX *>(base + col_off);
         const int r0 = (int)(tile * R);
         const int rows = min(R, a.n - r0);
         const int e0 = s_rp[0], e1 = s_rp[rows];
         const int vs = e0 & ~(VA - 1), ve = (e1 + VA - 1) & ~(VA - 1);
-        const int cs = e0 & ~3, ce = (e1 + 3) & ~3;
+        const int cs = e0 & ~(CA - 1), ce = (e1 + CA - 1) & ~(CA - 1);
         const bool staged = (ve - vs) <= a.cap && (ce - cs) <= a.cap && e1 > e0;
-        T acc = T(0);
-        const int r = r0 + lr;
-        // epilogue operands first: their loads overlap the gathers below
-        T pu0 = T(0), pw0 = T(0), pu1 = T(0), pw1 = T(0);
-        if (lg == 0 && lr < rows) {
-            if (u0) pu0 = u0[r];
-            if (w0) pw0 = w0[r];
-            if (o1) {
-                if (u1) pu1 = u1[r];
-                if (w1) pw1 = w1[r];
+        T acc[RP], pu0[RP], pw0[RP], pu1[RP], pw1[RP];
+        int kb[RP], ke[RP], rr[RP];
+        bool ok[RP];
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+            const int l = lr + q * rstep;
+            ok[q] = l < rows;
+            rr[q] = r0 + l;
+            kb[q] = ok[q] ? s_rp[l] + lg : 0;
+            ke[q] = ok[q] ? s_rp[l + 1] : 0;
+            acc[q] = pu0[q] = pw0[q] = pu1[q] = pw1[q] = T(0);
+            // epilogue operands first: their loads overlap the gathers below
+            if (lg == 0 && ok[q]) {
+                if (u0) pu0[q] = u0[rr[q]];
+                if (w0) pw0[q] = w0[rr[q]];
+                if (o1) {
+                    if (u1) pu1[q] = u1[rr[q]];
+                    if (w1) pw1[q] = w1[rr[q]];
+                }
             }
         }
-        if (lr < rows) {
-            const int k0 = s_rp[lr], k1 = s_rp[lr + 1];
-            if (staged) {
-                // all of a lane's gathers (up to 8 per batch) are issued before the first FMA
-                for (int k = k0 + lg; k < k1; k += 8 * G) {
-                    int q[8];
-                    T xv[8];
+        if (staged) {
+            // all of a lane's gathers (up to 8 per row per batch) are issued before the first FMA
+            bool more = true;
+            while (more) {
+                int qc[RP][8];
+                T xv[RP][8];
+#pragma unroll
+                for (int q = 0; q < RP; ++q)
 #pragma unroll
                     for (int t = 0; t < 8; ++t) {
-                        const int kk = k + t * G;
-                        q[t] = kk < k1 ? s_col[kk - cs] : -1;
+                        const int kk = kb[q] + t * G;
+                        qc[q][t] = kk < ke[q] ? col_of<IDX>(s_col[kk - cs], rr[q]) : -1;
                     }
-                    if (x2 == nullptr) {
+                if (x2 == nullptr) {
 #pragma unroll
-                        for (int t = 0; t < 8; ++t) xv[t] = q[t] >= 0 ? __ldg(x + q[t]) : T(0);
-                    } else {
+                    for (int q = 0; q < RP; ++q)
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) xv[q][t] = qc[q][t] >= 0 ? __ldg(x + qc[q][t]) : T(0);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < RP; ++q)
 #pragma unroll
                         for (int t = 0; t < 8; ++t)
-                            xv[t] = q[t] >= 0 ? fma(c2, __ldg(x2 + q[t]), __ldg(x + q[t])) : T(0);
-                    }
+                            xv[q][t] = qc[q][t] >= 0 ? fma(c2, __ldg(x2 + qc[q][t]), __ldg(x + qc[q][t])) : T(0);
+                }
+                more = false;
+#pragma unroll
+                for (int q = 0; q < RP; ++q) {
 #pragma unroll
                     for (int t = 0; t < 8; ++t)
-                        if (q[t] >= 0) acc = fma(s_val[k + t * G - vs], xv[t], acc);
-                }
-            } else {
-                for (int k = k0 + lg; k < k1; k += G) {
-                    const int q = __ldg(a.colidx + k);
-                    const T xv = x2 ? fma(c2, __ldg(x2 + q), __ldg(x + q)) : __ldg(x + q);
-                    acc = fma(__ldg(a.vals + k), xv, acc);
+                        if (qc[q][t] >= 0) acc[q] = fma(s_val[kb[q] + t * G - vs], xv[q][t], acc[q]);
+                    kb[q] += 8 * G;
+                    more = more || kb[q] < ke[q];
                 }
             }
+        } else {
+#pragma unroll
+            for (int q = 0; q < RP; ++q)
+                for (int k = kb[q]; k < ke[q]; k += G) {
+                    const int qq = col_of<IDX>(__ldg(a.cols + k), rr[q]);
+                    const T xv = x2 ? fma(c2, __ldg(x2 + qq), __ldg(x + qq)) : __ldg(x + qq);
+                    acc[q] = fma(__ldg(a.vals + k), xv, acc[q]);
+                }
         }
-        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lg == 0 && lr < rows) {
-            T v = ca0 * acc;
-            if (u0) v = fma(cb0, pu0, v);
-            if (w0) v = fma(cc0, pw0, v);
-            o0[r] = v;
-            if (o1) {
-                T v1 = ca1 * acc;
-                if (u1) v1 = fma(cb1, pu1, v1);
-                if (w1) v1 = fma(cc1, pw1, v1);
-                o1[r] = v1;
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+            for (int o = G >> 1; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            if (lg == 0 && ok[q]) {
+                T v = ca0 * acc[q];
+                if (u0) v = fma(cb0, pu0[q], v);
+                if (w0) v = fma(cc0, pw0[q], v);
+                o0[rr[q]] = v;
+                if (o1) {
+                    T v1 = ca1 * acc[q];
+                    if (u1) v1 = fma(cb1, pu1[q], v1);
+                    if (w1) v1 = fma(cc1, pw1[q], v1);
+                    o1[rr[q]] = v1;
+                }
             }
         }
         __syncwarp();
@@ -299,54 +345,94 @@ __global__ void __launch_bounds__(kSpmvThreads, 3) k_spmv(SpmvArgs<T> a)
 }
 
 namespace {
-template <typename T>
+template <typename T, typename IDX>
 int spmv_per_sm(int cap)
 {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<T>, kSpmvThreads, kSpmvStages * spmv_stage_bytes<T>(cap));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<T, IDX>, kSpmvThreads,
+                                                  kSpmvStages * spmv_stage_bytes<T, IDX>(cap));
     return nb > 0 ? nb : 1;
+}
+
+template <typename T, typename IDX>
+cudaError_t spmv_go(const DevMatrix &A, const T *vals, const IDX *cols, int cap, int blocks, const SpmvEpi &e,
+                    Cycle *st, int check_done, cudaStream_t s)
+{
+    const int R = A.rows_per_tile;
+    const long long ntiles = ((long long)A.n + R - 1) / R;
+    SpmvArgs<T, IDX> a{A.n, A.rowptr, cols, vals, R, A.lanes_per_row, cap, st, check_done, e};
+    long long g = blocks;
+    if (g > ntiles) g = ntiles;
+    return launch_pdl(k_spmv<T, IDX>, dim3((unsigned)g), dim3(kSpmvThreads),
+                      kSpmvStages * spmv_stage_bytes<T, IDX>(cap), s, a);
+}
+
+template <typename T, typename IDX>
+cudaError_t spmv_set_smem()
+{
+    return cudaFuncSetAttribute(k_spmv<T, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(kSpmvStages * spmv_stage_bytes<T, IDX>(kSpmvCapMax)));
 }
 }  // namespace
 
 cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *st, int check_done, cudaStream_t s)
 {
-    const int R = A.rows_per_tile;
-    const long long ntiles = ((long long)A.n + R - 1) / R;
     if (prec == kF64) {
-        SpmvArgs<double> a{A.n, A.rowptr, A.colidx, A.vals64, R, A.lanes_per_row, A.cap64, st, check_done, e};
-        long long g = (long long)A.spmv_blocks64;
-        if (g > ntiles) g = ntiles;
-        return launch_pdl(k_spmv<double>, dim3((unsigned)g), dim3(kSpmvThreads),
-                          kSpmvStages * spmv_stage_bytes<double>(A.cap64), s, a);
-    } else {
-        SpmvArgs<float> a{A.n, A.rowptr, A.colidx, A.vals32, R, A.lanes_per_row, A.cap32, st, check_done, e};
-        long long g = (long long)A.spmv_blocks32;
-        if (g > ntiles) g = ntiles;
-        return launch_pdl(k_spmv<float>, dim3((unsigned)g), dim3(kSpmvThreads),
-                          kSpmvStages * spmv_stage_bytes<float>(A.cap32), s, a);
+        if (A.coloff) return spmv_go<double, short>(A, A.vals64, A.coloff, A.cap64, A.spmv_blocks64, e, st, check_done, s);
+        return spmv_go<double, int>(A, A.vals64, A.colidx, A.cap64, A.spmv_blocks64, e, st, check_done, s);
     }
+    if (A.coloff) return spmv_go<float, short>(A, A.vals32, A.coloff, A.cap32, A.spmv_blocks32, e, st, check_done, s);
+    return spmv_go<float, int>(A, A.vals32, A.colidx, A.cap32, A.spmv_blocks32, e, st, check_done, s);
 }
 
 // Sets the dynamic shared memory limit (for the largest staging capacity, once) and returns
-// the persistent grid sizes for this matrix's capacities.
+// the persistent grid sizes for this matrix's capacities and index format.
 cudaError_t spmv_configure(DevMatrix *A)
 {
     static bool done = false;
     if (!done) {
-        cudaError_t err = cudaFuncSetAttribute(k_spmv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(kSpmvStages * spmv_stage_bytes<double>(kSpmvCapMax)));
-        if (err != cudaSuccess) return err;
-        err = cudaFuncSetAttribute(k_spmv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(kSpmvStages * spmv_stage_bytes<float>(kSpmvCapMax)));
+        cudaError_t err = spmv_set_smem<double, int>();
+        if (err == cudaSuccess) err = spmv_set_smem<double, short>();
+        if (err == cudaSuccess) err = spmv_set_smem<float, int>();
+        if (err == cudaSuccess) err = spmv_set_smem<float, short>();
         if (err != cudaSuccess) return err;
         done = true;
     }
-    A->spmv_blocks64 = spmv_per_sm<double>(A->cap64) * A->num_sms;
-    A->spmv_blocks32 = spmv_per_sm<float>(A->cap32) * A->num_sms;
+    if (A->coloff) {
+        A->spmv_blocks64 = spmv_per_sm<double, short>(A->cap64) * A->num_sms;
+        A->spmv_blocks32 = spmv_per_sm<float, short>(A->cap32) * A->num_sms;
+    } else {
+        A->spmv_blocks64 = spmv_per_sm<double, int>(A->cap64) * A->num_sms;
+        A->spmv_blocks32 = spmv_per_sm<float, int>(A->cap32) * A->num_sms;
+    }
     return cudaSuccess;
 }
 
+// int16 column offsets (col - row) when every entry is within 32767 of its row; flag = 1 otherwise
+__global__ void k_make_coloff(int n, const int *__restrict__ rowptr, const int *__restrict__ colidx, short *out,
+                              int *flag)
+{
+    const int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+            const int d = colidx[k] - r;
+            if (d < -32767 || d > 32767) atomicOr(flag, 1);
+            out[k] = (short)d;
+        }
+    }
+}
+
+cudaError_t launch_make_coloff(int n, const int *rowptr, const int *colidx, short *out, int *flag, cudaStream_t s)
+{
+    int grid = (n + kThreads - 1) / kThreads;
+    if (grid > 8192) grid = 8192;
+    k_make_coloff<<<grid, kThreads, 0, s>>>(n, rowptr, colidx, out, flag);
+    return cudaGetLastError();
+}
+
 int spmv_cap_max() { return kSpmvCapMax; }
+
+int spmv_rows_per_thread() { return kSpmvRpt; }
 
 // ---------------------------------------------------------------- matrix-free epilogue (last root of the product form)
 
