@@ -35,6 +35,27 @@ UNIT = "ms"
 WORKLOAD = "3D convection-diffusion 7-point upwind, 128^3 (n=2097152, nnz=14581760), Pe 50, GMRES(50), rtol 1e-8"
 
 
+# DRAM traffic of one k_spmv<float, short> launch (a root step of the p(A) chain, C2 matrix) from the ncu
+# capture summarised in profiles/k_spmv_c2_128cubed.md, and the kernel source it was taken with: when the
+# source changes, the number no longer describes the kernel and the bench reports null.
+SPMV_TRAFFIC = {"src_sha256_16": "4c6c9bfc5084f604", "dram_bytes": 112686592 + 6483200,
+                "algorithmic_bytes": 112656384 + 16777216,
+                "launch": "k_spmv<float, short> root step (gather P; write Y and P'), ncu --set full, cold caches"}
+
+
+def spmv_traffic():
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_1907_00072_gb300", "csrc", "ppg_spmv.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None, None
+    if sha != SPMV_TRAFFIC["src_sha256_16"]:
+        return None, None
+    return SPMV_TRAFFIC["dram_bytes"], SPMV_TRAFFIC
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -301,6 +322,7 @@ def main():
                     "restarts": inf.stats["restarts"], "relres_true": inf.stats["relres_true"],
                     "status": inf.status}
 
+    traffic, traffic_info = spmv_traffic()
     cpu = None
     if rank == 0 and not args.no_cpu:
         tb, ti = oracle_sample(a, b_h, args.degree, iters=2)
@@ -325,7 +347,8 @@ def main():
                      "kernel": ("k_spmv<float>" if prec == ppg.PPG_F32 else "k_spmv<double>")
                                + " (SpMV chain: fused Horner / root steps of p(A) and the SpMV with A)",
                      "achieved": round(spmv_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(spmv_gbs / hbm, 3),
-                     "peak_source": "measured" if "hbm_gbs" in pk else "fallback", "traffic": None,
+                     "peak_source": "measured" if "hbm_gbs" in pk else "fallback", "traffic": traffic,
+                     "traffic_note": traffic_info,
                      "timed_segments": ps["spmv_segments"], "ms_total": round(ps["spmv_ms"], 3),
                      "bytes_total": ps["spmv_bytes"]},
         "roofline_ortho": {"bound": "hbm", "kernel": "k_gs (two-pass classical Gram-Schmidt)",
