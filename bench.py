@@ -35,6 +35,13 @@ UNIT = "ms"
 WORKLOAD = "3D convection-diffusion 7-point upwind, 128^3 (n=2097152, nnz=14581760), Pe 50, GMRES(50), rtol 1e-8"
 
 
+def workload_name(N, nnz=None):
+    if N == 128:
+        return WORKLOAD
+    return (f"3D convection-diffusion 7-point upwind, {N}^3 (n={N ** 3}" + (f", nnz={nnz}" if nnz else "")
+            + "), Pe 50, GMRES(50), rtol 1e-8")
+
+
 # DRAM traffic of one k_spmv<float, short> launch (a root step of the p(A) chain, C2 matrix) from the ncu
 # capture summarised in profiles/k_spmv_c2_128cubed.md, and the kernel source it was taken with: when the
 # source changes, the number no longer describes the kernel and the bench reports null.
@@ -169,7 +176,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "degree": args.degree, "basis": "arnoldi-form (oracle)",
+        "config": {"workload": workload_name(args.N, a.nnz), "degree": args.degree, "basis": "arnoldi-form (oracle)",
                    "restart": 50, "iterations_assumed": est_iters},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"oracle polynomial build (degree {args.degree}) + 2 GMRES(50) iterations on the "
@@ -337,7 +344,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == ppg.PPG_F32 else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "degree": args.degree, "basis": "roots (Leja)", "restart": 50,
+        "config": {"workload": workload_name(args.N, a.nnz), "degree": args.degree, "basis": "roots (Leja)",
+                   "restart": 50,
                    "precision": "f32 inner, f64 refinement" if prec == ppg.PPG_F32 else "f64",
                    "l2": "inputs larger than L2 (CSR 175 MB, basis up to 857 MB)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
