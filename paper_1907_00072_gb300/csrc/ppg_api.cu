@@ -15,7 +15,9 @@
 #include <cmath>
 #include <mutex>
 #include <new>
+#include <stdlib.h>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ppg.h"
@@ -89,6 +91,8 @@ struct ppg_ctx {
     int *d_info = nullptr;      // 16 ints
     int *h_info = nullptr;      // pinned
     double *h_small = nullptr;  // pinned, 4 * kKmax
+    int *h_prog = nullptr;      // pinned, mapped: the device's progress word (Cycle::prog)
+    int *d_prog = nullptr;      // its device address
 
     char *ws = nullptr;
     size_t ws_bytes = 0;
@@ -528,6 +532,7 @@ ppg_status init_cycle_state(ppg_ctx *c, int mode, int m, long long maxit, double
     h->tol = tol;
     h->inner_rtol = inner;
     h->cycle_done = 1;
+    h->prog = c->d_prog;
     PPG_CK(cudaMemcpyAsync(c->st, h, kCycleHeader, cudaMemcpyHostToDevice, c->stream));
     PPG_CK(cudaMemsetAsync(c->st->ticket, 0, sizeof(c->st->ticket), c->stream));
     return PPG_OK;
@@ -657,6 +662,48 @@ void prof_collect(ppg_ctx *c, ppg_stats *st)
     }
 }
 
+// Iterations kept queued on the stream beyond the last one the device has finished.  The
+// device publishes its progress after every iteration (Cycle::prog); once a cycle ends
+// (convergence, breakdown, restart length or iteration limit) the host enqueues nothing
+// more for it, so at most this many launched iterations return without work.
+int launch_ahead()
+{
+    static const int v = [] {
+        const char *e = getenv("PPG_LAUNCH_AHEAD");
+        const int a = e ? atoi(e) : 0;
+        return a > 0 ? a : 2;
+    }();
+    return v;
+}
+
+// Enqueues the iterations of one restart cycle.  The host waits (yielding) while `ahead`
+// iterations are queued; the wait also ends when the stream has drained, which a cycle whose
+// kernels returned early (an error flag) can cause: the caller reads the state next.
+ppg_status run_cycle(ppg_ctx *c, Iter &it, int restart)
+{
+    volatile int *prog = c->h_prog;
+    *prog = 0;
+    const int ahead = launch_ahead();
+    for (int j = 0; j < restart; ++j) {
+        for (int spin = 0;; ++spin) {
+            const int p = *prog;
+            if (p >> 16) return PPG_OK;
+            if (j - (p & 0xffff) < ahead) break;
+            if ((spin & 63) == 63) {
+                const cudaError_t q = cudaStreamQuery(c->stream);
+                if (q == cudaSuccess) {
+                    if (*prog >> 16) return PPG_OK;
+                    break;
+                }
+                if (q != cudaErrorNotReady) PPG_CK(q);
+            }
+            std::this_thread::yield();
+        }
+        PPG_TRY(it.iteration(j));
+    }
+    return PPG_OK;
+}
+
 ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int restart, int maxit,
                       const ppg_opts *opts, ppg_stats *stats)
 {
@@ -701,7 +748,7 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
         residuals++;
         PPG_TRY(read_state(c));
         while (!c->h_st->stop) {
-            for (int j = 0; j < restart; ++j) PPG_TRY(it.iteration(j));
+            PPG_TRY(run_cycle(c, it, restart));
             PPG_TRY(it.cycle_end(x));
             if (c->prof) PPG_TRY(prof_close_cycle(c));
             c->launches++;
@@ -918,6 +965,8 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
     PPG_CK(cudaMallocHost(&c->h_st, kCycleHeader));
     PPG_CK(cudaMallocHost(&c->h_info, sizeof(int) * 16));
     PPG_CK(cudaMallocHost(&c->h_small, sizeof(double) * 4 * kKmax));
+    PPG_CK(cudaHostAlloc(&c->h_prog, 64, cudaHostAllocMapped));
+    PPG_CK(cudaHostGetDevicePointer((void **)&c->d_prog, c->h_prog, 0));
     PPG_CK(cudaEventCreate(&c->ev0));
     PPG_CK(cudaEventCreate(&c->ev1));
 
@@ -991,6 +1040,7 @@ void ppg_destroy(ppg_ctx *c)
     cudaFreeHost(c->h_st);
     cudaFreeHost(c->h_info);
     cudaFreeHost(c->h_small);
+    cudaFreeHost(c->h_prog);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);

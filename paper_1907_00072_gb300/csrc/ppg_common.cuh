@@ -36,6 +36,7 @@ struct Cycle {
     int mode;        // 0: GMRES (Givens, tests); 1: plain Arnoldi (no tests, stop at m)
     int stop;        // 1: solve finished (converged, maxit or error)
     int n_breakdowns;
+    int *prog;       // host-mapped progress word: (cycle_done << 16) | j after each iteration, or null
     long long iters;    // iterations over all cycles
     long long maxit;
     long long cycles;

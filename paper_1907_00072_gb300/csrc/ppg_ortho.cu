@@ -86,6 +86,16 @@ __device__ void finish_pass2(Cycle *st, const double *tot, int k)
 // H[j+1, j] and updates g; the cycle ends on a small estimate |g_{j+1}|, a breakdown,
 // the restart length or the iteration limit, and then y = R^{-1} g is formed and the
 // coefficients of the correction z = V y are left in coef.
+// Publishes the iteration count and the end-of-cycle flag to the host-mapped progress word, so
+// that the host stops enqueueing a cycle's iterations once it has ended.
+__device__ void publish_progress(const Cycle *st)
+{
+    if (st->prog) {
+        __threadfence_system();
+        *(volatile int *)st->prog = (st->cycle_done << 16) | st->j;
+    }
+}
+
 __device__ void finish_pass3(Cycle *st, double nsq)
 {
     const int j = st->j;
@@ -104,6 +114,7 @@ __device__ void finish_pass3(Cycle *st, double nsq)
         st->cycle_done = 1;
         st->k = 0;
         st->j = j + 1;
+        publish_progress(st);
         return;
     }
     const bool brk = !(nrm > 1e-14 * sqrt(st->w0sq));
@@ -153,6 +164,7 @@ __device__ void finish_pass3(Cycle *st, double nsq)
             for (int c = 0; c < k; ++c) st->coef[c] = -st->y[c] * st->sigma[c];
         }
     }
+    publish_progress(st);
 }
 
 // ---------------------------------------------------------------- the pass kernel
