@@ -36,11 +36,15 @@ PPG_BASIS_POWER = 0
 PPG_BASIS_ROOTS = 1
 PPG_F64 = 0
 PPG_F32 = 1
+PPG_SPMV_QUERY = -1
+PPG_SPMV_AUTO = 0
+PPG_SPMV_CSR = 1
+PPG_SPMV_SELL = 2
 
 # every symbol include/ppg.h declares
 EXPORTED = (
     "ppg_create", "ppg_destroy", "ppg_set_stream", "ppg_workspace_bytes", "ppg_set_workspace", "ppg_spmv",
-    "ppg_build_poly", "ppg_set_poly", "ppg_get_poly", "ppg_apply_poly", "ppg_apply_poly_noalloc", "ppg_solve",
+    "ppg_spmv_format", "ppg_build_poly", "ppg_set_poly", "ppg_get_poly", "ppg_apply_poly", "ppg_apply_poly_noalloc", "ppg_solve",
     "ppg_solve_transpose",
     "ppg_csr_outer", "ppg_arnoldi", "ppg_hessenberg_eigs", "ppg_fill_uniform", "ppg_solve_batched",
     "ppg_status_string", "ppg_last_error", "ppg_version",
@@ -95,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "ppg_workspace_bytes": (I, [P, I, I, I, ctypes.POINTER(ctypes.c_size_t)]),
         "ppg_set_workspace": (I, [P, P, ctypes.c_size_t]),
         "ppg_spmv": (I, [P, P, P, I]),
+        "ppg_spmv_format": (I, [P, I, ctypes.POINTER(I)]),
         "ppg_build_poly": (I, [P, I, I, P, U64, ctypes.POINTER(I)]),
         "ppg_set_poly": (I, [P, I, I, P]),
         "ppg_get_poly": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), P, I, ctypes.POINTER(D)]),
@@ -187,6 +192,13 @@ def ppg_set_workspace(ctx, ws):
 
 def ppg_spmv(ctx, x, y):
     return _check(load_library().ppg_spmv(ctx, _ptr(x), _ptr(y), _prec_of(x)), "ppg_spmv")
+
+
+def ppg_spmv_format(ctx, request=PPG_SPMV_QUERY):
+    """Selects (or with PPG_SPMV_QUERY reports) the sparse format the SpMV kernels read; returns the one in effect."""
+    out = ctypes.c_int(0)
+    _check(load_library().ppg_spmv_format(ctx, request, ctypes.byref(out)), "ppg_spmv_format")
+    return out.value
 
 
 def ppg_build_poly(ctx, degree, basis=PPG_BASIS_ROOTS, v0=None, seed=2):
@@ -358,6 +370,9 @@ class Solver:
         y = self._torch.empty_like(x) if y is None else y
         ppg_spmv(self.ctx, x, y)
         return y
+
+    def spmv_format(self, request=PPG_SPMV_QUERY):
+        return ppg_spmv_format(self.ctx, request)
 
     def build_poly(self, degree, basis=PPG_BASIS_ROOTS, v0=None, seed=2):
         self._workspace(1, max(degree, 30) if degree < 0 else degree)

@@ -74,6 +74,12 @@ struct ppg_ctx {
     short *d_coloff = nullptr;
     double *d_vals = nullptr;
     float *d_vals32 = nullptr;
+    int *d_sptr = nullptr;       // sliced ELL copy (DevMatrix::sptr ...)
+    short *d_soff = nullptr;
+    int *d_scol = nullptr;
+    double *d_svals64 = nullptr;
+    float *d_svals32 = nullptr;
+    int sell_auto = 0;           // the format the automatic choice picked
     long long ld = 0;  // padded vector length
 
     // polynomial (host copy; coefficients enter kernels as launch arguments)
@@ -182,6 +188,11 @@ ppg_status ensure_f32(ppg_ctx *c)
     PPG_CK(cudaMemsetAsync(c->d_vals32, 0, (size_t)(c->A.nnz + 8) * sizeof(float), c->stream));
     if (c->A.nnz > 0) PPG_CK(launch_cast_f32(c->d_vals, c->d_vals32, c->A.nnz, c->stream));
     c->A.vals32 = c->d_vals32;
+    if (c->A.nslices > 0) {
+        PPG_CK(cudaMalloc(&c->d_svals32, (size_t)c->A.spadded * sizeof(float)));
+        PPG_CK(launch_cast_f32(c->d_svals64, c->d_svals32, c->A.spadded, c->stream));
+        c->A.svals32 = c->d_svals32;
+    }
     return PPG_OK;
 }
 
@@ -254,14 +265,17 @@ bool same_vec(const VecRef &u, const VecRef &v)
     return u.base == v.base && u.ld == v.ld && u.col == v.col && u.follow == v.follow;
 }
 
-// Algorithmic bytes of one SpMV launch: values and column indices (in the stored format: int16
-// offsets or int32 indices) once, row pointers once, each distinct vector read once and each
-// output written once.
+// Algorithmic bytes of one SpMV launch: values and column indices once in the stored format
+// (row-block CSR: int16 offsets or int32 indices plus row pointers; sliced ELL: the padded
+// entries plus slice offsets), each distinct vector read once and each output written once.
 double spmv_bytes(const DevMatrix &A, int prec, const SpmvEpi &e)
 {
     const double es = prec == kF64 ? 8.0 : 4.0;
-    const double is = A.coloff ? 2.0 : 4.0;
-    double b = (double)A.nnz * (es + is) + 4.0 * (A.n + 1.0);
+    double b;
+    if (A.format == kFmtSell && A.nslices > 0)
+        b = (double)A.spadded * (es + (A.soff ? 2.0 : 4.0)) + 4.0 * (A.nslices + 1.0);
+    else
+        b = (double)A.nnz * (es + (A.coloff ? 2.0 : 4.0)) + 4.0 * (A.n + 1.0);
     const VecRef *reads[6] = {&e.x, &e.x2, &e.u0, &e.w0, &e.u1, &e.w1};
     int distinct = 0;
     for (int i = 0; i < 6; ++i) {
@@ -1013,6 +1027,43 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
     c->A.cap64 = (int)std::max<long long>(cap, 64);
     c->A.cap32 = (int)std::max<long long>(cap, 64);
     PPG_CK(spmv_configure(&c->A));
+
+    // sliced ELL copy: 32-row slices padded to their longest row (selectable with ppg_spmv_format)
+    {
+        const long long ns = (n + 31) / 32;
+        std::vector<int> hsp(ns + 1, 0);
+        long long pos = 0;
+        bool fits = true;
+        for (long long sl = 0; sl < ns; ++sl) {
+            int w = 0;
+            for (long long r = sl * 32; r < std::min<long long>(n, sl * 32 + 32); ++r) w = std::max(w, hrp[r + 1] - hrp[r]);
+            pos += 32LL * w;
+            if (pos >= (1LL << 31) - 64) {
+                fits = false;
+                break;
+            }
+            hsp[sl + 1] = (int)pos;
+        }
+        if (fits && nnz > 0) {
+            PPG_CK(cudaMalloc(&c->d_sptr, sizeof(int) * (ns + 1)));
+            PPG_CK(cudaMemcpy(c->d_sptr, hsp.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
+            PPG_CK(cudaMalloc(&c->d_svals64, sizeof(double) * std::max<long long>(pos, 1)));
+            if (c->d_coloff)
+                PPG_CK(cudaMalloc(&c->d_soff, sizeof(short) * std::max<long long>(pos, 1)));
+            else
+                PPG_CK(cudaMalloc(&c->d_scol, sizeof(int) * std::max<long long>(pos, 1)));
+            PPG_CK(launch_sell_fill((int)n, (int)ns, c->d_rowptr, c->d_colidx, c->d_vals, c->d_sptr, c->d_soff,
+                                    c->d_scol, c->d_svals64, c->stream));
+            c->A.nslices = (int)ns;
+            c->A.sptr = c->d_sptr;
+            c->A.soff = c->d_soff;
+            c->A.scol = c->d_scol;
+            c->A.svals64 = c->d_svals64;
+            c->A.spadded = pos;
+            c->sell_auto = kFmtCsr;  // measured slower than the TMA row-block kernel on every workload here
+        }
+        c->A.format = c->A.nslices > 0 ? c->sell_auto : kFmtCsr;
+    }
     PPG_CK(gs_configure());
     PPG_CK(gram_configure());
 
@@ -1033,6 +1084,11 @@ void ppg_destroy(ppg_ctx *c)
     cudaFree(c->d_coloff);
     cudaFree(c->d_vals);
     cudaFree(c->d_vals32);
+    cudaFree(c->d_sptr);
+    cudaFree(c->d_soff);
+    cudaFree(c->d_scol);
+    cudaFree(c->d_svals64);
+    cudaFree(c->d_svals32);
     cudaFree(c->st);
     cudaFree(c->d_small);
     cudaFree(c->d_info);
@@ -1045,6 +1101,24 @@ void ppg_destroy(ppg_ctx *c)
     if (c->ev1) cudaEventDestroy(c->ev1);
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
     delete c;
+}
+
+ppg_status ppg_spmv_format(ppg_ctx *c, int request, int *in_effect)
+{
+    g_last_error.clear();
+    if (!c) return fail(PPG_ERR_INVALID_ARG, "null context");
+    switch (request) {
+    case PPG_SPMV_QUERY: break;
+    case PPG_SPMV_AUTO: c->A.format = c->A.nslices > 0 ? c->sell_auto : kFmtCsr; break;
+    case PPG_SPMV_CSR: c->A.format = kFmtCsr; break;
+    case PPG_SPMV_SELL:
+        if (c->A.nslices == 0) return fail(PPG_ERR_INVALID_ARG, "no sliced ELL copy for this matrix");
+        c->A.format = kFmtSell;
+        break;
+    default: return fail(PPG_ERR_INVALID_ARG, "unknown SpMV format request %d", request);
+    }
+    if (in_effect) *in_effect = c->A.format == kFmtSell ? PPG_SPMV_SELL : PPG_SPMV_CSR;
+    return PPG_OK;
 }
 
 ppg_status ppg_set_stream(ppg_ctx *c, void *stream)

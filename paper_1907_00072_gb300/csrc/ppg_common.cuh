@@ -114,6 +114,17 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// adds to the bytes the current phase waits for, without arriving
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -171,9 +182,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 
 // Programmatic dependent launch.  Kernels of the solve path are launched so that they may
-// start while the previous kernel of the stream drains: each lets its own dependents start
-// (pdl_trigger) and waits for its predecessor's completion and memory (pdl_wait) before it
-// reads anything the predecessor may have written.  Both are no-ops for ordinary launches.
+// start while the previous kernel of the stream drains.  Each waits for its predecessor's
+// completion and memory (pdl_wait) before it reads anything the predecessor may have written,
+// and only then lets its own dependents start (pdl_trigger).  So when a kernel starts, every
+// kernel launched before its predecessor has completed: data those wrote (and constant data)
+// may be read before the wait.  Both are no-ops for ordinary launches.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
@@ -193,6 +206,35 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// A float32 value carried as an unevaluated sum hi + lo.  Adding two of them with Knuth's
+// two-sum keeps the rounding error of the high parts, so a warp tree of such additions is
+// accurate to about float64 level using float32 arithmetic only (float64 instructions are
+// scarce on this GPU: a warp-wide float64 add occupies the FP64 pipe ~64 times longer).
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    const float s = a.hi + b.hi;
+    const float bv = s - a.hi;
+    const float err = (a.hi - (s - bv)) + (b.hi - bv);
+    const float lo = a.lo + b.lo + err;
+    const float hi = s + lo;
+    return F2{hi, lo - (hi - s)};
+}
+
+// warp tree of compensated float32 sums, converted to float64 once
+__device__ __forceinline__ double warp_sum_f2(F2 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const F2 w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = f2_add(v, w);
+    }
+    return (double)v.hi + (double)v.lo;
+}
+
 // Sum over the CTA in a fixed order (warp trees, then warp 0 over the warp sums).
 // Every thread must call it; the result is valid in every thread.
 __device__ __forceinline__ double block_sum(double v, double *scratch /* >= 33 doubles */)
@@ -206,6 +248,24 @@ __device__ __forceinline__ double block_sum(double v, double *scratch /* >= 33 d
         double t = (lane < (int)(blockDim.x >> 5)) ? scratch[lane] : 0.0;
         t = warp_sum(t);
         if (lane == 0) scratch[32] = t;
+    }
+    __syncthreads();
+    return scratch[32];
+}
+
+// block_sum for a compensated float32 value: the warp trees run in float32, only the eight
+// warp totals are added in float64
+__device__ __forceinline__ double block_sum_f2(F2 v, double *scratch /* >= 33 doubles */)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const double wv = warp_sum_f2(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = wv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += scratch[q];
+        scratch[32] = t;
     }
     __syncthreads();
     return scratch[32];

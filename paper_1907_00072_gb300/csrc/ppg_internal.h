@@ -48,7 +48,21 @@ struct DevMatrix {
     int resid_blocks;     // grid of the persistent residual / norm kernels
     int spmv_blocks64;    // persistent SpMV grids
     int spmv_blocks32;
+    // sliced ELL copy (slices of 32 rows; entry k of row 32 s + l at sptr[s] + 32 k + l, slices padded
+    // to their longest row with a sentinel index), used by the SpMV when format == kFmtSell
+    int format;           // kFmtCsr or kFmtSell
+    int nslices;          // 0 when no sliced copy exists
+    const int *sptr;      // nslices + 1 entry offsets
+    const short *soff;    // int16 col - row, sentinel kSellPadOff; or null (then scol)
+    const int *scol;      // int32 columns, sentinel -1
+    const double *svals64;
+    const float *svals32;  // may be null until first needed
+    long long spadded;     // sptr[nslices]
 };
+
+constexpr int kFmtCsr = 0;
+constexpr int kFmtSell = 1;
+constexpr short kSellPadOff = -32768;  // outside the int16 offsets a row may use (|col - row| <= 32767)
 
 // Fused SpMV epilogue (one row r, Ax = (A (x + s2 x2))[r], x2 optional):
 //   out0[r] = a0 * Ax + b0 * u0[r] + c0 * w0[r]
@@ -156,6 +170,9 @@ cudaError_t batch_configure();
 
 // one-time kernel attribute setup (dynamic shared memory limits)
 cudaError_t spmv_configure(DevMatrix *A);
+// fills the sliced ELL copy (entries and padding; sptr given) from the CSR arrays
+cudaError_t launch_sell_fill(int n, int nslices, const int *rowptr, const int *colidx, const double *vals,
+                             const int *sptr, short *soff, int *scol, double *svals, cudaStream_t s);
 cudaError_t launch_make_coloff(int n, const int *rowptr, const int *colidx, short *out, int *flag, cudaStream_t s);
 int spmv_cap_max();
 int spmv_rows_per_thread();

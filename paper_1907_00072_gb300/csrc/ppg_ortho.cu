@@ -24,14 +24,22 @@ namespace ppg {
 // 32 KB.  At run time a stage holds exactly the launch's column bound kst (<= KM) plus w, and
 // as many stages as fit the shared-memory budget are used, so that small k still keeps many
 // bytes in flight.
+#ifndef PPG_GS_SMEM_KB
+#define PPG_GS_SMEM_KB 72
+#endif
+#ifndef PPG_GS_TILE_BYTES
+#define PPG_GS_TILE_BYTES 32768  // a full-width stage (KM columns) of one tile
+#endif
 constexpr int kGsMaxStages = 8;
-constexpr int kGsSmemBudget = 72 * 1024;  // dynamic shared memory per CTA: three CTAs per SM
+constexpr int kGsSmemBudget = PPG_GS_SMEM_KB * 1024;  // dynamic shared memory per CTA
 
 constexpr int pow2_floor(int v) { return v < 2 ? 1 : 2 * pow2_floor(v / 2); }
 
 template <typename T, int KM>
 struct GsCfg {
-    static constexpr int TR = pow2_floor(32768 / (KM * (int)sizeof(T)));  // rows per tile (divides 1024)
+    static constexpr int TR = pow2_floor(PPG_GS_TILE_BYTES / (KM * (int)sizeof(T))) > 32
+                                  ? pow2_floor(PPG_GS_TILE_BYTES / (KM * (int)sizeof(T)))
+                                  : 32;  // rows per tile (divides 1024)
     static constexpr int RPT = TR >= kThreads ? TR / kThreads : 1;       // rows per thread (update phase)
     static constexpr int TPR = TR >= kThreads ? 1 : kThreads / TR;       // threads per row (update phase)
     static constexpr int RPL = TR / 32;                                  // rows per lane (dot phase, stride 32)
@@ -45,11 +53,12 @@ template <typename T>
 struct Acc {
     double s = 0.0;
     __device__ __forceinline__ void add(double v) { s += v; }
-    __device__ __forceinline__ double get() const { return s; }
+    __device__ __forceinline__ double warp_total() const { return warp_sum(s); }
+    __device__ __forceinline__ double block_total(double *scratch) const { return block_sum(s, scratch); }
 };
 template <>
 struct Acc<float> {
-    float s = 0.f, c = 0.f;
+    float s = 0.f, c = 0.f;  // the running sum is s - c
     __device__ __forceinline__ void add(float v)
     {
         const float y = v - c;
@@ -57,7 +66,9 @@ struct Acc<float> {
         c = (t - s) - y;
         s = t;
     }
-    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+    // across lanes and warps with compensated float32 sums (see F2)
+    __device__ __forceinline__ double warp_total() const { return warp_sum_f2(F2{s, -c}); }
+    __device__ __forceinline__ double block_total(double *scratch) const { return block_sum_f2(F2{s, -c}, scratch); }
 };
 
 // ---------------------------------------------------------------- finalisation (last CTA, thread 0)
@@ -183,53 +194,85 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     __shared__ double scratch[33];
     __shared__ int s_last;
 
-    pdl_trigger();
-    pdl_wait();
     const int op = a.op;
-    if (a.kcols_from_k) {
-        if (st->k == 0) return;
-    } else if (st->cycle_done) {
-        return;
-    }
-    const int k = a.kcols_from_k ? st->k : st->j + 1;
-    if (k > KM || k > a.kstage) {  // the host's bound is too small: refuse rather than overrun a stage
-        if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&st->error, kErrTimeout);
-        return;
-    }
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const T *__restrict__ U = (const T *)a.U;
     T *w = (T *)a.w;
-    T *out = a.out_follow ? (T *)a.U + (long long)(st->j + 1) * a.ldu : (T *)a.out;
     const bool need_w = (op != kGsCombine);
     T *stage0 = reinterpret_cast<T *>(smem);
-    const int nst = a.nstages;                      // pipeline depth (2..kGsMaxStages)
+    const int nst = a.nstages;                            // pipeline depth (2..kGsMaxStages)
     const long long SS = (long long)(a.kstage + 1) * TR;  // elements per stage: kst columns + w
-
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t colb = TR * (uint32_t)sizeof(T);
     if (tid == 0) {
         for (int q = 0; q < nst; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
     }
-    for (int c = tid; c < KM; c += kThreads) s_coef[c] = (c < k && op != kGsDot) ? (T)st->coef[c] : T(0);
     __syncthreads();
 
-    auto issue = [&](long long tile, int stage) {
+    // Stage fills, by the lanes of warp 0.  A stage's barrier completes once lane 0 has arrived
+    // (with the w copy) and all bytes have landed, so the basis columns may be requested earlier.
+    auto issue_cols = [&](long long tile, int stage, int kc) {
         T *sU = stage0 + stage * SS;
-        const uint32_t colb = TR * (uint32_t)sizeof(T);
-        const uint32_t bytes = colb * (uint32_t)k + (need_w ? colb : 0u);
-        mbar_arrive_expect_tx(&bars[stage], bytes);
+        if (lane == 0) mbar_expect_tx(&bars[stage], colb * (uint32_t)kc);
+        __syncwarp();
+        fence_proxy_async_smem();
         const long long row0 = tile * TR;
-        for (int c = 0; c < k; ++c) bulk_g2s(sU + c * TR, U + (long long)c * a.ldu + row0, colb, &bars[stage]);
-        if (need_w) bulk_g2s(sU + (long long)a.kstage * TR, w + row0, colb, &bars[stage]);
+        for (int c = lane; c < kc; c += 32) bulk_g2s(sU + c * TR, U + (long long)c * a.ldu + row0, colb, &bars[stage]);
     };
-
-    // prologue: the first nst - 1 tiles; tile it + nst - 1 is issued at the start of iteration it
-    // into the stage freed by iteration it - 1
-    if (tid == 0) {
-        for (int q = 0; q < nst - 1; ++q) {
-            const long long t = blockIdx.x + (long long)q * gridDim.x;
-            if (t < a.ntiles) issue(t, q);
+    auto issue_w = [&](long long tile, int stage) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&bars[stage], need_w ? colb : 0u);
+            if (need_w) bulk_g2s(stage0 + stage * SS + (long long)a.kstage * TR, w + tile * TR, colb, &bars[stage]);
         }
+    };
+    auto tile_of = [&](int q) { return blockIdx.x + (long long)q * gridDim.x; };
+
+    // Before the wait on the predecessor: the basis columns of the first stages.  For the
+    // iteration passes the host's column count is the device's k, and the columns were written
+    // at least two launches back (every kernel of the stream releases its dependents only after
+    // its own wait, so all launches before the predecessor are complete here).  Pass 2 also
+    // takes w early: the SpMV wrote it two launches back and pass 1 only reads it.
+    const bool early = !a.kcols_from_k;
+    const bool early_w = early && op == kGsUpdDot;
+    if (early && wid == 0) {
+        for (int q = 0; q < nst - 1; ++q)
+            if (tile_of(q) < a.ntiles) {
+                issue_cols(tile_of(q), q, a.kstage);
+                if (early_w) issue_w(tile_of(q), q);
+            }
     }
+
+    pdl_wait();
+    pdl_trigger();
+    const bool skip = a.kcols_from_k ? (st->k == 0) : (st->cycle_done != 0);
+    const int k = a.kcols_from_k ? st->k : st->j + 1;
+    // the host's bound must cover k (else refuse rather than overrun a stage)
+    const bool bad = !skip && (k > KM || k > a.kstage || (early && k != a.kstage));
+    if (skip || bad) {
+        if (bad && tid == 0 && blockIdx.x == 0) atomicOr(&st->error, kErrTimeout);
+        if (early) {  // the copies already requested land before the CTA's shared memory is released
+            if (wid == 0 && lane == 0 && !early_w)
+                for (int q = 0; q < nst - 1; ++q)
+                    if (tile_of(q) < a.ntiles) mbar_arrive(&bars[q]);
+            if (tid == 0)
+                for (int q = 0; q < nst - 1; ++q)
+                    if (tile_of(q) < a.ntiles) mbar_wait_bounded(&bars[q], 0, kWaitLimitNs);
+        }
+        return;
+    }
+    T *out = a.out_follow ? (T *)a.U + (long long)(st->j + 1) * a.ldu : (T *)a.out;
+    for (int c = tid; c < KM; c += kThreads) s_coef[c] = (c < k && op != kGsDot) ? (T)st->coef[c] : T(0);
+
+    // prologue: the first nst - 1 tiles (their remaining copies); tile it + nst - 1 is issued at
+    // the start of iteration it into the stage freed by iteration it - 1
+    if (wid == 0) {
+        for (int q = 0; q < nst - 1; ++q)
+            if (tile_of(q) < a.ntiles) {
+                if (!early) issue_cols(tile_of(q), q, k);
+                if (!early_w) issue_w(tile_of(q), q);
+            }
+    }
+    __syncthreads();
 
     Acc<T> acc[CPW];
     Acc<T> nrm;  // float32 path: float32 Kahan sum per thread, float64 across threads
@@ -237,11 +280,11 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     int it = 0;
     for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
         const int stage = it % nst;
-        if (tid == 0) {
+        if (wid == 0) {
             const long long nt = tile + (long long)(nst - 1) * gridDim.x;
             if (nt < a.ntiles) {
-                fence_proxy_async_smem();
-                issue(nt, (it + nst - 1) % nst);
+                issue_cols(nt, (it + nst - 1) % nst, k);
+                issue_w(nt, (it + nst - 1) % nst);
             }
         }
         if (!mbar_wait_bounded(&bars[stage], (it / nst) & 1, kWaitLimitNs)) {
@@ -335,13 +378,13 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
         for (int i = 0; i < CPW; ++i) {
             const int c = wid + 8 * i;
             if (c < k) {
-                const double v = warp_sum(acc[i].get());
+                const double v = acc[i].warp_total();
                 if (lane == 0) a.partials[(long long)c * a.nblk + blockIdx.x] = v;
             }
         }
     }
     if (op != kGsCombine) {
-        const double nsum = block_sum(nrm.get(), scratch);
+        const double nsum = nrm.block_total(scratch);
         if (tid == 0) a.partials[(long long)kKmax * a.nblk + blockIdx.x] = nsum;
     }
     if (op == kGsCombine) return;

@@ -110,11 +110,6 @@ __device__ __forceinline__ int col_of(IDX c, int r)
         return (int)c;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
 // Persistent, warp-specialised row-block CSR SpMV.  Tiles of R consecutive rows are
 // dealt round-robin to the CTAs.  The producer warp keeps up to three tiles in flight:
 // for each it reads the tile's non-zero range from the row pointers and issues TMA bulk
@@ -154,7 +149,6 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv(Spmv
         fence_mbar_init();
     }
     __syncthreads();
-    pdl_trigger();
 
     if (wid == kSpmvConsumerWarps) {
         // ---------------- producer
@@ -174,6 +168,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv(Spmv
                     // the first stages hold matrix data only (constant): from here on the
                     // predecessor must be complete, and this launch may have nothing to do
                     pdl_wait();
+                    pdl_trigger();
                     if ((a.check_done == kSkipIfDone && st->cycle_done) ||
                         (a.check_done == kSkipIfNoCols && st->k == 0))
                         break;
@@ -207,6 +202,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv(Spmv
 
     // consumers: nothing a predecessor wrote is read before this point
     pdl_wait();
+    pdl_trigger();
     if ((a.check_done == kSkipIfDone && st->cycle_done) || (a.check_done == kSkipIfNoCols && st->k == 0)) {
         // nothing to do: let the prefetched matrix tiles land before the CTA exits
         for (int q = 0; q < prefetched; ++q) mbar_wait_bounded(&full[q], 0, kWaitLimitNs);
@@ -344,6 +340,243 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv(Spmv
     }
 }
 
+// ---------------------------------------------------------------- the fused SpMV step, sliced ELL
+
+// Streaming loads of matrix data: read once per launch, so they bypass L1 (which keeps the x gathers).
+template <typename T>
+__device__ __forceinline__ T ld_matrix(const T *p);
+template <>
+__device__ __forceinline__ double ld_matrix<double>(const double *p)
+{
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+template <>
+__device__ __forceinline__ float ld_matrix<float>(const float *p)
+{
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+template <>
+__device__ __forceinline__ short ld_matrix<short>(const short *p)
+{
+    unsigned short v;
+    asm volatile("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return (short)v;
+}
+template <>
+__device__ __forceinline__ int ld_matrix<int>(const int *p)
+{
+    int v;
+    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// column of a sliced-ELL entry, or -1 for padding
+template <typename IDX>
+__device__ __forceinline__ int sell_col(IDX c, int r)
+{
+    if constexpr (sizeof(IDX) == 2)
+        return c == kSellPadOff ? -1 : r + (int)c;
+    else
+        return (int)c;
+}
+
+template <typename T, typename IDX>
+struct SellArgs {
+    int n;
+    int nslices;
+    const int *sptr;
+    const IDX *cols;
+    const T *vals;
+    Cycle *st;
+    int check_done;
+    SpmvEpi e;
+};
+
+#ifndef PPG_SELL_MIN_BLOCKS
+#define PPG_SELL_MIN_BLOCKS 8  // 128-thread CTAs per SM the register allocation is sized for (float)
+#endif
+#ifndef PPG_SELL_MIN_BLOCKS_64
+#define PPG_SELL_MIN_BLOCKS_64 4  // (double)
+#endif
+
+constexpr int kSellWarps = 4;  // slices per 128-thread CTA
+constexpr int kSellChunk = 8;  // entries of a row loaded together
+
+// Loads chunk k0 of a slice's entries for one lane: kSellChunk entries 32 apart (padding and
+// entries past the slice read as value 0, column -1).
+template <typename T, typename IDX>
+__device__ __forceinline__ void sell_load(const T *vals, const IDX *cols, int k0, int ke, int lane, int row, T *v,
+                                          int *c)
+{
+#pragma unroll
+    for (int u = 0; u < kSellChunk; ++u) {
+        const int k = k0 + 32 * u;
+        const bool in = k < ke;
+        v[u] = in ? ld_matrix<T>(vals + k + lane) : T(0);
+        c[u] = in ? sell_col<IDX>(ld_matrix<IDX>(cols + k + lane), row) : -1;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T sell_dot(const T *__restrict__ x, const T *__restrict__ x2, T c2, const T *v,
+                                      const int *c, T acc)
+{
+    T xv[kSellChunk];
+    if (x2 == nullptr) {
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : T(0);
+    } else {
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u) xv[u] = c[u] >= 0 ? fma(c2, __ldg(x2 + c[u]), __ldg(x + c[u])) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kSellChunk; ++u)
+        if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+    return acc;
+}
+
+// Persistent: each CTA owns a contiguous range of 32-row slices (neighbouring rows share x in
+// L1) and its warps take every kSellWarps-th slice of it, one lane per row.  A slice's entries
+// are stored entry index by entry index, so each load of values and indices is one coalesced
+// request.  The first entries of the next slice are requested before this slice's x gathers,
+// and the first slice's before the wait on the predecessor kernel (the matrix is constant),
+// which overlaps them with the previous link of the chain.  Epilogue as in k_spmv.
+template <typename T, typename IDX>
+__global__ void __launch_bounds__(kSellWarps * 32, sizeof(T) == 4 ? PPG_SELL_MIN_BLOCKS : PPG_SELL_MIN_BLOCKS_64)
+    k_spmv_sell(SellArgs<T, IDX> a)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int per = (a.nslices + gridDim.x - 1) / gridDim.x;
+    const int s_end = min(a.nslices, (int)blockIdx.x * per + per);
+    int sl = (int)blockIdx.x * per + wid;
+    if (sl >= s_end) return;
+    T v[kSellChunk];
+    int c[kSellChunk];
+    int kb = a.sptr[sl], ke = a.sptr[sl + 1];
+    int kbn = 0, ken = 0;
+    if (sl + kSellWarps < s_end) {
+        kbn = a.sptr[sl + kSellWarps];
+        ken = a.sptr[sl + kSellWarps + 1];
+    }
+    sell_load<T, IDX>(a.vals, a.cols, kb, ke, lane, sl * 32 + lane, v, c);
+
+    pdl_wait();
+    pdl_trigger();
+    const Cycle *st = a.st;
+    if ((a.check_done == kSkipIfDone && st->cycle_done) || (a.check_done == kSkipIfNoCols && st->k == 0)) return;
+    double cf = 0.0;
+    switch (lane) {
+    case 0: cf = resolve(a.e.a0, st); break;
+    case 1: cf = resolve(a.e.b0, st); break;
+    case 2: cf = resolve(a.e.c0, st); break;
+    case 3: cf = resolve(a.e.a1, st); break;
+    case 4: cf = resolve(a.e.b1, st); break;
+    case 5: cf = resolve(a.e.c1, st); break;
+    case 6: cf = resolve(a.e.s2, st); break;
+    default: break;
+    }
+    const T ca0 = (T)__shfl_sync(0xffffffffu, cf, 0), cb0 = (T)__shfl_sync(0xffffffffu, cf, 1);
+    const T cc0 = (T)__shfl_sync(0xffffffffu, cf, 2), ca1 = (T)__shfl_sync(0xffffffffu, cf, 3);
+    const T cb1 = (T)__shfl_sync(0xffffffffu, cf, 4), cc1 = (T)__shfl_sync(0xffffffffu, cf, 5);
+    const T c2 = (T)__shfl_sync(0xffffffffu, cf, 6);
+    const T *__restrict__ x = resolve_ptr<T>(a.e.x, st);
+    const T *__restrict__ x2 = resolve_ptr<T>(a.e.x2, st);
+    T *o0 = resolve_ptr<T>(a.e.out0, st);
+    const T *u0 = resolve_ptr<T>(a.e.u0, st);
+    const T *w0 = resolve_ptr<T>(a.e.w0, st);
+    T *o1 = resolve_ptr<T>(a.e.out1, st);
+    const T *u1 = resolve_ptr<T>(a.e.u1, st);
+    const T *w1 = resolve_ptr<T>(a.e.w1, st);
+
+    for (; sl < s_end; sl += kSellWarps) {
+        const int row = sl * 32 + lane;
+        const bool live = row < a.n;
+        // epilogue operands first: their loads overlap the gathers
+        T pu0 = T(0), pw0 = T(0), pu1 = T(0), pw1 = T(0);
+        if (live) {
+            if (u0) pu0 = u0[row];
+            if (w0) pw0 = w0[row];
+            if (o1) {
+                if (u1) pu1 = u1[row];
+                if (w1) pw1 = w1[row];
+            }
+        }
+        // the next slice's first entries and the slice offsets of the one after it
+        const int sn = sl + kSellWarps;
+        T vn[kSellChunk];
+        int cn[kSellChunk];
+        sell_load<T, IDX>(a.vals, a.cols, kbn, ken, lane, sn * 32 + lane, vn, cn);
+        int kbnn = 0, kenn = 0;
+        if (sn + kSellWarps < s_end) {
+            kbnn = a.sptr[sn + kSellWarps];
+            kenn = a.sptr[sn + kSellWarps + 1];
+        }
+        T acc = sell_dot<T>(x, x2, c2, v, c, T(0));
+        for (int k = kb + 32 * kSellChunk; k < ke; k += 32 * kSellChunk) {  // rows longer than one chunk
+            sell_load<T, IDX>(a.vals, a.cols, k, ke, lane, row, v, c);
+            acc = sell_dot<T>(x, x2, c2, v, c, acc);
+        }
+        if (live) {
+            T r0 = ca0 * acc;
+            if (u0) r0 = fma(cb0, pu0, r0);
+            if (w0) r0 = fma(cc0, pw0, r0);
+            o0[row] = r0;
+            if (o1) {
+                T r1 = ca1 * acc;
+                if (u1) r1 = fma(cb1, pu1, r1);
+                if (w1) r1 = fma(cc1, pw1, r1);
+                o1[row] = r1;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u) {
+            v[u] = vn[u];
+            c[u] = cn[u];
+        }
+        kb = kbn;
+        ke = ken;
+        kbn = kbnn;
+        ken = kenn;
+    }
+}
+
+// one thread per row (rows n .. 32 nslices - 1 are empty): copies the row's entries into its
+// slice and marks the slice's remaining entries of the row as padding
+__global__ void k_sell_fill(int n, int nslices, const int *__restrict__ rowptr, const int *__restrict__ colidx,
+                            const double *__restrict__ vals, const int *__restrict__ sptr, short *soff, int *scol,
+                            double *svals)
+{
+    const int stride = gridDim.x * blockDim.x;
+    const int rows = nslices * 32;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
+        const int sl = r >> 5;
+        const int base = sptr[sl] + (r & 31);
+        const int width = (sptr[sl + 1] - sptr[sl]) >> 5;
+        const int k0 = r < n ? rowptr[r] : 0, len = r < n ? rowptr[r + 1] - k0 : 0;
+        for (int q = 0; q < width; ++q) {
+            const int pos = base + 32 * q;
+            const bool real = q < len;
+            svals[pos] = real ? vals[k0 + q] : 0.0;
+            if (soff) soff[pos] = real ? (short)(colidx[k0 + q] - r) : kSellPadOff;
+            if (scol) scol[pos] = real ? colidx[k0 + q] : -1;
+        }
+    }
+}
+
+cudaError_t launch_sell_fill(int n, int nslices, const int *rowptr, const int *colidx, const double *vals,
+                             const int *sptr, short *soff, int *scol, double *svals, cudaStream_t s)
+{
+    int grid = (nslices * 32 + kThreads - 1) / kThreads;
+    if (grid > 8192) grid = 8192;
+    if (grid < 1) grid = 1;
+    k_sell_fill<<<grid, kThreads, 0, s>>>(n, nslices, rowptr, colidx, vals, sptr, soff, scol, svals);
+    return cudaGetLastError();
+}
+
 namespace {
 template <typename T, typename IDX>
 int spmv_per_sm(int cap)
@@ -368,6 +601,24 @@ cudaError_t spmv_go(const DevMatrix &A, const T *vals, const IDX *cols, int cap,
 }
 
 template <typename T, typename IDX>
+cudaError_t sell_go(const DevMatrix &A, const T *vals, const IDX *cols, const SpmvEpi &e, Cycle *st, int check_done,
+                    cudaStream_t s)
+{
+    SellArgs<T, IDX> a{A.n, A.nslices, A.sptr, cols, vals, st, check_done, e};
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int nb = 0;
+        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_sell<T, IDX>, kSellWarps * 32, 0);
+        if (err != cudaSuccess) return err;
+        per_sm = nb > 0 ? nb : 1;
+    }
+    long long grid = (long long)per_sm * A.num_sms;
+    const long long need = (A.nslices + kSellWarps - 1) / kSellWarps;
+    if (grid > need) grid = need;
+    return launch_pdl(k_spmv_sell<T, IDX>, dim3((unsigned)grid), dim3(kSellWarps * 32), 0, s, a);
+}
+
+template <typename T, typename IDX>
 cudaError_t spmv_set_smem()
 {
     return cudaFuncSetAttribute(k_spmv<T, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -377,6 +628,14 @@ cudaError_t spmv_set_smem()
 
 cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *st, int check_done, cudaStream_t s)
 {
+    if (A.format == kFmtSell && A.nslices > 0) {
+        if (prec == kF64) {
+            if (A.soff) return sell_go<double, short>(A, A.svals64, A.soff, e, st, check_done, s);
+            return sell_go<double, int>(A, A.svals64, A.scol, e, st, check_done, s);
+        }
+        if (A.soff) return sell_go<float, short>(A, A.svals32, A.soff, e, st, check_done, s);
+        return sell_go<float, int>(A, A.svals32, A.scol, e, st, check_done, s);
+    }
     if (prec == kF64) {
         if (A.coloff) return spmv_go<double, short>(A, A.vals64, A.coloff, A.cap64, A.spmv_blocks64, e, st, check_done, s);
         return spmv_go<double, int>(A, A.vals64, A.colidx, A.cap64, A.spmv_blocks64, e, st, check_done, s);
@@ -439,8 +698,8 @@ int spmv_rows_per_thread() { return kSpmvRpt; }
 template <typename T>
 __global__ void k_axpy(int n, SpmvEpi e, Cycle *st, int check)
 {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     if (check == kSkipIfDone && st->cycle_done) return;
     if (check == kSkipIfNoCols && st->k == 0) return;
     T *o0 = resolve_ptr<T>(e.out0, st);
@@ -506,8 +765,8 @@ __global__ void __launch_bounds__(kThreads) k_residual(int n, const int *__restr
 {
     __shared__ double scratch[33];
     __shared__ int s_last;
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     if (st->stop) return;
     double nrm = 0.0;
     const int stride = gridDim.x * blockDim.x;
@@ -552,8 +811,8 @@ __global__ void __launch_bounds__(kThreads) k_norm_start(int n, const double *__
 {
     __shared__ double scratch[33];
     __shared__ int s_last;
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     double acc = 0.0;
     const int stride = gridDim.x * blockDim.x;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
@@ -601,8 +860,8 @@ cudaError_t launch_norm_start(int n, int out_prec, const double *v, void *out, i
 template <typename Te>
 __global__ void k_xupdate(int n, const Te *__restrict__ e, double *__restrict__ x, Cycle *st)
 {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     if (st->k == 0) return;
     const int stride = gridDim.x * blockDim.x;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) x[r] += (double)e[r];
@@ -619,8 +878,8 @@ cudaError_t launch_xupdate(int n, int prec, const void *e, double *x, Cycle *st,
 template <typename T>
 __global__ void k_copy_in(int n, const T *__restrict__ src, T *__restrict__ dst)
 {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     const int stride = gridDim.x * blockDim.x;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) dst[r] = src[r];
 }

@@ -66,6 +66,19 @@ def long_row_matrix():
     return w.CSR(n, rowptr.astype(np.int32), colidx, vals, "long_rows")
 
 
+def wide_band_matrix():
+    """Entries farther than 32767 from the diagonal (int32 column indices in every format)."""
+    n = 70001
+    i = np.arange(n)
+    cols = np.stack([i, (i + 40000) % n, (i * 7 + 3) % n], axis=1)
+    rows = [np.unique(c) for c in cols]
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum([len(c) for c in rows])
+    colidx = np.concatenate(rows).astype(np.int32)
+    vals = w.uniform(9, len(colidx)) + (colidx == np.repeat(i, np.diff(rowptr))) * 4.0
+    return w.CSR(n, rowptr.astype(np.int32), colidx, vals, "wide_band")
+
+
 MATRICES = {
     "c1_2d_64": w.c1_matrix,
     "3d_7pt_21": lambda: w.convdiff(21, 3, 50.0),
@@ -73,7 +86,10 @@ MATRICES = {
     "random_ragged": lambda: w.random_csr(3001, 6, 17, diag_shift=0.5),
     "long_rows": long_row_matrix,
     "bidiag1": w.bidiag1,
+    "wide_band": wide_band_matrix,
 }
+
+FORMATS = {"csr": ppg.PPG_SPMV_CSR, "sell": ppg.PPG_SPMV_SELL}
 
 
 # ---------------------------------------------------------------- generator
@@ -89,11 +105,13 @@ def test_fill_uniform_is_the_published_splitmix64_stream():
 # ---------------------------------------------------------------- SpMV
 
 
+@pytest.mark.parametrize("fmt", list(FORMATS))
 @pytest.mark.parametrize("name", list(MATRICES))
-def test_spmv_f64_matches_oracle(name):
+def test_spmv_f64_matches_oracle(name, fmt):
     a = MATRICES[name]()
     x = w.uniform(31, a.n)
     s = solver_for(a)
+    assert s.spmv_format(FORMATS[fmt]) == FORMATS[fmt]
     y = s.spmv(T(x)).cpu().numpy()
     ref = oracle.spmv(a, x)
     bound, lens = row_abs_bound(a, x)
@@ -101,15 +119,38 @@ def test_spmv_f64_matches_oracle(name):
     assert np.all(err <= 4 * U64 * (lens + 1) * bound + 1e-300), np.max(err / (bound + 1e-300))
 
 
-@pytest.mark.parametrize("name", ["c1_2d_64", "27pt_13", "long_rows"])
-def test_spmv_f32_matches_oracle(name):
+@pytest.mark.parametrize("fmt", list(FORMATS))
+@pytest.mark.parametrize("name", ["c1_2d_64", "27pt_13", "long_rows", "wide_band"])
+def test_spmv_f32_matches_oracle(name, fmt):
     a = MATRICES[name]()
     x = w.uniform(32, a.n).astype(np.float32)
     s = solver_for(a)
+    assert s.spmv_format(FORMATS[fmt]) == FORMATS[fmt]
     y = s.spmv(T(x, torch.float32)).cpu().numpy().astype(np.float64)
     ref = oracle.spmv(a, x.astype(np.float64))
     bound, lens = row_abs_bound(a, x.astype(np.float64))
     assert np.all(np.abs(y - ref) <= 4 * U32 * (lens + 2) * bound + 1e-30)
+
+
+def test_spmv_format_choice_and_nonfinite_padding():
+    """The automatic choice is the row-block CSR kernel; the sliced copy is selectable; padding
+    entries of the sliced format never touch x (an Inf in x reaches only the rows that reference it)."""
+    s = solver_for(w.c1_matrix())
+    assert s.spmv_format() == ppg.PPG_SPMV_CSR
+    assert s.spmv_format(ppg.PPG_SPMV_SELL) == ppg.PPG_SPMV_SELL
+    assert s.spmv_format(ppg.PPG_SPMV_AUTO) == ppg.PPG_SPMV_CSR
+    with pytest.raises(ppg.PPGError):
+        s.spmv_format(7)
+    a = MATRICES["random_ragged"]()
+    s = solver_for(a)
+    s.spmv_format(ppg.PPG_SPMV_SELL)
+    x = w.uniform(33, a.n)
+    x[100] = np.inf
+    y = s.spmv(T(x)).cpu().numpy()
+    touches = np.zeros(a.n, bool)
+    rows = np.repeat(np.arange(a.n), np.diff(a.rowptr))
+    touches[rows[a.colidx == 100]] = True
+    assert np.all(~np.isfinite(y[touches])) and np.all(np.isfinite(y[~touches]))
 
 
 # ---------------------------------------------------------------- p(A) v
@@ -364,6 +405,28 @@ def test_solve_matches_oracle(deg, basis, mat):
     assert abs(info.stats["relres_true"] - _true_relres(a, b, xg)) <= 1e-10
     assert np.linalg.norm(xg - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
     assert abs(info.stats["iterations"] - ref.iters) <= max(1, 0.05 * ref.iters)
+
+
+@pytest.mark.parametrize("fmt", list(FORMATS))
+@pytest.mark.parametrize("mat", ["c1", "random"])
+def test_solve_in_both_sparse_formats(mat, fmt):
+    """The same solve through the row-block CSR kernel and the sliced ELL kernel: both follow the
+    oracle's iteration count and reach its solution."""
+    a = ROOT_MATS[mat]()
+    b = w.rhs(a.n)
+    v0 = w.v0(a.n)
+    s = solver_for(a)
+    assert s.spmv_format(FORMATS[fmt]) == FORMATS[fmt]
+    s.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=T(v0))
+    p = oracle.poly_gmres(a, v0, 10)
+    ref = oracle.gmres(a, b, p, tol=1e-8, m=50, maxit=5000)
+    for prec in (ppg.PPG_F64, ppg.PPG_F32):
+        x, info = s.solve(T(b), tol=1e-8, restart=50, maxit=5000, precision=prec)
+        xs = x.cpu().numpy()
+        assert info.stats["converged"] == 1 and _true_relres(a, b, xs) <= 1e-8
+        if prec == ppg.PPG_F64:
+            assert abs(info.stats["iterations"] - ref.iters) <= max(1, 0.05 * ref.iters)
+        assert np.linalg.norm(xs - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
 
 
 @pytest.mark.parametrize("restart", [1, 7, 30])
