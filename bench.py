@@ -202,7 +202,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=60)
     ap.add_argument("--profile-harness", action="store_true",
-                    help="for ncu: build the polynomial and run 20 iterations of one solve, print no benchmark line")
+                    help="for ncu: build the polynomial and run --harness-iters iterations of one solve, print no "
+                         "benchmark line")
+    ap.add_argument("--harness-iters", type=int, default=20)
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"],
                     help="c2 (default): the benchmark line; c1/c3/c4/c5: the other configurations, one JSON line each")
     args = ap.parse_args()
@@ -235,7 +237,7 @@ def main():
 
     if args.profile_harness:
         s.build_poly(args.degree, ppg.PPG_BASIS_ROOTS, v0=v0)
-        _, info = s.solve(b, tol=1e-8, restart=50, maxit=20, precision=prec)
+        _, info = s.solve(b, tol=1e-8, restart=50, maxit=args.harness_iters, precision=prec)
         torch.cuda.synchronize()
         print(json.dumps({"profile_harness": True, "iterations": info.stats["iterations"],
                           "launches": info.stats["kernel_launches"]}))

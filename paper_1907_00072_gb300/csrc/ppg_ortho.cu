@@ -30,16 +30,27 @@ namespace ppg {
 #ifndef PPG_GS_TILE_BYTES
 #define PPG_GS_TILE_BYTES 32768  // a full-width stage (KM columns) of one tile
 #endif
+#ifndef PPG_GS_TILE_BYTES_WIDE
+#define PPG_GS_TILE_BYTES_WIDE PPG_GS_TILE_BYTES  // the same for the buckets KM >= 64
+#endif
+#ifndef PPG_GS_SMEM_KB_WIDE
+#define PPG_GS_SMEM_KB_WIDE PPG_GS_SMEM_KB
+#endif
+#ifndef PPG_GS_STAGES
+#define PPG_GS_STAGES 2  // cap on the pipeline depth: more CTAs per SM beat deeper pipelines (measured)
+#endif
 constexpr int kGsMaxStages = 8;
-constexpr int kGsSmemBudget = PPG_GS_SMEM_KB * 1024;  // dynamic shared memory per CTA
 
 constexpr int pow2_floor(int v) { return v < 2 ? 1 : 2 * pow2_floor(v / 2); }
 
 template <typename T, int KM>
 struct GsCfg {
-    static constexpr int TR = pow2_floor(PPG_GS_TILE_BYTES / (KM * (int)sizeof(T))) > 32
-                                  ? pow2_floor(PPG_GS_TILE_BYTES / (KM * (int)sizeof(T)))
+    static constexpr int kTileBytes = KM >= 64 ? PPG_GS_TILE_BYTES_WIDE : PPG_GS_TILE_BYTES;
+    static constexpr int TR = pow2_floor(kTileBytes / (KM * (int)sizeof(T))) > 32
+                                  ? pow2_floor(kTileBytes / (KM * (int)sizeof(T)))
                                   : 32;  // rows per tile (divides 1024)
+    static constexpr int kSmemBudget = (KM >= 64 ? PPG_GS_SMEM_KB_WIDE : PPG_GS_SMEM_KB) * 1024;  // per CTA
+    static_assert(2 * (KM + 1) * TR * (int)sizeof(T) <= kSmemBudget, "two full-width stages must fit");
     static constexpr int RPT = TR >= kThreads ? TR / kThreads : 1;       // rows per thread (update phase)
     static constexpr int TPR = TR >= kThreads ? 1 : kThreads / TR;       // threads per row (update phase)
     static constexpr int RPL = TR / 32;                                  // rows per lane (dot phase, stride 32)
@@ -421,14 +432,16 @@ template <typename T, int KM>
 struct GsInst {
     static cudaError_t configure()
     {
-        return cudaFuncSetAttribute(k_gs<T, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGsSmemBudget);
+        return cudaFuncSetAttribute(k_gs<T, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    GsCfg<T, KM>::kSmemBudget);
     }
     static cudaError_t launch(GsArgs a, int kcols, long long ld, int num_sms, Cycle *st, cudaStream_t s)
     {
         constexpr int TR = GsCfg<T, KM>::TR;
         const size_t stage_bytes = (size_t)(kcols + 1) * TR * sizeof(T);
-        int nst = (int)(kGsSmemBudget / stage_bytes);
+        int nst = (int)(GsCfg<T, KM>::kSmemBudget / stage_bytes);
         if (nst > kGsMaxStages) nst = kGsMaxStages;
+        if (nst > PPG_GS_STAGES) nst = PPG_GS_STAGES;
         if (nst < 2) return cudaErrorInvalidValue;
         a.kstage = kcols;
         a.nstages = nst;

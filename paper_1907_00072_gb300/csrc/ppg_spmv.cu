@@ -80,6 +80,12 @@ struct SpmvArgs {
 #ifndef PPG_SPMV_MIN_BLOCKS
 #define PPG_SPMV_MIN_BLOCKS 3  // CTAs per SM the register allocation is sized for
 #endif
+#ifndef PPG_SPMV_CARVEOUT
+#define PPG_SPMV_CARVEOUT -1  // preferred shared-memory carveout (percent; -1: the driver's choice)
+#endif
+#ifndef PPG_SPMV_CTAS_PER_SM
+#define PPG_SPMV_CTAS_PER_SM 0  // cap on resident CTAs per SM (0: occupancy)
+#endif
 
 #ifndef PPG_SPMV_RPT
 #define PPG_SPMV_RPT 1  // rows per consumer thread when rows are short (gathers of all issued together)
@@ -584,6 +590,7 @@ int spmv_per_sm(int cap)
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<T, IDX>, kSpmvThreads,
                                                   kSpmvStages * spmv_stage_bytes<T, IDX>(cap));
+    if (PPG_SPMV_CTAS_PER_SM > 0 && nb > PPG_SPMV_CTAS_PER_SM) nb = PPG_SPMV_CTAS_PER_SM;
     return nb > 0 ? nb : 1;
 }
 
@@ -621,8 +628,11 @@ cudaError_t sell_go(const DevMatrix &A, const T *vals, const IDX *cols, const Sp
 template <typename T, typename IDX>
 cudaError_t spmv_set_smem()
 {
-    return cudaFuncSetAttribute(k_spmv<T, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(kSpmvStages * spmv_stage_bytes<T, IDX>(kSpmvCapMax)));
+    cudaError_t e = cudaFuncSetAttribute(k_spmv<T, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kSpmvStages * spmv_stage_bytes<T, IDX>(kSpmvCapMax)));
+    if (e == cudaSuccess && PPG_SPMV_CARVEOUT >= 0)
+        e = cudaFuncSetAttribute(k_spmv<T, IDX>, cudaFuncAttributePreferredSharedMemoryCarveout, PPG_SPMV_CARVEOUT);
+    return e;
 }
 }  // namespace
 
