@@ -82,32 +82,25 @@ struct Acc<float> {
     __device__ __forceinline__ double block_total(double *scratch) const { return block_sum_f2(F2{s, -c}, scratch); }
 };
 
-// ---------------------------------------------------------------- finalisation (last CTA, thread 0)
+// ---------------------------------------------------------------- finalisation (last CTA)
+//
+// The device state lives in global memory, where every dependent access of a serial loop costs
+// an L2 round trip; the last CTA therefore does the per-column work with all its threads and
+// runs the serial recurrences (Givens rotations, back substitution) on shared-memory copies.
 
-__device__ void finish_pass1(Cycle *st, const double *tot, int k, double wsq)
+// Passes 1 and 2: h = sigma .* tot (the pass's Hessenberg coefficients of v_0..v_{k-1}) and the
+// coefficients the next update multiplies the stored columns by (coef = h .* sigma).
+__device__ void cta_finish_pass12(Cycle *st, const double *tot, int k, double *h_out, bool pass1, double wsq)
 {
-    for (int c = 0; c < k; ++c) {
-        const double h = st->sigma[c] * tot[c];
-        st->h1[c] = h;
-        st->coef[c] = h * st->sigma[c];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        const double sg = st->sigma[c];
+        const double h = sg * tot[c];
+        h_out[c] = h;
+        st->coef[c] = h * sg;
     }
-    st->w0sq = wsq;
+    if (pass1 && threadIdx.x == 0) st->w0sq = wsq;
 }
 
-__device__ void finish_pass2(Cycle *st, const double *tot, int k)
-{
-    for (int c = 0; c < k; ++c) {
-        const double h = st->sigma[c] * tot[c];
-        st->h2[c] = h;
-        st->coef[c] = h * st->sigma[c];
-    }
-}
-
-// Completes Hessenberg column j: H[0..j, j] = h1 + h2, H[j+1, j] = ||v_{j+1}||.  In GMRES
-// mode the previous Givens rotations are applied to the column, a new rotation zeroes
-// H[j+1, j] and updates g; the cycle ends on a small estimate |g_{j+1}|, a breakdown,
-// the restart length or the iteration limit, and then y = R^{-1} g is formed and the
-// coefficients of the correction z = V y are left in coef.
 // Publishes the iteration count and the end-of-cycle flag to the host-mapped progress word, so
 // that the host stops enqueueing a cycle's iterations once it has ended.
 __device__ void publish_progress(const Cycle *st)
@@ -118,75 +111,125 @@ __device__ void publish_progress(const Cycle *st)
     }
 }
 
-__device__ void finish_pass3(Cycle *st, double nsq)
+// Pass 3: completes Hessenberg column j, H[0..j, j] = h1 + h2, H[j+1, j] = ||v_{j+1}||.  In GMRES
+// mode the previous Givens rotations are applied to the column, a new rotation zeroes H[j+1, j]
+// and updates g; the cycle ends on a small estimate |g_{j+1}|, a breakdown, the restart length or
+// the iteration limit, and then y = R^{-1} g is formed and the coefficients of the correction
+// z = V y are left in coef.  sh: shared scratch of sh_bytes (at least 3 (kKmax + 1) doubles).
+__device__ void cta_finish_pass3(Cycle *st, double nsq, double *sh, size_t sh_bytes, int *s_int)
 {
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int j = st->j;
-    const double nrm = sqrt(nsq);
-    double *Hj = st->H + (long long)j * kLdH;
-    double *Rj = st->R + (long long)j * kLdH;
-    bool finite = isfinite(nrm);
-    for (int i = 0; i <= j; ++i) {
-        Hj[i] = st->h1[i] + st->h2[i];
-        finite = finite && isfinite(Hj[i]);
+    double *col = sh;                // column j as built, then rotated (j + 2 values)
+    double *cs = sh + (kKmax + 1);   // rotations 0 .. j-1
+    double *sn = cs + kKmax;
+    if (tid == 0) s_int[0] = 0;
+    __syncthreads();
+    for (int i = tid; i <= j; i += nt) {
+        const double h = st->h1[i] + st->h2[i];
+        col[i] = h;
+        st->H[(long long)j * kLdH + i] = h;
+        if (!isfinite(h)) s_int[0] = 1;
     }
-    Hj[j + 1] = nrm;
-    if (!finite) {
-        st->error |= kErrNonfinite;
-        st->stop = 1;
-        st->cycle_done = 1;
-        st->k = 0;
-        st->j = j + 1;
-        publish_progress(st);
-        return;
-    }
-    const bool brk = !(nrm > 1e-14 * sqrt(st->w0sq));
-    st->sigma[j + 1] = brk ? 0.0 : 1.0 / nrm;
-    st->iters += 1;
-    bool done = brk || (j + 1 >= st->m) || (st->iters >= st->maxit);
-    if (st->mode == 0) {
-        for (int i = 0; i <= j + 1; ++i) Rj[i] = Hj[i];
-        for (int i = 0; i < j; ++i) {
-            const double a = Rj[i], b = Rj[i + 1];
-            Rj[i] = st->cs[i] * a + st->sn[i] * b;
-            Rj[i + 1] = -st->sn[i] * a + st->cs[i] * b;
+    if (st->mode == 0)
+        for (int i = tid; i < j; i += nt) {
+            cs[i] = st->cs[i];
+            sn[i] = st->sn[i];
         }
-        const double a = Rj[j], b = Rj[j + 1];
-        const double r = hypot(a, b);
-        double c = 1.0, s = 0.0;
-        if (r != 0.0) {
-            c = a / r;
-            s = b / r;
-        }
-        st->cs[j] = c;
-        st->sn[j] = s;
-        Rj[j] = r;
-        Rj[j + 1] = 0.0;
-        const double gj = st->g[j];
-        st->g[j] = c * gj;
-        st->g[j + 1] = -s * gj;
-        const double res = fabs(st->g[j + 1]);
-        st->est = res / st->bnorm;
-        done = done || (res <= st->tol * st->bnorm) || (st->inner_rtol > 0.0 && res <= st->inner_rtol * st->beta);
-    }
-    if (brk) {
-        st->breakdown = 1;
-        st->n_breakdowns += 1;
-    }
-    st->j = j + 1;
-    if (done) {
-        const int k = j + 1;
-        st->k = k;
-        st->cycle_done = 1;
-        if (st->mode == 0) {
-            for (int i = k - 1; i >= 0; --i) {
-                double v = st->g[i];
-                for (int q = i + 1; q < k; ++q) v -= st->R[i + (long long)q * kLdH] * st->y[q];
-                st->y[i] = v / st->R[i + (long long)i * kLdH];
+    __syncthreads();
+    if (tid == 0) {
+        int kdone = 0;
+        const double nrm = sqrt(nsq);
+        st->H[(long long)j * kLdH + j + 1] = nrm;
+        col[j + 1] = nrm;
+        if (s_int[0] || !isfinite(nrm)) {
+            st->error |= kErrNonfinite;
+            st->stop = 1;
+            st->cycle_done = 1;
+            st->k = 0;
+            st->j = j + 1;
+            kdone = -1;
+        } else {
+            const bool brk = !(nrm > 1e-14 * sqrt(st->w0sq));
+            st->sigma[j + 1] = brk ? 0.0 : 1.0 / nrm;
+            st->iters += 1;
+            bool done = brk || (j + 1 >= st->m) || (st->iters >= st->maxit);
+            if (st->mode == 0) {
+                for (int i = 0; i < j; ++i) {
+                    const double a = col[i], b = col[i + 1];
+                    col[i] = cs[i] * a + sn[i] * b;
+                    col[i + 1] = -sn[i] * a + cs[i] * b;
+                }
+                const double a = col[j], b = col[j + 1];
+                const double r = hypot(a, b);
+                double c = 1.0, s = 0.0;
+                if (r != 0.0) {
+                    c = a / r;
+                    s = b / r;
+                }
+                st->cs[j] = c;
+                st->sn[j] = s;
+                col[j] = r;
+                col[j + 1] = 0.0;
+                const double gj = st->g[j];
+                st->g[j] = c * gj;
+                st->g[j + 1] = -s * gj;
+                const double res = fabs(s * gj);
+                st->est = res / st->bnorm;
+                done = done || (res <= st->tol * st->bnorm) ||
+                       (st->inner_rtol > 0.0 && res <= st->inner_rtol * st->beta);
             }
-            for (int c = 0; c < k; ++c) st->coef[c] = -st->y[c] * st->sigma[c];
+            if (brk) {
+                st->breakdown = 1;
+                st->n_breakdowns += 1;
+            }
+            st->j = j + 1;
+            if (done) {
+                st->k = j + 1;
+                st->cycle_done = 1;
+                kdone = j + 1;
+            }
+        }
+        s_int[1] = kdone;
+    }
+    __syncthreads();
+    const int kdone = s_int[1];
+    if (kdone >= 0 && st->mode == 0)
+        for (int i = tid; i <= j + 1; i += nt) st->R[(long long)j * kLdH + i] = col[i];
+    if (kdone > 0 && st->mode == 0) {
+        // y = R^{-1} g (k = kdone): R staged in shared memory when it fits, then column-oriented
+        // back substitution by warp 0 (y_i = g_i / R_ii, then g_q -= R_qi y_i for q < i in parallel)
+        const int k = kdone;
+        double *g = sh;            // k values
+        double *Rs = sh + k;       // k x k, column-major, ld k
+        const bool staged = (size_t)(k + k * k) * sizeof(double) <= sh_bytes;
+        __syncthreads();           // col, cs, sn no longer needed
+        for (int i = tid; i < k; i += nt) g[i] = st->g[i];
+        if (staged)
+            for (int e = tid; e < k * k; e += nt) {
+                const int q = e / k, i = e - q * k;
+                Rs[e] = i <= q ? st->R[(long long)q * kLdH + i] : 0.0;
+            }
+        __syncthreads();
+        if (tid < 32) {
+            for (int i = k - 1; i >= 0; --i) {
+                const double *Ri = staged ? Rs + (long long)i * k : st->R + (long long)i * kLdH;
+                const double yi = g[i] / Ri[i];
+                __syncwarp();
+                for (int q = tid; q < i; q += 32) g[q] -= Ri[q] * yi;
+                if (tid == 0) g[i] = yi;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int c = tid; c < k; c += nt) {
+            const double y = g[c];
+            st->y[c] = y;
+            st->coef[c] = -y * st->sigma[c];
         }
     }
-    publish_progress(st);
+    __syncthreads();
+    if (tid == 0) publish_progress(st);
 }
 
 // ---------------------------------------------------------------- the pass kernel
@@ -204,6 +247,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     __shared__ double s_red[KM + 1];
     __shared__ double scratch[33];
     __shared__ int s_last;
+    __shared__ int s_int[2];
 
     const int op = a.op;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -412,15 +456,14 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
             if (lane == 0) s_red[KM] = v;
         }
         __syncthreads();
-        if (tid == 0) {
-            if (op == kGsDot)
-                finish_pass1(st, s_red, k, s_red[KM]);
-            else if (op == kGsUpdDot)
-                finish_pass2(st, s_red, k);
-            else
-                finish_pass3(st, s_red[KM]);
-            st->ticket[2 + op] = 0;
-        }
+        if (op == kGsDot)
+            cta_finish_pass12(st, s_red, k, st->h1, true, s_red[KM]);
+        else if (op == kGsUpdDot)
+            cta_finish_pass12(st, s_red, k, st->h2, false, 0.0);
+        else
+            cta_finish_pass3(st, s_red[KM], reinterpret_cast<double *>(smem),
+                             (size_t)nst * (size_t)SS * sizeof(T), s_int);
+        if (tid == 0) st->ticket[2 + op] = 0;
     }
 }
 
