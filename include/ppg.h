@@ -150,6 +150,19 @@ enum {
 };
 ppg_status ppg_spmv_format(ppg_ctx *ctx, int request, int *in_effect);
 
+/* Pairing of the p(A) chain's links (Eq. 2 applied link by link: each link is one SpMV with a fused
+ * vector update), in the spirit of the matrix powers kernel Section VII points to.  When on, two
+ * consecutive links share one cooperative launch: every tile of rows staged in shared memory serves
+ * the first link and, two rounds of the persistent grid later (once all rows within the matrix
+ * bandwidth have their first-link result, counted per round), the second, so the matrix crosses HBM
+ * once per two links.  Applies to the row-block CSR kernel when the bandwidth max |col - row| spans
+ * no more tiles than the launch has CTAs; otherwise links run one per launch.  Results are
+ * bit-identical either way (same tiles, same per-row arithmetic).  Off by default: on the 128^3
+ * stencil a paired launch took 124 us against 2 x 28.8 us for two single ones (the per-round waits
+ * cost more than the saved matrix traffic).  request: 1 on, 0 off, -1 query; *in_effect (host, may
+ * be NULL) receives 1 when float32 chains of this matrix are paired.  Errors: PPG_ERR_INVALID_ARG. */
+ppg_status ppg_chain_fusion(ppg_ctx *ctx, int request, int *in_effect);
+
 /* ------------------------------------------------------------------ polynomial */
 
 /* Builds the minimum-residual polynomial of the given degree from the generating vector v0

@@ -44,7 +44,7 @@ PPG_SPMV_SELL = 2
 # every symbol include/ppg.h declares
 EXPORTED = (
     "ppg_create", "ppg_destroy", "ppg_set_stream", "ppg_workspace_bytes", "ppg_set_workspace", "ppg_spmv",
-    "ppg_spmv_format", "ppg_build_poly", "ppg_set_poly", "ppg_get_poly", "ppg_apply_poly", "ppg_apply_poly_noalloc", "ppg_solve",
+    "ppg_spmv_format", "ppg_chain_fusion", "ppg_build_poly", "ppg_set_poly", "ppg_get_poly", "ppg_apply_poly", "ppg_apply_poly_noalloc", "ppg_solve",
     "ppg_solve_transpose",
     "ppg_csr_outer", "ppg_arnoldi", "ppg_hessenberg_eigs", "ppg_fill_uniform", "ppg_solve_batched",
     "ppg_status_string", "ppg_last_error", "ppg_version",
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH):
         "ppg_set_workspace": (I, [P, P, ctypes.c_size_t]),
         "ppg_spmv": (I, [P, P, P, I]),
         "ppg_spmv_format": (I, [P, I, ctypes.POINTER(I)]),
+        "ppg_chain_fusion": (I, [P, I, ctypes.POINTER(I)]),
         "ppg_build_poly": (I, [P, I, I, P, U64, ctypes.POINTER(I)]),
         "ppg_set_poly": (I, [P, I, I, P]),
         "ppg_get_poly": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), P, I, ctypes.POINTER(D)]),
@@ -198,6 +199,14 @@ def ppg_spmv_format(ctx, request=PPG_SPMV_QUERY):
     """Selects (or with PPG_SPMV_QUERY reports) the sparse format the SpMV kernels read; returns the one in effect."""
     out = ctypes.c_int(0)
     _check(load_library().ppg_spmv_format(ctx, request, ctypes.byref(out)), "ppg_spmv_format")
+    return out.value
+
+
+def ppg_chain_fusion(ctx, request=-1):
+    """Turns pairing of the p(A) chain's links on (1) or off (0), or queries it (-1); returns whether
+    float32 chains of this matrix are paired."""
+    out = ctypes.c_int(0)
+    _check(load_library().ppg_chain_fusion(ctx, request, ctypes.byref(out)), "ppg_chain_fusion")
     return out.value
 
 
@@ -373,6 +382,9 @@ class Solver:
 
     def spmv_format(self, request=PPG_SPMV_QUERY):
         return ppg_spmv_format(self.ctx, request)
+
+    def chain_fusion(self, request=-1):
+        return ppg_chain_fusion(self.ctx, request)
 
     def build_poly(self, degree, basis=PPG_BASIS_ROOTS, v0=None, seed=2):
         self._workspace(1, max(degree, 30) if degree < 0 else degree)

@@ -62,6 +62,8 @@ constexpr size_t kCycleHeader = offsetof(Cycle, sigma);
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
+constexpr int kMaxRounds = 4096;  // rounds of the two-step kernel's persistent grid
+
 }  // namespace
 
 struct ppg_ctx {
@@ -80,6 +82,8 @@ struct ppg_ctx {
     double *d_svals64 = nullptr;
     float *d_svals32 = nullptr;
     int sell_auto = 0;           // the format the automatic choice picked
+    int *d_rounds = nullptr;     // two-step chain kernel: kMaxRounds round counters, a ticket, 8 diagnostics
+    int fuse = 0;                // pair consecutive links of the p(A) chain into one launch (measured slower)
     long long ld = 0;  // padded vector length
 
     // polynomial (host copy; coefficients enter kernels as launch arguments)
@@ -288,21 +292,97 @@ double spmv_bytes(const DevMatrix &A, int prec, const SpmvEpi &e)
     return b + (double)A.n * es * (distinct + writes);
 }
 
+// The two-step chain kernel applies to the row-block CSR kernel when the matrix bandwidth spans at
+// most as many tiles as its persistent grid has CTAs (and the rounds fit the counters).
+bool chain_pairs(const DevMatrix &A, int prec, bool have_counters)
+{
+    if (!have_counters || A.format != kFmtCsr || A.n <= 0) return false;
+    const long long R = A.rows_per_tile;
+    const long long ntiles = (A.n + R - 1) / R;
+    long long grid = prec == kF64 ? A.spmv2_blocks64 : A.spmv2_blocks32;
+    if (grid > ntiles) grid = ntiles;
+    const long long halo = ((long long)A.bw + R - 1) / R;
+    return grid > 0 && halo <= grid && (ntiles + grid - 1) / grid <= kMaxRounds;
+}
+
 struct Exec {
     ppg_ctx *c;
     const DevMatrix *A;
     int prec;
     cudaStream_t s;
 
-    ppg_status spmv(const SpmvEpi &e, int check)
+    // Links of a p(A) chain are issued through spmv(); inside a chain (depth > 0) each link is held
+    // back one call so that two consecutive links can share one launch (launch_spmv2).
+    int chain_depth = 0;
+    bool has_pending = false;
+    SpmvEpi pending;
+    int pending_check = 0;
+
+    ppg_status launch_one(const SpmvEpi &e, int check)
     {
         c->launches++;
         PPG_CK(launch_spmv(*A, prec, e, c->st, check, s));
         prof_add(c, spmv_bytes(*A, prec, e), 0.0);
         return PPG_OK;
     }
+    // e2 consumes an output of e1 by gather and writes neither of its own gathered inputs, and the
+    // matrix allows pairing (chain_pairs)
+    bool can_pair(const SpmvEpi &e1, const SpmvEpi &e2) const
+    {
+        if (!c->fuse || !chain_pairs(*A, prec, c->d_rounds != nullptr)) return false;
+        auto is_out = [&](const VecRef &v) {
+            return v.base && ((e1.out0.base && same_vec(v, e1.out0)) || (e1.out1.base && same_vec(v, e1.out1)));
+        };
+        if (!is_out(e2.x) || (e2.x2.base && !is_out(e2.x2))) return false;
+        for (const VecRef *o : {&e2.out0, &e2.out1})
+            if (o->base && (same_vec(*o, e2.x) || (e2.x2.base && same_vec(*o, e2.x2)))) return false;
+        return true;
+    }
+    ppg_status spmv(const SpmvEpi &e, int check)
+    {
+        if (has_pending) {
+            has_pending = false;
+            if (pending_check == check && can_pair(pending, e)) {
+                const cudaError_t err = launch_spmv2(*A, prec, pending, e, c->st, check, c->d_rounds,
+                                                     reinterpret_cast<unsigned int *>(c->d_rounds + kMaxRounds),
+                                                     c->d_rounds + kMaxRounds + 8, s);
+                if (err == cudaSuccess) {
+                    c->launches++;
+                    const double mat = spmv_bytes(*A, prec, epi_none());  // the matrix, read once for both
+                    prof_add(c, spmv_bytes(*A, prec, pending) + spmv_bytes(*A, prec, e) - mat, 0.0);
+                    return PPG_OK;
+                }
+                // the grid cannot be resident at once (or the launch is refused): one link per launch
+                cudaGetLastError();
+                c->fuse = 0;
+                PPG_TRY(launch_one(pending, pending_check));
+                return launch_one(e, check);
+            }
+            PPG_TRY(launch_one(pending, check == pending_check ? check : pending_check));
+        }
+        if (chain_depth > 0 && c->fuse) {
+            pending = e;
+            pending_check = check;
+            has_pending = true;
+            return PPG_OK;
+        }
+        return launch_one(e, check);
+    }
+    ppg_status flush()
+    {
+        if (!has_pending) return PPG_OK;
+        has_pending = false;
+        return launch_one(pending, pending_check);
+    }
+    void chain_begin() { ++chain_depth; }
+    ppg_status chain_end()
+    {
+        if (--chain_depth == 0) return flush();
+        return PPG_OK;
+    }
     ppg_status axpy(const SpmvEpi &e, int check)
     {
+        PPG_TRY(flush());
         c->launches++;
         PPG_CK(launch_axpy(A->n, prec, e, c->st, check, s));
         return PPG_OK;
@@ -320,6 +400,13 @@ struct Exec {
     };
     ppg_status poly_apply(VecRef src, const double *sig, VecRef dst, char *const tmp[3], int check,
                           Deferred *defer = nullptr)
+    {
+        chain_begin();
+        PPG_TRY(poly_apply_links(src, sig, dst, tmp, check, defer));
+        return chain_end();
+    }
+    ppg_status poly_apply_links(VecRef src, const double *sig, VecRef dst, char *const tmp[3], int check,
+                                Deferred *defer)
     {
         if (!c->has_poly) {
             SpmvEpi e = epi_none();
@@ -434,6 +521,12 @@ struct Exec {
 
     // w = A p(A) (scale * src), fusing the scalar cases into one SpMV.
     ppg_status poly_then_A(VecRef src, const double *sig, VecRef w, char *const tmp[4], int check)
+    {
+        chain_begin();
+        PPG_TRY(poly_then_A_links(src, sig, w, tmp, check));
+        return chain_end();
+    }
+    ppg_status poly_then_A_links(VecRef src, const double *sig, VecRef w, char *const tmp[4], int check)
     {
         if (!c->has_poly || (c->basis == PPG_BASIS_POWER && c->degree == 0)) {
             const double s0 = c->has_poly ? c->coef[0] : 1.0;
@@ -556,7 +649,16 @@ ppg_status read_state(ppg_ctx *c)
 {
     PPG_CK(cudaMemcpyAsync(c->h_st, c->st, kCycleHeader, cudaMemcpyDeviceToHost, c->stream));
     PPG_CK(cudaStreamSynchronize(c->stream));
-    if (c->h_st->error & kErrTimeout) return fail(PPG_ERR_TIMEOUT, "a bounded device wait expired");
+    if (c->h_st->error & kErrTimeout) {
+        int d[8] = {0};
+        if (c->d_rounds) cudaMemcpy(d, c->d_rounds + kMaxRounds + 8, sizeof d, cudaMemcpyDeviceToHost);
+        if (d[0])
+            return fail(PPG_ERR_TIMEOUT,
+                        "a bounded device wait expired (two-step SpMV: %s wait, CTA %d of %d, iteration %d, round %d, "
+                        "have %d need %d)",
+                        d[0] == 1 ? "stage" : "round", d[1], d[6], d[2], d[3], d[4], d[5]);
+        return fail(PPG_ERR_TIMEOUT, "a bounded device wait expired");
+    }
     return PPG_OK;
 }
 
@@ -995,15 +1097,19 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
     // of its row (all banded / stencil matrices of moderate bandwidth)
     PPG_CK(cudaMalloc(&c->d_coloff, sizeof(short) * (nnz + 16)));
     PPG_CK(cudaMemsetAsync(c->d_coloff, 0, sizeof(short) * (nnz + 16), c->stream));
-    PPG_CK(cudaMemsetAsync(c->d_info, 0, sizeof(int), c->stream));
+    PPG_CK(cudaMemsetAsync(c->d_info, 0, 2 * sizeof(int), c->stream));
     if (nnz > 0) PPG_CK(launch_make_coloff((int)n, c->d_rowptr, c->d_colidx, c->d_coloff, c->d_info, c->stream));
-    PPG_CK(cudaMemcpyAsync(c->h_info, c->d_info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PPG_CK(cudaMemcpyAsync(c->h_info, c->d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     PPG_CK(cudaStreamSynchronize(c->stream));
     if (c->h_info[0] != 0) {
         cudaFree(c->d_coloff);
         c->d_coloff = nullptr;
     }
     c->A.coloff = c->d_coloff;
+    c->A.bw = c->h_info[1];
+    // round counters and ticket of the two-step chain kernel
+    PPG_CK(cudaMalloc(&c->d_rounds, sizeof(int) * (kMaxRounds + 16)));
+    PPG_CK(cudaMemsetAsync(c->d_rounds, 0, sizeof(int) * (kMaxRounds + 16), c->stream));
 
     // tiling: rows per tile from the mean row length, staging capacity from the largest tile
     const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
@@ -1084,6 +1190,7 @@ void ppg_destroy(ppg_ctx *c)
     cudaFree(c->d_coloff);
     cudaFree(c->d_vals);
     cudaFree(c->d_vals32);
+    cudaFree(c->d_rounds);
     cudaFree(c->d_sptr);
     cudaFree(c->d_soff);
     cudaFree(c->d_scol);
@@ -1118,6 +1225,16 @@ ppg_status ppg_spmv_format(ppg_ctx *c, int request, int *in_effect)
     default: return fail(PPG_ERR_INVALID_ARG, "unknown SpMV format request %d", request);
     }
     if (in_effect) *in_effect = c->A.format == kFmtSell ? PPG_SPMV_SELL : PPG_SPMV_CSR;
+    return PPG_OK;
+}
+
+ppg_status ppg_chain_fusion(ppg_ctx *c, int request, int *in_effect)
+{
+    g_last_error.clear();
+    if (!c) return fail(PPG_ERR_INVALID_ARG, "null context");
+    if (request != -1 && request != 0 && request != 1) return fail(PPG_ERR_INVALID_ARG, "request must be -1, 0 or 1");
+    if (request >= 0) c->fuse = request;
+    if (in_effect) *in_effect = (c->fuse && chain_pairs(c->A, kF32, c->d_rounds != nullptr)) ? 1 : 0;
     return PPG_OK;
 }
 

@@ -32,6 +32,24 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// A launch whose CTAs wait on one another: cooperative, so that the whole grid is resident at
+// once (the launch fails rather than starting part of the grid).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_coop(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // The context's device copy of the CSR matrix and the tiling chosen for it.
 struct DevMatrix {
     int n;
@@ -48,6 +66,9 @@ struct DevMatrix {
     int resid_blocks;     // grid of the persistent residual / norm kernels
     int spmv_blocks64;    // persistent SpMV grids
     int spmv_blocks32;
+    int spmv2_blocks64;   // persistent grids of the two-step kernel
+    int spmv2_blocks32;
+    int bw;               // bandwidth max |col - row|
     // sliced ELL copy (slices of 32 rows; entry k of row 32 s + l at sptr[s] + 32 k + l, slices padded
     // to their longest row with a sentinel index), used by the SpMV when format == kFmtSell
     int format;           // kFmtCsr or kFmtSell
@@ -173,6 +194,13 @@ cudaError_t spmv_configure(DevMatrix *A);
 // fills the sliced ELL copy (entries and padding; sptr given) from the CSR arrays
 cudaError_t launch_sell_fill(int n, int nslices, const int *rowptr, const int *colidx, const double *vals,
                              const int *sptr, short *soff, int *scol, double *svals, cudaStream_t s);
+// Two consecutive links of a chain in one launch: e2.x (and e2.x2) are outputs of e1, and e2
+// writes none of its own inputs x, x2.  Requires the bandwidth to span at most as many tiles
+// as the launch has CTAs (spmv2_tiles_ok); round_done (zero on entry, left zero) holds one int
+// per round of the persistent grid, ticket one unsigned int (zero), diag 8 ints (zero) where a
+// wait that gives up records itself.
+cudaError_t launch_spmv2(const DevMatrix &A, int prec, const SpmvEpi &e1, const SpmvEpi &e2, Cycle *st, int check_done,
+                         int *round_done, unsigned int *ticket, int *diag, cudaStream_t s);
 cudaError_t launch_make_coloff(int n, const int *rowptr, const int *colidx, short *out, int *flag, cudaStream_t s);
 int spmv_cap_max();
 int spmv_rows_per_thread();

@@ -116,6 +116,184 @@ __device__ __forceinline__ int col_of(IDX c, int r)
         return (int)c;
 }
 
+// An epilogue with its scalars and vector addresses resolved for this launch.
+template <typename T>
+struct EpiRes {
+    const T *x, *x2;
+    T *o0, *o1;
+    const T *u0, *w0, *u1, *w1;
+    T ca0, cb0, cc0, ca1, cb1, cc1, c2;
+};
+
+// Resolves e for the eight consumer warps (threads 0..6 evaluate the scalars into s_coef, then
+// the consumers meet at named barrier 1).
+template <typename T>
+__device__ EpiRes<T> resolve_epi(const SpmvEpi &e, const Cycle *st, double *s_coef, int tid)
+{
+    switch (tid) {
+    case 0: s_coef[0] = resolve(e.a0, st); break;
+    case 1: s_coef[1] = resolve(e.b0, st); break;
+    case 2: s_coef[2] = resolve(e.c0, st); break;
+    case 3: s_coef[3] = resolve(e.a1, st); break;
+    case 4: s_coef[4] = resolve(e.b1, st); break;
+    case 5: s_coef[5] = resolve(e.c1, st); break;
+    case 6: s_coef[6] = resolve(e.s2, st); break;
+    default: break;
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(kSpmvConsumerWarps * 32) : "memory");
+    EpiRes<T> E;
+    E.x = resolve_ptr<T>(e.x, st);
+    E.x2 = resolve_ptr<T>(e.x2, st);
+    E.o0 = resolve_ptr<T>(e.out0, st);
+    E.u0 = resolve_ptr<T>(e.u0, st);
+    E.w0 = resolve_ptr<T>(e.w0, st);
+    E.o1 = resolve_ptr<T>(e.out1, st);
+    E.u1 = resolve_ptr<T>(e.u1, st);
+    E.w1 = resolve_ptr<T>(e.w1, st);
+    E.ca0 = (T)s_coef[0];
+    E.cb0 = (T)s_coef[1];
+    E.cc0 = (T)s_coef[2];
+    E.ca1 = (T)s_coef[3];
+    E.cb1 = (T)s_coef[4];
+    E.cc1 = (T)s_coef[5];
+    E.c2 = (T)s_coef[6];
+    return E;
+}
+
+// x gathers: through the read-only path, or (data written earlier in the same launch by other
+// CTAs) with plain loads; a 128-byte line of such a vector is never read before all of it has
+// been written, so no stale copy can sit in this SM's L1
+template <typename T, bool COH>
+__device__ __forceinline__ T gather(const T *p);
+template <>
+__device__ __forceinline__ float gather<float, false>(const float *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ double gather<double, false>(const double *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float gather<float, true>(const float *p)
+{
+    float v;
+    asm volatile("ld.global.ca.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+template <>
+__device__ __forceinline__ double gather<double, true>(const double *p)
+{
+    double v;
+    asm volatile("ld.global.ca.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// One tile of a fused SpMV step, for the calling consumer thread: rows lr + q (256 / G) of the
+// tile whose row pointers, values and column indices the stage at base holds (or, for a tile
+// larger than a stage, whose values and columns are read from global memory).  COH: x and x2
+// were written earlier in the same launch and are gathered with coherent loads.
+template <typename T, typename IDX, bool COH>
+__device__ __forceinline__ void spmv_tile(const unsigned char *base, size_t val_off, size_t col_off, int cap,
+                                          long long tile, int R, int G, int n, const IDX *gcols, const T *gvals,
+                                          const EpiRes<T> &E, int tid)
+{
+    constexpr int VA = 16 / (int)sizeof(T);
+    constexpr int CA = 16 / (int)sizeof(IDX);
+    const int lr = tid / G;  // first row of this lane group; rows lr + q * (256 / G), q < kSpmvRpt
+    const int lg = tid & (G - 1);
+    constexpr int RP = kSpmvRpt;
+    const int rstep = kThreads / G;
+    const int *s_rp = reinterpret_cast<const int *>(base);
+    const T *s_val = reinterpret_cast<const T *>(base + val_off);
+    const IDX *s_col = reinterpret_cast<const IDX *>(base + col_off);
+    const int r0 = (int)(tile * R);
+    const int rows = min(R, n - r0);
+    const int e0 = s_rp[0], e1 = s_rp[rows];
+    const int vs = e0 & ~(VA - 1), ve = (e1 + VA - 1) & ~(VA - 1);
+    const int cs = e0 & ~(CA - 1), ce = (e1 + CA - 1) & ~(CA - 1);
+    const bool staged = (ve - vs) <= cap && (ce - cs) <= cap && e1 > e0;
+    T acc[RP], pu0[RP], pw0[RP], pu1[RP], pw1[RP];
+    int kb[RP], ke[RP], rr[RP];
+    bool ok[RP];
+#pragma unroll
+    for (int q = 0; q < RP; ++q) {
+        const int l = lr + q * rstep;
+        ok[q] = l < rows;
+        rr[q] = r0 + l;
+        kb[q] = ok[q] ? s_rp[l] + lg : 0;
+        ke[q] = ok[q] ? s_rp[l + 1] : 0;
+        acc[q] = pu0[q] = pw0[q] = pu1[q] = pw1[q] = T(0);
+        // epilogue operands first: their loads overlap the gathers below
+        if (lg == 0 && ok[q]) {
+            if (E.u0) pu0[q] = E.u0[rr[q]];
+            if (E.w0) pw0[q] = E.w0[rr[q]];
+            if (E.o1) {
+                if (E.u1) pu1[q] = E.u1[rr[q]];
+                if (E.w1) pw1[q] = E.w1[rr[q]];
+            }
+        }
+    }
+    if (staged) {
+        // all of a lane's gathers (up to 8 per row per batch) are issued before the first FMA
+        bool more = true;
+        while (more) {
+            int qc[RP][8];
+            T xv[RP][8];
+#pragma unroll
+            for (int q = 0; q < RP; ++q)
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int kk = kb[q] + t * G;
+                    qc[q][t] = kk < ke[q] ? col_of<IDX>(s_col[kk - cs], rr[q]) : -1;
+                }
+            if (E.x2 == nullptr) {
+#pragma unroll
+                for (int q = 0; q < RP; ++q)
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) xv[q][t] = qc[q][t] >= 0 ? gather<T, COH>(E.x + qc[q][t]) : T(0);
+            } else {
+#pragma unroll
+                for (int q = 0; q < RP; ++q)
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        xv[q][t] = qc[q][t] >= 0
+                                       ? fma(E.c2, gather<T, COH>(E.x2 + qc[q][t]), gather<T, COH>(E.x + qc[q][t]))
+                                       : T(0);
+            }
+            more = false;
+#pragma unroll
+            for (int q = 0; q < RP; ++q) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (qc[q][t] >= 0) acc[q] = fma(s_val[kb[q] + t * G - vs], xv[q][t], acc[q]);
+                kb[q] += 8 * G;
+                more = more || kb[q] < ke[q];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < RP; ++q)
+            for (int k = kb[q]; k < ke[q]; k += G) {
+                const int qq = col_of<IDX>(__ldg(gcols + k), rr[q]);
+                const T xv = E.x2 ? fma(E.c2, gather<T, COH>(E.x2 + qq), gather<T, COH>(E.x + qq))
+                                  : gather<T, COH>(E.x + qq);
+                acc[q] = fma(__ldg(gvals + k), xv, acc[q]);
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < RP; ++q) {
+        for (int o = G >> 1; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        if (lg == 0 && ok[q]) {
+            T v = E.ca0 * acc[q];
+            if (E.u0) v = fma(E.cb0, pu0[q], v);
+            if (E.w0) v = fma(E.cc0, pw0[q], v);
+            E.o0[rr[q]] = v;
+            if (E.o1) {
+                T v1 = E.ca1 * acc[q];
+                if (E.u1) v1 = fma(E.cb1, pu1[q], v1);
+                if (E.w1) v1 = fma(E.cc1, pw1[q], v1);
+                E.o1[rr[q]] = v1;
+            }
+        }
+    }
+}
+
 // Persistent, warp-specialised row-block CSR SpMV.  Tiles of R consecutive rows are
 // dealt round-robin to the CTAs.  The producer warp keeps up to three tiles in flight:
 // for each it reads the tile's non-zero range from the row pointers and issues TMA bulk
@@ -343,6 +521,204 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv(Spmv
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
+    }
+}
+
+// ---------------------------------------------------------------- two chain steps in one launch
+
+// A tile's staged matrix data serves two consecutive links of the p(A) chain (Section II,
+// Eq. 2): y1 = step 1 (A x), y2 = step 2 (A y1), where y2's input is an output of step 1.
+// Tiles are dealt round-robin, so round i of the persistent grid covers tiles i G .. i G + G-1.
+// Each CTA runs step 1 on its round-i tile, then step 2 on its round-(i-2) tile from the same
+// (still resident) stage.  Step 2 of a tile gathers step-1 rows up to the matrix bandwidth away;
+// with the bandwidth at most G tiles these lie in rounds i-3 .. i-1, whose completion the CTAs
+// count in round_done (a bounded wait; the last CTA clears the counters).  The CTAs wait on one
+// another, so the kernel is launched cooperatively (the whole grid resident at once).  The rows step 2
+// writes are no longer gathered by any step 1 at that point (rounds up to i-1 are complete and
+// round i gathers only rounds i-1 .. i+1), so step 2 may write into step 1's input vector.
+constexpr int kSpmv2Lag = 2;
+constexpr int kSpmv2Stages = kSpmvStages + kSpmv2Lag;
+
+template <typename T, typename IDX>
+struct Spmv2Args {
+    SpmvArgs<T, IDX> a;  // a.e: the first step
+    SpmvEpi e2;          // the second step (x, x2: outputs of the first)
+    int *round_done;     // per round: CTAs that have finished its first step (zero at launch)
+    unsigned int *ticket;
+    int *diag;           // 8 ints: where a bounded wait gave up (first CTA to time out)
+};
+
+// records a wait that gave up: kind 1 full barrier, 2 round counter; the first CTA wins
+__device__ __forceinline__ void spmv2_diag(int *diag, int kind, long long i, long long r, int have, int need)
+{
+    if (atomicCAS(diag, 0, kind) == 0) {
+        diag[1] = blockIdx.x;
+        diag[2] = (int)i;
+        diag[3] = (int)r;
+        diag[4] = have;
+        diag[5] = need;
+        diag[6] = gridDim.x;
+    }
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename T, typename IDX>
+__global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv2(Spmv2Args<T, IDX> p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kSpmv2Stages];
+    __shared__ __align__(8) uint64_t empty[kSpmv2Stages];
+    __shared__ double s_coef1[7], s_coef2[7];
+    __shared__ int s_fail;
+
+    const SpmvArgs<T, IDX> &a = p.a;
+    Cycle *st = a.st;
+    const int R = a.rows_per_tile;
+    const int G = a.lanes_per_row;
+    const long long ntiles = ((long long)a.n + R - 1) / R;
+    const size_t stage_bytes = spmv_stage_bytes<T, IDX>(a.cap);
+    const size_t val_off = kSpmvRpBytes;
+    const size_t col_off = kSpmvRpBytes + round128((size_t)a.cap * sizeof(T));
+    constexpr int VA = 16 / (int)sizeof(T);
+    constexpr int CA = 16 / (int)sizeof(IDX);
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const long long NG = gridDim.x;
+    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / NG + 1 : 0;
+    const int prefetched = (int)min((long long)kSpmvStages, my_tiles);
+
+    if (tid == 0) {
+        for (int q = 0; q < kSpmv2Stages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kSpmvConsumerWarps);
+        }
+        fence_mbar_init();
+        s_fail = 0;
+    }
+    __syncthreads();
+
+    if (wid == kSpmvConsumerWarps) {
+        // ---------------- producer: as in k_spmv, with stages released after the second step
+        if (lane == 0) {
+            auto bounds = [&](long long t, int &e0, int &e1) {
+                const int r0 = (int)(t * R);
+                e0 = __ldg(a.rowptr + r0);
+                e1 = __ldg(a.rowptr + min(r0 + R, a.n));
+            };
+            int ne0 = 0, ne1 = 0;
+            if (my_tiles > 0) bounds(blockIdx.x, ne0, ne1);
+            int i = 0;
+            for (long long tile = blockIdx.x; tile < ntiles; tile += NG, ++i) {
+                if (i == prefetched) {
+                    pdl_wait();
+                    pdl_trigger();
+                    if ((a.check_done == kSkipIfDone && st->cycle_done) ||
+                        (a.check_done == kSkipIfNoCols && st->k == 0))
+                        break;
+                }
+                const int e0 = ne0, e1 = ne1;
+                if (tile + NG < ntiles) bounds(tile + NG, ne0, ne1);
+                const int s = i % kSpmv2Stages, use = i / kSpmv2Stages;
+                if (use > 0 && !mbar_wait_bounded(&empty[s], (use - 1) & 1, kWaitLimitNs)) {
+                    atomicOr(&st->error, kErrTimeout);
+                    break;
+                }
+                const int r0 = (int)(tile * R);
+                const int rows = min(R, a.n - r0);
+                const int vs = e0 & ~(VA - 1), ve = (e1 + VA - 1) & ~(VA - 1);
+                const int cs = e0 & ~(CA - 1), ce = (e1 + CA - 1) & ~(CA - 1);
+                const bool staged = (ve - vs) <= a.cap && (ce - cs) <= a.cap && e1 > e0;
+                unsigned char *base = smem + s * stage_bytes;
+                const uint32_t rpb = ((uint32_t)(rows + 1) * 4u + 15u) & ~15u;
+                const uint32_t vb = staged ? (uint32_t)(ve - vs) * (uint32_t)sizeof(T) : 0u;
+                const uint32_t cb = staged ? (uint32_t)(ce - cs) * (uint32_t)sizeof(IDX) : 0u;
+                mbar_arrive_expect_tx(&full[s], rpb + vb + cb);
+                bulk_g2s(base, a.rowptr + r0, rpb, &full[s]);
+                if (staged) {
+                    bulk_g2s(base + val_off, a.vals + vs, vb, &full[s]);
+                    bulk_g2s(base + col_off, a.cols + cs, cb, &full[s]);
+                }
+            }
+        }
+        return;
+    }
+
+    pdl_wait();
+    pdl_trigger();
+    if ((a.check_done == kSkipIfDone && st->cycle_done) || (a.check_done == kSkipIfNoCols && st->k == 0)) {
+        for (int q = 0; q < prefetched; ++q) mbar_wait_bounded(&full[q], 0, kWaitLimitNs);
+        return;
+    }
+    const EpiRes<T> E1 = resolve_epi<T>(a.e, st, s_coef1, tid);
+    const EpiRes<T> E2 = resolve_epi<T>(p.e2, st, s_coef2, tid);
+    const long long nrounds = (ntiles + NG - 1) / NG;
+    int loaded = 0;  // stages this CTA's consumers have waited for (all copies issued so far landed)
+    for (long long i = 0; i < my_tiles + kSpmv2Lag; ++i) {
+        if (i < my_tiles) {
+            const int s = (int)(i % kSpmv2Stages);
+            if (!mbar_wait_bounded(&full[s], (int)(i / kSpmv2Stages) & 1, kWaitLimitNs)) {
+                if (lane == 0) {
+                    atomicOr(&st->error, kErrTimeout);
+                    spmv2_diag(p.diag, 1, i, i, s, 0);
+                }
+                s_fail = 1;
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(kSpmvConsumerWarps * 32) : "memory");
+            if (s_fail) break;
+            loaded = (int)i + 1;
+            spmv_tile<T, IDX, false>(smem + s * stage_bytes, val_off, col_off, a.cap, blockIdx.x + i * NG, R, G,
+                                     a.n, a.cols, a.vals, E1, tid);
+            // this CTA's part of round i is written: publish it
+            asm volatile("bar.sync 1, %0;" ::"n"(kSpmvConsumerWarps * 32) : "memory");
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(p.round_done + i, 1);
+            }
+        }
+        const long long j = i - kSpmv2Lag;
+        if (j >= 0 && j < my_tiles) {
+            if (tid == 0) {
+                // first-step rows within the bandwidth of round j: rounds j-1 .. j+1 complete
+                const unsigned long long t0 = global_timer_ns();
+                for (long long r = (j > 0 ? j - 1 : 0); r <= j + 1 && r < nrounds && !s_fail; ++r) {
+                    const int need = (int)min(NG, ntiles - r * NG);
+                    for (unsigned int spins = 1; ld_acquire(p.round_done + r) < need; ++spins)
+                        if ((spins & 63u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
+                            atomicOr(&st->error, kErrTimeout);
+                            spmv2_diag(p.diag, 2, i, r, ld_acquire(p.round_done + r), need);
+                            s_fail = 1;
+                            break;
+                        }
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(kSpmvConsumerWarps * 32) : "memory");
+            if (s_fail) break;
+            const int s = (int)(j % kSpmv2Stages);
+            spmv_tile<T, IDX, true>(smem + s * stage_bytes, val_off, col_off, a.cap, blockIdx.x + j * NG, R, G, a.n,
+                                    a.cols, a.vals, E2, tid);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+    }
+    if (s_fail) {
+        // copies the producer issued but no consumer waited for land before the CTA exits
+        for (long long q = loaded; q < my_tiles && q < loaded + kSpmv2Stages; ++q)
+            if (tid == 0) mbar_wait_bounded(&full[q % kSpmv2Stages], (int)(q / kSpmv2Stages) & 1, kWaitLimitNs);
+    }
+    // the last CTA clears the round counters for the next launch
+    asm volatile("bar.sync 1, %0;" ::"n"(kSpmvConsumerWarps * 32) : "memory");
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(p.ticket, 1u) == gridDim.x - 1) {
+            for (long long r = 0; r < nrounds; ++r) p.round_done[r] = 0;
+            __threadfence();
+            *p.ticket = 0u;
+        }
     }
 }
 
@@ -607,6 +983,45 @@ cudaError_t spmv_go(const DevMatrix &A, const T *vals, const IDX *cols, int cap,
                       kSpmvStages * spmv_stage_bytes<T, IDX>(cap), s, a);
 }
 
+// the opt-in shared memory per CTA of this device
+int smem_optin()
+{
+    static int v = 0;
+    if (v == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (v <= 0) v = 48 * 1024;
+    }
+    return v;
+}
+
+// CTAs per SM of the two-step kernel, 0 when its stages do not fit a CTA's shared memory
+template <typename T, typename IDX>
+int spmv2_per_sm(int cap)
+{
+    if (kSpmv2Stages * spmv_stage_bytes<T, IDX>(cap) + 1024 > (size_t)smem_optin()) return 0;
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv2<T, IDX>, kSpmvThreads,
+                                                  kSpmv2Stages * spmv_stage_bytes<T, IDX>(cap));
+    return nb > 0 ? nb : 0;
+}
+
+template <typename T, typename IDX>
+cudaError_t spmv2_go(const DevMatrix &A, const T *vals, const IDX *cols, int cap, int blocks, const SpmvEpi &e1,
+                     const SpmvEpi &e2, Cycle *st, int check_done, int *round_done, unsigned int *ticket, int *diag,
+                     cudaStream_t s)
+{
+    const int R = A.rows_per_tile;
+    const long long ntiles = ((long long)A.n + R - 1) / R;
+    Spmv2Args<T, IDX> p{{A.n, A.rowptr, cols, vals, R, A.lanes_per_row, cap, st, check_done, e1},
+                        e2, round_done, ticket, diag};
+    long long g = blocks;
+    if (g > ntiles) g = ntiles;
+    return launch_coop(k_spmv2<T, IDX>, dim3((unsigned)g), dim3(kSpmvThreads),
+                       kSpmv2Stages * spmv_stage_bytes<T, IDX>(cap), s, p);
+}
+
 template <typename T, typename IDX>
 cudaError_t sell_go(const DevMatrix &A, const T *vals, const IDX *cols, const SpmvEpi &e, Cycle *st, int check_done,
                     cudaStream_t s)
@@ -630,6 +1045,10 @@ cudaError_t spmv_set_smem()
 {
     cudaError_t e = cudaFuncSetAttribute(k_spmv<T, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kSpmvStages * spmv_stage_bytes<T, IDX>(kSpmvCapMax)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(
+            k_spmv2<T, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)min(kSpmv2Stages * spmv_stage_bytes<T, IDX>(kSpmvCapMax), (size_t)smem_optin() - 1024));
     if (e == cudaSuccess && PPG_SPMV_CARVEOUT >= 0)
         e = cudaFuncSetAttribute(k_spmv<T, IDX>, cudaFuncAttributePreferredSharedMemoryCarveout, PPG_SPMV_CARVEOUT);
     return e;
@@ -654,6 +1073,23 @@ cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *s
     return spmv_go<float, int>(A, A.vals32, A.colidx, A.cap32, A.spmv_blocks32, e, st, check_done, s);
 }
 
+cudaError_t launch_spmv2(const DevMatrix &A, int prec, const SpmvEpi &e1, const SpmvEpi &e2, Cycle *st, int check_done,
+                         int *round_done, unsigned int *ticket, int *diag, cudaStream_t s)
+{
+    if (prec == kF64) {
+        if (A.coloff)
+            return spmv2_go<double, short>(A, A.vals64, A.coloff, A.cap64, A.spmv2_blocks64, e1, e2, st, check_done,
+                                           round_done, ticket, diag, s);
+        return spmv2_go<double, int>(A, A.vals64, A.colidx, A.cap64, A.spmv2_blocks64, e1, e2, st, check_done,
+                                     round_done, ticket, diag, s);
+    }
+    if (A.coloff)
+        return spmv2_go<float, short>(A, A.vals32, A.coloff, A.cap32, A.spmv2_blocks32, e1, e2, st, check_done,
+                                      round_done, ticket, diag, s);
+    return spmv2_go<float, int>(A, A.vals32, A.colidx, A.cap32, A.spmv2_blocks32, e1, e2, st, check_done, round_done,
+                                ticket, diag, s);
+}
+
 // Sets the dynamic shared memory limit (for the largest staging capacity, once) and returns
 // the persistent grid sizes for this matrix's capacities and index format.
 cudaError_t spmv_configure(DevMatrix *A)
@@ -670,24 +1106,32 @@ cudaError_t spmv_configure(DevMatrix *A)
     if (A->coloff) {
         A->spmv_blocks64 = spmv_per_sm<double, short>(A->cap64) * A->num_sms;
         A->spmv_blocks32 = spmv_per_sm<float, short>(A->cap32) * A->num_sms;
+        A->spmv2_blocks64 = spmv2_per_sm<double, short>(A->cap64) * A->num_sms;
+        A->spmv2_blocks32 = spmv2_per_sm<float, short>(A->cap32) * A->num_sms;
     } else {
         A->spmv_blocks64 = spmv_per_sm<double, int>(A->cap64) * A->num_sms;
         A->spmv_blocks32 = spmv_per_sm<float, int>(A->cap32) * A->num_sms;
+        A->spmv2_blocks64 = spmv2_per_sm<double, int>(A->cap64) * A->num_sms;
+        A->spmv2_blocks32 = spmv2_per_sm<float, int>(A->cap32) * A->num_sms;
     }
     return cudaSuccess;
 }
 
-// int16 column offsets (col - row) when every entry is within 32767 of its row; flag = 1 otherwise
+// int16 column offsets (col - row) when every entry is within 32767 of its row; flag[0] = 1
+// otherwise.  flag[1] receives the bandwidth max |col - row|.
 __global__ void k_make_coloff(int n, const int *__restrict__ rowptr, const int *__restrict__ colidx, short *out,
                               int *flag)
 {
     const int stride = gridDim.x * blockDim.x;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        int bw = 0;
         for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
             const int d = colidx[k] - r;
             if (d < -32767 || d > 32767) atomicOr(flag, 1);
             out[k] = (short)d;
+            bw = max(bw, abs(d));
         }
+        if (bw > 0) atomicMax(flag + 1, bw);
     }
 }
 

@@ -580,3 +580,54 @@ def test_full_size_c2_solve_fp64_and_mixed(c2):
     assert r64 <= 1e-8 and r32 <= 1e-8
     d = np.linalg.norm(x64.cpu().numpy() - x32.cpu().numpy()) / np.linalg.norm(x64.cpu().numpy())
     assert d <= 1e-6
+
+
+# ---------------------------------------------------------------- paired chain links
+
+
+@pytest.mark.parametrize("mat", ["c1_2d_64", "3d_7pt_21", "27pt_13", "random_ragged", "wide_band"])
+def test_paired_chain_is_bit_identical(mat):
+    """Two links of the p(A) chain per launch (the matrix staged once for both) give exactly the
+    results of one link per launch: same tiles, same per-row arithmetic."""
+    a = MATRICES[mat]()
+    s = solver_for(a)
+    assert s.chain_fusion(-1) in (0, 1)
+    v0 = T(w.v0(a.n))
+    b = T(w.rhs(a.n))
+    v = T(w.uniform(41, a.n))
+    out = {}
+    for basis, deg in ((ppg.PPG_BASIS_ROOTS, 10), (ppg.PPG_BASIS_POWER, 5)):
+        s.build_poly(deg, basis, v0=v0)
+        for fuse in (1, 0):
+            s.chain_fusion(fuse)
+            res = [s.apply_poly(v).cpu().numpy(), s.apply_poly(v.float()).cpu().numpy()]
+            for prec in (ppg.PPG_F64, ppg.PPG_F32):
+                x, info = s.solve(b, tol=1e-8, restart=30, maxit=400, precision=prec)
+                res += [x.cpu().numpy(), info.stats["iterations"]]
+            out[(basis, fuse)] = res
+        for r1, r0 in zip(out[(basis, 1)], out[(basis, 0)]):
+            np.testing.assert_array_equal(r1, r0)
+
+
+def test_chain_pairing_applies_to_banded_matrices():
+    assert solver_for(w.c1_matrix()).chain_fusion(-1) == 0  # off by default
+    assert solver_for(w.c1_matrix()).chain_fusion(1) == 1
+    assert solver_for(w.convdiff(21, 3, 50.0)).chain_fusion(1) == 1
+    s = solver_for(w.c1_matrix())
+    assert s.chain_fusion(1) == 1 and s.chain_fusion(0) == 0 and s.chain_fusion(1) == 1
+    s.spmv_format(ppg.PPG_SPMV_SELL)
+    assert s.chain_fusion(-1) == 0  # pairing is a property of the row-block kernel
+
+
+def test_full_size_c2_paired_chain_matches_unpaired(c2):
+    a = c2
+    b = T(w.rhs(a.n))
+    s = solver_for(a)
+    assert s.chain_fusion(1) == 1
+    s.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=T(w.v0(a.n)))
+    x1, i1 = s.solve(b, tol=1e-8, restart=50, maxit=3000, precision=ppg.PPG_F32)
+    s.chain_fusion(0)
+    x0, i0 = s.solve(b, tol=1e-8, restart=50, maxit=3000, precision=ppg.PPG_F32)
+    assert i1.status == i0.status == ppg.PPG_OK
+    assert i1.stats["iterations"] == i0.stats["iterations"]
+    np.testing.assert_array_equal(x1.cpu().numpy(), x0.cpu().numpy())
