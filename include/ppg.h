@@ -70,8 +70,11 @@ typedef struct {
     int precision;     /* PPG_F64 (default) or PPG_F32 */
     double inner_rtol; /* PPG_F32 only: a restart cycle also ends when its residual estimate has dropped by
                           this factor (iterative refinement step); <= 0 selects 1e-6 */
-    int use_graph;     /* 1: run each restart cycle as one CUDA graph with device-side loop control;
-                          0: host-enqueued kernels; < 0: library default (graph) */
+    int use_graph;     /* 1: replay each Arnoldi iteration (the p(A) chain and the three Gram-Schmidt
+                          passes) from a CUDA graph, captured once per iteration index and kept while the
+                          polynomial, workspace, precision and storage format stay the same; kernels of a
+                          cycle that has ended still return at once on the device.  0: enqueue the
+                          kernels one by one; < 0: library default (graphs) */
     int profile;       /* 1: time every SpMV and Gram-Schmidt launch with CUDA events and report their
                           device time and algorithmic bytes in ppg_stats (adds a sync per cycle) */
     int reserved[4];

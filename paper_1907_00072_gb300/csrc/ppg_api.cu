@@ -84,6 +84,18 @@ struct ppg_ctx {
     int sell_auto = 0;           // the format the automatic choice picked
     int *d_rounds = nullptr;     // two-step chain kernel: kMaxRounds round counters, a ticket, 8 diagnostics
     int fuse = 0;                // pair consecutive links of the p(A) chain into one launch (measured slower)
+
+    // CUDA graphs of single iterations (ppg_opts.use_graph): one per iteration index, precision and
+    // polynomial presence, valid while the signature captured with it (workspace addresses,
+    // storage format, pairing, the polynomial itself) is unchanged
+    struct IterGraph {
+        cudaGraphExec_t exec = nullptr;
+        long long launches = 0;
+        std::vector<double> sig;
+    };
+    std::vector<IterGraph> igraphs;
+    cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
+    bool graphs_broken = false;         // capture failed once: launch directly from then on
     long long ld = 0;  // padded vector length
 
     // polynomial (host copy; coefficients enter kernels as launch arguments)
@@ -607,6 +619,76 @@ struct Iter {
         return PPG_OK;
     }
 
+    // Iteration j, replayed from a CUDA graph when use_graph is set (captured on first use, and
+    // again whenever the signature of what its launches depend on has changed).
+    bool use_graph = false;
+
+    void signature(std::vector<double> &sig) const
+    {
+        const ppg_ctx *c = x->c;
+        auto put = [&](unsigned long long v) {
+            double d;
+            memcpy(&d, &v, sizeof d);
+            sig.push_back(d);
+        };
+        put((unsigned long long)(uintptr_t)L->basis);
+        put((unsigned long long)(uintptr_t)L->partials);
+        put((unsigned long long)c->ld);
+        put((unsigned long long)((c->A.format << 8) | (c->fuse << 4) | (c->has_poly << 2) | c->basis));
+        put((unsigned long long)c->degree);
+        if (c->has_poly) {
+            sig.insert(sig.end(), c->coef.begin(), c->coef.end());
+            sig.insert(sig.end(), c->roots.begin(), c->roots.end());
+            sig.insert(sig.end(), c->table.begin(), c->table.end());
+        }
+    }
+
+    ppg_status run(int j)
+    {
+        ppg_ctx *c = x->c;
+        if (!use_graph || c->prof || c->graphs_broken || j >= kKmax) return iteration(j);
+        const size_t slot = (size_t)j + (size_t)kKmax * (size_t)(2 * (x->prec == kF64 ? 1 : 0) + (c->has_poly ? 1 : 0));
+        if (c->igraphs.size() < (size_t)(4 * kKmax)) c->igraphs.resize(4 * kKmax);
+        ppg_ctx::IterGraph &g = c->igraphs[slot];
+        std::vector<double> sig;
+        signature(sig);
+        if (!g.exec || g.sig != sig) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                c->graphs_broken = true;
+                return iteration(j);
+            }
+            cudaStream_t keep = x->s;
+            x->s = c->cap_stream;
+            const long long l0 = c->launches;
+            cudaGraph_t graph = nullptr;
+            ppg_status st = PPG_ERR_CUDA;
+            if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                st = iteration(j);
+                if (cudaStreamEndCapture(c->cap_stream, &graph) != cudaSuccess) st = PPG_ERR_CUDA;
+            }
+            x->s = keep;
+            const long long captured = c->launches - l0;  // kernels iteration j enqueued into the graph
+            c->launches = l0;
+            cudaGraphExec_t exec = nullptr;
+            if (st >= 0 && graph && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+            if (!exec) {  // this iteration cannot be captured here: launch directly from now on
+                cudaGetLastError();
+                c->graphs_broken = true;
+                return iteration(j);
+            }
+            g.exec = exec;
+            g.launches = captured;
+            g.sig.swap(sig);
+        }
+        PPG_CK(cudaGraphLaunch(g.exec, x->s));
+        c->launches += g.launches;
+        return PPG_OK;
+    }
+
     // x += p(A) V y with the coefficients the last pass-3 finalisation left in coef.
     ppg_status cycle_end(double *xsol)
     {
@@ -673,7 +755,8 @@ ppg_status run_arnoldi(ppg_ctx *c, const double *v, int steps, const Layout &L, 
     c->launches++;
     PPG_CK(launch_norm_start(c->A.n, kF64, v ? v : (const double *)L.basis, v ? (void *)L.basis : nullptr, 1, c->st,
                              L.partials, c->A.resid_blocks, c->stream));
-    for (int j = 0; j < steps; ++j) PPG_TRY(it.iteration(j));
+    it.use_graph = true;
+    for (int j = 0; j < steps; ++j) PPG_TRY(it.run(j));
     PPG_TRY(read_state(c));
     if (c->h_st->error & kErrNonfinite) return fail(PPG_ERR_NONFINITE, "non-finite value in the Arnoldi run");
     *done = c->h_st->j;
@@ -815,7 +898,7 @@ ppg_status run_cycle(ppg_ctx *c, Iter &it, int restart)
             }
             std::this_thread::yield();
         }
-        PPG_TRY(it.iteration(j));
+        PPG_TRY(it.run(j));
     }
     return PPG_OK;
 }
@@ -842,6 +925,7 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
 
     Exec ex{c, &c->A, prec, c->stream};
     Iter it{&ex, &L, ncols};
+    it.use_graph = !opts || opts->use_graph != 0;
     c->prof = opts && opts->profile;
     c->prof_open = false;
     c->recs.clear();
@@ -1190,6 +1274,9 @@ void ppg_destroy(ppg_ctx *c)
     cudaFree(c->d_coloff);
     cudaFree(c->d_vals);
     cudaFree(c->d_vals32);
+    for (ppg_ctx::IterGraph &g : c->igraphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     cudaFree(c->d_rounds);
     cudaFree(c->d_sptr);
     cudaFree(c->d_soff);

@@ -631,3 +631,26 @@ def test_full_size_c2_paired_chain_matches_unpaired(c2):
     assert i1.status == i0.status == ppg.PPG_OK
     assert i1.stats["iterations"] == i0.stats["iterations"]
     np.testing.assert_array_equal(x1.cpu().numpy(), x0.cpu().numpy())
+
+
+# ---------------------------------------------------------------- iteration graphs
+
+
+@pytest.mark.parametrize("mat", ["c1", "random"])
+def test_graph_replay_is_bit_identical(mat):
+    """Iterations replayed from captured CUDA graphs give exactly the results of launching the
+    kernels one by one, across repeated solves (cached graphs), a change of polynomial (re-capture)
+    and both precisions."""
+    a = ROOT_MATS[mat]()
+    b = T(w.rhs(a.n))
+    v0 = T(w.v0(a.n))
+    s = solver_for(a)
+    for deg, basis in ((10, ppg.PPG_BASIS_ROOTS), (10, ppg.PPG_BASIS_ROOTS), (5, ppg.PPG_BASIS_POWER),
+                       (3, ppg.PPG_BASIS_ROOTS)):
+        s.build_poly(deg, basis, v0=v0)
+        for prec in (ppg.PPG_F64, ppg.PPG_F32):
+            xg, ig = s.solve(b, tol=1e-8, restart=30, maxit=500, precision=prec, use_graph=1)
+            xd, idd = s.solve(b, tol=1e-8, restart=30, maxit=500, precision=prec, use_graph=0)
+            assert ig.status == idd.status == ppg.PPG_OK
+            assert ig.stats["iterations"] == idd.stats["iterations"]
+            np.testing.assert_array_equal(xg.cpu().numpy(), xd.cpu().numpy())
