@@ -94,7 +94,10 @@ struct SpmvArgs {
 constexpr int kSpmvConsumerWarps = 8;
 constexpr int kSpmvRpt = PPG_SPMV_RPT;
 constexpr int kSpmvThreads = (kSpmvConsumerWarps + 1) * 32;  // + one producer warp
-constexpr int kSpmvStages = 3;
+#ifndef PPG_SPMV_STAGES
+#define PPG_SPMV_STAGES 3
+#endif
+constexpr int kSpmvStages = PPG_SPMV_STAGES;
 constexpr int kSpmvRpBytes = (((256 * kSpmvRpt + 1) * 4 + 15) / 16 * 16 + 127) / 128 * 128;  // row pointers
 constexpr int kSpmvCapMax = 4096;
 
