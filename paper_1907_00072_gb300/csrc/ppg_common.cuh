@@ -181,6 +181,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 
+// Named barrier `id` over `nthreads` threads that also ORs a predicate across them.
+__device__ __forceinline__ bool bar_any(int id, int nthreads, bool v)
+{
+    unsigned int r;
+    asm volatile(
+        "{ .reg .pred p, q; setp.ne.u32 p, %1, 0; bar.red.or.pred q, %2, %3, p; selp.u32 %0, 1, 0, q; }"
+        : "=r"(r)
+        : "r"((unsigned int)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
 // Programmatic dependent launch.  Kernels of the solve path are launched so that they may
 // start while the previous kernel of the stream drains.  Each waits for its predecessor's
 // completion and memory (pdl_wait) before it reads anything the predecessor may have written,

@@ -234,8 +234,11 @@ __device__ void cta_finish_pass3(Cycle *st, double nsq, double *sh, size_t sh_by
 
 // ---------------------------------------------------------------- the pass kernel
 
+// Threads: eight compute warps (kThreads) and one producer warp that issues the stage copies.
+constexpr int kGsThreads = kThreads + 32;
+
 template <typename T, int KM>
-__global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
+__global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
 {
     using C = GsCfg<T, KM>;
     constexpr int TR = C::TR, TPR = C::TPR, RPT = C::RPT, RPL = C::RPL, CPW = C::CPW;
@@ -248,9 +251,11 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     __shared__ double scratch[33];
     __shared__ int s_last;
     __shared__ int s_int[2];
+    __shared__ int s_timeout;
 
     const int op = a.op;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const bool prod = wid == kThreads / 32;  // the producer warp
     const T *__restrict__ U = (const T *)a.U;
     T *w = (T *)a.w;
     const bool need_w = (op != kGsCombine);
@@ -261,10 +266,11 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     if (tid == 0) {
         for (int q = 0; q < nst; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
+        s_timeout = 0;
     }
     __syncthreads();
 
-    // Stage fills, by the lanes of warp 0.  A stage's barrier completes once lane 0 has arrived
+    // Stage fills, by the lanes of the producer warp.  A stage's barrier completes once lane 0 has arrived
     // (with the w copy) and all bytes have landed, so the basis columns may be requested earlier.
     auto issue_cols = [&](long long tile, int stage, int kc) {
         T *sU = stage0 + stage * SS;
@@ -289,7 +295,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     // takes w early: the SpMV wrote it two launches back and pass 1 only reads it.
     const bool early = !a.kcols_from_k;
     const bool early_w = early && op == kGsUpdDot;
-    if (early && wid == 0) {
+    if (early && prod) {
         for (int q = 0; q < nst - 1; ++q)
             if (tile_of(q) < a.ntiles) {
                 issue_cols(tile_of(q), q, a.kstage);
@@ -306,7 +312,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     if (skip || bad) {
         if (bad && tid == 0 && blockIdx.x == 0) atomicOr(&st->error, kErrTimeout);
         if (early) {  // the copies already requested land before the CTA's shared memory is released
-            if (wid == 0 && lane == 0 && !early_w)
+            if (prod && lane == 0 && !early_w)
                 for (int q = 0; q < nst - 1; ++q)
                     if (tile_of(q) < a.ntiles) mbar_arrive(&bars[q]);
             if (tid == 0)
@@ -320,7 +326,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
 
     // prologue: the first nst - 1 tiles (their remaining copies); tile it + nst - 1 is issued at
     // the start of iteration it into the stage freed by iteration it - 1
-    if (wid == 0) {
+    if (prod) {
         for (int q = 0; q < nst - 1; ++q)
             if (tile_of(q) < a.ntiles) {
                 if (!early) issue_cols(tile_of(q), q, k);
@@ -335,14 +341,27 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     int it = 0;
     for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
         const int stage = it % nst;
-        if (wid == 0) {
+        if (prod) {
+            // the producer refills the stage the previous iteration released, then meets the
+            // compute warps at the end-of-tile barrier
             const long long nt = tile + (long long)(nst - 1) * gridDim.x;
             if (nt < a.ntiles) {
                 issue_cols(nt, (it + nst - 1) % nst, k);
                 issue_w(nt, (it + nst - 1) % nst);
             }
+            __syncthreads();
+            if (s_timeout) {
+                timed_out = true;
+                break;
+            }
+            continue;
         }
-        if (!mbar_wait_bounded(&bars[stage], (it / nst) & 1, kWaitLimitNs)) {
+        // every compute thread waits for the stage; they agree on the outcome before any of them
+        // enters a barrier the others might not reach
+        const bool filled = mbar_wait_bounded(&bars[stage], (it / nst) & 1, kWaitLimitNs);
+        if (bar_any(1, kThreads, !filled)) {  // the stage never filled: skip its work
+            if (tid == 0) s_timeout = 1;
+            __syncthreads();
             timed_out = true;
             break;
         }
@@ -373,13 +392,13 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
                         if (op == kGsUpdNorm) nrm.add(wn * wn);
                     }
                 }
-                __syncthreads();
+                asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");  // compute warps only
             } else {
                 const int row = tid % TR, q = tid / TR;
                 T part = T(0);
                 for (int c = q; c < k; c += TPR) part = fma(sU[c * TR + row], s_coef[c], part);
                 s_part[q][row] = part;
-                __syncthreads();
+                asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
                 if (tid < TR) {
                     T sum = s_part[0][row];
 #pragma unroll
@@ -393,7 +412,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
                         if (op == kGsUpdNorm) nrm.add(wn * wn);
                     }
                 }
-                __syncthreads();
+                asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
             }
             dotvec = s_wn;
         } else {
@@ -419,6 +438,10 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
             }
         }
         __syncthreads();  // every thread is done with this stage before it is refilled
+        if (s_timeout) {
+            timed_out = true;
+            break;
+        }
     }
     if (timed_out) {
         if (tid == 0) atomicOr(&st->error, kErrTimeout);
@@ -428,7 +451,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     }
 
     // per-CTA partial sums
-    if (op == kGsDot || op == kGsUpdDot) {
+    if ((op == kGsDot || op == kGsUpdDot) && !prod) {
 #pragma unroll
         for (int i = 0; i < CPW; ++i) {
             const int c = wid + 8 * i;
@@ -445,7 +468,7 @@ __global__ void __launch_bounds__(kThreads) k_gs(GsArgs a, Cycle *st)
     if (op == kGsCombine) return;
 
     if (last_block_done(&st->ticket[2 + op], &s_last)) {
-        if (op != kGsUpdNorm) {
+        if (op != kGsUpdNorm && !prod) {
             for (int c = wid; c < k; c += 8) {
                 const double v = reduce_partials(a.partials, a.nblk, c);
                 if (lane == 0) s_red[c] = v;
@@ -490,13 +513,13 @@ struct GsInst {
         a.nstages = nst;
         const size_t smem = (size_t)nst * stage_bytes;
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gs<T, KM>, kThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gs<T, KM>, kGsThreads, smem);
         if (per < 1) per = 1;
         a.ntiles = ld / TR;
         long long g = (long long)per * num_sms;
         if (g > a.ntiles) g = a.ntiles;
         a.nblk = (int)(g > 0 ? g : 1);
-        return launch_pdl(k_gs<T, KM>, dim3(a.nblk), dim3(kThreads), smem, s, a, st);
+        return launch_pdl(k_gs<T, KM>, dim3(a.nblk), dim3(kGsThreads), smem, s, a, st);
     }
 };
 
