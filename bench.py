@@ -45,7 +45,7 @@ def workload_name(N, nnz=None):
 # DRAM traffic of one k_spmv<float, short> launch (a root step of the p(A) chain, C2 matrix) from the ncu
 # capture summarised in profiles/k_spmv_c2_128cubed.md, and the kernel source it was taken with: when the
 # source changes, the number no longer describes the kernel and the bench reports null.
-SPMV_TRAFFIC = {"src_sha256_16": "4c6c9bfc5084f604", "dram_bytes": 112686592 + 6483200,
+SPMV_TRAFFIC = {"src_sha256_16": "d4a35ed5402e2ff4", "dram_bytes": 112688128 + 6292992,
                 "algorithmic_bytes": 112656384 + 16777216,
                 "launch": "k_spmv<float, short> root step (gather P; write Y and P'), ncu --set full, cold caches"}
 
