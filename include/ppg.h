@@ -71,9 +71,10 @@ typedef struct {
     double inner_rtol; /* PPG_F32 only: a restart cycle also ends when its residual estimate has dropped by
                           this factor (iterative refinement step); <= 0 selects 1e-6 */
     int use_graph;     /* 1: replay each Arnoldi iteration (the p(A) chain and the three Gram-Schmidt
-                          passes) from a CUDA graph, captured once per iteration index and kept while the
-                          polynomial, workspace, precision and storage format stay the same; kernels of a
-                          cycle that has ended still return at once on the device.  0: enqueue the
+                          passes) from a CUDA graph, captured the second time an iteration index comes
+                          round with the same polynomial, workspace, precision and storage format (the
+                          first time it launches directly) and kept while those stay the same; kernels of
+                          a cycle that has ended still return at once on the device.  0: enqueue the
                           kernels one by one; < 0: library default (graphs) */
     int profile;       /* 1: time every SpMV and Gram-Schmidt launch with CUDA events and report their
                           device time and algorithmic bytes in ppg_stats (adds a sync per cycle) */

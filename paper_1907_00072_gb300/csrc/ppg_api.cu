@@ -655,6 +655,11 @@ struct Iter {
         if (!g.exec || g.sig != sig) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
+            // capture only once the same iteration comes round again: a one-off solve launches directly
+            if (g.sig != sig) {
+                g.sig.swap(sig);
+                return iteration(j);
+            }
             if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
                 cudaGetLastError();
                 c->graphs_broken = true;
