@@ -205,6 +205,8 @@ def main():
                     help="for ncu: build the polynomial and run --harness-iters iterations of one solve, print no "
                          "benchmark line")
     ap.add_argument("--harness-iters", type=int, default=20)
+    ap.add_argument("--spmv-format", default="auto", choices=["auto", "csr", "sell", "staged"],
+                    help="sparse format of the SpMV kernels (ppg_spmv_format)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"],
                     help="c2 (default): the benchmark line; c1/c3/c4/c5: the other configurations, one JSON line each")
     args = ap.parse_args()
@@ -230,6 +232,8 @@ def main():
     v0_h = w.v0(a.n)
     T = lambda x, dt=torch.float64: torch.as_tensor(x, dtype=dt, device=dev)  # noqa: E731
     s = ppg.Solver(T(a.rowptr, torch.int32), T(a.colidx, torch.int32), T(a.vals))
+    s.spmv_format({"auto": ppg.PPG_SPMV_AUTO, "csr": ppg.PPG_SPMV_CSR, "sell": ppg.PPG_SPMV_SELL,
+                   "staged": ppg.PPG_SPMV_STAGED}[args.spmv_format])
     b = T(b_h)
     v0 = T(v0_h)
     prec = ppg.PPG_F32 if args.precision == "f32" else ppg.PPG_F64

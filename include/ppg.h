@@ -138,19 +138,24 @@ ppg_status ppg_set_workspace(ppg_ctx *ctx, void *ws, size_t bytes);
 ppg_status ppg_spmv(ppg_ctx *ctx, const void *x, void *y, int precision);
 
 /* Sparse storage the SpMV kernels read.  The paper stores A in CSR (Epetra, Section II); this library
- * keeps the CSR arrays and, at ppg_create, also a sliced ELL copy: slices of 32 consecutive rows, each
- * padded to its longest row and stored entry index by entry index, so one warp reads a slice with
- * coalesced loads.  PPG_SPMV_AUTO selects the row-block CSR kernel (its TMA-staged tiles measured
- * faster than the sliced kernel on every matrix tried); PPG_SPMV_CSR and PPG_SPMV_SELL force one.
- * Every result is the same sum in another order.  request = PPG_SPMV_QUERY changes nothing; *in_effect (host, may be NULL)
- * receives the format now used (PPG_SPMV_CSR or PPG_SPMV_SELL).
- * Errors: PPG_ERR_INVALID_ARG (unknown request, or PPG_SPMV_SELL when the padded copy would exceed
- * 2^31 entries and was not built). */
+ * keeps the CSR arrays and, at ppg_create, also
+ *   - a sliced ELL copy: slices of 32 consecutive rows, each padded to its longest row and stored entry
+ *     index by entry index, so one warp reads a slice with coalesced loads (PPG_SPMV_SELL);
+ *   - for each 256-row tile, up to four contiguous ranges of x covering every column the tile's rows
+ *     reference (banded matrices): with PPG_SPMV_STAGED the float32 row-block kernel copies those
+ *     ranges and the tile's rows of the update operands into shared memory along with the matrix
+ *     tile, so that its x gathers read shared memory (available when 90 % of the tiles are covered).
+ * PPG_SPMV_AUTO selects the row-block CSR kernel; PPG_SPMV_CSR, PPG_SPMV_SELL and PPG_SPMV_STAGED force
+ * one (STAGED applies to float32 links without a second gathered input; others run as CSR).  Every
+ * result is the same sum; CSR and STAGED give identical bits.  request = PPG_SPMV_QUERY changes
+ * nothing; *in_effect (host, may be NULL) receives the format now used.
+ * Errors: PPG_ERR_INVALID_ARG (unknown request, or a format whose copy was not built). */
 enum {
     PPG_SPMV_QUERY = -1,
     PPG_SPMV_AUTO = 0,
     PPG_SPMV_CSR = 1,
-    PPG_SPMV_SELL = 2
+    PPG_SPMV_SELL = 2,
+    PPG_SPMV_STAGED = 3
 };
 ppg_status ppg_spmv_format(ppg_ctx *ctx, int request, int *in_effect);
 

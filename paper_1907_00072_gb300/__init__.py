@@ -40,6 +40,7 @@ PPG_SPMV_QUERY = -1
 PPG_SPMV_AUTO = 0
 PPG_SPMV_CSR = 1
 PPG_SPMV_SELL = 2
+PPG_SPMV_STAGED = 3
 
 # every symbol include/ppg.h declares
 EXPORTED = (

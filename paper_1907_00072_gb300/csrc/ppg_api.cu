@@ -83,6 +83,8 @@ struct ppg_ctx {
     float *d_svals32 = nullptr;
     int sell_auto = 0;           // the format the automatic choice picked
     int *d_rounds = nullptr;     // two-step chain kernel: kMaxRounds round counters, a ticket, 8 diagnostics
+    int *d_twin = nullptr;       // x windows per tile (DevMatrix::twin)
+    short *d_lidx = nullptr;     // window-buffer index per entry (DevMatrix::lidx)
     int fuse = 0;                // pair consecutive links of the p(A) chain into one launch (measured slower)
 
     // CUDA graphs of single iterations (ppg_opts.use_graph): one per iteration index, precision and
@@ -1221,6 +1223,69 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
     c->A.lanes_per_row = G;
     c->A.cap64 = (int)std::max<long long>(cap, 64);
     c->A.cap32 = (int)std::max<long long>(cap, 64);
+
+    // x windows per tile for the staged kernel: the tile's sorted distinct columns are grouped into
+    // ranges (columns closer than kXGap share one), each widened to 16-byte boundaries and kept
+    // inside [0, n rounded down to 4); a tile needing more than kXWin ranges or kXCap entries keeps
+    // global gathers (lengths 0)
+    if (nnz > 0 && R <= 256) {
+        std::vector<int> hcol(nnz);
+        PPG_CK(cudaMemcpy(hcol.data(), c->d_colidx, sizeof(int) * nnz, cudaMemcpyDeviceToHost));
+        const long long ntiles = (n + R - 1) / R;
+        const long long n4 = n & ~3LL;
+        std::vector<int> desc(ntiles * 2 * kXWin, 0);
+        std::vector<short> lidx(nnz + 16, 0);  // per entry: its index in the tile's window buffer
+        std::vector<int> cols;
+        long long windowed = 0;
+        for (long long t = 0; t < ntiles; ++t) {
+            const long long r0 = t * R, r1 = std::min<long long>(n, r0 + R);
+            cols.assign(hcol.begin() + hrp[r0], hcol.begin() + hrp[r1]);
+            if (cols.empty()) continue;
+            std::sort(cols.begin(), cols.end());
+            int lo[kXWin], hi[kXWin], nw = 0;
+            bool ok = true;
+            long long lw = cols[0], hw = cols[0];
+            for (size_t q = 1; q <= cols.size() && ok; ++q) {
+                if (q < cols.size() && cols[q] <= hw + kXGap) {
+                    hw = std::max<long long>(hw, cols[q]);
+                    continue;
+                }
+                const long long a = lw & ~3LL, b = (hw + 4) & ~3LL;  // [a, b) covers [lw, hw]
+                if (nw == kXWin || a < 0 || b > n4) ok = false;
+                else {
+                    lo[nw] = (int)a;
+                    hi[nw] = (int)b;
+                    ++nw;
+                }
+                if (q < cols.size()) lw = hw = cols[q];
+            }
+            long long total = 0;
+            for (int w = 0; w < nw; ++w) total += hi[w] - lo[w];
+            if (!ok || total > kXCap) continue;
+            int off[kXWin];
+            for (int w = 0, o = 0; w < nw; ++w) {
+                desc[t * 2 * kXWin + w] = lo[w];
+                desc[t * 2 * kXWin + kXWin + w] = hi[w] - lo[w];
+                off[w] = o;
+                o += hi[w] - lo[w];
+            }
+            for (long long k = hrp[r0]; k < hrp[r1]; ++k) {
+                const int col = hcol[k];
+                int w = 0;
+                while (w + 1 < nw && col >= lo[w + 1]) ++w;
+                lidx[k] = (short)(off[w] + col - lo[w]);
+            }
+            ++windowed;
+        }
+        if (windowed * 10 >= ntiles * 9) {  // worth a kernel of its own when nearly every tile is covered
+            PPG_CK(cudaMalloc(&c->d_twin, sizeof(int) * desc.size()));
+            PPG_CK(cudaMemcpy(c->d_twin, desc.data(), sizeof(int) * desc.size(), cudaMemcpyHostToDevice));
+            PPG_CK(cudaMalloc(&c->d_lidx, sizeof(short) * lidx.size()));
+            PPG_CK(cudaMemcpy(c->d_lidx, lidx.data(), sizeof(short) * lidx.size(), cudaMemcpyHostToDevice));
+            c->A.twin = c->d_twin;
+            c->A.lidx = c->d_lidx;
+        }
+    }
     PPG_CK(spmv_configure(&c->A));
 
     // sliced ELL copy: 32-row slices padded to their longest row (selectable with ppg_spmv_format)
@@ -1283,6 +1348,8 @@ void ppg_destroy(ppg_ctx *c)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     cudaFree(c->d_rounds);
+    cudaFree(c->d_twin);
+    cudaFree(c->d_lidx);
     cudaFree(c->d_sptr);
     cudaFree(c->d_soff);
     cudaFree(c->d_scol);
@@ -1314,9 +1381,14 @@ ppg_status ppg_spmv_format(ppg_ctx *c, int request, int *in_effect)
         if (c->A.nslices == 0) return fail(PPG_ERR_INVALID_ARG, "no sliced ELL copy for this matrix");
         c->A.format = kFmtSell;
         break;
+    case PPG_SPMV_STAGED:
+        if (!c->A.twin) return fail(PPG_ERR_INVALID_ARG, "no x windows for this matrix");
+        c->A.format = kFmtCsrStaged;
+        break;
     default: return fail(PPG_ERR_INVALID_ARG, "unknown SpMV format request %d", request);
     }
-    if (in_effect) *in_effect = c->A.format == kFmtSell ? PPG_SPMV_SELL : PPG_SPMV_CSR;
+    if (in_effect)
+        *in_effect = c->A.format == kFmtSell ? PPG_SPMV_SELL : c->A.format == kFmtCsrStaged ? PPG_SPMV_STAGED : PPG_SPMV_CSR;
     return PPG_OK;
 }
 

@@ -69,6 +69,11 @@ struct DevMatrix {
     int spmv2_blocks64;   // persistent grids of the two-step kernel
     int spmv2_blocks32;
     int bw;               // bandwidth max |col - row|
+    // x windows per tile (float32 staged kernel): kXWin (lo, len) pairs covering every column the
+    // tile's rows reference, or lengths 0 when the tile's columns do not fit kXCap entries
+    const int *twin;      // [ntiles][2 kXWin], or null
+    const short *lidx;    // per entry: index of its column in the tile's concatenated windows
+    int spmvw_blocks32;   // persistent grid of the staged kernel
     // sliced ELL copy (slices of 32 rows; entry k of row 32 s + l at sptr[s] + 32 k + l, slices padded
     // to their longest row with a sentinel index), used by the SpMV when format == kFmtSell
     int format;           // kFmtCsr or kFmtSell
@@ -83,6 +88,10 @@ struct DevMatrix {
 
 constexpr int kFmtCsr = 0;
 constexpr int kFmtSell = 1;
+constexpr int kFmtCsrStaged = 2;  // row-block CSR with the tile's x windows and row operands staged by TMA
+constexpr int kXWin = 4;          // x windows per tile
+constexpr int kXCap = 2048;       // x entries per tile
+constexpr int kXGap = 64;         // columns closer than this share a window
 constexpr short kSellPadOff = -32768;  // outside the int16 offsets a row may use (|col - row| <= 32767)
 
 // Fused SpMV epilogue (one row r, Ax = (A (x + s2 x2))[r], x2 optional):

@@ -527,6 +527,334 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv(Spmv
     }
 }
 
+// ---------------------------------------------------------------- staged x windows (float32)
+
+// The float32 SpMV step with every operand of a tile in shared memory.  Besides the tile's row
+// pointers, values and column indices, the producer copies the tile's x windows (up to kXWin
+// contiguous column ranges covering every column its rows reference, precomputed per tile) and the
+// tile's rows of the epilogue's row-wise operands (up to kWSlots distinct vectors), so the consumers
+// gather x from shared memory instead of L1/L2 and read no global memory at all.  The matrix part of
+// the first stages is requested before the wait on the predecessor (constant data), the vector parts
+// after it.  Tiles without windows gather from global memory; the last, partial tile reads its row
+// operands from global memory.  Arithmetic and its order are those of k_spmv.
+constexpr int kWSlots = 3;
+
+template <typename IDX>
+struct SpmvWArgs {
+    SpmvArgs<float, IDX> a;  // a.cols: the real column indices (tiles without windows)
+    const short *lidx;       // window-buffer index of every entry (staged in place of the columns)
+    const int *twin;
+    int nslot;
+    VecRef slot[kWSlots];  // distinct row-operand vectors
+    int slot_of[4];        // u0, w0, u1, w1: their slot, or -1 (absent)
+};
+
+__host__ __device__ constexpr size_t spmvw_stage_bytes(int cap, int idx_bytes)
+{
+    return kSpmvRpBytes + round128((size_t)cap * 4) + round128((size_t)cap * 2) + round128((size_t)kXCap * 4) +
+           (size_t)kWSlots * 256 * 4 + 128 + 0 * idx_bytes;
+}
+
+template <typename IDX>
+__global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_w(SpmvWArgs<IDX> p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kSpmvStages];
+    __shared__ __align__(8) uint64_t empty[kSpmvStages];
+    __shared__ double s_coef[7];
+    using T = float;
+
+    const SpmvArgs<float, IDX> &a = p.a;
+    Cycle *st = a.st;
+    const int R = a.rows_per_tile;
+    const int G = a.lanes_per_row;
+    const long long ntiles = ((long long)a.n + R - 1) / R;
+    const size_t stage_bytes = spmvw_stage_bytes(a.cap, (int)sizeof(IDX));
+    const size_t val_off = kSpmvRpBytes;
+    const size_t col_off = val_off + round128((size_t)a.cap * sizeof(T));
+    const size_t xw_off = col_off + round128((size_t)a.cap * 2);
+    const size_t sl_off = xw_off + round128((size_t)kXCap * 4);
+    const size_t hd_off = sl_off + (size_t)kWSlots * 256 * 4;
+    constexpr int VA = 16 / (int)sizeof(T);
+    constexpr int CA = 8;  // the staged indices are int16
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int prefetched = (int)min((long long)kSpmvStages, my_tiles);
+
+    if (tid == 0) {
+        for (int q = 0; q < kSpmvStages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kSpmvConsumerWarps);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (wid == kSpmvConsumerWarps) {
+        // ---------------- producer
+        if (lane == 0) {
+            auto bounds = [&](long long t, int &e0, int &e1) {
+                const int r0 = (int)(t * R);
+                e0 = __ldg(a.rowptr + r0);
+                e1 = __ldg(a.rowptr + min(r0 + R, a.n));
+            };
+            // the matrix part of tile t into stage s (bytes expected, no arrival): row pointers, values
+            // and the entries' window-buffer indices
+            auto issue_matrix = [&](long long t, int s, int e0, int e1) {
+                const int r0 = (int)(t * R);
+                const int rows = min(R, a.n - r0);
+                const int vs = e0 & ~(VA - 1), ve = (e1 + VA - 1) & ~(VA - 1);
+                const int cs = e0 & ~(CA - 1), ce = (e1 + CA - 1) & ~(CA - 1);
+                const bool staged = (ve - vs) <= a.cap && (ce - cs) <= a.cap && e1 > e0;
+                unsigned char *base = smem + s * stage_bytes;
+                const uint32_t rpb = ((uint32_t)(rows + 1) * 4u + 15u) & ~15u;
+                const uint32_t vb = staged ? (uint32_t)(ve - vs) * (uint32_t)sizeof(T) : 0u;
+                const uint32_t cb = staged ? (uint32_t)(ce - cs) * 2u : 0u;
+                mbar_expect_tx(&full[s], rpb + vb + cb);
+                bulk_g2s(base, a.rowptr + r0, rpb, &full[s]);
+                if (staged) {
+                    bulk_g2s(base + val_off, a.vals + vs, vb, &full[s]);
+                    bulk_g2s(base + col_off, p.lidx + cs, cb, &full[s]);
+                }
+            };
+            // the vector part of tile t (x windows, row operands, header), then the arrival
+            const T *x = nullptr;
+            const T *sv[kWSlots] = {nullptr, nullptr, nullptr};
+            // window descriptors of the prefetched stages and, one tile ahead, of the next tile
+            int4 dlo[kSpmvStages], dln[kSpmvStages];
+            auto desc = [&](long long t, int4 &lo4, int4 &ln4) {
+                lo4 = __ldg(reinterpret_cast<const int4 *>(p.twin + t * 2 * kXWin));
+                ln4 = __ldg(reinterpret_cast<const int4 *>(p.twin + t * 2 * kXWin + kXWin));
+            };
+            auto issue_vectors = [&](long long t, int s, const int4 lo4, const int4 ln4) {
+                unsigned char *base = smem + s * stage_bytes;
+                int *hd = reinterpret_cast<int *>(base + hd_off);
+                const int r0 = (int)(t * R);
+                const int lo[kXWin] = {lo4.x, lo4.y, lo4.z, lo4.w};
+                const int ln[kXWin] = {ln4.x, ln4.y, ln4.z, ln4.w};
+                uint32_t bytes = 0;
+                int off = 0, nw = 0;
+                for (int w = 0; w < kXWin; ++w) {
+                    hd[w] = ln[w] > 0 ? lo[w] : 0x7fffffff;
+                    hd[kXWin + w] = off;
+                    if (ln[w] > 0) {
+                        bytes += (uint32_t)ln[w] * 4u;
+                        off += ln[w];
+                        ++nw;
+                    }
+                }
+                const bool full_tile = r0 + R <= a.n;
+                hd[2 * kXWin] = nw;
+                hd[2 * kXWin + 1] = full_tile ? 1 : 0;
+                if (full_tile) bytes += (uint32_t)p.nslot * (uint32_t)R * 4u;
+                mbar_arrive_expect_tx(&full[s], bytes);
+                for (int w = 0, o = 0; w < kXWin; ++w)
+                    if (ln[w] > 0) {
+                        bulk_g2s(base + xw_off + (size_t)o * 4, x + lo[w], (uint32_t)ln[w] * 4u, &full[s]);
+                        o += ln[w];
+                    }
+                if (full_tile)
+                    for (int q = 0; q < p.nslot; ++q)
+                        bulk_g2s(base + sl_off + (size_t)q * 256 * 4, sv[q] + r0, (uint32_t)R * 4u, &full[s]);
+            };
+            int ne0 = 0, ne1 = 0;
+            int4 nlo = make_int4(0, 0, 0, 0), nln = make_int4(0, 0, 0, 0);
+            if (my_tiles > 0) {
+                bounds(blockIdx.x, ne0, ne1);
+                desc(blockIdx.x, nlo, nln);
+            }
+            int i = 0;
+            bool waited = false;
+            for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+                if (i == prefetched) {
+                    waited = true;
+                    pdl_wait();
+                    pdl_trigger();
+                    if ((a.check_done == kSkipIfDone && st->cycle_done) ||
+                        (a.check_done == kSkipIfNoCols && st->k == 0)) {
+                        // the prefetched stages still expect no arrival: complete them so that the
+                        // consumers' drain can see their copies land
+                        for (int q = 0; q < prefetched; ++q) mbar_arrive(&full[q]);
+                        break;
+                    }
+                    x = resolve_ptr<T>(a.e.x, st);
+                    for (int q = 0; q < p.nslot; ++q) sv[q] = resolve_ptr<T>(p.slot[q], st);
+                    for (int q = 0; q < prefetched; ++q)
+                        issue_vectors(blockIdx.x + (long long)q * gridDim.x, q, dlo[q], dln[q]);
+                }
+                const int e0 = ne0, e1 = ne1;
+                const int4 clo = nlo, cln = nln;
+                if (tile + gridDim.x < ntiles) {
+                    bounds(tile + gridDim.x, ne0, ne1);
+                    desc(tile + gridDim.x, nlo, nln);
+                }
+                const int s = i % kSpmvStages, round = i / kSpmvStages;
+                if (round > 0 && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitLimitNs)) {
+                    atomicOr(&st->error, kErrTimeout);
+                    break;
+                }
+                issue_matrix(tile, s, e0, e1);
+                if (i >= prefetched) issue_vectors(tile, s, clo, cln);
+                else {
+                    dlo[i] = clo;
+                    dln[i] = cln;
+                }
+            }
+            if (!waited) {
+                // no more tiles than stages: the wait and the vector parts were not reached in the loop
+                pdl_wait();
+                pdl_trigger();
+                if ((a.check_done == kSkipIfDone && st->cycle_done) ||
+                    (a.check_done == kSkipIfNoCols && st->k == 0)) {
+                    for (int q = 0; q < i; ++q) mbar_arrive(&full[q]);
+                } else {
+                    x = resolve_ptr<T>(a.e.x, st);
+                    for (int q = 0; q < p.nslot; ++q) sv[q] = resolve_ptr<T>(p.slot[q], st);
+                    for (int q = 0; q < i; ++q) issue_vectors(blockIdx.x + (long long)q * gridDim.x, q, dlo[q], dln[q]);
+                }
+            }
+        }
+        return;
+    }
+
+    // consumers: nothing a predecessor wrote is read before this point
+    pdl_wait();
+    pdl_trigger();
+    if ((a.check_done == kSkipIfDone && st->cycle_done) || (a.check_done == kSkipIfNoCols && st->k == 0)) {
+        for (int q = 0; q < prefetched; ++q) mbar_wait_bounded(&full[q], 0, kWaitLimitNs);
+        return;
+    }
+    if (tid < 7) {
+        switch (tid) {
+        case 0: s_coef[0] = resolve(a.e.a0, st); break;
+        case 1: s_coef[1] = resolve(a.e.b0, st); break;
+        case 2: s_coef[2] = resolve(a.e.c0, st); break;
+        case 3: s_coef[3] = resolve(a.e.a1, st); break;
+        case 4: s_coef[4] = resolve(a.e.b1, st); break;
+        case 5: s_coef[5] = resolve(a.e.c1, st); break;
+        default: s_coef[6] = resolve(a.e.s2, st); break;
+        }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(kSpmvConsumerWarps * 32) : "memory");
+
+    const T *__restrict__ x = resolve_ptr<T>(a.e.x, st);
+    T *o0 = resolve_ptr<T>(a.e.out0, st);
+    const T *u0 = resolve_ptr<T>(a.e.u0, st);
+    const T *w0 = resolve_ptr<T>(a.e.w0, st);
+    T *o1 = resolve_ptr<T>(a.e.out1, st);
+    const T *u1 = resolve_ptr<T>(a.e.u1, st);
+    const T *w1 = resolve_ptr<T>(a.e.w1, st);
+    const T ca0 = (T)s_coef[0], cb0 = (T)s_coef[1], cc0 = (T)s_coef[2];
+    const T ca1 = (T)s_coef[3], cb1 = (T)s_coef[4], cc1 = (T)s_coef[5];
+    const int lr = tid / G;
+    const int lg = tid & (G - 1);
+    int i = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+        const int s = i % kSpmvStages;
+        if (!mbar_wait_bounded(&full[s], (i / kSpmvStages) & 1, kWaitLimitNs)) {
+            if (lane == 0) atomicOr(&st->error, kErrTimeout);
+            mbar_wait_bounded(&full[s], (i / kSpmvStages) & 1, kWaitLimitNs);
+            return;
+        }
+        const unsigned char *base = smem + s * stage_bytes;
+        const int *s_rp = reinterpret_cast<const int *>(base);
+        const T *s_val = reinterpret_cast<const T *>(base + val_off);
+        const short *s_li = reinterpret_cast<const short *>(base + col_off);
+        const T *s_x = reinterpret_cast<const T *>(base + xw_off);
+        const T *s_sl = reinterpret_cast<const T *>(base + sl_off);
+        const int *hd = reinterpret_cast<const int *>(base + hd_off);
+        const int nw = hd[2 * kXWin];
+        const bool rows_staged = hd[2 * kXWin + 1] != 0;
+        const int r0 = (int)(tile * R);
+        const int rows = min(R, a.n - r0);
+        const int e0 = s_rp[0], e1 = s_rp[rows];
+        const int vs = e0 & ~(VA - 1), ve = (e1 + VA - 1) & ~(VA - 1);
+        const int cs = e0 & ~(CA - 1), ce = (e1 + CA - 1) & ~(CA - 1);
+        const bool staged = (ve - vs) <= a.cap && (ce - cs) <= a.cap && e1 > e0;
+        const int l = lr;
+        const bool ok = l < rows;
+        const int rr = r0 + l;
+        int kb = ok ? s_rp[l] + lg : 0;
+        const int ke = ok ? s_rp[l + 1] : 0;
+        T acc = T(0), pu0 = T(0), pw0 = T(0), pu1 = T(0), pw1 = T(0);
+        if (lg == 0 && ok) {
+            if (rows_staged) {
+                if (u0) pu0 = s_sl[p.slot_of[0] * 256 + l];
+                if (w0) pw0 = s_sl[p.slot_of[1] * 256 + l];
+                if (o1) {
+                    if (u1) pu1 = s_sl[p.slot_of[2] * 256 + l];
+                    if (w1) pw1 = s_sl[p.slot_of[3] * 256 + l];
+                }
+            } else {
+                if (u0) pu0 = u0[rr];
+                if (w0) pw0 = w0[rr];
+                if (o1) {
+                    if (u1) pu1 = u1[rr];
+                    if (w1) pw1 = w1[rr];
+                }
+            }
+        }
+        if (staged && nw > 0) {
+            // every column lies in the staged windows: one shared-memory load per entry
+            bool more = true;
+            while (more) {
+                bool in[8];
+                T xv[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int kk = kb + t * G;
+                    in[t] = kk < ke;
+                    xv[t] = in[t] ? s_x[s_li[kk - cs]] : T(0);
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (in[t]) acc = fma(s_val[kb + t * G - vs], xv[t], acc);
+                kb += 8 * G;
+                more = kb < ke;
+            }
+        } else if (staged) {
+            // no windows for this tile: the values are staged, the columns and x come from global memory
+            bool more = true;
+            while (more) {
+                int qc[8];
+                T xv[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int kk = kb + t * G;
+                    qc[t] = kk < ke ? col_of<IDX>(__ldg(a.cols + kk), rr) : -1;
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) xv[t] = qc[t] >= 0 ? __ldg(x + qc[t]) : T(0);
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (qc[t] >= 0) acc = fma(s_val[kb + t * G - vs], xv[t], acc);
+                kb += 8 * G;
+                more = kb < ke;
+            }
+        } else {
+            for (int k = kb; k < ke; k += G) {
+                const int qq = col_of<IDX>(__ldg(a.cols + k), rr);
+                acc = fma(__ldg(a.vals + k), __ldg(x + qq), acc);
+            }
+        }
+        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lg == 0 && ok) {
+            T v = ca0 * acc;
+            if (u0) v = fma(cb0, pu0, v);
+            if (w0) v = fma(cc0, pw0, v);
+            o0[rr] = v;
+            if (o1) {
+                T v1 = ca1 * acc;
+                if (u1) v1 = fma(cb1, pu1, v1);
+                if (w1) v1 = fma(cc1, pw1, v1);
+                o1[rr] = v1;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+}
+
 // ---------------------------------------------------------------- two chain steps in one launch
 
 // A tile's staged matrix data serves two consecutive links of the p(A) chain (Section II,
@@ -1025,6 +1353,55 @@ cudaError_t spmv2_go(const DevMatrix &A, const T *vals, const IDX *cols, int cap
                        kSpmv2Stages * spmv_stage_bytes<T, IDX>(cap), s, p);
 }
 
+bool vec_same(const VecRef &u, const VecRef &v)
+{
+    return u.base == v.base && u.ld == v.ld && u.col == v.col && u.follow == v.follow;
+}
+
+// a vector the TMA engine may copy from: 16-byte aligned start, and for a column reference a
+// column stride of whole 16-byte units
+bool vec_aligned(const VecRef &v)
+{
+    return ((uintptr_t)v.base & 15u) == 0 && (v.follow == 0 || ((v.ld * 4) & 15) == 0) &&
+           (((long long)v.col * v.ld * 4) & 15) == 0;
+}
+
+template <typename IDX>
+cudaError_t spmvw_go(const DevMatrix &A, const IDX *cols, const SpmvEpi &e, Cycle *st, int check_done, cudaStream_t s,
+                     bool *launched)
+{
+    *launched = false;
+    if (e.x2.base || !vec_aligned(e.x)) return cudaSuccess;
+    SpmvWArgs<IDX> p{};
+    const VecRef *ops[4] = {&e.u0, &e.w0, &e.u1, &e.w1};
+    p.nslot = 0;
+    for (int q = 0; q < 4; ++q) {
+        p.slot_of[q] = -1;
+        if (!ops[q]->base || (q >= 2 && !e.out1.base)) continue;
+        if (!vec_aligned(*ops[q])) return cudaSuccess;
+        int found = -1;
+        for (int t = 0; t < p.nslot; ++t)
+            if (vec_same(p.slot[t], *ops[q])) found = t;
+        if (found < 0) {
+            if (p.nslot == kWSlots) return cudaSuccess;
+            p.slot[p.nslot] = *ops[q];
+            found = p.nslot++;
+        }
+        p.slot_of[q] = found;
+    }
+    const int R = A.rows_per_tile;
+    const long long ntiles = ((long long)A.n + R - 1) / R;
+    p.a = SpmvArgs<float, IDX>{A.n, A.rowptr, cols, A.vals32, R, A.lanes_per_row, A.cap32, st, check_done, e};
+    p.lidx = A.lidx;
+    p.twin = A.twin;
+    long long g = A.spmvw_blocks32;
+    if (g > ntiles) g = ntiles;
+    if (g <= 0) return cudaSuccess;
+    *launched = true;
+    return launch_pdl(k_spmv_w<IDX>, dim3((unsigned)g), dim3(kSpmvThreads),
+                      kSpmvStages * spmvw_stage_bytes(A.cap32, (int)sizeof(IDX)), s, p);
+}
+
 template <typename T, typename IDX>
 cudaError_t sell_go(const DevMatrix &A, const T *vals, const IDX *cols, const SpmvEpi &e, Cycle *st, int check_done,
                     cudaStream_t s)
@@ -1054,12 +1431,30 @@ cudaError_t spmv_set_smem()
             (int)min(kSpmv2Stages * spmv_stage_bytes<T, IDX>(kSpmvCapMax), (size_t)smem_optin() - 1024));
     if (e == cudaSuccess && PPG_SPMV_CARVEOUT >= 0)
         e = cudaFuncSetAttribute(k_spmv<T, IDX>, cudaFuncAttributePreferredSharedMemoryCarveout, PPG_SPMV_CARVEOUT);
+    if (e == cudaSuccess && sizeof(T) == 4)
+        e = cudaFuncSetAttribute(k_spmv_w<IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kSpmvStages * spmvw_stage_bytes(kSpmvCapMax, (int)sizeof(IDX))));
     return e;
+}
+
+template <typename IDX>
+int spmvw_per_sm(int cap)
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_w<IDX>, kSpmvThreads,
+                                                  kSpmvStages * spmvw_stage_bytes(cap, (int)sizeof(IDX)));
+    return nb > 0 ? nb : 0;
 }
 }  // namespace
 
 cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *st, int check_done, cudaStream_t s)
 {
+    if (A.format == kFmtCsrStaged && prec == kF32 && A.twin) {
+        bool launched = false;
+        const cudaError_t err = A.coloff ? spmvw_go<short>(A, A.coloff, e, st, check_done, s, &launched)
+                                         : spmvw_go<int>(A, A.colidx, e, st, check_done, s, &launched);
+        if (launched || err != cudaSuccess) return err;
+    }
     if (A.format == kFmtSell && A.nslices > 0) {
         if (prec == kF64) {
             if (A.soff) return sell_go<double, short>(A, A.svals64, A.soff, e, st, check_done, s);
@@ -1111,11 +1506,13 @@ cudaError_t spmv_configure(DevMatrix *A)
         A->spmv_blocks32 = spmv_per_sm<float, short>(A->cap32) * A->num_sms;
         A->spmv2_blocks64 = spmv2_per_sm<double, short>(A->cap64) * A->num_sms;
         A->spmv2_blocks32 = spmv2_per_sm<float, short>(A->cap32) * A->num_sms;
+        A->spmvw_blocks32 = spmvw_per_sm<short>(A->cap32) * A->num_sms;
     } else {
         A->spmv_blocks64 = spmv_per_sm<double, int>(A->cap64) * A->num_sms;
         A->spmv_blocks32 = spmv_per_sm<float, int>(A->cap32) * A->num_sms;
         A->spmv2_blocks64 = spmv2_per_sm<double, int>(A->cap64) * A->num_sms;
         A->spmv2_blocks32 = spmv2_per_sm<float, int>(A->cap32) * A->num_sms;
+        A->spmvw_blocks32 = spmvw_per_sm<int>(A->cap32) * A->num_sms;
     }
     return cudaSuccess;
 }

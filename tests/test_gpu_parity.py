@@ -90,6 +90,7 @@ MATRICES = {
 }
 
 FORMATS = {"csr": ppg.PPG_SPMV_CSR, "sell": ppg.PPG_SPMV_SELL}
+STAGED_MATS = ["c1_2d_64", "3d_7pt_21", "27pt_13"]
 
 
 # ---------------------------------------------------------------- generator
@@ -654,3 +655,52 @@ def test_graph_replay_is_bit_identical(mat):
             assert ig.status == idd.status == ppg.PPG_OK
             assert ig.stats["iterations"] == idd.stats["iterations"]
             np.testing.assert_array_equal(xg.cpu().numpy(), xd.cpu().numpy())
+
+
+
+# ---------------------------------------------------------------- staged x windows
+
+
+@pytest.mark.parametrize("mat", STAGED_MATS)
+def test_staged_kernel_is_bit_identical(mat):
+    """The float32 kernel that stages a tile's x windows and row operands in shared memory gives exactly
+    the row-block kernel's results: single SpMVs, p(A) in both bases, and whole solves."""
+    a = MATRICES[mat]()
+    s = solver_for(a)
+    assert s.spmv_format(ppg.PPG_SPMV_STAGED) == ppg.PPG_SPMV_STAGED
+    v = T(w.uniform(42, a.n), torch.float32)
+    b = T(w.rhs(a.n))
+    v0 = T(w.v0(a.n))
+    got = {}
+    for fmt in (ppg.PPG_SPMV_STAGED, ppg.PPG_SPMV_CSR):
+        s.spmv_format(fmt)
+        res = [s.spmv(v).cpu().numpy()]
+        for basis, deg in ((ppg.PPG_BASIS_ROOTS, 10), (ppg.PPG_BASIS_POWER, 5)):
+            s.build_poly(deg, basis, v0=v0)
+            res.append(s.apply_poly(v).cpu().numpy())
+            x, info = s.solve(b, tol=1e-8, restart=30, maxit=400, precision=ppg.PPG_F32)
+            res += [x.cpu().numpy(), info.stats["iterations"]]
+        got[fmt] = res
+    for r1, r0 in zip(got[ppg.PPG_SPMV_STAGED], got[ppg.PPG_SPMV_CSR]):
+        np.testing.assert_array_equal(r1, r0)
+
+
+def test_staged_kernel_refuses_matrices_without_windows():
+    s = solver_for(long_row_matrix())
+    with pytest.raises(ppg.PPGError):
+        s.spmv_format(ppg.PPG_SPMV_STAGED)
+
+
+def test_full_size_c2_staged_matches_row_block(c2):
+    a = c2
+    b = T(w.rhs(a.n))
+    s = solver_for(a)
+    s.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=T(w.v0(a.n)))
+    out = {}
+    for fmt in (ppg.PPG_SPMV_STAGED, ppg.PPG_SPMV_CSR):
+        assert s.spmv_format(fmt) == fmt
+        x, info = s.solve(b, tol=1e-8, restart=50, maxit=3000, precision=ppg.PPG_F32)
+        assert info.status == ppg.PPG_OK
+        out[fmt] = (x.cpu().numpy(), info.stats["iterations"])
+    assert out[ppg.PPG_SPMV_STAGED][1] == out[ppg.PPG_SPMV_CSR][1]
+    np.testing.assert_array_equal(out[ppg.PPG_SPMV_STAGED][0], out[ppg.PPG_SPMV_CSR][0])
