@@ -42,12 +42,12 @@ def workload_name(N, nnz=None):
             + "), Pe 50, GMRES(50), rtol 1e-8")
 
 
-# DRAM traffic of one k_spmv<float, short> launch (a root step of the p(A) chain, C2 matrix) from the ncu
+# DRAM traffic of one k_spmv_w<short> launch (a root step of the p(A) chain, C2 matrix) from the ncu
 # capture summarised in profiles/k_spmv_c2_128cubed.md, and the kernel source it was taken with: when the
 # source changes, the number no longer describes the kernel and the bench reports null.
-SPMV_TRAFFIC = {"src_sha256_16": "d4a35ed5402e2ff4", "dram_bytes": 112688128 + 6292992,
+SPMV_TRAFFIC = {"src_sha256_16": "ff8c285059ba7f8c", "dram_bytes": 113426944 + 6853120,
                 "algorithmic_bytes": 112656384 + 16777216,
-                "launch": "k_spmv<float, short> root step (gather P; write Y and P'), ncu --set full, cold caches"}
+                "launch": "k_spmv_w<short> root step (gather P from staged windows; write Y and P'), ncu --set full, cold caches"}
 
 
 def spmv_traffic():
@@ -358,8 +358,10 @@ def main():
         "iterations": last["iterations"], "restarts": last["restarts"], "relres_true": last["relres_true"],
         "relres_host_check": relres_host,
         "roofline": {"bound": "hbm",
-                     "kernel": ("k_spmv<float>" if prec == ppg.PPG_F32 else "k_spmv<double>")
-                               + " (SpMV chain: fused Horner / root steps of p(A) and the SpMV with A)",
+                     "kernel": ("k_spmv_w<short> (x windows staged in shared memory)"
+                                if prec == ppg.PPG_F32 and s.spmv_format() == ppg.PPG_SPMV_STAGED
+                                else "k_spmv<float>" if prec == ppg.PPG_F32 else "k_spmv<double>")
+                               + ": the SpMV chain, fused root steps of p(A) and the SpMV with A",
                      "achieved": round(spmv_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(spmv_gbs / hbm, 3),
                      "peak_source": "measured" if "hbm_gbs" in pk else "fallback", "traffic": traffic,
                      "traffic_note": traffic_info,

@@ -141,13 +141,15 @@ ppg_status ppg_spmv(ppg_ctx *ctx, const void *x, void *y, int precision);
  * keeps the CSR arrays and, at ppg_create, also
  *   - a sliced ELL copy: slices of 32 consecutive rows, each padded to its longest row and stored entry
  *     index by entry index, so one warp reads a slice with coalesced loads (PPG_SPMV_SELL);
- *   - for each 256-row tile, up to four contiguous ranges of x covering every column the tile's rows
- *     reference (banded matrices): with PPG_SPMV_STAGED the float32 row-block kernel copies those
- *     ranges and the tile's rows of the update operands into shared memory along with the matrix
- *     tile, so that its x gathers read shared memory (available when 90 % of the tiles are covered).
- * PPG_SPMV_AUTO selects the row-block CSR kernel; PPG_SPMV_CSR, PPG_SPMV_SELL and PPG_SPMV_STAGED force
- * one (STAGED applies to float32 links without a second gathered input; others run as CSR).  Every
- * result is the same sum; CSR and STAGED give identical bits.  request = PPG_SPMV_QUERY changes
+ *   - for each tile of rows, up to four contiguous ranges of x covering every column the tile's rows
+ *     reference (banded matrices), and per entry its index into those ranges: with PPG_SPMV_STAGED the
+ *     float32 row-block kernel copies the ranges into shared memory along with the matrix tile, so
+ *     that each x gather is one shared-memory load (available when 90 % of the tiles are covered).
+ * PPG_SPMV_AUTO selects STAGED when the windows exist and the row-block CSR kernel otherwise (measured on
+ * the 128^3, 27-point 100^3 and 64^3 stencils: STAGED 3-17 % faster per SpMV, SELL slower than both);
+ * PPG_SPMV_CSR, PPG_SPMV_SELL and PPG_SPMV_STAGED force one (STAGED applies to float32 links without a
+ * second gathered input; others run as CSR).  Every result is the same sum; CSR and STAGED give
+ * identical bits.  request = PPG_SPMV_QUERY changes
  * nothing; *in_effect (host, may be NULL) receives the format now used.
  * Errors: PPG_ERR_INVALID_ARG (unknown request, or a format whose copy was not built). */
 enum {

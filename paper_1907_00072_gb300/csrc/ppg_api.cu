@@ -81,7 +81,6 @@ struct ppg_ctx {
     int *d_scol = nullptr;
     double *d_svals64 = nullptr;
     float *d_svals32 = nullptr;
-    int sell_auto = 0;           // the format the automatic choice picked
     int *d_rounds = nullptr;     // two-step chain kernel: kMaxRounds round counters, a ticket, 8 diagnostics
     int *d_twin = nullptr;       // x windows per tile (DevMatrix::twin)
     short *d_lidx = nullptr;     // window-buffer index per entry (DevMatrix::lidx)
@@ -1320,9 +1319,8 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
             c->A.scol = c->d_scol;
             c->A.svals64 = c->d_svals64;
             c->A.spadded = pos;
-            c->sell_auto = kFmtCsr;  // measured slower than the TMA row-block kernel on every workload here
         }
-        c->A.format = c->A.nslices > 0 ? c->sell_auto : kFmtCsr;
+        c->A.format = c->A.twin ? kFmtCsrStaged : kFmtCsr;
     }
     PPG_CK(gs_configure());
     PPG_CK(gram_configure());
@@ -1375,7 +1373,7 @@ ppg_status ppg_spmv_format(ppg_ctx *c, int request, int *in_effect)
     if (!c) return fail(PPG_ERR_INVALID_ARG, "null context");
     switch (request) {
     case PPG_SPMV_QUERY: break;
-    case PPG_SPMV_AUTO: c->A.format = c->A.nslices > 0 ? c->sell_auto : kFmtCsr; break;
+    case PPG_SPMV_AUTO: c->A.format = c->A.twin ? kFmtCsrStaged : kFmtCsr; break;
     case PPG_SPMV_CSR: c->A.format = kFmtCsr; break;
     case PPG_SPMV_SELL:
         if (c->A.nslices == 0) return fail(PPG_ERR_INVALID_ARG, "no sliced ELL copy for this matrix");

@@ -537,6 +537,9 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv(Spmv
 // the first stages is requested before the wait on the predecessor (constant data), the vector parts
 // after it.  Tiles without windows gather from global memory; the last, partial tile reads its row
 // operands from global memory.  Arithmetic and its order are those of k_spmv.
+#ifndef PPG_SPMV_STAGE_ROWS
+#define PPG_SPMV_STAGE_ROWS 0  // 1: the staged kernel also stages the update operands' rows (measured slower)
+#endif
 constexpr int kWSlots = 3;
 
 template <typename IDX>
@@ -643,7 +646,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_w(Sp
                         ++nw;
                     }
                 }
-                const bool full_tile = r0 + R <= a.n;
+                const bool full_tile = r0 + R <= a.n && p.nslot > 0;
                 hd[2 * kXWin] = nw;
                 hd[2 * kXWin + 1] = full_tile ? 1 : 0;
                 if (full_tile) bytes += (uint32_t)p.nslot * (uint32_t)R * 4u;
@@ -1377,7 +1380,7 @@ cudaError_t spmvw_go(const DevMatrix &A, const IDX *cols, const SpmvEpi &e, Cycl
     p.nslot = 0;
     for (int q = 0; q < 4; ++q) {
         p.slot_of[q] = -1;
-        if (!ops[q]->base || (q >= 2 && !e.out1.base)) continue;
+        if (!PPG_SPMV_STAGE_ROWS || !ops[q]->base || (q >= 2 && !e.out1.base)) continue;
         if (!vec_aligned(*ops[q])) return cudaSuccess;
         int found = -1;
         for (int t = 0; t < p.nslot; ++t)

@@ -134,12 +134,14 @@ def test_spmv_f32_matches_oracle(name, fmt):
 
 
 def test_spmv_format_choice_and_nonfinite_padding():
-    """The automatic choice is the row-block CSR kernel; the sliced copy is selectable; padding
-    entries of the sliced format never touch x (an Inf in x reaches only the rows that reference it)."""
+    """The automatic choice is the staged row-block kernel for banded matrices and the plain one otherwise;
+    the sliced copy is selectable; padding entries of the sliced format never touch x (an Inf in x
+    reaches only the rows that reference it)."""
     s = solver_for(w.c1_matrix())
-    assert s.spmv_format() == ppg.PPG_SPMV_CSR
+    assert s.spmv_format() == ppg.PPG_SPMV_STAGED  # banded: x windows exist
     assert s.spmv_format(ppg.PPG_SPMV_SELL) == ppg.PPG_SPMV_SELL
-    assert s.spmv_format(ppg.PPG_SPMV_AUTO) == ppg.PPG_SPMV_CSR
+    assert s.spmv_format(ppg.PPG_SPMV_AUTO) == ppg.PPG_SPMV_STAGED
+    assert solver_for(long_row_matrix()).spmv_format() == ppg.PPG_SPMV_CSR
     with pytest.raises(ppg.PPGError):
         s.spmv_format(7)
     a = MATRICES["random_ragged"]()
@@ -592,6 +594,7 @@ def test_paired_chain_is_bit_identical(mat):
     results of one link per launch: same tiles, same per-row arithmetic."""
     a = MATRICES[mat]()
     s = solver_for(a)
+    s.spmv_format(ppg.PPG_SPMV_CSR)  # pairing applies to the row-block kernel
     assert s.chain_fusion(-1) in (0, 1)
     v0 = T(w.v0(a.n))
     b = T(w.rhs(a.n))
@@ -611,19 +614,26 @@ def test_paired_chain_is_bit_identical(mat):
 
 
 def test_chain_pairing_applies_to_banded_matrices():
-    assert solver_for(w.c1_matrix()).chain_fusion(-1) == 0  # off by default
-    assert solver_for(w.c1_matrix()).chain_fusion(1) == 1
-    assert solver_for(w.convdiff(21, 3, 50.0)).chain_fusion(1) == 1
-    s = solver_for(w.c1_matrix())
+    def csr(a):
+        s = solver_for(a)
+        s.spmv_format(ppg.PPG_SPMV_CSR)
+        return s
+    assert csr(w.c1_matrix()).chain_fusion(-1) == 0  # off by default
+    assert csr(w.c1_matrix()).chain_fusion(1) == 1
+    assert csr(w.convdiff(21, 3, 50.0)).chain_fusion(1) == 1
+    s = csr(w.c1_matrix())
     assert s.chain_fusion(1) == 1 and s.chain_fusion(0) == 0 and s.chain_fusion(1) == 1
     s.spmv_format(ppg.PPG_SPMV_SELL)
     assert s.chain_fusion(-1) == 0  # pairing is a property of the row-block kernel
+    s.spmv_format(ppg.PPG_SPMV_STAGED)
+    assert s.chain_fusion(-1) == 0
 
 
 def test_full_size_c2_paired_chain_matches_unpaired(c2):
     a = c2
     b = T(w.rhs(a.n))
     s = solver_for(a)
+    s.spmv_format(ppg.PPG_SPMV_CSR)
     assert s.chain_fusion(1) == 1
     s.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=T(w.v0(a.n)))
     x1, i1 = s.solve(b, tol=1e-8, restart=50, maxit=3000, precision=ppg.PPG_F32)
