@@ -84,6 +84,9 @@ struct ppg_ctx {
     int *d_rounds = nullptr;     // two-step chain kernel: kMaxRounds round counters, a ticket, 8 diagnostics
     int *d_twin = nullptr;       // x windows per tile (DevMatrix::twin)
     short *d_lidx = nullptr;     // window-buffer index per entry (DevMatrix::lidx)
+    float *d_evals = nullptr;    // tile-ELL copy (DevMatrix::evals, eidx, toff)
+    short *d_eidx = nullptr;
+    int *d_toff = nullptr;
     int fuse = 0;                // pair consecutive links of the p(A) chain into one launch (measured slower)
 
     // CUDA graphs of single iterations (ppg_opts.use_graph): one per iteration index, precision and
@@ -1284,6 +1287,50 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
             c->A.twin = c->d_twin;
             c->A.lidx = c->d_lidx;
         }
+        // tile-ELL copy for one lane per row when every tile has windows: tile t is a dense R x w_t block
+        // (entry k of row l at k R + l) of float32 values and window indices, padded with value 0 and
+        // the index kXCap of a zero kept after the windows
+        if (c->A.twin && windowed == ntiles && R == kThreads) {
+            std::vector<double> hval(nnz);
+            PPG_CK(cudaMemcpy(hval.data(), c->d_vals, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+            std::vector<int> toff(ntiles + 1, 0);
+            int wmax = 0;
+            for (long long t = 0; t < ntiles; ++t) {
+                const long long r0 = t * R, r1 = std::min<long long>(n, r0 + R);
+                int wt = 0;
+                for (long long r = r0; r < r1; ++r) wt = std::max(wt, hrp[r + 1] - hrp[r]);
+                wmax = std::max(wmax, wt);
+                if ((long long)toff[t] + (long long)R * wt >= (1LL << 31) - 64) {
+                    wmax = -1;
+                    break;
+                }
+                toff[t + 1] = toff[t] + R * wt;
+            }
+            if (wmax > 0 && wmax <= 16) {
+                const size_t total = (size_t)toff[ntiles];
+                std::vector<float> ev(total + 16, 0.0f);
+                std::vector<short> ei(total + 16, (short)kXCap);
+                for (long long t = 0; t < ntiles; ++t) {
+                    const long long r0 = t * R, r1 = std::min<long long>(n, r0 + R);
+                    for (long long r = r0; r < r1; ++r)
+                        for (int k = 0; k < hrp[r + 1] - hrp[r]; ++k) {
+                            const size_t e = (size_t)toff[t] + (size_t)k * R + (size_t)(r - r0);
+                            ev[e] = (float)hval[hrp[r] + k];
+                            ei[e] = lidx[hrp[r] + k];
+                        }
+                }
+                PPG_CK(cudaMalloc(&c->d_evals, sizeof(float) * ev.size()));
+                PPG_CK(cudaMemcpy(c->d_evals, ev.data(), sizeof(float) * ev.size(), cudaMemcpyHostToDevice));
+                PPG_CK(cudaMalloc(&c->d_eidx, sizeof(short) * ei.size()));
+                PPG_CK(cudaMemcpy(c->d_eidx, ei.data(), sizeof(short) * ei.size(), cudaMemcpyHostToDevice));
+                PPG_CK(cudaMalloc(&c->d_toff, sizeof(int) * toff.size()));
+                PPG_CK(cudaMemcpy(c->d_toff, toff.data(), sizeof(int) * toff.size(), cudaMemcpyHostToDevice));
+                c->A.evals = c->d_evals;
+                c->A.eidx = c->d_eidx;
+                c->A.toff = c->d_toff;
+                c->A.ewmax = wmax;
+            }
+        }
     }
     PPG_CK(spmv_configure(&c->A));
 
@@ -1348,6 +1395,9 @@ void ppg_destroy(ppg_ctx *c)
     cudaFree(c->d_rounds);
     cudaFree(c->d_twin);
     cudaFree(c->d_lidx);
+    cudaFree(c->d_evals);
+    cudaFree(c->d_eidx);
+    cudaFree(c->d_toff);
     cudaFree(c->d_sptr);
     cudaFree(c->d_soff);
     cudaFree(c->d_scol);

@@ -73,6 +73,13 @@ struct DevMatrix {
     // tile's rows reference, or lengths 0 when the tile's columns do not fit kXCap entries
     const int *twin;      // [ntiles][2 kXWin], or null
     const short *lidx;    // per entry: index of its column in the tile's concatenated windows
+    // tile-ELL copy (one lane per row, every tile windowed): tile t holds entries toff[t] ..
+    // toff[t+1]-1, entry k of row l at toff[t] + k R + l; padding has value 0 and index kXCap
+    const float *evals;
+    const short *eidx;
+    const int *toff;      // ntiles + 1
+    int ewmax;            // widest tile (entries per row)
+    int spmve_blocks;     // persistent grid of the tile-ELL kernel
     int spmvw_blocks32;   // persistent grid of the staged kernel
     // sliced ELL copy (slices of 32 rows; entry k of row 32 s + l at sptr[s] + 32 k + l, slices padded
     // to their longest row with a sentinel index), used by the SpMV when format == kFmtSell

@@ -858,6 +858,225 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_w(Sp
     }
 }
 
+// ---------------------------------------------------------------- staged x windows, tile-ELL (float32)
+
+// As k_spmv_w for one lane per row, with each tile stored as a dense R x w block (entry k of row l
+// at k R + l): the stage holds the block's values and window indices and the tile's x windows plus a
+// zero at index kXCap for the padding, so a row is w shared-memory multiply-adds with no row pointers
+// or bounds tests.  Same arithmetic as k_spmv (padding adds 0 * 0).
+__host__ __device__ constexpr size_t spmve_stage_bytes(int wmax)
+{
+    return round128((size_t)kThreads * wmax * 4) + round128((size_t)kThreads * wmax * 2) +
+           round128((size_t)(kXCap + 4) * 4) + 128;
+}
+
+struct SpmvEArgs {
+    int n;
+    const float *vals;  // tile-ELL values
+    const short *idx;   // tile-ELL window indices
+    const int *toff;
+    const int *twin;
+    int wmax;
+    Cycle *st;
+    int check_done;
+    SpmvEpi e;
+};
+
+__global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(SpmvEArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kSpmvStages];
+    __shared__ __align__(8) uint64_t empty[kSpmvStages];
+    __shared__ double s_coef[7];
+    using T = float;
+    constexpr int R = kThreads;
+
+    Cycle *st = a.st;
+    const long long ntiles = ((long long)a.n + R - 1) / R;
+    const size_t stage_bytes = spmve_stage_bytes(a.wmax);
+    const size_t ix_off = round128((size_t)R * a.wmax * 4);
+    const size_t xw_off = ix_off + round128((size_t)R * a.wmax * 2);
+    const size_t hd_off = xw_off + round128((size_t)(kXCap + 4) * 4);
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int prefetched = (int)min((long long)kSpmvStages, my_tiles);
+
+    if (tid == 0) {
+        for (int q = 0; q < kSpmvStages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kSpmvConsumerWarps);
+        }
+        fence_mbar_init();
+    }
+    if (tid < kSpmvStages * 4) {  // the zero the padding indexes, in every stage (no copy writes there)
+        T *z = reinterpret_cast<T *>(smem + (tid / 4) * stage_bytes + xw_off);
+        z[kXCap + (tid & 3)] = T(0);
+    }
+    __syncthreads();
+
+    if (wid == kSpmvConsumerWarps) {
+        // ---------------- producer
+        if (lane == 0) {
+            int4 dlo[kSpmvStages], dln[kSpmvStages];
+            auto desc = [&](long long t, int4 &lo4, int4 &ln4) {
+                lo4 = __ldg(reinterpret_cast<const int4 *>(a.twin + t * 2 * kXWin));
+                ln4 = __ldg(reinterpret_cast<const int4 *>(a.twin + t * 2 * kXWin + kXWin));
+            };
+            auto span = [&](long long t, int &o0, int &o1) {
+                o0 = __ldg(a.toff + t);
+                o1 = __ldg(a.toff + t + 1);
+            };
+            auto issue_matrix = [&](int s, int o0, int o1) {
+                unsigned char *base = smem + s * stage_bytes;
+                const uint32_t nb = (uint32_t)(o1 - o0);
+                mbar_expect_tx(&full[s], nb * 6u);
+                if (nb) {
+                    bulk_g2s(base, a.vals + o0, nb * 4u, &full[s]);
+                    bulk_g2s(base + ix_off, a.idx + o0, nb * 2u, &full[s]);
+                }
+                reinterpret_cast<int *>(base + hd_off)[0] = (int)(nb / R);
+            };
+            const T *x = nullptr;
+            auto issue_vectors = [&](int s, const int4 lo4, const int4 ln4) {
+                unsigned char *base = smem + s * stage_bytes;
+                const int lo[kXWin] = {lo4.x, lo4.y, lo4.z, lo4.w};
+                const int ln[kXWin] = {ln4.x, ln4.y, ln4.z, ln4.w};
+                uint32_t bytes = 0;
+                for (int w = 0; w < kXWin; ++w) bytes += (uint32_t)ln[w] * 4u;
+                mbar_arrive_expect_tx(&full[s], bytes);
+                for (int w = 0, o = 0; w < kXWin; ++w)
+                    if (ln[w] > 0) {
+                        bulk_g2s(base + xw_off + (size_t)o * 4, x + lo[w], (uint32_t)ln[w] * 4u, &full[s]);
+                        o += ln[w];
+                    }
+            };
+            int no0 = 0, no1 = 0;
+            int4 nlo = make_int4(0, 0, 0, 0), nln = make_int4(0, 0, 0, 0);
+            if (my_tiles > 0) {
+                span(blockIdx.x, no0, no1);
+                desc(blockIdx.x, nlo, nln);
+            }
+            int i = 0;
+            bool waited = false;
+            for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+                if (i == prefetched) {
+                    waited = true;
+                    pdl_wait();
+                    pdl_trigger();
+                    if ((a.check_done == kSkipIfDone && st->cycle_done) ||
+                        (a.check_done == kSkipIfNoCols && st->k == 0)) {
+                        for (int q = 0; q < prefetched; ++q) mbar_arrive(&full[q]);
+                        break;
+                    }
+                    x = resolve_ptr<T>(a.e.x, st);
+                    for (int q = 0; q < prefetched; ++q) issue_vectors(q, dlo[q], dln[q]);
+                }
+                const int o0 = no0, o1 = no1;
+                const int4 clo = nlo, cln = nln;
+                if (tile + gridDim.x < ntiles) {
+                    span(tile + gridDim.x, no0, no1);
+                    desc(tile + gridDim.x, nlo, nln);
+                }
+                const int s = i % kSpmvStages, round = i / kSpmvStages;
+                if (round > 0 && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitLimitNs)) {
+                    atomicOr(&st->error, kErrTimeout);
+                    break;
+                }
+                issue_matrix(s, o0, o1);
+                if (i >= prefetched) issue_vectors(s, clo, cln);
+                else {
+                    dlo[i] = clo;
+                    dln[i] = cln;
+                }
+            }
+            if (!waited) {
+                pdl_wait();
+                pdl_trigger();
+                if ((a.check_done == kSkipIfDone && st->cycle_done) ||
+                    (a.check_done == kSkipIfNoCols && st->k == 0)) {
+                    for (int q = 0; q < i; ++q) mbar_arrive(&full[q]);
+                } else {
+                    x = resolve_ptr<T>(a.e.x, st);
+                    for (int q = 0; q < i; ++q) issue_vectors(q, dlo[q], dln[q]);
+                }
+            }
+        }
+        return;
+    }
+
+    // consumers: nothing a predecessor wrote is read before this point
+    pdl_wait();
+    pdl_trigger();
+    if ((a.check_done == kSkipIfDone && st->cycle_done) || (a.check_done == kSkipIfNoCols && st->k == 0)) {
+        for (int q = 0; q < prefetched; ++q) mbar_wait_bounded(&full[q], 0, kWaitLimitNs);
+        return;
+    }
+    if (tid < 7) {
+        switch (tid) {
+        case 0: s_coef[0] = resolve(a.e.a0, st); break;
+        case 1: s_coef[1] = resolve(a.e.b0, st); break;
+        case 2: s_coef[2] = resolve(a.e.c0, st); break;
+        case 3: s_coef[3] = resolve(a.e.a1, st); break;
+        case 4: s_coef[4] = resolve(a.e.b1, st); break;
+        case 5: s_coef[5] = resolve(a.e.c1, st); break;
+        default: s_coef[6] = resolve(a.e.s2, st); break;
+        }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(kSpmvConsumerWarps * 32) : "memory");
+
+    T *o0 = resolve_ptr<T>(a.e.out0, st);
+    const T *u0 = resolve_ptr<T>(a.e.u0, st);
+    const T *w0 = resolve_ptr<T>(a.e.w0, st);
+    T *o1 = resolve_ptr<T>(a.e.out1, st);
+    const T *u1 = resolve_ptr<T>(a.e.u1, st);
+    const T *w1 = resolve_ptr<T>(a.e.w1, st);
+    const T ca0 = (T)s_coef[0], cb0 = (T)s_coef[1], cc0 = (T)s_coef[2];
+    const T ca1 = (T)s_coef[3], cb1 = (T)s_coef[4], cc1 = (T)s_coef[5];
+    int i = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+        const int s = i % kSpmvStages;
+        const int rr = (int)(tile * R) + tid;
+        const bool ok = rr < a.n;
+        // row operands first: their loads overlap the wait and the products
+        T pu0 = T(0), pw0 = T(0), pu1 = T(0), pw1 = T(0);
+        if (ok) {
+            if (u0) pu0 = u0[rr];
+            if (w0) pw0 = w0[rr];
+            if (o1) {
+                if (u1) pu1 = u1[rr];
+                if (w1) pw1 = w1[rr];
+            }
+        }
+        if (!mbar_wait_bounded(&full[s], (i / kSpmvStages) & 1, kWaitLimitNs)) {
+            if (lane == 0) atomicOr(&st->error, kErrTimeout);
+            mbar_wait_bounded(&full[s], (i / kSpmvStages) & 1, kWaitLimitNs);
+            return;
+        }
+        const unsigned char *base = smem + s * stage_bytes;
+        const T *s_val = reinterpret_cast<const T *>(base);
+        const short *s_ix = reinterpret_cast<const short *>(base + ix_off);
+        const T *s_x = reinterpret_cast<const T *>(base + xw_off);
+        const int w = reinterpret_cast<const int *>(base + hd_off)[0];
+        T acc = T(0);
+#pragma unroll 8
+        for (int k = 0; k < w; ++k) acc = fma(s_val[k * R + tid], s_x[s_ix[k * R + tid]], acc);
+        if (ok) {
+            T v = ca0 * acc;
+            if (u0) v = fma(cb0, pu0, v);
+            if (w0) v = fma(cc0, pw0, v);
+            o0[rr] = v;
+            if (o1) {
+                T v1 = ca1 * acc;
+                if (u1) v1 = fma(cb1, pu1, v1);
+                if (w1) v1 = fma(cc1, pw1, v1);
+                o1[rr] = v1;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+}
+
 // ---------------------------------------------------------------- two chain steps in one launch
 
 // A tile's staged matrix data serves two consecutive links of the p(A) chain (Section II,
@@ -1394,6 +1613,14 @@ cudaError_t spmvw_go(const DevMatrix &A, const IDX *cols, const SpmvEpi &e, Cycl
     }
     const int R = A.rows_per_tile;
     const long long ntiles = ((long long)A.n + R - 1) / R;
+    if (A.evals && A.spmve_blocks > 0) {
+        SpmvEArgs q{A.n, A.evals, A.eidx, A.toff, A.twin, A.ewmax, st, check_done, e};
+        long long g = A.spmve_blocks;
+        if (g > ntiles) g = ntiles;
+        *launched = true;
+        return launch_pdl(k_spmv_e, dim3((unsigned)g), dim3(kSpmvThreads), kSpmvStages * spmve_stage_bytes(A.ewmax), s,
+                          q);
+    }
     p.a = SpmvArgs<float, IDX>{A.n, A.rowptr, cols, A.vals32, R, A.lanes_per_row, A.cap32, st, check_done, e};
     p.lidx = A.lidx;
     p.twin = A.twin;
@@ -1437,6 +1664,9 @@ cudaError_t spmv_set_smem()
     if (e == cudaSuccess && sizeof(T) == 4)
         e = cudaFuncSetAttribute(k_spmv_w<IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kSpmvStages * spmvw_stage_bytes(kSpmvCapMax, (int)sizeof(IDX))));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spmv_e, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kSpmvStages * spmve_stage_bytes(16)));
     return e;
 }
 
@@ -1491,6 +1721,13 @@ cudaError_t launch_spmv2(const DevMatrix &A, int prec, const SpmvEpi &e1, const 
                                 ticket, diag, s);
 }
 
+int spmve_per_sm(int wmax)
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e, kSpmvThreads, kSpmvStages * spmve_stage_bytes(wmax));
+    return nb > 0 ? nb : 0;
+}
+
 // Sets the dynamic shared memory limit (for the largest staging capacity, once) and returns
 // the persistent grid sizes for this matrix's capacities and index format.
 cudaError_t spmv_configure(DevMatrix *A)
@@ -1504,6 +1741,7 @@ cudaError_t spmv_configure(DevMatrix *A)
         if (err != cudaSuccess) return err;
         done = true;
     }
+    A->spmve_blocks = A->evals ? spmve_per_sm(A->ewmax) * A->num_sms : 0;
     if (A->coloff) {
         A->spmv_blocks64 = spmv_per_sm<double, short>(A->cap64) * A->num_sms;
         A->spmv_blocks32 = spmv_per_sm<float, short>(A->cap32) * A->num_sms;
