@@ -45,9 +45,11 @@ def workload_name(N, nnz=None):
 # DRAM traffic of one k_spmv_w<short> launch (a root step of the p(A) chain, C2 matrix) from the ncu
 # capture summarised in profiles/k_spmv_c2_128cubed.md, and the kernel source it was taken with: when the
 # source changes, the number no longer describes the kernel and the bench reports null.
-SPMV_TRAFFIC = {"src_sha256_16": "ff8c285059ba7f8c", "dram_bytes": 113426944 + 6853120,
+SPMV_TRAFFIC = {"src_sha256_16": "bc5d0aba73812cc0", "dram_bytes": 105299456 + 6657792,
                 "algorithmic_bytes": 112656384 + 16777216,
-                "launch": "k_spmv_w<short> root step (gather P from staged windows; write Y and P'), ncu --set full, cold caches"}
+                "launch": "k_spmv_e root step (tile-ELL values and window indices, x windows staged in "
+                          "shared memory; write Y and P'), ncu --set full, cold caches; most of the 16.8 MB "
+                          "of writes are still in L2 when the kernel ends"}
 
 
 def spmv_traffic():
@@ -358,7 +360,7 @@ def main():
         "iterations": last["iterations"], "restarts": last["restarts"], "relres_true": last["relres_true"],
         "relres_host_check": relres_host,
         "roofline": {"bound": "hbm",
-                     "kernel": ("k_spmv_w<short> (x windows staged in shared memory)"
+                     "kernel": ("k_spmv_e (tile-ELL blocks, x windows staged in shared memory)"
                                 if prec == ppg.PPG_F32 and s.spmv_format() == ppg.PPG_SPMV_STAGED
                                 else "k_spmv<float>" if prec == ppg.PPG_F32 else "k_spmv<double>")
                                + ": the SpMV chain, fused root steps of p(A) and the SpMV with A",

@@ -236,14 +236,21 @@ __device__ __forceinline__ F2 f2_add(F2 a, F2 b)
     return F2{hi, lo - (hi - s)};
 }
 
-// warp tree of compensated float32 sums, converted to float64 once
-__device__ __forceinline__ double warp_sum_f2(F2 v)
+// warp tree of compensated float32 sums (lane 0's result is the one used)
+__device__ __forceinline__ F2 warp_tree_f2(F2 v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const F2 w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
         v = f2_add(v, w);
     }
+    return v;
+}
+
+// the same, converted to float64 once
+__device__ __forceinline__ double warp_sum_f2(F2 v)
+{
+    v = warp_tree_f2(v);
     return (double)v.hi + (double)v.lo;
 }
 
@@ -300,6 +307,78 @@ __device__ __forceinline__ bool last_block_done(unsigned int *ticket, int *s_fla
         return true;
     }
     return false;
+}
+
+// block_sum_f2 without the conversion: the warp totals are added as compensated pairs too, by
+// thread 0 in warp order.  Every thread must call it; the result is valid in every thread.
+__device__ __forceinline__ F2 block_sum_f2_pair(F2 v, F2 *scratch /* >= 33 */)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_tree_f2(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        F2 t = scratch[0];
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) t = f2_add(t, scratch[q]);
+        scratch[32] = t;
+    }
+    __syncthreads();
+    return scratch[32];
+}
+
+// Deterministic sums of per-CTA partial slots slot[c * ld + b], b < nblk, for one column c by one
+// warp, with many loads in flight: lane l takes the slot pairs (2q, 2q + 1) for q = l + 32 u in
+// increasing u, eight 16-byte loads at a time, then a fixed shuffle tree.  ld is even and the
+// slots are 16-byte aligned.  Float64 slots, or compensated float32 pairs (F2) in 8-byte slots.
+__device__ __forceinline__ double reduce_slots_f64(const double *slot, int ld, int nblk, int c)
+{
+    const int lane = threadIdx.x & 31;
+    const double2 *p = reinterpret_cast<const double2 *>(slot + (long long)c * ld);
+    const int npair = (nblk + 1) >> 1;
+    double s = 0.0;
+    for (int q0 = lane; q0 < npair; q0 += 32 * 8) {
+        double2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + 32 * u;
+            v[u] = q < npair ? __ldcg(p + q) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + 32 * u;
+            if (q < npair) {
+                s += v[u].x;
+                if (2 * q + 1 < nblk) s += v[u].y;
+            }
+        }
+    }
+    return warp_sum(s);
+}
+
+__device__ __forceinline__ double reduce_slots_f2(const double *slot, int ld, int nblk, int c)
+{
+    const int lane = threadIdx.x & 31;
+    const float4 *p = reinterpret_cast<const float4 *>(slot + (long long)c * ld);
+    const int npair = (nblk + 1) >> 1;
+    F2 s{0.f, 0.f};
+    for (int q0 = lane; q0 < npair; q0 += 32 * 8) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + 32 * u;
+            v[u] = q < npair ? __ldcg(p + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + 32 * u;
+            if (q < npair) {
+                s = f2_add(s, F2{v[u].x, v[u].y});
+                if (2 * q + 1 < nblk) s = f2_add(s, F2{v[u].z, v[u].w});
+            }
+        }
+    }
+    return warp_sum_f2(s);
 }
 
 // Deterministic reduction of partials[c * nblk + b] over b for one column c by one warp:

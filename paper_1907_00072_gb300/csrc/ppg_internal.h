@@ -80,6 +80,7 @@ struct DevMatrix {
     const int *toff;      // ntiles + 1
     int ewmax;            // widest tile (entries per row)
     int spmve_blocks;     // persistent grid of the tile-ELL kernel
+    int spmvex_blocks;    // the same with a second staged input (A (x + s2 x2))
     int spmvw_blocks32;   // persistent grid of the staged kernel
     // sliced ELL copy (slices of 32 rows; entry k of row 32 s + l at sptr[s] + 32 k + l, slices padded
     // to their longest row with a sentinel index), used by the SpMV when format == kFmtSell

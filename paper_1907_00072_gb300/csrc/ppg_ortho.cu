@@ -64,8 +64,21 @@ template <typename T>
 struct Acc {
     double s = 0.0;
     __device__ __forceinline__ void add(double v) { s += v; }
-    __device__ __forceinline__ double warp_total() const { return warp_sum(s); }
-    __device__ __forceinline__ double block_total(double *scratch) const { return block_sum(s, scratch); }
+    // every lane calls these; lane 0 (thread 0) stores the slot
+    __device__ __forceinline__ void store_warp_total(double *slot) const
+    {
+        const double v = warp_sum(s);
+        if ((threadIdx.x & 31) == 0) *slot = v;
+    }
+    __device__ __forceinline__ void store_block_total(double *slot, double *scratch) const
+    {
+        const double v = block_sum(s, scratch);
+        if (threadIdx.x == 0) *slot = v;
+    }
+    static __device__ __forceinline__ double reduce(const double *slots, int ld, int nblk, int c)
+    {
+        return reduce_slots_f64(slots, ld, nblk, c);
+    }
 };
 template <>
 struct Acc<float> {
@@ -77,9 +90,22 @@ struct Acc<float> {
         c = (t - s) - y;
         s = t;
     }
-    // across lanes and warps with compensated float32 sums (see F2)
-    __device__ __forceinline__ double warp_total() const { return warp_sum_f2(F2{s, -c}); }
-    __device__ __forceinline__ double block_total(double *scratch) const { return block_sum_f2(F2{s, -c}, scratch); }
+    // across lanes, warps and CTAs with compensated float32 sums (see F2), kept as pairs until
+    // the final column sum
+    __device__ __forceinline__ void store_warp_total(double *slot) const
+    {
+        const F2 v = warp_tree_f2(F2{s, -c});
+        if ((threadIdx.x & 31) == 0) *reinterpret_cast<float2 *>(slot) = make_float2(v.hi, v.lo);
+    }
+    __device__ __forceinline__ void store_block_total(double *slot, double *scratch) const
+    {
+        const F2 v = block_sum_f2_pair(F2{s, -c}, reinterpret_cast<F2 *>(scratch));
+        if (threadIdx.x == 0) *reinterpret_cast<float2 *>(slot) = make_float2(v.hi, v.lo);
+    }
+    static __device__ __forceinline__ double reduce(const double *slots, int ld, int nblk, int c)
+    {
+        return reduce_slots_f2(slots, ld, nblk, c);
+    }
 };
 
 // ---------------------------------------------------------------- finalisation (last CTA)
@@ -102,27 +128,49 @@ __device__ void cta_finish_pass12(Cycle *st, const double *tot, int k, double *h
 }
 
 // Publishes the iteration count and the end-of-cycle flag to the host-mapped progress word, so
-// that the host stops enqueueing a cycle's iterations once it has ended.
-__device__ void publish_progress(const Cycle *st)
+// that the host stops enqueueing a cycle's iterations once it has ended.  The host uses the word
+// only to pace its launches (anything it acts on is read after the stream has synchronised), so
+// the store needs no fence.
+__device__ void publish_progress(const Cycle *st, int cycle_done, int j)
 {
-    if (st->prog) {
-        __threadfence_system();
-        *(volatile int *)st->prog = (st->cycle_done << 16) | st->j;
-    }
+    if (st->prog) *(volatile int *)st->prog = (cycle_done << 16) | j;
 }
 
 // Pass 3: completes Hessenberg column j, H[0..j, j] = h1 + h2, H[j+1, j] = ||v_{j+1}||.  In GMRES
 // mode the previous Givens rotations are applied to the column, a new rotation zeroes H[j+1, j]
 // and updates g; the cycle ends on a small estimate |g_{j+1}|, a breakdown, the restart length or
 // the iteration limit, and then y = R^{-1} g is formed and the coefficients of the correction
-// z = V y are left in coef.  sh: shared scratch of sh_bytes (at least 3 (kKmax + 1) doubles).
-__device__ void cta_finish_pass3(Cycle *st, double nsq, double *sh, size_t sh_bytes, int *s_int)
+// z = V y are left in coef.  sh: shared scratch of sh_bytes (at least 5 (kKmax + 2) doubles).
+//
+// Float64 instructions are scarce on this GPU, so the serial part is kept short: the rotations
+// form the recurrence a_{i+1} = -s_i a_i + c_i b_{i+1} (a_0 = b_0, b = the column as built),
+// whose products c_i b_{i+1} and rotated entries c_i a_i + s_i b_{i+1} are formed by all
+// threads, leaving one multiply-add per step to thread 0; the norm and its reciprocal are
+// formed by another warp meanwhile, and the state's scalars are loaded up front.
+__device__ void cta_finish_pass3(Cycle *st, int j, double nsq, double *sh, size_t sh_bytes, int *s_int)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int j = st->j;
-    double *col = sh;                // column j as built, then rotated (j + 2 values)
-    double *cs = sh + (kKmax + 1);   // rotations 0 .. j-1
-    double *sn = cs + kKmax;
+    double *col = sh;                // column j as built (j + 1 values)
+    double *cs = sh + (kKmax + 2);   // rotations 0 .. j-1
+    double *sn = cs + (kKmax + 2);
+    double *cb = sn + (kKmax + 2);   // cs[i] col[i+1]
+    double *ar = cb + (kKmax + 2);   // a_i, then the rotated column (j + 2 values)
+    __shared__ double s_nrm[2];      // ||v_{j+1}||, sigma_{j+1}
+    // thread 0's scalars, loaded before any store
+    long long iters = 0, maxit = 0;
+    int m = 0;
+    double gj = 0.0, bnorm = 0.0, tol = 0.0, irtol = 0.0, beta = 0.0;
+    if (tid == 0) {
+        iters = st->iters;
+        maxit = st->maxit;
+        m = st->m;
+        gj = st->g[j];
+        bnorm = st->bnorm;
+        tol = st->tol;
+        irtol = st->inner_rtol;
+        beta = st->beta;
+    }
+    const bool gm = st->mode == 0;
     if (tid == 0) s_int[0] = 0;
     __syncthreads();
     for (int i = tid; i <= j; i += nt) {
@@ -130,18 +178,35 @@ __device__ void cta_finish_pass3(Cycle *st, double nsq, double *sh, size_t sh_by
         col[i] = h;
         st->H[(long long)j * kLdH + i] = h;
         if (!isfinite(h)) s_int[0] = 1;
-    }
-    if (st->mode == 0)
-        for (int i = tid; i < j; i += nt) {
-            cs[i] = st->cs[i];
-            sn[i] = st->sn[i];
+        if (gm && i < j) {
+            const double c = st->cs[i], sv = st->sn[i];
+            cs[i] = c;
+            sn[i] = sv;
+            cb[i] = c * (st->h1[i + 1] + st->h2[i + 1]);
         }
+    }
     __syncthreads();
+    if (tid == 0 && gm) {
+        double a = col[0];
+        for (int i = 0; i < j; ++i) {
+            ar[i] = a;
+            a = fma(-sn[i], a, cb[i]);
+        }
+        ar[j] = a;
+    } else if (tid == 32) {
+        const double nrm = sqrt(nsq);
+        const bool brk = !(nrm > 1e-14 * sqrt(st->w0sq));
+        s_nrm[0] = nrm;
+        s_nrm[1] = brk ? 0.0 : 1.0 / nrm;
+        s_int[2] = brk;
+    }
+    __syncthreads();
+    if (gm)
+        for (int i = tid; i < j; i += nt) ar[i] = fma(cs[i], ar[i], sn[i] * col[i + 1]);
     if (tid == 0) {
         int kdone = 0;
-        const double nrm = sqrt(nsq);
+        const double nrm = s_nrm[0];
         st->H[(long long)j * kLdH + j + 1] = nrm;
-        col[j + 1] = nrm;
         if (s_int[0] || !isfinite(nrm)) {
             st->error |= kErrNonfinite;
             st->stop = 1;
@@ -149,18 +214,14 @@ __device__ void cta_finish_pass3(Cycle *st, double nsq, double *sh, size_t sh_by
             st->k = 0;
             st->j = j + 1;
             kdone = -1;
+            publish_progress(st, 1, j + 1);
         } else {
-            const bool brk = !(nrm > 1e-14 * sqrt(st->w0sq));
-            st->sigma[j + 1] = brk ? 0.0 : 1.0 / nrm;
-            st->iters += 1;
-            bool done = brk || (j + 1 >= st->m) || (st->iters >= st->maxit);
-            if (st->mode == 0) {
-                for (int i = 0; i < j; ++i) {
-                    const double a = col[i], b = col[i + 1];
-                    col[i] = cs[i] * a + sn[i] * b;
-                    col[i + 1] = -sn[i] * a + cs[i] * b;
-                }
-                const double a = col[j], b = col[j + 1];
+            const bool brk = s_int[2] != 0;
+            st->sigma[j + 1] = s_nrm[1];
+            st->iters = iters + 1;
+            bool done = brk || (j + 1 >= m) || (iters + 1 >= maxit);
+            if (gm) {
+                const double a = ar[j], b = nrm;
                 const double r = hypot(a, b);
                 double c = 1.0, s = 0.0;
                 if (r != 0.0) {
@@ -169,15 +230,13 @@ __device__ void cta_finish_pass3(Cycle *st, double nsq, double *sh, size_t sh_by
                 }
                 st->cs[j] = c;
                 st->sn[j] = s;
-                col[j] = r;
-                col[j + 1] = 0.0;
-                const double gj = st->g[j];
+                ar[j] = r;
+                ar[j + 1] = 0.0;
                 st->g[j] = c * gj;
                 st->g[j + 1] = -s * gj;
                 const double res = fabs(s * gj);
-                st->est = res / st->bnorm;
-                done = done || (res <= st->tol * st->bnorm) ||
-                       (st->inner_rtol > 0.0 && res <= st->inner_rtol * st->beta);
+                st->est = res / bnorm;
+                done = done || (res <= tol * bnorm) || (irtol > 0.0 && res <= irtol * beta);
             }
             if (brk) {
                 st->breakdown = 1;
@@ -188,22 +247,24 @@ __device__ void cta_finish_pass3(Cycle *st, double nsq, double *sh, size_t sh_by
                 st->k = j + 1;
                 st->cycle_done = 1;
                 kdone = j + 1;
+            } else {
+                publish_progress(st, 0, j + 1);
             }
         }
         s_int[1] = kdone;
     }
     __syncthreads();
     const int kdone = s_int[1];
-    if (kdone >= 0 && st->mode == 0)
-        for (int i = tid; i <= j + 1; i += nt) st->R[(long long)j * kLdH + i] = col[i];
-    if (kdone > 0 && st->mode == 0) {
+    if (kdone >= 0 && gm)
+        for (int i = tid; i <= j + 1; i += nt) st->R[(long long)j * kLdH + i] = ar[i];
+    if (kdone > 0 && gm) {
         // y = R^{-1} g (k = kdone): R staged in shared memory when it fits, then column-oriented
         // back substitution by warp 0 (y_i = g_i / R_ii, then g_q -= R_qi y_i for q < i in parallel)
         const int k = kdone;
         double *g = sh;            // k values
         double *Rs = sh + k;       // k x k, column-major, ld k
         const bool staged = (size_t)(k + k * k) * sizeof(double) <= sh_bytes;
-        __syncthreads();           // col, cs, sn no longer needed
+        __syncthreads();           // col, cs, sn, ar no longer needed
         for (int i = tid; i < k; i += nt) g[i] = st->g[i];
         if (staged)
             for (int e = tid; e < k * k; e += nt) {
@@ -229,7 +290,7 @@ __device__ void cta_finish_pass3(Cycle *st, double nsq, double *sh, size_t sh_by
         }
     }
     __syncthreads();
-    if (tid == 0) publish_progress(st);
+    if (tid == 0 && kdone > 0) publish_progress(st, 1, j + 1);
 }
 
 // ---------------------------------------------------------------- the pass kernel
@@ -250,7 +311,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
     __shared__ double s_red[KM + 1];
     __shared__ double scratch[33];
     __shared__ int s_last;
-    __shared__ int s_int[2];
+    __shared__ int s_int[3];
     __shared__ int s_timeout;
 
     const int op = a.op;
@@ -450,33 +511,28 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
         return;
     }
 
-    // per-CTA partial sums
-    if ((op == kGsDot || op == kGsUpdDot) && !prod) {
+    // per-CTA partial sums: one 8-byte slot per column and CTA (a compensated float32 pair for the
+    // float32 basis), column stride pld = nblk rounded up to even so that slots load in pairs
+    const int pld = (a.nblk + 1) & ~1;
+    const bool want_dots = op == kGsDot || op == kGsUpdDot;
+    const bool want_norm = op == kGsDot || op == kGsUpdNorm;
+    if (want_dots && !prod) {
 #pragma unroll
         for (int i = 0; i < CPW; ++i) {
             const int c = wid + 8 * i;
-            if (c < k) {
-                const double v = acc[i].warp_total();
-                if (lane == 0) a.partials[(long long)c * a.nblk + blockIdx.x] = v;
-            }
+            if (c < k) acc[i].store_warp_total(a.partials + (long long)c * pld + blockIdx.x);
         }
     }
-    if (op != kGsCombine) {
-        const double nsum = nrm.block_total(scratch);
-        if (tid == 0) a.partials[(long long)kKmax * a.nblk + blockIdx.x] = nsum;
-    }
+    if (want_norm) nrm.store_block_total(a.partials + (long long)kKmax * pld + blockIdx.x, scratch);
     if (op == kGsCombine) return;
 
     if (last_block_done(&st->ticket[2 + op], &s_last)) {
-        if (op != kGsUpdNorm && !prod) {
-            for (int c = wid; c < k; c += 8) {
-                const double v = reduce_partials(a.partials, a.nblk, c);
-                if (lane == 0) s_red[c] = v;
-            }
-        }
-        if (wid == 0) {
-            const double v = reduce_partials(a.partials, a.nblk, kKmax);
-            if (lane == 0) s_red[KM] = v;
+        // the column sums (and the norm, as job k) spread over all nine warps
+        const int njobs = (want_dots ? k : 0) + (want_norm ? 1 : 0);
+        for (int q = wid; q < njobs; q += kGsThreads / 32) {
+            const bool is_norm = !want_dots || q == k;
+            const double v = Acc<T>::reduce(a.partials, pld, a.nblk, is_norm ? kKmax : q);
+            if (lane == 0) s_red[is_norm ? KM : q] = v;
         }
         __syncthreads();
         if (op == kGsDot)
@@ -484,7 +540,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
         else if (op == kGsUpdDot)
             cta_finish_pass12(st, s_red, k, st->h2, false, 0.0);
         else
-            cta_finish_pass3(st, s_red[KM], reinterpret_cast<double *>(smem),
+            cta_finish_pass3(st, k - 1, s_red[KM], reinterpret_cast<double *>(smem),
                              (size_t)nst * (size_t)SS * sizeof(T), s_int);
         if (tid == 0) st->ticket[2 + op] = 0;
     }

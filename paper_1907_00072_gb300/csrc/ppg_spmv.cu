@@ -863,11 +863,13 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_w(Sp
 // As k_spmv_w for one lane per row, with each tile stored as a dense R x w block (entry k of row l
 // at k R + l): the stage holds the block's values and window indices and the tile's x windows plus a
 // zero at index kXCap for the padding, so a row is w shared-memory multiply-adds with no row pointers
-// or bounds tests.  Same arithmetic as k_spmv (padding adds 0 * 0).
-__host__ __device__ constexpr size_t spmve_stage_bytes(int wmax)
+// or bounds tests.  Same arithmetic as k_spmv (padding adds 0 * 0).  X2: the epilogue's second input
+// x2 (A (x + s2 x2)) is staged too, over the same windows, and combined per gathered entry as k_spmv
+// does.
+__host__ __device__ constexpr size_t spmve_stage_bytes(int wmax, bool x2 = false)
 {
     return round128((size_t)kThreads * wmax * 4) + round128((size_t)kThreads * wmax * 2) +
-           round128((size_t)(kXCap + 4) * 4) + 128;
+           (x2 ? 2 : 1) * round128((size_t)(kXCap + 4) * 4) + 128;
 }
 
 struct SpmvEArgs {
@@ -882,6 +884,7 @@ struct SpmvEArgs {
     SpmvEpi e;
 };
 
+template <bool X2>
 __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(SpmvEArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -893,10 +896,11 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
 
     Cycle *st = a.st;
     const long long ntiles = ((long long)a.n + R - 1) / R;
-    const size_t stage_bytes = spmve_stage_bytes(a.wmax);
+    const size_t stage_bytes = spmve_stage_bytes(a.wmax, X2);
     const size_t ix_off = round128((size_t)R * a.wmax * 4);
     const size_t xw_off = ix_off + round128((size_t)R * a.wmax * 2);
-    const size_t hd_off = xw_off + round128((size_t)(kXCap + 4) * 4);
+    constexpr size_t kXwBytes = round128((size_t)(kXCap + 4) * 4);
+    const size_t hd_off = xw_off + (X2 ? 2 : 1) * kXwBytes;
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int prefetched = (int)min((long long)kSpmvStages, my_tiles);
@@ -911,6 +915,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
     if (tid < kSpmvStages * 4) {  // the zero the padding indexes, in every stage (no copy writes there)
         T *z = reinterpret_cast<T *>(smem + (tid / 4) * stage_bytes + xw_off);
         z[kXCap + (tid & 3)] = T(0);
+        if (X2) z[kXwBytes / 4 + kXCap + (tid & 3)] = T(0);
     }
     __syncthreads();
 
@@ -936,17 +941,20 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                 }
                 reinterpret_cast<int *>(base + hd_off)[0] = (int)(nb / R);
             };
-            const T *x = nullptr;
+            const T *x = nullptr, *x2 = nullptr;
             auto issue_vectors = [&](int s, const int4 lo4, const int4 ln4) {
                 unsigned char *base = smem + s * stage_bytes;
                 const int lo[kXWin] = {lo4.x, lo4.y, lo4.z, lo4.w};
                 const int ln[kXWin] = {ln4.x, ln4.y, ln4.z, ln4.w};
                 uint32_t bytes = 0;
                 for (int w = 0; w < kXWin; ++w) bytes += (uint32_t)ln[w] * 4u;
-                mbar_arrive_expect_tx(&full[s], bytes);
+                mbar_arrive_expect_tx(&full[s], X2 ? 2 * bytes : bytes);
                 for (int w = 0, o = 0; w < kXWin; ++w)
                     if (ln[w] > 0) {
                         bulk_g2s(base + xw_off + (size_t)o * 4, x + lo[w], (uint32_t)ln[w] * 4u, &full[s]);
+                        if (X2)
+                            bulk_g2s(base + xw_off + kXwBytes + (size_t)o * 4, x2 + lo[w], (uint32_t)ln[w] * 4u,
+                                     &full[s]);
                         o += ln[w];
                     }
             };
@@ -969,6 +977,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                         break;
                     }
                     x = resolve_ptr<T>(a.e.x, st);
+                    if (X2) x2 = resolve_ptr<T>(a.e.x2, st);
                     for (int q = 0; q < prefetched; ++q) issue_vectors(q, dlo[q], dln[q]);
                 }
                 const int o0 = no0, o1 = no1;
@@ -997,6 +1006,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                     for (int q = 0; q < i; ++q) mbar_arrive(&full[q]);
                 } else {
                     x = resolve_ptr<T>(a.e.x, st);
+                    if (X2) x2 = resolve_ptr<T>(a.e.x2, st);
                     for (int q = 0; q < i; ++q) issue_vectors(q, dlo[q], dln[q]);
                 }
             }
@@ -1032,6 +1042,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
     const T *w1 = resolve_ptr<T>(a.e.w1, st);
     const T ca0 = (T)s_coef[0], cb0 = (T)s_coef[1], cc0 = (T)s_coef[2];
     const T ca1 = (T)s_coef[3], cb1 = (T)s_coef[4], cc1 = (T)s_coef[5];
+    const T c2 = (T)s_coef[6];
     int i = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
         const int s = i % kSpmvStages;
@@ -1058,8 +1069,17 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
         const T *s_x = reinterpret_cast<const T *>(base + xw_off);
         const int w = reinterpret_cast<const int *>(base + hd_off)[0];
         T acc = T(0);
+        if (X2) {
+            const T *s_x2 = s_x + kXwBytes / 4;
 #pragma unroll 8
-        for (int k = 0; k < w; ++k) acc = fma(s_val[k * R + tid], s_x[s_ix[k * R + tid]], acc);
+            for (int k = 0; k < w; ++k) {
+                const int q = s_ix[k * R + tid];
+                acc = fma(s_val[k * R + tid], fma(c2, s_x2[q], s_x[q]), acc);
+            }
+        } else {
+#pragma unroll 8
+            for (int k = 0; k < w; ++k) acc = fma(s_val[k * R + tid], s_x[s_ix[k * R + tid]], acc);
+        }
         if (ok) {
             T v = ca0 * acc;
             if (u0) v = fma(cb0, pu0, v);
@@ -1593,7 +1613,8 @@ cudaError_t spmvw_go(const DevMatrix &A, const IDX *cols, const SpmvEpi &e, Cycl
                      bool *launched)
 {
     *launched = false;
-    if (e.x2.base || !vec_aligned(e.x)) return cudaSuccess;
+    if (!vec_aligned(e.x) || (e.x2.base && !(vec_aligned(e.x2) && A.evals && A.spmvex_blocks > 0)))
+        return cudaSuccess;
     SpmvWArgs<IDX> p{};
     const VecRef *ops[4] = {&e.u0, &e.w0, &e.u1, &e.w1};
     p.nslot = 0;
@@ -1615,11 +1636,13 @@ cudaError_t spmvw_go(const DevMatrix &A, const IDX *cols, const SpmvEpi &e, Cycl
     const long long ntiles = ((long long)A.n + R - 1) / R;
     if (A.evals && A.spmve_blocks > 0) {
         SpmvEArgs q{A.n, A.evals, A.eidx, A.toff, A.twin, A.ewmax, st, check_done, e};
-        long long g = A.spmve_blocks;
+        const bool x2 = e.x2.base != nullptr;
+        long long g = x2 ? A.spmvex_blocks : A.spmve_blocks;
         if (g > ntiles) g = ntiles;
         *launched = true;
-        return launch_pdl(k_spmv_e, dim3((unsigned)g), dim3(kSpmvThreads), kSpmvStages * spmve_stage_bytes(A.ewmax), s,
-                          q);
+        const size_t smem = kSpmvStages * spmve_stage_bytes(A.ewmax, x2);
+        return x2 ? launch_pdl(k_spmv_e<true>, dim3((unsigned)g), dim3(kSpmvThreads), smem, s, q)
+                  : launch_pdl(k_spmv_e<false>, dim3((unsigned)g), dim3(kSpmvThreads), smem, s, q);
     }
     p.a = SpmvArgs<float, IDX>{A.n, A.rowptr, cols, A.vals32, R, A.lanes_per_row, A.cap32, st, check_done, e};
     p.lidx = A.lidx;
@@ -1665,8 +1688,11 @@ cudaError_t spmv_set_smem()
         e = cudaFuncSetAttribute(k_spmv_w<IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kSpmvStages * spmvw_stage_bytes(kSpmvCapMax, (int)sizeof(IDX))));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spmv_e, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_spmv_e<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kSpmvStages * spmve_stage_bytes(16)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spmv_e<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kSpmvStages * spmve_stage_bytes(16, true)));
     return e;
 }
 
@@ -1721,10 +1747,15 @@ cudaError_t launch_spmv2(const DevMatrix &A, int prec, const SpmvEpi &e1, const 
                                 ticket, diag, s);
 }
 
-int spmve_per_sm(int wmax)
+int spmve_per_sm(int wmax, bool x2)
 {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e, kSpmvThreads, kSpmvStages * spmve_stage_bytes(wmax));
+    if (x2)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e<true>, kSpmvThreads,
+                                                      kSpmvStages * spmve_stage_bytes(wmax, true));
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e<false>, kSpmvThreads,
+                                                      kSpmvStages * spmve_stage_bytes(wmax));
     return nb > 0 ? nb : 0;
 }
 
@@ -1741,7 +1772,8 @@ cudaError_t spmv_configure(DevMatrix *A)
         if (err != cudaSuccess) return err;
         done = true;
     }
-    A->spmve_blocks = A->evals ? spmve_per_sm(A->ewmax) * A->num_sms : 0;
+    A->spmve_blocks = A->evals ? spmve_per_sm(A->ewmax, false) * A->num_sms : 0;
+    A->spmvex_blocks = A->evals ? spmve_per_sm(A->ewmax, true) * A->num_sms : 0;
     if (A->coloff) {
         A->spmv_blocks64 = spmv_per_sm<double, short>(A->cap64) * A->num_sms;
         A->spmv_blocks32 = spmv_per_sm<float, short>(A->cap32) * A->num_sms;
