@@ -329,23 +329,26 @@ __device__ __forceinline__ F2 block_sum_f2_pair(F2 v, F2 *scratch /* >= 33 */)
 
 // Deterministic sums of per-CTA partial slots slot[c * ld + b], b < nblk, for one column c by one
 // warp, with many loads in flight: lane l takes the slot pairs (2q, 2q + 1) for q = l + 32 u in
-// increasing u, eight 16-byte loads at a time, then a fixed shuffle tree.  ld is even and the
+// increasing u, kSlotLoads 16-byte loads at a time (one round for up to 512 CTAs), then a fixed
+// shuffle tree.  ld is even and the
 // slots are 16-byte aligned.  Float64 slots, or compensated float32 pairs (F2) in 8-byte slots.
+constexpr int kSlotLoads = 8;
+
 __device__ __forceinline__ double reduce_slots_f64(const double *slot, int ld, int nblk, int c)
 {
     const int lane = threadIdx.x & 31;
     const double2 *p = reinterpret_cast<const double2 *>(slot + (long long)c * ld);
     const int npair = (nblk + 1) >> 1;
     double s = 0.0;
-    for (int q0 = lane; q0 < npair; q0 += 32 * 8) {
-        double2 v[8];
+    for (int q0 = lane; q0 < npair; q0 += 32 * kSlotLoads) {
+        double2 v[kSlotLoads];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kSlotLoads; ++u) {
             const int q = q0 + 32 * u;
             v[u] = q < npair ? __ldcg(p + q) : make_double2(0.0, 0.0);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kSlotLoads; ++u) {
             const int q = q0 + 32 * u;
             if (q < npair) {
                 s += v[u].x;
@@ -362,15 +365,15 @@ __device__ __forceinline__ double reduce_slots_f2(const double *slot, int ld, in
     const float4 *p = reinterpret_cast<const float4 *>(slot + (long long)c * ld);
     const int npair = (nblk + 1) >> 1;
     F2 s{0.f, 0.f};
-    for (int q0 = lane; q0 < npair; q0 += 32 * 8) {
-        float4 v[8];
+    for (int q0 = lane; q0 < npair; q0 += 32 * kSlotLoads) {
+        float4 v[kSlotLoads];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kSlotLoads; ++u) {
             const int q = q0 + 32 * u;
             v[u] = q < npair ? __ldcg(p + q) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kSlotLoads; ++u) {
             const int q = q0 + 32 * u;
             if (q < npair) {
                 s = f2_add(s, F2{v[u].x, v[u].y});

@@ -114,19 +114,6 @@ struct Acc<float> {
 // an L2 round trip; the last CTA therefore does the per-column work with all its threads and
 // runs the serial recurrences (Givens rotations, back substitution) on shared-memory copies.
 
-// Passes 1 and 2: h = sigma .* tot (the pass's Hessenberg coefficients of v_0..v_{k-1}) and the
-// coefficients the next update multiplies the stored columns by (coef = h .* sigma).
-__device__ void cta_finish_pass12(Cycle *st, const double *tot, int k, double *h_out, bool pass1, double wsq)
-{
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        const double sg = st->sigma[c];
-        const double h = sg * tot[c];
-        h_out[c] = h;
-        st->coef[c] = h * sg;
-    }
-    if (pass1 && threadIdx.x == 0) st->w0sq = wsq;
-}
-
 // Publishes the iteration count and the end-of-cycle flag to the host-mapped progress word, so
 // that the host stops enqueueing a cycle's iterations once it has ended.  The host uses the word
 // only to pace its launches (anything it acts on is read after the stream has synchronised), so
@@ -140,52 +127,63 @@ __device__ void publish_progress(const Cycle *st, int cycle_done, int j)
 // mode the previous Givens rotations are applied to the column, a new rotation zeroes H[j+1, j]
 // and updates g; the cycle ends on a small estimate |g_{j+1}|, a breakdown, the restart length or
 // the iteration limit, and then y = R^{-1} g is formed and the coefficients of the correction
-// z = V y are left in coef.  sh: shared scratch of sh_bytes (at least 5 (kKmax + 2) doubles).
+// z = V y are left in coef.  ||v_{j+1}||^2 is the sum of the CTAs' norm slots.  sh: shared
+// scratch of sh_bytes (at least 5 (kKmax + 2) doubles).
 //
-// Float64 instructions are scarce on this GPU, so the serial part is kept short: the rotations
-// form the recurrence a_{i+1} = -s_i a_i + c_i b_{i+1} (a_0 = b_0, b = the column as built),
-// whose products c_i b_{i+1} and rotated entries c_i a_i + s_i b_{i+1} are formed by all
-// threads, leaving one multiply-add per step to thread 0; the norm and its reciprocal are
-// formed by another warp meanwhile, and the state's scalars are loaded up front.
-__device__ void cta_finish_pass3(Cycle *st, int j, double nsq, double *sh, size_t sh_bytes, int *s_int)
+// Float64 instructions are scarce on this GPU, so the serial part is kept short: warp 0 sums the
+// norm slots while the other warps stage the column, the rotations and the state's scalars; the
+// rotations form the recurrence a_{i+1} = -s_i a_i + c_i b_{i+1} (a_0 = b_0, b = the column as
+// built), whose products c_i b_{i+1} and rotated entries c_i a_i + s_i b_{i+1} are formed by all
+// threads, leaving one multiply-add per step to thread 0, while warp 1 forms the norm and its
+// reciprocal.
+template <typename T>
+__device__ void cta_finish_pass3(Cycle *st, int j, const double *slots, int pld, int nblk, double *sh,
+                                 size_t sh_bytes, int *s_int)
 {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, wid = tid >> 5, lane = tid & 31;
     double *col = sh;                // column j as built (j + 1 values)
     double *cs = sh + (kKmax + 2);   // rotations 0 .. j-1
     double *sn = cs + (kKmax + 2);
     double *cb = sn + (kKmax + 2);   // cs[i] col[i+1]
     double *ar = cb + (kKmax + 2);   // a_i, then the rotated column (j + 2 values)
-    __shared__ double s_nrm[2];      // ||v_{j+1}||, sigma_{j+1}
-    // thread 0's scalars, loaded before any store
-    long long iters = 0, maxit = 0;
-    int m = 0;
-    double gj = 0.0, bnorm = 0.0, tol = 0.0, irtol = 0.0, beta = 0.0;
-    if (tid == 0) {
-        iters = st->iters;
-        maxit = st->maxit;
-        m = st->m;
-        gj = st->g[j];
-        bnorm = st->bnorm;
-        tol = st->tol;
-        irtol = st->inner_rtol;
-        beta = st->beta;
-    }
-    const bool gm = st->mode == 0;
+    // [0] ||v||^2  [1] ||v||  [2] sigma_{j+1}  [3] g_j  [4] tol ||b||  [5] inner_rtol beta (or -1)
+    // [6] 1 / ||b||  [7] breakdown threshold on ||v||^2
+    __shared__ double sc[8];
+    __shared__ long long s_it[2];  // iters, maxit
+    __shared__ int s_m[2];         // restart length, mode
     if (tid == 0) s_int[0] = 0;
     __syncthreads();
-    for (int i = tid; i <= j; i += nt) {
-        const double h = st->h1[i] + st->h2[i];
-        col[i] = h;
-        st->H[(long long)j * kLdH + i] = h;
-        if (!isfinite(h)) s_int[0] = 1;
-        if (gm && i < j) {
-            const double c = st->cs[i], sv = st->sn[i];
-            cs[i] = c;
-            sn[i] = sv;
-            cb[i] = c * (st->h1[i + 1] + st->h2[i + 1]);
+    if (wid == 0) {
+        const double v = Acc<T>::reduce(slots, pld, nblk, kKmax);
+        if (lane == 0) sc[0] = v;
+    } else {
+        if (tid == nt - 1) {
+            s_it[0] = st->iters;
+            s_it[1] = st->maxit;
+            s_m[0] = st->m;
+            s_m[1] = st->mode;
+            const double bn = st->bnorm, irt = st->inner_rtol;
+            sc[3] = st->g[j];
+            sc[4] = st->tol * bn;
+            sc[5] = irt > 0.0 ? irt * st->beta : -1.0;
+            sc[6] = 1.0 / bn;
+            sc[7] = 1e-28 * st->w0sq;
+        }
+        for (int i = tid - 32; i <= j; i += nt - 32) {
+            const double h = st->h1[i] + st->h2[i];
+            col[i] = h;
+            st->H[(long long)j * kLdH + i] = h;
+            if (!isfinite(h)) s_int[0] = 1;
+            if (i < j) {  // used in GMRES mode only
+                const double c = st->cs[i], sv = st->sn[i];
+                cs[i] = c;
+                sn[i] = sv;
+                cb[i] = c * (st->h1[i + 1] + st->h2[i + 1]);
+            }
         }
     }
     __syncthreads();
+    const bool gm = s_m[1] == 0;
     if (tid == 0 && gm) {
         double a = col[0];
         for (int i = 0; i < j; ++i) {
@@ -194,10 +192,10 @@ __device__ void cta_finish_pass3(Cycle *st, int j, double nsq, double *sh, size_
         }
         ar[j] = a;
     } else if (tid == 32) {
-        const double nrm = sqrt(nsq);
-        const bool brk = !(nrm > 1e-14 * sqrt(st->w0sq));
-        s_nrm[0] = nrm;
-        s_nrm[1] = brk ? 0.0 : 1.0 / nrm;
+        const double nsq = sc[0], nrm = sqrt(nsq);
+        const bool brk = !(nsq > sc[7]);
+        sc[1] = nrm;
+        sc[2] = brk ? 0.0 : 1.0 / nrm;
         s_int[2] = brk;
     }
     __syncthreads();
@@ -205,7 +203,7 @@ __device__ void cta_finish_pass3(Cycle *st, int j, double nsq, double *sh, size_
         for (int i = tid; i < j; i += nt) ar[i] = fma(cs[i], ar[i], sn[i] * col[i + 1]);
     if (tid == 0) {
         int kdone = 0;
-        const double nrm = s_nrm[0];
+        const double nrm = sc[1];
         st->H[(long long)j * kLdH + j + 1] = nrm;
         if (s_int[0] || !isfinite(nrm)) {
             st->error |= kErrNonfinite;
@@ -217,26 +215,29 @@ __device__ void cta_finish_pass3(Cycle *st, int j, double nsq, double *sh, size_
             publish_progress(st, 1, j + 1);
         } else {
             const bool brk = s_int[2] != 0;
-            st->sigma[j + 1] = s_nrm[1];
-            st->iters = iters + 1;
-            bool done = brk || (j + 1 >= m) || (iters + 1 >= maxit);
+            const long long it = s_it[0] + 1;
+            st->sigma[j + 1] = sc[2];
+            st->iters = it;
+            bool done = brk || (j + 1 >= s_m[0]) || (it >= s_it[1]);
             if (gm) {
-                const double a = ar[j], b = nrm;
-                const double r = hypot(a, b);
+                const double a = ar[j];
+                const double r = sqrt(fma(a, a, nrm * nrm));
                 double c = 1.0, s = 0.0;
                 if (r != 0.0) {
-                    c = a / r;
-                    s = b / r;
+                    const double ri = 1.0 / r;
+                    c = a * ri;
+                    s = nrm * ri;
                 }
                 st->cs[j] = c;
                 st->sn[j] = s;
                 ar[j] = r;
                 ar[j + 1] = 0.0;
+                const double gj = sc[3];
                 st->g[j] = c * gj;
                 st->g[j + 1] = -s * gj;
                 const double res = fabs(s * gj);
-                st->est = res / bnorm;
-                done = done || (res <= tol * bnorm) || (irtol > 0.0 && res <= irtol * beta);
+                st->est = res * sc[6];
+                done = done || (res <= sc[4]) || (res <= sc[5]);
             }
             if (brk) {
                 st->breakdown = 1;
@@ -288,9 +289,9 @@ __device__ void cta_finish_pass3(Cycle *st, int j, double nsq, double *sh, size_
             st->y[c] = y;
             st->coef[c] = -y * st->sigma[c];
         }
+        __syncthreads();
+        if (tid == 0) publish_progress(st, 1, j + 1);
     }
-    __syncthreads();
-    if (tid == 0 && kdone > 0) publish_progress(st, 1, j + 1);
 }
 
 // ---------------------------------------------------------------- the pass kernel
@@ -308,7 +309,6 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
     __shared__ T s_wn[TR];
     __shared__ T s_part[TPR > 1 ? TPR : 1][TPR > 1 ? TR : 1];
     __shared__ T s_coef[KM];
-    __shared__ double s_red[KM + 1];
     __shared__ double scratch[33];
     __shared__ int s_last;
     __shared__ int s_int[3];
@@ -527,21 +527,30 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
     if (op == kGsCombine) return;
 
     if (last_block_done(&st->ticket[2 + op], &s_last)) {
-        // the column sums (and the norm, as job k) spread over all nine warps
-        const int njobs = (want_dots ? k : 0) + (want_norm ? 1 : 0);
-        for (int q = wid; q < njobs; q += kGsThreads / 32) {
-            const bool is_norm = !want_dots || q == k;
-            const double v = Acc<T>::reduce(a.partials, pld, a.nblk, is_norm ? kKmax : q);
-            if (lane == 0) s_red[is_norm ? KM : q] = v;
+        if (op != kGsUpdNorm) {
+            // passes 1 and 2: each warp sums the slots of its columns and finalises them: the
+            // pass's Hessenberg coefficients h = sigma .* sum and the next update's coefficients
+            // coef = h .* sigma (sigma is loaded ahead of the sum); pass 1's norm is job k
+            double *h_out = op == kGsDot ? st->h1 : st->h2;
+            const int njobs = k + (want_norm ? 1 : 0);
+            for (int q = wid; q < njobs; q += kGsThreads / 32) {
+                const bool is_norm = q == k;
+                const double sg = (!is_norm && lane == 0) ? st->sigma[q] : 0.0;
+                const double v = Acc<T>::reduce(a.partials, pld, a.nblk, is_norm ? kKmax : q);
+                if (lane == 0) {
+                    if (is_norm) {
+                        st->w0sq = v;
+                    } else {
+                        const double h = sg * v;
+                        h_out[q] = h;
+                        st->coef[q] = h * sg;
+                    }
+                }
+            }
+        } else {
+            cta_finish_pass3<T>(st, k - 1, a.partials, pld, a.nblk, reinterpret_cast<double *>(smem),
+                                (size_t)nst * (size_t)SS * sizeof(T), s_int);
         }
-        __syncthreads();
-        if (op == kGsDot)
-            cta_finish_pass12(st, s_red, k, st->h1, true, s_red[KM]);
-        else if (op == kGsUpdDot)
-            cta_finish_pass12(st, s_red, k, st->h2, false, 0.0);
-        else
-            cta_finish_pass3(st, k - 1, s_red[KM], reinterpret_cast<double *>(smem),
-                             (size_t)nst * (size_t)SS * sizeof(T), s_int);
         if (tid == 0) st->ticket[2 + op] = 0;
     }
 }
