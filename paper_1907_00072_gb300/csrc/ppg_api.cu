@@ -1238,7 +1238,7 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
         std::vector<int> desc(ntiles * 2 * kXWin, 0);
         std::vector<short> lidx(nnz + 16, 0);  // per entry: its index in the tile's window buffer
         std::vector<int> cols;
-        long long windowed = 0;
+        long long windowed = 0, xmax = 0;
         for (long long t = 0; t < ntiles; ++t) {
             const long long r0 = t * R, r1 = std::min<long long>(n, r0 + R);
             cols.assign(hcol.begin() + hrp[r0], hcol.begin() + hrp[r1]);
@@ -1264,6 +1264,7 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
             long long total = 0;
             for (int w = 0; w < nw; ++w) total += hi[w] - lo[w];
             if (!ok || total > kXCap) continue;
+            xmax = std::max(xmax, total);
             int off[kXWin];
             for (int w = 0, o = 0; w < nw; ++w) {
                 desc[t * 2 * kXWin + w] = lo[w];
@@ -1289,7 +1290,7 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
         }
         // tile-ELL copy for one lane per row when every tile has windows: tile t is a dense R x w_t block
         // (entry k of row l at k R + l) of float32 values and window indices, padded with value 0 and
-        // the index kXCap of a zero kept after the windows
+        // the index xmax (the longest window total) of a zero kept after the windows
         if (c->A.twin && windowed == ntiles && R == kThreads) {
             std::vector<double> hval(nnz);
             PPG_CK(cudaMemcpy(hval.data(), c->d_vals, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
@@ -1309,7 +1310,7 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
             if (wmax > 0 && wmax <= 16) {
                 const size_t total = (size_t)toff[ntiles];
                 std::vector<float> ev(total + 16, 0.0f);
-                std::vector<short> ei(total + 16, (short)kXCap);
+                std::vector<short> ei(total + 16, (short)xmax);
                 for (long long t = 0; t < ntiles; ++t) {
                     const long long r0 = t * R, r1 = std::min<long long>(n, r0 + R);
                     for (long long r = r0; r < r1; ++r)
@@ -1329,6 +1330,7 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
                 c->A.eidx = c->d_eidx;
                 c->A.toff = c->d_toff;
                 c->A.ewmax = wmax;
+                c->A.excap = (int)xmax;
             }
         }
     }

@@ -79,6 +79,7 @@ struct DevMatrix {
     const short *eidx;
     const int *toff;      // ntiles + 1
     int ewmax;            // widest tile (entries per row)
+    int excap;            // longest window total over the tiles (the padding's zero sits at this index)
     int spmve_blocks;     // persistent grid of the tile-ELL kernel
     int spmvex_blocks;    // the same with a second staged input (A (x + s2 x2))
     int spmvw_blocks32;   // persistent grid of the staged kernel

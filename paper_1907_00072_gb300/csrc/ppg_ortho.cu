@@ -563,8 +563,12 @@ template <typename T, int KM>
 struct GsInst {
     static cudaError_t configure()
     {
-        return cudaFuncSetAttribute(k_gs<T, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    GsCfg<T, KM>::kSmemBudget);
+        cudaError_t e = cudaFuncSetAttribute(k_gs<T, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             GsCfg<T, KM>::kSmemBudget);
+        if (e == cudaSuccess)  // one L1 / shared-memory split for the kernels of an iteration
+            e = cudaFuncSetAttribute(k_gs<T, KM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+        return e;
     }
     static cudaError_t launch(GsArgs a, int kcols, long long ld, int num_sms, Cycle *st, cudaStream_t s)
     {

@@ -862,14 +862,14 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_w(Sp
 
 // As k_spmv_w for one lane per row, with each tile stored as a dense R x w block (entry k of row l
 // at k R + l): the stage holds the block's values and window indices and the tile's x windows plus a
-// zero at index kXCap for the padding, so a row is w shared-memory multiply-adds with no row pointers
-// or bounds tests.  Same arithmetic as k_spmv (padding adds 0 * 0).  X2: the epilogue's second input
+// zero at index xcap (the matrix's longest window total, at most kXCap) for the padding, so a row is
+// w shared-memory multiply-adds with no row pointers or bounds tests.  Same arithmetic as k_spmv (padding adds 0 * 0).  X2: the epilogue's second input
 // x2 (A (x + s2 x2)) is staged too, over the same windows, and combined per gathered entry as k_spmv
 // does.
-__host__ __device__ constexpr size_t spmve_stage_bytes(int wmax, bool x2 = false)
+__host__ __device__ constexpr size_t spmve_stage_bytes(int wmax, bool x2, int xcap)
 {
     return round128((size_t)kThreads * wmax * 4) + round128((size_t)kThreads * wmax * 2) +
-           (x2 ? 2 : 1) * round128((size_t)(kXCap + 4) * 4) + 128;
+           (x2 ? 2 : 1) * round128((size_t)(xcap + 4) * 4) + 128;
 }
 
 struct SpmvEArgs {
@@ -879,6 +879,7 @@ struct SpmvEArgs {
     const int *toff;
     const int *twin;
     int wmax;
+    int xcap;  // index of the zero after the windows (padding entries point there)
     Cycle *st;
     int check_done;
     SpmvEpi e;
@@ -896,11 +897,11 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
 
     Cycle *st = a.st;
     const long long ntiles = ((long long)a.n + R - 1) / R;
-    const size_t stage_bytes = spmve_stage_bytes(a.wmax, X2);
+    const size_t stage_bytes = spmve_stage_bytes(a.wmax, X2, a.xcap);
     const size_t ix_off = round128((size_t)R * a.wmax * 4);
     const size_t xw_off = ix_off + round128((size_t)R * a.wmax * 2);
-    constexpr size_t kXwBytes = round128((size_t)(kXCap + 4) * 4);
-    const size_t hd_off = xw_off + (X2 ? 2 : 1) * kXwBytes;
+    const size_t xw_bytes = round128((size_t)(a.xcap + 4) * 4);
+    const size_t hd_off = xw_off + (X2 ? 2 : 1) * xw_bytes;
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int prefetched = (int)min((long long)kSpmvStages, my_tiles);
@@ -914,8 +915,8 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
     }
     if (tid < kSpmvStages * 4) {  // the zero the padding indexes, in every stage (no copy writes there)
         T *z = reinterpret_cast<T *>(smem + (tid / 4) * stage_bytes + xw_off);
-        z[kXCap + (tid & 3)] = T(0);
-        if (X2) z[kXwBytes / 4 + kXCap + (tid & 3)] = T(0);
+        z[a.xcap + (tid & 3)] = T(0);
+        if (X2) z[xw_bytes / 4 + a.xcap + (tid & 3)] = T(0);
     }
     __syncthreads();
 
@@ -953,7 +954,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                     if (ln[w] > 0) {
                         bulk_g2s(base + xw_off + (size_t)o * 4, x + lo[w], (uint32_t)ln[w] * 4u, &full[s]);
                         if (X2)
-                            bulk_g2s(base + xw_off + kXwBytes + (size_t)o * 4, x2 + lo[w], (uint32_t)ln[w] * 4u,
+                            bulk_g2s(base + xw_off + xw_bytes + (size_t)o * 4, x2 + lo[w], (uint32_t)ln[w] * 4u,
                                      &full[s]);
                         o += ln[w];
                     }
@@ -1070,7 +1071,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
         const int w = reinterpret_cast<const int *>(base + hd_off)[0];
         T acc = T(0);
         if (X2) {
-            const T *s_x2 = s_x + kXwBytes / 4;
+            const T *s_x2 = s_x + xw_bytes / 4;
 #pragma unroll 8
             for (int k = 0; k < w; ++k) {
                 const int q = s_ix[k * R + tid];
@@ -1635,12 +1636,12 @@ cudaError_t spmvw_go(const DevMatrix &A, const IDX *cols, const SpmvEpi &e, Cycl
     const int R = A.rows_per_tile;
     const long long ntiles = ((long long)A.n + R - 1) / R;
     if (A.evals && A.spmve_blocks > 0) {
-        SpmvEArgs q{A.n, A.evals, A.eidx, A.toff, A.twin, A.ewmax, st, check_done, e};
+        SpmvEArgs q{A.n, A.evals, A.eidx, A.toff, A.twin, A.ewmax, A.excap, st, check_done, e};
         const bool x2 = e.x2.base != nullptr;
         long long g = x2 ? A.spmvex_blocks : A.spmve_blocks;
         if (g > ntiles) g = ntiles;
         *launched = true;
-        const size_t smem = kSpmvStages * spmve_stage_bytes(A.ewmax, x2);
+        const size_t smem = kSpmvStages * spmve_stage_bytes(A.ewmax, x2, A.excap);
         return x2 ? launch_pdl(k_spmv_e<true>, dim3((unsigned)g), dim3(kSpmvThreads), smem, s, q)
                   : launch_pdl(k_spmv_e<false>, dim3((unsigned)g), dim3(kSpmvThreads), smem, s, q);
     }
@@ -1689,10 +1690,18 @@ cudaError_t spmv_set_smem()
                                  (int)(kSpmvStages * spmvw_stage_bytes(kSpmvCapMax, (int)sizeof(IDX))));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_spmv_e<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kSpmvStages * spmve_stage_bytes(16)));
+                                 (int)(kSpmvStages * spmve_stage_bytes(16, false, kXCap)));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_spmv_e<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kSpmvStages * spmve_stage_bytes(16, true)));
+                                 (int)(kSpmvStages * spmve_stage_bytes(16, true, kXCap)));
+    // the largest shared-memory split for the kernels that alternate with the Gram-Schmidt passes,
+    // so that consecutive launches never wait for an SM to change its L1 / shared-memory split
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spmv_e<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spmv_e<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
     return e;
 }
 
@@ -1747,15 +1756,15 @@ cudaError_t launch_spmv2(const DevMatrix &A, int prec, const SpmvEpi &e1, const 
                                 ticket, diag, s);
 }
 
-int spmve_per_sm(int wmax, bool x2)
+int spmve_per_sm(int wmax, bool x2, int xcap)
 {
     int nb = 0;
     if (x2)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e<true>, kSpmvThreads,
-                                                      kSpmvStages * spmve_stage_bytes(wmax, true));
+                                                      kSpmvStages * spmve_stage_bytes(wmax, true, xcap));
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e<false>, kSpmvThreads,
-                                                      kSpmvStages * spmve_stage_bytes(wmax));
+                                                      kSpmvStages * spmve_stage_bytes(wmax, false, xcap));
     return nb > 0 ? nb : 0;
 }
 
@@ -1772,8 +1781,8 @@ cudaError_t spmv_configure(DevMatrix *A)
         if (err != cudaSuccess) return err;
         done = true;
     }
-    A->spmve_blocks = A->evals ? spmve_per_sm(A->ewmax, false) * A->num_sms : 0;
-    A->spmvex_blocks = A->evals ? spmve_per_sm(A->ewmax, true) * A->num_sms : 0;
+    A->spmve_blocks = A->evals ? spmve_per_sm(A->ewmax, false, A->excap) * A->num_sms : 0;
+    A->spmvex_blocks = A->evals ? spmve_per_sm(A->ewmax, true, A->excap) * A->num_sms : 0;
     if (A->coloff) {
         A->spmv_blocks64 = spmv_per_sm<double, short>(A->cap64) * A->num_sms;
         A->spmv_blocks32 = spmv_per_sm<float, short>(A->cap32) * A->num_sms;
