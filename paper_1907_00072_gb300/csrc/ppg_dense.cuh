@@ -44,12 +44,36 @@ PPG_HD inline int hess_eigs(int n, double *a, int lda, double *wr, double *wi, i
     int hi = n - 1;
     int its = 0, total = 0;
     while (hi >= 0) {
+        // l: the largest index <= hi whose subdiagonal entry is negligible (0 if none)
         int l = hi;
-        while (l > 0) {
-            double s = fabs(PPG_A(l - 1, l - 1)) + fabs(PPG_A(l, l));
-            if (s == 0.0) s = anorm;
-            if (fabs(PPG_A(l, l - 1)) <= eps * s) break;
-            --l;
+        bool scan = true;
+#if defined(__CUDA_ARCH__)
+        if (nl == 32) {  // one candidate per lane, the largest found by a ballot
+            bool neg = false;
+            const int c = hi - lane;
+            if (c > 0) {
+                double s = fabs(PPG_A(c - 1, c - 1)) + fabs(PPG_A(c, c));
+                if (s == 0.0) s = anorm;
+                neg = fabs(PPG_A(c, c - 1)) <= eps * s;
+            }
+            const unsigned int m = __ballot_sync(0xffffffffu, neg);
+            if (m) {
+                l = hi - (__ffs(m) - 1);
+                scan = false;
+            } else if (hi <= 32) {
+                l = 0;
+                scan = false;
+            }
+        }
+#endif
+        if (scan) {  // serial scan (host build, or no hit among more than 32 candidates)
+            l = hi;
+            while (l > 0) {
+                double s = fabs(PPG_A(l - 1, l - 1)) + fabs(PPG_A(l, l));
+                if (s == 0.0) s = anorm;
+                if (fabs(PPG_A(l, l - 1)) <= eps * s) break;
+                --l;
+            }
         }
         PPG_WSYNC();
         if (l > 0 && lane == 0) PPG_A(l, l - 1) = 0.0;
@@ -118,11 +142,17 @@ PPG_HD inline int hess_eigs(int n, double *a, int lda, double *wr, double *wi, i
             const double scale = fabs(x) + fabs(y) + fabs(z);
             PPG_WSYNC();
             if (scale != 0.0) {
-                const double xs = x / scale, ys = y / scale, zs = z / scale;
-                double alpha = sqrt(xs * xs + ys * ys + zs * zs);
+                // reflector I - beta v v^T mapping (x, y, z) to (alpha, 0, 0); the entries are scaled by
+                // 1 / scale only when their squares could leave the float64 range (float64 division
+                // and square root are slow on this GPU).  With alpha = -sign(x) ||(x, y, z)|| and
+                // v0 = x - alpha, v^T v = -2 alpha v0.
+                const bool wide = scale > 1e150 || scale < 1e-150;
+                const double rs = wide ? 1.0 / scale : 1.0;
+                const double xs = wide ? x * rs : x, ys = wide ? y * rs : y, zs = wide ? z * rs : z;
+                double alpha = sqrt(fma(xs, xs, fma(ys, ys, zs * zs)));
                 if (xs > 0.0) alpha = -alpha;
                 const double v0 = xs - alpha, v1 = ys, v2 = zs;
-                const double beta = 2.0 / (v0 * v0 + v1 * v1 + v2 * v2);
+                const double beta = -1.0 / (alpha * v0);
                 const int jlo = (k - 1 > l) ? k - 1 : l;
                 for (int j = jlo + lane; j <= hi; j += nl) {
                     double t = v0 * PPG_A(k, j) + v1 * PPG_A(k + 1, j);
