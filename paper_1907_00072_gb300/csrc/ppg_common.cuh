@@ -272,24 +272,6 @@ __device__ __forceinline__ double block_sum(double v, double *scratch /* >= 33 d
     return scratch[32];
 }
 
-// block_sum for a compensated float32 value: the warp trees run in float32, only the eight
-// warp totals are added in float64
-__device__ __forceinline__ double block_sum_f2(F2 v, double *scratch /* >= 33 doubles */)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const double wv = warp_sum_f2(v);
-    __syncthreads();
-    if (lane == 0) scratch[wid] = wv;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += scratch[q];
-        scratch[32] = t;
-    }
-    __syncthreads();
-    return scratch[32];
-}
-
 // The "last CTA done" ticket: every CTA calls this after writing its partial results;
 // exactly one CTA (the last to arrive) gets true.  Includes the fences that make the
 // other CTAs' partials visible to it.
@@ -309,8 +291,8 @@ __device__ __forceinline__ bool last_block_done(unsigned int *ticket, int *s_fla
     return false;
 }
 
-// block_sum_f2 without the conversion: the warp totals are added as compensated pairs too, by
-// thread 0 in warp order.  Every thread must call it; the result is valid in every thread.
+// Sum of a compensated float32 value over the CTA, kept as a pair: warp trees, then thread 0 adds
+// the warp totals in warp order.  Every thread must call it; the result is valid in every thread.
 __device__ __forceinline__ F2 block_sum_f2_pair(F2 v, F2 *scratch /* >= 33 */)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
