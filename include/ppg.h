@@ -143,13 +143,17 @@ ppg_status ppg_spmv(ppg_ctx *ctx, const void *x, void *y, int precision);
  *     index by entry index, so one warp reads a slice with coalesced loads (PPG_SPMV_SELL);
  *   - for each tile of rows, up to four contiguous ranges of x covering every column the tile's rows
  *     reference (banded matrices), and per entry its index into those ranges: with PPG_SPMV_STAGED the
- *     float32 row-block kernel copies the ranges into shared memory along with the matrix tile, so
- *     that each x gather is one shared-memory load (available when 90 % of the tiles are covered).
+ *     float32 kernel copies the ranges into shared memory along with the matrix tile, so that each x
+ *     gather is one shared-memory load (available when 90 % of the tiles are covered).  When every
+ *     tile is covered and rows take one lane each (tiles of 256 rows, mean row length <= 10), the
+ *     matrix is also stored tile by tile as dense 256 x w blocks of float32 values and window indices
+ *     (w = the tile's longest row, padding pointing at a zero), which STAGED then reads instead: no row
+ *     pointers, w shared-memory multiply-adds per row.
  * PPG_SPMV_AUTO selects STAGED when the windows exist and the row-block CSR kernel otherwise (measured on
- * the 128^3, 27-point 100^3 and 64^3 stencils: STAGED 3-17 % faster per SpMV, SELL slower than both);
- * PPG_SPMV_CSR, PPG_SPMV_SELL and PPG_SPMV_STAGED force one (STAGED applies to float32 links without a
- * second gathered input; others run as CSR).  Every result is the same sum; CSR and STAGED give
- * identical bits.  request = PPG_SPMV_QUERY changes
+ * the 128^3 7-point stencil: one SpMV 25.2 us with CSR, 16.6 us STAGED with the dense blocks; SELL
+ * slower than both); PPG_SPMV_CSR, PPG_SPMV_SELL and PPG_SPMV_STAGED force one (STAGED applies to
+ * float32 links, the two-input link w = A (x + s x2) only with the dense blocks; others run as CSR).
+ * Every result is the same sum; CSR and STAGED give identical bits.  request = PPG_SPMV_QUERY changes
  * nothing; *in_effect (host, may be NULL) receives the format now used.
  * Errors: PPG_ERR_INVALID_ARG (unknown request, or a format whose copy was not built). */
 enum {
