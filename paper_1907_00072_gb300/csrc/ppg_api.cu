@@ -87,6 +87,7 @@ struct ppg_ctx {
     float *d_evals = nullptr;    // tile-ELL copy (DevMatrix::evals, eidx, toff)
     short *d_eidx = nullptr;
     int *d_toff = nullptr;
+    int *d_etwin = nullptr;
     int fuse = 0;                // pair consecutive links of the p(A) chain into one launch (measured slower)
 
     // CUDA graphs of single iterations (ppg_opts.use_graph): one per iteration index, precision and
@@ -1226,25 +1227,27 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
     c->A.cap64 = (int)std::max<long long>(cap, 64);
     c->A.cap32 = (int)std::max<long long>(cap, 64);
 
-    // x windows per tile for the staged kernel: the tile's sorted distinct columns are grouped into
+    // x windows per tile for the staged kernels: the tile's sorted distinct columns are grouped into
     // ranges (columns closer than kXGap share one), each widened to 16-byte boundaries and kept
     // inside [0, n rounded down to 4); a tile needing more than kXWin ranges or kXCap entries keeps
-    // global gathers (lengths 0)
-    if (nnz > 0 && R <= 256) {
-        std::vector<int> hcol(nnz);
-        PPG_CK(cudaMemcpy(hcol.data(), c->d_colidx, sizeof(int) * nnz, cudaMemcpyDeviceToHost));
-        const long long ntiles = (n + R - 1) / R;
+    // global gathers (lengths 0).  desc: [tiles][2 kXWin] (starts, lengths); lidx: per entry, its
+    // index in the tile's concatenated windows; returns the number of covered tiles and the longest
+    // window total.
+    auto make_windows = [&](const std::vector<int> &hcol, long long Rt, int maxw, std::vector<int> &desc,
+                            std::vector<short> &lidx, long long *xmax) -> long long {
+        const long long ntiles = (n + Rt - 1) / Rt;
         const long long n4 = n & ~3LL;
-        std::vector<int> desc(ntiles * 2 * kXWin, 0);
-        std::vector<short> lidx(nnz + 16, 0);  // per entry: its index in the tile's window buffer
+        desc.assign(ntiles * 2 * maxw, 0);
+        lidx.assign(nnz + 16, 0);
         std::vector<int> cols;
-        long long windowed = 0, xmax = 0;
+        long long windowed = 0;
+        *xmax = 0;
         for (long long t = 0; t < ntiles; ++t) {
-            const long long r0 = t * R, r1 = std::min<long long>(n, r0 + R);
+            const long long r0 = t * Rt, r1 = std::min<long long>(n, r0 + Rt);
             cols.assign(hcol.begin() + hrp[r0], hcol.begin() + hrp[r1]);
             if (cols.empty()) continue;
             std::sort(cols.begin(), cols.end());
-            int lo[kXWin], hi[kXWin], nw = 0;
+            int lo[kEWin], hi[kEWin], nw = 0;
             bool ok = true;
             long long lw = cols[0], hw = cols[0];
             for (size_t q = 1; q <= cols.size() && ok; ++q) {
@@ -1253,7 +1256,7 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
                     continue;
                 }
                 const long long a = lw & ~3LL, b = (hw + 4) & ~3LL;  // [a, b) covers [lw, hw]
-                if (nw == kXWin || a < 0 || b > n4) ok = false;
+                if (nw == maxw || a < 0 || b > n4) ok = false;
                 else {
                     lo[nw] = (int)a;
                     hi[nw] = (int)b;
@@ -1264,11 +1267,11 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
             long long total = 0;
             for (int w = 0; w < nw; ++w) total += hi[w] - lo[w];
             if (!ok || total > kXCap) continue;
-            xmax = std::max(xmax, total);
-            int off[kXWin];
+            *xmax = std::max(*xmax, total);
+            int off[kEWin];
             for (int w = 0, o = 0; w < nw; ++w) {
-                desc[t * 2 * kXWin + w] = lo[w];
-                desc[t * 2 * kXWin + kXWin + w] = hi[w] - lo[w];
+                desc[t * 2 * maxw + w] = lo[w];
+                desc[t * 2 * maxw + maxw + w] = hi[w] - lo[w];
                 off[w] = o;
                 o += hi[w] - lo[w];
             }
@@ -1280,6 +1283,16 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
             }
             ++windowed;
         }
+        return windowed;
+    };
+    if (nnz > 0 && R <= 256) {
+        std::vector<int> hcol(nnz);
+        PPG_CK(cudaMemcpy(hcol.data(), c->d_colidx, sizeof(int) * nnz, cudaMemcpyDeviceToHost));
+        const long long ntiles = (n + R - 1) / R;
+        std::vector<int> desc;
+        std::vector<short> lidx;
+        long long xmax = 0;
+        const long long windowed = make_windows(hcol, R, kXWin, desc, lidx, &xmax);
         if (windowed * 10 >= ntiles * 9) {  // worth a kernel of its own when nearly every tile is covered
             PPG_CK(cudaMalloc(&c->d_twin, sizeof(int) * desc.size()));
             PPG_CK(cudaMemcpy(c->d_twin, desc.data(), sizeof(int) * desc.size(), cudaMemcpyHostToDevice));
@@ -1288,36 +1301,51 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
             c->A.twin = c->d_twin;
             c->A.lidx = c->d_lidx;
         }
-        // tile-ELL copy for one lane per row when every tile has windows: tile t is a dense R x w_t block
-        // (entry k of row l at k R + l) of float32 values and window indices, padded with value 0 and
-        // the index xmax (the longest window total) of a zero kept after the windows
-        if (c->A.twin && windowed == ntiles && R == kThreads) {
+        // tile-ELL copy, one thread per row, for tiles of kThreads rows whose windows (up to kEWin
+        // ranges each) all exist: tile t is a dense kThreads x w_t block (entry k of row l at
+        // k kThreads + l) of float32 values and window indices, padded with value 0 and the index
+        // exmax (the longest window total) of a zero kept after the windows.  w_t is the tile's longest
+        // row rounded up to a multiple of the row-block kernel's lanes per row G: the thread sums
+        // entries k = g mod G apart and combines the G sums in the lanes' shuffle order, so both
+        // kernels give the same bits.
+        const int G = c->A.lanes_per_row;
+        const long long RE = kThreads;
+        const long long etiles = (n + RE - 1) / RE;
+        const char *ell_env = getenv("PPG_SPMV_ELL");  // 0: no tile-ELL copy (the windowed CSR kernel runs)
+        const bool ell_on = !ell_env || atoi(ell_env) != 0;
+        std::vector<int> edesc;
+        std::vector<short> elidx;
+        long long exmax = 0, ewindowed = -1;
+        if (ell_on && c->A.twin && (G == 1 || G == 2 || G == 4) && spmv_rows_per_thread() == 1)
+            ewindowed = make_windows(hcol, RE, kEWin, edesc, elidx, &exmax);
+        if (ewindowed == etiles) {
             std::vector<double> hval(nnz);
             PPG_CK(cudaMemcpy(hval.data(), c->d_vals, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
-            std::vector<int> toff(ntiles + 1, 0);
+            std::vector<int> toff(etiles + 1, 0);
             int wmax = 0;
-            for (long long t = 0; t < ntiles; ++t) {
-                const long long r0 = t * R, r1 = std::min<long long>(n, r0 + R);
+            for (long long t = 0; t < etiles; ++t) {
+                const long long r0 = t * RE, r1 = std::min<long long>(n, r0 + RE);
                 int wt = 0;
                 for (long long r = r0; r < r1; ++r) wt = std::max(wt, hrp[r + 1] - hrp[r]);
+                wt = (wt + G - 1) / G * G;
                 wmax = std::max(wmax, wt);
-                if ((long long)toff[t] + (long long)R * wt >= (1LL << 31) - 64) {
+                if ((long long)toff[t] + RE * wt >= (1LL << 31) - 64) {
                     wmax = -1;
                     break;
                 }
-                toff[t + 1] = toff[t] + R * wt;
+                toff[t + 1] = toff[t] + (int)(RE * wt);
             }
-            if (wmax > 0 && wmax <= 16) {
-                const size_t total = (size_t)toff[ntiles];
+            if (wmax > 0 && wmax <= kEllWidthMax) {
+                const size_t total = (size_t)toff[etiles];
                 std::vector<float> ev(total + 16, 0.0f);
-                std::vector<short> ei(total + 16, (short)xmax);
-                for (long long t = 0; t < ntiles; ++t) {
-                    const long long r0 = t * R, r1 = std::min<long long>(n, r0 + R);
+                std::vector<short> ei(total + 16, (short)exmax);
+                for (long long t = 0; t < etiles; ++t) {
+                    const long long r0 = t * RE, r1 = std::min<long long>(n, r0 + RE);
                     for (long long r = r0; r < r1; ++r)
                         for (int k = 0; k < hrp[r + 1] - hrp[r]; ++k) {
-                            const size_t e = (size_t)toff[t] + (size_t)k * R + (size_t)(r - r0);
+                            const size_t e = (size_t)toff[t] + (size_t)k * RE + (size_t)(r - r0);
                             ev[e] = (float)hval[hrp[r] + k];
-                            ei[e] = lidx[hrp[r] + k];
+                            ei[e] = elidx[hrp[r] + k];
                         }
                 }
                 PPG_CK(cudaMalloc(&c->d_evals, sizeof(float) * ev.size()));
@@ -1326,11 +1354,14 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
                 PPG_CK(cudaMemcpy(c->d_eidx, ei.data(), sizeof(short) * ei.size(), cudaMemcpyHostToDevice));
                 PPG_CK(cudaMalloc(&c->d_toff, sizeof(int) * toff.size()));
                 PPG_CK(cudaMemcpy(c->d_toff, toff.data(), sizeof(int) * toff.size(), cudaMemcpyHostToDevice));
+                PPG_CK(cudaMalloc(&c->d_etwin, sizeof(int) * edesc.size()));
+                PPG_CK(cudaMemcpy(c->d_etwin, edesc.data(), sizeof(int) * edesc.size(), cudaMemcpyHostToDevice));
+                c->A.etwin = c->d_etwin;
                 c->A.evals = c->d_evals;
                 c->A.eidx = c->d_eidx;
                 c->A.toff = c->d_toff;
                 c->A.ewmax = wmax;
-                c->A.excap = (int)xmax;
+                c->A.excap = (int)exmax;
             }
         }
     }
@@ -1400,6 +1431,7 @@ void ppg_destroy(ppg_ctx *c)
     cudaFree(c->d_evals);
     cudaFree(c->d_eidx);
     cudaFree(c->d_toff);
+    cudaFree(c->d_etwin);
     cudaFree(c->d_sptr);
     cudaFree(c->d_soff);
     cudaFree(c->d_scol);

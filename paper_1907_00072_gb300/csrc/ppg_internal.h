@@ -77,7 +77,8 @@ struct DevMatrix {
     // toff[t+1]-1, entry k of row l at toff[t] + k R + l; padding has value 0 and index kXCap
     const float *evals;
     const short *eidx;
-    const int *toff;      // ntiles + 1
+    const int *toff;      // tiles of kThreads rows + 1
+    const int *etwin;     // x windows of those tiles: [tiles][2 kEWin] (starts, then lengths)
     int ewmax;            // widest tile (entries per row)
     int excap;            // longest window total over the tiles (the padding's zero sits at this index)
     int spmve_blocks;     // persistent grid of the tile-ELL kernel
@@ -99,7 +100,9 @@ constexpr int kFmtCsr = 0;
 constexpr int kFmtSell = 1;
 constexpr int kFmtCsrStaged = 2;  // row-block CSR with the tile's x windows and row operands staged by TMA
 constexpr int kXWin = 4;          // x windows per tile
+constexpr int kEWin = 8;          // x windows per tile of the tile-ELL kernel
 constexpr int kXCap = 2048;       // x entries per tile
+constexpr int kEllWidthMax = 32;  // widest tile-ELL tile (entries per row, rounded to lanes per row)
 constexpr int kXGap = 64;         // columns closer than this share a window
 constexpr short kSellPadOff = -32768;  // outside the int16 offsets a row may use (|col - row| <= 32767)
 

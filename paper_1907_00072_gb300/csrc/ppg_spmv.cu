@@ -860,12 +860,14 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_w(Sp
 
 // ---------------------------------------------------------------- staged x windows, tile-ELL (float32)
 
-// As k_spmv_w for one lane per row, with each tile stored as a dense R x w block (entry k of row l
-// at k R + l): the stage holds the block's values and window indices and the tile's x windows plus a
-// zero at index xcap (the matrix's longest window total, at most kXCap) for the padding, so a row is
-// w shared-memory multiply-adds with no row pointers or bounds tests.  Same arithmetic as k_spmv (padding adds 0 * 0).  X2: the epilogue's second input
-// x2 (A (x + s2 x2)) is staged too, over the same windows, and combined per gathered entry as k_spmv
-// does.
+// As k_spmv_w for one thread per row, with each tile of kThreads rows stored as a dense R x w block
+// (entry k of row l at k R + l): the stage holds the block's values and window indices and the tile's
+// x windows plus a zero at index xcap (the matrix's longest window total, at most kXCap) for the
+// padding, so a row is w shared-memory multiply-adds with no row pointers or bounds tests.  G: the
+// row-block kernel's lanes per row; the thread keeps G sums (entries k = g mod G) and combines them
+// in that kernel's shuffle order, so the results are k_spmv's bits (padding adds 0 * 0).  X2: the
+// epilogue's second input x2 (A (x + s2 x2)) is staged too, over the same windows, and combined per
+// gathered entry as k_spmv does.
 __host__ __device__ constexpr size_t spmve_stage_bytes(int wmax, bool x2, int xcap)
 {
     return round128((size_t)kThreads * wmax * 4) + round128((size_t)kThreads * wmax * 2) +
@@ -885,12 +887,13 @@ struct SpmvEArgs {
     SpmvEpi e;
 };
 
-template <bool X2>
+template <bool X2, int G>
 __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(SpmvEArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[kSpmvStages];
     __shared__ __align__(8) uint64_t empty[kSpmvStages];
+    __shared__ int4 s_desc[kSpmvStages][4];
     __shared__ double s_coef[7];
     using T = float;
     constexpr int R = kThreads;
@@ -923,10 +926,13 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
     if (wid == kSpmvConsumerWarps) {
         // ---------------- producer
         if (lane == 0) {
-            int4 dlo[kSpmvStages], dln[kSpmvStages];
-            auto desc = [&](long long t, int4 &lo4, int4 &ln4) {
-                lo4 = __ldg(reinterpret_cast<const int4 *>(a.twin + t * 2 * kXWin));
-                ln4 = __ldg(reinterpret_cast<const int4 *>(a.twin + t * 2 * kXWin + kXWin));
+            // a tile's window descriptors: starts in d[0..1], lengths in d[2..3] (kEWin each); those of
+            // the tiles requested before the wait are kept in shared memory until their windows are
+            // requested after it
+            auto desc = [&](long long t, int4 *d) {
+                const int4 *src = reinterpret_cast<const int4 *>(a.twin + t * 2 * kEWin);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) d[u] = __ldg(src + u);
             };
             auto span = [&](long long t, int &o0, int &o1) {
                 o0 = __ldg(a.toff + t);
@@ -943,14 +949,17 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                 reinterpret_cast<int *>(base + hd_off)[0] = (int)(nb / R);
             };
             const T *x = nullptr, *x2 = nullptr;
-            auto issue_vectors = [&](int s, const int4 lo4, const int4 ln4) {
+            auto issue_vectors = [&](int s, const int4 *d) {
                 unsigned char *base = smem + s * stage_bytes;
-                const int lo[kXWin] = {lo4.x, lo4.y, lo4.z, lo4.w};
-                const int ln[kXWin] = {ln4.x, ln4.y, ln4.z, ln4.w};
+                const int lo[kEWin] = {d[0].x, d[0].y, d[0].z, d[0].w, d[1].x, d[1].y, d[1].z, d[1].w};
+                const int ln[kEWin] = {d[2].x, d[2].y, d[2].z, d[2].w, d[3].x, d[3].y, d[3].z, d[3].w};
                 uint32_t bytes = 0;
-                for (int w = 0; w < kXWin; ++w) bytes += (uint32_t)ln[w] * 4u;
+#pragma unroll
+                for (int w = 0; w < kEWin; ++w) bytes += (uint32_t)ln[w] * 4u;
                 mbar_arrive_expect_tx(&full[s], X2 ? 2 * bytes : bytes);
-                for (int w = 0, o = 0; w < kXWin; ++w)
+                int o = 0;
+#pragma unroll
+                for (int w = 0; w < kEWin; ++w)
                     if (ln[w] > 0) {
                         bulk_g2s(base + xw_off + (size_t)o * 4, x + lo[w], (uint32_t)ln[w] * 4u, &full[s]);
                         if (X2)
@@ -960,10 +969,10 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                     }
             };
             int no0 = 0, no1 = 0;
-            int4 nlo = make_int4(0, 0, 0, 0), nln = make_int4(0, 0, 0, 0);
+            int4 nd[4];
             if (my_tiles > 0) {
                 span(blockIdx.x, no0, no1);
-                desc(blockIdx.x, nlo, nln);
+                desc(blockIdx.x, nd);
             }
             int i = 0;
             bool waited = false;
@@ -979,25 +988,24 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                     }
                     x = resolve_ptr<T>(a.e.x, st);
                     if (X2) x2 = resolve_ptr<T>(a.e.x2, st);
-                    for (int q = 0; q < prefetched; ++q) issue_vectors(q, dlo[q], dln[q]);
+                    for (int q = 0; q < prefetched; ++q) issue_vectors(q, s_desc[q]);
                 }
+                // this tile's bounds and descriptors (loaded one step ago); the next tile's are
+                // loaded while this stage waits to be free
                 const int o0 = no0, o1 = no1;
-                const int4 clo = nlo, cln = nln;
+                const int s = i % kSpmvStages, round = i / kSpmvStages;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) s_desc[s][u] = nd[u];
                 if (tile + gridDim.x < ntiles) {
                     span(tile + gridDim.x, no0, no1);
-                    desc(tile + gridDim.x, nlo, nln);
+                    desc(tile + gridDim.x, nd);
                 }
-                const int s = i % kSpmvStages, round = i / kSpmvStages;
                 if (round > 0 && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitLimitNs)) {
                     atomicOr(&st->error, kErrTimeout);
                     break;
                 }
                 issue_matrix(s, o0, o1);
-                if (i >= prefetched) issue_vectors(s, clo, cln);
-                else {
-                    dlo[i] = clo;
-                    dln[i] = cln;
-                }
+                if (i >= prefetched) issue_vectors(s, s_desc[s]);
             }
             if (!waited) {
                 pdl_wait();
@@ -1008,7 +1016,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                 } else {
                     x = resolve_ptr<T>(a.e.x, st);
                     if (X2) x2 = resolve_ptr<T>(a.e.x2, st);
-                    for (int q = 0; q < i; ++q) issue_vectors(q, dlo[q], dln[q]);
+                    for (int q = 0; q < i; ++q) issue_vectors(q, s_desc[q]);
                 }
             }
         }
@@ -1070,16 +1078,39 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
         const T *s_x = reinterpret_cast<const T *>(base + xw_off);
         const int w = reinterpret_cast<const int *>(base + hd_off)[0];
         T acc = T(0);
-        if (X2) {
-            const T *s_x2 = s_x + xw_bytes / 4;
+        if constexpr (G == 1) {
+            if (X2) {
+                const T *s_x2 = s_x + xw_bytes / 4;
 #pragma unroll 8
-            for (int k = 0; k < w; ++k) {
-                const int q = s_ix[k * R + tid];
-                acc = fma(s_val[k * R + tid], fma(c2, s_x2[q], s_x[q]), acc);
+                for (int k = 0; k < w; ++k) {
+                    const int q = s_ix[k * R + tid];
+                    acc = fma(s_val[k * R + tid], fma(c2, s_x2[q], s_x[q]), acc);
+                }
+            } else {
+#pragma unroll 8
+                for (int k = 0; k < w; ++k) acc = fma(s_val[k * R + tid], s_x[s_ix[k * R + tid]], acc);
             }
         } else {
-#pragma unroll 8
-            for (int k = 0; k < w; ++k) acc = fma(s_val[k * R + tid], s_x[s_ix[k * R + tid]], acc);
+            // w is a multiple of G (the host pads each tile to it)
+            T part[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) part[g] = T(0);
+            const T *s_x2 = s_x + xw_bytes / 4;
+#pragma unroll 2
+            for (int k = 0; k < w; k += G) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int e = (k + g) * R + tid;
+                    const int q = s_ix[e];
+                    const T xv = X2 ? fma(c2, s_x2[q], s_x[q]) : s_x[q];
+                    part[g] = fma(s_val[e], xv, part[g]);
+                }
+            }
+#pragma unroll
+            for (int o = G >> 1; o > 0; o >>= 1)
+#pragma unroll
+                for (int l = 0; l < o; ++l) part[l] = part[l] + part[l + o];
+            acc = part[0];
         }
         if (ok) {
             T v = ca0 * acc;
@@ -1636,14 +1667,25 @@ cudaError_t spmvw_go(const DevMatrix &A, const IDX *cols, const SpmvEpi &e, Cycl
     const int R = A.rows_per_tile;
     const long long ntiles = ((long long)A.n + R - 1) / R;
     if (A.evals && A.spmve_blocks > 0) {
-        SpmvEArgs q{A.n, A.evals, A.eidx, A.toff, A.twin, A.ewmax, A.excap, st, check_done, e};
+        SpmvEArgs q{A.n, A.evals, A.eidx, A.toff, A.etwin, A.ewmax, A.excap, st, check_done, e};
         const bool x2 = e.x2.base != nullptr;
+        const long long etiles = ((long long)A.n + kThreads - 1) / kThreads;
         long long g = x2 ? A.spmvex_blocks : A.spmve_blocks;
-        if (g > ntiles) g = ntiles;
+        if (g > etiles) g = etiles;
         *launched = true;
         const size_t smem = kSpmvStages * spmve_stage_bytes(A.ewmax, x2, A.excap);
-        return x2 ? launch_pdl(k_spmv_e<true>, dim3((unsigned)g), dim3(kSpmvThreads), smem, s, q)
-                  : launch_pdl(k_spmv_e<false>, dim3((unsigned)g), dim3(kSpmvThreads), smem, s, q);
+        const dim3 grid((unsigned)g), block(kSpmvThreads);
+        switch (A.lanes_per_row) {
+        case 2:
+            return x2 ? launch_pdl(k_spmv_e<true, 2>, grid, block, smem, s, q)
+                      : launch_pdl(k_spmv_e<false, 2>, grid, block, smem, s, q);
+        case 4:
+            return x2 ? launch_pdl(k_spmv_e<true, 4>, grid, block, smem, s, q)
+                      : launch_pdl(k_spmv_e<false, 4>, grid, block, smem, s, q);
+        default:
+            return x2 ? launch_pdl(k_spmv_e<true, 1>, grid, block, smem, s, q)
+                      : launch_pdl(k_spmv_e<false, 1>, grid, block, smem, s, q);
+        }
     }
     p.a = SpmvArgs<float, IDX>{A.n, A.rowptr, cols, A.vals32, R, A.lanes_per_row, A.cap32, st, check_done, e};
     p.lidx = A.lidx;
@@ -1674,6 +1716,26 @@ cudaError_t sell_go(const DevMatrix &A, const T *vals, const IDX *cols, const Sp
     return launch_pdl(k_spmv_sell<T, IDX>, dim3((unsigned)grid), dim3(kSellWarps * 32), 0, s, a);
 }
 
+// Dynamic shared memory limit (the widest tile and the largest windows) and the largest
+// shared-memory carveout for the tile-ELL kernels: they alternate with the Gram-Schmidt passes, and
+// consecutive launches should never wait for an SM to change its L1 / shared-memory split.
+template <int G>
+cudaError_t spmve_set_smem()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_spmv_e<false, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kSpmvStages * spmve_stage_bytes(kEllWidthMax, false, kXCap)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spmv_e<true, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kSpmvStages * spmve_stage_bytes(kEllWidthMax, true, kXCap)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spmv_e<false, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spmv_e<true, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 template <typename T, typename IDX>
 cudaError_t spmv_set_smem()
 {
@@ -1688,20 +1750,9 @@ cudaError_t spmv_set_smem()
     if (e == cudaSuccess && sizeof(T) == 4)
         e = cudaFuncSetAttribute(k_spmv_w<IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kSpmvStages * spmvw_stage_bytes(kSpmvCapMax, (int)sizeof(IDX))));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spmv_e<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kSpmvStages * spmve_stage_bytes(16, false, kXCap)));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spmv_e<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kSpmvStages * spmve_stage_bytes(16, true, kXCap)));
-    // the largest shared-memory split for the kernels that alternate with the Gram-Schmidt passes,
-    // so that consecutive launches never wait for an SM to change its L1 / shared-memory split
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spmv_e<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spmv_e<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = spmve_set_smem<1>();
+    if (e == cudaSuccess) e = spmve_set_smem<2>();
+    if (e == cudaSuccess) e = spmve_set_smem<4>();
     return e;
 }
 
@@ -1756,16 +1807,23 @@ cudaError_t launch_spmv2(const DevMatrix &A, int prec, const SpmvEpi &e1, const 
                                 ticket, diag, s);
 }
 
-int spmve_per_sm(int wmax, bool x2, int xcap)
+template <int G>
+int spmve_per_sm_g(int wmax, bool x2, int xcap)
 {
     int nb = 0;
+    const size_t smem = kSpmvStages * spmve_stage_bytes(wmax, x2, xcap);
     if (x2)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e<true>, kSpmvThreads,
-                                                      kSpmvStages * spmve_stage_bytes(wmax, true, xcap));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e<true, G>, kSpmvThreads, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e<false>, kSpmvThreads,
-                                                      kSpmvStages * spmve_stage_bytes(wmax, false, xcap));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e<false, G>, kSpmvThreads, smem);
     return nb > 0 ? nb : 0;
+}
+
+int spmve_per_sm(int G, int wmax, bool x2, int xcap)
+{
+    if (G == 2) return spmve_per_sm_g<2>(wmax, x2, xcap);
+    if (G == 4) return spmve_per_sm_g<4>(wmax, x2, xcap);
+    return spmve_per_sm_g<1>(wmax, x2, xcap);
 }
 
 // Sets the dynamic shared memory limit (for the largest staging capacity, once) and returns
@@ -1781,8 +1839,8 @@ cudaError_t spmv_configure(DevMatrix *A)
         if (err != cudaSuccess) return err;
         done = true;
     }
-    A->spmve_blocks = A->evals ? spmve_per_sm(A->ewmax, false, A->excap) * A->num_sms : 0;
-    A->spmvex_blocks = A->evals ? spmve_per_sm(A->ewmax, true, A->excap) * A->num_sms : 0;
+    A->spmve_blocks = A->evals ? spmve_per_sm(A->lanes_per_row, A->ewmax, false, A->excap) * A->num_sms : 0;
+    A->spmvex_blocks = A->evals ? spmve_per_sm(A->lanes_per_row, A->ewmax, true, A->excap) * A->num_sms : 0;
     if (A->coloff) {
         A->spmv_blocks64 = spmv_per_sm<double, short>(A->cap64) * A->num_sms;
         A->spmv_blocks32 = spmv_per_sm<float, short>(A->cap32) * A->num_sms;
