@@ -88,6 +88,7 @@ struct ppg_ctx {
     short *d_eidx = nullptr;
     int *d_toff = nullptr;
     int *d_etwin = nullptr;
+    double *d_evals64 = nullptr;
     int fuse = 0;                // pair consecutive links of the p(A) chain into one launch (measured slower)
 
     // CUDA graphs of single iterations (ppg_opts.use_graph): one per iteration index, precision and
@@ -1338,6 +1339,7 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
             if (wmax > 0 && wmax <= kEllWidthMax) {
                 const size_t total = (size_t)toff[etiles];
                 std::vector<float> ev(total + 16, 0.0f);
+                std::vector<double> ev64(total + 16, 0.0);
                 std::vector<short> ei(total + 16, (short)exmax);
                 for (long long t = 0; t < etiles; ++t) {
                     const long long r0 = t * RE, r1 = std::min<long long>(n, r0 + RE);
@@ -1345,11 +1347,14 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
                         for (int k = 0; k < hrp[r + 1] - hrp[r]; ++k) {
                             const size_t e = (size_t)toff[t] + (size_t)k * RE + (size_t)(r - r0);
                             ev[e] = (float)hval[hrp[r] + k];
+                            ev64[e] = hval[hrp[r] + k];
                             ei[e] = elidx[hrp[r] + k];
                         }
                 }
                 PPG_CK(cudaMalloc(&c->d_evals, sizeof(float) * ev.size()));
                 PPG_CK(cudaMemcpy(c->d_evals, ev.data(), sizeof(float) * ev.size(), cudaMemcpyHostToDevice));
+                PPG_CK(cudaMalloc(&c->d_evals64, sizeof(double) * ev64.size()));
+                PPG_CK(cudaMemcpy(c->d_evals64, ev64.data(), sizeof(double) * ev64.size(), cudaMemcpyHostToDevice));
                 PPG_CK(cudaMalloc(&c->d_eidx, sizeof(short) * ei.size()));
                 PPG_CK(cudaMemcpy(c->d_eidx, ei.data(), sizeof(short) * ei.size(), cudaMemcpyHostToDevice));
                 PPG_CK(cudaMalloc(&c->d_toff, sizeof(int) * toff.size()));
@@ -1358,6 +1363,7 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
                 PPG_CK(cudaMemcpy(c->d_etwin, edesc.data(), sizeof(int) * edesc.size(), cudaMemcpyHostToDevice));
                 c->A.etwin = c->d_etwin;
                 c->A.evals = c->d_evals;
+                c->A.evals64 = c->d_evals64;
                 c->A.eidx = c->d_eidx;
                 c->A.toff = c->d_toff;
                 c->A.ewmax = wmax;
@@ -1432,6 +1438,7 @@ void ppg_destroy(ppg_ctx *c)
     cudaFree(c->d_eidx);
     cudaFree(c->d_toff);
     cudaFree(c->d_etwin);
+    cudaFree(c->d_evals64);
     cudaFree(c->d_sptr);
     cudaFree(c->d_soff);
     cudaFree(c->d_scol);

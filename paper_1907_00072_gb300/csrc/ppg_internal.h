@@ -50,6 +50,12 @@ cudaError_t launch_coop(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t 
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// Persistent grid and pipeline depth of a tile-ELL kernel (one value type).
+struct EllLaunch {
+    int blocks, nst;        // one input
+    int blocks_x2, nst_x2;  // with a second staged input (A (x + s2 x2))
+};
+
 // The context's device copy of the CSR matrix and the tiling chosen for it.
 struct DevMatrix {
     int n;
@@ -81,8 +87,8 @@ struct DevMatrix {
     const int *etwin;     // x windows of those tiles: [tiles][2 kEWin] (starts, then lengths)
     int ewmax;            // widest tile (entries per row)
     int excap;            // longest window total over the tiles (the padding's zero sits at this index)
-    int spmve_blocks;     // persistent grid of the tile-ELL kernel
-    int spmvex_blocks;    // the same with a second staged input (A (x + s2 x2))
+    const double *evals64; // the same blocks' values in float64 (float64 solves and the construction)
+    EllLaunch ell[2];     // tile-ELL grid and stages: [0] float32, [1] float64
     int spmvw_blocks32;   // persistent grid of the staged kernel
     // sliced ELL copy (slices of 32 rows; entry k of row 32 s + l at sptr[s] + 32 k + l, slices padded
     // to their longest row with a sentinel index), used by the SpMV when format == kFmtSell

@@ -868,26 +868,27 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_w(Sp
 // in that kernel's shuffle order, so the results are k_spmv's bits (padding adds 0 * 0).  X2: the
 // epilogue's second input x2 (A (x + s2 x2)) is staged too, over the same windows, and combined per
 // gathered entry as k_spmv does.
-__host__ __device__ constexpr size_t spmve_stage_bytes(int wmax, bool x2, int xcap)
+__host__ __device__ constexpr size_t spmve_stage_bytes(int wmax, bool x2, int xcap, int sv = 4)
 {
-    return round128((size_t)kThreads * wmax * 4) + round128((size_t)kThreads * wmax * 2) +
-           (x2 ? 2 : 1) * round128((size_t)(xcap + 4) * 4) + 128;
+    return round128((size_t)kThreads * wmax * sv) + round128((size_t)kThreads * wmax * 2) +
+           (x2 ? 2 : 1) * round128((size_t)(xcap + 4) * sv) + 128;
 }
 
 struct SpmvEArgs {
     int n;
-    const float *vals;  // tile-ELL values
+    const void *vals;   // tile-ELL values (float or double, the kernel's T)
     const short *idx;   // tile-ELL window indices
     const int *toff;
     const int *twin;
     int wmax;
     int xcap;  // index of the zero after the windows (padding entries point there)
+    int nst;   // pipeline stages in use (2 or 3: three when they fit the shared memory)
     Cycle *st;
     int check_done;
     SpmvEpi e;
 };
 
-template <bool X2, int G>
+template <typename T, bool X2, int G>
 __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(SpmvEArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -895,31 +896,33 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
     __shared__ __align__(8) uint64_t empty[kSpmvStages];
     __shared__ int4 s_desc[kSpmvStages][4];
     __shared__ double s_coef[7];
-    using T = float;
     constexpr int R = kThreads;
+    constexpr int SV = (int)sizeof(T);
+    const T *vals = static_cast<const T *>(a.vals);
+    const int S = a.nst;
 
     Cycle *st = a.st;
     const long long ntiles = ((long long)a.n + R - 1) / R;
-    const size_t stage_bytes = spmve_stage_bytes(a.wmax, X2, a.xcap);
-    const size_t ix_off = round128((size_t)R * a.wmax * 4);
+    const size_t stage_bytes = spmve_stage_bytes(a.wmax, X2, a.xcap, SV);
+    const size_t ix_off = round128((size_t)R * a.wmax * SV);
     const size_t xw_off = ix_off + round128((size_t)R * a.wmax * 2);
-    const size_t xw_bytes = round128((size_t)(a.xcap + 4) * 4);
+    const size_t xw_bytes = round128((size_t)(a.xcap + 4) * SV);
     const size_t hd_off = xw_off + (X2 ? 2 : 1) * xw_bytes;
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int prefetched = (int)min((long long)kSpmvStages, my_tiles);
+    const int prefetched = (int)min((long long)S, my_tiles);
 
     if (tid == 0) {
-        for (int q = 0; q < kSpmvStages; ++q) {
+        for (int q = 0; q < S; ++q) {
             mbar_init(&full[q], 1);
             mbar_init(&empty[q], kSpmvConsumerWarps);
         }
         fence_mbar_init();
     }
-    if (tid < kSpmvStages * 4) {  // the zero the padding indexes, in every stage (no copy writes there)
+    if (tid < S * 4) {  // the zero the padding indexes, in every stage (no copy writes there)
         T *z = reinterpret_cast<T *>(smem + (tid / 4) * stage_bytes + xw_off);
         z[a.xcap + (tid & 3)] = T(0);
-        if (X2) z[xw_bytes / 4 + a.xcap + (tid & 3)] = T(0);
+        if (X2) z[xw_bytes / SV + a.xcap + (tid & 3)] = T(0);
     }
     __syncthreads();
 
@@ -941,9 +944,9 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
             auto issue_matrix = [&](int s, int o0, int o1) {
                 unsigned char *base = smem + s * stage_bytes;
                 const uint32_t nb = (uint32_t)(o1 - o0);
-                mbar_expect_tx(&full[s], nb * 6u);
+                mbar_expect_tx(&full[s], nb * (uint32_t)(SV + 2));
                 if (nb) {
-                    bulk_g2s(base, a.vals + o0, nb * 4u, &full[s]);
+                    bulk_g2s(base, vals + o0, nb * (uint32_t)SV, &full[s]);
                     bulk_g2s(base + ix_off, a.idx + o0, nb * 2u, &full[s]);
                 }
                 reinterpret_cast<int *>(base + hd_off)[0] = (int)(nb / R);
@@ -955,16 +958,16 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                 const int ln[kEWin] = {d[2].x, d[2].y, d[2].z, d[2].w, d[3].x, d[3].y, d[3].z, d[3].w};
                 uint32_t bytes = 0;
 #pragma unroll
-                for (int w = 0; w < kEWin; ++w) bytes += (uint32_t)ln[w] * 4u;
+                for (int w = 0; w < kEWin; ++w) bytes += (uint32_t)ln[w] * (uint32_t)SV;
                 mbar_arrive_expect_tx(&full[s], X2 ? 2 * bytes : bytes);
                 int o = 0;
 #pragma unroll
                 for (int w = 0; w < kEWin; ++w)
                     if (ln[w] > 0) {
-                        bulk_g2s(base + xw_off + (size_t)o * 4, x + lo[w], (uint32_t)ln[w] * 4u, &full[s]);
+                        bulk_g2s(base + xw_off + (size_t)o * SV, x + lo[w], (uint32_t)ln[w] * (uint32_t)SV, &full[s]);
                         if (X2)
-                            bulk_g2s(base + xw_off + xw_bytes + (size_t)o * 4, x2 + lo[w], (uint32_t)ln[w] * 4u,
-                                     &full[s]);
+                            bulk_g2s(base + xw_off + xw_bytes + (size_t)o * SV, x2 + lo[w],
+                                     (uint32_t)ln[w] * (uint32_t)SV, &full[s]);
                         o += ln[w];
                     }
             };
@@ -974,7 +977,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                 span(blockIdx.x, no0, no1);
                 desc(blockIdx.x, nd);
             }
-            int i = 0;
+            int i = 0, ps = 0, pround = 0;  // stage and round of tile i (no division by S)
             bool waited = false;
             for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
                 if (i == prefetched) {
@@ -993,7 +996,11 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                 // this tile's bounds and descriptors (loaded one step ago); the next tile's are
                 // loaded while this stage waits to be free
                 const int o0 = no0, o1 = no1;
-                const int s = i % kSpmvStages, round = i / kSpmvStages;
+                const int s = ps, round = pround;
+                if (++ps == S) {
+                    ps = 0;
+                    ++pround;
+                }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) s_desc[s][u] = nd[u];
                 if (tile + gridDim.x < ntiles) {
@@ -1052,9 +1059,9 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
     const T ca0 = (T)s_coef[0], cb0 = (T)s_coef[1], cc0 = (T)s_coef[2];
     const T ca1 = (T)s_coef[3], cb1 = (T)s_coef[4], cc1 = (T)s_coef[5];
     const T c2 = (T)s_coef[6];
-    int i = 0;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
-        const int s = i % kSpmvStages;
+    int s = 0;
+    uint32_t ph = 0;  // stage and phase of the current tile (no division by S)
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int rr = (int)(tile * R) + tid;
         const bool ok = rr < a.n;
         // row operands first: their loads overlap the wait and the products
@@ -1067,9 +1074,9 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                 if (w1) pw1 = w1[rr];
             }
         }
-        if (!mbar_wait_bounded(&full[s], (i / kSpmvStages) & 1, kWaitLimitNs)) {
+        if (!mbar_wait_bounded(&full[s], ph, kWaitLimitNs)) {
             if (lane == 0) atomicOr(&st->error, kErrTimeout);
-            mbar_wait_bounded(&full[s], (i / kSpmvStages) & 1, kWaitLimitNs);
+            mbar_wait_bounded(&full[s], ph, kWaitLimitNs);
             return;
         }
         const unsigned char *base = smem + s * stage_bytes;
@@ -1080,7 +1087,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
         T acc = T(0);
         if constexpr (G == 1) {
             if (X2) {
-                const T *s_x2 = s_x + xw_bytes / 4;
+                const T *s_x2 = s_x + xw_bytes / SV;
 #pragma unroll 8
                 for (int k = 0; k < w; ++k) {
                     const int q = s_ix[k * R + tid];
@@ -1095,7 +1102,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
             T part[G];
 #pragma unroll
             for (int g = 0; g < G; ++g) part[g] = T(0);
-            const T *s_x2 = s_x + xw_bytes / 4;
+            const T *s_x2 = s_x + xw_bytes / SV;
 #pragma unroll 2
             for (int k = 0; k < w; k += G) {
 #pragma unroll
@@ -1126,6 +1133,10 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+        }
     }
 }
 
@@ -1640,12 +1651,42 @@ bool vec_aligned(const VecRef &v)
            (((long long)v.col * v.ld * 4) & 15) == 0;
 }
 
+// The tile-ELL launch for value type T (float: ell[0], double: ell[1]).
+template <typename T>
+cudaError_t spmve_go(const DevMatrix &A, const SpmvEpi &e, Cycle *st, int check_done, cudaStream_t s, bool *launched)
+{
+    *launched = false;
+    const EllLaunch &L = A.ell[sizeof(T) == 8 ? 1 : 0];
+    const bool x2 = e.x2.base != nullptr;
+    long long g = x2 ? L.blocks_x2 : L.blocks;
+    const int nst = x2 ? L.nst_x2 : L.nst;
+    if (g <= 0) return cudaSuccess;
+    const void *vals = sizeof(T) == 8 ? (const void *)A.evals64 : (const void *)A.evals;
+    SpmvEArgs q{A.n, vals, A.eidx, A.toff, A.etwin, A.ewmax, A.excap, nst, st, check_done, e};
+    const long long etiles = ((long long)A.n + kThreads - 1) / kThreads;
+    if (g > etiles) g = etiles;
+    *launched = true;
+    const size_t smem = (size_t)nst * spmve_stage_bytes(A.ewmax, x2, A.excap, (int)sizeof(T));
+    const dim3 grid((unsigned)g), block(kSpmvThreads);
+    switch (A.lanes_per_row) {
+    case 2:
+        return x2 ? launch_pdl(k_spmv_e<T, true, 2>, grid, block, smem, s, q)
+                  : launch_pdl(k_spmv_e<T, false, 2>, grid, block, smem, s, q);
+    case 4:
+        return x2 ? launch_pdl(k_spmv_e<T, true, 4>, grid, block, smem, s, q)
+                  : launch_pdl(k_spmv_e<T, false, 4>, grid, block, smem, s, q);
+    default:
+        return x2 ? launch_pdl(k_spmv_e<T, true, 1>, grid, block, smem, s, q)
+                  : launch_pdl(k_spmv_e<T, false, 1>, grid, block, smem, s, q);
+    }
+}
+
 template <typename IDX>
 cudaError_t spmvw_go(const DevMatrix &A, const IDX *cols, const SpmvEpi &e, Cycle *st, int check_done, cudaStream_t s,
                      bool *launched)
 {
     *launched = false;
-    if (!vec_aligned(e.x) || (e.x2.base && !(vec_aligned(e.x2) && A.evals && A.spmvex_blocks > 0)))
+    if (!vec_aligned(e.x) || (e.x2.base && !(vec_aligned(e.x2) && A.evals && A.ell[0].blocks_x2 > 0)))
         return cudaSuccess;
     SpmvWArgs<IDX> p{};
     const VecRef *ops[4] = {&e.u0, &e.w0, &e.u1, &e.w1};
@@ -1666,27 +1707,7 @@ cudaError_t spmvw_go(const DevMatrix &A, const IDX *cols, const SpmvEpi &e, Cycl
     }
     const int R = A.rows_per_tile;
     const long long ntiles = ((long long)A.n + R - 1) / R;
-    if (A.evals && A.spmve_blocks > 0) {
-        SpmvEArgs q{A.n, A.evals, A.eidx, A.toff, A.etwin, A.ewmax, A.excap, st, check_done, e};
-        const bool x2 = e.x2.base != nullptr;
-        const long long etiles = ((long long)A.n + kThreads - 1) / kThreads;
-        long long g = x2 ? A.spmvex_blocks : A.spmve_blocks;
-        if (g > etiles) g = etiles;
-        *launched = true;
-        const size_t smem = kSpmvStages * spmve_stage_bytes(A.ewmax, x2, A.excap);
-        const dim3 grid((unsigned)g), block(kSpmvThreads);
-        switch (A.lanes_per_row) {
-        case 2:
-            return x2 ? launch_pdl(k_spmv_e<true, 2>, grid, block, smem, s, q)
-                      : launch_pdl(k_spmv_e<false, 2>, grid, block, smem, s, q);
-        case 4:
-            return x2 ? launch_pdl(k_spmv_e<true, 4>, grid, block, smem, s, q)
-                      : launch_pdl(k_spmv_e<false, 4>, grid, block, smem, s, q);
-        default:
-            return x2 ? launch_pdl(k_spmv_e<true, 1>, grid, block, smem, s, q)
-                      : launch_pdl(k_spmv_e<false, 1>, grid, block, smem, s, q);
-        }
-    }
+    if (A.evals && A.ell[0].blocks > 0) return spmve_go<float>(A, e, st, check_done, s, launched);
     p.a = SpmvArgs<float, IDX>{A.n, A.rowptr, cols, A.vals32, R, A.lanes_per_row, A.cap32, st, check_done, e};
     p.lidx = A.lidx;
     p.twin = A.twin;
@@ -1719,19 +1740,23 @@ cudaError_t sell_go(const DevMatrix &A, const T *vals, const IDX *cols, const Sp
 // Dynamic shared memory limit (the widest tile and the largest windows) and the largest
 // shared-memory carveout for the tile-ELL kernels: they alternate with the Gram-Schmidt passes, and
 // consecutive launches should never wait for an SM to change its L1 / shared-memory split.
-template <int G>
+template <typename T, int G>
 cudaError_t spmve_set_smem()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_spmv_e<false, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kSpmvStages * spmve_stage_bytes(kEllWidthMax, false, kXCap)));
+    const int sv = (int)sizeof(T);
+    const size_t cap = (size_t)smem_optin() - 1024;
+    size_t b1 = 3 * spmve_stage_bytes(kEllWidthMax, false, kXCap, sv);
+    size_t b2 = 3 * spmve_stage_bytes(kEllWidthMax, true, kXCap, sv);
+    if (b1 > cap) b1 = cap;
+    if (b2 > cap) b2 = cap;
+    cudaError_t e = cudaFuncSetAttribute(k_spmv_e<T, false, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spmv_e<true, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kSpmvStages * spmve_stage_bytes(kEllWidthMax, true, kXCap)));
+        e = cudaFuncSetAttribute(k_spmv_e<T, true, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b2);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spmv_e<false, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(k_spmv_e<T, false, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spmv_e<true, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(k_spmv_e<T, true, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
     return e;
 }
@@ -1750,9 +1775,9 @@ cudaError_t spmv_set_smem()
     if (e == cudaSuccess && sizeof(T) == 4)
         e = cudaFuncSetAttribute(k_spmv_w<IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kSpmvStages * spmvw_stage_bytes(kSpmvCapMax, (int)sizeof(IDX))));
-    if (e == cudaSuccess) e = spmve_set_smem<1>();
-    if (e == cudaSuccess) e = spmve_set_smem<2>();
-    if (e == cudaSuccess) e = spmve_set_smem<4>();
+    if (e == cudaSuccess) e = spmve_set_smem<T, 1>();
+    if (e == cudaSuccess) e = spmve_set_smem<T, 2>();
+    if (e == cudaSuccess) e = spmve_set_smem<T, 4>();
     return e;
 }
 
@@ -1782,6 +1807,12 @@ cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *s
         if (A.soff) return sell_go<float, short>(A, A.svals32, A.soff, e, st, check_done, s);
         return sell_go<float, int>(A, A.svals32, A.scol, e, st, check_done, s);
     }
+    if (A.format == kFmtCsrStaged && prec == kF64 && A.evals64 && vec_aligned(e.x) &&
+        (!e.x2.base || vec_aligned(e.x2))) {
+        bool launched = false;
+        const cudaError_t err = spmve_go<double>(A, e, st, check_done, s, &launched);
+        if (launched || err != cudaSuccess) return err;
+    }
     if (prec == kF64) {
         if (A.coloff) return spmv_go<double, short>(A, A.vals64, A.coloff, A.cap64, A.spmv_blocks64, e, st, check_done, s);
         return spmv_go<double, int>(A, A.vals64, A.colidx, A.cap64, A.spmv_blocks64, e, st, check_done, s);
@@ -1807,23 +1838,40 @@ cudaError_t launch_spmv2(const DevMatrix &A, int prec, const SpmvEpi &e1, const 
                                 ticket, diag, s);
 }
 
-template <int G>
-int spmve_per_sm_g(int wmax, bool x2, int xcap)
+template <typename T, int G>
+int spmve_per_sm_g(int wmax, bool x2, int xcap, int nst)
 {
     int nb = 0;
-    const size_t smem = kSpmvStages * spmve_stage_bytes(wmax, x2, xcap);
+    const size_t smem = (size_t)nst * spmve_stage_bytes(wmax, x2, xcap, (int)sizeof(T));
+    if (smem > (size_t)smem_optin() - 1024) return 0;
     if (x2)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e<true, G>, kSpmvThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e<T, true, G>, kSpmvThreads, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e<false, G>, kSpmvThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_e<T, false, G>, kSpmvThreads, smem);
     return nb > 0 ? nb : 0;
 }
 
-int spmve_per_sm(int G, int wmax, bool x2, int xcap)
+template <typename T>
+int spmve_per_sm_t(int G, int wmax, bool x2, int xcap, int nst)
 {
-    if (G == 2) return spmve_per_sm_g<2>(wmax, x2, xcap);
-    if (G == 4) return spmve_per_sm_g<4>(wmax, x2, xcap);
-    return spmve_per_sm_g<1>(wmax, x2, xcap);
+    if (G == 2) return spmve_per_sm_g<T, 2>(wmax, x2, xcap, nst);
+    if (G == 4) return spmve_per_sm_g<T, 4>(wmax, x2, xcap, nst);
+    return spmve_per_sm_g<T, 1>(wmax, x2, xcap, nst);
+}
+
+// Tile-ELL grid and pipeline depth for value type T: three stages when they fit, else two.
+template <typename T>
+void spmve_plan(DevMatrix *A, EllLaunch *L)
+{
+    for (int x2 = 0; x2 < 2; ++x2) {
+        int nst = 3, per = spmve_per_sm_t<T>(A->lanes_per_row, A->ewmax, x2 != 0, A->excap, 3);
+        if (per == 0) {
+            nst = 2;
+            per = spmve_per_sm_t<T>(A->lanes_per_row, A->ewmax, x2 != 0, A->excap, 2);
+        }
+        (x2 ? L->blocks_x2 : L->blocks) = per * A->num_sms;
+        (x2 ? L->nst_x2 : L->nst) = nst;
+    }
 }
 
 // Sets the dynamic shared memory limit (for the largest staging capacity, once) and returns
@@ -1839,8 +1887,10 @@ cudaError_t spmv_configure(DevMatrix *A)
         if (err != cudaSuccess) return err;
         done = true;
     }
-    A->spmve_blocks = A->evals ? spmve_per_sm(A->lanes_per_row, A->ewmax, false, A->excap) * A->num_sms : 0;
-    A->spmvex_blocks = A->evals ? spmve_per_sm(A->lanes_per_row, A->ewmax, true, A->excap) * A->num_sms : 0;
+    A->ell[0] = EllLaunch{};
+    A->ell[1] = EllLaunch{};
+    if (A->evals) spmve_plan<float>(A, &A->ell[0]);
+    if (A->evals64) spmve_plan<double>(A, &A->ell[1]);
     if (A->coloff) {
         A->spmv_blocks64 = spmv_per_sm<double, short>(A->cap64) * A->num_sms;
         A->spmv_blocks32 = spmv_per_sm<float, short>(A->cap32) * A->num_sms;

@@ -672,13 +672,16 @@ def test_graph_replay_is_bit_identical(mat):
 
 
 @pytest.mark.parametrize("mat", STAGED_MATS)
-def test_staged_kernel_is_bit_identical(mat):
-    """The float32 kernel that stages a tile's x windows and row operands in shared memory gives exactly
-    the row-block kernel's results: single SpMVs, p(A) in both bases, and whole solves."""
+@pytest.mark.parametrize("prec", [ppg.PPG_F32, ppg.PPG_F64])
+def test_staged_kernel_is_bit_identical(mat, prec):
+    """The kernels that stage a tile's x windows in shared memory (windowed CSR, and the tile-ELL blocks
+    with one thread per row) give exactly the row-block kernel's results in float32 and float64: single
+    SpMVs, polynomial construction and p(A) in both bases, and whole solves."""
     a = MATRICES[mat]()
     s = solver_for(a)
     assert s.spmv_format(ppg.PPG_SPMV_STAGED) == ppg.PPG_SPMV_STAGED
-    v = T(w.uniform(42, a.n), torch.float32)
+    vdt = torch.float32 if prec == ppg.PPG_F32 else torch.float64
+    v = T(w.uniform(42, a.n), vdt)
     b = T(w.rhs(a.n))
     v0 = T(w.v0(a.n))
     got = {}
@@ -688,7 +691,7 @@ def test_staged_kernel_is_bit_identical(mat):
         for basis, deg in ((ppg.PPG_BASIS_ROOTS, 10), (ppg.PPG_BASIS_POWER, 5)):
             s.build_poly(deg, basis, v0=v0)
             res.append(s.apply_poly(v).cpu().numpy())
-            x, info = s.solve(b, tol=1e-8, restart=30, maxit=400, precision=ppg.PPG_F32)
+            x, info = s.solve(b, tol=1e-8, restart=30, maxit=400, precision=prec)
             res += [x.cpu().numpy(), info.stats["iterations"]]
         got[fmt] = res
     for r1, r0 in zip(got[ppg.PPG_SPMV_STAGED], got[ppg.PPG_SPMV_CSR]):
