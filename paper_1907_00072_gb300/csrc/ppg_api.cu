@@ -1230,8 +1230,8 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
 
     // x windows per tile for the staged kernels: the tile's sorted distinct columns are grouped into
     // ranges (columns closer than kXGap share one), each widened to 16-byte boundaries and kept
-    // inside [0, n rounded down to 4); a tile needing more than kXWin ranges or kXCap entries keeps
-    // global gathers (lengths 0).  desc: [tiles][2 kXWin] (starts, lengths); lidx: per entry, its
+    // inside [0, n rounded down to 4); a tile needing more than maxw ranges or kXCap entries keeps
+    // global gathers (lengths 0).  desc: [tiles][2 maxw] (starts, lengths); lidx: per entry, its
     // index in the tile's concatenated windows; returns the number of covered tiles and the longest
     // window total.
     auto make_windows = [&](const std::vector<int> &hcol, long long Rt, int maxw, std::vector<int> &desc,

@@ -79,8 +79,9 @@ struct DevMatrix {
     // tile's rows reference, or lengths 0 when the tile's columns do not fit kXCap entries
     const int *twin;      // [ntiles][2 kXWin], or null
     const short *lidx;    // per entry: index of its column in the tile's concatenated windows
-    // tile-ELL copy (one lane per row, every tile windowed): tile t holds entries toff[t] ..
-    // toff[t+1]-1, entry k of row l at toff[t] + k R + l; padding has value 0 and index kXCap
+    // tile-ELL copy (one thread per row, tiles of kThreads rows, every tile windowed): tile t holds
+    // entries toff[t] .. toff[t+1]-1, entry k of row l at toff[t] + k kThreads + l; padding has value 0
+    // and index excap
     const float *evals;
     const short *eidx;
     const int *toff;      // tiles of kThreads rows + 1
