@@ -45,7 +45,7 @@ def workload_name(N, nnz=None):
 # DRAM traffic of one k_spmv_w<short> launch (a root step of the p(A) chain, C2 matrix) from the ncu
 # capture summarised in profiles/k_spmv_c2_128cubed.md, and the kernel source it was taken with: when the
 # source changes, the number no longer describes the kernel and the bench reports null.
-SPMV_TRAFFIC = {"src_sha256_16": "67c15ca163ec6d62", "dram_bytes": 105260032 + 5647872,
+SPMV_TRAFFIC = {"src_sha256_16": "0a7e88457ddfc9ac", "dram_bytes": 105260032 + 5647872,
                 "algorithmic_bytes": 112656384 + 16777216,
                 "launch": "k_spmv_e root step (tile-ELL values and window indices, x windows staged in "
                           "shared memory; write Y and P'), ncu --set full, cold caches; most of the 16.8 MB "

@@ -1317,7 +1317,7 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
         std::vector<int> edesc;
         std::vector<short> elidx;
         long long exmax = 0, ewindowed = -1;
-        if (ell_on && c->A.twin && (G == 1 || G == 2 || G == 4) && spmv_rows_per_thread() == 1)
+        if (ell_on && (G == 1 || G == 2 || G == 4) && spmv_rows_per_thread() == 1)
             ewindowed = make_windows(hcol, RE, kEWin, edesc, elidx, &exmax);
         if (ewindowed == etiles) {
             std::vector<double> hval(nnz);
@@ -1406,7 +1406,7 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
             c->A.svals64 = c->d_svals64;
             c->A.spadded = pos;
         }
-        c->A.format = c->A.twin ? kFmtCsrStaged : kFmtCsr;
+        c->A.format = (c->A.twin || c->A.evals) ? kFmtCsrStaged : kFmtCsr;
     }
     PPG_CK(gs_configure());
     PPG_CK(gram_configure());
@@ -1464,14 +1464,14 @@ ppg_status ppg_spmv_format(ppg_ctx *c, int request, int *in_effect)
     if (!c) return fail(PPG_ERR_INVALID_ARG, "null context");
     switch (request) {
     case PPG_SPMV_QUERY: break;
-    case PPG_SPMV_AUTO: c->A.format = c->A.twin ? kFmtCsrStaged : kFmtCsr; break;
+    case PPG_SPMV_AUTO: c->A.format = (c->A.twin || c->A.evals) ? kFmtCsrStaged : kFmtCsr; break;
     case PPG_SPMV_CSR: c->A.format = kFmtCsr; break;
     case PPG_SPMV_SELL:
         if (c->A.nslices == 0) return fail(PPG_ERR_INVALID_ARG, "no sliced ELL copy for this matrix");
         c->A.format = kFmtSell;
         break;
     case PPG_SPMV_STAGED:
-        if (!c->A.twin) return fail(PPG_ERR_INVALID_ARG, "no x windows for this matrix");
+        if (!c->A.twin && !c->A.evals) return fail(PPG_ERR_INVALID_ARG, "no x windows for this matrix");
         c->A.format = kFmtCsrStaged;
         break;
     default: return fail(PPG_ERR_INVALID_ARG, "unknown SpMV format request %d", request);

@@ -1686,8 +1686,7 @@ cudaError_t spmvw_go(const DevMatrix &A, const IDX *cols, const SpmvEpi &e, Cycl
                      bool *launched)
 {
     *launched = false;
-    if (!vec_aligned(e.x) || (e.x2.base && !(vec_aligned(e.x2) && A.evals && A.ell[0].blocks_x2 > 0)))
-        return cudaSuccess;
+    if (!vec_aligned(e.x) || e.x2.base) return cudaSuccess;
     SpmvWArgs<IDX> p{};
     const VecRef *ops[4] = {&e.u0, &e.w0, &e.u1, &e.w1};
     p.nslot = 0;
@@ -1707,7 +1706,6 @@ cudaError_t spmvw_go(const DevMatrix &A, const IDX *cols, const SpmvEpi &e, Cycl
     }
     const int R = A.rows_per_tile;
     const long long ntiles = ((long long)A.n + R - 1) / R;
-    if (A.evals && A.ell[0].blocks > 0) return spmve_go<float>(A, e, st, check_done, s, launched);
     p.a = SpmvArgs<float, IDX>{A.n, A.rowptr, cols, A.vals32, R, A.lanes_per_row, A.cap32, st, check_done, e};
     p.lidx = A.lidx;
     p.twin = A.twin;
@@ -1793,6 +1791,13 @@ int spmvw_per_sm(int cap)
 
 cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *st, int check_done, cudaStream_t s)
 {
+    // staged storage: the tile-ELL blocks where they exist, else the windowed CSR kernel (float32)
+    if (A.format == kFmtCsrStaged && A.evals && vec_aligned(e.x) && (!e.x2.base || vec_aligned(e.x2))) {
+        bool launched = false;
+        const cudaError_t err = prec == kF64 ? spmve_go<double>(A, e, st, check_done, s, &launched)
+                                             : spmve_go<float>(A, e, st, check_done, s, &launched);
+        if (launched || err != cudaSuccess) return err;
+    }
     if (A.format == kFmtCsrStaged && prec == kF32 && A.twin) {
         bool launched = false;
         const cudaError_t err = A.coloff ? spmvw_go<short>(A, A.coloff, e, st, check_done, s, &launched)
@@ -1806,12 +1811,6 @@ cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *s
         }
         if (A.soff) return sell_go<float, short>(A, A.svals32, A.soff, e, st, check_done, s);
         return sell_go<float, int>(A, A.svals32, A.scol, e, st, check_done, s);
-    }
-    if (A.format == kFmtCsrStaged && prec == kF64 && A.evals64 && vec_aligned(e.x) &&
-        (!e.x2.base || vec_aligned(e.x2))) {
-        bool launched = false;
-        const cudaError_t err = spmve_go<double>(A, e, st, check_done, s, &launched);
-        if (launched || err != cudaSuccess) return err;
     }
     if (prec == kF64) {
         if (A.coloff) return spmv_go<double, short>(A, A.vals64, A.coloff, A.cap64, A.spmv_blocks64, e, st, check_done, s);

@@ -79,18 +79,36 @@ def wide_band_matrix():
     return w.CSR(n, rowptr.astype(np.int32), colidx, vals, "wide_band")
 
 
+def multi_band_matrix():
+    """Five clusters of columns per row (offsets 0, +-1, +-2 and three-wide bands at +-3000 and +-6000):
+    every 256-row tile needs five x windows, more than the windowed CSR kernel takes, so only the
+    tile-ELL copy (up to eight windows per tile) stages x; 17 entries per row give two partial sums per
+    row; n is not a multiple of the tile height (x windows end on 16-byte boundaries inside the vector, so
+    n is a multiple of 4 for the last tile to have them)."""
+    n = 30012
+    offsets = [-6001, -6000, -5999, -3001, -3000, -2999, -2, -1, 0, 1, 2, 2999, 3000, 3001, 5999, 6000, 6001]
+    i = np.arange(n)[:, None]
+    cols = i + np.asarray(offsets)[None, :]
+    valid = (cols >= 0) & (cols < n)
+    vals = w.uniform(10, n * len(offsets)).reshape(n, len(offsets))
+    vals[:, offsets.index(0)] += 20.0
+    return w._assemble(n, offsets, valid, vals, "multi_band")
+
+
 MATRICES = {
     "c1_2d_64": w.c1_matrix,
     "3d_7pt_21": lambda: w.convdiff(21, 3, 50.0),
     "27pt_13": lambda: w.stencil27_perturbed(13),
+    "27pt_12": lambda: w.stencil27_perturbed(12),
     "random_ragged": lambda: w.random_csr(3001, 6, 17, diag_shift=0.5),
     "long_rows": long_row_matrix,
     "bidiag1": w.bidiag1,
     "wide_band": wide_band_matrix,
+    "multi_band": multi_band_matrix,
 }
 
 FORMATS = {"csr": ppg.PPG_SPMV_CSR, "sell": ppg.PPG_SPMV_SELL}
-STAGED_MATS = ["c1_2d_64", "3d_7pt_21", "27pt_13"]
+STAGED_MATS = ["c1_2d_64", "3d_7pt_21", "27pt_13", "27pt_12", "multi_band"]
 
 
 # ---------------------------------------------------------------- generator
@@ -121,7 +139,7 @@ def test_spmv_f64_matches_oracle(name, fmt):
 
 
 @pytest.mark.parametrize("fmt", list(FORMATS))
-@pytest.mark.parametrize("name", ["c1_2d_64", "27pt_13", "long_rows", "wide_band"])
+@pytest.mark.parametrize("name", ["c1_2d_64", "27pt_13", "long_rows", "wide_band", "multi_band"])
 def test_spmv_f32_matches_oracle(name, fmt):
     a = MATRICES[name]()
     x = w.uniform(32, a.n).astype(np.float32)
