@@ -150,11 +150,12 @@ ppg_status ppg_spmv(ppg_ctx *ctx, const void *x, void *y, int precision);
  *     window indices (w = the tile's longest row, padding pointing at a zero), and a float64 copy of
  *     them, which STAGED then reads instead in float32 and float64: one thread per row, no row
  *     pointers, w shared-memory multiply-adds per row.
- * PPG_SPMV_AUTO selects STAGED when the windows exist and the row-block CSR kernel otherwise (measured per
- * SpMV: 7-point 128^3 25.2 us with CSR, 16.6 us STAGED; 27-point 100^3 44.4 and 28.5 us; SELL slower than
- * both); PPG_SPMV_CSR, PPG_SPMV_SELL and PPG_SPMV_STAGED force one (STAGED applies to
- * float32 links, and float64 and two-input links w = A (x + s x2) where the dense blocks exist; others run
- * as CSR).
+ * The windows end on 16-byte boundaries inside x, so when n is not a multiple of 4 the last tile has
+ * none and no dense blocks are built.  STAGED is available when either copy exists; PPG_SPMV_AUTO then
+ * selects it, and the row-block CSR kernel otherwise (measured per SpMV: 7-point 128^3 25.2 us with CSR,
+ * 16.6 us STAGED; 27-point 100^3 44.4 and 28.5 us; SELL slower than both).  PPG_SPMV_CSR, PPG_SPMV_SELL
+ * and PPG_SPMV_STAGED force one (STAGED applies to float32 links, and to float64 and two-input links
+ * w = A (x + s x2) where the dense blocks exist; others run as CSR).
  * Every result is the same sum; CSR and STAGED give identical bits.  request = PPG_SPMV_QUERY changes
  * nothing; *in_effect (host, may be NULL) receives the format now used.
  * Errors: PPG_ERR_INVALID_ARG (unknown request, or a format whose copy was not built). */
