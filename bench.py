@@ -365,7 +365,8 @@ def main():
         "config": {"workload": workload_name(args.N, a.nnz), "degree": args.degree, "basis": "roots (Leja)",
                    "restart": 50,
                    "precision": "f32 inner, f64 refinement" if prec == ppg.PPG_F32 else "f64",
-                   "l2": "inputs larger than L2 (CSR 175 MB, basis up to 857 MB)",
+                   "l2": "working set of a step larger than L2 (matrix blocks 88 MB float32 + 117 MB "
+                         "float64, basis up to 428 MB float32), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iterations": last["iterations"], "restarts": last["restarts"], "relres_true": last["relres_true"],
         "relres_host_check": relres_host,
