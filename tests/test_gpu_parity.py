@@ -152,7 +152,8 @@ def test_spmv_f32_matches_oracle(name, fmt):
 
 
 def test_spmv_format_choice_and_nonfinite_padding():
-    """The automatic choice is the staged row-block kernel for banded matrices and the plain one otherwise;
+    """The automatic choice is the staged storage (x windows, tile-ELL blocks) for banded matrices and the
+    plain row-block kernel otherwise;
     the sliced copy is selectable; padding entries of the sliced format never touch x (an Inf in x
     reaches only the rows that reference it)."""
     s = solver_for(w.c1_matrix())
