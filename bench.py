@@ -10,7 +10,7 @@ p(A)/Arnoldi solve with float64 iterative refinement; the float64 solve and the
 other degrees are reported under "variants".
 
   python bench.py [--gpus N --steps K --warmup W] [--degree D] [--precision f32|f64]
-  python bench.py --impl reference ...   # the CPU oracle, bounded sample, same metric
+  python bench.py --impl reference ...   # the CPU oracle: one full solve per step, same metric
 """
 from __future__ import annotations
 
@@ -159,41 +159,54 @@ def max_over_ranks(v, world, device=None):
 # --------------------------------------------------------------------------- CPU oracle
 
 
-def oracle_sample(a, b, deg, iters=2):
-    """The oracle on the same workload, bounded: polynomial build + `iters` GMRES iterations."""
+def oracle_solve(N, deg, with_x=False):
+    """One full oracle time-to-solution on the benchmark workload (one host core): the polynomial
+    of the given degree from the seeded v0, then MGS PP-GMRES(50) to relative residual 1e-8.
+    Returns (seconds, iterations, relres, x or None)."""
     import oracle
 
+    a = w.c2_matrix(N)
+    b = w.rhs(a.n)
     v0 = w.v0(a.n)
     t0 = time.perf_counter()
     p = oracle.poly_gmres(a, v0, deg)
+    r = oracle.gmres(a, b, p, tol=1e-8, m=50, maxit=20000)
     t1 = time.perf_counter()
-    r = oracle.gmres(a, b, p, tol=1e-8, m=50, maxit=iters)
-    t2 = time.perf_counter()
-    return t1 - t0, (t2 - t1) / max(r.iters, 1)
+    return t1 - t0, r.iters, r.relres, (r.x if with_x else None)
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the oracle, as it stands, on the host cores.  Every step is one full
+    time-to-solution (build + solve to 1e-8, one core each); the steps run as independent processes,
+    at most --ref-workers at a time, so the run ends within a few minutes; each reports its own time."""
     if rank != 0:
         return
-    a = w.c2_matrix(args.N)
-    b = w.rhs(a.n)
-    est_iters = args.ref_iters
-    times = []
-    for i in range(args.warmup + args.steps):
-        tb, ti = oracle_sample(a, b, args.degree, iters=2)
-        if i >= args.warmup:
-            times.append((tb + est_iters * ti) * 1e3)
-    v = statistics.mean(times)
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    nsteps = args.warmup + args.steps
+    workers = max(1, min(args.ref_workers, nsteps, os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(oracle_solve, [args.N] * nsteps, [args.degree] * nsteps))
+    wall = time.perf_counter() - t0
+    timed = res[args.warmup:]
+    v = statistics.mean(t for t, _, _, _ in timed) * 1e3
+    iters = timed[-1][1]
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.N, a.nnz), "degree": args.degree, "basis": "arnoldi-form (oracle)",
-                   "restart": 50, "iterations_assumed": est_iters},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"oracle polynomial build (degree {args.degree}) + 2 GMRES(50) iterations on the "
-                                   f"full matrix per step; time-to-solution = build + {est_iters} x per-iteration time"},
-        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.N, w.expected_nnz_convdiff(args.N, 3)), "degree": args.degree,
+                   "basis": "arnoldi-form (oracle)", "restart": 50},
+        "iterations": iters, "relres_true": timed[-1][2],
+        "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "host_cores": os.cpu_count(), "concurrent_steps": workers,
+                         "sample": f"full solve per step: oracle polynomial build (degree {args.degree}) + MGS "
+                                   f"PP-GMRES(50) to relative residual 1e-8 ({iters} iterations), one core per "
+                                   f"step, {workers} steps at a time on {os.cpu_count()} host cores"},
+        "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "consistency": {"wall_s": round(wall, 1), "sum_of_step_seconds": round(sum(t for t, _, _, _ in res), 1)},
     }
     print(json.dumps(line), flush=True)
 
@@ -212,7 +225,8 @@ def main():
     ap.add_argument("--N", type=int, default=128, help="grid side (128 is the benchmark workload)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--ref-iters", type=int, default=60)
+    ap.add_argument("--ref-workers", type=int, default=8,
+                    help="reference arm: full oracle solves run at once (one core each)")
     ap.add_argument("--profile-harness", action="store_true",
                     help="for ncu: build the polynomial and run --harness-iters iterations of one solve, print no "
                          "benchmark line")
@@ -260,9 +274,9 @@ def main():
         s.close()
         return
 
-    def step(deg=args.degree, precision=prec, bvec=b):
+    def step(deg=args.degree, precision=prec, bvec=b, f32_form=ppg.PPG_F32_FLEXIBLE):
         used, _ = s.build_poly(deg, ppg.PPG_BASIS_ROOTS, v0=v0)
-        x, info = s.solve(bvec, tol=1e-8, restart=50, maxit=20000, precision=precision)
+        x, info = s.solve(bvec, tol=1e-8, restart=50, maxit=20000, precision=precision, f32_form=f32_form)
         return x, info
 
     for _ in range(args.warmup):
@@ -329,33 +343,43 @@ def main():
     idx_bytes = 2 if np.abs(a.colidx.astype(np.int64) - rows).max() <= 32767 else 4  # stored index format
     spmv_bytes = a.nnz * (sv + idx_bytes) + 4 * (a.n + 1) + 2 * a.n * sv
 
-    # ---- variants: degree x precision, one measured solve each
+    x_bench = x.cpu().numpy()
+
+    # ---- variants: degree x precision (x float32 form), one warm-up and five timed steps each
     variants = {}
     if not args.no_variants:
+        forms = (("f64", ppg.PPG_F64, ppg.PPG_F32_FLEXIBLE), ("f32", ppg.PPG_F32, ppg.PPG_F32_FLEXIBLE),
+                 ("f32_standard", ppg.PPG_F32, ppg.PPG_F32_STANDARD))
         for deg in (1, 10, 25, 40):
-            for pname, pv in (("f64", ppg.PPG_F64), ("f32", ppg.PPG_F32)):
-                step(deg, pv)
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                ea.record(stream)
-                _, inf = step(deg, pv)
-                eb.record(stream)
-                torch.cuda.synchronize()
+            for pname, pv, form in forms:
+                step(deg, pv, f32_form=form)
+                ms_list = []
+                for _ in range(5):
+                    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    ea.record(stream)
+                    _, inf = step(deg, pv, f32_form=form)
+                    eb.record(stream)
+                    torch.cuda.synchronize()
+                    ms_list.append(ea.elapsed_time(eb))
                 variants[f"d{deg}_{pname}"] = {
-                    "ms": round(ea.elapsed_time(eb), 3), "iterations": inf.stats["iterations"],
-                    "restarts": inf.stats["restarts"], "relres_true": inf.stats["relres_true"],
-                    "status": inf.status}
+                    "ms_median": round(statistics.median(ms_list), 3), "ms_min": round(min(ms_list), 3),
+                    "ms_max": round(max(ms_list), 3), "repeats": len(ms_list),
+                    "iterations": inf.stats["iterations"], "restarts": inf.stats["restarts"],
+                    "relres_true": inf.stats["relres_true"], "status": inf.status}
 
     traffic, traffic_info = spmv_traffic()
     cpu = None
+    parity = None
     if rank == 0 and not args.no_cpu:
-        tb, ti = oracle_sample(a, b_h, args.degree, iters=2)
-        it64 = variants.get(f"d{args.degree}_f64", {}).get("iterations", last["iterations"])
-        cpu_ms = (tb + it64 * ti) * 1e3
-        cpu = {"value": round(cpu_ms, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"oracle build (degree {args.degree}) + 2 GMRES(50) iterations on the full matrix; "
-                         f"time-to-solution = build + {it64} iterations x measured per-iteration time"}
+        # one full oracle solve (after the GPU work: no host load during the timed region)
+        secs, it_o, rr_o, x_o = oracle_solve(args.N, args.degree, with_x=True)
+        cpu = {"value": round(secs * 1e3, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "host_cores": os.cpu_count(),
+               "sample": f"one full solve: oracle polynomial build (degree {args.degree}) + MGS PP-GMRES(50) to "
+                         f"relative residual 1e-8 ({it_o} iterations) on one host core"}
+        parity = {"oracle_iterations": it_o, "oracle_relres": rr_o, "iterations": last["iterations"],
+                  "x_err_vs_oracle": float(np.linalg.norm(x_bench - x_o) / np.linalg.norm(x_o))}
 
     line = {
         "metric": METRIC, "value": round(ms, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -364,7 +388,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload_name(args.N, a.nnz), "degree": args.degree, "basis": "roots (Leja)",
                    "restart": 50,
-                   "precision": "f32 inner, f64 refinement" if prec == ppg.PPG_F32 else "f64",
+                   "precision": ("f32 inner (flexible form, restart projection), f64 refinement"
+                                 if prec == ppg.PPG_F32 else "f64"),
                    "l2": "working set of a step larger than L2 (matrix blocks 88 MB float32 + 117 MB "
                          "float64, basis up to 428 MB float32), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -387,6 +412,7 @@ def main():
         "spmv_plain": {"achieved": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
                        "ms_per_launch": round(spmv_ms, 5), "bytes_per_launch": spmv_bytes},
         "cpu_baseline": cpu,
+        "parity": parity,
         "e2e": {"value": round(e2e_ms, 3), "unit": UNIT, "h2d_bytes_per_step": 8 * a.n, "d2h_bytes_per_step": 8 * a.n},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),

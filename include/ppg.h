@@ -66,10 +66,21 @@ enum {
     PPG_F32 = 1  /* float32 p(A) and Arnoldi; float64 true residual, Hessenberg least squares and updates of x */
 };
 
+/* form of the float32 inner solve (ppg_opts.f32_form) */
+enum {
+    PPG_F32_FLEXIBLE = 0, /* default: the preconditioned vectors z_j = p(A) v_j are kept (float32) and x += Z y
+                             at the end of a cycle (flexible GMRES, the same iterates as right-preconditioned
+                             GMRES in exact arithmetic), and before a restart the float64 true residual is
+                             projected onto the finished cycle's space (x += Z u, u the least-squares solution
+                             of H u ~ V^T r, zero in exact arithmetic) */
+    PPG_F32_STANDARD = 1  /* x += p(A) V y with p(A) applied in float32, no projection */
+};
+
 typedef struct {
     int precision;     /* PPG_F64 (default) or PPG_F32 */
     double inner_rtol; /* PPG_F32 only: a restart cycle also ends when its residual estimate has dropped by
-                          this factor (iterative refinement step); <= 0 selects 1e-6 */
+                          this factor (iterative refinement step); <= 0 selects the default of the form
+                          (flexible: 1e-7, about the accuracy one float32 cycle attains; standard: 1e-6) */
     int use_graph;     /* 1: replay each Arnoldi iteration (the p(A) chain and the three Gram-Schmidt
                           passes) from a CUDA graph, captured the second time an iteration index comes
                           round with the same polynomial, workspace, precision and storage format (the
@@ -78,7 +89,8 @@ typedef struct {
                           kernels one by one; < 0: library default (graphs) */
     int profile;       /* 1: time every SpMV and Gram-Schmidt launch with CUDA events and report their
                           device time and algorithmic bytes in ppg_stats (adds a sync per cycle) */
-    int reserved[4];
+    int f32_form;      /* PPG_F32 only: PPG_F32_FLEXIBLE (0, default) or PPG_F32_STANDARD */
+    int reserved[3];
 } ppg_opts;
 
 typedef struct {

@@ -167,7 +167,7 @@ def run_c5(args):
     s = _solver(a)
     s.build_poly(20, ppg.PPG_BASIS_ROOTS, v0=_T(w.v0(a.n), torch.float64))
     roots = s.get_poly()[2]
-    vals = _T(a.vals, torch.float64).requires_grad_(True)
+    vals = s.vals.requires_grad_(True)  # the tensor the context was created from
     b = _T(bh, torch.float64).requires_grad_(True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -159,6 +159,8 @@ struct Layout {
     int ncols;
     char *vec[kNumVecs];  // working vectors of ld elements
     size_t esize;
+    char *zbasis;  // float32 layouts: the preconditioned basis Z (ncols - 1 columns) of flexible solves,
+                   // in the half of the float64-sized region that float32 columns leave free
 };
 
 size_t partial_doubles(const ppg_ctx *c)
@@ -195,10 +197,13 @@ ppg_status get_layout(ppg_ctx *c, int ncols, size_t esize, Layout *L)
     L->ncols = ncols;
     L->esize = esize;
     for (int i = 0; i < kNumVecs; ++i) L->vec[i] = L->basis + (size_t)(ncols + i) * c->ld * esize;
+    // (ncols + kNumVecs) float64 columns hold, in float32, the basis, the vectors and Z
+    L->zbasis = esize == sizeof(float) ? L->basis + (size_t)(ncols + kNumVecs) * c->ld * esize : nullptr;
+    const int zcols = L->zbasis ? ncols - 1 : 0;
     // rows n..ld-1 of every column and vector must read as zero
     if (c->ld > c->A.n) {
         PPG_CK(cudaMemset2DAsync(L->basis + (size_t)c->A.n * esize, c->ld * esize, 0, (c->ld - c->A.n) * esize,
-                                 ncols + kNumVecs, c->stream));
+                                 ncols + kNumVecs + zcols, c->stream));
     }
     return PPG_OK;
 }
@@ -568,6 +573,49 @@ struct Exec {
         return spmv(e, check);
     }
 
+    // Flexible form: z = p(A) (scale * src) is written to zdst (the preconditioned basis column of the
+    // iteration) and w = A z.  When the product form ends with a real root, the last update
+    // z = y + t P rides on the SpMV's gather as in poly_then_A, and the SpMV's second output writes
+    // that z (the same fused value the gather used) to zdst.
+    ppg_status poly_then_A_flex(VecRef src, const double *sig, VecRef zdst, VecRef w, char *const tmp[4], int check)
+    {
+        chain_begin();
+        PPG_TRY(poly_then_A_flex_links(src, sig, zdst, w, tmp, check));
+        return chain_end();
+    }
+    ppg_status poly_then_A_flex_links(VecRef src, const double *sig, VecRef zdst, VecRef w, char *const tmp[4],
+                                      int check)
+    {
+        char *t3[3] = {tmp[1], tmp[2], tmp[3]};
+        const int k = c->degree + 1;
+        const bool defer = c->basis == PPG_BASIS_ROOTS && k >= 2 && c->roots[2 * (k - 1) + 1] == 0.0;
+        const VecRef acc = defer ? vfix(tmp[0]) : zdst;
+        Deferred d;
+        PPG_TRY(poly_apply_links(src, sig, acc, t3, check, defer ? &d : nullptr));
+        SpmvEpi e = epi_none();
+        e.x = acc;
+        e.out0 = w;
+        e.a0 = simm(1.0);
+        if (d.active) {
+            e.x2 = d.P;
+            e.s2 = d.t;
+            e.out1 = zdst;
+            e.a1 = simm(0.0);
+            e.u1 = acc;
+            e.b1 = simm(1.0);
+            e.w1 = d.P;
+            e.c1 = d.t;
+        } else if (defer) {  // the chain did not leave the last root to the SpMV: z is the accumulator
+            SpmvEpi cpy = epi_none();
+            cpy.out0 = zdst;
+            cpy.u0 = acc;
+            cpy.b0 = simm(1.0);
+            PPG_TRY(axpy(cpy, check));
+            e.x = zdst;
+        }
+        return spmv(e, check);
+    }
+
     // number of SpMVs in one application of p(A)
     int poly_spmvs() const
     {
@@ -582,13 +630,16 @@ struct Iter {
     Exec *x;
     const Layout *L;
     int maxcols;  // restart + 1: bound on the columns a cycle-end combination uses
+    bool flex = false;  // flexible float32 form: z_j = p(A) v_j kept in L->zbasis, x += Z y
 
-    ppg_status gs(int op, int from_k, void *out, int out_follow, int kcols)
+    // U: the basis the pass streams (null: the Krylov basis V); w: its vector input (null: vec[0])
+    ppg_status gs(int op, int from_k, void *out, int out_follow, int kcols, const void *U = nullptr,
+                  void *w = nullptr)
     {
         GsArgs a{};
-        a.U = L->basis;
+        a.U = U ? U : L->basis;
         a.ldu = x->c->ld;
-        a.w = L->vec[0];
+        a.w = w ? w : L->vec[0];
         a.out = out;
         a.out_follow = out_follow;
         a.op = op;
@@ -599,11 +650,22 @@ struct Iter {
         // bytes: k columns read, w read (except when combining), one vector written (passes 2-4);
         // at the cycle end k is known only after the cycle (kcol_bytes is scaled by it then)
         const double col = (double)x->A->n * (x->prec == kF64 ? 8.0 : 4.0);
-        const double fixed = col * ((op != kGsCombine ? 1.0 : 0.0) + (op != kGsDot ? 1.0 : 0.0));
+        double fixed = col * ((op != kGsCombine ? 1.0 : 0.0) + (op != kGsDot ? 1.0 : 0.0));
+        if (op == kGsProj) fixed = 2.0 * col;  // w and the extra column v_k
         if (from_k)
             prof_add(x->c, fixed, col);
         else
             prof_add(x->c, fixed + col * kcols, 0.0);
+        return PPG_OK;
+    }
+
+    // x += Z y (flexible form): k columns of Z read, x read and written in float64
+    ppg_status combine_x(double *xsol, int skip_if_stop)
+    {
+        x->c->launches++;
+        PPG_CK(launch_combine_x(x->prec, L->zbasis, x->c->ld, x->A->n, xsol, x->c->st, skip_if_stop,
+                                x->c->num_sms, x->s));
+        prof_add(x->c, 16.0 * x->A->n, (double)x->A->n * (x->prec == kF64 ? 8.0 : 4.0));
         return PPG_OK;
     }
 
@@ -615,7 +677,11 @@ struct Iter {
         c->prof_j = j;
         char *tmp[4] = {L->vec[1], L->vec[2], L->vec[3], L->vec[4]};
         prof_open(c, x->s, 0);
-        PPG_TRY(x->poly_then_A(vcol(L->basis, c->ld, 0), c->st->sigma, vfix(L->vec[0]), tmp, kSkipIfDone));
+        if (flex)
+            PPG_TRY(x->poly_then_A_flex(vcol(L->basis, c->ld, 0), c->st->sigma, vcol(L->zbasis, c->ld, 0),
+                                        vfix(L->vec[0]), tmp, kSkipIfDone));
+        else
+            PPG_TRY(x->poly_then_A(vcol(L->basis, c->ld, 0), c->st->sigma, vfix(L->vec[0]), tmp, kSkipIfDone));
         prof_close(c, x->s);
         prof_open(c, x->s, 1);
         PPG_TRY(gs(kGsDot, 0, nullptr, 0, j + 1));
@@ -639,6 +705,7 @@ struct Iter {
         };
         put((unsigned long long)(uintptr_t)L->basis);
         put((unsigned long long)(uintptr_t)L->partials);
+        put((unsigned long long)(uintptr_t)(flex ? L->zbasis : nullptr));
         put((unsigned long long)c->ld);
         put((unsigned long long)((c->A.format << 8) | (c->fuse << 4) | (c->has_poly << 2) | c->basis));
         put((unsigned long long)c->degree);
@@ -653,8 +720,9 @@ struct Iter {
     {
         ppg_ctx *c = x->c;
         if (!use_graph || c->prof || c->graphs_broken || j >= kKmax) return iteration(j);
-        const size_t slot = (size_t)j + (size_t)kKmax * (size_t)(2 * (x->prec == kF64 ? 1 : 0) + (c->has_poly ? 1 : 0));
-        if (c->igraphs.size() < (size_t)(4 * kKmax)) c->igraphs.resize(4 * kKmax);
+        const size_t form = flex ? 2 : (x->prec == kF64 ? 1 : 0);
+        const size_t slot = (size_t)j + (size_t)kKmax * (size_t)(2 * form + (c->has_poly ? 1 : 0));
+        if (c->igraphs.size() < (size_t)(6 * kKmax)) c->igraphs.resize(6 * kKmax);
         ppg_ctx::IterGraph &g = c->igraphs[slot];
         std::vector<double> sig;
         signature(sig);
@@ -700,10 +768,17 @@ struct Iter {
         return PPG_OK;
     }
 
-    // x += p(A) V y with the coefficients the last pass-3 finalisation left in coef.
+    // x += p(A) V y with the coefficients the last pass-3 finalisation left in coef (flexible form:
+    // x += Z y with the y it left, in float64).
     ppg_status cycle_end(double *xsol)
     {
         x->c->prof_j = -2;
+        if (flex) {
+            prof_open(x->c, x->s, 1);
+            PPG_TRY(combine_x(xsol, 0));
+            prof_close(x->c, x->s);
+            return PPG_OK;
+        }
         char *z = L->vec[5], *e = L->vec[6];
         prof_open(x->c, x->s, 1);
         PPG_TRY(gs(kGsCombine, 1, z, 0, maxcols));
@@ -718,6 +793,22 @@ struct Iter {
         }
         x->c->launches++;
         PPG_CK(launch_xupdate(x->A->n, x->prec, corr, xsol, x->c->st, x->s));
+        return PPG_OK;
+    }
+
+    // Flexible form, before a restart: r = b - A x (float64, kept in float32 in vec[7]); unless the
+    // solve stops there, y = argmin ||H y - V^T r|| over the finished cycle's space and x += Z y.
+    // The residual that follows starts the next cycle.
+    ppg_status restart_projection(const double *b, double *xsol)
+    {
+        ppg_ctx *c = x->c;
+        c->prof_j = -2;
+        c->launches++;
+        PPG_CK(launch_residual(c->A, x->prec, b, xsol, L->vec[7], c->st, L->partials, x->s, 1));
+        prof_open(c, x->s, 1);
+        PPG_TRY(gs(kGsProj, 1, nullptr, 0, maxcols, L->basis, L->vec[7]));
+        PPG_TRY(combine_x(xsol, 1));
+        prof_close(c, x->s);
         return PPG_OK;
     }
 };
@@ -854,6 +945,22 @@ ppg_status prof_close_cycle(ppg_ctx *c)
     return PPG_OK;
 }
 
+// Profiling of a restart projection (flexible form): its launches did work when the device
+// counted a projection; k is still the finished cycle's (the next residual resets it).
+ppg_status prof_close_proj(ppg_ctx *c, long long nproj_before)
+{
+    PPG_TRY(read_state(c));
+    const bool ran = c->h_st->nproj > nproj_before;
+    const int k = c->h_st->k;
+    for (size_t i = c->rec_first; i < c->recs.size(); ++i) {
+        ppg_ctx::ProfRec &r = c->recs[i];
+        r.valid = ran;
+        r.bytes += r.kcol_bytes * k;
+    }
+    c->rec_first = c->recs.size();
+    return PPG_OK;
+}
+
 void prof_collect(ppg_ctx *c, ppg_stats *st)
 {
     for (const ppg_ctx::ProfRec &r : c->recs) {
@@ -922,9 +1029,14 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
     if (maxit < 0 || !(tol >= 0.0)) return fail(PPG_ERR_INVALID_ARG, "bad tol or maxit");
     const int prec = opts ? opts->precision : PPG_F64;
     if (prec != PPG_F64 && prec != PPG_F32) return fail(PPG_ERR_INVALID_ARG, "unknown precision");
+    const int form = opts ? opts->f32_form : PPG_F32_FLEXIBLE;
+    if (form != PPG_F32_FLEXIBLE && form != PPG_F32_STANDARD) return fail(PPG_ERR_INVALID_ARG, "unknown f32_form");
+    // the flexible form keeps z_j = p(A) v_j; with no polynomial (or a scalar one) z_j is v_j itself
+    const bool flex = prec == PPG_F32 && form == PPG_F32_FLEXIBLE && c->has_poly &&
+                      !(c->basis == PPG_BASIS_POWER && c->degree == 0);
     double inner = 0.0;
     if (prec == PPG_F32) {
-        inner = (opts && opts->inner_rtol > 0.0) ? opts->inner_rtol : 1e-6;
+        inner = (opts && opts->inner_rtol > 0.0) ? opts->inner_rtol : (flex ? 1e-7 : 1e-6);
         PPG_TRY(ensure_f32(c));
     }
     const size_t es = prec == PPG_F64 ? 8 : 4;
@@ -936,6 +1048,7 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
 
     Exec ex{c, &c->A, prec, c->stream};
     Iter it{&ex, &L, ncols};
+    it.flex = flex;
     it.use_graph = !opts || opts->use_graph != 0;
     c->prof = opts && opts->profile;
     c->prof_open = false;
@@ -948,7 +1061,6 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
     c->launches++;
     PPG_CK(launch_norm_start(c->A.n, kF64, b, nullptr, 0, c->st, L.partials, c->A.resid_blocks, c->stream));
     PPG_TRY(read_state(c));
-    long long residuals = 0;
     if (c->h_st->bnorm == 0.0) {
         PPG_CK(cudaMemsetAsync(x, 0, sizeof(double) * c->A.n, c->stream));
         c->h_st->converged = 1;
@@ -956,15 +1068,18 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
     } else {
         c->launches++;
         PPG_CK(launch_residual(c->A, prec, b, x, L.basis, c->st, L.partials, c->stream));
-        residuals++;
         PPG_TRY(read_state(c));
         while (!c->h_st->stop) {
             PPG_TRY(run_cycle(c, it, restart));
             PPG_TRY(it.cycle_end(x));
             if (c->prof) PPG_TRY(prof_close_cycle(c));
+            if (flex) {
+                const long long np = c->h_st->nproj;
+                PPG_TRY(it.restart_projection(b, x));
+                if (c->prof) PPG_TRY(prof_close_proj(c, np));
+            }
             c->launches++;
             PPG_CK(launch_residual(c->A, prec, b, x, L.basis, c->st, L.partials, c->stream));
-            residuals++;
             PPG_TRY(read_state(c));
         }
     }
@@ -977,9 +1092,12 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
         memset(stats, 0, sizeof *stats);
         stats->iterations = h.iters;
         stats->restarts = h.cycles;
+        // per iteration p(A) and A; per cycle end p(A) once (not in the flexible form); every
+        // true residual; dots: three per iteration (Section III), a norm per residual, and one block
+        // inner product per restart projection
         const int ps = ex.poly_spmvs();
-        stats->spmvs = h.iters * (long long)(ps + 1) + h.cycles * (long long)ps + residuals;
-        stats->dots = 3 * h.iters + residuals;
+        stats->spmvs = h.iters * (long long)(ps + 1) + (flex ? 0 : h.cycles * (long long)ps) + h.nres;
+        stats->dots = 3 * h.iters + h.nres + h.nproj;
         stats->kernel_launches = c->launches - launches0;
         stats->relres_true = h.relres;
         stats->relres_est = h.est;

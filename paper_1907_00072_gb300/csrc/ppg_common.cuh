@@ -40,6 +40,8 @@ struct Cycle {
     long long iters;    // iterations over all cycles
     long long maxit;
     long long cycles;
+    long long nres;     // float64 true residuals computed (b - A x)
+    long long nproj;    // restart projections done (flexible float32 solves)
     double bnorm;       // ||b||
     double tol;         // relative tolerance
     double inner_rtol;  // cycle ends when |g_{j+1}| <= inner_rtol * beta (0: off)

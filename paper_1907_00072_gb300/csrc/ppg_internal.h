@@ -131,6 +131,8 @@ enum GsOp : int {
     kGsUpdDot = 2,     // w -= U coef; h2 = sigma .* (U^T w)      -> finalize pass 2
     kGsUpdNorm = 3,    // out = w - U coef; ||out||^2             -> finalize pass 3 (Hessenberg column)
     kGsCombine = 4,    // out = -U coef (cycle end: z = V y)
+    kGsProj = 6,       // c = sigma .* (U^T w) over the finished cycle's k + 1 columns, then y = the least-
+                       // squares solution of H y ~ c with the cycle's rotations and R (restart projection)
 };
 
 struct GsArgs {
@@ -148,6 +150,12 @@ struct GsArgs {
     int nstages;  // pipeline depth; set by launch_gs
 };
 
+// x += U y (float64 x and y = Cycle::y, k = Cycle::k columns of U; flexible cycle end and restart
+// projection, U = the preconditioned basis Z); rows n..ld-1 of U are not read.  skip_if_stop: return
+// at once when the solve has stopped.
+cudaError_t launch_combine_x(int prec, const void *U, long long ld, long long n, double *x, Cycle *st,
+                             int skip_if_stop, int num_sms, cudaStream_t s);
+
 cudaError_t launch_validate(int n, long long nnz, const int *rowptr, const int *colidx, int *flag, cudaStream_t s);
 cudaError_t launch_cast_f32(const double *in, float *out, long long count, cudaStream_t s);
 // check: 0 always run; kSkipIfDone: return when the cycle is done (iteration kernels);
@@ -157,8 +165,11 @@ cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *s
 cudaError_t launch_axpy(int n, int prec, const SpmvEpi &e, Cycle *st, int check, cudaStream_t s);
 // r = b - A x in float64 written as prec into out (column 0 of the basis); ||r|| finalises the
 // start of a restart cycle in st.
+// proj = 1: the residual before a restart projection: out = r unscaled; the convergence, iteration-
+// limit and finiteness tests as above, but a solve that goes on keeps the finished cycle's state
+// (k, the rotations, R) for the projection and the next residual starts the cycle.
 cudaError_t launch_residual(const DevMatrix &A, int out_prec, const double *b, const double *x, void *out,
-                            Cycle *st, double *partials, cudaStream_t s);
+                            Cycle *st, double *partials, cudaStream_t s, int proj = 0);
 // ||v||: mode 0 stores ||v|| in st->bnorm; mode 1 starts an Arnoldi run from v (beta, sigma_0, copy into out)
 cudaError_t launch_norm_start(int n, int out_prec, const double *v, void *out, int mode, Cycle *st,
                               double *partials, int nblk, cudaStream_t s);

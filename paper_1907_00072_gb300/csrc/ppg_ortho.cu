@@ -108,6 +108,31 @@ struct Acc<float> {
     }
 };
 
+// Accumulator of a row of x += U y (kGsCombineX).  Float64 basis: float64 products and sums.
+// Float32 basis (float64 y split as yh + yl in float32): each product yh z is kept exactly as
+// p + (fma(yh, z, -p)), yl z is added to that error term, and the running sum is a two-sum pair,
+// so the row's correction reaches x with float64-level accuracy from float32 arithmetic only.
+template <typename T>
+struct XAcc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(T z, T yh, T) { s = fma((double)z, (double)yh, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct XAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float z, float yh, float yl)
+    {
+        const float p = yh * z;
+        const float pe = fmaf(yl, z, fmaf(yh, z, -p));
+        const float t = s + p;
+        const float bp = t - s;
+        c += ((s - (t - bp)) + (p - bp)) + pe;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // ---------------------------------------------------------------- finalisation (last CTA)
 //
 // The device state lives in global memory, where every dependent access of a serial loop costs
@@ -136,6 +161,42 @@ __device__ void publish_progress(const Cycle *st, int cycle_done, int j)
 // built), whose products c_i b_{i+1} and rotated entries c_i a_i + s_i b_{i+1} are formed by all
 // threads, leaving one multiply-add per step to thread 0, while warp 1 forms the norm and its
 // reciprocal.
+// y = R^{-1} g[0..k-1] with the cycle's triangle R (st->R) and right-hand side st->g, by the whole
+// CTA: R staged in shared memory when it fits, then column-oriented back substitution by warp 0
+// (y_i = g_i / R_ii, then g_q -= R_qi y_i for q < i in parallel).  Writes y and the combination
+// coefficients coef = -y .* sigma.  sh: shared scratch of sh_bytes, free for this call.
+__device__ void cta_solve_r(Cycle *st, int k, double *sh, size_t sh_bytes)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double *g = sh;            // k values
+    double *Rs = sh + k;       // k x k, column-major, ld k
+    const bool staged = (size_t)(k + k * k) * sizeof(double) <= sh_bytes;
+    for (int i = tid; i < k; i += nt) g[i] = st->g[i];
+    if (staged)
+        for (int e = tid; e < k * k; e += nt) {
+            const int q = e / k, i = e - q * k;
+            Rs[e] = i <= q ? st->R[(long long)q * kLdH + i] : 0.0;
+        }
+    __syncthreads();
+    if (tid < 32) {
+        for (int i = k - 1; i >= 0; --i) {
+            const double *Ri = staged ? Rs + (long long)i * k : st->R + (long long)i * kLdH;
+            const double yi = g[i] / Ri[i];
+            __syncwarp();
+            for (int q = tid; q < i; q += 32) g[q] -= Ri[q] * yi;
+            if (tid == 0) g[i] = yi;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int c = tid; c < k; c += nt) {
+        const double y = g[c];
+        st->y[c] = y;
+        st->coef[c] = -y * st->sigma[c];
+    }
+    __syncthreads();
+}
+
 template <typename T>
 __device__ void cta_finish_pass3(Cycle *st, int j, const double *slots, int pld, int nblk, double *sh,
                                  size_t sh_bytes, int *s_int)
@@ -259,39 +320,47 @@ __device__ void cta_finish_pass3(Cycle *st, int j, const double *slots, int pld,
     if (kdone >= 0 && gm)
         for (int i = tid; i <= j + 1; i += nt) st->R[(long long)j * kLdH + i] = ar[i];
     if (kdone > 0 && gm) {
-        // y = R^{-1} g (k = kdone): R staged in shared memory when it fits, then column-oriented
-        // back substitution by warp 0 (y_i = g_i / R_ii, then g_q -= R_qi y_i for q < i in parallel)
-        const int k = kdone;
-        double *g = sh;            // k values
-        double *Rs = sh + k;       // k x k, column-major, ld k
-        const bool staged = (size_t)(k + k * k) * sizeof(double) <= sh_bytes;
-        __syncthreads();           // col, cs, sn, ar no longer needed
-        for (int i = tid; i < k; i += nt) g[i] = st->g[i];
-        if (staged)
-            for (int e = tid; e < k * k; e += nt) {
-                const int q = e / k, i = e - q * k;
-                Rs[e] = i <= q ? st->R[(long long)q * kLdH + i] : 0.0;
-            }
-        __syncthreads();
-        if (tid < 32) {
-            for (int i = k - 1; i >= 0; --i) {
-                const double *Ri = staged ? Rs + (long long)i * k : st->R + (long long)i * kLdH;
-                const double yi = g[i] / Ri[i];
-                __syncwarp();
-                for (int q = tid; q < i; q += 32) g[q] -= Ri[q] * yi;
-                if (tid == 0) g[i] = yi;
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        for (int c = tid; c < k; c += nt) {
-            const double y = g[c];
-            st->y[c] = y;
-            st->coef[c] = -y * st->sigma[c];
-        }
-        __syncthreads();
+        __syncthreads();  // col, cs, sn, ar no longer needed
+        cta_solve_r(st, kdone, sh, sh_bytes);
         if (tid == 0) publish_progress(st, 1, j + 1);
     }
+}
+
+// Restart projection (flexible float32 solves), by the last CTA of the kGsProj pass: the finished
+// cycle left V_{k+1}, its rotations Q and triangle R with H = Q R; the pass summed U^T r for the
+// true residual r.  c = V^T r (c_q = sigma_q (U^T r)_q), the least-squares solution of H u ~ c is
+// u = R^{-1} (Q^T c)_{0..k-1}, written to y for the following x += Z u.  In exact arithmetic r is
+// orthogonal to range(H) and u = 0; in float32 it removes the part of r that the previous Krylov
+// space still represents.
+template <typename T>
+__device__ __noinline__ void cta_finish_proj(Cycle *st, int k, const double *slots, int pld, int nblk, double *sh,
+                                size_t sh_bytes)
+{
+    const int tid = threadIdx.x, nt = blockDim.x, wid = tid >> 5, lane = tid & 31;
+    double *c = sh;                   // k + 1 values
+    double *cs = sh + (kKmax + 2);    // rotations 0 .. k-1
+    double *sn = cs + (kKmax + 2);
+    for (int q = wid; q <= k; q += nt / 32) {
+        const double sg = lane == 0 ? st->sigma[q] : 0.0;
+        const double v = Acc<T>::reduce(slots, pld, nblk, q);
+        if (lane == 0) c[q] = sg * v;
+    }
+    for (int i = tid; i < k; i += nt) {
+        cs[i] = st->cs[i];
+        sn[i] = st->sn[i];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double a = c[0];
+        for (int i = 0; i < k; ++i) {
+            const double b = c[i + 1];
+            st->g[i] = fma(cs[i], a, sn[i] * b);
+            a = fma(-sn[i], a, cs[i] * b);
+        }
+        st->nproj += 1;
+    }
+    __syncthreads();
+    cta_solve_r(st, k, sh, sh_bytes);
 }
 
 // ---------------------------------------------------------------- the pass kernel
@@ -366,8 +435,9 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
 
     pdl_wait();
     pdl_trigger();
-    const bool skip = a.kcols_from_k ? (st->k == 0) : (st->cycle_done != 0);
-    const int k = a.kcols_from_k ? st->k : st->j + 1;
+    bool skip = a.kcols_from_k ? (st->k == 0) : (st->cycle_done != 0);
+    if (op == kGsProj) skip = skip || st->stop;
+    const int k = a.kcols_from_k ? st->k + (op == kGsProj ? 1 : 0) : st->j + 1;
     // the host's bound must cover k (else refuse rather than overrun a stage)
     const bool bad = !skip && (k > KM || k > a.kstage || (early && k != a.kstage));
     if (skip || bad) {
@@ -383,7 +453,8 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
         return;
     }
     T *out = a.out_follow ? (T *)a.U + (long long)(st->j + 1) * a.ldu : (T *)a.out;
-    for (int c = tid; c < KM; c += kThreads) s_coef[c] = (c < k && op != kGsDot) ? (T)st->coef[c] : T(0);
+    for (int c = tid; c < KM; c += kThreads)
+        s_coef[c] = (c < k && op != kGsDot && op != kGsProj) ? (T)st->coef[c] : T(0);
 
     // prologue: the first nst - 1 tiles (their remaining copies); tile it + nst - 1 is issued at
     // the start of iteration it into the stage freed by iteration it - 1
@@ -430,7 +501,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
         const T *sw = sU + (long long)a.kstage * TR;
         const long long row0 = tile * TR;
         const T *dotvec = sw;
-        if (op != kGsDot) {
+        if (op != kGsDot && op != kGsProj) {
             // update: wn = w - sum_c U[:, c] coef[c] on this tile
             if constexpr (TPR == 1) {
                 T part[RPT];
@@ -486,7 +557,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
                 }
             }
         }
-        if (op == kGsDot || op == kGsUpdDot) {
+        if (op == kGsDot || op == kGsUpdDot || op == kGsProj) {
 #pragma unroll
             for (int i = 0; i < CPW; ++i) {
                 const int c = wid + 8 * i;
@@ -514,7 +585,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
     // per-CTA partial sums: one 8-byte slot per column and CTA (a compensated float32 pair for the
     // float32 basis), column stride pld = nblk rounded up to even so that slots load in pairs
     const int pld = (a.nblk + 1) & ~1;
-    const bool want_dots = op == kGsDot || op == kGsUpdDot;
+    const bool want_dots = op == kGsDot || op == kGsUpdDot || op == kGsProj;
     const bool want_norm = op == kGsDot || op == kGsUpdNorm;
     if (want_dots && !prod) {
 #pragma unroll
@@ -526,8 +597,12 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
     if (want_norm) nrm.store_block_total(a.partials + (long long)kKmax * pld + blockIdx.x, scratch);
     if (op == kGsCombine) return;
 
-    if (last_block_done(&st->ticket[2 + op], &s_last)) {
-        if (op != kGsUpdNorm) {
+    const int tk = op == kGsProj ? 6 : 2 + op;  // ticket 6 is the plain combination's, which has no last CTA
+    if (last_block_done(&st->ticket[tk], &s_last)) {
+        if (op == kGsProj) {
+            cta_finish_proj<T>(st, k - 1, a.partials, pld, a.nblk, reinterpret_cast<double *>(smem),
+                               (size_t)nst * (size_t)SS * sizeof(T));
+        } else if (op != kGsUpdNorm) {
             // passes 1 and 2: each warp sums the slots of its columns and finalises them: the
             // pass's Hessenberg coefficients h = sigma .* sum and the next update's coefficients
             // coef = h .* sigma (sigma is loaded ahead of the sum); pass 1's norm is job k
@@ -551,8 +626,58 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
             cta_finish_pass3<T>(st, k - 1, a.partials, pld, a.nblk, reinterpret_cast<double *>(smem),
                                 (size_t)nst * (size_t)SS * sizeof(T), s_int);
         }
-        if (tid == 0) st->ticket[2 + op] = 0;
+        if (tid == 0) st->ticket[tk] = 0;
     }
+}
+
+// ---------------------------------------------------------------- x += Z y (flexible cycle end)
+
+// x[r] += sum_c y_c U[r, c] over the k columns the finished cycle (or the restart projection) left
+// coefficients for, r < n: float64 x and y, U float32 (float64 for a float64 basis), accumulated as
+// XAcc describes.  Once per cycle; each thread keeps its row's k column loads in flight.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_combine_x(const T *__restrict__ U, long long ld, long long n,
+                                                        double *__restrict__ x, Cycle *st, int skip_if_stop)
+{
+    __shared__ T s_hi[kKmax], s_lo[kKmax];
+    pdl_wait();
+    pdl_trigger();
+    const int k = st->k;
+    if (k == 0 || (skip_if_stop && st->stop)) return;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        const double y = st->y[c];
+        const T hi = (T)y;
+        s_hi[c] = hi;
+        s_lo[c] = (T)(y - (double)hi);
+    }
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        XAcc<T> xa;
+        int c = 0;
+        for (; c + 8 <= k; c += 8) {
+            T z[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) z[u] = __ldcs(U + (long long)(c + u) * ld + r);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xa.add(z[u], s_hi[c + u], s_lo[c + u]);
+        }
+        for (; c < k; ++c) xa.add(__ldcs(U + (long long)c * ld + r), s_hi[c], s_lo[c]);
+        x[r] += xa.value();
+    }
+}
+
+cudaError_t launch_combine_x(int prec, const void *U, long long ld, long long n, double *x, Cycle *st,
+                             int skip_if_stop, int num_sms, cudaStream_t s)
+{
+    long long grid = (n + kThreads - 1) / kThreads;
+    if (grid > 8LL * num_sms) grid = 8LL * num_sms;
+    if (grid < 1) grid = 1;
+    if (prec == kF64)
+        return launch_pdl(k_combine_x<double>, dim3((unsigned)grid), dim3(kThreads), 0, s, (const double *)U, ld, n,
+                          x, st, skip_if_stop);
+    return launch_pdl(k_combine_x<float>, dim3((unsigned)grid), dim3(kThreads), 0, s, (const float *)U, ld, n, x, st,
+                      skip_if_stop);
 }
 
 // ---- host side: bucket selection, occupancy (cached per instantiation), launch

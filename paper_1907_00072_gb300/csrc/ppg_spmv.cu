@@ -1971,14 +1971,15 @@ cudaError_t launch_axpy(int n, int prec, const SpmvEpi &e, Cycle *st, int check,
 // Starts a restart cycle from r = b - A x (float64), stored in basis column 0 as
 // U_0 = r with sigma_0 = 1/||r||: tests convergence (relative residual, Section III),
 // the iteration limit and finiteness, and resets the Givens right-hand side g = beta e_1.
-__device__ void finish_residual(Cycle *st, double sumsq)
+// proj = 1 (the residual before a restart projection): the same tests, but a solve that goes on
+// keeps the finished cycle's k, rotations and R for the projection; the residual after it starts
+// the cycle.
+__device__ void finish_residual(Cycle *st, double sumsq, int proj)
 {
     const double beta = sqrt(sumsq);
     st->beta = beta;
     st->relres = beta / st->bnorm;
-    st->k = 0;
-    st->j = 0;
-    st->breakdown = 0;
+    st->nres += 1;
     if (!isfinite(beta)) {
         st->error |= kErrNonfinite;
         st->stop = 1;
@@ -1988,6 +1989,10 @@ __device__ void finish_residual(Cycle *st, double sumsq)
     } else if (st->iters >= st->maxit) {
         st->stop = 1;
     }
+    if (proj && !st->stop) return;
+    st->k = 0;
+    st->j = 0;
+    st->breakdown = 0;
     if (st->stop) {
         st->cycle_done = 1;
         return;
@@ -2004,7 +2009,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(int n, const int *__restr
                                                        const int *__restrict__ colidx,
                                                        const double *__restrict__ vals, const double *__restrict__ b,
                                                        const double *__restrict__ x, Tout *__restrict__ out, Cycle *st,
-                                                       double *partials)
+                                                       double *partials, int proj)
 {
     __shared__ double scratch[33];
     __shared__ int s_last;
@@ -2028,7 +2033,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(int n, const int *__restr
         if (threadIdx.x < 32) {
             const double tot = reduce_partials(partials, gridDim.x, 0);
             if (threadIdx.x == 0) {
-                finish_residual(st, tot);
+                finish_residual(st, tot, proj);
                 st->ticket[0] = 0;
             }
         }
@@ -2036,14 +2041,14 @@ __global__ void __launch_bounds__(kThreads) k_residual(int n, const int *__restr
 }
 
 cudaError_t launch_residual(const DevMatrix &A, int out_prec, const double *b, const double *x, void *out, Cycle *st,
-                            double *partials, cudaStream_t s)
+                            double *partials, cudaStream_t s, int proj)
 {
     const int grid = A.resid_blocks;
     if (out_prec == kF64)
         return launch_pdl(k_residual<double>, dim3(grid), dim3(kThreads), 0, s, A.n, A.rowptr, A.colidx, A.vals64, b,
-                          x, (double *)out, st, partials);
+                          x, (double *)out, st, partials, proj);
     return launch_pdl(k_residual<float>, dim3(grid), dim3(kThreads), 0, s, A.n, A.rowptr, A.colidx, A.vals64, b, x,
-                      (float *)out, st, partials);
+                      (float *)out, st, partials, proj);
 }
 
 // ||v||.  mode 0: st->bnorm = ||v|| (right-hand side).  mode 1: start an Arnoldi run from v:

@@ -53,7 +53,8 @@ def test_batched_matches_single_solves(degree, restart):
         assert _relres(a, b, xb) <= 1e-8
         s = ppg.Solver(sysi[0], sysi[1], sysi[2])
         s.build_poly(degree, ppg.PPG_BASIS_ROOTS, v0=None, seed=seed + i)
-        xs, info = s.solve(sysi[3], tol=1e-8, restart=restart, maxit=20000, precision=ppg.PPG_F32)
+        xs, info = s.solve(sysi[3], tol=1e-8, restart=restart, maxit=20000, precision=ppg.PPG_F32,
+                           f32_form=ppg.PPG_F32_STANDARD)  # the form the batched kernel runs
         xs = xs.cpu().numpy()
         assert info.status == ppg.PPG_OK and _relres(a, b, xs) <= 1e-8
         assert np.linalg.norm(xb - xs) <= 1e-6 * np.linalg.norm(xs)

@@ -1,0 +1,99 @@
+"""Parity with the oracle at the benchmark configurations' full sizes.
+
+The 128^3 convection-diffusion system (n = 2,097,152, GMRES(50), degrees 10 and 25) and the
+perturbed 27-point 100^3 system (n = 1,000,000, degree 25) are solved on the GPU through the C
+ABI and by the oracle (its own polynomial construction from the same seeded v0, MGS Arnoldi,
+float64), and compared:
+  * true relative residual ||b - A x|| / ||b|| <= 1e-8, recomputed on the host (Section III's test);
+  * ||x - x_oracle|| <= 1e-6 ||x_oracle||;
+  * iteration counts: within 5% for the float64 solve.  The float32 solve with float64 refinement
+    reaches about 1e-7 in one float32 cycle, so a 1e-8 target always takes a second refinement
+    step; with the restart projection that step costs one basis vector, and the count is held to
+    max(5%, one iteration) of the oracle's.
+The oracle solves run in spawned worker processes (tests/_oracle_jobs.py) while the GPU works.
+"""
+import concurrent.futures as cf
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import _oracle_jobs
+import oracle
+import workloads as w
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="no CUDA device")]
+
+import paper_1907_00072_gb300 as ppg  # noqa: E402
+
+DEV = "cuda:0"
+CASES = [("c2", 10), ("c2", 25), ("c3", 25)]
+
+
+@pytest.fixture(scope="module")
+def oracle_runs():
+    ex = cf.ProcessPoolExecutor(max_workers=len(CASES), mp_context=mp.get_context("spawn"))
+    futs = {key: ex.submit(_oracle_jobs.solve, *key) for key in CASES}
+    yield futs
+    ex.shutdown(wait=True, cancel_futures=True)
+
+
+_mats = {}
+
+
+def _matrix(config):
+    if config not in _mats:
+        _mats.clear()  # one full-size matrix at a time
+        _mats[config] = _oracle_jobs.matrix(config)
+    return _mats[config]
+
+
+def _T(a, dt=torch.float64):
+    return torch.as_tensor(np.asarray(a), dtype=dt, device=DEV)
+
+
+def _gpu_solve(config, degree, precision):
+    a = _matrix(config)
+    b = w.rhs(a.n)
+    s = ppg.Solver(_T(a.rowptr, torch.int32), _T(a.colidx, torch.int32), _T(a.vals))
+    used, _ = s.build_poly(degree, ppg.PPG_BASIS_ROOTS, v0=_T(w.v0(a.n)))
+    assert used == degree
+    x, info = s.solve(_T(b), tol=1e-8, restart=50, maxit=5000, precision=precision)
+    xs = x.cpu().numpy()
+    s.close()
+    relres = np.linalg.norm(b - oracle.spmv(a, xs)) / np.linalg.norm(b)
+    return xs, info, relres
+
+
+def _check(config, degree, precision, ref):
+    xs, info, relres = _gpu_solve(config, degree, precision)
+    it, it_ref = info.stats["iterations"], ref["iters"]
+    err = np.linalg.norm(xs - ref["x"]) / np.linalg.norm(ref["x"])
+    msg = (f"{config} degree {degree}: GPU {it} iterations, relres {relres:.3e}, |x - x_oracle|/|x_oracle| "
+           f"{err:.3e}; oracle {it_ref} iterations, relres {ref['relres']:.3e}")
+    assert ref["converged"], msg
+    assert info.status == ppg.PPG_OK, msg
+    assert relres <= 1e-8, msg
+    assert abs(info.stats["relres_true"] - relres) <= 1e-3 * relres, msg
+    assert err <= 1e-6, msg
+    if precision == ppg.PPG_F64:
+        assert abs(it - it_ref) <= 0.05 * it_ref, msg
+    else:
+        assert abs(it - it_ref) <= max(0.05 * it_ref, 1), msg
+    print(msg)
+
+
+def test_c2_degree10_float64_matches_oracle(oracle_runs):
+    _check("c2", 10, ppg.PPG_F64, oracle_runs[("c2", 10)].result())
+
+
+@pytest.mark.parametrize("degree", [10, 25])
+def test_c2_float32_refined_matches_oracle(oracle_runs, degree):
+    _check("c2", degree, ppg.PPG_F32, oracle_runs[("c2", degree)].result())
+
+
+def test_c3_degree25_float32_refined_matches_oracle(oracle_runs):
+    _check("c3", 25, ppg.PPG_F32, oracle_runs[("c3", 25)].result())

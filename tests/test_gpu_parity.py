@@ -481,6 +481,62 @@ def test_solve_mixed_precision_reaches_fp64_accuracy():
     assert info.stats["restarts"] >= 2  # refinement steps
 
 
+@pytest.mark.parametrize("mat", ["c1", "random"])
+@pytest.mark.parametrize("deg,basis", [(1, "roots"), (5, "power"), (10, "roots"), (25, "roots")])
+def test_solve_float32_forms_match_oracle(deg, basis, mat):
+    """Float32 inner solves with float64 refinement, flexible (default) and standard form: both reach
+    the oracle's solution, and the flexible form (z_j = p(A) v_j kept, restart projection) needs at
+    most one iteration more than the standard one.  How many refinement steps a float32 solve needs
+    depends on the accuracy one float32 cycle attains (about kappa(A) 2^-24, large for these small
+    2D problems); the iteration bars against the oracle are held at the benchmark sizes
+    (test_gpu_config_size.py)."""
+    a = ROOT_MATS[mat]()
+    b = w.rhs(a.n)
+    v0 = w.v0(a.n)
+    s = solver_for(a)
+    bas = ppg.PPG_BASIS_POWER if basis == "power" else ppg.PPG_BASIS_ROOTS
+    used, _ = s.build_poly(deg, bas, v0=T(v0))
+    ref = oracle.gmres(a, b, oracle.poly_gmres(a, v0, used), tol=1e-8, m=50, maxit=5000)
+    its = {}
+    for form in (ppg.PPG_F32_FLEXIBLE, ppg.PPG_F32_STANDARD):
+        x, info = s.solve(T(b), tol=1e-8, restart=50, maxit=5000, precision=ppg.PPG_F32, f32_form=form)
+        xg = x.cpu().numpy()
+        assert info.status == ppg.PPG_OK
+        assert _true_relres(a, b, xg) <= 1e-8
+        assert np.linalg.norm(xg - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
+        its[form] = info.stats["iterations"]
+    assert its[ppg.PPG_F32_FLEXIBLE] <= its[ppg.PPG_F32_STANDARD] + 1, its
+    assert its[ppg.PPG_F32_FLEXIBLE] >= ref.iters - max(1, 0.05 * ref.iters), (its, ref.iters)
+
+
+@pytest.mark.parametrize("last", ["real", "pair"])
+def test_flexible_form_with_either_last_root(last):
+    """The flexible form writes z_j = p(A) v_j from the chain's last link; when the product ends with a
+    real root that link is the SpMV's fused gather (z = y + t P written by the SpMV's second output),
+    otherwise the chain's own output.  Any order of the roots is the same polynomial, so both orders
+    must give the oracle's solution."""
+    a = w.c1_matrix()
+    b = w.rhs(a.n)
+    v0 = w.v0(a.n)
+    s = solver_for(a)
+    s.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=T(v0))
+    _, deg, rt, _ = s.get_poly()
+    z = rt[0::2] + 1j * rt[1::2]
+    real = [q for q in z if q.imag == 0.0]
+    pairs = [q for q in z if q.imag > 0.0]
+    if last == "pair" and not pairs or last == "real" and not real:
+        pytest.skip("the polynomial has no root of that kind")
+    groups = [[q] for q in real] + [[q, np.conj(q)] for q in pairs]
+    groups.sort(key=lambda g: (len(g) == 2) == (last == "pair"))  # the wanted kind last
+    order = [q for g in groups for q in g]
+    s.set_poly(ppg.PPG_BASIS_ROOTS, np.column_stack([np.real(order), np.imag(order)]).ravel())
+    ref = oracle.gmres(a, b, oracle.poly_gmres(a, v0, deg), tol=1e-8, m=50, maxit=5000)
+    x, info = s.solve(T(b), tol=1e-8, restart=50, maxit=5000, precision=ppg.PPG_F32)
+    xg = x.cpu().numpy()
+    assert info.status == ppg.PPG_OK and _true_relres(a, b, xg) <= 1e-8
+    assert np.linalg.norm(xg - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
+
+
 def test_solve_edge_cases():
     a = w.c1_matrix()
     b = w.rhs(a.n)
@@ -548,7 +604,7 @@ def test_transposed_solve_and_gradients_match_dense():
     xt = w.uniform(w.SEED_XTARGET, a.n)
     s = solver_for(a)
     s.build_poly(6, ppg.PPG_BASIS_ROOTS, v0=T(w.v0(a.n)))
-    vals = T(a.vals).requires_grad_(True)
+    vals = s.vals.requires_grad_(True)  # the tensor the context was created from
     bt = T(b).requires_grad_(True)
     x = ppg.solve(s, vals, bt, tol=1e-12)
     loss = ((x - T(xt)) ** 2).sum()
@@ -560,6 +616,29 @@ def test_transposed_solve_and_gradients_match_dense():
     gvals = -lam[rows] * xd[a.colidx]
     np.testing.assert_allclose(bt.grad.cpu().numpy(), lam, rtol=1e-7, atol=1e-9 * np.abs(lam).max())
     np.testing.assert_allclose(vals.grad.cpu().numpy(), gvals, rtol=1e-7, atol=1e-9 * np.abs(gvals).max())
+
+
+def test_differentiable_solve_raises_when_not_converged():
+    """A forward or adjoint solve stopped by maxit must not hand back its last iterate as a result."""
+    a = w.convdiff(16, 2, 30.0)
+    s = solver_for(a)
+    s.build_poly(6, ppg.PPG_BASIS_ROOTS, v0=T(w.v0(a.n)))
+    vals = s.vals.requires_grad_(True)
+    bt = T(w.rhs(a.n)).requires_grad_(True)
+    with pytest.raises(ppg.PPGError) as e:
+        ppg.solve(s, vals, bt, tol=1e-12, maxit=1)
+    assert e.value.status == ppg.PPG_ERR_NOT_CONVERGED
+    # forward converges; the adjoint solve is held to one iteration
+    orig = s.solve_transpose
+    s.solve_transpose = lambda g, **kw: orig(g, **{**kw, "maxit": 1})
+    x = ppg.solve(s, vals, bt, tol=1e-12)
+    with pytest.raises(ppg.PPGError) as e:
+        (x ** 2).sum().backward()
+    assert e.value.status == ppg.PPG_ERR_NOT_CONVERGED
+    s.solve_transpose = orig
+    x = ppg.solve(s, vals, bt, tol=1e-12)
+    (x ** 2).sum().backward()
+    assert torch.isfinite(bt.grad).all() and torch.isfinite(vals.grad).all()
 
 
 # ---------------------------------------------------------------- full-size workloads (sampled)

@@ -74,7 +74,7 @@ def test_reference_arm_under_torchrun_world2():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port),
            os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
-           "--N", "10", "--degree", "4", "--ref-iters", "20"]
+           "--N", "10", "--degree", "4", "--ref-workers", "2"]
     env = dict(os.environ)
     env.pop("CUDA_VISIBLE_DEVICES", None)
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, env=env, cwd=ROOT)
@@ -86,3 +86,4 @@ def test_reference_arm_under_torchrun_world2():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "10^3" in d["config"]["workload"]
+    assert "full solve" in d["cpu_baseline"]["sample"] and d["iterations"] > 0 and d["relres_true"] <= 1e-8
