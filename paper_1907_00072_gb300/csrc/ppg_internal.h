@@ -32,6 +32,36 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// As launch_pdl, and when win_bytes > 0 the launch's global accesses to [win_base, win_base +
+// win_bytes) are marked persisting in L2 for a fraction win_hit of the window (the rest streaming),
+// so that data read by every launch of a chain (the float32 matrix blocks) can stay in L2 between
+// launches while the vectors stream through.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl_l2(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          const void *win_base, size_t win_bytes, float win_hit, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (win_bytes > 0) {
+        attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[1].val.accessPolicyWindow.base_ptr = const_cast<void *>(win_base);
+        attr[1].val.accessPolicyWindow.num_bytes = win_bytes;
+        attr[1].val.accessPolicyWindow.hitRatio = win_hit;
+        attr[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.numAttrs = 2;
+    }
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // A launch whose CTAs wait on one another: cooperative, so that the whole grid is resident at
 // once (the launch fails rather than starting part of the grid).
 template <typename... KArgs, typename... Args>
@@ -89,6 +119,11 @@ struct DevMatrix {
     int ewmax;            // widest tile (entries per row)
     int excap;            // longest window total over the tiles (the padding's zero sits at this index)
     const double *evals64; // the same blocks' values in float64 (float64 solves and the construction)
+    // L2 residency of the float32 blocks (values and indices, one allocation): float32 tile-ELL launches
+    // mark this window persisting for a fraction l2_hit of it; l2_bytes = 0: off
+    const void *l2_base;
+    size_t l2_bytes;
+    float l2_hit;
     EllLaunch ell[2];     // tile-ELL grid and stages: [0] float32, [1] float64
     int spmvw_blocks32;   // persistent grid of the staged kernel
     // sliced ELL copy (slices of 32 rows; entry k of row 32 s + l at sptr[s] + 32 k + l, slices padded

@@ -1668,16 +1668,17 @@ cudaError_t spmve_go(const DevMatrix &A, const SpmvEpi &e, Cycle *st, int check_
     *launched = true;
     const size_t smem = (size_t)nst * spmve_stage_bytes(A.ewmax, x2, A.excap, (int)sizeof(T));
     const dim3 grid((unsigned)g), block(kSpmvThreads);
+    const size_t wb = sizeof(T) == 4 ? A.l2_bytes : 0;  // the float32 blocks may stay in L2
     switch (A.lanes_per_row) {
     case 2:
-        return x2 ? launch_pdl(k_spmv_e<T, true, 2>, grid, block, smem, s, q)
-                  : launch_pdl(k_spmv_e<T, false, 2>, grid, block, smem, s, q);
+        return x2 ? launch_pdl_l2(k_spmv_e<T, true, 2>, grid, block, smem, s, A.l2_base, wb, A.l2_hit, q)
+                  : launch_pdl_l2(k_spmv_e<T, false, 2>, grid, block, smem, s, A.l2_base, wb, A.l2_hit, q);
     case 4:
-        return x2 ? launch_pdl(k_spmv_e<T, true, 4>, grid, block, smem, s, q)
-                  : launch_pdl(k_spmv_e<T, false, 4>, grid, block, smem, s, q);
+        return x2 ? launch_pdl_l2(k_spmv_e<T, true, 4>, grid, block, smem, s, A.l2_base, wb, A.l2_hit, q)
+                  : launch_pdl_l2(k_spmv_e<T, false, 4>, grid, block, smem, s, A.l2_base, wb, A.l2_hit, q);
     default:
-        return x2 ? launch_pdl(k_spmv_e<T, true, 1>, grid, block, smem, s, q)
-                  : launch_pdl(k_spmv_e<T, false, 1>, grid, block, smem, s, q);
+        return x2 ? launch_pdl_l2(k_spmv_e<T, true, 1>, grid, block, smem, s, A.l2_base, wb, A.l2_hit, q)
+                  : launch_pdl_l2(k_spmv_e<T, false, 1>, grid, block, smem, s, A.l2_base, wb, A.l2_hit, q);
     }
 }
 
