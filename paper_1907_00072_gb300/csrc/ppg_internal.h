@@ -163,8 +163,9 @@ struct SpmvEpi {
 // Gram-Schmidt / basis kernels over the column-major basis U (ld entries per column).
 enum GsOp : int {
     kGsDot = 1,        // h1 = sigma .* (U^T w), ||w||^2          -> finalize pass 1
-    kGsUpdDot = 2,     // w -= U coef; h2 = sigma .* (U^T w)      -> finalize pass 2
-    kGsUpdNorm = 3,    // out = w - U coef; ||out||^2             -> finalize pass 3 (Hessenberg column)
+    kGsUpdDot = 2,     // w -= U coef; h2 = sigma .* (U^T w), ||w||^2 -> finalize pass 2 and the Hessenberg
+                       // column (||v_{j+1}||^2 = ||w||^2 - ||h2||^2)
+    kGsUpdNorm = 3,    // out = w - U (h2 .* sigma) into column j + 1 (pass 3: update only, no reduction)
     kGsCombine = 4,    // out = -U coef (cycle end: z = V y)
     kGsProj = 6,       // c = sigma .* (U^T w) over the finished cycle's k + 1 columns, then y = the least-
                        // squares solution of H y ~ c with the cycle's rotations and R (restart projection)
@@ -175,7 +176,7 @@ struct GsArgs {
     long long ldu;
     void *w;          // input vector (kGsDot, kGsUpdDot: updated in place)
     void *out;        // kGsUpdNorm / kGsCombine output (VecRef-like, column follows j when out_follow)
-    int out_follow;   // 1: out = U + (j + 1) * ldu
+    int out_follow;   // 1: out = U + k * ldu (k the pass's column count, i.e. column j + 1)
     int op;
     int kcols_from_k; // 1: number of columns is Cycle::k (cycle end), else Cycle::j + 1
     long long ntiles;
@@ -183,6 +184,7 @@ struct GsArgs {
     int nblk;
     int kstage;   // columns one pipeline stage holds (>= the columns used); set by launch_gs
     int nstages;  // pipeline depth; set by launch_gs
+    int use_tmap; // 1: a tile's kstage basis columns arrive by one 2-D tensor copy (set by launch_gs)
 };
 
 // x += U y (float64 x and y = Cycle::y, k = Cycle::k columns of U; flexible cycle end and restart

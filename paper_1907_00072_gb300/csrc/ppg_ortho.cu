@@ -5,16 +5,23 @@
 // inner products and one norm per iteration).  With w = A p(A) v_j the three
 // passes over the basis are
 //   pass 1:  h1 = V^T w                         (block inner product, and ||w||^2)
-//   pass 2:  w <- w - V h1,  h2 = V^T w         (update fused with the second inner product)
-//   pass 3:  v_{j+1} <- w - V h2, ||v_{j+1}||^2 (update fused with the norm)
-// Each pass streams the basis once.  Tiles of the column-major basis (TR rows x k
-// columns) are staged in shared memory with TMA bulk copies, double-buffered across
-// a persistent grid, so the update and the inner product of pass 2 read each tile
-// from HBM once.  Per-CTA partial sums go to a [column x CTA] buffer and the last CTA
-// to finish reduces them in a fixed order (deterministic results) and finalises the
-// Hessenberg column on the device: Givens rotations and the convergence test of
-// GMRES never leave the GPU.
+//   pass 2:  w <- w - V h1,  h2 = V^T w         (update fused with the second inner product
+//                                                and the norm ||w||^2 of the updated w)
+//   pass 3:  v_{j+1} <- w - V h2                (update only)
+// Each pass streams the basis once.  The norm of v_{j+1} follows from pass 2 by Pythagoras,
+// ||w - V h2||^2 = ||w||^2 - ||h2||^2 for orthonormal V (after one orthogonalisation h2 is tiny
+// against w, so the difference is exact to working precision), so an iteration has two global
+// reductions, not three.  Tiles of the column-major basis (TR rows x k columns) are staged in
+// shared memory with TMA bulk copies, double-buffered across a persistent grid, so the update and
+// the inner product of pass 2 read each tile from HBM once.  Per-CTA partial sums go to a
+// [column x CTA] buffer and the last CTA to finish reduces them in a fixed order (deterministic
+// results) and finalises the Hessenberg column on the device: Givens rotations and the
+// convergence test of GMRES never leave the GPU.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include "ppg_internal.h"
 
@@ -31,10 +38,10 @@ namespace ppg {
 #define PPG_GS_TILE_BYTES 32768  // a full-width stage (KM columns) of one tile
 #endif
 #ifndef PPG_GS_TILE_BYTES_WIDE
-#define PPG_GS_TILE_BYTES_WIDE PPG_GS_TILE_BYTES  // the same for the buckets KM >= 64
+#define PPG_GS_TILE_BYTES_WIDE 65536  // the same for the buckets KM >= 64 (tiles of 256 float32 rows)
 #endif
 #ifndef PPG_GS_SMEM_KB_WIDE
-#define PPG_GS_SMEM_KB_WIDE PPG_GS_SMEM_KB
+#define PPG_GS_SMEM_KB_WIDE 132
 #endif
 #ifndef PPG_GS_STAGES
 #define PPG_GS_STAGES 2  // cap on the pipeline depth: more CTAs per SM beat deeper pipelines (measured)
@@ -198,8 +205,7 @@ __device__ void cta_solve_r(Cycle *st, int k, double *sh, size_t sh_bytes)
 }
 
 template <typename T>
-__device__ void cta_finish_pass3(Cycle *st, int j, const double *slots, int pld, int nblk, double *sh,
-                                 size_t sh_bytes, int *s_int)
+__device__ void cta_finish_pass3(Cycle *st, int j, double wsq, double *sh, size_t sh_bytes, int *s_int)
 {
     const int tid = threadIdx.x, nt = blockDim.x, wid = tid >> 5, lane = tid & 31;
     double *col = sh;                // column j as built (j + 1 values)
@@ -208,15 +214,24 @@ __device__ void cta_finish_pass3(Cycle *st, int j, const double *slots, int pld,
     double *cb = sn + (kKmax + 2);   // cs[i] col[i+1]
     double *ar = cb + (kKmax + 2);   // a_i, then the rotated column (j + 2 values)
     // [0] ||v||^2  [1] ||v||  [2] sigma_{j+1}  [3] g_j  [4] tol ||b||  [5] inner_rtol beta (or -1)
-    // [6] 1 / ||b||  [7] breakdown threshold on ||v||^2
-    __shared__ double sc[8];
+    // [6] 1 / ||b||  [7] breakdown threshold on ||v||^2  [8] ||w'||^2
+    __shared__ double sc[9];
     __shared__ long long s_it[2];  // iters, maxit
     __shared__ int s_m[2];         // restart length, mode
     if (tid == 0) s_int[0] = 0;
     __syncthreads();
     if (wid == 0) {
-        const double v = Acc<T>::reduce(slots, pld, nblk, kKmax);
-        if (lane == 0) sc[0] = v;
+        // ||v_{j+1}||^2 = ||w'||^2 - ||h2||^2 (h2 = V^T w', written by this CTA before the call)
+        double s2 = 0.0;
+        for (int i = lane; i <= j; i += 32) {
+            const double h = st->h2[i];
+            s2 = fma(h, h, s2);
+        }
+        s2 = warp_sum(s2);
+        if (lane == 0) {
+            sc[0] = wsq - s2;
+            sc[8] = wsq;
+        }
     } else {
         if (tid == nt - 1) {
             s_it[0] = st->iters;
@@ -253,8 +268,11 @@ __device__ void cta_finish_pass3(Cycle *st, int j, const double *slots, int pld,
         }
         ar[j] = a;
     } else if (tid == 32) {
-        const double nsq = sc[0], nrm = sqrt(nsq);
-        const bool brk = !(nsq > sc[7]);
+        const double nsq = sc[0];
+        // breakdown: v_{j+1} negligible against ||w||, or the second pass removed more than 99 % of w'
+        // (then the difference of squares is no longer accurate): either way the cycle ends there
+        const bool brk = !(nsq > sc[7]) || !(nsq > 1e-2 * sc[8]);
+        const double nrm = !isfinite(nsq) ? nsq : (brk ? 0.0 : sqrt(nsq));  // NaN / Inf stay visible
         sc[1] = nrm;
         sc[2] = brk ? 0.0 : 1.0 / nrm;
         s_int[2] = brk;
@@ -369,7 +387,7 @@ __device__ __noinline__ void cta_finish_proj(Cycle *st, int k, const double *slo
 constexpr int kGsThreads = kThreads + 32;
 
 template <typename T, int KM>
-__global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
+__global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st, const __grid_constant__ CUtensorMap tmap)
 {
     using C = GsCfg<T, KM>;
     constexpr int TR = C::TR, TPR = C::TPR, RPT = C::RPT, RPL = C::RPL, CPW = C::CPW;
@@ -382,6 +400,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
     __shared__ int s_last;
     __shared__ int s_int[3];
     __shared__ int s_timeout;
+    __shared__ double s_wsq;  // pass 2: ||w'||^2
 
     const int op = a.op;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -402,13 +421,25 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
 
     // Stage fills, by the lanes of the producer warp.  A stage's barrier completes once lane 0 has arrived
     // (with the w copy) and all bytes have landed, so the basis columns may be requested earlier.
+    // With a tensor map (iteration passes) the tile's kc = kstage columns are one box copy;
+    // otherwise one bulk copy per column.
     auto issue_cols = [&](long long tile, int stage, int kc) {
         T *sU = stage0 + stage * SS;
         if (lane == 0) mbar_expect_tx(&bars[stage], colb * (uint32_t)kc);
         __syncwarp();
         fence_proxy_async_smem();
         const long long row0 = tile * TR;
-        for (int c = lane; c < kc; c += 32) bulk_g2s(sU + c * TR, U + (long long)c * a.ldu + row0, colb, &bars[stage]);
+        if (a.use_tmap) {
+            if (lane == 0) {
+                if constexpr (TR <= 256)
+                    tma_load_2d(sU, &tmap, (int)row0, 0, &bars[stage]);
+                else
+                    tma_load_3d(sU, &tmap, 0, (int)(row0 / 256), 0, &bars[stage]);
+            }
+        } else {
+            for (int c = lane; c < kc; c += 32)
+                bulk_g2s(sU + c * TR, U + (long long)c * a.ldu + row0, colb, &bars[stage]);
+        }
     };
     auto issue_w = [&](long long tile, int stage) {
         if (lane == 0) {
@@ -437,7 +468,14 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
     pdl_trigger();
     bool skip = a.kcols_from_k ? (st->k == 0) : (st->cycle_done != 0);
     if (op == kGsProj) skip = skip || st->stop;
-    const int k = a.kcols_from_k ? st->k + (op == kGsProj ? 1 : 0) : st->j + 1;
+    int k = a.kcols_from_k ? st->k + (op == kGsProj ? 1 : 0) : st->j + 1;
+    if (op == kGsUpdNorm) {
+        // pass 3 follows the finalisation of its own iteration (done by pass 2, which advanced j to
+        // the host's column count); it also runs when that finalisation ended the cycle, since the
+        // new basis vector is used by the restart projection
+        skip = st->j != a.kstage;
+        k = a.kstage;
+    }
     // the host's bound must cover k (else refuse rather than overrun a stage)
     const bool bad = !skip && (k > KM || k > a.kstage || (early && k != a.kstage));
     if (skip || bad) {
@@ -452,9 +490,13 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
         }
         return;
     }
-    T *out = a.out_follow ? (T *)a.U + (long long)(st->j + 1) * a.ldu : (T *)a.out;
+    T *out = a.out_follow ? (T *)a.U + (long long)k * a.ldu : (T *)a.out;
+    // pass 3's coefficients h2 .* sigma are formed here: the finalisation may have replaced coef by
+    // the cycle-end combination's
     for (int c = tid; c < KM; c += kThreads)
-        s_coef[c] = (c < k && op != kGsDot && op != kGsProj) ? (T)st->coef[c] : T(0);
+        s_coef[c] = (c < k && op != kGsDot && op != kGsProj)
+                        ? (T)(op == kGsUpdNorm ? st->h2[c] * st->sigma[c] : st->coef[c])
+                        : T(0);
 
     // prologue: the first nst - 1 tiles (their remaining copies); tile it + nst - 1 is issued at
     // the start of iteration it into the stage freed by iteration it - 1
@@ -519,9 +561,9 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
                     if (op == kGsUpdDot) {
                         w[row0 + row] = wn;
                         s_wn[row] = wn;
+                        nrm.add(wn * wn);
                     } else {
                         out[row0 + row] = wn;
-                        if (op == kGsUpdNorm) nrm.add(wn * wn);
                     }
                 }
                 asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");  // compute warps only
@@ -539,9 +581,9 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
                     if (op == kGsUpdDot) {
                         w[row0 + row] = wn;
                         s_wn[row] = wn;
+                        nrm.add(wn * wn);
                     } else {
                         out[row0 + row] = wn;
-                        if (op == kGsUpdNorm) nrm.add(wn * wn);
                     }
                 }
                 asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
@@ -586,7 +628,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
     // float32 basis), column stride pld = nblk rounded up to even so that slots load in pairs
     const int pld = (a.nblk + 1) & ~1;
     const bool want_dots = op == kGsDot || op == kGsUpdDot || op == kGsProj;
-    const bool want_norm = op == kGsDot || op == kGsUpdNorm;
+    const bool want_norm = op == kGsDot || op == kGsUpdDot;
     if (want_dots && !prod) {
 #pragma unroll
         for (int i = 0; i < CPW; ++i) {
@@ -595,17 +637,18 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
         }
     }
     if (want_norm) nrm.store_block_total(a.partials + (long long)kKmax * pld + blockIdx.x, scratch);
-    if (op == kGsCombine) return;
+    if (op == kGsCombine || op == kGsUpdNorm) return;  // pass 3 is an update only: no reduction
 
     const int tk = op == kGsProj ? 6 : 2 + op;  // ticket 6 is the plain combination's, which has no last CTA
     if (last_block_done(&st->ticket[tk], &s_last)) {
         if (op == kGsProj) {
             cta_finish_proj<T>(st, k - 1, a.partials, pld, a.nblk, reinterpret_cast<double *>(smem),
                                (size_t)nst * (size_t)SS * sizeof(T));
-        } else if (op != kGsUpdNorm) {
+        } else {
             // passes 1 and 2: each warp sums the slots of its columns and finalises them: the
             // pass's Hessenberg coefficients h = sigma .* sum and the next update's coefficients
-            // coef = h .* sigma (sigma is loaded ahead of the sum); pass 1's norm is job k
+            // coef = h .* sigma (sigma is loaded ahead of the sum); the norm is job k (pass 1:
+            // ||w||^2, the breakdown scale; pass 2: ||w'||^2 of the once-orthogonalised vector)
             double *h_out = op == kGsDot ? st->h1 : st->h2;
             const int njobs = k + (want_norm ? 1 : 0);
             for (int q = wid; q < njobs; q += kGsThreads / 32) {
@@ -614,7 +657,10 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
                 const double v = Acc<T>::reduce(a.partials, pld, a.nblk, is_norm ? kKmax : q);
                 if (lane == 0) {
                     if (is_norm) {
-                        st->w0sq = v;
+                        if (op == kGsDot)
+                            st->w0sq = v;
+                        else
+                            s_wsq = v;
                     } else {
                         const double h = sg * v;
                         h_out[q] = h;
@@ -622,9 +668,13 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st)
                     }
                 }
             }
-        } else {
-            cta_finish_pass3<T>(st, k - 1, a.partials, pld, a.nblk, reinterpret_cast<double *>(smem),
-                                (size_t)nst * (size_t)SS * sizeof(T), s_int);
+            if (op == kGsUpdDot) {
+                // the Hessenberg column is complete: ||v_{j+1}||^2 = ||w'||^2 - ||h2||^2 (v_{j+1} =
+                // w' - V h2 with V orthonormal), so pass 3 needs no reduction of its own
+                __syncthreads();
+                cta_finish_pass3<T>(st, k - 1, s_wsq, reinterpret_cast<double *>(smem),
+                                    (size_t)nst * (size_t)SS * sizeof(T), s_int);
+            }
         }
         if (tid == 0) st->ticket[tk] = 0;
     }
@@ -684,6 +734,63 @@ cudaError_t launch_combine_x(int prec, const void *U, long long ld, long long n,
 
 namespace {
 
+// Tensor-map copies of the basis tiles (PPG_GS_TMAP=0 in the environment: one bulk copy per column).
+bool gs_tmap_enabled()
+{
+    static const bool v = [] {
+        const char *e = getenv("PPG_GS_TMAP");
+        return !(e && atoi(e) == 0);
+    }();
+    return v;
+}
+
+// The driver's tensor-map encoder, looked up once through the runtime (no link to libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of the first kcols columns of the column-major basis U (ld elements per column) whose
+// box is one tile of a stage, TR rows x kcols columns, laid out column after column as the stage
+// keeps it.  A box side holds at most 256 elements, so the rows are a 2-D (row chunk, chunk index)
+// pair of 256 x TR/256 when TR > 256: three dimensions (rows in chunk, chunk, column).  The tile at
+// row r0 is then the box at (0, r0 / 256, 0), else at (r0, 0).  False when it cannot be made.
+template <typename T>
+bool basis_tmap(CUtensorMap *m, const void *U, long long ld, int kcols, int TR)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc || kcols < 1 || kcols > 256 || ((uintptr_t)U & 15u) != 0) return false;
+    const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r;
+    if (TR <= 256) {
+        const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)kcols};
+        const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(T)};
+        const cuuint32_t box[2] = {(cuuint32_t)TR, (cuuint32_t)kcols};
+        r = enc(m, dt, 2, const_cast<void *>(U), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        if (TR % 256 != 0 || ld % 256 != 0 || TR / 256 > 256) return false;
+        const cuuint64_t dims[3] = {256, (cuuint64_t)(ld / 256), (cuuint64_t)kcols};
+        const cuuint64_t strides[2] = {256 * sizeof(T), (cuuint64_t)ld * sizeof(T)};
+        const cuuint32_t box[3] = {256, (cuuint32_t)(TR / 256), (cuuint32_t)kcols};
+        r = enc(m, dt, 3, const_cast<void *>(U), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    return r == CUDA_SUCCESS;
+}
+
 template <typename T, int KM>
 struct GsInst {
     static cudaError_t configure()
@@ -713,7 +820,11 @@ struct GsInst {
         long long g = (long long)per * num_sms;
         if (g > a.ntiles) g = a.ntiles;
         a.nblk = (int)(g > 0 ? g : 1);
-        return launch_pdl(k_gs<T, KM>, dim3(a.nblk), dim3(kGsThreads), smem, s, a, st);
+        // iteration passes (k = kcols on the device) of buckets whose tile columns are small copies
+        CUtensorMap tm;
+        memset(&tm, 0, sizeof tm);
+        a.use_tmap = (!a.kcols_from_k && gs_tmap_enabled() && basis_tmap<T>(&tm, a.U, ld, kcols, TR)) ? 1 : 0;
+        return launch_pdl(k_gs<T, KM>, dim3(a.nblk), dim3(kGsThreads), smem, s, a, st, tm);
     }
 };
 
