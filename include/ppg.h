@@ -90,7 +90,15 @@ typedef struct {
     int profile;       /* 1: time every SpMV and Gram-Schmidt launch with CUDA events and report their
                           device time and algorithmic bytes in ppg_stats (adds a sync per cycle) */
     int f32_form;      /* PPG_F32 only: PPG_F32_FLEXIBLE (0, default) or PPG_F32_STANDARD */
-    int reserved[3];
+    int wait_limit_us; /* limit of the library's software waits, in microseconds: the two-step kernel's waits on
+                          its round counters (ppg_chain_fusion) and the host's wait for the device's progress
+                          between enqueued iterations.  <= 0 or >= 10^6: 1 s.  A wait that runs out ends the solve
+                          with PPG_ERR_TIMEOUT once the work already queued has finished (every device wait is
+                          bounded; waits on TMA copies keep their 1 s limit), and ppg_last_error() says where */
+    int test_unreachable_wait; /* tests of the failure path only (0 otherwise): 1 makes every round of the
+                          two-step kernel need one CTA more than its launch has, so that its round-counter
+                          waits run out after wait_limit_us */
+    int reserved[1];
 } ppg_opts;
 
 typedef struct {
@@ -239,8 +247,8 @@ ppg_status ppg_apply_poly(ppg_ctx *ctx, const void *v, void *out, int precision)
  *   - precision PPG_F32 needs the context's float32 copy of the matrix, which this call does not
  *     create: make one float32 ppg_spmv / ppg_apply_poly / ppg_solve call first (else
  *     PPG_ERR_INVALID_ARG).
- *   - The first call on a device looks up the array's device address (once per device, with that
- *     device current); make that first call before any stream capture.
+ *   - ppg_create, which allocates anyway, looks up the array's device address (once per device) for
+ *     every matrix within the limit, so this call maps no memory and allocates nothing.
  *   - Every call uses the same array, which keeps the previous call's contents; calls whose work
  *     overlaps on the GPU (different streams, or concurrent host threads) race with each other.
  *     Calls enqueued on one stream run one after another and are safe.

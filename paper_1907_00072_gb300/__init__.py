@@ -56,7 +56,8 @@ EXPORTED = (
 
 class ppg_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
-                ("profile", ctypes.c_int), ("f32_form", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("profile", ctypes.c_int), ("f32_form", ctypes.c_int), ("wait_limit_us", ctypes.c_int),
+                ("test_unreachable_wait", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class ppg_stats(ctypes.Structure):
@@ -337,13 +338,16 @@ def ppg_apply_poly_noalloc(ctx, v, out):
     return _check(load_library().ppg_apply_poly_noalloc(ctx, _ptr(v), _ptr(out), prec), "ppg_apply_poly_noalloc")
 
 
-def _opts(precision=PPG_F64, inner_rtol=0.0, use_graph=-1, profile=0, f32_form=PPG_F32_FLEXIBLE):
+def _opts(precision=PPG_F64, inner_rtol=0.0, use_graph=-1, profile=0, f32_form=PPG_F32_FLEXIBLE, wait_limit_us=0,
+          test_unreachable_wait=0):
     o = ppg_opts()
     o.precision = precision
     o.inner_rtol = inner_rtol
     o.use_graph = use_graph
     o.profile = profile
     o.f32_form = f32_form
+    o.wait_limit_us = wait_limit_us
+    o.test_unreachable_wait = test_unreachable_wait
     return o
 
 
@@ -356,11 +360,11 @@ def _solve_args(ctx, b, x, where, names):
 
 
 def ppg_solve(ctx, b, x, tol=1e-8, restart=50, maxit=10000, precision=PPG_F64, inner_rtol=0.0, use_graph=-1,
-              profile=0, f32_form=PPG_F32_FLEXIBLE):
+              profile=0, f32_form=PPG_F32_FLEXIBLE, wait_limit_us=0, test_unreachable_wait=0):
     """Solves A x = b in place (x holds x0).  Returns (status, stats dict)."""
     _solve_args(ctx, b, x, "ppg_solve", ("b", "x"))
     st = ppg_stats()
-    o = _opts(precision, inner_rtol, use_graph, profile, f32_form)
+    o = _opts(precision, inner_rtol, use_graph, profile, f32_form, wait_limit_us, test_unreachable_wait)
     s = _check(load_library().ppg_solve(ctx, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit),
                                         ctypes.byref(o), ctypes.byref(st)), "ppg_solve")
     return s, st.as_dict()
@@ -554,11 +558,11 @@ class Solver:
         return out
 
     def solve(self, b, x=None, tol=1e-8, restart=50, maxit=10000, precision=PPG_F64, inner_rtol=0.0, use_graph=-1,
-              profile=0, f32_form=PPG_F32_FLEXIBLE):
+              profile=0, f32_form=PPG_F32_FLEXIBLE, wait_limit_us=0, test_unreachable_wait=0):
         self._workspace(restart, 0, precision)
         x = self._torch.zeros_like(b) if x is None else x
         status, stats = ppg_solve(self.ctx, b, x, tol, restart, maxit, precision, inner_rtol, use_graph, profile,
-                                  f32_form)
+                                  f32_form, wait_limit_us, test_unreachable_wait)
         return x, SolveInfo(status, stats)
 
     def solve_transpose(self, g, lam=None, tol=1e-8, restart=50, maxit=10000, precision=PPG_F64, inner_rtol=0.0):

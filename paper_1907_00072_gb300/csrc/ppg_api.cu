@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <mutex>
 #include <new>
@@ -90,6 +91,8 @@ struct ppg_ctx {
     int *d_etwin = nullptr;
     double *d_evals64 = nullptr;
     int fuse = 0;                // pair consecutive links of the p(A) chain into one launch (measured slower)
+    WaitCfg waits;               // limits of the software waits (set per solve from ppg_opts)
+    char *noalloc_base = nullptr; // device address of the allocation-free apply's scratch (n <= its limit)
 
     // CUDA graphs of single iterations (ppg_opts.use_graph): one per iteration index, precision and
     // polynomial presence, valid while the signature captured with it (workspace addresses,
@@ -401,7 +404,7 @@ struct Exec {
             if (pending_check == check && can_pair(pending, e)) {
                 const cudaError_t err = launch_spmv2(*A, prec, pending, e, c->st, check, c->d_rounds,
                                                      reinterpret_cast<unsigned int *>(c->d_rounds + kMaxRounds),
-                                                     c->d_rounds + kMaxRounds + 8, s);
+                                                     c->d_rounds + kMaxRounds + 8, c->waits, s);
                 if (err == cudaSuccess) {
                     c->launches++;
                     const double mat = spmv_bytes(*A, prec, epi_none());  // the matrix, read once for both
@@ -868,7 +871,10 @@ ppg_status read_state(ppg_ctx *c)
     PPG_CK(cudaStreamSynchronize(c->stream));
     if (c->h_st->error & kErrTimeout) {
         int d[8] = {0};
-        if (c->d_rounds) cudaMemcpy(d, c->d_rounds + kMaxRounds + 8, sizeof d, cudaMemcpyDeviceToHost);
+        if (c->d_rounds) {  // read and clear the two-step kernel's record of the wait that gave up
+            cudaMemcpy(d, c->d_rounds + kMaxRounds + 8, sizeof d, cudaMemcpyDeviceToHost);
+            cudaMemset(c->d_rounds + kMaxRounds + 8, 0, sizeof d);
+        }
         if (d[0])
             return fail(PPG_ERR_TIMEOUT,
                         "a bounded device wait expired (two-step SpMV: %s wait, CTA %d of %d, iteration %d, round %d, "
@@ -1029,16 +1035,25 @@ int launch_ahead()
 // Enqueues the iterations of one restart cycle.  The host waits (yielding) while `ahead`
 // iterations are queued; the wait also ends when the stream has drained, which a cycle whose
 // kernels returned early (an error flag) can cause: the caller reads the state next.
+// The wait is bounded too (c->waits.ns without any progress by the device): when it runs out the
+// host enqueues nothing more, lets the work already queued finish (every device wait is bounded) and
+// reports PPG_ERR_TIMEOUT.
 ppg_status run_cycle(ppg_ctx *c, Iter &it, int restart)
 {
     volatile int *prog = c->h_prog;
     *prog = 0;
     const int ahead = launch_ahead();
     for (int j = 0; j < restart; ++j) {
+        auto t0 = std::chrono::steady_clock::now();
+        int seen = *prog & 0xffff;
         for (int spin = 0;; ++spin) {
             const int p = *prog;
             if (p >> 16) return PPG_OK;
             if (j - (p & 0xffff) < ahead) break;
+            if ((p & 0xffff) != seen) {  // progress: the limit counts from the last step the device made
+                seen = p & 0xffff;
+                t0 = std::chrono::steady_clock::now();
+            }
             if ((spin & 63) == 63) {
                 const cudaError_t q = cudaStreamQuery(c->stream);
                 if (q == cudaSuccess) {
@@ -1046,6 +1061,16 @@ ppg_status run_cycle(ppg_ctx *c, Iter &it, int restart)
                     break;
                 }
                 if (q != cudaErrorNotReady) PPG_CK(q);
+            }
+            const long long waited =
+                std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count();
+            if ((unsigned long long)waited > c->waits.ns) {
+                // the device's own record first: a device wait that ran out explains the delay
+                PPG_TRY(read_state(c));
+                return fail(PPG_ERR_TIMEOUT,
+                            "the host's wait for the device's progress ran out after %lld us (iteration %d queued, "
+                            "device at iteration %d of the cycle)",
+                            waited / 1000, j, *prog & 0xffff);
             }
             std::this_thread::yield();
         }
@@ -1067,6 +1092,15 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
     // the flexible form keeps z_j = p(A) v_j; with no polynomial (or a scalar one) z_j is v_j itself
     const bool flex = prec == PPG_F32 && form == PPG_F32_FLEXIBLE && c->has_poly &&
                       !(c->basis == PPG_BASIS_POWER && c->degree == 0);
+    // limits of the software waits for this solve (the context keeps the defaults otherwise)
+    c->waits = WaitCfg{};
+    if (opts && opts->wait_limit_us > 0 && opts->wait_limit_us < 1000000)
+        c->waits.ns = 1000ull * (unsigned long long)opts->wait_limit_us;
+    if (opts && opts->test_unreachable_wait) c->waits.extra_need = 1;
+    struct Restore {
+        ppg_ctx *c;
+        ~Restore() { c->waits = WaitCfg{}; }
+    } restore{c};
     double inner = 0.0;
     if (prec == PPG_F32) {
         inner = (opts && opts->inner_rtol > 0.0) ? opts->inner_rtol : (flex ? 1e-7 : 1e-6);
@@ -1529,6 +1563,9 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
         }
     }
     PPG_CK(spmv_configure(&c->A));
+    // the allocation-free apply's scratch: its module data is mapped here, where the context allocates
+    // anyway, so that ppg_apply_poly_noalloc itself maps nothing
+    if (n <= kNoAllocMaxN) PPG_TRY(noalloc_scratch(c->device, &c->noalloc_base));
 
     // sliced ELL copy: 32-row slices padded to their longest row (selectable with ppg_spmv_format)
     {
@@ -1830,8 +1867,8 @@ ppg_status ppg_apply_poly_noalloc(ppg_ctx *c, const void *v, void *out, int prec
                     "the float32 copy of the matrix does not exist yet and this call may not allocate it: make one "
                     "float32 ppg_spmv, ppg_apply_poly or ppg_solve call first");
     PPG_TRY(set_device(c));
-    char *base = nullptr;
-    PPG_TRY(noalloc_scratch(c->device, &base));
+    char *base = c->noalloc_base;  // looked up by ppg_create
+    if (!base) PPG_TRY(noalloc_scratch(c->device, &base));
     char *vec[kNoAllocVecs];
     for (int i = 0; i < kNoAllocVecs; ++i) vec[i] = base + (size_t)i * kNoAllocMaxN * sizeof(double);
     PPG_CK(launch_copy_in(c->A.n, precision, v, vec[0], c->stream));

@@ -205,6 +205,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
 
+// A bounded wait ran out: record it and end the solve, so that the kernels still queued for the
+// cycle return at once (the host then reports PPG_ERR_TIMEOUT).
+__device__ __forceinline__ void timeout_stop(Cycle *st)
+{
+    atomicOr(&st->error, kErrTimeout);
+    st->stop = 1;
+    st->cycle_done = 1;
+    st->k = 0;
+}
+
 // Named barrier `id` over `nthreads` threads that also ORs a predicate across them.
 __device__ __forceinline__ bool bar_any(int id, int nthreads, bool v)
 {

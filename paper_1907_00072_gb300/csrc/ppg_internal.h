@@ -275,8 +275,15 @@ cudaError_t launch_sell_fill(int n, int nslices, const int *rowptr, const int *c
 // as the launch has CTAs (spmv2_tiles_ok); round_done (zero on entry, left zero) holds one int
 // per round of the persistent grid, ticket one unsigned int (zero), diag 8 ints (zero) where a
 // wait that gives up records itself.
+// Limits of the library's software waits: the round-counter waits of the two-step kernel give up
+// after ns; extra_need (tests of the failure path only) makes a round need that many CTAs more than
+// the launch has, so that those waits run out.
+struct WaitCfg {
+    unsigned long long ns = kWaitLimitNs;
+    int extra_need = 0;
+};
 cudaError_t launch_spmv2(const DevMatrix &A, int prec, const SpmvEpi &e1, const SpmvEpi &e2, Cycle *st, int check_done,
-                         int *round_done, unsigned int *ticket, int *diag, cudaStream_t s);
+                         int *round_done, unsigned int *ticket, int *diag, const WaitCfg &wc, cudaStream_t s);
 cudaError_t launch_make_coloff(int n, const int *rowptr, const int *colidx, short *out, int *flag, cudaStream_t s);
 int spmv_cap_max();
 int spmv_rows_per_thread();

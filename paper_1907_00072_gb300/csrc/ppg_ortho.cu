@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st, const __
     // the host's bound must cover k (else refuse rather than overrun a stage)
     const bool bad = !skip && (k > KM || k > a.kstage || (early && k != a.kstage));
     if (skip || bad) {
-        if (bad && tid == 0 && blockIdx.x == 0) atomicOr(&st->error, kErrTimeout);
+        if (bad && tid == 0 && blockIdx.x == 0) timeout_stop(st);
         if (early) {  // the copies already requested land before the CTA's shared memory is released
             if (prod && lane == 0 && !early_w)
                 for (int q = 0; q < nst - 1; ++q)
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st, const __
         }
     }
     if (timed_out) {
-        if (tid == 0) atomicOr(&st->error, kErrTimeout);
+        if (tid == 0) timeout_stop(st);
         // copies already issued into the stages may still land: wait for them (bounded) first
         for (int q = 0; q < nst - 1; ++q) mbar_wait_bounded(&bars[(it + q) % nst], ((it + q) / nst) & 1, kWaitLimitNs);
         return;
@@ -960,7 +960,7 @@ __global__ void __launch_bounds__(kThreads) k_gram_cholesky(int n, long long ld,
         }
     }
     if (timed_out) {
-        if (tid == 0) atomicOr(&st->error, kErrTimeout);
+        if (tid == 0) timeout_stop(st);
         // copies already issued into either stage may still land: wait for them (bounded) first
         mbar_wait_bounded(&bars[it & 1], (it >> 1) & 1, kWaitLimitNs);
         mbar_wait_bounded(&bars[(it + 1) & 1], ((it + 1) >> 1) & 1, kWaitLimitNs);

@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv(Spmv
                 if (tile + gridDim.x < ntiles) bounds(tile + gridDim.x, ne0, ne1);
                 const int s = i % kSpmvStages, round = i / kSpmvStages;
                 if (round > 0 && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitLimitNs)) {
-                    atomicOr(&st->error, kErrTimeout);
+                    timeout_stop(st);
                     break;
                 }
                 const int r0 = (int)(tile * R);
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv(Spmv
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
         const int s = i % kSpmvStages;
         if (!mbar_wait_bounded(&full[s], (i / kSpmvStages) & 1, kWaitLimitNs)) {
-            if (lane == 0) atomicOr(&st->error, kErrTimeout);
+            if (lane == 0) timeout_stop(st);
             mbar_wait_bounded(&full[s], (i / kSpmvStages) & 1, kWaitLimitNs);
             return;
         }
@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_w(Sp
                 }
                 const int s = i % kSpmvStages, round = i / kSpmvStages;
                 if (round > 0 && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitLimitNs)) {
-                    atomicOr(&st->error, kErrTimeout);
+                    timeout_stop(st);
                     break;
                 }
                 issue_matrix(tile, s, e0, e1);
@@ -755,7 +755,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_w(Sp
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
         const int s = i % kSpmvStages;
         if (!mbar_wait_bounded(&full[s], (i / kSpmvStages) & 1, kWaitLimitNs)) {
-            if (lane == 0) atomicOr(&st->error, kErrTimeout);
+            if (lane == 0) timeout_stop(st);
             mbar_wait_bounded(&full[s], (i / kSpmvStages) & 1, kWaitLimitNs);
             return;
         }
@@ -1008,7 +1008,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                     desc(tile + gridDim.x, nd);
                 }
                 if (round > 0 && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitLimitNs)) {
-                    atomicOr(&st->error, kErrTimeout);
+                    timeout_stop(st);
                     break;
                 }
                 issue_matrix(s, o0, o1);
@@ -1075,7 +1075,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
             }
         }
         if (!mbar_wait_bounded(&full[s], ph, kWaitLimitNs)) {
-            if (lane == 0) atomicOr(&st->error, kErrTimeout);
+            if (lane == 0) timeout_stop(st);
             mbar_wait_bounded(&full[s], ph, kWaitLimitNs);
             return;
         }
@@ -1162,6 +1162,8 @@ struct Spmv2Args {
     int *round_done;     // per round: CTAs that have finished its first step (zero at launch)
     unsigned int *ticket;
     int *diag;           // 8 ints: where a bounded wait gave up (first CTA to time out)
+    unsigned long long round_wait_ns;  // limit of one round-counter wait
+    int extra_need;      // tests of the failure path: CTAs a round needs beyond the launch's (0 normally)
 };
 
 // records a wait that gave up: kind 1 full barrier, 2 round counter; the first CTA wins
@@ -1241,7 +1243,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv2(Spm
                 if (tile + NG < ntiles) bounds(tile + NG, ne0, ne1);
                 const int s = i % kSpmv2Stages, use = i / kSpmv2Stages;
                 if (use > 0 && !mbar_wait_bounded(&empty[s], (use - 1) & 1, kWaitLimitNs)) {
-                    atomicOr(&st->error, kErrTimeout);
+                    timeout_stop(st);
                     break;
                 }
                 const int r0 = (int)(tile * R);
@@ -1279,7 +1281,7 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv2(Spm
             const int s = (int)(i % kSpmv2Stages);
             if (!mbar_wait_bounded(&full[s], (int)(i / kSpmv2Stages) & 1, kWaitLimitNs)) {
                 if (lane == 0) {
-                    atomicOr(&st->error, kErrTimeout);
+                    timeout_stop(st);
                     spmv2_diag(p.diag, 1, i, i, s, 0);
                 }
                 s_fail = 1;
@@ -1302,10 +1304,10 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv2(Spm
                 // first-step rows within the bandwidth of round j: rounds j-1 .. j+1 complete
                 const unsigned long long t0 = global_timer_ns();
                 for (long long r = (j > 0 ? j - 1 : 0); r <= j + 1 && r < nrounds && !s_fail; ++r) {
-                    const int need = (int)min(NG, ntiles - r * NG);
+                    const int need = (int)min(NG, ntiles - r * NG) + p.extra_need;
                     for (unsigned int spins = 1; ld_acquire(p.round_done + r) < need; ++spins)
-                        if ((spins & 63u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
-                            atomicOr(&st->error, kErrTimeout);
+                        if ((spins & 63u) == 0 && global_timer_ns() - t0 > p.round_wait_ns) {
+                            timeout_stop(st);
                             spmv2_diag(p.diag, 2, i, r, ld_acquire(p.round_done + r), need);
                             s_fail = 1;
                             break;
@@ -1626,12 +1628,12 @@ int spmv2_per_sm(int cap)
 template <typename T, typename IDX>
 cudaError_t spmv2_go(const DevMatrix &A, const T *vals, const IDX *cols, int cap, int blocks, const SpmvEpi &e1,
                      const SpmvEpi &e2, Cycle *st, int check_done, int *round_done, unsigned int *ticket, int *diag,
-                     cudaStream_t s)
+                     const WaitCfg &wc, cudaStream_t s)
 {
     const int R = A.rows_per_tile;
     const long long ntiles = ((long long)A.n + R - 1) / R;
     Spmv2Args<T, IDX> p{{A.n, A.rowptr, cols, vals, R, A.lanes_per_row, cap, st, check_done, e1},
-                        e2, round_done, ticket, diag};
+                        e2, round_done, ticket, diag, wc.ns, wc.extra_need};
     long long g = blocks;
     if (g > ntiles) g = ntiles;
     return launch_coop(k_spmv2<T, IDX>, dim3((unsigned)g), dim3(kSpmvThreads),
@@ -1822,20 +1824,20 @@ cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *s
 }
 
 cudaError_t launch_spmv2(const DevMatrix &A, int prec, const SpmvEpi &e1, const SpmvEpi &e2, Cycle *st, int check_done,
-                         int *round_done, unsigned int *ticket, int *diag, cudaStream_t s)
+                         int *round_done, unsigned int *ticket, int *diag, const WaitCfg &wc, cudaStream_t s)
 {
     if (prec == kF64) {
         if (A.coloff)
             return spmv2_go<double, short>(A, A.vals64, A.coloff, A.cap64, A.spmv2_blocks64, e1, e2, st, check_done,
-                                           round_done, ticket, diag, s);
+                                           round_done, ticket, diag, wc, s);
         return spmv2_go<double, int>(A, A.vals64, A.colidx, A.cap64, A.spmv2_blocks64, e1, e2, st, check_done,
-                                     round_done, ticket, diag, s);
+                                     round_done, ticket, diag, wc, s);
     }
     if (A.coloff)
         return spmv2_go<float, short>(A, A.vals32, A.coloff, A.cap32, A.spmv2_blocks32, e1, e2, st, check_done,
-                                      round_done, ticket, diag, s);
+                                      round_done, ticket, diag, wc, s);
     return spmv2_go<float, int>(A, A.vals32, A.colidx, A.cap32, A.spmv2_blocks32, e1, e2, st, check_done, round_done,
-                                ticket, diag, s);
+                                ticket, diag, wc, s);
 }
 
 template <typename T, int G>
