@@ -288,6 +288,17 @@ ppg_status ppg_arnoldi(ppg_ctx *ctx, const double *v, int k, double *V, double *
  * polynomial.  wr, wi: device float64[k].  Exposed for testing.  1 <= k <= 64. */
 ppg_status ppg_hessenberg_eigs(ppg_ctx *ctx, int k, const double *H, int ld, double *wr, double *wi);
 
+/* Solves the normal equations G y = r of Eq. 1 for a caller-given Gram matrix with the device's Cholesky, the
+ * one ppg_build_poly(PPG_BASIS_POWER) runs: column by column with LAPACK POTRF's test (a pivot that is not
+ * positive, NaN included, stops the factorisation; *info = its 1-based order, 0 if none), then the solve with
+ * the leading block that factored, so that the degree used is degree (info = 0) or info - 2 (Section IV).
+ * G_h: (degree+1) x (degree+1) column-major, r_h: degree+1 values, coef_h: degree+1 values out (zero beyond
+ * the degree used); all host memory.  info, degree_used (host) may be NULL.  0 <= degree <= 62.  Exposed to
+ * test the factorisation and the degree rule on a given G.  Allocates a small device buffer; synchronises.
+ * Returns PPG_OK, PPG_WARN_DEGREE_CLAMPED, or an error (PPG_ERR_POLY_BREAKDOWN when degree 0 fails). */
+ppg_status ppg_gram_solve(ppg_ctx *ctx, int degree, const double *G_h, const double *r_h, double *coef_h, int *info,
+                          int *degree_used);
+
 /* Fills out[i] = uniform in [-1, 1) from the counter-based SplitMix64 stream `seed` (element i is the
  * stream's position i: z = mix(mix(seed) + (i+1) * 0x9E3779B97F4A7C15), u = (z >> 11) * 2^-53).
  * This is the generator ppg_build_poly uses when v0 is NULL. */

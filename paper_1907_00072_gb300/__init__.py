@@ -49,7 +49,7 @@ EXPORTED = (
     "ppg_create", "ppg_destroy", "ppg_set_stream", "ppg_workspace_bytes", "ppg_set_workspace", "ppg_spmv",
     "ppg_spmv_format", "ppg_chain_fusion", "ppg_build_poly", "ppg_set_poly", "ppg_get_poly", "ppg_apply_poly", "ppg_apply_poly_noalloc", "ppg_solve",
     "ppg_solve_transpose",
-    "ppg_csr_outer", "ppg_arnoldi", "ppg_hessenberg_eigs", "ppg_fill_uniform", "ppg_solve_batched",
+    "ppg_csr_outer", "ppg_arnoldi", "ppg_hessenberg_eigs", "ppg_gram_solve", "ppg_fill_uniform", "ppg_solve_batched",
     "ppg_status_string", "ppg_last_error", "ppg_version",
 )
 
@@ -115,6 +115,7 @@ def load_library(path: str = LIB_PATH):
         "ppg_csr_outer": (I, [P, P, P, D, P]),
         "ppg_arnoldi": (I, [P, P, I, P, P, ctypes.POINTER(I)]),
         "ppg_hessenberg_eigs": (I, [P, I, P, I, P, P]),
+        "ppg_gram_solve": (I, [P, I, P, P, P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "ppg_fill_uniform": (I, [P, P, I64, U64]),
         "ppg_solve_batched": (I, [I, ctypes.POINTER(ppg_batch_system), I, D, I, I, U64, P,
                                   ctypes.POINTER(ppg_stats)]),
@@ -428,6 +429,26 @@ def ppg_hessenberg_eigs(ctx, H, wr, wi):
     _f64(ctx, wr, where, "wr", length=k)
     _f64(ctx, wi, where, "wi", length=k)
     return _check(load_library().ppg_hessenberg_eigs(ctx, k, _ptr(H), ld, _ptr(wr), _ptr(wi)), where)
+
+
+def ppg_gram_solve(ctx, G, r):
+    """Solves G y = r (Eq. 1's normal equations) with the device Cholesky and Section IV's degree rule.
+    G: (d+1, d+1) and r: (d+1,) host arrays.  Returns (y, info, degree_used, status)."""
+    import numpy as np
+
+    where = "ppg_gram_solve"
+    _ctx(ctx, where)
+    Gf = np.asfortranarray(G, dtype=np.float64)
+    rf = np.ascontiguousarray(r, dtype=np.float64)
+    kk = Gf.shape[0]
+    if Gf.ndim != 2 or Gf.shape[1] != kk or rf.shape != (kk,):
+        raise ValueError(f"{where}: G must be square and r of its order")
+    y = np.zeros(kk)
+    info, used = ctypes.c_int(0), ctypes.c_int(0)
+    st = _check(load_library().ppg_gram_solve(ctx, kk - 1, Gf.ctypes.data_as(ctypes.c_void_p),
+                                              rf.ctypes.data_as(ctypes.c_void_p), y.ctypes.data_as(ctypes.c_void_p),
+                                              ctypes.byref(info), ctypes.byref(used)), where)
+    return y, info.value, used.value, st
 
 
 def ppg_fill_uniform(ctx, out, seed):

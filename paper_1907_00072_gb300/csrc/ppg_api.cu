@@ -2140,6 +2140,32 @@ ppg_status ppg_hessenberg_eigs(ppg_ctx *c, int k, const double *H, int ld, doubl
     return PPG_OK;
 }
 
+ppg_status ppg_gram_solve(ppg_ctx *c, int degree, const double *G_h, const double *r_h, double *coef_h, int *info,
+                          int *degree_used)
+{
+    PPG_TRY(check_ctx(c));
+    if (degree < 0 || degree > kSmallMax - 2 || !G_h || !r_h || !coef_h)
+        return fail(PPG_ERR_INVALID_ARG, "bad arguments (0 <= degree <= %d, non-null G, r, coef)", kSmallMax - 2);
+    PPG_TRY(set_device(c));
+    const int kk = degree + 1;
+    double *d = nullptr;
+    PPG_CK(cudaMalloc(&d, sizeof(double) * (size_t)(kk * kk + 2 * kk)));
+    struct Free {
+        double *p;
+        ~Free() { cudaFree(p); }
+    } guard{d};
+    PPG_CK(cudaMemcpyAsync(d, G_h, sizeof(double) * kk * kk, cudaMemcpyHostToDevice, c->stream));
+    PPG_CK(cudaMemcpyAsync(d + kk * kk, r_h, sizeof(double) * kk, cudaMemcpyHostToDevice, c->stream));
+    PPG_CK(launch_gram_solve(d, d + kk * kk, degree, d + kk * kk + kk, c->d_info, c->stream));
+    PPG_CK(cudaMemcpyAsync(coef_h, d + kk * kk + kk, sizeof(double) * kk, cudaMemcpyDeviceToHost, c->stream));
+    PPG_CK(cudaMemcpyAsync(c->h_info, c->d_info, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+    PPG_CK(cudaStreamSynchronize(c->stream));
+    if (info) *info = c->h_info[0];
+    if (degree_used) *degree_used = c->h_info[1];
+    if (c->h_info[1] < 0) return fail(PPG_ERR_POLY_BREAKDOWN, "the Gram matrix is not positive at degree 0");
+    return c->h_info[0] ? PPG_WARN_DEGREE_CLAMPED : PPG_OK;
+}
+
 ppg_status ppg_fill_uniform(ppg_ctx *c, double *out, int64_t n, uint64_t seed)
 {
     PPG_TRY(check_ctx(c));

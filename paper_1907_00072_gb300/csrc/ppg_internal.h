@@ -226,6 +226,10 @@ int gs_max_blocks(int num_sms);
 cudaError_t launch_gram_cholesky(int n, long long ld, const double *B, int deg, double *partials, int nblk,
                                  double *coef_out, int *info_out, Cycle *st, cudaStream_t s);
 int gram_grid(int num_sms);
+// The same Cholesky and solve on a given (deg + 1)^2 Gram matrix G and right-hand side r (device
+// pointers); coef_out deg + 1 values, info_out 3 ints as launch_gram_cholesky's.
+cudaError_t launch_gram_solve(const double *G, const double *r, int deg, double *coef_out, int *info_out,
+                              cudaStream_t s);
 
 // Roots of 1 - z p(z): harmonic Ritz values of the Arnoldi Hessenberg matrix, Leja ordered.
 cudaError_t launch_roots(const Cycle *st, int k, double *roots_out /* 2k */, double *table_out, int *status_out,

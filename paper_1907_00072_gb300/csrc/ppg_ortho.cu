@@ -869,6 +869,65 @@ cudaError_t launch_gs(int prec, int kcols, long long ld, int num_sms, GsArgs a, 
 
 // ---------------------------------------------------------------- Gram matrix of Eq. 1 and its Cholesky solve
 
+// The normal equations G y = r of Eq. 1 (G = (AV)^T AV, kk = deg + 1, column-major in shared memory,
+// overwritten by its Cholesky factor L), by the whole CTA: column-by-column Cholesky with LAPACK
+// POTRF's test (a pivot that is not > 0, NaN included, stops the factorisation with info = its 1-based
+// order), then forward and back substitution with the leading block that factored.  The degree used is
+// deg when info = 0, else info - 2 (the largest degree with no Cholesky failure, Section IV).
+// info_out: [0] info, [1] degree used, [2] 1 if the coefficients are finite; coef_out: kk values
+// (zero beyond the degree used).  Products and differences are rounded separately (no fused
+// multiply-add), so a given G factors to the same bits as a plain IEEE evaluation of the same loops.
+__device__ void cta_gram_solve(double *G, const double *r, double *y, int kk, int deg, double *coef_out, int *info_out,
+                               int *s_info)
+{
+    const int tid = threadIdx.x;
+    if (tid == 0) *s_info = 0;
+    __syncthreads();
+    for (int j = 0; j < kk; ++j) {
+        if (tid == 0) {
+            double d = G[j + j * kk];
+            for (int p = 0; p < j; ++p) d = __dsub_rn(d, __dmul_rn(G[j + p * kk], G[j + p * kk]));
+            if (!(d > 0.0))
+                *s_info = j + 1;
+            else
+                G[j + j * kk] = sqrt(d);
+        }
+        __syncthreads();
+        if (*s_info) break;
+        const double ljj = G[j + j * kk];
+        for (int i = j + 1 + tid; i < kk; i += blockDim.x) {
+            double s = G[i + j * kk];
+            for (int p = 0; p < j; ++p) s = __dsub_rn(s, __dmul_rn(G[i + p * kk], G[j + p * kk]));
+            G[i + j * kk] = s / ljj;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const int info = *s_info;
+        const int used = info ? info - 2 : deg;
+        for (int i = 0; i < kk; ++i) y[i] = 0.0;
+        const int m = used + 1;
+        for (int i = 0; i < m; ++i) {
+            double s = r[i];
+            for (int p = 0; p < i; ++p) s = __dsub_rn(s, __dmul_rn(G[i + p * kk], y[p]));
+            y[i] = s / G[i + i * kk];
+        }
+        for (int i = m - 1; i >= 0; --i) {
+            double s = y[i];
+            for (int p = i + 1; p < m; ++p) s = __dsub_rn(s, __dmul_rn(G[p + i * kk], y[p]));
+            y[i] = s / G[i + i * kk];
+        }
+        bool finite = true;
+        for (int i = 0; i < kk; ++i) {
+            coef_out[i] = (i < m) ? y[i] : 0.0;
+            finite = finite && isfinite(coef_out[i]);
+        }
+        info_out[0] = info;
+        info_out[1] = used;
+        info_out[2] = finite ? 1 : 0;
+    }
+}
+
 // B holds the power basis [v0, A v0, ..., A^{d+1} v0] column-major (ld rows per column,
 // rows beyond n zero).  One streaming pass forms every inner product B_a . B_b
 // (0 <= a <= b <= d+1) from TMA-staged row tiles; the last CTA reduces them, factors
@@ -996,52 +1055,33 @@ __global__ void __launch_bounds__(kThreads) k_gram_cholesky(int n, long long ld,
             }
         }
     }
-    if (tid == 0) s_info = 0;
+    cta_gram_solve(G, r, y, kk, deg, coef_out, info_out, &s_info);
+    if (tid == 0) st->ticket[7] = 0;
+}
+
+// Standalone use of the same factorisation and solve on a caller-given Gram matrix (tests).
+__global__ void __launch_bounds__(kThreads) k_gram_solve(const double *__restrict__ Gin, const double *__restrict__ rin,
+                                                         int deg, double *coef_out, int *info_out)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_info;
+    const int kk = deg + 1;
+    double *G = reinterpret_cast<double *>(smem);
+    double *r = G + kk * kk;
+    double *y = r + kk;
+    for (int e = threadIdx.x; e < kk * kk; e += blockDim.x) G[e] = Gin[e];
+    for (int i = threadIdx.x; i < kk; i += blockDim.x) r[i] = rin[i];
     __syncthreads();
-    for (int j = 0; j < kk; ++j) {
-        if (tid == 0) {
-            double d = G[j + j * kk];
-            for (int p = 0; p < j; ++p) d -= G[j + p * kk] * G[j + p * kk];
-            if (!(d > 0.0))
-                s_info = j + 1;
-            else
-                G[j + j * kk] = sqrt(d);
-        }
-        __syncthreads();
-        if (s_info) break;
-        const double ljj = G[j + j * kk];
-        for (int i = j + 1 + tid; i < kk; i += kThreads) {
-            double s = G[i + j * kk];
-            for (int p = 0; p < j; ++p) s -= G[i + p * kk] * G[j + p * kk];
-            G[i + j * kk] = s / ljj;
-        }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        const int info = s_info;
-        const int used = info ? info - 2 : deg;
-        for (int i = 0; i < kk; ++i) y[i] = 0.0;
-        const int m = used + 1;
-        for (int i = 0; i < m; ++i) {
-            double s = r[i];
-            for (int p = 0; p < i; ++p) s -= G[i + p * kk] * y[p];
-            y[i] = s / G[i + i * kk];
-        }
-        for (int i = m - 1; i >= 0; --i) {
-            double s = y[i];
-            for (int p = i + 1; p < m; ++p) s -= G[p + i * kk] * y[p];
-            y[i] = s / G[i + i * kk];
-        }
-        bool finite = true;
-        for (int i = 0; i < kk; ++i) {
-            coef_out[i] = (i < m) ? y[i] : 0.0;
-            finite = finite && isfinite(coef_out[i]);
-        }
-        info_out[0] = info;
-        info_out[1] = used;
-        info_out[2] = finite ? 1 : 0;
-        st->ticket[7] = 0;
-    }
+    cta_gram_solve(G, r, y, kk, deg, coef_out, info_out, &s_info);
+}
+
+cudaError_t launch_gram_solve(const double *G, const double *r, int deg, double *coef_out, int *info_out,
+                              cudaStream_t s)
+{
+    const int kk = deg + 1;
+    const size_t smem = sizeof(double) * (size_t)(kk * kk + 2 * kk);
+    k_gram_solve<<<1, kThreads, smem, s>>>(G, r, deg, coef_out, info_out);
+    return cudaGetLastError();
 }
 
 int gram_grid(int num_sms)

@@ -332,7 +332,8 @@ def test_build_poly_roots_are_roots_of_the_oracle_polynomial(deg, mat):
     z = roots[0::2] + 1j * roots[1::2]
     for zi in z:
         assert abs(1 - _zp_complex(p, zi)) <= 1e-9, (zi, abs(1 - _zp_complex(p, zi)))
-    # (2) conjugate pairs are adjacent, positive imaginary part first
+    # (2) conjugate pairs are adjacent, positive imaginary part first, and the order is the modified
+    # Leja order of these roots (the rule _leja restates)
     i = 0
     while i < len(z):
         if z[i].imag != 0:
@@ -340,6 +341,7 @@ def test_build_poly_roots_are_roots_of_the_oracle_polynomial(deg, mat):
             i += 2
         else:
             i += 1
+    assert list(z) == list(_leja(list(z))), "the device's order is not the modified Leja order"
     # (3) the construction residual equals the GMRES residual of the oracle (Eq. 1)
     assert abs(resid - p.resid / np.linalg.norm(v0)) <= 1e-8 * max(resid, 1e-3)
     # (4) applying the roots form equals the oracle's Arnoldi-form application
@@ -347,6 +349,95 @@ def test_build_poly_roots_are_roots_of_the_oracle_polynomial(deg, mat):
     y = s.apply_poly(T(x)).cpu().numpy()
     ref = oracle.poly_apply(a, p, x)
     assert np.linalg.norm(y - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("mat", ["c1", "27pt", "random"])
+@pytest.mark.parametrize("deg", [5, 30])
+def test_device_cholesky_on_the_oracles_gram_matrix(mat, deg):
+    """The device's Cholesky with Section IV's degree rule, given the oracle's own Gram matrix of Eq. 1
+    (degree 30 is past the first failing pivot on every matrix here): the same POTRF info, the same
+    degree, and the same coefficients bit for bit (both evaluate the same loops without fused
+    multiply-adds)."""
+    a = ROOT_MATS[mat]()
+    p = oracle.poly_normal_eq(a, w.v0(a.n), deg)
+    s = solver_for(a)
+    y, info, used, st = ppg.ppg_gram_solve(s.ctx, p.gram, p.rhs)
+    assert (info, used) == (p.info, p.used)
+    assert st == (ppg.PPG_WARN_DEGREE_CLAMPED if info else ppg.PPG_OK)
+    np.testing.assert_array_equal(y[: used + 1], p.coef[: used + 1])
+    assert not y[used + 1:].any()
+    if deg == 30:
+        assert info > 0  # the power basis fails before degree 30 (Section IV)
+
+
+def test_device_cholesky_pivot_rule():
+    """POTRF's test on constructed matrices: the first pivot that is not positive (NaN included) stops
+    the factorisation at its 1-based order, as LAPACK's dpotrf reports it; a positive definite G is
+    solved to rounding."""
+    from scipy.linalg import lapack
+
+    s = solver_for(w.c1_matrix())
+    rng = np.random.default_rng(5)
+    k = 9
+    M = rng.standard_normal((k, k))
+    G = M @ M.T + k * np.eye(k)
+    r = rng.standard_normal(k)
+    y, info, used, st = ppg.ppg_gram_solve(s.ctx, G, r)
+    assert (info, used, st) == (0, k - 1, ppg.PPG_OK)
+    np.testing.assert_allclose(y, np.linalg.solve(G, r), rtol=1e-12, atol=1e-14)
+    # a negative pivot at order 5: the Schur complement of the leading 4 x 4 block made -1
+    L = np.linalg.cholesky(G[:4, :4])
+    Gb = G.copy()
+    Gb[4, 4] = G[4, :4] @ np.linalg.solve(G[:4, :4], G[:4, 4]) - 1.0
+    assert lapack.dpotrf(Gb, lower=1)[1] == 5 and oracle.cholesky(Gb)[1] == 5
+    y, info, used, st = ppg.ppg_gram_solve(s.ctx, Gb, r)
+    assert (info, used, st) == (5, 3, ppg.PPG_WARN_DEGREE_CLAMPED)
+    np.testing.assert_allclose(y[:4], np.linalg.solve(G[:4, :4], r[:4]), rtol=1e-12)
+    assert L.shape == (4, 4)
+    # NaN on the diagonal at order 3
+    Gn = G.copy()
+    Gn[2, 2] = np.nan
+    y, info, used, st = ppg.ppg_gram_solve(s.ctx, Gn, r)
+    assert (info, used) == (3, 1)
+    # degree 0 fails: no polynomial
+    G0 = G.copy()
+    G0[0, 0] = -1.0
+    with pytest.raises(ppg.PPGError) as e:
+        ppg.ppg_gram_solve(s.ctx, G0, r)
+    assert e.value.status == ppg.PPG_ERR_POLY_BREAKDOWN
+
+
+def _mgs_dots(iters, cycles, m):
+    """Inner products + norms of MGS Arnoldi over the cycles (j + 2 at step j), all full but the last."""
+    tot = 0
+    left = iters
+    for _ in range(cycles):
+        k = min(m, left)
+        tot += sum(j + 2 for j in range(k))
+        left -= k
+    return tot
+
+
+@pytest.mark.parametrize("restart", [7, 50])
+@pytest.mark.parametrize("mat", ["c1", "random"])
+def test_counters_match_the_oracle(mat, restart):
+    """SpMVs counted as in Section III (per iteration p(A) and A, per cycle end p(A), every true residual)
+    equal the oracle's; the dots differ only by the orthogonalisation: the oracle's MGS takes j + 2 per
+    step, two-pass classical Gram-Schmidt 3 (two block inner products and a norm), plus one norm per true
+    residual in both."""
+    a = ROOT_MATS[mat]()
+    b = w.rhs(a.n)
+    v0 = w.v0(a.n)
+    s = solver_for(a)
+    s.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=T(v0))
+    ref = oracle.gmres(a, b, oracle.poly_gmres(a, v0, 10), tol=1e-8, m=restart, maxit=5000)
+    x, info = s.solve(T(b), tol=1e-8, restart=restart, maxit=5000)
+    st = info.stats
+    assert (st["iterations"], st["restarts"]) == (ref.iters, ref.restarts)
+    assert st["spmvs"] == ref.spmvs
+    residual_norms = ref.dots - _mgs_dots(ref.iters, ref.restarts, restart)
+    assert residual_norms == ref.restarts + 1
+    assert st["dots"] == 3 * st["iterations"] + residual_norms
 
 
 def test_build_poly_v0_from_seed_equals_passing_the_vector():
@@ -616,6 +707,55 @@ def test_transposed_solve_and_gradients_match_dense():
     gvals = -lam[rows] * xd[a.colidx]
     np.testing.assert_allclose(bt.grad.cpu().numpy(), lam, rtol=1e-7, atol=1e-9 * np.abs(lam).max())
     np.testing.assert_allclose(vals.grad.cpu().numpy(), gvals, rtol=1e-7, atol=1e-9 * np.abs(gvals).max())
+
+
+def test_adjoint_gradients_match_central_differences_32cubed():
+    """The adjoint behind ppg.solve on a 3D convection-diffusion system (32^3, Pe 50, degree 20,
+    L = ||x - x_t||^2): dL/db and dL/dvals on 50 seeded entries each against central differences with
+    h = 1e-6, relative error <= 1e-4.  The perturbed systems are solved exactly, not iteratively: a
+    sparse LU of A on the host, and for a value a_ij the rank-one identity (A + d e_i e_j^T)^-1 b =
+    x - d x_j / (1 + d z_j) z with z = A^-1 e_i; L(+h) - L(-h) is formed from the two solution changes,
+    so neither an iterative solver's stopping error nor the size of L enters the difference quotient."""
+    import scipy.sparse.linalg as sla
+
+    a = w.convdiff(32, 3, 50.0)
+    bh = w.rhs(a.n)
+    xth = w.uniform(w.SEED_XTARGET, a.n)
+    s = solver_for(a)
+    s.build_poly(20, ppg.PPG_BASIS_ROOTS, v0=T(w.v0(a.n)))
+    vals = s.vals.requires_grad_(True)
+    b = T(bh).requires_grad_(True)
+    x = ppg.solve(s, vals, b, tol=1e-13, restart=50, maxit=5000)
+    ((x - T(xth)) ** 2).sum().backward()
+    gb, gv = b.grad.cpu().numpy(), vals.grad.cpu().numpy()
+
+    lu = sla.splu(a.to_scipy().tocsc())
+    xh = lu.solve(bh)
+    r = xh - xth
+    h = 1e-6
+    rng = np.random.default_rng(11)
+    rows = np.repeat(np.arange(a.n), np.diff(a.rowptr))
+
+    def dL(c_plus, c_minus, z):
+        # L(x + c z) - L(x) = 2 c r.z + c^2 z.z, differenced between the two perturbations
+        rz, zz = r @ z, z @ z
+        return 2 * (c_plus - c_minus) * rz + (c_plus ** 2 - c_minus ** 2) * zz
+
+    def rel(fd, g, scale):
+        return abs(fd - g) / max(abs(g), 1e-3 * scale)
+
+    errs_b, errs_v = [], []
+    for i in rng.choice(a.n, 50, replace=False):
+        z = lu.solve(np.eye(1, a.n, i).ravel())
+        errs_b.append(rel(dL(h, -h, z) / (2 * h), gb[i], np.abs(gb).max()))
+    for k in rng.choice(a.nnz, 50, replace=False):
+        i, j = rows[k], a.colidx[k]
+        z = lu.solve(np.eye(1, a.n, i).ravel())
+        cp = -h * xh[j] / (1 + h * z[j])
+        cm = h * xh[j] / (1 - h * z[j])
+        errs_v.append(rel(dL(cp, cm, z) / (2 * h), gv[k], np.abs(gv).max()))
+    assert max(errs_b) <= 1e-4, max(errs_b)
+    assert max(errs_v) <= 1e-4, max(errs_v)
 
 
 def test_differentiable_solve_raises_when_not_converged():
