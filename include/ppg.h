@@ -319,12 +319,18 @@ typedef struct {
 /* Solves nsys independent systems in one persistent launch (replayed from a CUDA graph).  Each
  * system is owned by one thread-block cluster, which builds the system's minimum-residual polynomial
  * (roots form, the given degree, v0 uniform in [-1, 1] from the SplitMix64 stream seed + i, float64
- * construction) and runs float32 PP-GMRES(restart) cycles, each ending with a float64 residual and
- * update of x (iterative refinement; a cycle stops early once its residual estimate drops by 1e-6),
- * until ||b - A x|| <= tol ||b|| or maxit iterations.  Systems start largest first.  The number of
- * CTAs per system is chosen by timing the construction phase of the batch for 4, 8 and 16 CTAs on the
- * first call with a new batch (cached afterwards).  per_sys (host, nsys entries, may be NULL) receives
- * each system's statistics (time_ms: the whole batch).  restart <= 40,
+ * construction) and runs float32 PP-GMRES(restart) cycles in the flexible form of ppg_solve's
+ * default (z_j = p(A) v_j kept, x += Z y in float64, the float64 true residual projected onto the
+ * finished cycle's space before a restart; a cycle also stops once its residual estimate drops by
+ * 1e-7), until ||b - A x|| <= tol ||b|| or maxit iterations.  Systems start largest first.  The first
+ * call with a new batch shape (the sorted list of (n, nnz), degree and restart) tunes the launch by
+ * timing short solves of the batch itself (x in scratch memory, so the caller's x is untouched): the
+ * CTAs per system (4, 8 or 16: the rows each CTA owns), then, per class of rows per CTA (< 256,
+ * < 2048, more), the SpMV's threads per row (1, 2, 4 or 8); the choice is cached for the shape.
+ * per_sys (host, nsys entries, may be NULL) receives each system's statistics (time_ms: the whole
+ * batch; spmv_ms: the system's own time on the device, from its cluster's start to its end; gs_ms:
+ * when that cluster started, after the launch's first; ctas_per_system: the tuned cluster size).
+ * restart <= 40,
  * degree <= 31.  stream as in ppg_create.  Synchronises.  The library keeps one workspace per device
  * for batched calls (not thread-safe across host threads on one device).
  * Returns PPG_OK, PPG_ERR_NOT_CONVERGED if any system missed the tolerance, or an error. */

@@ -13,6 +13,7 @@ Each prints one JSON line.  Times are CUDA-event times on the solver's stream.
 from __future__ import annotations
 
 import json
+import os
 import statistics
 import time
 
@@ -110,6 +111,13 @@ def run_c3(args):
                       "unit": "ms", "results": res, "rel_error_f32_ir_vs_f64": err}))
 
 
+def _peaks():
+    try:
+        return json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
 def run_c4(args):
     import torch
 
@@ -144,6 +152,24 @@ def run_c4(args):
 
     seq_ms, _ = _time(seq, 1, 1)
     total_n = sum(a.n for a, _ in mats)
+    # algorithmic bytes of the batch (every matrix entry and vector once per pass): float64 construction
+    # (d+1 SpMVs and the three basis passes per step), float32 iterations (d+1 SpMVs, passes over k+1,
+    # k+2, k+2 and k+1 columns, the cycles' iterations taken as equal), float64 residuals, x updates
+    d, m = 15, 30
+    tot = 0.0
+    for (a, _), st in zip(mats, stats):
+        n, nnz = a.n, a.nnz
+        sp64 = nnz * 12 + 4 * (n + 1) + 2 * n * 8
+        sp32 = nnz * 8 + 4 * (n + 1) + 3 * n * 4
+        tot += (d + 1) * sp64 + sum((4 * (j + 1) + 5) * n * 8 for j in range(d + 1))
+        it, cyc = st["iterations"], max(st["restarts"], 1)
+        tot += it * (d + 1) * sp32
+        per = it / cyc
+        tot += cyc * sum((4 * (j + 1) + 5) * n * 4 for j in range(int(round(per))))
+        nres = st["spmvs"] - it * (d + 1) - (d + 1)
+        tot += max(nres, 0) * (nnz * 12 + 4 * (n + 1) + 3 * n * 8) + cyc * (per * n * 4 + 2 * n * 8)
+    pk = _peaks().get("hbm_gbs", 6800.0)
+    gbs = tot / (ms * 1e-3) / 1e9
     print(json.dumps({
         "workload": "c4: 256 x 2D upwind, sides log-uniform 32..448, Pe U[1,100], degree 15, GMRES(30), f32+f64 IR",
         "systems": len(systems), "total_rows": total_n, "total_nnz": sum(a.nnz for a, _ in mats),
@@ -151,7 +177,10 @@ def run_c4(args):
         "systems_per_s": round(len(systems) / (ms * 1e-3), 1), "status": status,
         "ctas_per_system": stats[0]["ctas_per_system"], "iterations_total": int(sum(iters)),
         "iterations_min_max": [int(min(iters)), int(max(iters))], "relres_max_host": max(rr),
-        "all_converged": bool(all(st["converged"] for st in stats)), "host_generation_s": round(gen_s, 2)}))
+        "all_converged": bool(all(st["converged"] for st in stats)), "host_generation_s": round(gen_s, 2),
+        "roofline": {"bound": "hbm", "kernel": "k_batch (one cluster per system)", "algorithmic_bytes": tot,
+                     "achieved": round(gbs, 1), "peak": pk, "unit": "GB/s", "frac": round(gbs / pk, 3),
+                     "note": "algorithmic bytes estimated from each system's iterations, cycles and SpMV count"}}))
     for sv in solvers:
         sv.close()
 

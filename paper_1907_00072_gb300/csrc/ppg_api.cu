@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <new>
 #include <stdlib.h>
@@ -1208,9 +1209,17 @@ struct BatchCache {
     int cap_sys = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
-    // autotuner
-    long long tune_key = -1;
-    int cluster = 0;
+    // autotuner: per batch shape (the sorted (n, nnz) list, degree and restart), the cluster size
+    // and the SpMV's threads per row of each size class
+    struct Tuned {
+        int cluster = 0;
+        int lanes[3] = {1, 1, 1};
+    };
+    std::map<std::vector<long long>, Tuned> tuned;
+    int cluster = 0;  // the current call's
+    BatchSys *tune_d = nullptr;  // descriptors of the tuning runs (x in scratch memory)
+    int *tune_order_d = nullptr;
+    int cap_tune = 0;
     // captured launch
     cudaGraphExec_t exec = nullptr;
     std::vector<long long> exec_key;
@@ -1232,6 +1241,16 @@ ppg_status batch_setup(BatchCache &bc, int nsys)
         PPG_CK(cudaEventCreate(&bc.t0));
         PPG_CK(cudaEventCreate(&bc.t1));
         bc.configured = true;
+    }
+    if (nsys > bc.cap_tune) {
+        cudaFree(bc.tune_d);
+        cudaFree(bc.tune_order_d);
+        bc.tune_d = nullptr;
+        bc.tune_order_d = nullptr;
+        bc.cap_tune = 0;
+        PPG_CK(cudaMalloc(&bc.tune_d, sizeof(BatchSys) * nsys));
+        PPG_CK(cudaMalloc(&bc.tune_order_d, sizeof(int) * nsys));
+        bc.cap_tune = nsys;
     }
     if (nsys > bc.cap_sys) {
         cudaFree(bc.sys_d);
@@ -1911,7 +1930,8 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
         const long long n = sys_h[i].n, nnz = sys_h[i].nnz;
         off[i] = total;
         total += align256(sizeof(float) * (nnz + 8)) + align256(sizeof(float) * n * (restart + 1)) +
-                 align256(sizeof(float) * n * 6) + align256(sizeof(double) * n * (degree + 2)) +
+                 align256(sizeof(float) * n * restart) + align256(sizeof(float) * n * 6) +
+                 align256(sizeof(double) * n * (degree + 2)) + align256(sizeof(double) * n) +
                  align256(sizeof(double) * n);
         total_nnz += nnz;
         total_n += n;
@@ -1924,6 +1944,7 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
         bc.ws_bytes = total;
     }
     std::vector<BatchSys> hs(nsys);
+    std::vector<double *> xscratch(nsys);
     for (int i = 0; i < nsys; ++i) {
         const ppg_batch_system &q = sys_h[i];
         BatchSys &d = hs[i];
@@ -1939,11 +1960,16 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
         p += align256(sizeof(float) * (q.nnz + 8));
         d.V = reinterpret_cast<float *>(p);
         p += align256(sizeof(float) * q.n * (restart + 1));
+        d.Z = reinterpret_cast<float *>(p);
+        p += align256(sizeof(float) * q.n * restart);
         d.fw = reinterpret_cast<float *>(p);
         p += align256(sizeof(float) * q.n * 6);
         d.V64 = reinterpret_cast<double *>(p);
         p += align256(sizeof(double) * q.n * (degree + 2));
         d.dw = reinterpret_cast<double *>(p);
+        p += align256(sizeof(double) * q.n);
+        xscratch[i] = reinterpret_cast<double *>(p);  // x of the tuning runs
+        d.lanes = 1;
     }
     // largest systems first: the hardware then fills idle SMs with the smaller ones
     std::vector<int> order(nsys);
@@ -1956,37 +1982,92 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
     PPG_CK(cudaMemcpyAsync(bc.order_d, order.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, bc.stream));
     PPG_CK(launch_batch_cast(bc.sys_d, nsys, bc.stream));
 
-    BatchParams prm{degree, restart, (long long)maxit, tol, 1e-6, (unsigned long long)seed};
+    // flexible float32 form with the restart projection (as ppg_solve's default), inner tolerance 1e-7
+    BatchParams prm{degree, restart, (long long)maxit, tol, 1e-7, (unsigned long long)seed, 1};
 
-    // autotuner: CTAs per system (the row tile of each CTA) is chosen by timing the polynomial
-    // construction of this very batch (maxit = 0 leaves x untouched) for each launchable size
-    const long long tune_key = total_nnz * 131 + nsys * 7 + degree;
-    if (bc.tune_key != tune_key || bc.cluster == 0) {
-        int best = 0;
-        float best_ms = 0.f;
-        const int cands[3] = {4, 8, 16};
-        for (int ci = 0; ci < 3; ++ci) {
-            const int cl = cands[ci];
-            if (batch_max_clusters(cl) < 1) continue;
-            BatchParams tp = prm;
-            tp.maxit = 0;
-            for (int rep = 0; rep < 2; ++rep) {  // the first run also warms caches
+    // autotuner, once per batch shape, on this very batch with x in scratch memory: the cluster size
+    // (CTAs per system, i.e. the rows of each CTA) by timing whole solves -- the launch ends with its
+    // slowest system, whose iterations a short run does not show -- then, per size class of rows per
+    // CTA, the SpMV's threads per row by timing short solves (construction and half a cycle)
+    std::vector<long long> shape;
+    {
+        std::vector<std::pair<long long, long long>> sh(nsys);
+        for (int i = 0; i < nsys; ++i) sh[i] = {sys_h[i].n, sys_h[i].nnz};
+        std::sort(sh.begin(), sh.end());
+        for (const auto &q : sh) {
+            shape.push_back(q.first);
+            shape.push_back(q.second);
+        }
+        shape.push_back(degree);
+        shape.push_back(restart);
+    }
+    auto cls_of = [](long long n, int cluster) {
+        const long long rpc = (n + cluster - 1) / cluster;
+        return rpc < kThreads ? 0 : (rpc < 8 * kThreads ? 1 : 2);
+    };
+    auto it_t = bc.tuned.find(shape);
+    if (it_t == bc.tuned.end()) {
+        BatchCache::Tuned tb;
+        std::vector<BatchSys> ht = hs;
+        for (int i = 0; i < nsys; ++i) ht[i].x = xscratch[i];
+        BatchParams tp = prm;
+        const long long short_maxit = std::max(1, std::min(maxit, std::max(1, restart / 2)));
+        // one timed solve of the systems listed in ord (x reset to the caller's x0 first)
+        auto timed = [&](const std::vector<int> &ord, int cluster, int reps, float *ms) -> ppg_status {
+            PPG_CK(cudaMemcpyAsync(bc.tune_d, ht.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice, bc.stream));
+            PPG_CK(cudaMemcpyAsync(bc.tune_order_d, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice,
+                                   bc.stream));
+            float best = 0.f;
+            for (int rep = 0; rep < reps; ++rep) {  // short runs: the first one also warms caches
+                for (int i : ord)
+                    PPG_CK(cudaMemcpyAsync(xscratch[i], sys_h[i].x, sizeof(double) * sys_h[i].n,
+                                           cudaMemcpyDeviceToDevice, bc.stream));
                 PPG_CK(cudaEventRecord(bc.t0, bc.stream));
-                PPG_CK(launch_batch(bc.sys_d, bc.order_d, nsys, cl, tp, bc.out_d, bc.stream));
+                PPG_CK(launch_batch(bc.tune_d, bc.tune_order_d, (int)ord.size(), cluster, tp, bc.out_d, bc.stream));
                 PPG_CK(cudaEventRecord(bc.t1, bc.stream));
+                PPG_CK(cudaEventSynchronize(bc.t1));
+                PPG_CK(cudaEventElapsedTime(&best, bc.t0, bc.t1));
             }
-            PPG_CK(cudaEventSynchronize(bc.t1));
+            *ms = best;
+            return PPG_OK;
+        };
+        float best_ms = 0.f;
+        tp.maxit = maxit;
+        for (int cl : {4, 8, 16}) {
+            if (batch_max_clusters(cl) < 1) continue;
+            for (int i = 0; i < nsys; ++i) ht[i].lanes = cls_of(sys_h[i].n, cl) == 0 ? 2 : 1;
             float ms = 0.f;
-            PPG_CK(cudaEventElapsedTime(&ms, bc.t0, bc.t1));
-            if (!best || ms < best_ms) {
-                best = cl;
+            PPG_TRY(timed(order, cl, 1, &ms));
+            if (!tb.cluster || ms < best_ms) {
+                tb.cluster = cl;
                 best_ms = ms;
             }
         }
-        if (!best) return fail(PPG_ERR_CUDA, "no cluster size is launchable for the batched solver");
-        bc.cluster = best;
-        bc.tune_key = tune_key;
+        if (!tb.cluster) return fail(PPG_ERR_CUDA, "no cluster size is launchable for the batched solver");
+        tp.maxit = short_maxit;
+        for (int c = 0; c < 3; ++c) {
+            std::vector<int> sub;
+            for (int i : order)
+                if (cls_of(sys_h[i].n, tb.cluster) == c) sub.push_back(i);
+            if (sub.empty()) continue;
+            float cbest = 0.f;
+            for (int lanes : {1, 2, 4, 8}) {
+                if (c == 2 && lanes > 2) continue;  // long row blocks: one or two threads per row
+                for (int i : sub) ht[i].lanes = lanes;
+                float ms = 0.f;
+                PPG_TRY(timed(sub, tb.cluster, 2, &ms));
+                if (lanes == 1 || ms < cbest) {
+                    tb.lanes[c] = lanes;
+                    cbest = ms;
+                }
+            }
+        }
+        it_t = bc.tuned.emplace(shape, tb).first;
     }
+    const BatchCache::Tuned &tb = it_t->second;
+    bc.cluster = tb.cluster;
+    for (int i = 0; i < nsys; ++i) hs[i].lanes = tb.lanes[cls_of(sys_h[i].n, tb.cluster)];
+    PPG_CK(cudaMemcpyAsync(bc.sys_d, hs.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice, bc.stream));
 
     // the solve itself: one launch, captured once as a graph and replayed
     std::vector<long long> key = {(long long)(uintptr_t)bc.sys_d, nsys, bc.cluster, degree, restart, maxit,
@@ -2022,6 +2103,8 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
     float ms = 0.f;
     cudaEventElapsedTime(&ms, bc.t0, bc.t1);
     ppg_status worst = PPG_OK;
+    long long t_first = ho.empty() ? 0 : ho[0].t_start;
+    for (const BatchOut &o : ho) t_first = std::min(t_first, o.t_start);
     for (int i = 0; i < nsys; ++i) {
         const BatchOut &o = ho[i];
         if (per_sys) {
@@ -2039,6 +2122,8 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
             st.breakdowns = o.breakdowns;
             st.ctas_per_system = bc.cluster;
             st.time_ms = ms;
+            st.spmv_ms = (double)(o.t_end - o.t_start) * 1e-6;  // this system's own time on the device
+            st.gs_ms = (double)(o.t_start - t_first) * 1e-6;     // when its cluster started in the launch
         }
         if (o.status == 2 && worst >= 0) worst = fail(PPG_ERR_NONFINITE, "system %d: non-finite value", i);
         if (o.status == 3 && worst >= 0) worst = fail(PPG_ERR_POLY_BREAKDOWN, "system %d: no usable polynomial", i);

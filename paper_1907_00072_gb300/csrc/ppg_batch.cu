@@ -122,37 +122,95 @@ __device__ void cta_update(const T *coef, const T *V, long long ld, int k, const
 {
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
         T acc = w ? w[r] : T(0);
+#pragma unroll 8
         for (int c = 0; c < k; ++c) acc = fma(-coef[c], V[(long long)c * ld + r], acc);
         out[r] = acc;
     }
 }
 
 // One fused SpMV step on this CTA's rows: with Ax = (A (x + s2 x2))[r],
-//   o0[r] = a0 Ax + b0 u0[r] + c0 w0[r];   o1[r] = a1 Ax + b1 u1[r]  (null terms dropped)
-template <typename T, typename TV>
-__device__ void cta_spmv(const int *rowptr, const int *colidx, const TV *vals, int r0, int r1, const T *x, const T *x2,
-                         T s2, T *o0, T a0, const T *u0, T b0, const T *w0, T c0, T *o1, T a1, const T *u1, T b1)
+//   o0[r] = a0 Ax + b0 u0[r] + c0 w0[r];   o1[r] = a1 Ax + b1 u1[r] + c1 w1[r]  (null terms dropped)
+// G threads per row: lane g of a row's group takes entries g, g + G, ... and the group sums by a
+// shuffle tree (rows of a few entries: G = 1; G > 1 keeps all threads busy on systems with fewer
+// rows per CTA than threads).  The loop's trip count is the same for every thread of the CTA.
+template <int G, typename T, typename TV>
+__device__ void cta_spmv_g(const int *rowptr, const int *colidx, const TV *vals, int r0, int r1, const T *x,
+                           const T *x2, T s2, T *o0, T a0, const T *u0, T b0, const T *w0, T c0, T *o1, T a1,
+                           const T *u1, T b1, const T *w1, T c1)
 {
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        T acc = T(0);
-        const int k1 = rowptr[r + 1];
-        if (x2) {
-            for (int k = rowptr[r]; k < k1; ++k) {
-                const int q = colidx[k];
-                acc = fma((T)vals[k], fma(s2, x2[q], x[q]), acc);
+    // each group takes U rows per sweep and walks their entries together, so that U independent
+    // index/value loads and U gathers are in flight per step (the rows are short: latency, not
+    // arithmetic, is what a small CTA group waits on)
+    constexpr int U = 4;
+    const int per = blockDim.x / G, grp = threadIdx.x / G, g = threadIdx.x % G;
+    for (int base = r0; base < r1; base += per * U) {
+        int ks[U], ke[U];
+        T acc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int r = base + grp + u * per;
+            ks[u] = r < r1 ? rowptr[r] + g : 0;
+            ke[u] = r < r1 ? rowptr[r + 1] : 0;
+            acc[u] = T(0);
+        }
+        for (int t = 0;; t += G) {
+            bool any = false;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = ks[u] + t;
+                if (k < ke[u]) {
+                    const int q = colidx[k];
+                    const T xv = x2 ? fma(s2, x2[q], x[q]) : x[q];
+                    acc[u] = fma((T)vals[k], xv, acc[u]);
+                    any = true;
+                }
             }
-        } else {
-            for (int k = rowptr[r]; k < k1; ++k) acc = fma((T)vals[k], x[colidx[k]], acc);
+            if (!any) break;
         }
-        T v = a0 * acc;
-        if (u0) v = fma(b0, u0[r], v);
-        if (w0) v = fma(c0, w0[r], v);
-        o0[r] = v;
-        if (o1) {
-            T v1 = a1 * acc;
-            if (u1) v1 = fma(b1, u1[r], v1);
-            o1[r] = v1;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int o = G >> 1; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int r = base + grp + u * per;
+            if (r < r1 && g == 0) {
+                T v = a0 * acc[u];
+                if (u0) v = fma(b0, u0[r], v);
+                if (w0) v = fma(c0, w0[r], v);
+                o0[r] = v;
+                if (o1) {
+                    T v1 = a1 * acc[u];
+                    if (u1) v1 = fma(b1, u1[r], v1);
+                    if (w1) v1 = fma(c1, w1[r], v1);
+                    o1[r] = v1;
+                }
+            }
+        }
+    }
+    // rows are written by other threads than the ones the row-strided loops that follow (dots,
+    // updates) give them to
+    __syncthreads();
+}
+
+template <typename T, typename TV>
+__device__ void cta_spmv(int G, const int *rowptr, const int *colidx, const TV *vals, int r0, int r1, const T *x,
+                         const T *x2, T s2, T *o0, T a0, const T *u0, T b0, const T *w0, T c0, T *o1, T a1,
+                         const T *u1, T b1, const T *w1 = nullptr, T c1 = T(0))
+{
+    switch (G) {
+    case 2:
+        cta_spmv_g<2>(rowptr, colidx, vals, r0, r1, x, x2, s2, o0, a0, u0, b0, w0, c0, o1, a1, u1, b1, w1, c1);
+        break;
+    case 4:
+        cta_spmv_g<4>(rowptr, colidx, vals, r0, r1, x, x2, s2, o0, a0, u0, b0, w0, c0, o1, a1, u1, b1, w1, c1);
+        break;
+    case 8:
+        cta_spmv_g<8>(rowptr, colidx, vals, r0, r1, x, x2, s2, o0, a0, u0, b0, w0, c0, o1, a1, u1, b1, w1, c1);
+        break;
+    default:
+        cta_spmv_g<1>(rowptr, colidx, vals, r0, r1, x, x2, s2, o0, a0, u0, b0, w0, c0, o1, a1, u1, b1, w1, c1);
     }
 }
 
@@ -185,7 +243,7 @@ __device__ int cluster_poly(cg::cluster_group &cl, const BShared &s, const Batch
                 }
             } else {
                 float *Pn = pp ? P1 : P0;
-                cta_spmv<float, float>(S.rowptr, S.colidx, S.vals32, r0, r1, P, nullptr, 0.f, dst, 0.f, P, t * sP,
+                cta_spmv<float, float>(S.lanes, S.rowptr, S.colidx, S.vals32, r0, r1, P, nullptr, 0.f, dst, 0.f, P, t * sP,
                                        first ? nullptr : dst, 1.f, Pn, -t * sP, P, sP);
                 csync(cl);
                 ++spmvs;
@@ -197,13 +255,13 @@ __device__ int cluster_poly(cg::cluster_group &cl, const BShared &s, const Batch
         } else {
             const float c2a = (float)s.table[2 * i], cq = (float)s.table[2 * i + 1];
             const bool last = (i + 2 >= k);
-            cta_spmv<float, float>(S.rowptr, S.colidx, S.vals32, r0, r1, P, nullptr, 0.f, dst, -cq * sP, P, c2a * sP,
+            cta_spmv<float, float>(S.lanes, S.rowptr, S.colidx, S.vals32, r0, r1, P, nullptr, 0.f, dst, -cq * sP, P, c2a * sP,
                                    first ? nullptr : dst, 1.f, Tv, sP, nullptr, 0.f);
             csync(cl);
             ++spmvs;
             if (!last) {
                 float *Pn = pp ? P1 : P0;
-                cta_spmv<float, float>(S.rowptr, S.colidx, S.vals32, r0, r1, Tv, nullptr, 0.f, Pn, cq, Tv, -c2a, P,
+                cta_spmv<float, float>(S.lanes, S.rowptr, S.colidx, S.vals32, r0, r1, Tv, nullptr, 0.f, Pn, cq, Tv, -c2a, P,
                                        sP, nullptr, 0.f, nullptr, 0.f);
                 csync(cl);
                 ++spmvs;
@@ -219,6 +277,96 @@ __device__ int cluster_poly(cg::cluster_group &cl, const BShared &s, const Batch
     return spmvs;
 }
 
+// r = b - A x in float64 on this CTA's rows (rows as the rest of the kernel strides them)
+__device__ void cta_residual(const BatchSys &S, double *r_out, int r0, int r1)
+{
+    cta_spmv<double, double>(S.lanes, S.rowptr, S.colidx, S.vals64, r0, r1, S.x, nullptr, 0.0, r_out, -1.0, S.b, 1.0,
+                             nullptr, 0.0, nullptr, 0.0, nullptr, 0.0);
+}
+
+// ||r|| over the cluster and the tests of a true residual (Section III): converged, iteration limit,
+// non-finite.  Leaves beta, relres, done, status in s.
+__device__ void batch_residual_norm(cg::cluster_group &cl, BShared &s, int &buf, const double *r, int r0, int r1,
+                                    const BatchParams &p)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double a = 0.0;
+    for (int q = r0 + tid; q < r1; q += blockDim.x) a = fma(r[q], r[q], a);
+    a = warp_sum(a);
+    if (lane == 0) s.scratch[wid] = a;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += s.scratch[q];
+        s.part[buf][0] = t;
+    }
+    __syncthreads();
+    cluster_reduce(cl, s, 1, buf);
+    if (tid == 0) {
+        s.beta = sqrt(s.red[0]);
+        s.relres = s.bnorm > 0.0 ? s.beta / s.bnorm : 0.0;
+        s.spmvs += 1;
+        s.done = 0;
+        if (!isfinite(s.beta)) s.status = 2;
+        else if (s.relres <= p.tol || s.bnorm == 0.0) s.done = 1;
+        else if (s.iters >= p.maxit) s.done = 2;
+    }
+    __syncthreads();
+}
+
+// s.part[buf][c] = this CTA's rows of V_c . r (c < k), float32 V and float64 r, summed in float64
+__device__ void cta_dots_mixed(BShared &s, int buf, const float *V, long long ld, int k, const double *r, int r0,
+                               int r1)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int c0 = 0; c0 < k; c0 += kBChunk) {
+        const int cn = min(kBChunk, k - c0);
+        double acc[kBChunk];
+#pragma unroll
+        for (int q = 0; q < kBChunk; ++q) acc[q] = 0.0;
+        for (int q0 = r0 + tid; q0 < r1; q0 += blockDim.x) {
+            const double vr = r[q0];
+#pragma unroll
+            for (int q = 0; q < kBChunk; ++q)
+                if (q < cn) acc[q] = fma((double)V[(long long)(c0 + q) * ld + q0], vr, acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < kBChunk; ++q) {
+            if (q < cn) {
+                const double t = warp_sum(acc[q]);
+                if (lane == 0) s.scratch[q * 8 + wid] = t;
+            }
+        }
+        __syncthreads();
+        if (tid < cn) {
+            double t = 0.0;
+            for (int q = 0; q < 8; ++q) t += s.scratch[tid * 8 + q];
+            s.part[buf][c0 + tid] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// y = R^{-1} g (k columns of the cycle's rotated Hessenberg matrix), by one thread
+__device__ void back_substitute(BShared &s, int k)
+{
+    for (int i = k - 1; i >= 0; --i) {
+        double v = s.g[i];
+        for (int q = i + 1; q < k; ++q) v -= s.u.R[i + q * (kBMaxM + 1)] * s.y[q];
+        s.y[i] = v / s.u.R[i + i * (kBMaxM + 1)];
+    }
+}
+
+// x += sum_{c<k} y_c Z_c on this CTA's rows (float32 Z, float64 x and y, float64 sums)
+__device__ void cta_xupdate_z(const float *Z, long long ld, int k, const double *y, double *x, int r0, int r1)
+{
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < k; ++c) acc = fma((double)Z[(long long)c * ld + r], y[c], acc);
+        x[r] += acc;
+    }
+}
+
 __device__ __forceinline__ unsigned long long bmix(unsigned long long z)
 {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -226,7 +374,7 @@ __device__ __forceinline__ unsigned long long bmix(unsigned long long z)
     return z ^ (z >> 31);
 }
 
-__global__ void __launch_bounds__(kThreads) k_batch(const BatchSys *__restrict__ sys, const int *__restrict__ order,
+__global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchSys *__restrict__ sys, const int *__restrict__ order,
                                                     BatchParams p, BatchOut *out)
 {
     __shared__ BShared s;
@@ -239,6 +387,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(const BatchSys *__restrict__
     const int r0 = min(n, rank * chunk), r1 = min(n, r0 + chunk);
     const int tid = threadIdx.x;
     int buf = 0;
+    const long long t_start = (long long)global_timer_ns();
     if (tid == 0) {
         s.status = 0;
         s.iters = s.cycles = s.spmvs = s.breakdowns = 0;
@@ -267,7 +416,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(const BatchSys *__restrict__
         const int steps = p.degree + 1;
         int done = 0;
         for (int j = 0; j < steps; ++j) {
-            cta_spmv<double, double>(S.rowptr, S.colidx, S.vals64, r0, r1, V64 + j * ld, nullptr, 0.0, w64,
+            cta_spmv<double, double>(S.lanes, S.rowptr, S.colidx, S.vals64, r0, r1, V64 + j * ld, nullptr, 0.0, w64,
                                      s.sigma[j], nullptr, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0);
             cta_dots<double>(s, buf, V64, ld, j + 1, w64, r0, r1, true);
             cluster_reduce(cl, s, j + 2, buf);
@@ -358,43 +507,56 @@ __global__ void __launch_bounds__(kThreads) k_batch(const BatchSys *__restrict__
             for (int r = r0 + tid; r < r1; r += blockDim.x) S.x[r] = 0.0;
     }
     const int m = p.m;
+    int kprev = 0;  // columns of the previous cycle (flexible form: the restart projection uses them)
     while (s.status == 0) {
-        // true residual r = b - A x in float64, stored as float32 basis column 0
+        // true residual r = b - A x in float64
         csync(cl);  // x complete
-        for (int r = r0 + tid; r < r1; r += blockDim.x) {
-            double acc = 0.0;
-            for (int k = S.rowptr[r]; k < S.rowptr[r + 1]; ++k) acc = fma(S.vals64[k], S.x[S.colidx[k]], acc);
-            const double v = S.b[r] - acc;
-            V[r] = (float)v;
-            w64[r] = v;
-        }
-        cta_dots<double>(s, buf, w64, ld, 0, w64, r0, r1, true);
-        cluster_reduce(cl, s, 1, buf);
-        if (tid == 0) {
-            s.beta = sqrt(s.red[0]);
-            s.relres = s.bnorm > 0.0 ? s.beta / s.bnorm : 0.0;
-            s.spmvs += 1;
-            s.done = 0;
-            if (!isfinite(s.beta)) s.status = 2;
-            else if (s.relres <= p.tol || s.bnorm == 0.0) s.done = 1;
-            else if (s.iters >= p.maxit) s.done = 2;
-            if (!s.status && !s.done) {
-                s.cycles += 1;
-                s.sigma[0] = 1.0 / s.beta;
-                for (int q = 0; q <= m; ++q) s.g[q] = 0.0;
-                s.g[0] = s.beta;
-            }
-        }
-        __syncthreads();
+        cta_residual(S, w64, r0, r1);
+        batch_residual_norm(cl, s, buf, w64, r0, r1, p);
         if (s.status || s.done) break;
+        if (p.flexible && kprev > 0) {
+            // restart projection: y = argmin ||H y - V^T r|| over the previous cycle's space (its
+            // rotations and R are still in shared memory), x += Z y, and the residual again
+            cta_dots_mixed(s, buf, V, ld, kprev + 1, w64, r0, r1);
+            cluster_reduce(cl, s, kprev + 1, buf);
+            if (tid == 0) {
+                double a = s.sigma[0] * s.red[0];
+                for (int i = 0; i < kprev; ++i) {
+                    const double bb = s.sigma[i + 1] * s.red[i + 1];
+                    s.g[i] = s.cs[i] * a + s.sn[i] * bb;
+                    a = -s.sn[i] * a + s.cs[i] * bb;
+                }
+                back_substitute(s, kprev);
+            }
+            __syncthreads();
+            cta_xupdate_z(S.Z, ld, kprev, s.y, S.x, r0, r1);
+            csync(cl);  // x complete
+            cta_residual(S, w64, r0, r1);
+            batch_residual_norm(cl, s, buf, w64, r0, r1, p);
+            if (s.status || s.done) break;
+        }
+        // start the cycle from r: basis column 0
+        for (int r = r0 + tid; r < r1; r += blockDim.x) V[r] = (float)w64[r];
+        if (tid == 0) {
+            s.cycles += 1;
+            s.sigma[0] = 1.0 / s.beta;
+            for (int q = 0; q <= m; ++q) s.g[q] = 0.0;
+            s.g[0] = s.beta;
+        }
+        csync(cl);  // column 0 is gathered next
         int kc = 0;
         for (int j = 0; j < m; ++j) {
-            // w = A p(A) v_j  (v_j = sigma_j U_j)
+            // w = A p(A) v_j  (v_j = sigma_j U_j); flexible form: the SpMV also writes z_j = p(A) v_j,
+            // the value its own gather forms, to Z_j
             const float *dP = nullptr;
             float dt = 0.f;
             int sp = cluster_poly(cl, s, S, r0, r1, V + j * ld, (float)s.sigma[j], Y, P0, P1, Tv, true, &dP, &dt);
-            cta_spmv<float, float>(S.rowptr, S.colidx, S.vals32, r0, r1, Y, dP, dt, w, 1.f, nullptr, 0.f, nullptr,
-                                   0.f, nullptr, 0.f, nullptr, 0.f);
+            if (p.flexible)
+                cta_spmv<float, float>(S.lanes, S.rowptr, S.colidx, S.vals32, r0, r1, Y, dP, dt, w, 1.f, nullptr, 0.f,
+                                       nullptr, 0.f, S.Z + j * ld, 0.f, Y, 1.f, dP, dt);
+            else
+                cta_spmv<float, float>(S.lanes, S.rowptr, S.colidx, S.vals32, r0, r1, Y, dP, dt, w, 1.f, nullptr, 0.f,
+                                       nullptr, 0.f, nullptr, 0.f, nullptr, 0.f);
             // pass 1
             cta_dots<float>(s, buf, V, ld, j + 1, w, r0, r1, true);
             cluster_reduce(cl, s, j + 2, buf);
@@ -468,24 +630,25 @@ __global__ void __launch_bounds__(kThreads) k_batch(const BatchSys *__restrict__
             if (s.done) break;
         }
         if (s.status) break;
-        // cycle end: y = R^{-1} g, z = V y, x += p(A) z
+        // cycle end: y = R^{-1} g; flexible: x += Z y; standard: z = V y, x += p(A) z
         if (tid == 0) {
-            for (int i = kc - 1; i >= 0; --i) {
-                double v = s.g[i];
-                for (int q = i + 1; q < kc; ++q) v -= s.u.R[i + q * (kBMaxM + 1)] * s.y[q];
-                s.y[i] = v / s.u.R[i + i * (kBMaxM + 1)];
-            }
+            back_substitute(s, kc);
             for (int c = 0; c < kc; ++c) {
                 s.coef[c] = -s.y[c] * s.sigma[c];
                 s.fcoef[c] = (float)s.coef[c];
             }
         }
         __syncthreads();
-        cta_update<float>(s.fcoef, V, ld, kc, nullptr, z, r0, r1);
-        csync(cl);
-        const int sp = cluster_poly(cl, s, S, r0, r1, z, 1.f, Y, P0, P1, Tv, false, nullptr, nullptr);
-        for (int r = r0 + tid; r < r1; r += blockDim.x) S.x[r] += (double)Y[r];
-        if (tid == 0) s.spmvs += sp;
+        if (p.flexible) {
+            cta_xupdate_z(S.Z, ld, kc, s.y, S.x, r0, r1);
+        } else {
+            cta_update<float>(s.fcoef, V, ld, kc, nullptr, z, r0, r1);
+            csync(cl);
+            const int sp = cluster_poly(cl, s, S, r0, r1, z, 1.f, Y, P0, P1, Tv, false, nullptr, nullptr);
+            for (int r = r0 + tid; r < r1; r += blockDim.x) S.x[r] += (double)Y[r];
+            if (tid == 0) s.spmvs += sp;
+        }
+        kprev = kc;
         __syncthreads();
     }
     if (rank == 0 && tid == 0) {
@@ -499,6 +662,8 @@ __global__ void __launch_bounds__(kThreads) k_batch(const BatchSys *__restrict__
         o.degree = s.nroots - 1;
         o.converged = (s.status == 0 && s.done == 1) ? 1 : 0;
         o.breakdowns = (int)s.breakdowns;
+        o.t_start = t_start;
+        o.t_end = (long long)global_timer_ns();
         out[si] = o;
     }
     // keep this CTA's shared memory alive until every CTA of the cluster is done reading it

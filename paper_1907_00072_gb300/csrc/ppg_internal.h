@@ -246,18 +246,22 @@ struct BatchSys {
     const double *b;
     double *x;
     float *V;     // (restart + 1) columns of n entries
+    float *Z;     // restart columns of n entries: z_j = p(A) v_j of the flexible form
     float *fw;    // 6 vectors of n entries
     double *V64;  // (degree + 2) columns of n entries
     double *dw;   // 1 vector of n entries
+    int lanes;    // threads per row of the system's SpMVs (1, 2, 4 or 8; chosen by the autotuner)
 };
 struct BatchParams {
     int degree, m;
     long long maxit;
     double tol, inner_rtol;
     unsigned long long seed;
+    int flexible;  // 1: flexible float32 form with the restart projection (as ppg_solve's default)
 };
 struct BatchOut {
     long long iters, cycles, spmvs;
+    long long t_start, t_end;  // the system's cluster: global timer (ns) at its start and end
     double relres, est;
     int status, degree, converged, breakdowns;
 };

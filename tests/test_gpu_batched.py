@@ -2,7 +2,7 @@
 
 Each system of the batch builds its polynomial from the SplitMix64 stream seed + i; the single
 solve is given the same stream, so both build the same minimum-residual polynomial and run the
-same float32 PP-GMRES with float64 refinement.  Solutions must agree to 1e-6 relative, both must
+same float32 PP-GMRES with float64 refinement (flexible form with the restart projection).  Solutions must agree to 1e-6 relative, both must
 reach a true relative residual of 1e-8 (checked on the host with the oracle's SpMV), and their
 iteration counts must agree within 5%.
 """
@@ -53,13 +53,62 @@ def test_batched_matches_single_solves(degree, restart):
         assert _relres(a, b, xb) <= 1e-8
         s = ppg.Solver(sysi[0], sysi[1], sysi[2])
         s.build_poly(degree, ppg.PPG_BASIS_ROOTS, v0=None, seed=seed + i)
-        xs, info = s.solve(sysi[3], tol=1e-8, restart=restart, maxit=20000, precision=ppg.PPG_F32,
-                           f32_form=ppg.PPG_F32_STANDARD)  # the form the batched kernel runs
+        xs, info = s.solve(sysi[3], tol=1e-8, restart=restart, maxit=20000, precision=ppg.PPG_F32)
         xs = xs.cpu().numpy()
         assert info.status == ppg.PPG_OK and _relres(a, b, xs) <= 1e-8
         assert np.linalg.norm(xb - xs) <= 1e-6 * np.linalg.norm(xs)
         assert abs(st["iterations"] - info.stats["iterations"]) <= max(2, 0.05 * info.stats["iterations"])
         s.close()
+
+
+def test_batched_at_the_configuration_extremes():
+    """Grid sides 32 and 448 (n = 1,024 and 200,704) with Peclet 1 and 100, degree 15, GMRES(30), in one
+    launch with a few systems between: every system converges to 1e-8 and matches its single solve
+    (solution within 1e-6, iterations within max(2, 5%)); the smallest is checked against the oracle."""
+    specs = [(448, 100.0), (448, 1.0), (200, 50.0), (90, 20.0), (32, 100.0), (32, 1.0)]
+    mats, systems = _batch(specs)
+    seed = 21
+    status, stats = ppg.ppg_solve_batched(systems, degree=15, tol=1e-8, restart=30, maxit=20000, seed=seed)
+    assert status == ppg.PPG_OK
+    assert stats[0]["ctas_per_system"] in (4, 8, 16)
+    for i, ((a, b), sysi, st) in enumerate(zip(mats, systems, stats)):
+        xb = sysi[4].cpu().numpy()
+        assert st["converged"] == 1 and st["degree_used"] == 15
+        assert _relres(a, b, xb) <= 1e-8
+        s = ppg.Solver(sysi[0], sysi[1], sysi[2])
+        s.build_poly(15, ppg.PPG_BASIS_ROOTS, v0=None, seed=seed + i)
+        xs, info = s.solve(sysi[3], tol=1e-8, restart=30, maxit=20000, precision=ppg.PPG_F32)
+        xs = xs.cpu().numpy()
+        assert info.status == ppg.PPG_OK
+        assert np.linalg.norm(xb - xs) <= 1e-6 * np.linalg.norm(xs), i
+        assert abs(st["iterations"] - info.stats["iterations"]) <= max(2, 0.05 * info.stats["iterations"]), i
+        s.close()
+    a, b = mats[-1]
+    ref = oracle.gmres(a, b, oracle.poly_gmres(a, w.uniform(seed + len(specs) - 1, a.n), 15), tol=1e-8, m=30,
+                       maxit=20000)
+    xb = systems[-1][4].cpu().numpy()
+    assert ref.converged
+    assert np.linalg.norm(xb - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
+    assert abs(stats[-1]["iterations"] - ref.iters) <= max(2, 0.05 * ref.iters)
+
+
+def test_batched_tuning_keeps_the_callers_x_and_is_cached():
+    """The autotuner's trial solves run on scratch copies of x: a second call with the same shape starts
+    from the caller's x0 again and gives the same result bit for bit (the choice is cached)."""
+    specs = [(64, 10.0), (40, 60.0), (33, 90.0)]
+    mats, systems = _batch(specs)
+    x0 = [torch.full_like(sy[4], 0.25) for sy in systems]
+    for sy, x in zip(systems, x0):
+        sy[4].copy_(x)
+    st1, s1 = ppg.ppg_solve_batched(systems, degree=8, tol=1e-9, restart=20, seed=5)
+    r1 = [sy[4].clone() for sy in systems]
+    for sy, x in zip(systems, x0):
+        sy[4].copy_(x)
+    st2, s2 = ppg.ppg_solve_batched(systems, degree=8, tol=1e-9, restart=20, seed=5)
+    assert st1 == st2 == ppg.PPG_OK
+    for a, b in zip(r1, systems):
+        assert torch.equal(a, b[4])
+    assert [q["iterations"] for q in s1] == [q["iterations"] for q in s2]
 
 
 def test_batched_matches_oracle_on_a_small_system():
