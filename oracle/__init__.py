@@ -63,6 +63,19 @@ def _load():
         _lib.orc_poly_arnoldi_to_power.argtypes = [ci, p, p, d, p]
         _lib.orc_gmres.argtypes = [i64, p, p, p, ci, ci, p, p, p, d, p, p, d, ci, ci, p, p, ci]
         _lib.orc_gmres.restype = ci
+        # the same routines with ILU(0) factors on the left (Section VI); lu = NULL is the plain method
+        _lib.orc_ilu0.argtypes = [i64, p, p, p, p]
+        _lib.orc_ilu0.restype = ci
+        _lib.orc_ilu0_apply.argtypes = [i64, p, p, p, p, p]
+        _lib.orc_poly_apply_lu.argtypes = [i64, p, p, p, p, ci, ci, p, p, p, d, p, p]
+        _lib.orc_poly_normal_eq_lu.argtypes = [i64, p, p, p, p, p, ci, p, p, p, p]
+        _lib.orc_poly_normal_eq_lu.restype = ci
+        _lib.orc_arnoldi_lu.argtypes = [i64, p, p, p, p, ci, ci, p, p, p, d, p, ci, p, p, p]
+        _lib.orc_arnoldi_lu.restype = ci
+        _lib.orc_poly_gmres_lu.argtypes = [i64, p, p, p, p, p, ci, p, p, p, p]
+        _lib.orc_poly_gmres_lu.restype = ci
+        _lib.orc_gmres_lu.argtypes = [i64, p, p, p, p, ci, ci, p, p, p, d, p, p, d, ci, ci, p, p, ci]
+        _lib.orc_gmres_lu.restype = ci
     return _lib
 
 
@@ -131,6 +144,34 @@ def spmv_rows(a, x, rows):
     return y
 
 
+def _lu(lu):
+    return None if lu is None else _f64(lu)
+
+
+def ilu0(a):
+    """ILU(0) factors of a (columns sorted within rows, diagonal present): one array on a's pattern
+    with the unit lower factor L below the diagonal and U on and above it (Section VI's M = L U)."""
+    lib = _load()
+    n, rp, ci, va = _csr(a)
+    lu = np.empty(len(va))
+    st = lib.orc_ilu0(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(lu))
+    if st == -2:
+        raise MemoryError("oracle allocation failed")
+    if st < 0:
+        raise ValueError(f"ILU(0) breaks down at row {-st - 1} (no diagonal or a zero pivot)")
+    return lu
+
+
+def ilu0_apply(a, lu, x):
+    """(L U)^{-1} x for the factors of ilu0."""
+    lib = _load()
+    n, rp, ci, _ = _csr(a)
+    lu, x = _f64(lu), _f64(x)
+    y = np.empty(n)
+    lib.orc_ilu0_apply(n, _ptr(rp), _ptr(ci), _ptr(lu), _ptr(x), _ptr(y))
+    return y
+
+
 def transpose(a):
     import workloads
 
@@ -153,8 +194,9 @@ def cholesky(G):
     return np.tril(a), info
 
 
-def poly_normal_eq(a, v0, deg):
-    """The paper's construction (Eq. 1 + Cholesky); degree clamped per Section IV."""
+def poly_normal_eq(a, v0, deg, lu=None):
+    """The paper's construction (Eq. 1 + Cholesky); degree clamped per Section IV.  With lu (ILU(0)
+    factors, see ilu0) the polynomial is that of M^{-1} A."""
     lib = _load()
     n, rp, ci, va = _csr(a)
     v0 = _f64(v0)
@@ -162,8 +204,8 @@ def poly_normal_eq(a, v0, deg):
     info = ctypes.c_int(0)
     gram = np.zeros((deg + 1) * (deg + 1))
     rhs = np.zeros(deg + 1)
-    used = lib.orc_poly_normal_eq(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(v0), deg, _ptr(coef), ctypes.byref(info),
-                                  _ptr(gram), _ptr(rhs))
+    used = lib.orc_poly_normal_eq_lu(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(_lu(lu)), _ptr(v0), deg, _ptr(coef),
+                                     ctypes.byref(info), _ptr(gram), _ptr(rhs))
     if used == -2:
         raise MemoryError("oracle allocation failed")
     p = Poly(POLY_POWER, max(used, 0), coef[: max(used, 0) + 1].copy(), info=info.value)
@@ -173,8 +215,8 @@ def poly_normal_eq(a, v0, deg):
     return p
 
 
-def poly_gmres(a, v0, deg):
-    """Minimum-residual polynomial from deg+1 MGS Arnoldi steps (Arnoldi form)."""
+def poly_gmres(a, v0, deg, lu=None):
+    """Minimum-residual polynomial from deg+1 MGS Arnoldi steps (Arnoldi form); with lu, of M^{-1} A."""
     lib = _load()
     n, rp, ci, va = _csr(a)
     v0 = _f64(v0)
@@ -182,8 +224,8 @@ def poly_gmres(a, v0, deg):
     y = np.zeros(deg + 1)
     beta = ctypes.c_double(0)
     resid = ctypes.c_double(0)
-    built = lib.orc_poly_gmres(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(v0), deg, _ptr(H), _ptr(y),
-                               ctypes.byref(beta), ctypes.byref(resid))
+    built = lib.orc_poly_gmres_lu(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(_lu(lu)), _ptr(v0), deg, _ptr(H), _ptr(y),
+                                  ctypes.byref(beta), ctypes.byref(resid))
     if built == -2:
         raise MemoryError("oracle allocation failed")
     if built < deg:  # breakdown: keep the exact lower-degree polynomial
@@ -199,13 +241,15 @@ def arnoldi_to_power(p: Poly) -> np.ndarray:
     return coef
 
 
-def poly_apply(a, p: Poly, x):
+def poly_apply(a, p: Poly, x, lu=None):
+    """p(A) x, or p(M^{-1} A) x with ILU(0) factors lu."""
     lib = _load()
     n, rp, ci, va = _csr(a)
     x = _f64(x)
     out = np.empty(n)
     keep = p._keep()  # noqa: F841 (arrays must outlive the call)
-    lib.orc_poly_apply(n, _ptr(rp), _ptr(ci), _ptr(va), *p.args(), _ptr(x), _ptr(out))
+    lu = _lu(lu)
+    lib.orc_poly_apply_lu(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(lu), *p.args(), _ptr(x), _ptr(out))
     return out
 
 
@@ -216,8 +260,9 @@ def poly_eval_zp(p: Poly, z):
     return np.array([lib.orc_poly_eval_zp(*p.args(), float(t)) for t in np.atleast_1d(z)])
 
 
-def arnoldi(a, p: Poly, v, k):
-    """k MGS Arnoldi steps of A p(A) from v: returns (V n x (k+1), Hbar (k+1) x k, beta, steps)."""
+def arnoldi(a, p: Poly, v, k, lu=None):
+    """k MGS Arnoldi steps of A p(A) (with lu: B p(B), B = M^{-1} A) from v: returns (V n x (k+1),
+    Hbar (k+1) x k, beta, steps)."""
     lib = _load()
     n, rp, ci, va = _csr(a)
     v = _f64(v)
@@ -225,8 +270,9 @@ def arnoldi(a, p: Poly, v, k):
     H = np.zeros((k + 1) * k)
     beta = ctypes.c_double(0)
     keep = p._keep()  # noqa: F841
-    done = lib.orc_arnoldi(n, _ptr(rp), _ptr(ci), _ptr(va), *p.args(), _ptr(v), k, _ptr(V), _ptr(H),
-                           ctypes.byref(beta))
+    lu = _lu(lu)
+    done = lib.orc_arnoldi_lu(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(lu), *p.args(), _ptr(v), k, _ptr(V), _ptr(H),
+                              ctypes.byref(beta))
     return V.reshape(k + 1, n).T, H.reshape(k, k + 1).T, beta.value, done
 
 
@@ -243,8 +289,9 @@ class SolveResult:
     hist: np.ndarray
 
 
-def gmres(a, b, p: Poly = IDENTITY, tol=1e-8, m=50, maxit=10000, x0=None):
-    """Right-preconditioned restarted GMRES(m) with MGS Arnoldi."""
+def gmres(a, b, p: Poly = IDENTITY, tol=1e-8, m=50, maxit=10000, x0=None, lu=None):
+    """Right-preconditioned restarted GMRES(m) with MGS Arnoldi; with lu (ILU(0) factors) the
+    composition of Section VI, M^{-1} A p(M^{-1} A) u = M^{-1} b with x = p(M^{-1} A) u."""
     lib = _load()
     n, rp, ci, va = _csr(a)
     b = _f64(b)
@@ -252,8 +299,9 @@ def gmres(a, b, p: Poly = IDENTITY, tol=1e-8, m=50, maxit=10000, x0=None):
     stats = np.zeros(8)
     hist = np.zeros(maxit)
     keep = p._keep()  # noqa: F841
-    st = lib.orc_gmres(n, _ptr(rp), _ptr(ci), _ptr(va), *p.args(), _ptr(b), _ptr(x), float(tol), int(m), int(maxit),
-                       _ptr(stats), _ptr(hist), int(maxit))
+    lu = _lu(lu)
+    st = lib.orc_gmres_lu(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(lu), *p.args(), _ptr(b), _ptr(x), float(tol), int(m),
+                          int(maxit), _ptr(stats), _ptr(hist), int(maxit))
     if st == -2:
         raise MemoryError("oracle allocation failed")
     it = int(stats[0])

@@ -24,6 +24,11 @@
  *     Hessenberg least-squares problem, and a true residual at every restart.
  *     Relative residual ||b - A x|| / ||b|| is the stopping measure
  *     (Section III).
+ *   - the composition of Section VI: ILU(0) M = L U (no fill: L U agrees with A
+ *     on A's sparsity pattern) applied on the left and the polynomial on the
+ *     right, M^{-1} A p(M^{-1} A) y = M^{-1} b, x = p(M^{-1} A) y; the polynomial
+ *     is then the minimum-residual polynomial of B = M^{-1} A.  Every "_lu"
+ *     routine takes the factors; with lu = NULL it is the plain method.
  *
  * Every routine is written out loop by loop, in float64, one core.
  *
@@ -54,6 +59,7 @@ typedef struct {
     const int32_t *rowptr;
     const int32_t *colidx;
     const double *vals;
+    const double *lu; /* ILU(0) factors on the same pattern (Section VI's left preconditioner), or NULL */
 } csr_t;
 
 typedef struct {
@@ -109,8 +115,98 @@ static void spmv(const csr_t *A, const double *x, double *y)
 
 void orc_spmv(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, const double *x, double *y)
 {
-    csr_t A = {n, rp, ci, va};
+    csr_t A = {n, rp, ci, va, NULL};
     spmv(&A, x, y);
+}
+
+/* ------------------------------------------------------------------ */
+/* ILU(0): M = L U with L unit lower and U upper triangular, both on    */
+/* the sparsity pattern of A (Section VI's left preconditioner)        */
+/* ------------------------------------------------------------------ */
+
+/* Incomplete LU with no fill, row by row: for row i and each of its entries k < i in
+ * increasing column order, l_ik = a_ik / u_kk, then every entry j > k of row i that
+ * row k also has is reduced by l_ik u_kj; entries row k has but row i lacks are
+ * dropped.  lu (nnz values, A's pattern) receives L below the diagonal (its unit
+ * diagonal not stored) and U on and above it.  Columns within a row must be sorted
+ * and every row must hold its diagonal.  Returns 0, -(i+1) if row i has no diagonal
+ * or a zero pivot, -2 on allocation failure. */
+int orc_ilu0(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, double *lu)
+{
+    int64_t nnz = rp[n];
+    memcpy(lu, va, sizeof(double) * (size_t)nnz);
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *diag = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!pos || !diag) {
+        free(pos);
+        free(diag);
+        return -2;
+    }
+    for (int64_t j = 0; j < n; ++j) pos[j] = -1;
+    int status = 0;
+    for (int64_t i = 0; i < n && !status; ++i) {
+        diag[i] = -1;
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
+            pos[ci[t]] = t;
+            if (ci[t] == i) diag[i] = t;
+        }
+        if (diag[i] < 0) status = -(int)(i + 1);
+        for (int32_t t = rp[i]; t < rp[i + 1] && !status; ++t) {
+            int32_t k = ci[t];
+            if (k >= i) break;
+            double lik = lu[t] / lu[diag[k]];
+            lu[t] = lik;
+            for (int32_t q = diag[k] + 1; q < rp[k + 1]; ++q) {
+                int32_t p = pos[ci[q]];
+                if (p >= 0) lu[p] -= lik * lu[q];
+            }
+        }
+        if (!status && !(lu[diag[i]] != 0.0)) status = -(int)(i + 1);
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) pos[ci[t]] = -1;
+    }
+    free(pos);
+    free(diag);
+    return status;
+}
+
+/* y = (L U)^{-1} x: forward substitution with the unit lower factor, then back
+ * substitution with the upper one (rows sorted, diagonal present). */
+static void ilu0_solve(const csr_t *A, const double *x, double *y)
+{
+    int64_t n = A->n;
+    const int32_t *rp = A->rowptr, *ci = A->colidx;
+    const double *lu = A->lu;
+    for (int64_t i = 0; i < n; ++i) {
+        double s = x[i];
+        for (int32_t t = rp[i]; t < rp[i + 1] && ci[t] < i; ++t) s -= lu[t] * y[ci[t]];
+        y[i] = s;
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double s = y[i], d = 0.0;
+        for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
+            if (ci[t] > i) s -= lu[t] * y[ci[t]];
+            else if (ci[t] == i) d = lu[t];
+        }
+        y[i] = s / d;
+    }
+}
+
+void orc_ilu0_apply(int64_t n, const int32_t *rp, const int32_t *ci, const double *lu, const double *x, double *y)
+{
+    csr_t A = {n, rp, ci, NULL, lu};
+    ilu0_solve(&A, x, y);
+}
+
+/* the operator the Krylov methods see: y = A x, or with ILU(0) factors y = M^{-1} A x */
+static void opmul(const csr_t *A, const double *x, double *y)
+{
+    spmv(A, x, y);
+    if (A->lu) {
+        double *t = dalloc(A->n);
+        memcpy(t, y, sizeof(double) * (size_t)A->n);
+        ilu0_solve(A, t, y);
+        free(t);
+    }
 }
 
 /* rows listed in `rows` only: y[t] = (A x)[rows[t]] (used to check sampled outputs) */
@@ -158,7 +254,7 @@ static void poly_apply_power(const csr_t *A, int deg, const double *coef, const 
     memcpy(t, x, (size_t)n * sizeof(double));
     for (int64_t i = 0; i < n; ++i) out[i] = coef[0] * t[i];
     for (int p = 1; p <= deg; ++p) {
-        spmv(A, t, t2); /* t2 = A^p x */
+        opmul(A, t, t2); /* t2 = A^p x */
         memcpy(t, t2, (size_t)n * sizeof(double));
         axpy(n, coef[p], t, out);
     }
@@ -174,7 +270,7 @@ static void poly_apply_arnoldi(const csr_t *A, int deg, const double *H, const d
     for (int64_t i = 0; i < n; ++i) T[i] = x[i] / beta;
     for (int j = 1; j <= deg; ++j) {
         double *tj = T + (int64_t)j * n;
-        spmv(A, T + (int64_t)(j - 1) * n, tj);
+        opmul(A, T + (int64_t)(j - 1) * n, tj);
         for (int i = 0; i < j; ++i) axpy(n, -H[i + (int64_t)(j - 1) * ldh], T + (int64_t)i * n, tj);
         scal(n, 1.0 / H[j + (int64_t)(j - 1) * ldh], tj);
     }
@@ -217,14 +313,20 @@ static int poly_apply(const csr_t *A, const poly_t *p, const double *x, double *
     }
 }
 
-void orc_poly_apply(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, int kind, int deg,
+void orc_poly_apply_lu(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, const double *lu, int kind, int deg,
                     const double *coef, const double *H, const double *y, double beta, const double *x, double *out)
 {
-    csr_t A = {n, rp, ci, va};
+    csr_t A = {n, rp, ci, va, lu};
     poly_t p = {kind, deg, coef, H, y, beta};
     poly_ws w;
     if (poly_ws_init(&w, n, &p) == 0) poly_apply(&A, &p, x, out, &w);
     poly_ws_free(&w);
+}
+
+void orc_poly_apply(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, int kind, int deg,
+                    const double *coef, const double *H, const double *y, double beta, const double *x, double *out)
+{
+    orc_poly_apply_lu(n, rp, ci, va, NULL, kind, deg, coef, H, y, beta, x, out);
 }
 
 /* scalar evaluation z p(z) for real z (used for the alpha p(alpha) plots of Section V) */
@@ -307,10 +409,10 @@ static void cholesky_solve(int k, const double *L, int ld, const double *r, doub
  * fails); *info receives POTRF's info for the requested degree.  gram_out
  * (optional, (deg+1)^2, column-major) receives G before factoring and rhs_out
  * (optional) receives r. */
-int orc_poly_normal_eq(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, const double *v0, int deg,
+int orc_poly_normal_eq_lu(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, const double *lu, const double *v0, int deg,
                        double *coef, int *info, double *gram_out, double *rhs_out)
 {
-    csr_t A = {n, rp, ci, va};
+    csr_t A = {n, rp, ci, va, lu};
     int k = deg + 1;
     double *AV = dalloc(n * k);
     double *G = dalloc((int64_t)k * k);
@@ -319,8 +421,8 @@ int orc_poly_normal_eq(int64_t n, const int32_t *rp, const int32_t *ci, const do
         free(AV); free(G); free(r);
         return -2;
     }
-    spmv(&A, v0, AV);
-    for (int j = 1; j < k; ++j) spmv(&A, AV + (int64_t)(j - 1) * n, AV + (int64_t)j * n);
+    opmul(&A, v0, AV);
+    for (int j = 1; j < k; ++j) opmul(&A, AV + (int64_t)(j - 1) * n, AV + (int64_t)j * n);
     for (int a = 0; a < k; ++a) {
         for (int b = 0; b < k; ++b) G[a + b * k] = dot(n, AV + (int64_t)a * n, AV + (int64_t)b * n);
         r[a] = dot(n, AV + (int64_t)a * n, v0);
@@ -336,6 +438,12 @@ int orc_poly_normal_eq(int64_t n, const int32_t *rp, const int32_t *ci, const do
     free(G);
     free(r);
     return used;
+}
+
+int orc_poly_normal_eq(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, const double *v0, int deg,
+                       double *coef, int *info, double *gram_out, double *rhs_out)
+{
+    return orc_poly_normal_eq_lu(n, rp, ci, va, NULL, v0, deg, coef, info, gram_out, rhs_out);
 }
 
 /* ------------------------------------------------------------------ */
@@ -354,7 +462,7 @@ typedef struct {
 static void op_apply(op_t *op, const double *x, double *out)
 {
     op->spmvs += poly_apply(op->A, op->p, x, op->z, &op->ws);
-    spmv(op->A, op->z, out);
+    opmul(op->A, op->z, out);
     op->spmvs += 1;
 }
 
@@ -381,11 +489,11 @@ static int arnoldi_step(op_t *op, int64_t n, double *V, int j, double *H, int ld
 /* k steps of Arnoldi for A p(A) from v (normalised internally).  V: n x (k+1),
  * H: (k+1) x k column-major (ld = k+1).  Returns the number of steps completed
  * (< k only on breakdown); *beta = ||v||. */
-int orc_arnoldi(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, int kind, int deg,
+int orc_arnoldi_lu(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, const double *lu, int kind, int deg,
                 const double *coef, const double *Hp, const double *yp, double betap, const double *v, int k,
                 double *V, double *H, double *beta)
 {
-    csr_t A = {n, rp, ci, va};
+    csr_t A = {n, rp, ci, va, lu};
     poly_t p = {kind, deg, coef, Hp, yp, betap};
     op_t op = {&A, &p, {0}, dalloc(n), 0};
     if (poly_ws_init(&op.ws, n, &p) != 0 || !op.z) {
@@ -405,6 +513,13 @@ int orc_arnoldi(int64_t n, const int32_t *rp, const int32_t *ci, const double *v
     poly_ws_free(&op.ws);
     free(op.z);
     return done;
+}
+
+int orc_arnoldi(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, int kind, int deg,
+                const double *coef, const double *Hp, const double *yp, double betap, const double *v, int k,
+                double *V, double *H, double *beta)
+{
+    return orc_arnoldi_lu(n, rp, ci, va, NULL, kind, deg, coef, Hp, yp, betap, v, k, V, H, beta);
 }
 
 /* ------------------------------------------------------------------ */
@@ -471,19 +586,25 @@ static double hess_lsq(int k, const double *H, int ldh, double beta, double *y)
  * ||v0 - A p(A) v0|| = *resid (the GMRES residual, Section II).  On breakdown after j
  * steps the exact polynomial has degree j-1; the return value is the degree built
  * (entries of y beyond it are zero).  Returns -2 on allocation failure. */
-int orc_poly_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, const double *v0, int deg,
+int orc_poly_gmres_lu(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, const double *lu, const double *v0, int deg,
                    double *H, double *y, double *beta, double *resid)
 {
     int k = deg + 1;
     double *V = dalloc(n * (k + 1));
     if (!V) return -2;
-    int done = orc_arnoldi(n, rp, ci, va, ORC_POLY_NONE, 0, NULL, NULL, NULL, 1.0, v0, k, V, H, beta);
+    int done = orc_arnoldi_lu(n, rp, ci, va, lu, ORC_POLY_NONE, 0, NULL, NULL, NULL, 1.0, v0, k, V, H, beta);
     free(V);
     if (done < 0) return done;
     for (int j = 0; j <= deg; ++j) y[j] = 0.0;
     *resid = hess_lsq(done, H, k + 1, *beta, y);
     if (done < k) *resid = 0.0; /* breakdown: v0 lies in an invariant subspace, p is exact */
     return done - 1;
+}
+
+int orc_poly_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, const double *v0, int deg,
+                   double *H, double *y, double *beta, double *resid)
+{
+    return orc_poly_gmres_lu(n, rp, ci, va, NULL, v0, deg, H, y, beta, resid);
 }
 
 /* Power coefficients of the Arnoldi-form polynomial: K_{k} = V_k R with column j of R the
@@ -525,12 +646,16 @@ void orc_poly_arnoldi_to_power(int deg, const double *H, const double *y, double
  * with p(A) V y and the true residual b - A x is recomputed.  The solve stops when
  * ||b - A x|| <= tol ||b|| or maxit is reached.  hist (optional, capacity hist_cap)
  * receives |g_{j+1}| / ||b|| per iteration.  Returns 0 if converged, 1 if not,
- * -2 on allocation failure. */
-int orc_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, int kind, int deg,
+ * -2 on allocation failure.
+ * With ILU(0) factors (Section VI) the system is M^{-1} A p(M^{-1} A) u = M^{-1} b:
+ * each cycle starts from the preconditioned residual M^{-1} (b - A x), the Givens
+ * estimate is relative to ||M^{-1} b|| (the left-preconditioned residual GMRES
+ * minimises), and the stopping test stays the true ||b - A x|| <= tol ||b||. */
+int orc_gmres_lu(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, const double *lu, int kind, int deg,
               const double *coef, const double *Hp, const double *yp, double betap, const double *b, double *x,
               double tol, int m, int maxit, double *stats, double *hist, int hist_cap)
 {
-    csr_t A = {n, rp, ci, va};
+    csr_t A = {n, rp, ci, va, lu};
     poly_t p = {kind, deg, coef, Hp, yp, betap};
     op_t op = {&A, &p, {0}, dalloc(n), 0};
     double *V = dalloc(n * (m + 1));
@@ -552,6 +677,12 @@ int orc_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
         converged = 1;
         goto done;
     }
+    double enorm = bnorm; /* the norm the Givens estimate is relative to */
+    if (lu) {
+        ilu0_solve(&A, b, z);
+        enorm = nrm2(n, z);
+        dots += 1;
+    }
     for (;;) {
         spmv(&A, x, r); /* true residual */
         op.spmvs += 1;
@@ -564,6 +695,12 @@ int orc_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
             break;
         }
         if (iters >= maxit) break;
+        if (lu) { /* left preconditioning: the cycle's residual is M^{-1} r */
+            memcpy(z, r, sizeof(double) * (size_t)n);
+            ilu0_solve(&A, z, r);
+            beta = nrm2(n, r);
+            dots += 1;
+        }
         cycles += 1;
         for (int64_t i = 0; i < n; ++i) V[i] = r[i] / beta;
         for (int i = 0; i <= m; ++i) g[i] = 0.0;
@@ -579,7 +716,7 @@ int orc_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
             rot(cs[j], sn[j], &g[j], &g[j + 1]);
             iters += 1;
             k = j + 1;
-            est = fabs(g[j + 1]) / bnorm;
+            est = fabs(g[j + 1]) / enorm;
             if (hist && iters <= hist_cap) hist[iters - 1] = est;
             if (brk) {
                 brk_count += 1;
@@ -621,4 +758,11 @@ out:
     free(z);
     free(pz);
     return status;
+}
+
+int orc_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, int kind, int deg,
+              const double *coef, const double *Hp, const double *yp, double betap, const double *b, double *x,
+              double tol, int m, int maxit, double *stats, double *hist, int hist_cap)
+{
+    return orc_gmres_lu(n, rp, ci, va, NULL, kind, deg, coef, Hp, yp, betap, b, x, tol, m, maxit, stats, hist, hist_cap);
 }

@@ -386,3 +386,114 @@ def test_bidiag_matrices_converge(name, golden_dir):
         assert r.converged
         true = np.linalg.norm(b - a.to_scipy() @ r.x) / np.linalg.norm(b)
         assert true <= 1e-8
+
+
+# ---------------------------------------------------------------- ILU(0) on the left (Section VI)
+
+
+def _lu_dense(a, lu):
+    """Dense unit-lower L and upper U from the oracle's ILU(0) array on a's pattern."""
+    L = np.eye(a.n)
+    U = np.zeros((a.n, a.n))
+    for i in range(a.n):
+        for t in range(a.rowptr[i], a.rowptr[i + 1]):
+            j = a.colidx[t]
+            if j < i:
+                L[i, j] = lu[t]
+            else:
+                U[i, j] = lu[t]
+    return L, U
+
+
+def test_ilu0_is_the_exact_lu_without_fill():
+    """A tridiagonal matrix has no fill, so ILU(0) is its exact LU factorisation: L U = A."""
+    a = w.convdiff(60, 1, 20.0)
+    lu = oracle.ilu0(a)
+    L, U = _lu_dense(a, lu)
+    np.testing.assert_allclose(L @ U, a.to_dense(), rtol=0, atol=1e-13 * np.abs(a.vals).max())
+    # then M^{-1} A = I: GMRES with ILU(0) on the left converges in one iteration
+    b = w.rhs(a.n)
+    r = oracle.gmres(a, b, oracle.IDENTITY, tol=1e-12, m=20, lu=lu)
+    assert r.converged and r.iters == 1
+
+
+@pytest.mark.parametrize("case", ["convdiff2d", "random"])
+def test_ilu0_reproduces_a_on_its_pattern(case):
+    """The defining property of ILU(0): (L U)_ij = a_ij wherever a has an entry (the products that
+    fall outside the pattern are the dropped fill, which is not zero here)."""
+    a = w.convdiff(12, 2, 30.0) if case == "convdiff2d" else _rand_dd(150, 71, shift=3.0)
+    lu = oracle.ilu0(a)
+    L, U = _lu_dense(a, lu)
+    P = L @ U
+    ad = a.to_dense()
+    rows = np.repeat(np.arange(a.n), np.diff(a.rowptr))
+    scale = np.abs(a.vals).max()
+    assert np.abs(P[rows, a.colidx] - a.vals).max() <= 1e-12 * scale
+    mask = np.ones_like(ad, dtype=bool)
+    mask[rows, a.colidx] = False
+    assert np.abs(P[mask]).max() > 1e-6 * scale  # fill was dropped: M is not A
+
+
+def test_ilu0_apply_inverts_lu():
+    a = w.convdiff(12, 2, 30.0)
+    lu = oracle.ilu0(a)
+    L, U = _lu_dense(a, lu)
+    x = w.uniform(72, a.n)
+    y = oracle.ilu0_apply(a, lu, x)
+    np.testing.assert_allclose(L @ (U @ y), x, rtol=0, atol=1e-12 * np.abs(x).max())
+
+
+@pytest.mark.parametrize("deg", [1, 3, 5])
+def test_poly_of_the_ilu_preconditioned_operator_is_minimal(deg):
+    """With ILU(0) the polynomial is the minimum-residual polynomial of B = M^{-1} A: ||v0 - B p(B) v0|| is
+    the least-squares minimum over B's Krylov space, and the three routes agree."""
+    a = _rand_dd(90, 73, shift=2.0)
+    lu = oracle.ilu0(a)
+    L, U = _lu_dense(a, lu)
+    B = np.linalg.solve(U, np.linalg.solve(L, a.to_dense()))
+    v0 = w.uniform(74, a.n)
+    K = np.empty((a.n, deg + 1))
+    t = v0.copy()
+    for j in range(deg + 1):
+        t = B @ t
+        K[:, j] = t
+    c, *_ = np.linalg.lstsq(K, v0, rcond=None)
+    best = np.linalg.norm(v0 - K @ c)
+    pg = oracle.poly_gmres(a, v0, deg, lu=lu)
+    assert abs(pg.resid - best) <= 1e-10 * np.linalg.norm(v0)
+    px = oracle.poly_apply(a, pg, v0, lu=lu)
+    assert abs(np.linalg.norm(v0 - B @ px) - best) <= 1e-10 * np.linalg.norm(v0)
+    pn = oracle.poly_normal_eq(a, v0, deg, lu=lu)
+    if pn.info == 0:  # the power basis of B ~ I is ill-conditioned early: a clamped degree is checked below
+        assert np.linalg.norm(v0 - B @ oracle.poly_apply(a, pn, v0, lu=lu)) <= best * (1 + 1e-6)
+    else:
+        assert pn.deg == pn.info - 2 < deg
+
+
+def test_gmres_with_ilu_left_and_poly_right():
+    """Section VI's composition: the solution solves A x = b (true residual), and the first cycle's
+    estimates are the Krylov minima of M^{-1} A p(M^{-1} A) for the preconditioned residual M^{-1} b,
+    relative to ||M^{-1} b||."""
+    a = _rand_dd(120, 75, shift=0.8)
+    lu = oracle.ilu0(a)
+    L, U = _lu_dense(a, lu)
+    Minv = lambda v: np.linalg.solve(U, np.linalg.solve(L, v))  # noqa: E731
+    b = w.rhs(a.n)
+    p = oracle.poly_gmres(a, w.v0(a.n), 3, lu=lu)
+    r = oracle.gmres(a, b, p, tol=1e-10, m=40, maxit=500, lu=lu)
+    assert r.converged
+    np.testing.assert_allclose(a.to_dense() @ r.x, b, rtol=0, atol=1e-9 * np.linalg.norm(b))
+    Bop = np.column_stack([Minv(a.to_dense() @ oracle.poly_apply(a, p, e, lu=lu)) for e in np.eye(a.n)])
+    rb = Minv(b)
+    h = oracle.gmres(a, b, p, tol=1e-14, m=30, maxit=5, lu=lu).hist
+    assert len(h) >= 3
+    t = rb.copy()
+    Kl = []
+    for k in range(1, len(h) + 1):
+        Kl.append(t)
+        Q, _ = np.linalg.qr(np.column_stack(Kl))
+        BQ = Bop @ Q
+        c, *_ = np.linalg.lstsq(BQ, rb, rcond=None)
+        best = np.linalg.norm(rb - BQ @ c) / np.linalg.norm(rb)
+        assert abs(h[k - 1] - best) <= 1e-9 * max(best, 1e-3)
+        t = Bop @ t
