@@ -42,10 +42,10 @@ def workload_name(N, nnz=None):
             + "), Pe 50, GMRES(50), rtol 1e-8")
 
 
-# DRAM traffic of one k_spmv_w<short> launch (a root step of the p(A) chain, C2 matrix) from the ncu
+# DRAM traffic of one k_spmv_e<float> launch (a root step of the p(A) chain, C2 matrix) from the ncu
 # capture summarised in profiles/k_spmv_c2_128cubed.md, and the kernel source it was taken with: when the
 # source changes, the number no longer describes the kernel and the bench reports null.
-SPMV_TRAFFIC = {"src_sha256_16": "0a7e88457ddfc9ac", "dram_bytes": 105260032 + 5647872,
+SPMV_TRAFFIC = {"src_sha256_16": "6a7844d022592221", "dram_bytes": 105253376 + 4877056,
                 "algorithmic_bytes": 112656384 + 16777216,
                 "launch": "k_spmv_e root step (tile-ELL values and window indices, x windows staged in "
                           "shared memory; write Y and P'), ncu --set full, cold caches; most of the 16.8 MB "
@@ -233,8 +233,9 @@ def main():
     ap.add_argument("--harness-iters", type=int, default=20)
     ap.add_argument("--spmv-format", default="auto", choices=["auto", "csr", "sell", "staged"],
                     help="sparse format of the SpMV kernels (ppg_spmv_format)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"],
-                    help="c2 (default): the benchmark line; c1/c3/c4/c5: the other configurations, one JSON line each")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "ilu"],
+                    help="c2 (default): the benchmark line; c1/c3/c4/c5: the other configurations, one JSON line "
+                         "each; ilu: ILU(0) on the left with and without the polynomial on the 128^3 system")
     args = ap.parse_args()
 
     world, rank, local = dist_init(args)

@@ -235,6 +235,23 @@ ppg_status ppg_get_poly(ppg_ctx *ctx, int *basis, int *degree, double *coef_h, i
  * device vectors of length n of the matching type and must not overlap. */
 ppg_status ppg_apply_poly(ppg_ctx *ctx, const void *v, void *out, int precision);
 
+/* ILU(0) on the left of the polynomial (Section VI): with enable = 1 the context factors its matrix
+ * as M = L U, the incomplete LU with no fill (L U agrees with A on A's sparsity pattern; computed on
+ * the device, once), and from then on the operator of ppg_build_poly, ppg_apply_poly and ppg_solve
+ * is B = M^{-1} A: the polynomial is the minimum-residual polynomial of B and ppg_solve solves
+ * M^{-1} A p(M^{-1} A) u = M^{-1} b with x = p(M^{-1} A) u, each restart cycle starting from the
+ * preconditioned residual M^{-1} (b - A x), its estimate relative to ||M^{-1} b||, the stopping test
+ * the true ||b - A x|| <= tol ||b||.  The float32 solve runs the standard form (PPG_F32_STANDARD)
+ * and no CUDA graphs.  enable = 0 returns to A (the factors are kept).  Changing the setting drops the
+ * current polynomial (build it again).  ppg_spmv still computes A x; ppg_solve_transpose and
+ * ppg_apply_poly_noalloc refuse to run while ILU(0) is on.  lu_out (device, nnz doubles, may be
+ * NULL) receives the factors on A's pattern: L below the diagonal (unit diagonal not stored), U on and
+ * above it.  The triangular solves are one cooperative launch each, whose warps wait (bounded, 1 s)
+ * for the rows they depend on.  Synchronises.
+ * Errors: PPG_ERR_INVALID_ARG (a row's columns not sorted, a diagonal entry missing),
+ * PPG_ERR_POLY_BREAKDOWN (a zero or non-finite pivot), PPG_ERR_OOM, PPG_ERR_CUDA. */
+ppg_status ppg_set_left_ilu0(ppg_ctx *ctx, int enable, double *lu_out);
+
 /* Allocation-free variant of ppg_apply_poly (the paper has no counterpart; this is a service of the
  * library).  For callers that may not allocate device memory at the point of the call -- for example
  * a service that reserves its whole device-memory budget at start-up, or code running where a

@@ -50,6 +50,7 @@ EXPORTED = (
     "ppg_spmv_format", "ppg_chain_fusion", "ppg_build_poly", "ppg_set_poly", "ppg_get_poly", "ppg_apply_poly", "ppg_apply_poly_noalloc", "ppg_solve",
     "ppg_solve_transpose",
     "ppg_csr_outer", "ppg_arnoldi", "ppg_hessenberg_eigs", "ppg_gram_solve", "ppg_fill_uniform", "ppg_solve_batched",
+    "ppg_set_left_ilu0",
     "ppg_status_string", "ppg_last_error", "ppg_version",
 )
 
@@ -116,6 +117,7 @@ def load_library(path: str = LIB_PATH):
         "ppg_arnoldi": (I, [P, P, I, P, P, ctypes.POINTER(I)]),
         "ppg_hessenberg_eigs": (I, [P, I, P, I, P, P]),
         "ppg_gram_solve": (I, [P, I, P, P, P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "ppg_set_left_ilu0": (I, [P, I, P]),
         "ppg_fill_uniform": (I, [P, P, I64, U64]),
         "ppg_solve_batched": (I, [I, ctypes.POINTER(ppg_batch_system), I, D, I, I, U64, P,
                                   ctypes.POINTER(ppg_stats)]),
@@ -451,6 +453,16 @@ def ppg_gram_solve(ctx, G, r):
     return y, info.value, used.value, st
 
 
+def ppg_set_left_ilu0(ctx, enable=1, lu_out=None):
+    """ILU(0) on the left of the polynomial (Section VI) on or off; lu_out (float64 tensor of nnz, optional)
+    receives the factors on A's pattern."""
+    where = "ppg_set_left_ilu0"
+    _ctx(ctx, where)
+    if lu_out is not None:
+        _f64(ctx, lu_out, where, "lu_out", length=ctx.nnz)
+    return _check(load_library().ppg_set_left_ilu0(ctx, int(enable), _ptr(lu_out)), where)
+
+
 def ppg_fill_uniform(ctx, out, seed):
     where = "ppg_fill_uniform"
     _ctx(ctx, where)
@@ -555,6 +567,12 @@ class Solver:
         y = self._torch.empty_like(x) if y is None else y
         ppg_spmv(self.ctx, x, y)
         return y
+
+    def set_left_ilu0(self, enable=1, want_factors=False):
+        """ILU(0) on the left (Section VI); returns the factors (float64, nnz) when want_factors."""
+        lu = self._torch.empty(self.nnz, dtype=self._torch.float64, device=self.device) if want_factors else None
+        ppg_set_left_ilu0(self.ctx, enable, lu)
+        return lu
 
     def spmv_format(self, request=PPG_SPMV_QUERY):
         return ppg_spmv_format(self.ctx, request)

@@ -93,6 +93,16 @@ struct ppg_ctx {
     double *d_evals64 = nullptr;
     int fuse = 0;                // pair consecutive links of the p(A) chain into one launch (measured slower)
     WaitCfg waits;               // limits of the software waits (set per solve from ppg_opts)
+    // ILU(0) on the left (ppg_set_left_ilu0): factors on A's pattern, the rows of each triangle sorted
+    // by level, per-row ready words of the triangular solves, and five vectors of ld doubles (the
+    // SpMV's result and the two solves' outputs of a composed link; a residual and its M^{-1} image)
+    int ilu_on = 0;
+    double *d_lu64 = nullptr;
+    float *d_lu32 = nullptr;
+    int *d_ilu_diag = nullptr, *d_lorder = nullptr, *d_uorder = nullptr, *d_ilu_flags = nullptr;
+    int *d_ilu_abort = nullptr;
+    int ilu_epoch = 0;
+    char *ilu_vec = nullptr;
     char *noalloc_base = nullptr; // device address of the allocation-free apply's scratch (n <= its limit)
 
     // CUDA graphs of single iterations (ppg_opts.use_graph): one per iteration index, precision and
@@ -370,6 +380,7 @@ struct Exec {
     const DevMatrix *A;
     int prec;
     cudaStream_t s;
+    bool plain = false;  // y = A x even when ILU(0) is on (ppg_spmv)
 
     // Links of a p(A) chain are issued through spmv(); inside a chain (depth > 0) each link is held
     // back one call so that two consecutive links can share one launch (launch_spmv2).
@@ -380,16 +391,74 @@ struct Exec {
 
     ppg_status launch_one(const SpmvEpi &e, int check)
     {
+        if (c->ilu_on && !plain) return launch_ilu_link(e, check);
         c->launches++;
         PPG_CK(launch_spmv(*A, prec, e, c->st, check, s));
         prof_add(c, spmv_bytes(*A, prec, e), 0.0);
         return PPG_OK;
     }
+
+    // One link with ILU(0) on the left (Section VI): the link's A becomes B = M^{-1} A = U^{-1} L^{-1} A:
+    // t1 = A (x + s2 x2), t2 = L^{-1} t1, then U^{-1} t2 with the link's epilogue applied to it.
+    char *ilu_v(int q) const { return c->ilu_vec + (size_t)q * c->ld * sizeof(double); }
+    ppg_status ilu_solve(bool lower, VecRef x, void *y, const SpmvEpi &epi, int check)
+    {
+        IluSolveArgs a{};
+        a.n = A->n;
+        a.rp = c->d_rowptr;
+        a.ci = c->d_colidx;
+        a.lu = prec == kF64 ? (const void *)c->d_lu64 : (const void *)c->d_lu32;
+        a.order = lower ? c->d_lorder : c->d_uorder;
+        a.flags = c->d_ilu_flags;
+        a.epoch = ++c->ilu_epoch;
+        a.abort = c->d_ilu_abort;
+        a.x = x;
+        a.y = y;
+        a.e = epi;
+        a.st = c->st;
+        a.check = check;
+        c->launches++;
+        PPG_CK(launch_ilu_solve(prec, lower, a, c->num_sms, s));
+        const double sv = prec == kF64 ? 8.0 : 4.0;
+        prof_add(c, (double)A->nnz * (sv + 4.0) + 4.0 * (A->n + 1) + 4.0 * A->n * (2.0 + sv), 0.0);
+        return PPG_OK;
+    }
+    ppg_status launch_ilu_link(const SpmvEpi &e, int check)
+    {
+        SpmvEpi s1 = epi_none();
+        s1.x = e.x;
+        s1.x2 = e.x2;
+        s1.s2 = e.s2;
+        s1.out0 = vfix(ilu_v(0));
+        s1.a0 = simm(1.0);
+        c->launches++;
+        PPG_CK(launch_spmv(*A, prec, s1, c->st, check, s));
+        prof_add(c, spmv_bytes(*A, prec, s1), 0.0);
+        PPG_TRY(ilu_solve(true, vfix(ilu_v(0)), ilu_v(1), epi_none(), check));
+        SpmvEpi ep = e;
+        ep.x = ep.x2 = vnone();
+        return ilu_solve(false, vfix(ilu_v(1)), ilu_v(2), ep, check);
+    }
+    // dst = M^{-1} src (float64 vectors), skipped once the solve has stopped
+    ppg_status ilu_apply64(const double *src, double *dst)
+    {
+        const int keep = prec;
+        prec = kF64;
+        ppg_status st = ilu_solve(true, vfix(src), ilu_v(1), epi_none(), kSkipIfStop);
+        if (st >= 0) {
+            SpmvEpi ep = epi_none();
+            ep.out0 = vfix(dst);
+            ep.a0 = simm(1.0);
+            st = ilu_solve(false, vfix(ilu_v(1)), ilu_v(2), ep, kSkipIfStop);
+        }
+        prec = keep;
+        return st;
+    }
     // e2 consumes an output of e1 by gather and writes neither of its own gathered inputs, and the
     // matrix allows pairing (chain_pairs)
     bool can_pair(const SpmvEpi &e1, const SpmvEpi &e2) const
     {
-        if (!c->fuse || !chain_pairs(*A, prec, c->d_rounds != nullptr)) return false;
+        if (!c->fuse || (c->ilu_on && !plain) || !chain_pairs(*A, prec, c->d_rounds != nullptr)) return false;
         auto is_out = [&](const VecRef &v) {
             return v.base && ((e1.out0.base && same_vec(v, e1.out0)) || (e1.out1.base && same_vec(v, e1.out1)));
         };
@@ -756,7 +825,7 @@ struct Iter {
     ppg_status run(int j)
     {
         ppg_ctx *c = x->c;
-        if (!use_graph || c->prof || c->graphs_broken || j >= kKmax) return iteration(j);
+        if (!use_graph || c->prof || c->graphs_broken || j >= kKmax || c->ilu_on) return iteration(j);
         const size_t form = flex ? 2 : (x->prec == kF64 ? 1 : 0);
         const size_t slot = (size_t)j + (size_t)kKmax * (size_t)(2 * form + (c->has_poly ? 1 : 0));
         if (c->igraphs.size() < (size_t)(6 * kKmax)) c->igraphs.resize(6 * kKmax);
@@ -1091,8 +1160,9 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
     const int form = opts ? opts->f32_form : PPG_F32_FLEXIBLE;
     if (form != PPG_F32_FLEXIBLE && form != PPG_F32_STANDARD) return fail(PPG_ERR_INVALID_ARG, "unknown f32_form");
     // the flexible form keeps z_j = p(A) v_j; with no polynomial (or a scalar one) z_j is v_j itself
+    // (with ILU(0) on the left the standard form runs: its operator is M^{-1} A throughout)
     const bool flex = prec == PPG_F32 && form == PPG_F32_FLEXIBLE && c->has_poly &&
-                      !(c->basis == PPG_BASIS_POWER && c->degree == 0);
+                      !(c->basis == PPG_BASIS_POWER && c->degree == 0) && !c->ilu_on;
     // limits of the software waits for this solve (the context keeps the defaults otherwise)
     c->waits = WaitCfg{};
     if (opts && opts->wait_limit_us > 0 && opts->wait_limit_us < 1000000)
@@ -1128,14 +1198,37 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
     PPG_TRY(init_cycle_state(c, 0, restart, maxit, tol, inner));
     c->launches++;
     PPG_CK(launch_norm_start(c->A.n, kF64, b, nullptr, 0, c->st, L.partials, c->A.resid_blocks, c->stream));
+    // ILU(0) on the left (Section VI): the estimate is relative to ||M^{-1} b||, and every cycle starts
+    // from the preconditioned residual M^{-1} (b - A x) while the stopping test stays on b - A x
+    double *ilu_r = c->ilu_on ? reinterpret_cast<double *>(ex.ilu_v(3)) : nullptr;
+    double *ilu_rm = c->ilu_on ? reinterpret_cast<double *>(ex.ilu_v(4)) : nullptr;
+    auto start_cycle = [&]() -> ppg_status {
+        c->launches++;
+        if (!c->ilu_on) {
+            PPG_CK(launch_residual(c->A, prec, b, x, L.basis, c->st, L.partials, c->stream));
+            return PPG_OK;
+        }
+        PPG_CK(launch_residual(c->A, kF64, b, x, ilu_r, c->st, L.partials, c->stream, 1));
+        PPG_TRY(ex.ilu_apply64(ilu_r, ilu_rm));
+        c->launches++;
+        PPG_CK(launch_norm_start(c->A.n, prec, ilu_rm, L.basis, 3, c->st, L.partials, c->A.resid_blocks,
+                                 c->stream));
+        return PPG_OK;
+    };
+    if (c->ilu_on) {
+        PPG_CK(cudaMemsetAsync(c->d_ilu_abort, 0, sizeof(int), c->stream));
+        PPG_TRY(ex.ilu_apply64(b, ilu_rm));
+        c->launches++;
+        PPG_CK(launch_norm_start(c->A.n, kF64, ilu_rm, nullptr, 2, c->st, L.partials, c->A.resid_blocks,
+                                 c->stream));
+    }
     PPG_TRY(read_state(c));
     if (c->h_st->bnorm == 0.0) {
         PPG_CK(cudaMemsetAsync(x, 0, sizeof(double) * c->A.n, c->stream));
         c->h_st->converged = 1;
         c->h_st->relres = 0.0;
     } else {
-        c->launches++;
-        PPG_CK(launch_residual(c->A, prec, b, x, L.basis, c->st, L.partials, c->stream));
+        PPG_TRY(start_cycle());
         PPG_TRY(read_state(c));
         while (!c->h_st->stop) {
             PPG_TRY(run_cycle(c, it, restart));
@@ -1146,8 +1239,7 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
                 PPG_TRY(it.restart_projection(b, x));
                 if (c->prof) PPG_TRY(prof_close_proj(c, np));
             }
-            c->launches++;
-            PPG_CK(launch_residual(c->A, prec, b, x, L.basis, c->st, L.partials, c->stream));
+            PPG_TRY(start_cycle());
             PPG_TRY(read_state(c));
         }
     }
@@ -1648,6 +1740,14 @@ void ppg_destroy(ppg_ctx *c)
     cudaFree(c->d_twin);
     cudaFree(c->d_lidx);
     cudaFree(c->d_evals);  // also holds d_eidx
+    cudaFree(c->d_lu64);
+    cudaFree(c->d_lu32);
+    cudaFree(c->d_ilu_diag);
+    cudaFree(c->d_lorder);
+    cudaFree(c->d_uorder);
+    cudaFree(c->d_ilu_flags);
+    cudaFree(c->d_ilu_abort);
+    cudaFree(c->ilu_vec);
     cudaFree(c->d_toff);
     cudaFree(c->d_etwin);
     cudaFree(c->d_evals64);
@@ -1751,6 +1851,7 @@ ppg_status ppg_spmv(ppg_ctx *c, const void *x, void *y, int precision)
     PPG_TRY(set_device(c));
     if (precision == PPG_F32) PPG_TRY(ensure_f32(c));
     Exec ex{c, &c->A, precision, c->stream};
+    ex.plain = true;  // A itself, also with ILU(0) on
     SpmvEpi e = epi_none();
     e.x = vfix(x);
     e.out0 = vfix(y);
@@ -1764,6 +1865,7 @@ ppg_status ppg_build_poly(ppg_ctx *c, int degree, int basis, const double *v0, u
     if (degree < -1 || degree > kSmallMax - 2) return fail(PPG_ERR_INVALID_ARG, "degree must be in [-1, 62]");
     if (basis != PPG_BASIS_POWER && basis != PPG_BASIS_ROOTS) return fail(PPG_ERR_INVALID_ARG, "unknown basis");
     PPG_TRY(set_device(c));
+    if (c->ilu_on) PPG_CK(cudaMemsetAsync(c->d_ilu_abort, 0, sizeof(int), c->stream));
     const bool autodeg = degree < 0;
     int deg = autodeg ? 30 : degree;
     Layout L;
@@ -1851,6 +1953,95 @@ ppg_status ppg_get_poly(ppg_ctx *c, int *basis, int *degree, double *coef_h, int
     return PPG_OK;
 }
 
+ppg_status ppg_set_left_ilu0(ppg_ctx *c, int enable, double *lu_out)
+{
+    PPG_TRY(check_ctx(c));
+    PPG_TRY(set_device(c));
+    if (enable && !c->d_lu64) {
+        const long long n = c->A.n, nnz = c->A.nnz;
+        std::vector<int> rp(n + 1), ci(nnz > 0 ? nnz : 1);
+        PPG_CK(cudaMemcpy(rp.data(), c->d_rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
+        if (nnz > 0) PPG_CK(cudaMemcpy(ci.data(), c->d_colidx, sizeof(int) * nnz, cudaMemcpyDeviceToHost));
+        // the pattern: sorted rows, every diagonal present; levels of the two triangles' dependencies
+        std::vector<int> diag(n), llev(n, 0), ulev(n, 0);
+        int lmax = 0, umax = 0;
+        for (long long i = 0; i < n; ++i) {
+            diag[i] = -1;
+            int lv = 0;
+            for (int t = rp[i]; t < rp[i + 1]; ++t) {
+                if (t > rp[i] && ci[t] <= ci[t - 1])
+                    return fail(PPG_ERR_INVALID_ARG, "ILU(0) needs the columns of every row sorted (row %lld)", i);
+                if (ci[t] == i) diag[i] = t;
+                if (ci[t] < i) lv = std::max(lv, llev[ci[t]] + 1);
+            }
+            if (diag[i] < 0) return fail(PPG_ERR_INVALID_ARG, "ILU(0) needs every diagonal entry (row %lld)", i);
+            llev[i] = lv;
+            lmax = std::max(lmax, lv);
+        }
+        for (long long i = n - 1; i >= 0; --i) {
+            int lv = 0;
+            for (int t = diag[i] + 1; t < rp[i + 1]; ++t) lv = std::max(lv, ulev[ci[t]] + 1);
+            ulev[i] = lv;
+            umax = std::max(umax, lv);
+        }
+        auto sort_by = [&](const std::vector<int> &lev, int nl, std::vector<int> &order, std::vector<int> &start) {
+            start.assign(nl + 2, 0);
+            for (long long i = 0; i < n; ++i) start[lev[i] + 1]++;
+            for (int l = 0; l <= nl; ++l) start[l + 1] += start[l];
+            std::vector<int> fill(start.begin(), start.end() - 1);
+            order.resize(n);
+            for (long long i = 0; i < n; ++i) order[fill[lev[i]]++] = (int)i;
+        };
+        std::vector<int> lorder, lstart, uorder, ustart;
+        sort_by(llev, lmax, lorder, lstart);
+        sort_by(ulev, umax, uorder, ustart);
+        PPG_CK(cudaMalloc(&c->d_lu64, sizeof(double) * (nnz + 1)));
+        PPG_CK(cudaMalloc(&c->d_lu32, sizeof(float) * (nnz + 1)));
+        PPG_CK(cudaMalloc(&c->d_ilu_diag, sizeof(int) * n));
+        PPG_CK(cudaMalloc(&c->d_lorder, sizeof(int) * n));
+        PPG_CK(cudaMalloc(&c->d_uorder, sizeof(int) * n));
+        PPG_CK(cudaMalloc(&c->d_ilu_flags, sizeof(int) * n));
+        PPG_CK(cudaMalloc(&c->d_ilu_abort, sizeof(int)));
+        PPG_CK(cudaMalloc(&c->ilu_vec, sizeof(double) * 5 * c->ld));
+        PPG_CK(cudaMemcpy(c->d_ilu_diag, diag.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        PPG_CK(cudaMemcpy(c->d_lorder, lorder.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        PPG_CK(cudaMemcpy(c->d_uorder, uorder.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        PPG_CK(cudaMemset(c->d_ilu_flags, 0, sizeof(int) * n));
+        PPG_CK(cudaMemset(c->d_ilu_abort, 0, sizeof(int)));
+        PPG_CK(cudaMemset(c->ilu_vec, 0, sizeof(double) * 5 * c->ld));
+        c->ilu_epoch = 0;
+        // factorisation on the device, one launch per level of the lower triangle
+        if (nnz > 0) PPG_CK(cudaMemcpyAsync(c->d_lu64, c->d_vals, sizeof(double) * nnz, cudaMemcpyDeviceToDevice,
+                                            c->stream));
+        for (int l = 0; l <= lmax; ++l)
+            PPG_CK(launch_ilu0_level(c->d_lorder + lstart[l], lstart[l + 1] - lstart[l], c->d_rowptr, c->d_colidx,
+                                     c->d_ilu_diag, c->d_lu64, c->stream));
+        if (nnz > 0) PPG_CK(launch_ilu_cast(c->d_lu64, c->d_lu32, nnz, c->stream));
+        // pivots: U's diagonal must be finite and non-zero
+        std::vector<double> lu(nnz > 0 ? nnz : 1);
+        if (nnz > 0)
+            PPG_CK(cudaMemcpyAsync(lu.data(), c->d_lu64, sizeof(double) * nnz, cudaMemcpyDeviceToHost, c->stream));
+        PPG_CK(cudaStreamSynchronize(c->stream));
+        for (long long i = 0; i < n; ++i) {
+            const double d = lu[diag[i]];
+            if (!(d != 0.0) || !std::isfinite(d)) {
+                cudaFree(c->d_lu64);
+                c->d_lu64 = nullptr;
+                return fail(PPG_ERR_POLY_BREAKDOWN, "ILU(0) breaks down: pivot %lld is %g", i, d);
+            }
+        }
+    }
+    const int on = enable ? 1 : 0;
+    if (on != c->ilu_on) {
+        c->ilu_on = on;
+        c->has_poly = 0;  // a polynomial belongs to its operator (A, or M^{-1} A): build it again
+    }
+    if (lu_out && c->d_lu64)
+        PPG_CK(cudaMemcpyAsync(lu_out, c->d_lu64, sizeof(double) * c->A.nnz, cudaMemcpyDeviceToDevice, c->stream));
+    PPG_CK(cudaStreamSynchronize(c->stream));
+    return PPG_OK;
+}
+
 ppg_status ppg_apply_poly(ppg_ctx *c, const void *v, void *out, int precision)
 {
     PPG_TRY(check_ctx(c));
@@ -1859,6 +2050,7 @@ ppg_status ppg_apply_poly(ppg_ctx *c, const void *v, void *out, int precision)
     if (!c->has_poly) return fail(PPG_ERR_NO_POLY, "no polynomial has been built or set");
     PPG_TRY(set_device(c));
     if (precision == PPG_F32) PPG_TRY(ensure_f32(c));
+    if (c->ilu_on) PPG_CK(cudaMemsetAsync(c->d_ilu_abort, 0, sizeof(int), c->stream));
     const size_t es = precision == PPG_F64 ? 8 : 4;
     Layout L;
     PPG_TRY(get_layout(c, 1, es, &L));
@@ -1877,6 +2069,8 @@ ppg_status ppg_apply_poly_noalloc(ppg_ctx *c, const void *v, void *out, int prec
     if (!v || !out) return fail(PPG_ERR_INVALID_ARG, "null vector");
     if (precision != PPG_F64 && precision != PPG_F32) return fail(PPG_ERR_INVALID_ARG, "unknown precision");
     if (!c->has_poly) return fail(PPG_ERR_NO_POLY, "no polynomial has been built or set");
+    if (c->ilu_on)
+        return fail(PPG_ERR_INVALID_ARG, "ppg_apply_poly_noalloc does not apply ILU(0): turn it off or use ppg_apply_poly");
     if (c->A.n > kNoAllocMaxN)
         return fail(PPG_ERR_INVALID_ARG,
                     "ppg_apply_poly_noalloc handles at most %lld rows (n = %d); use ppg_apply_poly", kNoAllocMaxN,
@@ -2145,6 +2339,8 @@ ppg_status ppg_solve_transpose(ppg_ctx *c, const double *g, double *lambda, doub
 {
     PPG_TRY(check_ctx(c));
     PPG_TRY(set_device(c));
+    if (c->ilu_on)
+        return fail(PPG_ERR_INVALID_ARG, "the transposed solve does not compose with ILU(0): turn it off first");
     if (!c->tctx) {
         int *rpT = nullptr, *ciT = nullptr, *work = nullptr;
         double *vaT = nullptr;

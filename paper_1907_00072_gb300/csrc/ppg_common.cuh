@@ -43,6 +43,8 @@ struct Cycle {
     long long nres;     // float64 true residuals computed (b - A x)
     long long nproj;    // restart projections done (flexible float32 solves)
     double bnorm;       // ||b||
+    double enorm;       // the norm the in-cycle estimate is relative to: ||b||, or ||M^{-1} b|| with ILU(0)
+                        // on the left (the residual left-preconditioned GMRES minimises)
     double tol;         // relative tolerance
     double inner_rtol;  // cycle ends when |g_{j+1}| <= inner_rtol * beta (0: off)
     double beta;        // ||r|| at the start of the cycle

@@ -187,6 +187,33 @@ struct GsArgs {
     int use_tmap; // 1: a tile's kstage basis columns arrive by one 2-D tensor copy (set by launch_gs)
 };
 
+// ---- ILU(0) on the left (Section VI)
+// One level of the row-by-row ILU(0) factorisation (rows: the level's rows): lu holds A's values on
+// entry (A's sorted pattern, diag: each row's diagonal position) and L (unit diagonal not stored)
+// and U on exit, level by level.
+cudaError_t launch_ilu0_level(const int *rows, int count, const int *rp, const int *ci, const int *diag, double *lu,
+                              cudaStream_t s);
+cudaError_t launch_ilu_cast(const double *in, float *out, long long count, cudaStream_t s);
+// A triangular solve with the factors: lower: y = L^{-1} x (unit diagonal); upper: y = U^{-1} x.
+// order: the rows sorted by their level for this triangle; flags: one int per row, the solve's epoch
+// once the row is final (ints from earlier epochs are stale).  The epilogue e (its x, x2 unused)
+// is applied per row to y: out0 = a0 y + b0 u0 + c0 w0, out1 likewise.  abort: one int, zero.
+struct IluSolveArgs {
+    int n;
+    const int *rp, *ci;
+    const void *lu;     // factors in the solve's value type
+    const int *order;
+    int *flags;
+    int epoch;
+    int *abort;
+    VecRef x;           // input
+    void *y;            // the solution (also read by later rows)
+    SpmvEpi e;
+    Cycle *st;
+    int check;          // Check
+};
+cudaError_t launch_ilu_solve(int prec, bool lower, const IluSolveArgs &a, int num_sms, cudaStream_t s);
+
 // x += U y (float64 x and y = Cycle::y, k = Cycle::k columns of U; flexible cycle end and restart
 // projection, U = the preconditioned basis Z); rows n..ld-1 of U are not read.  skip_if_stop: return
 // at once when the solve has stopped.
@@ -197,7 +224,7 @@ cudaError_t launch_validate(int n, long long nnz, const int *rowptr, const int *
 cudaError_t launch_cast_f32(const double *in, float *out, long long count, cudaStream_t s);
 // check: 0 always run; kSkipIfDone: return when the cycle is done (iteration kernels);
 // kSkipIfNoCols: return when the finished cycle has no columns to combine (cycle-end kernels).
-enum Check : int { kNoCheck = 0, kSkipIfDone = 1, kSkipIfNoCols = 2 };
+enum Check : int { kNoCheck = 0, kSkipIfDone = 1, kSkipIfNoCols = 2, kSkipIfStop = 3 };
 cudaError_t launch_spmv(const DevMatrix &A, int prec, const SpmvEpi &e, Cycle *st, int check, cudaStream_t s);
 cudaError_t launch_axpy(int n, int prec, const SpmvEpi &e, Cycle *st, int check, cudaStream_t s);
 // r = b - A x in float64 written as prec into out (column 0 of the basis); ||r|| finalises the

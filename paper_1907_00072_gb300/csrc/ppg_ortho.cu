@@ -238,7 +238,7 @@ __device__ void cta_finish_pass3(Cycle *st, int j, double wsq, double *sh, size_
             s_it[1] = st->maxit;
             s_m[0] = st->m;
             s_m[1] = st->mode;
-            const double bn = st->bnorm, irt = st->inner_rtol;
+            const double bn = st->enorm, irt = st->inner_rtol;
             sc[3] = st->g[j];
             sc[4] = st->tol * bn;
             sc[5] = irt > 0.0 ? irt * st->beta : -1.0;

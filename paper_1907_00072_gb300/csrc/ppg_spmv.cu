@@ -2054,8 +2054,10 @@ cudaError_t launch_residual(const DevMatrix &A, int out_prec, const double *b, c
                       (float *)out, st, partials, proj);
 }
 
-// ||v||.  mode 0: st->bnorm = ||v|| (right-hand side).  mode 1: start an Arnoldi run from v:
-// out = v (converted), beta = ||v||, sigma_0 = 1/beta, j = 0.
+// ||v||.  mode 0: st->bnorm = st->enorm = ||v|| (right-hand side).  mode 1: start an Arnoldi run from
+// v: out = v (converted), beta = ||v||, sigma_0 = 1/beta, j = 0.  mode 2: st->enorm = ||v|| (the
+// left-preconditioned right-hand side M^{-1} b).  mode 3: unless the solve has stopped, start a GMRES
+// cycle from v (the left-preconditioned residual): out = v, beta, sigma_0, g = beta e_1, j = k = 0.
 template <typename Tout>
 __global__ void __launch_bounds__(kThreads) k_norm_start(int n, const double *__restrict__ v, Tout *__restrict__ out,
                                                          int mode, Cycle *st, double *partials)
@@ -2064,6 +2066,7 @@ __global__ void __launch_bounds__(kThreads) k_norm_start(int n, const double *__
     __shared__ int s_last;
     pdl_wait();
     pdl_trigger();
+    if (mode == 3 && st->stop) return;
     double acc = 0.0;
     const int stride = gridDim.x * blockDim.x;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
@@ -2080,9 +2083,27 @@ __global__ void __launch_bounds__(kThreads) k_norm_start(int n, const double *__
                 const double nv = sqrt(tot);
                 if (mode == 0) {
                     st->bnorm = nv;
+                    st->enorm = nv;
+                } else if (mode == 2) {
+                    st->enorm = nv;
+                } else if (mode == 3) {
+                    st->beta = nv;
+                    st->sigma[0] = (nv > 0.0) ? 1.0 / nv : 0.0;
+                    st->j = 0;
+                    st->k = 0;
+                    st->breakdown = 0;
+                    st->cycles += 1;
+                    st->cycle_done = (nv > 0.0 && isfinite(nv)) ? 0 : 1;
+                    if (!isfinite(nv)) {
+                        st->error |= kErrNonfinite;
+                        st->stop = 1;
+                    }
+                    for (int i = 0; i <= st->m; ++i) st->g[i] = 0.0;
+                    st->g[0] = nv;
                 } else {
                     st->beta = nv;
                     st->bnorm = nv;
+                    st->enorm = nv;
                     st->sigma[0] = (nv > 0.0) ? 1.0 / nv : 0.0;
                     st->j = 0;
                     st->k = 0;
