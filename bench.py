@@ -42,14 +42,15 @@ def workload_name(N, nnz=None):
             + "), Pe 50, GMRES(50), rtol 1e-8")
 
 
-# DRAM traffic of one k_spmv_e<float> launch (a root step of the p(A) chain, C2 matrix) from the ncu
-# capture summarised in profiles/k_spmv_c2_128cubed.md, and the kernel source it was taken with: when the
-# source changes, the number no longer describes the kernel and the bench reports null.
-SPMV_TRAFFIC = {"src_sha256_16": "6a7844d022592221", "dram_bytes": 105253376 + 4877056,
+# DRAM traffic of a k_spmv_e<float> root step in place in the chain (C2 matrix; the mean of three
+# consecutive root steps measured with ncu without flushing L2 between launches, so each link finds what
+# the previous one left), summarised in profiles/k_spmv_c2_128cubed.md, and the kernel source it was taken
+# with: when the source changes, the number no longer describes the kernel and the bench reports null.
+SPMV_TRAFFIC = {"src_sha256_16": "3cf4760b97b8d7a7", "dram_bytes": round((56585728 + 41273088 + 28707328) / 3),
                 "algorithmic_bytes": 112656384 + 16777216,
-                "launch": "k_spmv_e root step (tile-ELL values and window indices, x windows staged in "
-                          "shared memory; write Y and P'), ncu --set full, cold caches; most of the 16.8 MB "
-                          "of writes are still in L2 when the kernel ends"}
+                "launch": "k_spmv_e root step in the running chain (tile-ELL values and window indices, x windows "
+                          "staged in shared memory; write Y and P'); consecutive links walk their tiles in "
+                          "opposite orders, so two thirds of the algorithmic bytes come from L2"}
 
 
 def spmv_traffic():
@@ -233,6 +234,9 @@ def main():
     ap.add_argument("--harness-iters", type=int, default=20)
     ap.add_argument("--spmv-format", default="auto", choices=["auto", "csr", "sell", "staged"],
                     help="sparse format of the SpMV kernels (ppg_spmv_format)")
+    ap.add_argument("--systems", type=int, default=0,
+                    help="c4: solve only the first N systems of the batch (0: all 256), without the one-by-one "
+                         "comparison when N > 0 (a small case for profiling)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "ilu"],
                     help="c2 (default): the benchmark line; c1/c3/c4/c5: the other configurations, one JSON line "
                          "each; ilu: ILU(0) on the left with and without the polynomial on the 128^3 system")

@@ -113,6 +113,7 @@ typedef struct {
     int converged;       /* 1 if relres_true <= tol */
     int breakdowns;      /* cycles ended by a (lucky) Arnoldi breakdown */
     int ctas_per_system; /* ppg_solve_batched: CTAs (cluster size) per system; 0 otherwise */
+    int spmv_lanes;      /* ppg_solve_batched: threads per row of the system's SpMV (tuned); 0 otherwise */
     double time_ms;      /* wall time of the call on the device stream (CUDA events) */
     /* filled when ppg_opts.profile = 1, for launches that did work: device time and algorithmic
        bytes of the SpMV chain (p(A) steps and the SpMV that applies A) and of the Gram-Schmidt
@@ -277,7 +278,8 @@ ppg_status ppg_apply_poly_noalloc(ppg_ctx *ctx, const void *v, void *out, int pr
 /* Solves A x = b by right-preconditioned GMRES(restart) with the current polynomial (the identity if
  * none was built): the Krylov basis is built for A p(A) with two classical Gram-Schmidt passes per
  * iteration, the Hessenberg least-squares problem is solved with Givens rotations on the device, and
- * at each restart x += p(A) V y followed by a float64 true residual b - A x.  b and x are float64[n]
+ * at each restart x += p(A) V y (the float32 flexible form: x += Z y with the kept Z = p(A) V) followed
+ * by a float64 true residual b - A x.  b and x are float64[n]
  * (x: initial guess in, solution out).  Stops when ||b - A x|| / ||b|| <= tol or after maxit
  * iterations.  1 <= restart <= 127.  opts and stats may be NULL.  Synchronises.
  * Returns PPG_OK, PPG_ERR_NOT_CONVERGED, or an error. */

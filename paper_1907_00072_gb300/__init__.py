@@ -65,7 +65,8 @@ class ppg_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("restarts", ctypes.c_int64), ("spmvs", ctypes.c_int64),
                 ("dots", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("relres_true", ctypes.c_double),
                 ("relres_est", ctypes.c_double), ("degree_used", ctypes.c_int), ("converged", ctypes.c_int),
-                ("breakdowns", ctypes.c_int), ("ctas_per_system", ctypes.c_int), ("time_ms", ctypes.c_double),
+                ("breakdowns", ctypes.c_int), ("ctas_per_system", ctypes.c_int), ("spmv_lanes", ctypes.c_int),
+                ("time_ms", ctypes.c_double),
                 ("spmv_ms", ctypes.c_double), ("spmv_bytes", ctypes.c_double), ("spmv_segments", ctypes.c_int64),
                 ("gs_ms", ctypes.c_double), ("gs_bytes", ctypes.c_double), ("gs_segments", ctypes.c_int64)]
 

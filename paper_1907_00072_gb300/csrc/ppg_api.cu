@@ -92,6 +92,9 @@ struct ppg_ctx {
     int *d_etwin = nullptr;
     double *d_evals64 = nullptr;
     int fuse = 0;                // pair consecutive links of the p(A) chain into one launch (measured slower)
+    int spmv_alternate = 1;      // consecutive tile-ELL links visit their tiles in opposite orders
+    unsigned long long spmv_links = 0;
+    int gs_alternate = 1;        // Gram-Schmidt pass 2 visits its tiles in the opposite order of passes 1, 3
     WaitCfg waits;               // limits of the software waits (set per solve from ppg_opts)
     // ILU(0) on the left (ppg_set_left_ilu0): factors on A's pattern, the rows of each triangle sorted
     // by level, per-row ready words of the triangular solves, and five vectors of ld doubles (the
@@ -285,6 +288,7 @@ SpmvEpi epi_none()
     e.x = e.x2 = vnone();
     e.out0 = e.u0 = e.w0 = e.out1 = e.u1 = e.w1 = vnone();
     e.a0 = e.b0 = e.c0 = e.a1 = e.b1 = e.c1 = e.s2 = simm(0.0);
+    e.rev = 0;
     return e;
 }
 
@@ -393,7 +397,9 @@ struct Exec {
     {
         if (c->ilu_on && !plain) return launch_ilu_link(e, check);
         c->launches++;
-        PPG_CK(launch_spmv(*A, prec, e, c->st, check, s));
+        SpmvEpi ed = e;
+        if (c->spmv_alternate) ed.rev = (int)(c->spmv_links++ & 1);
+        PPG_CK(launch_spmv(*A, prec, ed, c->st, check, s));
         prof_add(c, spmv_bytes(*A, prec, e), 0.0);
         return PPG_OK;
     }
@@ -751,6 +757,7 @@ struct Iter {
         a.op = op;
         a.kcols_from_k = from_k;
         a.partials = L->partials;
+        a.rev = (x->c->gs_alternate && op == kGsUpdDot) ? 1 : 0;
         x->c->launches++;
         PPG_CK(launch_gs(x->prec, kcols, x->c->ld, x->c->num_sms, a, x->c->st, x->s));
         // bytes: k columns read, w read (except when combining), one vector written (passes 2-4);
@@ -1610,6 +1617,11 @@ ppg_status ppg_create(ppg_ctx **out, int64_t n, int64_t nnz, const int32_t *rowp
         const long long etiles = (n + RE - 1) / RE;
         const char *ell_env = getenv("PPG_SPMV_ELL");  // 0: no tile-ELL copy (the windowed CSR kernel runs)
         const bool ell_on = !ell_env || atoi(ell_env) != 0;
+        // L2 reuse between consecutive passes over the same data (0 turns each off)
+        const char *alt_env = getenv("PPG_SPMV_ALTERNATE");
+        c->spmv_alternate = alt_env ? atoi(alt_env) : 1;
+        const char *galt_env = getenv("PPG_GS_ALTERNATE");
+        c->gs_alternate = galt_env ? atoi(galt_env) : 1;
         std::vector<int> edesc;
         std::vector<short> elidx;
         long long exmax = 0, ewindowed = -1;
@@ -2315,6 +2327,7 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
             st.converged = o.converged;
             st.breakdowns = o.breakdowns;
             st.ctas_per_system = bc.cluster;
+            st.spmv_lanes = hs[i].lanes;
             st.time_ms = ms;
             st.spmv_ms = (double)(o.t_end - o.t_start) * 1e-6;  // this system's own time on the device
             st.gs_ms = (double)(o.t_start - t_first) * 1e-6;     // when its cluster started in the launch

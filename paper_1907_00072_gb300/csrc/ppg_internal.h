@@ -158,6 +158,7 @@ struct SpmvEpi {
     VecRef out0, u0, w0;
     VecRef out1, u1, w1;
     Scalar a0, b0, c0, a1, b1, c1, s2;
+    int rev;  // 1: the launch visits its row tiles last to first (tile-ELL kernel)
 };
 
 // Gram-Schmidt / basis kernels over the column-major basis U (ld entries per column).
@@ -185,6 +186,7 @@ struct GsArgs {
     int kstage;   // columns one pipeline stage holds (>= the columns used); set by launch_gs
     int nstages;  // pipeline depth; set by launch_gs
     int use_tmap; // 1: a tile's kstage basis columns arrive by one 2-D tensor copy (set by launch_gs)
+    int rev;      // 1: the pass visits its row tiles last to first
 };
 
 // ---- ILU(0) on the left (Section VI)

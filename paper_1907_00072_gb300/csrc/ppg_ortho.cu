@@ -447,7 +447,12 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st, const __
             if (need_w) bulk_g2s(stage0 + stage * SS + (long long)a.kstage * TR, w + tile * TR, colb, &bars[stage]);
         }
     };
-    auto tile_of = [&](int q) { return blockIdx.x + (long long)q * gridDim.x; };
+    // the CTA's q-th tile (q < my_tiles); a reversed pass visits the same tiles last to first, so it
+    // starts on the basis rows the previous (forward) pass read last, which are still in L2
+    const long long my_tiles = blockIdx.x < a.ntiles ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto tile_of = [&](long long q) {
+        return blockIdx.x + (a.rev ? my_tiles - 1 - q : q) * (long long)gridDim.x;
+    };
 
     // Before the wait on the predecessor: the basis columns of the first stages.  For the
     // iteration passes the host's column count is the device's k, and the columns were written
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st, const __
     const bool early_w = early && op == kGsUpdDot;
     if (early && prod) {
         for (int q = 0; q < nst - 1; ++q)
-            if (tile_of(q) < a.ntiles) {
+            if (q < my_tiles) {
                 issue_cols(tile_of(q), q, a.kstage);
                 if (early_w) issue_w(tile_of(q), q);
             }
@@ -483,10 +488,10 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st, const __
         if (early) {  // the copies already requested land before the CTA's shared memory is released
             if (prod && lane == 0 && !early_w)
                 for (int q = 0; q < nst - 1; ++q)
-                    if (tile_of(q) < a.ntiles) mbar_arrive(&bars[q]);
+                    if (q < my_tiles) mbar_arrive(&bars[q]);
             if (tid == 0)
                 for (int q = 0; q < nst - 1; ++q)
-                    if (tile_of(q) < a.ntiles) mbar_wait_bounded(&bars[q], 0, kWaitLimitNs);
+                    if (q < my_tiles) mbar_wait_bounded(&bars[q], 0, kWaitLimitNs);
         }
         return;
     }
@@ -502,7 +507,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st, const __
     // the start of iteration it into the stage freed by iteration it - 1
     if (prod) {
         for (int q = 0; q < nst - 1; ++q)
-            if (tile_of(q) < a.ntiles) {
+            if (q < my_tiles) {
                 if (!early) issue_cols(tile_of(q), q, k);
                 if (!early_w) issue_w(tile_of(q), q);
             }
@@ -513,13 +518,14 @@ __global__ void __launch_bounds__(kGsThreads) k_gs(GsArgs a, Cycle *st, const __
     Acc<T> nrm;  // float32 path: float32 Kahan sum per thread, float64 across threads
     bool timed_out = false;
     int it = 0;
-    for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+    for (; it < my_tiles; ++it) {
+        const long long tile = tile_of(it);
         const int stage = it % nst;
         if (prod) {
             // the producer refills the stage the previous iteration released, then meets the
             // compute warps at the end-of-tile barrier
-            const long long nt = tile + (long long)(nst - 1) * gridDim.x;
-            if (nt < a.ntiles) {
+            if (it + nst - 1 < my_tiles) {
+                const long long nt = tile_of(it + nst - 1);
                 issue_cols(nt, (it + nst - 1) % nst, k);
                 issue_w(nt, (it + nst - 1) % nst);
             }

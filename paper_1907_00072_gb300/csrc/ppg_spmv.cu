@@ -911,6 +911,10 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int prefetched = (int)min((long long)S, my_tiles);
+    // the CTA's i-th tile; a reversed launch visits the same tiles last to first, so it starts on the
+    // tiles the previous (forward) link read last, which are still in L2
+    const bool rev = a.e.rev != 0;
+    auto tile_at = [&](long long i) { return blockIdx.x + (rev ? my_tiles - 1 - i : i) * (long long)gridDim.x; };
 
     if (tid == 0) {
         for (int q = 0; q < S; ++q) {
@@ -974,12 +978,12 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
             int no0 = 0, no1 = 0;
             int4 nd[4];
             if (my_tiles > 0) {
-                span(blockIdx.x, no0, no1);
-                desc(blockIdx.x, nd);
+                span(tile_at(0), no0, no1);
+                desc(tile_at(0), nd);
             }
             int i = 0, ps = 0, pround = 0;  // stage and round of tile i (no division by S)
             bool waited = false;
-            for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+            for (; i < my_tiles; ++i) {
                 if (i == prefetched) {
                     waited = true;
                     pdl_wait();
@@ -1003,9 +1007,9 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) s_desc[s][u] = nd[u];
-                if (tile + gridDim.x < ntiles) {
-                    span(tile + gridDim.x, no0, no1);
-                    desc(tile + gridDim.x, nd);
+                if (i + 1 < my_tiles) {
+                    span(tile_at(i + 1), no0, no1);
+                    desc(tile_at(i + 1), nd);
                 }
                 if (round > 0 && !mbar_wait_bounded(&empty[s], (round - 1) & 1, kWaitLimitNs)) {
                     timeout_stop(st);
@@ -1061,7 +1065,8 @@ __global__ void __launch_bounds__(kSpmvThreads, PPG_SPMV_MIN_BLOCKS) k_spmv_e(Sp
     const T c2 = (T)s_coef[6];
     int s = 0;
     uint32_t ph = 0;  // stage and phase of the current tile (no division by S)
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (long long i = 0; i < my_tiles; ++i) {
+        const long long tile = tile_at(i);
         const int rr = (int)(tile * R) + tid;
         const bool ok = rr < a.n;
         // row operands first: their loads overlap the wait and the products
@@ -1746,8 +1751,8 @@ cudaError_t spmve_set_smem()
 {
     const int sv = (int)sizeof(T);
     const size_t cap = (size_t)smem_optin() - 1024;
-    size_t b1 = 3 * spmve_stage_bytes(kEllWidthMax, false, kXCap, sv);
-    size_t b2 = 3 * spmve_stage_bytes(kEllWidthMax, true, kXCap, sv);
+    size_t b1 = kSpmvStages * spmve_stage_bytes(kEllWidthMax, false, kXCap, sv);
+    size_t b2 = kSpmvStages * spmve_stage_bytes(kEllWidthMax, true, kXCap, sv);
     if (b1 > cap) b1 = cap;
     if (b2 > cap) b2 = cap;
     cudaError_t e = cudaFuncSetAttribute(k_spmv_e<T, false, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b1);
@@ -1861,16 +1866,18 @@ int spmve_per_sm_t(int G, int wmax, bool x2, int xcap, int nst)
     return spmve_per_sm_g<T, 1>(wmax, x2, xcap, nst);
 }
 
-// Tile-ELL grid and pipeline depth for value type T: three stages when they fit, else two.
+// Tile-ELL grid and pipeline depth for value type T: kSpmvStages stages when they fit, else fewer.
 template <typename T>
 void spmve_plan(DevMatrix *A, EllLaunch *L)
 {
     for (int x2 = 0; x2 < 2; ++x2) {
-        int nst = 3, per = spmve_per_sm_t<T>(A->lanes_per_row, A->ewmax, x2 != 0, A->excap, 3);
-        if (per == 0) {
-            nst = 2;
-            per = spmve_per_sm_t<T>(A->lanes_per_row, A->ewmax, x2 != 0, A->excap, 2);
+        // the deepest pipeline that leaves at least one CTA per SM
+        int nst = kSpmvStages, per = 0;
+        for (; nst >= 2; --nst) {
+            per = spmve_per_sm_t<T>(A->lanes_per_row, A->ewmax, x2 != 0, A->excap, nst);
+            if (per > 0) break;
         }
+        if (nst < 2) nst = 2;
         (x2 ? L->blocks_x2 : L->blocks) = per * A->num_sms;
         (x2 ? L->nst_x2 : L->nst) = nst;
     }
