@@ -91,13 +91,15 @@ typedef struct {
                           device time and algorithmic bytes in ppg_stats (adds a sync per cycle) */
     int f32_form;      /* PPG_F32 only: PPG_F32_FLEXIBLE (0, default) or PPG_F32_STANDARD */
     int wait_limit_us; /* limit of the library's software waits, in microseconds: the two-step kernel's waits on
-                          its round counters (ppg_chain_fusion) and the host's wait for the device's progress
-                          between enqueued iterations.  <= 0 or >= 10^6: 1 s.  A wait that runs out ends the solve
+                          its round counters (ppg_chain_fusion), the ILU(0) triangular solves' waits on the rows
+                          a row depends on, and the host's wait for the device's progress between enqueued
+                          iterations.  <= 0 or >= 10^6: 1 s.  A wait that runs out ends the solve
                           with PPG_ERR_TIMEOUT once the work already queued has finished (every device wait is
                           bounded; waits on TMA copies keep their 1 s limit), and ppg_last_error() says where */
     int test_unreachable_wait; /* tests of the failure path only (0 otherwise): 1 makes every round of the
-                          two-step kernel need one CTA more than its launch has, so that its round-counter
-                          waits run out after wait_limit_us */
+                          two-step kernel need one CTA more than its launch has, and every ILU(0) triangular
+                          solve wait for a mark that no row of the solve writes, so that those waits run out
+                          after wait_limit_us */
     int reserved[1];
 } ppg_opts;
 
@@ -247,8 +249,8 @@ ppg_status ppg_apply_poly(ppg_ctx *ctx, const void *v, void *out, int precision)
  * current polynomial (build it again).  ppg_spmv still computes A x; ppg_solve_transpose and
  * ppg_apply_poly_noalloc refuse to run while ILU(0) is on.  lu_out (device, nnz doubles, may be
  * NULL) receives the factors on A's pattern: L below the diagonal (unit diagonal not stored), U on and
- * above it.  The triangular solves are one cooperative launch each, whose warps wait (bounded, 1 s)
- * for the rows they depend on.  Synchronises.
+ * above it.  The triangular solves are one cooperative launch each, whose warps wait (bounded: 1 s, or a
+ * solve's ppg_opts.wait_limit_us) for the rows they depend on.  Synchronises.
  * Errors: PPG_ERR_INVALID_ARG (a row's columns not sorted, a diagonal entry missing),
  * PPG_ERR_POLY_BREAKDOWN (a zero or non-finite pivot), PPG_ERR_OOM, PPG_ERR_CUDA. */
 ppg_status ppg_set_left_ilu0(ppg_ctx *ctx, int enable, double *lu_out);

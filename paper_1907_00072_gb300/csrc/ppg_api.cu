@@ -423,6 +423,8 @@ struct Exec {
         a.e = epi;
         a.st = c->st;
         a.check = check;
+        a.wait_ns = c->waits.ns;
+        a.need_ahead = c->waits.extra_need ? 1 : 0;
         c->launches++;
         PPG_CK(launch_ilu_solve(prec, lower, a, c->num_sms, s));
         const double sv = prec == kF64 ? 8.0 : 4.0;
@@ -957,6 +959,13 @@ ppg_status read_state(ppg_ctx *c)
                         "a bounded device wait expired (two-step SpMV: %s wait, CTA %d of %d, iteration %d, round %d, "
                         "have %d need %d)",
                         d[0] == 1 ? "stage" : "round", d[1], d[6], d[2], d[3], d[4], d[5]);
+        int row = 0;
+        if (c->ilu_on && c->d_ilu_abort) cudaMemcpy(&row, c->d_ilu_abort, sizeof row, cudaMemcpyDeviceToHost);
+        if (row > 0)
+            return fail(PPG_ERR_TIMEOUT,
+                        "a bounded device wait expired (ILU(0) triangular solve: the wait on the rows that row %d "
+                        "depends on)",
+                        row - 1);
         return fail(PPG_ERR_TIMEOUT, "a bounded device wait expired");
     }
     return PPG_OK;

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_solve(IluSolveArgs a)
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (sub * G));
     const long long W = (long long)gridDim.x * (blockDim.x >> 5);
     const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int epoch = a.epoch;
+    const int epoch = a.epoch + a.need_ahead;
     // the next row's list entry and bounds are loaded a step ahead (they do not depend on other rows)
     int ni = 0, ne0 = 0, ne1 = 0;
     if (wg * R + sub < a.n) {
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) k_ilu_solve(IluSolveArgs a)
                     if (ilu_ld_acquire(a.flags + k) != epoch) {
                         const unsigned long long t0 = global_timer_ns();
                         for (unsigned int spins = 1; ilu_ld_acquire(a.flags + k) != epoch; ++spins) {
-                            if ((spins & 63u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
+                            if ((spins & 63u) == 0 && global_timer_ns() - t0 > a.wait_ns) {
                                 ok = false;
                                 break;
                             }
@@ -154,13 +154,13 @@ __global__ void __launch_bounds__(kThreads) k_ilu_solve(IluSolveArgs a)
                     if (w1) v = fma(cc1, w1[i], v);
                     o1[i] = v;
                 }
-                ilu_st_release(a.flags + i, epoch);  // orders this lane's stores of y and the outputs before it
+                ilu_st_release(a.flags + i, a.epoch);  // orders this lane's stores of y and the outputs before it
             }
         }
         if (__any_sync(0xffffffffu, !ok)) {
             if (lane == 0) {
                 timeout_stop(st);
-                atomicExch(a.abort, 1);
+                atomicCAS(a.abort, 0, i + 1);
             }
             return;
         }

@@ -199,7 +199,8 @@ cudaError_t launch_ilu_cast(const double *in, float *out, long long count, cudaS
 // A triangular solve with the factors: lower: y = L^{-1} x (unit diagonal); upper: y = U^{-1} x.
 // order: the rows sorted by their level for this triangle; flags: one int per row, the solve's epoch
 // once the row is final (ints from earlier epochs are stale).  The epilogue e (its x, x2 unused)
-// is applied per row to y: out0 = a0 y + b0 u0 + c0 w0, out1 likewise.  abort: one int, zero.
+// is applied per row to y: out0 = a0 y + b0 u0 + c0 w0, out1 likewise.  abort: one int, zero; a wait
+// that runs out stores there 1 + the row it was computing (the first such row wins) and stops the cycle.
 struct IluSolveArgs {
     int n;
     const int *rp, *ci;
@@ -213,6 +214,8 @@ struct IluSolveArgs {
     SpmvEpi e;
     Cycle *st;
     int check;          // Check
+    unsigned long long wait_ns;  // limit of one wait on a ready word
+    int need_ahead;     // tests of the failure path: waits expect epoch + need_ahead (0 normally)
 };
 cudaError_t launch_ilu_solve(int prec, bool lower, const IluSolveArgs &a, int num_sms, cudaStream_t s);
 

@@ -5,6 +5,8 @@ Every wait in the library is bounded.  These tests make two of them run out with
     round need one CTA more than the launch has (a count that nothing reaches), and a 2 ms limit;
   * the host's wait for the device's progress between enqueued iterations, with a 1 us limit on a
     system whose first iteration takes hundreds of microseconds.
+  * the ILU(0) triangular solves' waits on the rows a row depends on, with the same test switch (every
+    wait expects a mark that no row of the solve writes) and a 2 ms limit.
 Each solve must return PPG_ERR_TIMEOUT with a record of where the wait gave up, and the next solve
 on the same context, with the default limits, must converge.
 """
@@ -69,4 +71,21 @@ def test_host_progress_wait_runs_out_and_the_context_recovers():
     assert "wait for the device's progress ran out" in str(e.value)
     x, info = s.solve(_T(b), tol=1e-8, restart=50, maxit=500, precision=ppg.PPG_F32)
     assert info.status == ppg.PPG_OK and _relres(a, b, x.cpu().numpy()) <= 1e-8
+    s.close()
+
+
+def test_ilu_ready_word_wait_runs_out_and_the_context_recovers():
+    a = w.convdiff(21, 3, 50.0)
+    b = w.rhs(a.n)
+    s = _solver(a)
+    s.set_left_ilu0(1)
+    s.build_poly(5, ppg.PPG_BASIS_ROOTS, v0=_T(w.v0(a.n)))
+    for prec in (ppg.PPG_F64, ppg.PPG_F32):
+        with pytest.raises(ppg.PPGError) as e:
+            s.solve(_T(b), tol=1e-8, restart=50, maxit=500, precision=prec, wait_limit_us=2000,
+                    test_unreachable_wait=1)
+        assert e.value.status == ppg.PPG_ERR_TIMEOUT
+        assert "ILU(0) triangular solve" in str(e.value), str(e.value)
+        x, info = s.solve(_T(b), tol=1e-8, restart=50, maxit=500, precision=prec)
+        assert info.status == ppg.PPG_OK and _relres(a, b, x.cpu().numpy()) <= 1e-8
     s.close()
