@@ -98,8 +98,8 @@ typedef struct {
                           bounded; waits on TMA copies keep their 1 s limit), and ppg_last_error() says where */
     int test_unreachable_wait; /* tests of the failure path only (0 otherwise): 1 makes every round of the
                           two-step kernel need one CTA more than its launch has, and every ILU(0) triangular
-                          solve wait for a mark that no row of the solve writes, so that those waits run out
-                          after wait_limit_us */
+                          solve treat the rows it waits on as never ready, so that those waits run out after
+                          wait_limit_us */
     int reserved[1];
 } ppg_opts;
 

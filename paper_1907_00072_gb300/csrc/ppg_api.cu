@@ -97,14 +97,17 @@ struct ppg_ctx {
     int gs_alternate = 1;        // Gram-Schmidt pass 2 visits its tiles in the opposite order of passes 1, 3
     WaitCfg waits;               // limits of the software waits (set per solve from ppg_opts)
     // ILU(0) on the left (ppg_set_left_ilu0): factors on A's pattern, the rows of each triangle sorted
-    // by level, per-row ready words of the triangular solves, and five vectors of ld doubles (the
-    // SpMV's result and the two solves' outputs of a composed link; a residual and its M^{-1} image)
+    // by level, the triangular solves' abort word, and five vectors of ld doubles (the SpMV's result and
+    // the two solves' outputs of a composed link, which also mark their rows ready; a residual and its
+    // M^{-1} image)
     int ilu_on = 0;
     double *d_lu64 = nullptr;
     float *d_lu32 = nullptr;
-    int *d_ilu_diag = nullptr, *d_lorder = nullptr, *d_uorder = nullptr, *d_ilu_flags = nullptr;
+    int *d_ilu_diag = nullptr, *d_lorder = nullptr, *d_uorder = nullptr;
+    double *d_ilu_rd64 = nullptr;  // 1 / u_ii (the upper solve multiplies by it)
+    float *d_ilu_rd32 = nullptr;
+    int ilu_red = 32;              // lanes a row's sum is reduced over: a power of two >= the longest row
     int *d_ilu_abort = nullptr;
-    int ilu_epoch = 0;
     char *ilu_vec = nullptr;
     char *noalloc_base = nullptr; // device address of the allocation-free apply's scratch (n <= its limit)
 
@@ -415,8 +418,6 @@ struct Exec {
         a.ci = c->d_colidx;
         a.lu = prec == kF64 ? (const void *)c->d_lu64 : (const void *)c->d_lu32;
         a.order = lower ? c->d_lorder : c->d_uorder;
-        a.flags = c->d_ilu_flags;
-        a.epoch = ++c->ilu_epoch;
         a.abort = c->d_ilu_abort;
         a.x = x;
         a.y = y;
@@ -424,7 +425,9 @@ struct Exec {
         a.st = c->st;
         a.check = check;
         a.wait_ns = c->waits.ns;
-        a.need_ahead = c->waits.extra_need ? 1 : 0;
+        a.unreachable = c->waits.extra_need ? 1 : 0;
+        a.rdiag = prec == kF64 ? (const void *)c->d_ilu_rd64 : (const void *)c->d_ilu_rd32;
+        a.red = c->ilu_red;
         c->launches++;
         PPG_CK(launch_ilu_solve(prec, lower, a, c->num_sms, s));
         const double sv = prec == kF64 ? 8.0 : 4.0;
@@ -1764,9 +1767,10 @@ void ppg_destroy(ppg_ctx *c)
     cudaFree(c->d_lu64);
     cudaFree(c->d_lu32);
     cudaFree(c->d_ilu_diag);
+    cudaFree(c->d_ilu_rd64);
+    cudaFree(c->d_ilu_rd32);
     cudaFree(c->d_lorder);
     cudaFree(c->d_uorder);
-    cudaFree(c->d_ilu_flags);
     cudaFree(c->d_ilu_abort);
     cudaFree(c->ilu_vec);
     cudaFree(c->d_toff);
@@ -2021,16 +2025,13 @@ ppg_status ppg_set_left_ilu0(ppg_ctx *c, int enable, double *lu_out)
         PPG_CK(cudaMalloc(&c->d_ilu_diag, sizeof(int) * n));
         PPG_CK(cudaMalloc(&c->d_lorder, sizeof(int) * n));
         PPG_CK(cudaMalloc(&c->d_uorder, sizeof(int) * n));
-        PPG_CK(cudaMalloc(&c->d_ilu_flags, sizeof(int) * n));
         PPG_CK(cudaMalloc(&c->d_ilu_abort, sizeof(int)));
         PPG_CK(cudaMalloc(&c->ilu_vec, sizeof(double) * 5 * c->ld));
         PPG_CK(cudaMemcpy(c->d_ilu_diag, diag.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
         PPG_CK(cudaMemcpy(c->d_lorder, lorder.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
         PPG_CK(cudaMemcpy(c->d_uorder, uorder.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
-        PPG_CK(cudaMemset(c->d_ilu_flags, 0, sizeof(int) * n));
         PPG_CK(cudaMemset(c->d_ilu_abort, 0, sizeof(int)));
         PPG_CK(cudaMemset(c->ilu_vec, 0, sizeof(double) * 5 * c->ld));
-        c->ilu_epoch = 0;
         // factorisation on the device, one launch per level of the lower triangle
         if (nnz > 0) PPG_CK(cudaMemcpyAsync(c->d_lu64, c->d_vals, sizeof(double) * nnz, cudaMemcpyDeviceToDevice,
                                             c->stream));
@@ -2043,6 +2044,8 @@ ppg_status ppg_set_left_ilu0(ppg_ctx *c, int enable, double *lu_out)
         if (nnz > 0)
             PPG_CK(cudaMemcpyAsync(lu.data(), c->d_lu64, sizeof(double) * nnz, cudaMemcpyDeviceToHost, c->stream));
         PPG_CK(cudaStreamSynchronize(c->stream));
+        std::vector<double> rd64(n);
+        std::vector<float> rd32(n);
         for (long long i = 0; i < n; ++i) {
             const double d = lu[diag[i]];
             if (!(d != 0.0) || !std::isfinite(d)) {
@@ -2050,7 +2053,17 @@ ppg_status ppg_set_left_ilu0(ppg_ctx *c, int enable, double *lu_out)
                 c->d_lu64 = nullptr;
                 return fail(PPG_ERR_POLY_BREAKDOWN, "ILU(0) breaks down: pivot %lld is %g", i, d);
             }
+            rd64[i] = 1.0 / d;
+            rd32[i] = (float)rd64[i];
         }
+        PPG_CK(cudaMalloc(&c->d_ilu_rd64, sizeof(double) * n));
+        PPG_CK(cudaMalloc(&c->d_ilu_rd32, sizeof(float) * n));
+        PPG_CK(cudaMemcpy(c->d_ilu_rd64, rd64.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+        PPG_CK(cudaMemcpy(c->d_ilu_rd32, rd32.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+        int longest = 1;
+        for (long long i = 0; i < n; ++i) longest = std::max(longest, rp[i + 1] - rp[i]);
+        c->ilu_red = 1;
+        while (c->ilu_red < longest && c->ilu_red < 32) c->ilu_red *= 2;
     }
     const int on = enable ? 1 : 0;
     if (on != c->ilu_on) {

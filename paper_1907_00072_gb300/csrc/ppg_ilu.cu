@@ -10,11 +10,16 @@
 // separately, as in a plain IEEE evaluation of the same loops.
 //
 // Triangular solves: one cooperative launch (every CTA resident) where each group of lanes takes a row
-// from the level-sorted list in order, waits -- with a time limit -- for the rows its row depends on
-// (a per-row ready word set to this solve's epoch with release semantics), forms the row and
-// publishes it.  A row's dependencies are earlier in the list and every warp walks the
-// list in order, so the earliest unfinished row can always proceed; no level barriers.
+// from the level-sorted list in order, waits -- with a time limit -- for the rows its row depends on,
+// forms the row and publishes it.  The solution vector is its own ready mark: a fill launch sets every
+// entry to a signalling-NaN pattern that no arithmetic produces, a row's result replaces it with one
+// store, and a waiting lane polls the entry itself, so the value arrives with the load that sees it
+// ready (one L2 round trip per dependency instead of a flag and then the value).  A row's
+// dependencies are earlier in the list and every warp walks the list in order, so the earliest
+// unfinished row can always proceed; no level barriers.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "ppg_internal.h"
 
@@ -58,16 +63,53 @@ __global__ void k_ilu_cast(const double *__restrict__ in, float *__restrict__ ou
         out[q] = (float)in[q];
 }
 
-__device__ __forceinline__ int ilu_ld_acquire(const int *p)
+// Bit patterns of a pending entry (a signalling NaN: arithmetic only returns quiet NaNs) and of the
+// quiet NaN stored in its place should a result ever have the pending pattern.
+template <typename T>
+struct IluBits;
+template <>
+struct IluBits<float> {
+    using U = unsigned int;
+    static constexpr U kPending = 0x7FA11CE5u;
+    static constexpr U kQuietNaN = 0x7FFFFFFFu;
+    static __device__ __forceinline__ U bits(float v) { return __float_as_uint(v); }
+    static __device__ __forceinline__ float value(U b) { return __uint_as_float(b); }
+};
+template <>
+struct IluBits<double> {
+    using U = unsigned long long;
+    static constexpr U kPending = 0x7FF4A11CE5A11CE5ull;
+    static constexpr U kQuietNaN = 0x7FFFFFFFFFFFFFFFull;
+    static __device__ __forceinline__ U bits(double v) { return (U)__double_as_longlong(v); }
+    static __device__ __forceinline__ double value(U b) { return __longlong_as_double((long long)b); }
+};
+
+__device__ __forceinline__ unsigned int ilu_ld(const unsigned int *p)
 {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-
-__device__ __forceinline__ void ilu_st_release(int *p, int v)
+__device__ __forceinline__ unsigned long long ilu_ld(const unsigned long long *p)
 {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void ilu_st(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void ilu_st(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <typename T>
+__global__ void k_ilu_pending(typename IluBits<T>::U *y, long long n)
+{
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        y[q] = IluBits<T>::kPending;
 }
 
 // G lanes per row (the row walked in passes of G entries): a warp takes 32 / G consecutive rows of
@@ -82,9 +124,12 @@ __global__ void __launch_bounds__(kThreads) k_ilu_solve(IluSolveArgs a)
         (a.check == kSkipIfStop && st->stop))
         return;
     constexpr int R = 32 / G;
+    using B = IluBits<T>;
+    using U = typename B::U;
     const T *lu = static_cast<const T *>(a.lu);
+    const T *rd = static_cast<const T *>(a.rdiag);
     const T *xin = resolve_ptr<T>(a.x, st);
-    T *y = static_cast<T *>(a.y);
+    U *yb = static_cast<U *>(a.y);
     T *o0 = resolve_ptr<T>(a.e.out0, st);
     const T *u0 = resolve_ptr<T>(a.e.u0, st);
     const T *w0 = resolve_ptr<T>(a.e.w0, st);
@@ -97,51 +142,50 @@ __global__ void __launch_bounds__(kThreads) k_ilu_solve(IluSolveArgs a)
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (sub * G));
     const long long W = (long long)gridDim.x * (blockDim.x >> 5);
     const long long wg = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int epoch = a.epoch + a.need_ahead;
-    // the next row's list entry and bounds are loaded a step ahead (they do not depend on other rows)
+    // the next row's list entry, bounds and pivot reciprocal are loaded a step ahead (they do not depend
+    // on other rows)
     int ni = 0, ne0 = 0, ne1 = 0;
+    T nrd = T(0);
     if (wg * R + sub < a.n) {
         ni = a.order[wg * R + sub];
         ne0 = a.rp[ni];
         ne1 = a.rp[ni + 1];
+        if (!LOWER) nrd = rd[ni];
     }
     for (long long q0 = wg * R; q0 < a.n; q0 += W * R) {
         const long long q = q0 + sub;
         bool ok = true;
         const int i = ni, e0 = ne0, e1 = ne1;
+        const T rdi = nrd;
         if (q + W * R < a.n) {
             ni = a.order[q + W * R];
             ne0 = a.rp[ni];
             ne1 = a.rp[ni + 1];
+            if (!LOWER) nrd = rd[ni];
         }
         if (q < a.n) {
-            T sum = T(0), dg = T(0);
+            T sum = T(0);
             for (int e = e0 + gl; e < e1; e += G) {
                 const int k = a.ci[e];
                 if (LOWER ? (k < i) : (k > i)) {
-                    if (ilu_ld_acquire(a.flags + k) != epoch) {
+                    U v = ilu_ld(yb + k);
+                    if (v == B::kPending || a.unreachable) {
                         const unsigned long long t0 = global_timer_ns();
-                        for (unsigned int spins = 1; ilu_ld_acquire(a.flags + k) != epoch; ++spins) {
+                        for (unsigned int spins = 1; (v = ilu_ld(yb + k)) == B::kPending || a.unreachable; ++spins) {
                             if ((spins & 63u) == 0 && global_timer_ns() - t0 > a.wait_ns) {
                                 ok = false;
                                 break;
                             }
                         }
                     }
-                    if (ok) sum = fma(lu[e], y[k], sum);
-                } else if (!LOWER && k == i) {
-                    dg = lu[e];
+                    if (ok) sum = fma(lu[e], B::value(v), sum);
                 }
             }
             ok = __all_sync(gmask, ok);
-#pragma unroll
-            for (int o = G >> 1; o > 0; o >>= 1) {
-                sum += __shfl_xor_sync(gmask, sum, o);
-                if (!LOWER) dg += __shfl_xor_sync(gmask, dg, o);
-            }
+            // lanes at or above the longest row hold zero: reduce over the first a.red lanes only
+            for (int o = min(a.red, G) >> 1; o > 0; o >>= 1) sum += __shfl_xor_sync(gmask, sum, o);
             if (ok && gl == 0) {
-                const T yi = LOWER ? xin[i] - sum : (xin[i] - sum) / dg;
-                y[i] = yi;
+                const T yi = LOWER ? xin[i] - sum : (xin[i] - sum) * rdi;
                 if (o0) {
                     T v = ca0 * yi;
                     if (u0) v = fma(cb0, u0[i], v);
@@ -154,7 +198,8 @@ __global__ void __launch_bounds__(kThreads) k_ilu_solve(IluSolveArgs a)
                     if (w1) v = fma(cc1, w1[i], v);
                     o1[i] = v;
                 }
-                ilu_st_release(a.flags + i, a.epoch);  // orders this lane's stores of y and the outputs before it
+                const U ub = B::bits(yi);
+                ilu_st(yb + i, ub == B::kPending ? B::kQuietNaN : ub);  // the value is the row's ready mark
             }
         }
         if (__any_sync(0xffffffffu, !ok)) {
@@ -186,6 +231,13 @@ cudaError_t ilu_solve_go(const IluSolveArgs &a, int num_sms, cudaStream_t s)
 // CTAs per SM were slower.
 cudaError_t launch_ilu_solve(int prec, bool lower, const IluSolveArgs &a, int num_sms, cudaStream_t s)
 {
+    const unsigned fill_grid = (unsigned)std::min<long long>(((long long)a.n + kThreads - 1) / kThreads, 8LL * num_sms);
+    if (prec == kF64)
+        k_ilu_pending<double><<<fill_grid, kThreads, 0, s>>>(static_cast<IluBits<double>::U *>(a.y), a.n);
+    else
+        k_ilu_pending<float><<<fill_grid, kThreads, 0, s>>>(static_cast<IluBits<float>::U *>(a.y), a.n);
+    const cudaError_t fe = cudaGetLastError();
+    if (fe != cudaSuccess) return fe;
     if (prec == kF64)
         return lower ? ilu_solve_go<double, true, 32>(a, num_sms, s) : ilu_solve_go<double, false, 32>(a, num_sms, s);
     return lower ? ilu_solve_go<float, true, 32>(a, num_sms, s) : ilu_solve_go<float, false, 32>(a, num_sms, s);

@@ -197,8 +197,9 @@ cudaError_t launch_ilu0_level(const int *rows, int count, const int *rp, const i
                               cudaStream_t s);
 cudaError_t launch_ilu_cast(const double *in, float *out, long long count, cudaStream_t s);
 // A triangular solve with the factors: lower: y = L^{-1} x (unit diagonal); upper: y = U^{-1} x.
-// order: the rows sorted by their level for this triangle; flags: one int per row, the solve's epoch
-// once the row is final (ints from earlier epochs are stale).  The epilogue e (its x, x2 unused)
+// order: the rows sorted by their level for this triangle; y (n entries of the solve's type) is set
+// to a pending pattern by the launch and each entry, once written, marks its row final.  The epilogue
+// e (its x, x2 unused)
 // is applied per row to y: out0 = a0 y + b0 u0 + c0 w0, out1 likewise.  abort: one int, zero; a wait
 // that runs out stores there 1 + the row it was computing (the first such row wins) and stops the cycle.
 struct IluSolveArgs {
@@ -206,16 +207,16 @@ struct IluSolveArgs {
     const int *rp, *ci;
     const void *lu;     // factors in the solve's value type
     const int *order;
-    int *flags;
-    int epoch;
     int *abort;
     VecRef x;           // input
     void *y;            // the solution (also read by later rows)
     SpmvEpi e;
     Cycle *st;
     int check;          // Check
-    unsigned long long wait_ns;  // limit of one wait on a ready word
-    int need_ahead;     // tests of the failure path: waits expect epoch + need_ahead (0 normally)
+    const void *rdiag;  // 1 / u_ii in the solve's value type (upper solve)
+    int red;            // a power of two <= 32 and >= the longest row: lanes a row's sum is reduced over
+    unsigned long long wait_ns;  // limit of one wait on a row the row depends on
+    int unreachable;    // tests of the failure path: 1 makes every such wait treat the row as not ready
 };
 cudaError_t launch_ilu_solve(int prec, bool lower, const IluSolveArgs &a, int num_sms, cudaStream_t s);
 

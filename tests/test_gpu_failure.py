@@ -6,7 +6,7 @@ Every wait in the library is bounded.  These tests make two of them run out with
   * the host's wait for the device's progress between enqueued iterations, with a 1 us limit on a
     system whose first iteration takes hundreds of microseconds.
   * the ILU(0) triangular solves' waits on the rows a row depends on, with the same test switch (every
-    wait expects a mark that no row of the solve writes) and a 2 ms limit.
+    wait treats the row it waits on as not ready) and a 2 ms limit.
 Each solve must return PPG_ERR_TIMEOUT with a record of where the wait gave up, and the next solve
 on the same context, with the default limits, must converge.
 """
