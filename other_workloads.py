@@ -188,6 +188,8 @@ def run_c4(args):
         "systems_per_s": round(len(systems) / (ms * 1e-3), 1), "status": status,
         "ctas_per_system": stats[0]["ctas_per_system"], "spmv_lanes_by_rows_per_cta": lanes_by_class,
         "iterations_total": int(sum(iters)),
+        "slowest_system_ms": round(max(st["spmv_ms"] for st in stats), 3),
+        "last_start_ms": round(max(st["gs_ms"] for st in stats), 3),
         "iterations_min_max": [int(min(iters)), int(max(iters))], "relres_max_host": max(rr),
         "all_converged": bool(all(st["converged"] for st in stats)), "host_generation_s": round(gen_s, 2),
         "roofline": {"bound": "hbm", "kernel": "k_batch (one cluster per system)", "algorithmic_bytes": tot,
