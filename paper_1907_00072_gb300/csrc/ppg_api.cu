@@ -1318,12 +1318,16 @@ struct BatchCache {
     int *order_d = nullptr;
     BatchOut *out_d = nullptr;
     int cap_sys = 0;
-    cudaStream_t stream = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
-    // autotuner: per batch shape (the sorted (n, nnz) list, degree and restart), the cluster size
-    // and the SpMV's threads per row of each size class
+    cudaStream_t stream = nullptr, stream2 = nullptr;  // stream2: the small systems' launch of a split batch
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr, ev_fork = nullptr, ev_join = nullptr;
+    // autotuner: per batch shape (the sorted (n, nnz) list, degree and restart), the cluster size, and
+    // optionally a split: systems with at least big_rows rows run in clusters of `cluster`, the others in
+    // clusters of `cluster2` (a second launch, concurrent with the first); and the SpMV's threads per row
+    // of each class of rows per CTA
     struct Tuned {
         int cluster = 0;
+        int cluster2 = 0;
+        long long big_rows = 0;  // 0: one launch, every system in clusters of `cluster`
         int lanes[3] = {1, 1, 1};
     };
     std::map<std::vector<long long>, Tuned> tuned;
@@ -1347,8 +1351,11 @@ ppg_status batch_setup(BatchCache &bc, int nsys)
     if (!bc.configured) {
         PPG_CK(batch_configure());
         PPG_CK(cudaStreamCreateWithFlags(&bc.stream, cudaStreamNonBlocking));
+        PPG_CK(cudaStreamCreateWithFlags(&bc.stream2, cudaStreamNonBlocking));
         PPG_CK(cudaEventCreateWithFlags(&bc.ev_in, cudaEventDisableTiming));
         PPG_CK(cudaEventCreateWithFlags(&bc.ev_out, cudaEventDisableTiming));
+        PPG_CK(cudaEventCreateWithFlags(&bc.ev_fork, cudaEventDisableTiming));
+        PPG_CK(cudaEventCreateWithFlags(&bc.ev_join, cudaEventDisableTiming));
         PPG_CK(cudaEventCreate(&bc.t0));
         PPG_CK(cudaEventCreate(&bc.t1));
         bc.configured = true;
@@ -2233,6 +2240,38 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
         const long long rpc = (n + cluster - 1) / cluster;
         return rpc < kThreads ? 0 : (rpc < 8 * kThreads ? 1 : 2);
     };
+    auto cluster_of = [&](int i, const BatchCache::Tuned &t) {
+        return (t.big_rows > 0 && sys_h[i].n < t.big_rows) ? t.cluster2 : t.cluster;
+    };
+    // the systems of ord with the large ones (>= big_rows) first, each part in ord's order; returns
+    // how many are large
+    auto arrange = [&](const std::vector<int> &ord, long long big_rows, std::vector<int> &out) {
+        out.clear();
+        if (big_rows <= 0) {
+            out = ord;
+            return (int)ord.size();
+        }
+        for (int i : ord)
+            if (sys_h[i].n >= big_rows) out.push_back(i);
+        const int split = (int)out.size();
+        for (int i : ord)
+            if (sys_h[i].n < big_rows) out.push_back(i);
+        return split;
+    };
+    // the launch(es) of a batch arranged as above: the first `split` systems in clusters of c1 on s1, the
+    // rest in clusters of c2 on the second stream, joined back into s1
+    auto launch_arranged = [&](const BatchSys *sysd, const int *ordd, int cnt, int split, int c1, int c2,
+                               const BatchParams &pp, cudaStream_t s1) -> cudaError_t {
+        if (split >= cnt) return launch_batch(sysd, ordd, cnt, c1, pp, bc.out_d, s1);
+        if (split <= 0) return launch_batch(sysd, ordd, cnt, c2, pp, bc.out_d, s1);
+        cudaError_t e = cudaEventRecord(bc.ev_fork, s1);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(bc.stream2, bc.ev_fork, 0);
+        if (e == cudaSuccess) e = launch_batch(sysd, ordd, split, c1, pp, bc.out_d, s1);
+        if (e == cudaSuccess) e = launch_batch(sysd, ordd + split, cnt - split, c2, pp, bc.out_d, bc.stream2);
+        if (e == cudaSuccess) e = cudaEventRecord(bc.ev_join, bc.stream2);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s1, bc.ev_join, 0);
+        return e;
+    };
     auto it_t = bc.tuned.find(shape);
     if (it_t == bc.tuned.end()) {
         BatchCache::Tuned tb;
@@ -2240,18 +2279,22 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
         for (int i = 0; i < nsys; ++i) ht[i].x = xscratch[i];
         BatchParams tp = prm;
         const long long short_maxit = std::max(1, std::min(maxit, std::max(1, restart / 2)));
-        // one timed solve of the systems listed in ord (x reset to the caller's x0 first)
-        auto timed = [&](const std::vector<int> &ord, int cluster, int reps, float *ms) -> ppg_status {
+        // one timed solve of the systems listed in ord (x reset to the caller's x0 first) in the
+        // configuration t, with the threads per row already set in ht
+        std::vector<int> arranged;
+        auto timed = [&](const std::vector<int> &ord, const BatchCache::Tuned &t, int reps, float *ms) -> ppg_status {
+            const int split = arrange(ord, t.big_rows, arranged);
             PPG_CK(cudaMemcpyAsync(bc.tune_d, ht.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice, bc.stream));
-            PPG_CK(cudaMemcpyAsync(bc.tune_order_d, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice,
-                                   bc.stream));
+            PPG_CK(cudaMemcpyAsync(bc.tune_order_d, arranged.data(), sizeof(int) * arranged.size(),
+                                   cudaMemcpyHostToDevice, bc.stream));
             float best = 0.f;
             for (int rep = 0; rep < reps; ++rep) {  // short runs: the first one also warms caches
                 for (int i : ord)
                     PPG_CK(cudaMemcpyAsync(xscratch[i], sys_h[i].x, sizeof(double) * sys_h[i].n,
                                            cudaMemcpyDeviceToDevice, bc.stream));
                 PPG_CK(cudaEventRecord(bc.t0, bc.stream));
-                PPG_CK(launch_batch(bc.tune_d, bc.tune_order_d, (int)ord.size(), cluster, tp, bc.out_d, bc.stream));
+                PPG_CK(launch_arranged(bc.tune_d, bc.tune_order_d, (int)arranged.size(), split, t.cluster, t.cluster2,
+                                       tp, bc.stream));
                 PPG_CK(cudaEventRecord(bc.t1, bc.stream));
                 PPG_CK(cudaEventSynchronize(bc.t1));
                 PPG_CK(cudaEventElapsedTime(&best, bc.t0, bc.t1));
@@ -2259,47 +2302,72 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
             *ms = best;
             return PPG_OK;
         };
+        // candidates: every system in clusters of 4, 8 or 16; or the systems of at least 16384 / 65536
+        // rows in clusters of 16 and the others, in a concurrent launch, in clusters of 4 or 8
+        std::vector<BatchCache::Tuned> cands;
+        for (int cl : {4, 8, 16}) {
+            BatchCache::Tuned t;
+            t.cluster = t.cluster2 = cl;
+            cands.push_back(t);
+        }
+        for (long long big : {16384LL, 65536LL}) {
+            int nbig = 0;
+            for (int i = 0; i < nsys; ++i) nbig += sys_h[i].n >= big ? 1 : 0;
+            if (nbig == 0 || nbig == nsys) continue;
+            for (int c2 : {4, 8}) {
+                BatchCache::Tuned t;
+                t.cluster = 16;
+                t.cluster2 = c2;
+                t.big_rows = big;
+                cands.push_back(t);
+            }
+        }
         float best_ms = 0.f;
         tp.maxit = maxit;
-        for (int cl : {4, 8, 16}) {
-            if (batch_max_clusters(cl) < 1) continue;
-            for (int i = 0; i < nsys; ++i) ht[i].lanes = cls_of(sys_h[i].n, cl) == 0 ? 2 : 1;
+        for (const BatchCache::Tuned &t : cands) {
+            if (batch_max_clusters(t.cluster) < 1 || batch_max_clusters(t.cluster2) < 1) continue;
+            for (int i = 0; i < nsys; ++i) ht[i].lanes = cls_of(sys_h[i].n, cluster_of(i, t)) == 0 ? 2 : 1;
             float ms = 0.f;
-            PPG_TRY(timed(order, cl, 1, &ms));
+            PPG_TRY(timed(order, t, 1, &ms));
             if (!tb.cluster || ms < best_ms) {
-                tb.cluster = cl;
+                tb = t;
                 best_ms = ms;
             }
         }
         if (!tb.cluster) return fail(PPG_ERR_CUDA, "no cluster size is launchable for the batched solver");
+        for (int i = 0; i < nsys; ++i) ht[i].lanes = cls_of(sys_h[i].n, cluster_of(i, tb)) == 0 ? 2 : 1;
         tp.maxit = short_maxit;
         for (int c = 0; c < 3; ++c) {
             std::vector<int> sub;
             for (int i : order)
-                if (cls_of(sys_h[i].n, tb.cluster) == c) sub.push_back(i);
+                if (cls_of(sys_h[i].n, cluster_of(i, tb)) == c) sub.push_back(i);
             if (sub.empty()) continue;
             float cbest = 0.f;
             for (int lanes : {1, 2, 4, 8}) {
                 if (c == 2 && lanes > 2) continue;  // long row blocks: one or two threads per row
                 for (int i : sub) ht[i].lanes = lanes;
                 float ms = 0.f;
-                PPG_TRY(timed(sub, tb.cluster, 2, &ms));
+                PPG_TRY(timed(sub, tb, 2, &ms));
                 if (lanes == 1 || ms < cbest) {
                     tb.lanes[c] = lanes;
                     cbest = ms;
                 }
             }
+            for (int i : sub) ht[i].lanes = tb.lanes[c];
         }
         it_t = bc.tuned.emplace(shape, tb).first;
     }
     const BatchCache::Tuned &tb = it_t->second;
     bc.cluster = tb.cluster;
-    for (int i = 0; i < nsys; ++i) hs[i].lanes = tb.lanes[cls_of(sys_h[i].n, tb.cluster)];
+    for (int i = 0; i < nsys; ++i) hs[i].lanes = tb.lanes[cls_of(sys_h[i].n, cluster_of(i, tb))];
+    std::vector<int> arranged_final;
+    const int split = arrange(order, tb.big_rows, arranged_final);
     PPG_CK(cudaMemcpyAsync(bc.sys_d, hs.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice, bc.stream));
+    PPG_CK(cudaMemcpyAsync(bc.order_d, arranged_final.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, bc.stream));
 
     // the solve itself: one launch, captured once as a graph and replayed
-    std::vector<long long> key = {(long long)(uintptr_t)bc.sys_d, nsys, bc.cluster, degree, restart, maxit,
-                                  (long long)seed};
+    std::vector<long long> key = {(long long)(uintptr_t)bc.sys_d, nsys, tb.cluster, tb.cluster2, tb.big_rows,
+                                  split, degree, restart, maxit, (long long)seed};
     double tolbits;
     memcpy(&tolbits, &tol, sizeof tol);
     key.push_back((long long)tolbits);
@@ -2308,7 +2376,8 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
         bc.exec = nullptr;
         cudaGraph_t graph = nullptr;
         PPG_CK(cudaStreamBeginCapture(bc.stream, cudaStreamCaptureModeThreadLocal));
-        const cudaError_t le = launch_batch(bc.sys_d, bc.order_d, nsys, bc.cluster, prm, bc.out_d, bc.stream);
+        const cudaError_t le = launch_arranged(bc.sys_d, bc.order_d, nsys, split, tb.cluster, tb.cluster2, prm,
+                                               bc.stream);
         const cudaError_t ce = cudaStreamEndCapture(bc.stream, &graph);
         if (le != cudaSuccess || ce != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -2348,7 +2417,7 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
             st.degree_used = o.degree;
             st.converged = o.converged;
             st.breakdowns = o.breakdowns;
-            st.ctas_per_system = bc.cluster;
+            st.ctas_per_system = cluster_of(i, tb);
             st.spmv_lanes = hs[i].lanes;
             st.time_ms = ms;
             st.spmv_ms = (double)(o.t_end - o.t_start) * 1e-6;  // this system's own time on the device

@@ -72,7 +72,7 @@ def test_batched_at_the_configuration_extremes():
     assert status == ppg.PPG_OK
     assert stats[0]["ctas_per_system"] in (4, 8, 16)
     for i, ((a, b), sysi, st) in enumerate(zip(mats, systems, stats)):
-        assert st["ctas_per_system"] == stats[0]["ctas_per_system"] and st["spmv_lanes"] in (1, 2, 4, 8)
+        assert st["ctas_per_system"] in (4, 8, 16) and st["spmv_lanes"] in (1, 2, 4, 8)
         xb = sysi[4].cpu().numpy()
         assert st["converged"] == 1 and st["degree_used"] == 15
         assert _relres(a, b, xb) <= 1e-8
