@@ -25,6 +25,19 @@ namespace cg = cooperative_groups;
 
 namespace ppg {
 
+#ifndef PPG_BATCH_DOT_RU
+#define PPG_BATCH_DOT_RU 2  // rows per sweep of the float32 block inner products
+#endif
+#ifndef PPG_BATCH_MIN_BLOCKS
+#define PPG_BATCH_MIN_BLOCKS 4  // CTAs per SM the register allocation is sized for
+#endif
+#ifndef PPG_BATCH_SPMV_U
+#define PPG_BATCH_SPMV_U 4  // rows a thread group of the batched SpMV walks together
+#endif
+#ifndef PPG_BATCH_SPMV_E
+#define PPG_BATCH_SPMV_E 2  // entries of each of those rows whose loads are issued together (float32 values)
+#endif
+
 constexpr int kBMaxM = 40;      // restart length
 constexpr int kBMaxRoots = 32;  // degree + 1
 constexpr int kBChunk = 16;     // columns reduced per sweep
@@ -74,17 +87,26 @@ __device__ void cluster_reduce(cg::cluster_group &cl, BShared &s, int cnt, int &
 template <typename T>
 __device__ void cta_dots(BShared &s, int buf, const T *V, long long ld, int k, const T *v, int r0, int r1, bool norm)
 {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, bd = blockDim.x;
+    // float32: a thread takes two of its rows per sweep (the same rows in the same order as one at a
+    // time, so the sums are unchanged) to keep twice the loads in flight
+    constexpr int RU = sizeof(T) == 4 ? PPG_BATCH_DOT_RU : 1;
     for (int c0 = 0; c0 < k; c0 += kBChunk) {
         const int cn = min(kBChunk, k - c0);
         T acc[kBChunk];
 #pragma unroll
         for (int q = 0; q < kBChunk; ++q) acc[q] = T(0);
-        for (int r = r0 + tid; r < r1; r += blockDim.x) {
-            const T vr = v[r];
+        for (int r = r0 + tid; r < r1; r += RU * bd) {
 #pragma unroll
-            for (int q = 0; q < kBChunk; ++q)
-                if (q < cn) acc[q] = fma(V[(long long)(c0 + q) * ld + r], vr, acc[q]);
+            for (int u = 0; u < RU; ++u) {
+                const int ru = r + u * bd;
+                if (u == 0 || ru < r1) {
+                    const T vr = v[ru];
+#pragma unroll
+                    for (int q = 0; q < kBChunk; ++q)
+                        if (q < cn) acc[q] = fma(V[(long long)(c0 + q) * ld + ru], vr, acc[q]);
+                }
+            }
         }
 #pragma unroll
         for (int q = 0; q < kBChunk; ++q) {
@@ -120,11 +142,32 @@ __device__ void cta_dots(BShared &s, int buf, const T *V, long long ld, int k, c
 template <typename T>
 __device__ void cta_update(const T *coef, const T *V, long long ld, int k, const T *w, T *out, int r0, int r1)
 {
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        T acc = w ? w[r] : T(0);
-#pragma unroll 8
-        for (int c = 0; c < k; ++c) acc = fma(-coef[c], V[(long long)c * ld + r], acc);
-        out[r] = acc;
+    // four rows per thread and sweep: their column loads are in flight together (each row's sum runs
+    // over the columns in the same order as before)
+    constexpr int RU = 4;
+    const int bd = blockDim.x;
+    for (int base = r0 + threadIdx.x; base < r1; base += RU * bd) {
+        T acc[RU];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int r = base + u * bd;
+            acc[u] = (w && r < r1) ? w[r] : T(0);
+        }
+#pragma unroll 4
+        for (int c = 0; c < k; ++c) {
+            const T cc = -coef[c];
+            const T *Vc = V + (long long)c * ld;
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                const int r = base + u * bd;
+                if (r < r1) acc[u] = fma(cc, Vc[r], acc[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int r = base + u * bd;
+            if (r < r1) out[r] = acc[u];
+        }
     }
 }
 
@@ -138,10 +181,12 @@ __device__ void cta_spmv_g(const int *rowptr, const int *colidx, const TV *vals,
                            const T *x2, T s2, T *o0, T a0, const T *u0, T b0, const T *w0, T c0, T *o1, T a1,
                            const T *u1, T b1, const T *w1, T c1)
 {
-    // each group takes U rows per sweep and walks their entries together, so that U independent
-    // index/value loads and U gathers are in flight per step (the rows are short: latency, not
-    // arithmetic, is what a small CTA group waits on)
-    constexpr int U = 4;
+    // each group takes U rows per sweep and walks their entries E at a time: the U x E index/value
+    // loads are issued together, then the U x E gathers, so that a sweep waits on two loads in a row
+    // per E entries instead of two per entry (the rows are short: latency, not arithmetic, is what a
+    // small CTA group waits on).  Each row's entries are still summed in their order.
+    constexpr int U = PPG_BATCH_SPMV_U;
+    constexpr int E = sizeof(TV) == 4 ? PPG_BATCH_SPMV_E : (PPG_BATCH_SPMV_E > 2 ? PPG_BATCH_SPMV_E / 2 : 1);
     const int per = blockDim.x / G, grp = threadIdx.x / G, g = threadIdx.x % G;
     for (int base = r0; base < r1; base += per * U) {
         int ks[U], ke[U];
@@ -153,19 +198,34 @@ __device__ void cta_spmv_g(const int *rowptr, const int *colidx, const TV *vals,
             ke[u] = r < r1 ? rowptr[r + 1] : 0;
             acc[u] = T(0);
         }
-        for (int t = 0;; t += G) {
+        for (int t = 0;; t += G * E) {
+            int qi[U][E];
+            TV av[U][E];
             bool any = false;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int k = ks[u] + t;
-                if (k < ke[u]) {
-                    const int q = colidx[k];
-                    const T xv = x2 ? fma(s2, x2[q], x[q]) : x[q];
-                    acc[u] = fma((T)vals[k], xv, acc[u]);
-                    any = true;
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int k = ks[u] + t + e * G;
+                    qi[u][e] = -1;
+                    av[u][e] = TV(0);
+                    if (k < ke[u]) {
+                        qi[u][e] = colidx[k];
+                        av[u][e] = vals[k];
+                        any = true;
+                    }
                 }
-            }
             if (!any) break;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int q = qi[u][e];
+                    if (q >= 0) {
+                        const T xv = x2 ? fma(s2, x2[q], x[q]) : x[q];
+                        acc[u] = fma((T)av[u][e], xv, acc[u]);
+                    }
+                }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -360,10 +420,27 @@ __device__ void back_substitute(BShared &s, int k)
 // x += sum_{c<k} y_c Z_c on this CTA's rows (float32 Z, float64 x and y, float64 sums)
 __device__ void cta_xupdate_z(const float *Z, long long ld, int k, const double *y, double *x, int r0, int r1)
 {
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        double acc = 0.0;
-        for (int c = 0; c < k; ++c) acc = fma((double)Z[(long long)c * ld + r], y[c], acc);
-        x[r] += acc;
+    constexpr int RU = 4;  // rows per thread and sweep, as in cta_update
+    const int bd = blockDim.x;
+    for (int base = r0 + threadIdx.x; base < r1; base += RU * bd) {
+        double acc[RU];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) acc[u] = 0.0;
+#pragma unroll 2
+        for (int c = 0; c < k; ++c) {
+            const float *Zc = Z + (long long)c * ld;
+            const double yc = y[c];
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                const int r = base + u * bd;
+                if (r < r1) acc[u] = fma((double)Zc[r], yc, acc[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int r = base + u * bd;
+            if (r < r1) x[r] += acc[u];
+        }
     }
 }
 
@@ -374,7 +451,7 @@ __device__ __forceinline__ unsigned long long bmix(unsigned long long z)
     return z ^ (z >> 31);
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchSys *__restrict__ sys, const int *__restrict__ order,
+__global__ void __launch_bounds__(kThreads, PPG_BATCH_MIN_BLOCKS) k_batch(const BatchSys *__restrict__ sys, const int *__restrict__ order,
                                                     BatchParams p, BatchOut *out)
 {
     __shared__ BShared s;
@@ -572,21 +649,22 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchSys *__restric
             __syncthreads();
             // pass 2
             cta_update<float>(s.fcoef, V, ld, j + 1, w, w, r0, r1);
-            cta_dots<float>(s, buf, V, ld, j + 1, w, r0, r1, false);
-            cluster_reduce(cl, s, j + 1, buf);
-            if (tid == 0)
+            // (with ||w'||^2, so that pass 3 needs no reduction: ||v_{j+1}||^2 = ||w'||^2 - ||h2||^2)
+            cta_dots<float>(s, buf, V, ld, j + 1, w, r0, r1, true);
+            cluster_reduce(cl, s, j + 2, buf);
+            if (tid == 0) {
+                double h2sq = 0.0;
                 for (int c = 0; c <= j; ++c) {
                     s.h2[c] = s.sigma[c] * s.red[c];
+                    h2sq = fma(s.h2[c], s.h2[c], h2sq);
                     s.coef[c] = s.h2[c] * s.sigma[c];
                     s.fcoef[c] = (float)s.coef[c];
                 }
-            __syncthreads();
-            // pass 3: v_{j+1}
-            cta_update<float>(s.fcoef, V, ld, j + 1, w, V + (j + 1) * ld, r0, r1);
-            cta_dots<float>(s, buf, V + (j + 1) * ld, ld, 0, V + (j + 1) * ld, r0, r1, true);
-            cluster_reduce(cl, s, 1, buf);
-            if (tid == 0) {
-                const double nrm = sqrt(s.red[0]);
+                const double wpsq = s.red[j + 1], nsq = wpsq - h2sq;
+                // breakdown also when the second pass removed more than 99 % of ||w'||^2 (the difference
+                // of squares is no longer accurate there): the cycle ends and the restart carries on
+                const bool brk = !(nsq > 1e-28 * s.w0sq) || !(nsq > 1e-2 * wpsq);
+                const double nrm = !isfinite(nsq) ? nsq : (brk ? 0.0 : sqrt(nsq));
                 double *Rj = s.u.R + j * (kBMaxM + 1);
                 bool fin = isfinite(nrm);
                 for (int c = 0; c <= j; ++c) {
@@ -594,7 +672,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchSys *__restric
                     fin = fin && isfinite(Rj[c]);
                 }
                 Rj[j + 1] = nrm;
-                const bool brk = !(nrm > 1e-14 * sqrt(s.w0sq));
                 s.sigma[j + 1] = brk ? 0.0 : 1.0 / nrm;
                 for (int c = 0; c < j; ++c) {
                     const double a = Rj[c], b = Rj[c + 1];
@@ -626,6 +703,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchSys *__restric
                          s.iters >= p.maxit;
             }
             __syncthreads();
+            // pass 3: v_{j+1} = w' - V h2 (scaled by sigma_{j+1} where it is used), gathered next
+            cta_update<float>(s.fcoef, V, ld, j + 1, w, V + (j + 1) * ld, r0, r1);
+            csync(cl);
             kc = j + 1;
             if (s.done) break;
         }
