@@ -186,7 +186,10 @@ def run_c4(args):
         "batched_ms": round(ms, 3), "sequential_ms": None if seq_ms != seq_ms else round(seq_ms, 3),
         "speedup": None if seq_ms != seq_ms else round(seq_ms / ms, 2),
         "systems_per_s": round(len(systems) / (ms * 1e-3), 1), "status": status,
-        "ctas_per_system": stats[0]["ctas_per_system"], "spmv_lanes_by_rows_per_cta": lanes_by_class,
+        "ctas_per_system": stats[0]["ctas_per_system"],
+        "systems_by_ctas_per_system": {str(c): sum(1 for st in stats if st["ctas_per_system"] == c)
+                                       for c in sorted({st["ctas_per_system"] for st in stats})},
+        "spmv_lanes_by_rows_per_cta": lanes_by_class,
         "iterations_total": int(sum(iters)),
         "slowest_system_ms": round(max(st["spmv_ms"] for st in stats), 3),
         "last_start_ms": round(max(st["gs_ms"] for st in stats), 3),
