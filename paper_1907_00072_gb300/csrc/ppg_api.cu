@@ -2272,8 +2272,22 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s1, bc.ev_join, 0);
         return e;
     };
-    auto it_t = bc.tuned.find(shape);
-    if (it_t == bc.tuned.end()) {
+    // PPG_BATCH_CONFIG="cluster,cluster2,big_rows" in the environment fixes the configuration (threads
+    // per row: 2 for fewer than 256 rows per CTA, else 1) instead of tuning it; for tests and measurements
+    BatchCache::Tuned forced;
+    if (const char *env = getenv("PPG_BATCH_CONFIG")) {
+        long long c1 = 0, c2 = 0, big = 0;
+        if (sscanf(env, "%lld,%lld,%lld", &c1, &c2, &big) != 3 || (c1 != 4 && c1 != 8 && c1 != 16) ||
+            (c2 != 4 && c2 != 8 && c2 != 16) || big < 0)
+            return fail(PPG_ERR_INVALID_ARG, "PPG_BATCH_CONFIG must be \"cluster,cluster2,big_rows\" with "
+                                             "cluster sizes 4, 8 or 16");
+        forced.cluster = (int)c1;
+        forced.cluster2 = big > 0 ? (int)c2 : (int)c1;
+        forced.big_rows = big;
+        for (int c = 0; c < 3; ++c) forced.lanes[c] = c == 0 ? 2 : 1;
+    }
+    auto it_t = forced.cluster ? bc.tuned.end() : bc.tuned.find(shape);
+    if (!forced.cluster && it_t == bc.tuned.end()) {
         BatchCache::Tuned tb;
         std::vector<BatchSys> ht = hs;
         for (int i = 0; i < nsys; ++i) ht[i].x = xscratch[i];
@@ -2357,7 +2371,7 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
         }
         it_t = bc.tuned.emplace(shape, tb).first;
     }
-    const BatchCache::Tuned &tb = it_t->second;
+    const BatchCache::Tuned &tb = forced.cluster ? forced : it_t->second;
     bc.cluster = tb.cluster;
     for (int i = 0; i < nsys; ++i) hs[i].lanes = tb.lanes[cls_of(sys_h[i].n, cluster_of(i, tb))];
     std::vector<int> arranged_final;

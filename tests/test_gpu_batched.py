@@ -144,3 +144,37 @@ def test_batched_rejects_bad_arguments():
         ppg.ppg_solve_batched(systems, degree=40)
     with pytest.raises(ppg.PPGError):
         ppg.ppg_solve_batched(systems, restart=41)
+
+
+@pytest.mark.parametrize("config", ["16,4,16384", "8,4,4000", "4,16,16384"])
+def test_batched_split_launches_match_single_solves(config, monkeypatch):
+    """The configurations the tuner can choose, forced through PPG_BATCH_CONFIG: the large systems in
+    one launch and the others in a concurrent second launch with another cluster size (or one launch).
+    Every system reports its cluster size and matches its single solve."""
+    monkeypatch.setenv("PPG_BATCH_CONFIG", config)
+    c1, c2, big = (int(v) for v in config.split(","))
+    specs = [(200, 50.0), (150, 20.0), (90, 20.0), (64, 80.0), (32, 100.0), (40, 1.0)]
+    mats, systems = _batch(specs)
+    seed = 31
+    status, stats = ppg.ppg_solve_batched(systems, degree=10, tol=1e-8, restart=30, maxit=20000, seed=seed)
+    assert status == ppg.PPG_OK
+    for i, ((a, b), sysi, st) in enumerate(zip(mats, systems, stats)):
+        assert st["ctas_per_system"] == (c1 if a.n >= big else c2)
+        xb = sysi[4].cpu().numpy()
+        assert st["converged"] == 1 and _relres(a, b, xb) <= 1e-8
+        s = ppg.Solver(sysi[0], sysi[1], sysi[2])
+        s.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=None, seed=seed + i)
+        xs, info = s.solve(sysi[3], tol=1e-8, restart=30, maxit=20000, precision=ppg.PPG_F32)
+        xs = xs.cpu().numpy()
+        assert info.status == ppg.PPG_OK
+        assert np.linalg.norm(xb - xs) <= 1e-6 * np.linalg.norm(xs), i
+        assert abs(st["iterations"] - info.stats["iterations"]) <= max(2, 0.05 * info.stats["iterations"]), i
+        s.close()
+
+
+def test_batched_config_override_is_checked(monkeypatch):
+    monkeypatch.setenv("PPG_BATCH_CONFIG", "5,4,100")
+    mats, systems = _batch([(32, 10.0)])
+    with pytest.raises(ppg.PPGError) as e:
+        ppg.ppg_solve_batched(systems, degree=5, tol=1e-8, restart=20, seed=1)
+    assert e.value.status == ppg.PPG_ERR_INVALID_ARG
