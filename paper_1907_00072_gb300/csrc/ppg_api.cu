@@ -1328,6 +1328,7 @@ struct BatchCache {
         int cluster = 0;
         int cluster2 = 0;
         long long big_rows = 0;  // 0: one launch, every system in clusters of `cluster`
+        int threads = 256;       // threads per CTA of the (large systems') first launch
         int lanes[3] = {1, 1, 1};
     };
     std::map<std::vector<long long>, Tuned> tuned;
@@ -2261,29 +2262,32 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
     // the launch(es) of a batch arranged as above: the first `split` systems in clusters of c1 on s1, the
     // rest in clusters of c2 on the second stream, joined back into s1
     auto launch_arranged = [&](const BatchSys *sysd, const int *ordd, int cnt, int split, int c1, int c2,
-                               const BatchParams &pp, cudaStream_t s1) -> cudaError_t {
-        if (split >= cnt) return launch_batch(sysd, ordd, cnt, c1, pp, bc.out_d, s1);
+                               const BatchParams &pp, cudaStream_t s1, int t1) -> cudaError_t {
+        if (split >= cnt) return launch_batch(sysd, ordd, cnt, c1, pp, bc.out_d, s1, t1);
         if (split <= 0) return launch_batch(sysd, ordd, cnt, c2, pp, bc.out_d, s1);
         cudaError_t e = cudaEventRecord(bc.ev_fork, s1);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(bc.stream2, bc.ev_fork, 0);
-        if (e == cudaSuccess) e = launch_batch(sysd, ordd, split, c1, pp, bc.out_d, s1);
+        if (e == cudaSuccess) e = launch_batch(sysd, ordd, split, c1, pp, bc.out_d, s1, t1);
         if (e == cudaSuccess) e = launch_batch(sysd, ordd + split, cnt - split, c2, pp, bc.out_d, bc.stream2);
         if (e == cudaSuccess) e = cudaEventRecord(bc.ev_join, bc.stream2);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s1, bc.ev_join, 0);
         return e;
     };
-    // PPG_BATCH_CONFIG="cluster,cluster2,big_rows" in the environment fixes the configuration (threads
-    // per row: 2 for fewer than 256 rows per CTA, else 1) instead of tuning it; for tests and measurements
+    // PPG_BATCH_CONFIG="cluster,cluster2,big_rows[,threads]" in the environment fixes the configuration
+    // (threads per row: 2 for fewer than 256 rows per CTA, else 1) instead of tuning it; for tests and
+    // measurements
     BatchCache::Tuned forced;
     if (const char *env = getenv("PPG_BATCH_CONFIG")) {
-        long long c1 = 0, c2 = 0, big = 0;
-        if (sscanf(env, "%lld,%lld,%lld", &c1, &c2, &big) != 3 || (c1 != 4 && c1 != 8 && c1 != 16) ||
-            (c2 != 4 && c2 != 8 && c2 != 16) || big < 0)
-            return fail(PPG_ERR_INVALID_ARG, "PPG_BATCH_CONFIG must be \"cluster,cluster2,big_rows\" with "
-                                             "cluster sizes 4, 8 or 16");
+        long long c1 = 0, c2 = 0, big = 0, nt = 256;
+        const int got = sscanf(env, "%lld,%lld,%lld,%lld", &c1, &c2, &big, &nt);
+        if (got < 3 || (c1 != 4 && c1 != 8 && c1 != 16) || (c2 != 4 && c2 != 8 && c2 != 16) || big < 0 ||
+            (nt != 256 && nt != 512))
+            return fail(PPG_ERR_INVALID_ARG, "PPG_BATCH_CONFIG must be \"cluster,cluster2,big_rows[,threads]\" "
+                                             "with cluster sizes 4, 8 or 16 and 256 or 512 threads");
         forced.cluster = (int)c1;
         forced.cluster2 = big > 0 ? (int)c2 : (int)c1;
         forced.big_rows = big;
+        forced.threads = (int)nt;
         for (int c = 0; c < 3; ++c) forced.lanes[c] = c == 0 ? 2 : 1;
     }
     auto it_t = forced.cluster ? bc.tuned.end() : bc.tuned.find(shape);
@@ -2308,7 +2312,7 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
                                            cudaMemcpyDeviceToDevice, bc.stream));
                 PPG_CK(cudaEventRecord(bc.t0, bc.stream));
                 PPG_CK(launch_arranged(bc.tune_d, bc.tune_order_d, (int)arranged.size(), split, t.cluster, t.cluster2,
-                                       tp, bc.stream));
+                                       tp, bc.stream, t.threads));
                 PPG_CK(cudaEventRecord(bc.t1, bc.stream));
                 PPG_CK(cudaEventSynchronize(bc.t1));
                 PPG_CK(cudaEventElapsedTime(&best, bc.t0, bc.t1));
@@ -2328,18 +2332,20 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
             int nbig = 0;
             for (int i = 0; i < nsys; ++i) nbig += sys_h[i].n >= big ? 1 : 0;
             if (nbig == 0 || nbig == nsys) continue;
-            for (int c2 : {4, 8}) {
-                BatchCache::Tuned t;
-                t.cluster = 16;
-                t.cluster2 = c2;
-                t.big_rows = big;
-                cands.push_back(t);
-            }
+            for (int c2 : {4, 8})
+                for (int t1 : {256, 512}) {  // 512: twice the warps per large system, half the CTAs per SM
+                    BatchCache::Tuned t;
+                    t.cluster = 16;
+                    t.cluster2 = c2;
+                    t.big_rows = big;
+                    t.threads = t1;
+                    cands.push_back(t);
+                }
         }
         float best_ms = 0.f;
         tp.maxit = maxit;
         for (const BatchCache::Tuned &t : cands) {
-            if (batch_max_clusters(t.cluster) < 1 || batch_max_clusters(t.cluster2) < 1) continue;
+            if (batch_max_clusters(t.cluster, t.threads) < 1 || batch_max_clusters(t.cluster2) < 1) continue;
             for (int i = 0; i < nsys; ++i) ht[i].lanes = cls_of(sys_h[i].n, cluster_of(i, t)) == 0 ? 2 : 1;
             float ms = 0.f;
             PPG_TRY(timed(order, t, 1, &ms));
@@ -2381,7 +2387,7 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
 
     // the solve itself: one launch, captured once as a graph and replayed
     std::vector<long long> key = {(long long)(uintptr_t)bc.sys_d, nsys, tb.cluster, tb.cluster2, tb.big_rows,
-                                  split, degree, restart, maxit, (long long)seed};
+                                  tb.threads, split, degree, restart, maxit, (long long)seed};
     double tolbits;
     memcpy(&tolbits, &tol, sizeof tol);
     key.push_back((long long)tolbits);
@@ -2391,7 +2397,7 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
         cudaGraph_t graph = nullptr;
         PPG_CK(cudaStreamBeginCapture(bc.stream, cudaStreamCaptureModeThreadLocal));
         const cudaError_t le = launch_arranged(bc.sys_d, bc.order_d, nsys, split, tb.cluster, tb.cluster2, prm,
-                                               bc.stream);
+                                               bc.stream, tb.threads);
         const cudaError_t ce = cudaStreamEndCapture(bc.stream, &graph);
         if (le != cudaSuccess || ce != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);

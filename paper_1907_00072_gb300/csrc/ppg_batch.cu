@@ -41,6 +41,7 @@ namespace ppg {
 constexpr int kBMaxM = 40;      // restart length
 constexpr int kBMaxRoots = 32;  // degree + 1
 constexpr int kBChunk = 16;     // columns reduced per sweep
+constexpr int kBMaxWarps = 16;  // warps of the widest CTA (512 threads)
 constexpr int kBLdH = kBMaxRoots + 1;
 
 struct BShared {
@@ -59,7 +60,7 @@ struct BShared {
     double cs[kBMaxM], sn[kBMaxM], g[kBMaxM + 2], y[kBMaxM + 1];
     double part[2][kBMaxM + 2];
     double red[kBMaxM + 2];
-    double scratch[kBChunk * 8];
+    double scratch[kBChunk * kBMaxWarps];
     double roots[2 * kBMaxRoots], table[2 * kBMaxRoots];
     double beta, bnorm, w0sq, est, relres;
     int nroots, status, done, brk, kcols;
@@ -112,13 +113,13 @@ __device__ void cta_dots(BShared &s, int buf, const T *V, long long ld, int k, c
         for (int q = 0; q < kBChunk; ++q) {
             if (q < cn) {
                 const double t = warp_sum((double)acc[q]);
-                if (lane == 0) s.scratch[q * 8 + wid] = t;
+                if (lane == 0) s.scratch[q * kBMaxWarps + wid] = t;
             }
         }
         __syncthreads();
         if (tid < cn) {
             double t = 0.0;
-            for (int q = 0; q < 8; ++q) t += s.scratch[tid * 8 + q];
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s.scratch[tid * kBMaxWarps + q];
             s.part[buf][c0 + tid] = t;
         }
         __syncthreads();
@@ -131,7 +132,7 @@ __device__ void cta_dots(BShared &s, int buf, const T *V, long long ld, int k, c
         __syncthreads();
         if (tid == 0) {
             double t = 0.0;
-            for (int q = 0; q < 8; ++q) t += s.scratch[q];
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s.scratch[q];
             s.part[buf][k] = t;
         }
         __syncthreads();
@@ -357,7 +358,7 @@ __device__ void batch_residual_norm(cg::cluster_group &cl, BShared &s, int &buf,
     __syncthreads();
     if (tid == 0) {
         double t = 0.0;
-        for (int q = 0; q < 8; ++q) t += s.scratch[q];
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s.scratch[q];
         s.part[buf][0] = t;
     }
     __syncthreads();
@@ -394,13 +395,13 @@ __device__ void cta_dots_mixed(BShared &s, int buf, const float *V, long long ld
         for (int q = 0; q < kBChunk; ++q) {
             if (q < cn) {
                 const double t = warp_sum(acc[q]);
-                if (lane == 0) s.scratch[q * 8 + wid] = t;
+                if (lane == 0) s.scratch[q * kBMaxWarps + wid] = t;
             }
         }
         __syncthreads();
         if (tid < cn) {
             double t = 0.0;
-            for (int q = 0; q < 8; ++q) t += s.scratch[tid * 8 + q];
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s.scratch[tid * kBMaxWarps + q];
             s.part[buf][c0 + tid] = t;
         }
         __syncthreads();
@@ -451,8 +452,11 @@ __device__ __forceinline__ unsigned long long bmix(unsigned long long z)
     return z ^ (z >> 31);
 }
 
-__global__ void __launch_bounds__(kThreads, PPG_BATCH_MIN_BLOCKS) k_batch(const BatchSys *__restrict__ sys, const int *__restrict__ order,
-                                                    BatchParams p, BatchOut *out)
+// NT threads per CTA: 256, or 512 for large systems (more warps per system to hide the latency of
+// its loops; half as many CTAs per SM)
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? PPG_BATCH_MIN_BLOCKS : 2)
+    k_batch(const BatchSys *__restrict__ sys, const int *__restrict__ order, BatchParams p, BatchOut *out)
 {
     __shared__ BShared s;
     cg::cluster_group cl = cg::this_cluster();
@@ -573,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, PPG_BATCH_MIN_BLOCKS) k_batch(const 
         __syncthreads();
         if (tid == 0) {
             double t = 0.0;
-            for (int q = 0; q < 8; ++q) t += s.scratch[q];
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s.scratch[q];
             s.part[buf][0] = t;
         }
         __syncthreads();
@@ -771,15 +775,17 @@ cudaError_t launch_batch_cast(const BatchSys *sys_d, int nsys, cudaStream_t s)
 
 cudaError_t batch_configure()
 {
-    return cudaFuncSetAttribute(k_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e = cudaFuncSetAttribute(k_batch<256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch<512>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
 }
 
-// Number of clusters of `cluster` CTAs that can be resident at once (0: not launchable).
-int batch_max_clusters(int cluster)
+// Number of clusters of `cluster` CTAs of `threads` threads that can be resident at once (0: not launchable).
+int batch_max_clusters(int cluster, int threads)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cluster);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(threads);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cluster;
@@ -788,16 +794,17 @@ int batch_max_clusters(int cluster)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, (void *)k_batch, &cfg) != cudaSuccess) return 0;
+    const void *fn = threads == 512 ? (const void *)k_batch<512> : (const void *)k_batch<256>;
+    if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) != cudaSuccess) return 0;
     return nc;
 }
 
 cudaError_t launch_batch(const BatchSys *sys_d, const int *order_d, int nsys, int cluster, const BatchParams &p,
-                         BatchOut *out_d, cudaStream_t s)
+                         BatchOut *out_d, cudaStream_t s, int threads)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nsys * cluster));
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(threads == 512 ? 512 : 256);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -807,7 +814,8 @@ cudaError_t launch_batch(const BatchSys *sys_d, const int *order_d, int nsys, in
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch, sys_d, order_d, p, out_d);
+    if (threads == 512) return cudaLaunchKernelEx(&cfg, k_batch<512>, sys_d, order_d, p, out_d);
+    return cudaLaunchKernelEx(&cfg, k_batch<256>, sys_d, order_d, p, out_d);
 }
 
 }  // namespace ppg

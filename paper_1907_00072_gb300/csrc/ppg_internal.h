@@ -302,8 +302,8 @@ constexpr int kBatchMaxRestart = 40;
 constexpr int kBatchMaxDegree = 31;
 cudaError_t launch_batch_cast(const BatchSys *sys_d, int nsys, cudaStream_t s);
 cudaError_t launch_batch(const BatchSys *sys_d, const int *order_d, int nsys, int cluster, const BatchParams &p,
-                         BatchOut *out_d, cudaStream_t s);
-int batch_max_clusters(int cluster);
+                         BatchOut *out_d, cudaStream_t s, int threads = 256);
+int batch_max_clusters(int cluster, int threads = 256);
 cudaError_t batch_configure();
 
 // one-time kernel attribute setup (dynamic shared memory limits)

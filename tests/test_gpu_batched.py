@@ -146,13 +146,15 @@ def test_batched_rejects_bad_arguments():
         ppg.ppg_solve_batched(systems, restart=41)
 
 
-@pytest.mark.parametrize("config", ["16,4,16384", "8,4,4000", "4,16,16384"])
+@pytest.mark.parametrize("config", ["16,4,16384", "8,4,4000", "4,16,16384", "16,8,16384,512", "8,8,0,512"])
 def test_batched_split_launches_match_single_solves(config, monkeypatch):
     """The configurations the tuner can choose, forced through PPG_BATCH_CONFIG: the large systems in
     one launch and the others in a concurrent second launch with another cluster size (or one launch).
     Every system reports its cluster size and matches its single solve."""
     monkeypatch.setenv("PPG_BATCH_CONFIG", config)
-    c1, c2, big = (int(v) for v in config.split(","))
+    c1, c2, big = (int(v) for v in config.split(",")[:3])
+    if big == 0:
+        c2 = c1
     specs = [(200, 50.0), (150, 20.0), (90, 20.0), (64, 80.0), (32, 100.0), (40, 1.0)]
     mats, systems = _batch(specs)
     seed = 31
