@@ -347,9 +347,9 @@ typedef struct {
  * call with a new batch shape (the sorted list of (n, nnz), degree and restart) tunes the launch by
  * timing solves of the batch itself (x in scratch memory, so the caller's x is untouched): the CTAs
  * per system (the rows each CTA owns) -- 4, 8 or 16 for every system, or 16 (CTAs of 256 or 512
- * threads) for the systems of at least 16384 (or 65536) rows and 4 or 8 for the others, the two
- * groups then running as two concurrent launches -- then, per class of rows per CTA (< 256, < 2048,
- * more), the SpMV's threads per row (1, 2, 4 or 8); the choice is cached for the shape.
+ * threads) for the systems of at least 4096, 16384 or 65536 rows and 1, 2, 4 or 8 for the others, the
+ * two groups then running as two concurrent launches -- then, per class of rows per CTA (< 256,
+ * < 2048, more), the SpMV's threads per row (1, 2, 4 or 8); the choice is cached for the shape.
  * per_sys (host, nsys entries, may be NULL) receives each system's statistics (time_ms: the whole
  * batch; spmv_ms: the system's own time on the device, from its cluster's start to its end; gs_ms:
  * when that cluster started, after the first cluster's start; ctas_per_system: the system's tuned

@@ -2280,10 +2280,10 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
     if (const char *env = getenv("PPG_BATCH_CONFIG")) {
         long long c1 = 0, c2 = 0, big = 0, nt = 256;
         const int got = sscanf(env, "%lld,%lld,%lld,%lld", &c1, &c2, &big, &nt);
-        if (got < 3 || (c1 != 4 && c1 != 8 && c1 != 16) || (c2 != 4 && c2 != 8 && c2 != 16) || big < 0 ||
-            (nt != 256 && nt != 512))
+        auto size_ok = [](long long c) { return c == 1 || c == 2 || c == 4 || c == 8 || c == 16; };
+        if (got < 3 || !size_ok(c1) || !size_ok(c2) || big < 0 || (nt != 256 && nt != 512))
             return fail(PPG_ERR_INVALID_ARG, "PPG_BATCH_CONFIG must be \"cluster,cluster2,big_rows[,threads]\" "
-                                             "with cluster sizes 4, 8 or 16 and 256 or 512 threads");
+                                             "with cluster sizes 1, 2, 4, 8 or 16 and 256 or 512 threads");
         forced.cluster = (int)c1;
         forced.cluster2 = big > 0 ? (int)c2 : (int)c1;
         forced.big_rows = big;
@@ -2328,12 +2328,14 @@ ppg_status ppg_solve_batched(int nsys, const ppg_batch_system *sys_h, int degree
             t.cluster = t.cluster2 = cl;
             cands.push_back(t);
         }
-        for (long long big : {16384LL, 65536LL}) {
+        // (small systems in clusters of 1 or 2 CTAs synchronise with cheaper barriers)
+        for (long long big : {4096LL, 16384LL, 65536LL}) {
             int nbig = 0;
             for (int i = 0; i < nsys; ++i) nbig += sys_h[i].n >= big ? 1 : 0;
             if (nbig == 0 || nbig == nsys) continue;
-            for (int c2 : {4, 8})
+            for (int c2 : {1, 2, 4, 8})
                 for (int t1 : {256, 512}) {  // 512: twice the warps per large system, half the CTAs per SM
+                    if (t1 == 512 && big != 65536) continue;
                     BatchCache::Tuned t;
                     t.cluster = 16;
                     t.cluster2 = c2;

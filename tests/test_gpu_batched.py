@@ -72,7 +72,7 @@ def test_batched_at_the_configuration_extremes():
     assert status == ppg.PPG_OK
     assert stats[0]["ctas_per_system"] in (4, 8, 16)
     for i, ((a, b), sysi, st) in enumerate(zip(mats, systems, stats)):
-        assert st["ctas_per_system"] in (4, 8, 16) and st["spmv_lanes"] in (1, 2, 4, 8)
+        assert st["ctas_per_system"] in (1, 2, 4, 8, 16) and st["spmv_lanes"] in (1, 2, 4, 8)
         xb = sysi[4].cpu().numpy()
         assert st["converged"] == 1 and st["degree_used"] == 15
         assert _relres(a, b, xb) <= 1e-8
@@ -146,7 +146,8 @@ def test_batched_rejects_bad_arguments():
         ppg.ppg_solve_batched(systems, restart=41)
 
 
-@pytest.mark.parametrize("config", ["16,4,16384", "8,4,4000", "4,16,16384", "16,8,16384,512", "8,8,0,512"])
+@pytest.mark.parametrize("config", ["16,4,16384", "8,4,4000", "4,16,16384", "16,8,16384,512", "8,8,0,512", "16,1,4000",
+                                    "2,2,0"])
 def test_batched_split_launches_match_single_solves(config, monkeypatch):
     """The configurations the tuner can choose, forced through PPG_BATCH_CONFIG: the large systems in
     one launch and the others in a concurrent second launch with another cluster size (or one launch).
