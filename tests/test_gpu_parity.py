@@ -955,3 +955,29 @@ def test_full_size_c2_staged_matches_row_block(c2):
         out[fmt] = (x.cpu().numpy(), info.stats["iterations"])
     assert out[ppg.PPG_SPMV_STAGED][1] == out[ppg.PPG_SPMV_CSR][1]
     np.testing.assert_array_equal(out[ppg.PPG_SPMV_STAGED][0], out[ppg.PPG_SPMV_CSR][0])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5])
+def test_tiny_systems(n):
+    """Degenerate sizes: the Krylov space has at most n dimensions, so a degree-10 construction stops
+    early -- the roots form at degree n - 1 (the Arnoldi run breaks down), the power form where the
+    Gram matrix's pivots stop being positive (at most degree n: one rounding-level pivot may still
+    pass POTRF's test, Section IV) -- and GMRES converges within a few iterations; every entry point
+    works on a one-row matrix."""
+    rng = np.random.default_rng(n)
+    dense = rng.uniform(-1, 1, (n, n)) + np.diag(np.full(n, n + 2.0))
+    rp = np.arange(0, n * n + 1, n, dtype=np.int32)
+    ci = np.tile(np.arange(n, dtype=np.int32), n)
+    a = w.CSR(n, rp, ci, dense.reshape(-1), f"dense{n}")
+    b = w.uniform(3, n)
+    s = solver_for(a)
+    y = s.spmv(T(b)).cpu().numpy()
+    np.testing.assert_allclose(y, dense @ b, rtol=1e-13, atol=1e-13)
+    for basis in (ppg.PPG_BASIS_ROOTS, ppg.PPG_BASIS_POWER):
+        used, _ = s.build_poly(10, basis, v0=T(w.uniform(4, n)))
+        assert 0 <= used <= (n - 1 if basis == ppg.PPG_BASIS_ROOTS else n)
+        for prec in (ppg.PPG_F64, ppg.PPG_F32):
+            x, info = s.solve(T(b), tol=1e-10, restart=10, maxit=100, precision=prec)
+            assert info.status == ppg.PPG_OK and info.stats["iterations"] <= 3 * n
+            np.testing.assert_allclose(x.cpu().numpy(), np.linalg.solve(dense, b), rtol=1e-8, atol=1e-12)
+    s.close()
