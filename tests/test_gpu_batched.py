@@ -181,3 +181,18 @@ def test_batched_config_override_is_checked(monkeypatch):
     with pytest.raises(ppg.PPGError) as e:
         ppg.ppg_solve_batched(systems, degree=5, tol=1e-8, restart=20, seed=1)
     assert e.value.status == ppg.PPG_ERR_INVALID_ARG
+
+
+def test_batched_degenerate_sizes():
+    """Systems of 1, 4 and 9 rows (grid sides 1, 2, 3) in a batch with an ordinary one: most CTAs of a
+    tiny system's cluster own no rows, and its Krylov space is exhausted before the degree asked for;
+    every system still matches a dense solve."""
+    specs = [(1, 10.0), (2, 50.0), (3, 5.0), (40, 20.0)]
+    mats, systems = _batch(specs)
+    status, stats = ppg.ppg_solve_batched(systems, degree=8, tol=1e-10, restart=20, maxit=2000, seed=7)
+    assert status == ppg.PPG_OK
+    for (a, b), sysi, st in zip(mats, systems, stats):
+        xb = sysi[4].cpu().numpy()
+        xd = np.linalg.solve(a.to_dense(), b)
+        assert st["converged"] == 1 and _relres(a, b, xb) <= 1e-10
+        assert np.linalg.norm(xb - xd) <= 1e-6 * np.linalg.norm(xd)

@@ -137,3 +137,23 @@ def test_ilu_rejects_unsorted_rows():
         s.set_left_ilu0(1)
     assert e.value.status == ppg.PPG_ERR_INVALID_ARG and "sorted" in str(e.value)
     s.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_ilu_on_dense_tiny_matrices_is_exact(n):
+    """On a dense matrix ILU(0) has no fill to drop: M = L U = A, M^{-1} A = I, and the composed solve
+    gives the exact solution at once."""
+    rng = np.random.default_rng(10 + n)
+    dense = rng.uniform(-1, 1, (n, n)) + np.diag(np.full(n, n + 2.0))
+    rp = np.arange(0, n * n + 1, n, dtype=np.int32)
+    ci = np.tile(np.arange(n, dtype=np.int32), n)
+    a = w.CSR(n, rp, ci, dense.reshape(-1), f"dense{n}")
+    s = _solver(a)
+    lu = s.set_left_ilu0(1, want_factors=True).cpu().numpy()
+    np.testing.assert_array_equal(lu, oracle.ilu0(a))
+    s.build_poly(4, ppg.PPG_BASIS_ROOTS, v0=_T(w.uniform(4, n)))
+    b = w.uniform(3, n)
+    x, info = s.solve(_T(b), tol=1e-10, restart=10, maxit=50)
+    assert info.status == ppg.PPG_OK and info.stats["iterations"] <= 2
+    np.testing.assert_allclose(x.cpu().numpy(), np.linalg.solve(dense, b), rtol=1e-10, atol=1e-13)
+    s.close()
