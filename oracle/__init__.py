@@ -76,6 +76,9 @@ def _load():
         _lib.orc_poly_gmres_lu.restype = ci
         _lib.orc_gmres_lu.argtypes = [i64, p, p, p, p, ci, ci, p, p, p, d, p, p, d, ci, ci, p, p, ci]
         _lib.orc_gmres_lu.restype = ci
+        # s-step GMRES with the polynomial (Newton basis, block CGS2, Cholesky QR)
+        _lib.orc_sstep_gmres.argtypes = [i64, p, p, p, ci, ci, p, p, p, d, p, p, d, ci, ci, ci, d, p, p, ci]
+        _lib.orc_sstep_gmres.restype = ci
     return _lib
 
 
@@ -307,3 +310,25 @@ def gmres(a, b, p: Poly = IDENTITY, tol=1e-8, m=50, maxit=10000, x0=None, lu=Non
     it = int(stats[0])
     return SolveResult(x, bool(stats[4]), it, int(stats[1]), int(stats[2]), int(stats[3]), float(stats[5]),
                        float(stats[6]), hist[:it].copy())
+
+
+def sstep_gmres(a, b, p: Poly = IDENTITY, s=5, theta=0.0, tol=1e-8, m=50, maxit=10000, x0=None):
+    """s-step GMRES(m) with right preconditioning A p(A) u = b: per block, s Newton vectors
+    (B - theta I) z / ||.|| from the last basis vector (B = A p(A)), block classical Gram-Schmidt twice
+    against the basis, Cholesky QR within the block, and the block's Hessenberg columns recovered from
+    the change of basis.  The same iterates as gmres() in exact arithmetic.  Returns (SolveResult,
+    number of breakdowns)."""
+    lib = _load()
+    n, rp, ci, va = _csr(a)
+    b = _f64(b)
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    stats = np.zeros(8)
+    hist = np.zeros(maxit)
+    keep = p._keep()  # noqa: F841
+    st = lib.orc_sstep_gmres(n, _ptr(rp), _ptr(ci), _ptr(va), *p.args(), _ptr(b), _ptr(x), float(tol), int(m),
+                             int(maxit), int(s), float(theta), _ptr(stats), _ptr(hist), int(maxit))
+    if st == -2:
+        raise MemoryError("oracle allocation failed")
+    it = int(stats[0])
+    return SolveResult(x, bool(stats[4]), it, int(stats[1]), int(stats[2]), int(stats[3]), float(stats[5]),
+                       float(stats[6]), hist[:it].copy()), int(stats[7])

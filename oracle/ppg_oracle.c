@@ -29,6 +29,13 @@
  *     right, M^{-1} A p(M^{-1} A) y = M^{-1} b, x = p(M^{-1} A) y; the polynomial
  *     is then the minimum-residual polynomial of B = M^{-1} A.  Every "_lu"
  *     routine takes the factors; with lu = NULL it is the plain method.
+ *   - the combination Section VII proposes: the polynomial inside an s-step
+ *     (communication-avoiding) GMRES, orthogonalising once per s applications
+ *     of A p(A).  The paper gives no algorithm; orc_sstep_gmres takes the
+ *     standard s-step construction (Newton basis, block Gram-Schmidt, Cholesky
+ *     QR, Hessenberg columns recovered from the change of basis).  It produces
+ *     GMRES's iterates in exact arithmetic, and its pins are the Krylov minima
+ *     of dense least squares and the dense solution.
  *
  * Every routine is written out loop by loop, in float64, one core.
  *
@@ -765,4 +772,251 @@ int orc_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
               double tol, int m, int maxit, double *stats, double *hist, int hist_cap)
 {
     return orc_gmres_lu(n, rp, ci, va, NULL, kind, deg, coef, Hp, yp, betap, b, x, tol, m, maxit, stats, hist, hist_cap);
+}
+
+/* ------------------------------------------------------------------ */
+/* s-step (communication-avoiding) GMRES with the polynomial (Section VII's combination)          */
+/* ------------------------------------------------------------------ */
+
+/* The same right-preconditioned GMRES(m) iterates as orc_gmres (in exact arithmetic), built s basis
+ * vectors at a time: from the last basis vector q_k, a Newton basis z_{i+1} = (B - theta I) z_i / nu_i
+ * (B = A p(A), nu_i = the norm, i < s) is formed with SpMVs only; the block Z = [z_1 .. z_s] is then
+ * orthogonalised against Q = [q_0 .. q_k] by block classical Gram-Schmidt twice (C = Q^T Z, Z -= Q C),
+ * and within itself by Cholesky QR (Z^T Z = R^T R, Q_new = Z R^{-1}).  With U+ = [q_k, z_1 .. z_s] =
+ * [Q, Q_new] S (S: column 0 = e_k, column i = [C_i; R_i]) and B U = U+ T (T: theta on the diagonal,
+ * nu_i below it), the Arnoldi relation gives the block's Hessenberg columns
+ *     H[:, k .. k+s-1] = (S T - [H_old S_a; 0]) S_b^{-1},
+ * S_a = S's rows 0 .. k-1 and S_b its rows k .. k+s-1 (upper triangular) over columns 0 .. s-1,
+ * H_old = the Hessenberg columns 0 .. k-1 (rows 0 .. k).  The columns then go through the Givens
+ * rotations one by one, as in orc_gmres.  A Newton vector of norm 0 or a Cholesky pivot that is not
+ * positive shortens the block to the vectors before it; an empty block is a breakdown (the cycle ends).
+ * stats as orc_gmres, with stats[3] = global reductions: one per Newton norm, two block inner products
+ * and one Gram matrix per block, one per true residual. */
+int orc_sstep_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, int kind, int deg,
+                    const double *coef, const double *Hp, const double *yp, double betap, const double *b, double *x,
+                    double tol, int m, int maxit, int s, double theta, double *stats, double *hist, int hist_cap)
+{
+    csr_t A = {n, rp, ci, va, NULL};
+    poly_t p = {kind, deg, coef, Hp, yp, betap};
+    op_t op = {&A, &p, {0}, dalloc(n), 0};
+    if (s < 1) s = 1;
+    if (s > m) s = m;
+    const int ldh = m + 1;
+    double *V = dalloc(n * (m + 1));
+    double *Z = dalloc(n * s);
+    double *r = dalloc(n);
+    double *Hraw = dalloc((int64_t)ldh * m), *R = dalloc((int64_t)ldh * m);
+    double *cs = dalloc(m), *sn = dalloc(m), *g = dalloc(m + 1), *yv = dalloc(m);
+    double *nu = dalloc(s), *C = dalloc((int64_t)(m + 1) * s), *C2 = dalloc((int64_t)(m + 1) * s);
+    double *G = dalloc((int64_t)s * s), *S = dalloc((int64_t)(m + 1 + s) * (s + 1));
+    double *Hb = dalloc((int64_t)(m + 1 + s) * s), *zc = dalloc(n), *pz = dalloc(n);
+    int ok = (poly_ws_init(&op.ws, n, &p) == 0) && op.z && V && Z && r && Hraw && R && cs && sn && g && yv && nu &&
+             C && C2 && G && S && Hb && zc && pz;
+    for (int i = 0; i < ORC_NSTATS; ++i) stats[i] = 0.0;
+    int status = -2;
+    if (!ok) goto out;
+
+    double bnorm = nrm2(n, b);
+    long iters = 0, cycles = 0, dots = 0, brk_count = 0;
+    int converged = 0;
+    double relres = 0.0, est = 0.0;
+    if (bnorm == 0.0) {
+        memset(x, 0, sizeof(double) * (size_t)n);
+        converged = 1;
+        goto done;
+    }
+    for (;;) {
+        spmv(&A, x, r);
+        op.spmvs += 1;
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+        double beta = nrm2(n, r);
+        dots += 1;
+        relres = beta / bnorm;
+        if (relres <= tol) {
+            converged = 1;
+            break;
+        }
+        if (iters >= maxit) break;
+        cycles += 1;
+        for (int64_t i = 0; i < n; ++i) V[i] = r[i] / beta;
+        for (int i = 0; i <= m; ++i) g[i] = 0.0;
+        g[0] = beta;
+        int k = 0, stop = 0;
+        while (k < m && !stop) {
+            int sb = s;
+            if (sb > m - k) sb = m - k;
+            if (sb > maxit - iters) sb = (int)(maxit - iters);
+            /* Newton basis from q_k */
+            const double *zp = V + (int64_t)k * n;
+            int got = 0;
+            for (int i = 0; i < sb; ++i) {
+                double *zi = Z + (int64_t)i * n;
+                op_apply(&op, zp, zi);
+                axpy(n, -theta, zp, zi);
+                double v = nrm2(n, zi);
+                dots += 1;
+                if (!(v > 0.0) || !isfinite(v)) break;
+                nu[i] = v;
+                scal(n, 1.0 / v, zi);
+                zp = zi;
+                got = i + 1;
+            }
+            sb = got;
+            /* block classical Gram-Schmidt, twice: C = Q^T Z, Z -= Q C */
+            for (int c = 0; c <= k; ++c)
+                for (int i = 0; i < sb; ++i) C[c + i * (m + 1)] = 0.0;
+            for (int pass = 0; pass < 2 && sb > 0; ++pass) {
+                for (int i = 0; i < sb; ++i)
+                    for (int c = 0; c <= k; ++c)
+                        C2[c + i * (m + 1)] = dot(n, V + (int64_t)c * n, Z + (int64_t)i * n);
+                dots += 1;
+                for (int i = 0; i < sb; ++i)
+                    for (int c = 0; c <= k; ++c) {
+                        axpy(n, -C2[c + i * (m + 1)], V + (int64_t)c * n, Z + (int64_t)i * n);
+                        C[c + i * (m + 1)] += C2[c + i * (m + 1)];
+                    }
+            }
+            /* Cholesky QR of the block: G = Z^T Z = R^T R (R upper, in G's upper triangle) */
+            if (sb > 0) {
+                for (int i = 0; i < sb; ++i)
+                    for (int j = 0; j < sb; ++j) G[i + j * s] = dot(n, Z + (int64_t)i * n, Z + (int64_t)j * n);
+                dots += 1;
+                /* column-by-column Cholesky (the lower factor L = R^T, as orc_cholesky) */
+                int fact = sb;
+                for (int j = 0; j < sb && fact == sb; ++j) {
+                    double d = G[j + j * s];
+                    for (int q = 0; q < j; ++q) d -= G[j + q * s] * G[j + q * s];
+                    /* the Newton vectors have norm 1 before the projections, and Z^T Z resolves a
+                     * remainder's squared norm to about the unit roundoff: a pivot below the breakdown
+                     * threshold (a remainder below 1e-7) means z_j lies in the span already built */
+                    if (!(d > ORC_BREAKDOWN)) {
+                        fact = j;
+                        break;
+                    }
+                    d = sqrt(d);
+                    G[j + j * s] = d;
+                    for (int i = j + 1; i < sb; ++i) {
+                        double v = G[i + j * s];
+                        for (int q = 0; q < j; ++q) v -= G[i + q * s] * G[j + q * s];
+                        G[i + j * s] = v / d;
+                    }
+                }
+                sb = fact;
+            }
+            if (sb == 0) { /* B q_k = theta q_k + nu_0 z_1 lies in span(Q): a lucky breakdown, column k of
+                            * H is theta e_k + nu_0 C[:, 0] with a zero subdiagonal entry */
+                double *hc = Hraw + (int64_t)k * ldh;
+                for (int i = 0; i <= m; ++i) hc[i] = 0.0;
+                if (got > 0)
+                    for (int c = 0; c <= k; ++c) hc[c] = nu[0] * C[c];
+                hc[k] += theta;
+                double *rc = R + (int64_t)k * ldh;
+                for (int i = 0; i <= k + 1; ++i) rc[i] = hc[i];
+                for (int i = 0; i < k; ++i) rot(cs[i], sn[i], &rc[i], &rc[i + 1]);
+                rc[k] = make_rot(rc[k], rc[k + 1], &cs[k], &sn[k]);
+                rc[k + 1] = 0.0;
+                rot(cs[k], sn[k], &g[k], &g[k + 1]);
+                iters += 1;
+                k += 1;
+                est = fabs(g[k]) / bnorm;
+                if (hist && iters <= hist_cap) hist[iters - 1] = est;
+                brk_count += 1;
+                break;
+            }
+            /* Q_new = Z R^{-1}, R = L^T: column i of Q_new = (z_i - sum_{q<i} R[q,i] Q_new_q) / R[i,i] */
+            for (int i = 0; i < sb; ++i) {
+                double *qi = V + (int64_t)(k + 1 + i) * n;
+                memcpy(qi, Z + (int64_t)i * n, sizeof(double) * (size_t)n);
+                for (int q = 0; q < i; ++q) axpy(n, -G[i + q * s], V + (int64_t)(k + 1 + q) * n, qi);
+                scal(n, 1.0 / G[i + i * s], qi);
+            }
+            /* S ((k+1+sb) x (sb+1)) and the block's Hessenberg columns */
+            const int ns = k + 1 + sb;
+            for (int i = 0; i < ns * (sb + 1); ++i) S[i] = 0.0;
+            S[k] = 1.0;
+            for (int i = 1; i <= sb; ++i) {
+                for (int c = 0; c <= k; ++c) S[c + i * ns] = C[c + (i - 1) * (m + 1)];
+                for (int q = 0; q < i; ++q) S[k + 1 + q + i * ns] = G[(i - 1) + q * s]; /* R[q, i-1] = L[i-1, q] */
+            }
+            /* Hb = S T - [H_old S_a; 0]   (ns x sb) */
+            for (int j = 0; j < sb; ++j)
+                for (int i = 0; i < ns; ++i) {
+                    double v = theta * S[i + j * ns] + nu[j] * S[i + (j + 1) * ns];
+                    if (i <= k)
+                        for (int q = 0; q < k; ++q) v -= Hraw[i + (int64_t)q * ldh] * S[q + j * ns];
+                    Hb[i + j * ns] = v;
+                }
+            /* Hb := Hb S_b^{-1} (S_b = S rows k .. k+sb-1, columns 0 .. sb-1, upper triangular) */
+            for (int j = 0; j < sb; ++j) {
+                const double d = S[k + j + j * ns];
+                for (int i = 0; i < ns; ++i) {
+                    double v = Hb[i + j * ns];
+                    for (int q = 0; q < j; ++q) v -= Hb[i + q * ns] * S[k + q + j * ns];
+                    Hb[i + j * ns] = v / d;
+                }
+            }
+            /* the new columns through the Givens rotations, one iteration each */
+            for (int j = 0; j < sb; ++j) {
+                const int col = k + j;
+                double *hc = Hraw + (int64_t)col * ldh, *rc = R + (int64_t)col * ldh;
+                for (int i = 0; i <= m; ++i) hc[i] = 0.0;
+                for (int i = 0; i <= col + 1 && i < ns; ++i) hc[i] = Hb[i + j * ns];
+                for (int i = 0; i <= col + 1; ++i) rc[i] = hc[i];
+                for (int i = 0; i < col; ++i) rot(cs[i], sn[i], &rc[i], &rc[i + 1]);
+                rc[col] = make_rot(rc[col], rc[col + 1], &cs[col], &sn[col]);
+                rc[col + 1] = 0.0;
+                rot(cs[col], sn[col], &g[col], &g[col + 1]);
+                iters += 1;
+                est = fabs(g[col + 1]) / bnorm;
+                if (hist && iters <= hist_cap) hist[iters - 1] = est;
+                if (est <= tol || iters >= maxit) {
+                    k = col + 1;
+                    stop = 1;
+                    break;
+                }
+            }
+            if (!stop) k += sb;
+        }
+        /* y = R^{-1} g over the k columns, x += p(A) V y */
+        for (int i = k - 1; i >= 0; --i) {
+            double v = g[i];
+            for (int q = i + 1; q < k; ++q) v -= R[i + (int64_t)q * ldh] * yv[q];
+            yv[i] = v / R[i + (int64_t)i * ldh];
+        }
+        memset(zc, 0, sizeof(double) * (size_t)n);
+        for (int i = 0; i < k; ++i) axpy(n, yv[i], V + (int64_t)i * n, zc);
+        op.spmvs += poly_apply(&A, &p, zc, pz, &op.ws);
+        axpy(n, 1.0, pz, x);
+    }
+done:
+    stats[0] = (double)iters;
+    stats[1] = (double)cycles;
+    stats[2] = (double)op.spmvs;
+    stats[3] = (double)dots;
+    stats[4] = converged ? 1.0 : 0.0;
+    stats[5] = relres;
+    stats[6] = est;
+    stats[7] = (double)brk_count;
+    status = converged ? 0 : 1;
+out:
+    poly_ws_free(&op.ws);
+    free(op.z);
+    free(V);
+    free(Z);
+    free(r);
+    free(Hraw);
+    free(R);
+    free(cs);
+    free(sn);
+    free(g);
+    free(yv);
+    free(nu);
+    free(C);
+    free(C2);
+    free(G);
+    free(S);
+    free(Hb);
+    free(zc);
+    free(pz);
+    return status;
 }

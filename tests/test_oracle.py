@@ -497,3 +497,78 @@ def test_gmres_with_ilu_left_and_poly_right():
         best = np.linalg.norm(rb - BQ @ c) / np.linalg.norm(rb)
         assert abs(h[k - 1] - best) <= 1e-9 * max(best, 1e-3)
         t = Bop @ t
+
+
+# ---------------------------------------------------------------- s-step GMRES with the polynomial
+
+
+def test_sstep_first_cycle_residuals_are_krylov_minima():
+    """Each iteration of the s-step solver still minimises ||b - M c|| over the Krylov space of
+    M = A p(A), checked by dense least squares on an orthonormal basis of that space, for blocks of
+    1, 3 and 4 (the last one ragged against the 6 iterations)."""
+    a = _rand_dd(120, 62, shift=0.3)
+    b = w.rhs(a.n)
+    p = oracle.poly_gmres(a, w.v0(a.n), 3)
+    M = np.column_stack([oracle.spmv(a, oracle.poly_apply(a, p, e)) for e in np.eye(a.n)])
+    best = []
+    t, K = b.copy(), []
+    for k in range(1, 7):
+        K.append(t)
+        Q, _ = np.linalg.qr(np.column_stack(K))
+        c, *_ = np.linalg.lstsq(M @ Q, b, rcond=None)
+        best.append(np.linalg.norm(b - M @ Q @ c) / np.linalg.norm(b))
+        t = M @ t
+    for s in (1, 3, 4):
+        r, brk = oracle.sstep_gmres(a, b, p, s=s, theta=1.0, tol=1e-14, m=30, maxit=6)
+        assert r.iters == 6 and brk == 0
+        for k in range(6):
+            assert abs(r.hist[k] - best[k]) <= 1e-9 * max(best[k], 1e-3), (s, k)
+
+
+@pytest.mark.parametrize("s,theta", [(1, 0.0), (2, 1.0), (5, 1.0), (7, 0.5)])
+def test_sstep_matches_dense_solve_and_standard_gmres(s, theta):
+    """Restarted s-step GMRES (blocks that do not divide the restart length included) reaches the dense
+    solution, with the iteration count of standard GMRES."""
+    a = w.convdiff(12, 3, 20.0)
+    b = w.rhs(a.n)
+    xd = _dense_solve(a, b)
+    p = oracle.poly_gmres(a, w.v0(a.n), 6)
+    r, brk = oracle.sstep_gmres(a, b, p, s=s, theta=theta, tol=1e-10, m=9, maxit=2000)
+    assert r.converged and brk == 0 and r.relres <= 1e-10
+    assert np.linalg.norm(r.x - xd) <= 1e-8 * np.linalg.norm(xd)
+    ref = oracle.gmres(a, b, p, tol=1e-10, m=9, maxit=2000)
+    assert r.iters == ref.iters and r.restarts == ref.restarts
+
+
+def test_sstep_reductions_per_block():
+    """One global reduction per Newton norm, three per block (two Gram-Schmidt passes and the Gram
+    matrix), one per true residual: 11 iterations in blocks of 5 with GMRES(30) are 3 blocks of 5 Newton
+    vectors, 15 + 9 + 2 = 26 reductions."""
+    a = w.convdiff(12, 3, 20.0)
+    b = w.rhs(a.n)
+    p = oracle.poly_gmres(a, w.v0(a.n), 6)
+    r, _ = oracle.sstep_gmres(a, b, p, s=5, theta=1.0, tol=1e-10, m=30, maxit=2000)
+    assert r.iters == 11 and r.restarts == 1 and r.dots == 26
+
+
+def test_sstep_exhausted_krylov_space_is_a_lucky_breakdown():
+    """A diagonal matrix with three distinct eigenvalues and no polynomial: the Krylov space has
+    dimension 3, so the first block of 5 Newton vectors is rank 3 (a Cholesky pivot vanishes) and the
+    solver stops after 3 iterations with the exact solution."""
+    d = np.array([1.0, 2.0, 4.0] * 20)
+    n = d.size
+    a = w.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), d)
+    b = w.rhs(n)
+    r, _ = oracle.sstep_gmres(a, b, oracle.IDENTITY, s=5, theta=0.5, tol=1e-12, m=30, maxit=100)
+    assert r.converged and r.iters == 3
+    np.testing.assert_allclose(r.x, b / d, rtol=1e-10)
+
+
+def test_sstep_zero_rhs_and_maxit():
+    a = w.c1_matrix()
+    r, _ = oracle.sstep_gmres(a, np.zeros(a.n), oracle.IDENTITY, s=4, tol=1e-8, m=10, maxit=10)
+    assert r.converged and r.iters == 0 and not r.x.any()
+    r, _ = oracle.sstep_gmres(a, w.rhs(a.n), oracle.IDENTITY, s=4, theta=1.0, tol=1e-8, m=50, maxit=7)
+    assert not r.converged and r.iters == 7
+    ref = oracle.gmres(a, w.rhs(a.n), oracle.IDENTITY, tol=1e-8, m=50, maxit=7)
+    np.testing.assert_allclose(r.hist, ref.hist, rtol=1e-8)
