@@ -279,9 +279,10 @@ def main():
         s.close()
         return
 
-    def step(deg=args.degree, precision=prec, bvec=b, f32_form=ppg.PPG_F32_FLEXIBLE):
+    def step(deg=args.degree, precision=prec, bvec=b, f32_form=ppg.PPG_F32_FLEXIBLE, sstep=0):
         used, _ = s.build_poly(deg, ppg.PPG_BASIS_ROOTS, v0=v0)
-        x, info = s.solve(bvec, tol=1e-8, restart=50, maxit=20000, precision=precision, f32_form=f32_form)
+        x, info = s.solve(bvec, tol=1e-8, restart=50, maxit=20000, precision=precision, f32_form=f32_form,
+                          sstep=sstep, sstep_shift=1.0)
         return x, info
 
     for _ in range(args.warmup):
@@ -355,23 +356,26 @@ def main():
     if not args.no_variants:
         forms = (("f64", ppg.PPG_F64, ppg.PPG_F32_FLEXIBLE), ("f32", ppg.PPG_F32, ppg.PPG_F32_FLEXIBLE),
                  ("f32_standard", ppg.PPG_F32, ppg.PPG_F32_STANDARD))
-        for deg in (1, 10, 25, 40):
-            for pname, pv, form in forms:
-                step(deg, pv, f32_form=form)
-                ms_list = []
-                for _ in range(5):
-                    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    torch.cuda.synchronize()
-                    ea.record(stream)
-                    _, inf = step(deg, pv, f32_form=form)
-                    eb.record(stream)
-                    torch.cuda.synchronize()
-                    ms_list.append(ea.elapsed_time(eb))
-                variants[f"d{deg}_{pname}"] = {
-                    "ms_median": round(statistics.median(ms_list), 3), "ms_min": round(min(ms_list), 3),
-                    "ms_max": round(max(ms_list), 3), "repeats": len(ms_list),
-                    "iterations": inf.stats["iterations"], "restarts": inf.stats["restarts"],
-                    "relres_true": inf.stats["relres_true"], "status": inf.status}
+        # s-step blocks (Section VII's combination; standard float32 form, Newton shift 1) at the headline degree
+        runs = [(deg, pname, pv, form, 0) for deg in (1, 10, 25, 40) for pname, pv, form in forms]
+        runs += [(args.degree, f"f32_sstep{k}", ppg.PPG_F32, ppg.PPG_F32_STANDARD, k) for k in (4, 5, 8)]
+        runs += [(args.degree, "f64_sstep5", ppg.PPG_F64, ppg.PPG_F32_FLEXIBLE, 5)]
+        for deg, pname, pv, form, sst in runs:
+            step(deg, pv, f32_form=form, sstep=sst)
+            ms_list = []
+            for _ in range(5):
+                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ea.record(stream)
+                _, inf = step(deg, pv, f32_form=form, sstep=sst)
+                eb.record(stream)
+                torch.cuda.synchronize()
+                ms_list.append(ea.elapsed_time(eb))
+            variants[f"d{deg}_{pname}"] = {
+                "ms_median": round(statistics.median(ms_list), 3), "ms_min": round(min(ms_list), 3),
+                "ms_max": round(max(ms_list), 3), "repeats": len(ms_list),
+                "iterations": inf.stats["iterations"], "restarts": inf.stats["restarts"],
+                "relres_true": inf.stats["relres_true"], "dots": inf.stats["dots"], "status": inf.status}
 
     traffic, traffic_info = spmv_traffic()
     cpu = None

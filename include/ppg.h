@@ -100,14 +100,25 @@ typedef struct {
                           two-step kernel need one CTA more than its launch has, and every ILU(0) triangular
                           solve treat the rows it waits on as never ready, so that those waits run out after
                           wait_limit_us */
-    int reserved[1];
+    int sstep;         /* 0 (default): one basis vector per orthogonalisation.  1..8: s-step blocks (Section VII's
+                          combination of the polynomial with an s-step method): sstep vectors of the Newton basis
+                          (A p(A) - sstep_shift I)^i q_k are built by SpMV chains alone, then orthogonalised
+                          together by block classical Gram-Schmidt twice and Cholesky QR, three global
+                          reductions per block; the block's Hessenberg columns follow from the change of
+                          basis, so the iterates are GMRES's in exact arithmetic.  Requires restart <= 64 and no
+                          ILU(0); the float32 solve runs in the standard form.  A block whose Newton vector
+                          is numerically dependent (Cholesky pivot below 1e-14 (float64) or 1e-6 (float32)
+                          of its squared norm) ends the cycle with a lucky breakdown */
+    double sstep_shift; /* the Newton shift theta (sstep > 0): a point inside the spectrum of A p(A); a
+                          minimum-residual polynomial clusters that spectrum around 1 */
 } ppg_opts;
 
 typedef struct {
     int64_t iterations;  /* GMRES iterations (basis vectors built) */
     int64_t restarts;    /* restart cycles started */
     int64_t spmvs;       /* sparse matrix-vector products, counted as in Section III */
-    int64_t dots;        /* 2 block inner products + 1 norm per iteration (Section III) and 1 norm per cycle */
+    int64_t dots;        /* 2 block inner products + 1 norm per iteration (Section III) and 1 norm per cycle; s-step
+                            solves: 3 global reductions per block and 1 per cycle */
     int64_t kernel_launches;
     double relres_true;  /* ||b - A x|| / ||b|| of the returned x, computed in float64 */
     double relres_est;   /* last in-cycle Givens estimate |g_{j+1}| / ||b|| */

@@ -58,7 +58,7 @@ EXPORTED = (
 class ppg_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("f32_form", ctypes.c_int), ("wait_limit_us", ctypes.c_int),
-                ("test_unreachable_wait", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("test_unreachable_wait", ctypes.c_int), ("sstep", ctypes.c_int), ("sstep_shift", ctypes.c_double)]
 
 
 class ppg_stats(ctypes.Structure):
@@ -343,8 +343,10 @@ def ppg_apply_poly_noalloc(ctx, v, out):
 
 
 def _opts(precision=PPG_F64, inner_rtol=0.0, use_graph=-1, profile=0, f32_form=PPG_F32_FLEXIBLE, wait_limit_us=0,
-          test_unreachable_wait=0):
+          test_unreachable_wait=0, sstep=0, sstep_shift=1.0):
     o = ppg_opts()
+    o.sstep = sstep
+    o.sstep_shift = sstep_shift
     o.precision = precision
     o.inner_rtol = inner_rtol
     o.use_graph = use_graph
@@ -364,11 +366,14 @@ def _solve_args(ctx, b, x, where, names):
 
 
 def ppg_solve(ctx, b, x, tol=1e-8, restart=50, maxit=10000, precision=PPG_F64, inner_rtol=0.0, use_graph=-1,
-              profile=0, f32_form=PPG_F32_FLEXIBLE, wait_limit_us=0, test_unreachable_wait=0):
-    """Solves A x = b in place (x holds x0).  Returns (status, stats dict)."""
+              profile=0, f32_form=PPG_F32_FLEXIBLE, wait_limit_us=0, test_unreachable_wait=0, sstep=0,
+              sstep_shift=1.0):
+    """Solves A x = b in place (x holds x0).  Returns (status, stats dict).  sstep in 1..8 builds the basis
+    in s-step blocks with the Newton shift sstep_shift (ppg_opts.sstep)."""
     _solve_args(ctx, b, x, "ppg_solve", ("b", "x"))
     st = ppg_stats()
-    o = _opts(precision, inner_rtol, use_graph, profile, f32_form, wait_limit_us, test_unreachable_wait)
+    o = _opts(precision, inner_rtol, use_graph, profile, f32_form, wait_limit_us, test_unreachable_wait, sstep,
+              sstep_shift)
     s = _check(load_library().ppg_solve(ctx, _ptr(b), _ptr(x), float(tol), int(restart), int(maxit),
                                         ctypes.byref(o), ctypes.byref(st)), "ppg_solve")
     return s, st.as_dict()
@@ -598,11 +603,12 @@ class Solver:
         return out
 
     def solve(self, b, x=None, tol=1e-8, restart=50, maxit=10000, precision=PPG_F64, inner_rtol=0.0, use_graph=-1,
-              profile=0, f32_form=PPG_F32_FLEXIBLE, wait_limit_us=0, test_unreachable_wait=0):
+              profile=0, f32_form=PPG_F32_FLEXIBLE, wait_limit_us=0, test_unreachable_wait=0, sstep=0,
+              sstep_shift=1.0):
         self._workspace(restart, 0, precision)
         x = self._torch.zeros_like(b) if x is None else x
         status, stats = ppg_solve(self.ctx, b, x, tol, restart, maxit, precision, inner_rtol, use_graph, profile,
-                                  f32_form, wait_limit_us, test_unreachable_wait)
+                                  f32_form, wait_limit_us, test_unreachable_wait, sstep, sstep_shift)
         return x, SolveInfo(status, stats)
 
     def solve_transpose(self, g, lam=None, tol=1e-8, restart=50, maxit=10000, precision=PPG_F64, inner_rtol=0.0):

@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libppg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=default",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
-SOURCES = ["ppg_spmv.cu", "ppg_ortho.cu", "ppg_small.cu", "ppg_batch.cu", "ppg_ilu.cu", "ppg_api.cu"]
+SOURCES = ["ppg_spmv.cu", "ppg_ortho.cu", "ppg_small.cu", "ppg_batch.cu", "ppg_ilu.cu", "ppg_sstep.cu", "ppg_api.cu"]
 
 
 def nvcc() -> str:

@@ -110,6 +110,11 @@ struct ppg_ctx {
     int *d_ilu_abort = nullptr;
     char *ilu_vec = nullptr;
     char *noalloc_base = nullptr; // device address of the allocation-free apply's scratch (n <= its limit)
+    // s-step solves (ppg_opts.sstep): the block's device state and the passes' per-CTA sums, allocated
+    // on the first such solve
+    SStep *d_sstep = nullptr;
+    double *d_bgs_partials = nullptr;
+    int bgs_pld = 0;
 
     // CUDA graphs of single iterations (ppg_opts.use_graph): one per iteration index, precision and
     // polynomial presence, valid while the signature captured with it (workspace addresses,
@@ -659,14 +664,17 @@ struct Exec {
         return PPG_OK;
     }
 
-    // w = A p(A) (scale * src), fusing the scalar cases into one SpMV.
-    ppg_status poly_then_A(VecRef src, const double *sig, VecRef w, char *const tmp[4], int check)
+    // w = A p(A) (scale * src) - shift * (scale * src), fusing the scalar cases into one SpMV; the
+    // shift (the s-step Newton basis) rides on the last SpMV's epilogue.
+    ppg_status poly_then_A(VecRef src, const double *sig, VecRef w, char *const tmp[4], int check,
+                           double shift = 0.0)
     {
         chain_begin();
-        PPG_TRY(poly_then_A_links(src, sig, w, tmp, check));
+        PPG_TRY(poly_then_A_links(src, sig, w, tmp, check, shift));
         return chain_end();
     }
-    ppg_status poly_then_A_links(VecRef src, const double *sig, VecRef w, char *const tmp[4], int check)
+    ppg_status poly_then_A_links(VecRef src, const double *sig, VecRef w, char *const tmp[4], int check,
+                                 double shift)
     {
         if (!c->has_poly || (c->basis == PPG_BASIS_POWER && c->degree == 0)) {
             const double s0 = c->has_poly ? c->coef[0] : 1.0;
@@ -674,6 +682,10 @@ struct Exec {
             e.x = src;
             e.out0 = w;
             e.a0 = sscaled(s0, sig);
+            if (shift != 0.0) {
+                e.u0 = src;
+                e.b0 = sscaled(-shift, sig);
+            }
             return spmv(e, check);
         }
         char *t3[3] = {tmp[1], tmp[2], tmp[3]};
@@ -687,6 +699,10 @@ struct Exec {
         }
         e.out0 = w;
         e.a0 = simm(1.0);
+        if (shift != 0.0) {
+            e.u0 = src;
+            e.b0 = sscaled(-shift, sig);
+        }
         return spmv(e, check);
     }
 
@@ -805,6 +821,47 @@ struct Iter {
         PPG_TRY(gs(kGsDot, 0, nullptr, 0, j + 1));
         PPG_TRY(gs(kGsUpdDot, 0, nullptr, 0, j + 1));
         PPG_TRY(gs(kGsUpdNorm, 0, nullptr, 1, j + 1));
+        prof_close(c, x->s);
+        return PPG_OK;
+    }
+
+    // One s-step block: sb Newton vectors (B - theta I) from basis column k into columns k + 1 ..
+    // k + sb, the three block passes (their reductions finish the block on the device) and Z R^{-1}.
+    // The device's j equals k whenever the block does work (every block of a live cycle advances j by
+    // its size); once the cycle has ended every kernel returns at once.
+    ppg_status block(int k, int sb, double theta, double tau)
+    {
+        ppg_ctx *c = x->c;
+        c->prof_j = k;
+        char *tmp[4] = {L->vec[1], L->vec[2], L->vec[3], L->vec[4]};
+        prof_open(c, x->s, 0);
+        for (int i = 0; i < sb; ++i)  // columns follow the device's j (= k): j + i -> j + i + 1
+            PPG_TRY(x->poly_then_A(vcol(L->basis, c->ld, i), i == 0 ? c->st->sigma : nullptr,
+                                   vcol(L->basis, c->ld, i + 1), tmp, kSkipIfDone, theta));
+        prof_close(c, x->s);
+        prof_open(c, x->s, 1);
+        BgsArgs a{};
+        a.U = L->basis;
+        a.ld = c->ld;
+        a.n = x->A->n;
+        a.k = k;
+        a.sb = sb;
+        a.theta = theta;
+        a.tau = tau;
+        a.partials = c->d_bgs_partials;
+        a.pld = c->bgs_pld;
+        a.nblk = bgs_max_blocks(c->num_sms);
+        const double col = (double)x->A->n * (x->prec == kF64 ? 8.0 : 4.0);
+        for (int op : {kBgsDot, kBgsUpdDot, kBgsUpdGram}) {
+            a.op = op;
+            c->launches += 2;
+            PPG_CK(launch_bgs(x->prec, a, c->st, c->d_sstep, c->num_sms, x->s));
+            // k + 1 basis columns and the block read; the block written by the updates
+            prof_add(c, col * (k + 1 + sb + (op == kBgsDot ? 0 : sb)), 0.0);
+        }
+        c->launches++;
+        PPG_CK(launch_btri(x->prec, L->basis, c->ld, x->A->n, c->d_sstep, c->num_sms, x->s));
+        prof_add(c, 2.0 * col * sb, 0.0);
         prof_close(c, x->s);
         return PPG_OK;
     }
@@ -1168,6 +1225,73 @@ ppg_status run_cycle(ppg_ctx *c, Iter &it, int restart)
     return PPG_OK;
 }
 
+// Enqueues the blocks of one s-step restart cycle, paced like run_cycle: at most launch_ahead()
+// blocks beyond the one the device is working on.
+ppg_status run_cycle_sstep(ppg_ctx *c, Iter &it, int restart, int s, double theta, double tau)
+{
+    volatile int *prog = c->h_prog;
+    *prog = 0;
+    const int ahead = launch_ahead();
+    for (int k = 0; k < restart;) {
+        const int sb = std::min(s, restart - k);
+        auto t0 = std::chrono::steady_clock::now();
+        int seen = *prog & 0xffff;
+        for (int spin = 0;; ++spin) {
+            const int p = *prog;
+            if (p >> 16) return PPG_OK;
+            if (k - (p & 0xffff) < ahead * s) break;
+            if ((p & 0xffff) != seen) {
+                seen = p & 0xffff;
+                t0 = std::chrono::steady_clock::now();
+            }
+            if ((spin & 63) == 63) {
+                const cudaError_t q = cudaStreamQuery(c->stream);
+                if (q == cudaSuccess) {
+                    if (*prog >> 16) return PPG_OK;
+                    break;
+                }
+                if (q != cudaErrorNotReady) PPG_CK(q);
+            }
+            const long long waited =
+                std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count();
+            if ((unsigned long long)waited > c->waits.ns) {
+                PPG_TRY(read_state(c));
+                return fail(PPG_ERR_TIMEOUT,
+                            "the host's wait for the device's progress ran out after %lld us (block at column %d "
+                            "queued, device at column %d of the cycle)",
+                            waited / 1000, k, *prog & 0xffff);
+            }
+            std::this_thread::yield();
+        }
+        PPG_TRY(it.block(k, sb, theta, tau));
+        k += sb;
+    }
+    return PPG_OK;
+}
+
+ppg_status ensure_sstep(ppg_ctx *c)
+{
+    if (c->d_sstep) return PPG_OK;
+    const int nblk = bgs_max_blocks(c->num_sms);
+    const int pld = (nblk + 1) & ~1;
+    const size_t slots = (size_t)(kSMax * kSColsMax + kSMax) * (size_t)pld;
+    if (cudaMalloc(&c->d_bgs_partials, slots * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->d_bgs_partials = nullptr;
+        return fail(PPG_ERR_OOM, "cannot allocate the s-step passes' partial sums");
+    }
+    if (cudaMalloc(&c->d_sstep, sizeof(SStep)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->d_bgs_partials);
+        c->d_bgs_partials = nullptr;
+        c->d_sstep = nullptr;
+        return fail(PPG_ERR_OOM, "cannot allocate the s-step state");
+    }
+    PPG_CK(cudaMemsetAsync(c->d_sstep, 0, sizeof(SStep), c->stream));
+    c->bgs_pld = pld;
+    return PPG_OK;
+}
+
 ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int restart, int maxit,
                       const ppg_opts *opts, ppg_stats *stats)
 {
@@ -1178,10 +1302,20 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
     if (prec != PPG_F64 && prec != PPG_F32) return fail(PPG_ERR_INVALID_ARG, "unknown precision");
     const int form = opts ? opts->f32_form : PPG_F32_FLEXIBLE;
     if (form != PPG_F32_FLEXIBLE && form != PPG_F32_STANDARD) return fail(PPG_ERR_INVALID_ARG, "unknown f32_form");
+    // s-step blocks (Section VII's combination): sstep vectors per orthogonalisation, shift theta
+    const int sstep = opts ? opts->sstep : 0;
+    const double theta = opts ? opts->sstep_shift : 0.0;
+    if (sstep < 0 || sstep > kSMax) return fail(PPG_ERR_INVALID_ARG, "sstep must be in [0, %d]", kSMax);
+    if (sstep > 0) {
+        if (restart > kSColsMax) return fail(PPG_ERR_INVALID_ARG, "s-step solves take restart <= %d", kSColsMax);
+        if (c->ilu_on) return fail(PPG_ERR_INVALID_ARG, "s-step solves do not take ILU(0) on the left");
+        if (!std::isfinite(theta)) return fail(PPG_ERR_INVALID_ARG, "the s-step shift must be finite");
+    }
     // the flexible form keeps z_j = p(A) v_j; with no polynomial (or a scalar one) z_j is v_j itself
-    // (with ILU(0) on the left the standard form runs: its operator is M^{-1} A throughout)
+    // (with ILU(0) on the left the standard form runs: its operator is M^{-1} A throughout; s-step
+    // solves use the standard form: their block's vectors are not the preconditioned basis)
     const bool flex = prec == PPG_F32 && form == PPG_F32_FLEXIBLE && c->has_poly &&
-                      !(c->basis == PPG_BASIS_POWER && c->degree == 0) && !c->ilu_on;
+                      !(c->basis == PPG_BASIS_POWER && c->degree == 0) && !c->ilu_on && sstep == 0;
     // limits of the software waits for this solve (the context keeps the defaults otherwise)
     c->waits = WaitCfg{};
     if (opts && opts->wait_limit_us > 0 && opts->wait_limit_us < 1000000)
@@ -1200,6 +1334,10 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
     const int ncols = restart + 1;
     Layout L;
     PPG_TRY(get_layout(c, ncols, es, &L));
+    if (sstep > 0) PPG_TRY(ensure_sstep(c));
+    // dependence test of the block's Cholesky QR: a pivot below tau ||z||^2 (float64: the Arnoldi
+    // breakdown level; float32: the level to which a float32 block's Gram matrix resolves it)
+    const double tau = prec == PPG_F64 ? 1e-14 : 1e-6;
     const long long launches0 = c->launches;
     PPG_CK(cudaEventRecord(c->ev0, c->stream));
 
@@ -1250,7 +1388,10 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
         PPG_TRY(start_cycle());
         PPG_TRY(read_state(c));
         while (!c->h_st->stop) {
-            PPG_TRY(run_cycle(c, it, restart));
+            if (sstep > 0)
+                PPG_TRY(run_cycle_sstep(c, it, restart, sstep, theta, tau));
+            else
+                PPG_TRY(run_cycle(c, it, restart));
             PPG_TRY(it.cycle_end(x));
             if (c->prof) PPG_TRY(prof_close_cycle(c));
             if (flex) {
@@ -1275,8 +1416,13 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
         // true residual; dots: three per iteration (Section III), a norm per residual, and one block
         // inner product per restart projection
         const int ps = ex.poly_spmvs();
-        stats->spmvs = h.iters * (long long)(ps + 1) + (flex ? 0 : h.cycles * (long long)ps) + h.nres;
-        stats->dots = 3 * h.iters + h.nres + h.nproj;
+        if (sstep > 0) {  // per block: its Newton vectors' chains and three reductions
+            stats->spmvs = h.nnewton * (long long)(ps + 1) + h.cycles * (long long)ps + h.nres;
+            stats->dots = 3 * h.nblocks + h.nres;
+        } else {
+            stats->spmvs = h.iters * (long long)(ps + 1) + (flex ? 0 : h.cycles * (long long)ps) + h.nres;
+            stats->dots = 3 * h.iters + h.nres + h.nproj;
+        }
         stats->kernel_launches = c->launches - launches0;
         stats->relres_true = h.relres;
         stats->relres_est = h.est;
@@ -1790,6 +1936,8 @@ void ppg_destroy(ppg_ctx *c)
     cudaFree(c->d_svals64);
     cudaFree(c->d_svals32);
     cudaFree(c->st);
+    cudaFree(c->d_sstep);
+    cudaFree(c->d_bgs_partials);
     cudaFree(c->d_small);
     cudaFree(c->d_info);
     if (c->ws_owned) cudaFree(c->ws);

@@ -42,6 +42,8 @@ struct Cycle {
     long long cycles;
     long long nres;     // float64 true residuals computed (b - A x)
     long long nproj;    // restart projections done (flexible float32 solves)
+    long long nblocks;  // s-step blocks finished (each: three global reductions)
+    long long nnewton;  // s-step Newton vectors built (each: one application of A p(A))
     double bnorm;       // ||b||
     double enorm;       // the norm the in-cycle estimate is relative to: ||b||, or ||M^{-1} b|| with ILU(0)
                         // on the left (the residual left-preconditioned GMRES minimises)

@@ -189,6 +189,52 @@ struct GsArgs {
     int rev;      // 1: the pass visits its row tiles last to first
 };
 
+// ---- s-step GMRES with the polynomial (Section VII's combination)
+// A block of sb <= kSMax basis vectors is built from the last orthonormal column q_k of the basis U
+// (column k): the raw Newton vectors z_1 = (B - theta I) q_k, z_{i+1} = (B - theta I) z_i with B =
+// A p(A) go to columns k + 1 .. k + sb; block classical Gram-Schmidt twice against columns 0 .. k
+// and Cholesky QR turn them into orthonormal columns, and the block's Hessenberg columns follow
+// from the change of basis.
+constexpr int kSMax = 8;       // largest block
+constexpr int kSColsMax = 64;  // columns 0 .. k a block pass combines (restart <= 64)
+enum BgsOp : int {
+    kBgsDot = 0,      // P = U^T W and the squared norms of the raw Newton vectors W
+    kBgsUpdDot = 1,   // W -= U coef; P = U^T W
+    kBgsUpdGram = 2,  // W -= U coef; G = W^T W, then the block's finalisation
+};
+// Device state of the block being built (one per context).
+struct SStep {
+    double C[kSMax][kSColsMax];     // C[i][c] = q_c . z_i, summed over both Gram-Schmidt passes
+    double coef[kSMax][kSColsMax];  // the next update's coefficients of the stored columns
+    double w0[kSMax];               // ||z_i||^2 before the projections
+    double red[kSMax * kSColsMax + kSMax];  // the last pass's reduced sums
+    double tinv[kSMax * kSMax];     // R^{-1} (column-major, upper), for the triangular pass
+    int tri_cols;                   // columns the triangular pass turns into Z R^{-1} (0: none)
+    int tri_base;                   // the first of them
+    unsigned int ticket[4];
+};
+struct BgsArgs {
+    const void *U;     // the basis (column-major, ld entries per column)
+    long long ld;
+    int n;
+    int k;             // columns 0 .. k are the orthonormal basis; the block is columns k + 1 .. k + sb
+    int sb;
+    int op;            // BgsOp
+    double theta;      // the Newton shift
+    double tau;        // Cholesky pivot threshold relative to ||z_i||^2 (the dependence test)
+    double *partials;  // per-CTA sums: slot o of CTA b at o * pld + b
+    int pld;
+    int nblk;
+    long long ntiles;
+};
+// One pass over the block (nblk CTAs), then the reduction of its sums and, for kBgsUpdGram, the
+// block's finalisation: Cholesky, Hessenberg columns, Givens rotations and the cycle's tests.
+// Every kernel returns at once when the cycle has ended.
+cudaError_t launch_bgs(int prec, BgsArgs a, Cycle *st, SStep *ss, int num_sms, cudaStream_t s);
+int bgs_max_blocks(int num_sms);
+// columns tri_base .. tri_base + tri_cols - 1 of U become W R^{-1} (after a finalisation; else nothing)
+cudaError_t launch_btri(int prec, void *U, long long ld, int n, SStep *ss, int num_sms, cudaStream_t s);
+
 // ---- ILU(0) on the left (Section VI)
 // One level of the row-by-row ILU(0) factorisation (rows: the level's rows): lu holds A's values on
 // entry (A's sorted pattern, diag: each row's diagonal position) and L (unit diagonal not stored)

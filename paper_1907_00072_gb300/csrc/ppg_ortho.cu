@@ -23,6 +23,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include "ppg_cycle.cuh"
 #include "ppg_internal.h"
 
 namespace ppg {
@@ -146,15 +147,6 @@ struct XAcc<float> {
 // an L2 round trip; the last CTA therefore does the per-column work with all its threads and
 // runs the serial recurrences (Givens rotations, back substitution) on shared-memory copies.
 
-// Publishes the iteration count and the end-of-cycle flag to the host-mapped progress word, so
-// that the host stops enqueueing a cycle's iterations once it has ended.  The host uses the word
-// only to pace its launches (anything it acts on is read after the stream has synchronised), so
-// the store needs no fence.
-__device__ void publish_progress(const Cycle *st, int cycle_done, int j)
-{
-    if (st->prog) *(volatile int *)st->prog = (cycle_done << 16) | j;
-}
-
 // Pass 3: completes Hessenberg column j, H[0..j, j] = h1 + h2, H[j+1, j] = ||v_{j+1}||.  In GMRES
 // mode the previous Givens rotations are applied to the column, a new rotation zeroes H[j+1, j]
 // and updates g; the cycle ends on a small estimate |g_{j+1}|, a breakdown, the restart length or
@@ -168,42 +160,6 @@ __device__ void publish_progress(const Cycle *st, int cycle_done, int j)
 // built), whose products c_i b_{i+1} and rotated entries c_i a_i + s_i b_{i+1} are formed by all
 // threads, leaving one multiply-add per step to thread 0, while warp 1 forms the norm and its
 // reciprocal.
-// y = R^{-1} g[0..k-1] with the cycle's triangle R (st->R) and right-hand side st->g, by the whole
-// CTA: R staged in shared memory when it fits, then column-oriented back substitution by warp 0
-// (y_i = g_i / R_ii, then g_q -= R_qi y_i for q < i in parallel).  Writes y and the combination
-// coefficients coef = -y .* sigma.  sh: shared scratch of sh_bytes, free for this call.
-__device__ void cta_solve_r(Cycle *st, int k, double *sh, size_t sh_bytes)
-{
-    const int tid = threadIdx.x, nt = blockDim.x;
-    double *g = sh;            // k values
-    double *Rs = sh + k;       // k x k, column-major, ld k
-    const bool staged = (size_t)(k + k * k) * sizeof(double) <= sh_bytes;
-    for (int i = tid; i < k; i += nt) g[i] = st->g[i];
-    if (staged)
-        for (int e = tid; e < k * k; e += nt) {
-            const int q = e / k, i = e - q * k;
-            Rs[e] = i <= q ? st->R[(long long)q * kLdH + i] : 0.0;
-        }
-    __syncthreads();
-    if (tid < 32) {
-        for (int i = k - 1; i >= 0; --i) {
-            const double *Ri = staged ? Rs + (long long)i * k : st->R + (long long)i * kLdH;
-            const double yi = g[i] / Ri[i];
-            __syncwarp();
-            for (int q = tid; q < i; q += 32) g[q] -= Ri[q] * yi;
-            if (tid == 0) g[i] = yi;
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    for (int c = tid; c < k; c += nt) {
-        const double y = g[c];
-        st->y[c] = y;
-        st->coef[c] = -y * st->sigma[c];
-    }
-    __syncthreads();
-}
-
 template <typename T>
 __device__ void cta_finish_pass3(Cycle *st, int j, double wsq, double *sh, size_t sh_bytes, int *s_int)
 {
