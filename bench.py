@@ -331,6 +331,13 @@ def main():
     ps = pinfo.stats
     spmv_gbs = ps["spmv_bytes"] / (ps["spmv_ms"] * 1e-3) / 1e9
     gs_gbs = ps["gs_bytes"] / (ps["gs_ms"] * 1e-3) / 1e9
+    # the s-step solve's block passes (blocks of 4 Newton vectors; Section VII's combination), profiled
+    # the same way: the three block passes, their reductions and finalisation, and Z R^-1 per block
+    s.build_poly(args.degree, ppg.PPG_BASIS_ROOTS, v0=v0)
+    _, sinfo = s.solve(b, tol=1e-8, restart=50, maxit=20000, precision=prec, profile=1, sstep=4, sstep_shift=1.0,
+                       f32_form=ppg.PPG_F32_STANDARD)
+    sps = sinfo.stats
+    sstep_gbs = sps["gs_bytes"] / (sps["gs_ms"] * 1e-3) / 1e9
     # plain SpMV y = A x of the benchmark matrix, one event pair per launch
     dtype_t = torch.float32 if prec == ppg.PPG_F32 else torch.float64
     sv = 4 if prec == ppg.PPG_F32 else 8
@@ -418,6 +425,13 @@ def main():
                            "achieved": round(gs_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gs_gbs / hbm, 3),
                            "timed_segments": ps["gs_segments"], "ms_total": round(ps["gs_ms"], 3),
                            "bytes_total": ps["gs_bytes"]},
+        "roofline_sstep": {"bound": "hbm", "kernel": "k_bgs_dot, k_bgs_gram, k_bgs_finish, k_btri (s-step blocks of "
+                                                     "4 Newton vectors: block CGS2, Cholesky QR, Hessenberg recovery)",
+                           "achieved": round(sstep_gbs, 1), "peak": hbm, "unit": "GB/s",
+                           "frac": round(sstep_gbs / hbm, 3), "timed_segments": sps["gs_segments"],
+                           "ms_total": round(sps["gs_ms"], 3), "bytes_total": sps["gs_bytes"],
+                           "solve_ms": round(sps["time_ms"], 3), "iterations": sps["iterations"],
+                           "global_reductions": sps["dots"]},
         "spmv_plain": {"achieved": round(spmv_bytes / (spmv_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
                        "ms_per_launch": round(spmv_ms, 5), "bytes_per_launch": spmv_bytes},
         "cpu_baseline": cpu,

@@ -826,7 +826,8 @@ struct Iter {
     }
 
     // One s-step block: sb Newton vectors (B - theta I) from basis column k into columns k + 1 ..
-    // k + sb, the three block passes (their reductions finish the block on the device) and Z R^{-1}.
+    // k + sb, then the three block passes (the reductions of the first two finish the block on the
+    // device; the third forms (Z - Q C2) R^{-1}).
     // The device's j equals k whenever the block does work (every block of a live cycle advances j by
     // its size); once the cycle has ended every kernel returns at once.
     ppg_status block(int k, int sb, double theta, double tau)
@@ -852,16 +853,13 @@ struct Iter {
         a.pld = c->bgs_pld;
         a.nblk = bgs_max_blocks(c->num_sms);
         const double col = (double)x->A->n * (x->prec == kF64 ? 8.0 : 4.0);
-        for (int op : {kBgsDot, kBgsUpdDot, kBgsUpdGram}) {
+        for (int op : {kBgsDot, kBgsUpdDot, kBgsUpdTri}) {
             a.op = op;
-            c->launches += 2;
+            c->launches += op == kBgsUpdTri ? 1 : 2;
             PPG_CK(launch_bgs(x->prec, a, c->st, c->d_sstep, c->num_sms, x->s));
-            // k + 1 basis columns and the block read; the block written by the updates
+            // k + 1 basis columns and the block read; the block written by passes 2 and 3
             prof_add(c, col * (k + 1 + sb + (op == kBgsDot ? 0 : sb)), 0.0);
         }
-        c->launches++;
-        PPG_CK(launch_btri(x->prec, L->basis, c->ld, x->A->n, c->d_sstep, c->num_sms, x->s));
-        prof_add(c, 2.0 * col * sb, 0.0);
         prof_close(c, x->s);
         return PPG_OK;
     }

@@ -198,16 +198,16 @@ struct GsArgs {
 constexpr int kSMax = 8;       // largest block
 constexpr int kSColsMax = 64;  // columns 0 .. k a block pass combines (restart <= 64)
 enum BgsOp : int {
-    kBgsDot = 0,      // P = U^T W and the squared norms of the raw Newton vectors W
-    kBgsUpdDot = 1,   // W -= U coef; P = U^T W
-    kBgsUpdGram = 2,  // W -= U coef; G = W^T W, then the block's finalisation
+    kBgsDot = 0,     // P = U^T W and the squared norms of the raw Newton vectors W
+    kBgsUpdDot = 1,  // W -= U coef; P = U^T W and G = W^T W, then the block's finalisation
+    kBgsUpdTri = 2,  // W -= U coef, then W R^{-1} into the block's columns (no reduction)
 };
 // Device state of the block being built (one per context).
 struct SStep {
     double C[kSMax][kSColsMax];     // C[i][c] = q_c . z_i, summed over both Gram-Schmidt passes
     double coef[kSMax][kSColsMax];  // the next update's coefficients of the stored columns
     double w0[kSMax];               // ||z_i||^2 before the projections
-    double red[kSMax * kSColsMax + kSMax];  // the last pass's reduced sums
+    double red[kSMax * kSColsMax + kSMax * (kSMax + 1) / 2];  // the last pass's reduced sums
     double tinv[kSMax * kSMax];     // R^{-1} (column-major, upper), for the triangular pass
     int tri_cols;                   // columns the triangular pass turns into Z R^{-1} (0: none)
     int tri_base;                   // the first of them
@@ -227,13 +227,12 @@ struct BgsArgs {
     int nblk;
     long long ntiles;
 };
-// One pass over the block (nblk CTAs), then the reduction of its sums and, for kBgsUpdGram, the
-// block's finalisation: Cholesky, Hessenberg columns, Givens rotations and the cycle's tests.
-// Every kernel returns at once when the cycle has ended.
+// One pass over the block (nblk CTAs); for kBgsDot and kBgsUpdDot the reduction of its sums follows
+// and, after kBgsUpdDot, the block's finalisation: Cholesky, Hessenberg columns, Givens rotations and
+// the cycle's tests.  The passes return at once when the cycle has ended before the block (kBgsUpdTri:
+// when the finalisation left no columns to form).
 cudaError_t launch_bgs(int prec, BgsArgs a, Cycle *st, SStep *ss, int num_sms, cudaStream_t s);
 int bgs_max_blocks(int num_sms);
-// columns tri_base .. tri_base + tri_cols - 1 of U become W R^{-1} (after a finalisation; else nothing)
-cudaError_t launch_btri(int prec, void *U, long long ld, int n, SStep *ss, int num_sms, cudaStream_t s);
 
 // ---- ILU(0) on the left (Section VI)
 // One level of the row-by-row ILU(0) factorisation (rows: the level's rows): lu holds A's values on

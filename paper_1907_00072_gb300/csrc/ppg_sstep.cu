@@ -5,14 +5,14 @@
 // s-step construction.  A block of sb vectors is built from the last orthonormal basis column q_k:
 //   Newton vectors   z_1 = (B - theta I) q_k,  z_{i+1} = (B - theta I) z_i      (B = A p(A), raw:
 //                    the SpMV chain writes them to basis columns k + 1 .. k + sb, no reductions)
-//   pass 1 (dot)     P = Q^T Z, and ||z_i||^2                       (one global reduction)
-//   pass 2 (upd+dot) Z -= Q C1,  P = Q^T Z                           (one global reduction)
-//   pass 3 (upd+gram) Z -= Q C2,  G = Z^T Z                          (one global reduction)
-//   finalisation     G = R^T R (Cholesky), the block's Hessenberg columns
-//                    H[:, k .. k+sb-1] = (S T - [H_old S_a; 0]) S_b^{-1}  (S: the change of basis
-//                    [q_k, z_1 .. z_sb] = [Q, Q_new] S; T: theta on the diagonal, 1 below), the
-//                    Givens rotations and GMRES's tests column by column
-//   triangular pass  Q_new = Z R^{-1} in place
+//   pass 1 (dot)      P = Q^T Z, and ||z_i||^2                       (one global reduction)
+//   pass 2 (upd+dot)  Z -= Q C1,  C2 = Q^T Z, and Z^T Z                (one global reduction)
+//   finalisation      the projected block's Gram matrix G = Z^T Z - C2^T C2 (Pythagoras) = R^T R
+//                     (Cholesky), the block's Hessenberg columns
+//                     H[:, k .. k+sb-1] = (S T - [H_old S_a; 0]) S_b^{-1}  (S: the change of basis
+//                     [q_k, z_1 .. z_sb] = [Q, Q_new] S; T: theta on the diagonal, 1 below), the
+//                     Givens rotations and GMRES's tests column by column
+//   pass 3 (upd+tri)  Q_new = (Z - Q C2) R^{-1} into the block's columns (no reduction)
 // Each pass streams tiles of 256 rows of the k + 1 + sb columns into shared memory with cp.async
 // (16-byte copies, no barrier waits) and accumulates per-thread sums; the per-CTA sums are reduced in
 // a fixed order by a second kernel whose last CTA finishes the pass, so results are deterministic.
@@ -179,10 +179,12 @@ __device__ __forceinline__ void for_each_tile(T *sm, int nst, const T *U, long l
     cp_async_wait(0);  // the empty groups committed past the last tile
 }
 
-// The update of the block's columns on one tile, W -= U coef, written to the tile and (rows below n)
-// to HBM.  Thread t < RG * CG takes row group t % RG (V consecutive rows) and the block's columns
-// 2 (t / RG) and 2 (t / RG) + 1; s_coef has SBP = 2 CG columns (zeros beyond SB).
-template <typename T, int SB>
+// The update of the block's columns on one tile, W -= U coef, written to the tile and (kStore, rows
+// below n) to HBM.  Thread t < RG * CG takes row group t % RG (V consecutive rows) and the block's
+// columns 2 (t / RG) and 2 (t / RG) + 1; s_coef has SBP = 2 CG columns (zeros beyond SB).  (Splitting
+// the sum over c among all the CTA's warps, with the partial sums meeting in shared memory, measured
+// slower.)
+template <typename T, int SB, bool kStore = true>
 __device__ __forceinline__ void tile_update(T *cur, int kc, const T *s_coef, T *W, long long ld, long long row0, int n)
 {
     using VT = typename Vec<T>::type;
@@ -204,6 +206,7 @@ __device__ __forceinline__ void tile_update(T *cur, int kc, const T *s_coef, T *
     }
     sW[ia * RG + rg] = wa;
     if (ib < SB) sW[ib * RG + rg] = wb;
+    if (!kStore) return;
     const long long r = row0 + (long long)rg * V;
     if (r + V <= n) {
         *reinterpret_cast<VT *>(W + ia * ld + r) = wa;
@@ -219,18 +222,23 @@ __device__ __forceinline__ void tile_update(T *cur, int kc, const T *s_coef, T *
 
 // Passes 1 and 2 (KB >= k + 1 columns of Q, bucketed so that each of the 16 warps keeps KB / 16
 // columns' sums; SB = the block size sb).  In the dot phase a lane takes V consecutive rows.
-// Slots: P[c][i] at o = c * sb + i; pass 1 also ||z_i||^2 at o = (k + 1) * sb + i.
+// Slots: P[c][i] at o = c * sb + i; pass 1 also ||z_i||^2 at o = (k + 1) * sb + i; pass 2 the Gram
+// matrix of the updated block, pair p = tri_index(i, j) at o = (k + 1) * sb + p (a thread takes row
+// group t % RG and the pairs p with p % PG = t / RG).
 template <typename T, int KB, int SB>
 __global__ void __launch_bounds__(kBT) k_bgs_dot(BgsArgs a, Cycle *st, SStep *ss, int nst)
 {
     using VT = typename Vec<T>::type;
     constexpr int V = Vec<T>::V, RG = kTR / V, CG = (SB + 1) / 2, SBP = 2 * CG;
     constexpr int CPW = KB / kBW;
+    constexpr int NG = SB * (SB + 1) / 2;
+    constexpr int PG = kBT / RG;            // pair groups (8 float32, 4 float64)
+    constexpr int NS = (NG + PG - 1) / PG;  // pairs per thread
     static_assert(CPW >= 1, "bucket below the warp count");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     __shared__ __align__(16) T s_coef[KB * SBP];
-    __shared__ double red[kBW * 2];
+    __shared__ double red[kBW * (NS > 2 ? NS : 2)];
     pdl_wait();
     pdl_trigger();
     if (st->cycle_done || st->j != a.k) return;
@@ -247,6 +255,8 @@ __global__ void __launch_bounds__(kBT) k_bgs_dot(BgsArgs a, Cycle *st, SStep *ss
 #pragma unroll
         for (int i = 0; i < SB; ++i) acc[q][i] = T(0);
     T nacc[2] = {T(0), T(0)};  // pass 1: ||W_i||^2 of this thread's two columns (update mapping)
+    KSum<T> g[NS];             // pass 2: Gram pairs
+    const int grg = tid % RG, gpg = tid / RG;
     __syncthreads();
 
     for_each_tile(sm, nst, (const T *)a.U, a.ld, kc + SB, a.n, a.ntiles, [&](T *cur, long long row0) {
@@ -255,6 +265,15 @@ __global__ void __launch_bounds__(kBT) k_bgs_dot(BgsArgs a, Cycle *st, SStep *ss
         if (upd) {
             tile_update<T, SB>(cur, kc, s_coef, W, a.ld, row0, a.n);
             __syncthreads();
+            VT gw[SB];
+#pragma unroll
+            for (int i = 0; i < SB; ++i) gw[i] = sW[i * RG + grg];
+            int p = 0;
+#pragma unroll
+            for (int i = 0; i < SB; ++i)
+#pragma unroll
+                for (int j = i; j < SB; ++j, ++p)
+                    if (p % PG == gpg) g[p / PG].add(Vec<T>::dot(gw[i], gw[j]));
         } else if (tid < RG * CG) {
             const int rg = tid % RG, ia = 2 * (tid / RG), ib = ia + 1;
             const VT x = sW[ia * RG + rg];
@@ -295,53 +314,66 @@ __global__ void __launch_bounds__(kBT) k_bgs_dot(BgsArgs a, Cycle *st, SStep *ss
         // output i = 2 g + slot is held by the warps of column group g (RG / 32 warps each)
         double nv[2] = {(double)nacc[0], (double)nacc[1]};
         group_sums<2>(nv, false, CG, RG / 32, SB, red, a.partials + (long long)(kc * SB) * a.pld, a.pld);
+    } else {
+        double gv[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) gv[q] = g[q].value();
+        group_sums<NS>(gv, true, PG, RG / 32, NG, red, a.partials + (long long)(kc * SB) * a.pld, a.pld);
     }
 }
 
-// Pass 3: W -= U coef, then G = W^T W (upper triangle packed row by row: slot tri_index(i, j, SB)).
-// After the update a thread takes row group t % RG (V rows) and the pairs p with p % PG = t / RG.
+// Pass 3: W -= U coef (the second Gram-Schmidt pass's coefficients), then Q_new = W R^{-1} into
+// columns k + 1 .. k + nq (nq = tri_cols, set by the finalisation; R^{-1} in tinv).  No reduction.
+// After the update a thread takes row group t % RG and the new columns j with j % JG = t / RG.
 template <typename T, int SB>
-__global__ void __launch_bounds__(kBT) k_bgs_gram(BgsArgs a, Cycle *st, SStep *ss, int nst)
+__global__ void __launch_bounds__(kBT) k_bgs_tri(BgsArgs a, Cycle *st, SStep *ss, int nst)
 {
     using VT = typename Vec<T>::type;
     constexpr int V = Vec<T>::V, RG = kTR / V, CG = (SB + 1) / 2, SBP = 2 * CG;
-    constexpr int NG = SB * (SB + 1) / 2;
-    constexpr int PG = kBT / RG;             // pair groups (8 float32, 4 float64)
-    constexpr int NS = (NG + PG - 1) / PG;   // pairs per thread
+    constexpr int JG = kBT / RG;  // column groups of the triangular step (8 float32, 4 float64)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     __shared__ __align__(16) T s_coef[kSColsMax * SBP];
-    __shared__ double red[kBW * NS];
+    __shared__ T tv[kSMax * kSMax];
+    __shared__ int s_last;
     pdl_wait();
     pdl_trigger();
-    if (st->cycle_done || st->j != a.k) return;
+    // the finalisation may have ended the cycle, but its columns are still formed (the cycle-end
+    // combination reads them); nothing to do when it did not run (tri_cols 0) or ran for another block
+    const int nq = ss->tri_cols;
+    if (nq == 0 || ss->tri_base != a.k + 1) return;
     const int kc = a.k + 1, tid = threadIdx.x;
-    const int rg = tid % RG, pg = tid / RG;
+    const int rg = tid % RG, jg = tid / RG;
     for (int e = tid; e < kSColsMax * SBP; e += kBT) {
         const int c = e / SBP, i = e - c * SBP;
         s_coef[e] = (c < kc && i < SB) ? (T)ss->coef[i][c] : T(0);
     }
+    for (int e = tid; e < kSMax * kSMax; e += kBT) {
+        const int j = e / kSMax, i = e - j * kSMax;
+        tv[e] = (i <= j && j < nq) ? (T)ss->tinv[e] : T(0);
+    }
     T *W = (T *)a.U + (long long)kc * a.ld;
-    KSum<T> g[NS];
     __syncthreads();
     for_each_tile(sm, nst, (const T *)a.U, a.ld, kc + SB, a.n, a.ntiles, [&](T *cur, long long row0) {
-        tile_update<T, SB>(cur, kc, s_coef, W, a.ld, row0, a.n);
+        tile_update<T, SB, false>(cur, kc, s_coef, W, a.ld, row0, a.n);
         __syncthreads();
         const VT *sW = reinterpret_cast<const VT *>(cur + kc * kTR);
-        VT wv[SB];
-#pragma unroll
-        for (int i = 0; i < SB; ++i) wv[i] = sW[i * RG + rg];
-        int p = 0;
-#pragma unroll
-        for (int i = 0; i < SB; ++i)
-#pragma unroll
-            for (int j = i; j < SB; ++j, ++p)
-                if (p % PG == pg) g[p / PG].add(Vec<T>::dot(wv[i], wv[j]));
+        const long long r = row0 + (long long)rg * V;
+        for (int j = jg; j < nq; j += JG) {
+            VT v = Vec<T>::zero();
+            for (int i = 0; i <= j; ++i) Vec<T>::fnma(v, sW[i * RG + rg], -tv[j * kSMax + i]);
+            if (r + V <= a.n) {
+                *reinterpret_cast<VT *>(W + j * a.ld + r) = v;
+            } else {
+                for (int q = 0; q < V; ++q)
+                    if (r + q < a.n) W[j * a.ld + r + q] = Vec<T>::get(v, q);
+            }
+        }
     });
-    double gv[NS];
-#pragma unroll
-    for (int q = 0; q < NS; ++q) gv[q] = g[q].value();
-    group_sums<NS>(gv, true, PG, RG / 32, NG, red, a.partials, a.pld);
+    if (last_block_done(&ss->ticket[3], &s_last) && tid == 0) {
+        ss->tri_cols = 0;
+        ss->ticket[3] = 0;
+    }
 }
 
 // index of (i, j), i <= j < sb, in the packed upper triangle the Gram pass writes
@@ -578,50 +610,61 @@ __device__ void cta_finish_block(const BgsArgs &a, Cycle *st, SStep *ss, const d
 }
 
 // Reduction of a pass's per-CTA sums (one warp per sum, fixed order), then the pass's
-// finalisation by the last CTA.
+// finalisation by the last CTA.  Pass 1: C = C1, coef = sigma .* C1, the Newton norms.  Pass 2:
+// C += C2, coef = sigma .* C2, and the block's Gram matrix after the second update by Pythagoras,
+// G = W'^T W' - C2^T C2 (W' the once-orthogonalised block, C2 = Q^T W' small against it: the
+// difference is exact to working precision), then the block's finalisation.
 __global__ void __launch_bounds__(kThreads) k_bgs_finish(BgsArgs a, Cycle *st, SStep *ss)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_last;
+    __shared__ int s_last, s_bad;
+    __shared__ double s_c2[kSMax][kSColsMax];
+    __shared__ double s_g[kSMax * (kSMax + 1) / 2];
     pdl_wait();
     pdl_trigger();
     if (st->cycle_done || st->j != a.k) return;
-    const int kc = a.k + 1, sb = a.sb, lane = threadIdx.x & 31;
+    const int kc = a.k + 1, sb = a.sb, lane = threadIdx.x & 31, ng = sb * (sb + 1) / 2;
     const int gw = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5), nw = gridDim.x * (kThreads / 32);
-    int nout;
-    if (a.op == kBgsUpdGram) nout = sb * (sb + 1) / 2;
-    else nout = kc * sb + (a.op == kBgsDot ? sb : 0);
+    const int nout = kc * sb + (a.op == kBgsDot ? sb : ng);
     for (int o = gw; o < nout; o += nw) {
         const double v = reduce_slots_f64(a.partials, a.pld, a.nblk, o);
         if (lane == 0) ss->red[o] = v;
     }
     if (!last_block_done(&ss->ticket[a.op], &s_last)) return;
     const int tid = threadIdx.x;
-    if (a.op == kBgsUpdGram) {
-        double *sh = reinterpret_cast<double *>(smem_raw);
-        const size_t sh_bytes = (size_t)(kSColsMax + kSColsMax * kSColsMax) * sizeof(double);
-        cta_finish_block(a, st, ss, ss->red, sh, sh_bytes);
-    } else {
-        // C = sigma_c P (q_c = sigma_c U_c), summed over the passes; the next update subtracts
-        // U_c (sigma_c C_pass)
-        __shared__ int s_bad;
-        if (tid == 0) s_bad = 0;
-        __syncthreads();
-        for (int e = tid; e < kc * sb; e += kThreads) {
-            const int c = e / sb, i = e - c * sb;
-            const double sg = st->sigma[c];
-            const double cv = sg * ss->red[e];
-            if (!isfinite(cv)) s_bad = 1;
-            ss->C[i][c] = a.op == kBgsDot ? cv : ss->C[i][c] + cv;
-            ss->coef[i][c] = sg * cv;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    // C = sigma_c P (q_c = sigma_c U_c), summed over the passes; the next update subtracts U_c (sigma_c C_pass)
+    for (int e = tid; e < kc * sb; e += kThreads) {
+        const int c = e / sb, i = e - c * sb;
+        const double sg = st->sigma[c];
+        const double cv = sg * ss->red[e];
+        if (!isfinite(cv)) s_bad = 1;
+        ss->C[i][c] = a.op == kBgsDot ? cv : ss->C[i][c] + cv;
+        ss->coef[i][c] = sg * cv;
+        s_c2[i][c] = cv;
+    }
+    if (a.op == kBgsDot && tid < sb) {
+        const double v = ss->red[kc * sb + tid];
+        if (!isfinite(v)) s_bad = 1;  // a raw Newton vector overflowed (a zero one is a breakdown)
+        ss->w0[tid] = v;
+    }
+    __syncthreads();
+    if (a.op == kBgsUpdDot && tid < ng) {
+        int i = 0, q = tid;  // pair tid = (i, j), packed row by row
+        while (q >= sb - i) {
+            q -= sb - i;
+            ++i;
         }
-        if (a.op == kBgsDot && tid < sb) {
-            const double v = ss->red[kc * sb + tid];
-            if (!isfinite(v)) s_bad = 1;  // a raw Newton vector overflowed (a zero one is a breakdown)
-            ss->w0[tid] = v;
-        }
-        __syncthreads();
-        if (tid == 0 && s_bad) {
+        const int j = i + q;
+        double v = ss->red[kc * sb + tid];
+        for (int c = 0; c < kc; ++c) v -= s_c2[i][c] * s_c2[j][c];
+        if (!isfinite(v)) s_bad = 1;
+        s_g[tid] = v;
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (tid == 0) {
             // a non-finite sum: the solve ends with the error
             st->error |= kErrNonfinite;
             st->stop = 1;
@@ -629,59 +672,19 @@ __global__ void __launch_bounds__(kThreads) k_bgs_finish(BgsArgs a, Cycle *st, S
             st->k = 0;
             publish_progress(st, 1, st->j);
         }
+    } else if (a.op == kBgsUpdDot) {
+        double *sh = reinterpret_cast<double *>(smem_raw);
+        const size_t sh_bytes = (size_t)(kSColsMax + kSColsMax * kSColsMax) * sizeof(double);
+        cta_finish_block(a, st, ss, s_g, sh, sh_bytes);
     }
     if (tid == 0) ss->ticket[a.op] = 0;
 }
 
-// Q_new = W R^{-1}: columns tri_base .. tri_base + tri_cols - 1 in place, V rows per thread (16-byte
-// accesses; the ragged end of the rows element by element).
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_btri(T *U, long long ld, int n, SStep *ss)
-{
-    using VT = typename Vec<T>::type;
-    constexpr int V = Vec<T>::V;
-    __shared__ T tv[kSMax * kSMax];
-    __shared__ int s_last;
-    pdl_wait();
-    pdl_trigger();
-    const int nq = ss->tri_cols;
-    if (nq == 0) return;
-    const int base = ss->tri_base;
-    for (int e = threadIdx.x; e < kSMax * kSMax; e += kThreads) {
-        const int j = e / kSMax, i = e - j * kSMax;
-        tv[e] = (i <= j && j < nq) ? (T)ss->tinv[e] : T(0);
-    }
-    __syncthreads();
-    T *W = U + (long long)base * ld;
-    const long long ngroups = ((long long)n + V - 1) / V;
-    for (long long g = blockIdx.x * (long long)kThreads + threadIdx.x; g < ngroups; g += (long long)gridDim.x * kThreads) {
-        const long long r = g * V;
-        VT w[kSMax];
-#pragma unroll
-        for (int i = 0; i < kSMax; ++i) w[i] = i < nq ? *reinterpret_cast<const VT *>(W + i * ld + r) : Vec<T>::zero();
-#pragma unroll
-        for (int j = 0; j < kSMax; ++j) {
-            if (j < nq) {
-                VT v = Vec<T>::zero();
-#pragma unroll
-                for (int i = 0; i <= j; ++i) Vec<T>::fnma(v, w[i], -tv[j * kSMax + i]);
-                if (r + V <= n) {
-                    *reinterpret_cast<VT *>(W + j * ld + r) = v;
-                } else {
-                    for (int q = 0; q < V; ++q)
-                        if (r + q < n) W[j * ld + r + q] = Vec<T>::get(v, q);
-                }
-            }
-        }
-    }
-    if (last_block_done(&ss->ticket[3], &s_last) && threadIdx.x == 0) {
-        ss->tri_cols = 0;
-        ss->ticket[3] = 0;
-    }
-}
-
-// dynamic shared memory of a pass CTA, at most: two CTAs of 16 warps fit one SM where their registers do
+// Stages of a pass CTA fill this much dynamic shared memory (two CTAs of 16 warps fit one SM where their
+// registers do); a single stage may be larger: up to (64 + 8) columns of 256 float64 rows, 144 KB,
+// within the attribute kBgsSmemAttr every pass kernel is given.
 constexpr size_t kBgsSmemMax = 110 * 1024;
+constexpr size_t kBgsSmemAttr = (size_t)(kSColsMax + kSMax) * kTR * sizeof(double);
 
 // shared memory of one stage, and the stage count: as many as the budget holds, 1 .. kMaxStages
 template <typename T>
@@ -702,7 +705,7 @@ cudaError_t go_pass(void (*kernel)(KArgs...), int key, BgsArgs &a, Cycle *st, SS
     static bool attr[4 * kSMax] = {};
     static int per[4 * kSMax][kMaxStages * (kSColsMax + kSMax) + 1] = {};
     if (!attr[key]) {
-        const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBgsSmemMax);
+        const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBgsSmemAttr);
         if (e != cudaSuccess) return e;
         attr[key] = true;
     }
@@ -723,7 +726,7 @@ cudaError_t launch_pass_sb(BgsArgs &a, Cycle *st, SStep *ss, size_t smem, int ns
 {
     const int kc = a.k + 1;
     const int key = 4 * (SB - 1);
-    if (a.op == kBgsUpdGram) return go_pass<T>(k_bgs_gram<T, SB>, key, a, st, ss, smem, nst, num_sms, s);
+    if (a.op == kBgsUpdTri) return go_pass<T>(k_bgs_tri<T, SB>, key, a, st, ss, smem, nst, num_sms, s);
     if (kc <= 16) return go_pass<T>(k_bgs_dot<T, 16, SB>, key + 1, a, st, ss, smem, nst, num_sms, s);
     if (kc <= 32) return go_pass<T>(k_bgs_dot<T, 32, SB>, key + 2, a, st, ss, smem, nst, num_sms, s);
     return go_pass<T>(k_bgs_dot<T, 64, SB>, key + 3, a, st, ss, smem, nst, num_sms, s);
@@ -747,7 +750,7 @@ cudaError_t launch_bgs_t(BgsArgs a, Cycle *st, SStep *ss, int num_sms, cudaStrea
     case 7: e = launch_pass_sb<T, 7>(a, st, ss, smem, nst, num_sms, s); break;
     default: e = launch_pass_sb<T, 8>(a, st, ss, smem, nst, num_sms, s); break;
     }
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || a.op == kBgsUpdTri) return e;
     static bool attr = false;
     const size_t fsm = (size_t)(kSColsMax + kSColsMax * kSColsMax) * sizeof(double);
     if (!attr) {
@@ -755,7 +758,7 @@ cudaError_t launch_bgs_t(BgsArgs a, Cycle *st, SStep *ss, int num_sms, cudaStrea
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int nout = a.op == kBgsUpdGram ? a.sb * (a.sb + 1) / 2 : kc * a.sb + (a.op == kBgsDot ? a.sb : 0);
+    const int nout = kc * a.sb + (a.op == kBgsDot ? a.sb : a.sb * (a.sb + 1) / 2);
     const int grid = (nout + kThreads / 32 - 1) / (kThreads / 32);
     return launch_pdl(k_bgs_finish, dim3(grid), dim3(kThreads), fsm, s, a, st, ss);
 }
@@ -766,19 +769,11 @@ int bgs_max_blocks(int num_sms) { return 3 * num_sms; }
 
 cudaError_t launch_bgs(int prec, BgsArgs a, Cycle *st, SStep *ss, int num_sms, cudaStream_t s)
 {
-    if (a.k < 0 || a.k + 1 > kSColsMax || a.sb < 1 || a.sb > kSMax || a.op < kBgsDot || a.op > kBgsUpdGram ||
+    if (a.k < 0 || a.k + 1 > kSColsMax || a.sb < 1 || a.sb > kSMax || a.op < kBgsDot || a.op > kBgsUpdTri ||
         a.nblk < 1 || a.nblk > bgs_max_blocks(num_sms) || (a.pld & 1) || a.pld < a.nblk)
         return cudaErrorInvalidValue;
     a.ntiles = ((long long)a.n + kTR - 1) / kTR;
     return prec == kF64 ? launch_bgs_t<double>(a, st, ss, num_sms, s) : launch_bgs_t<float>(a, st, ss, num_sms, s);
-}
-
-cudaError_t launch_btri(int prec, void *U, long long ld, int n, SStep *ss, int num_sms, cudaStream_t s)
-{
-    const long long rows_blocks = ((long long)n + 4LL * kThreads - 1) / (4LL * kThreads);
-    const int grid = (int)(rows_blocks < 4LL * num_sms ? (rows_blocks > 0 ? rows_blocks : 1) : 4LL * num_sms);
-    if (prec == kF64) return launch_pdl(k_btri<double>, dim3(grid), dim3(kThreads), 0, s, (double *)U, ld, n, ss);
-    return launch_pdl(k_btri<float>, dim3(grid), dim3(kThreads), 0, s, (float *)U, ld, n, ss);
 }
 
 }  // namespace ppg

@@ -129,6 +129,26 @@ def test_sstep_lucky_breakdown_on_an_exhausted_krylov_space(prec):
     sol.close()
 
 
+@pytest.mark.parametrize("prec", [ppg.PPG_F64, ppg.PPG_F32])
+def test_sstep_largest_blocks_and_restart(prec):
+    """restart 64 with blocks of 8 (the largest basis the block passes stage: 64 + 8 columns per tile,
+    144 KB of float64) and blocks of 7 that do not divide it: the solve converges to the oracle's
+    solution."""
+    a = w.convdiff(17, 3, 20.0)
+    b = w.rhs(a.n)
+    v0 = w.v0(a.n)
+    sol = solver_for(a)
+    sol.build_poly(4, ppg.PPG_BASIS_ROOTS, v0=T(v0))
+    ref = oracle.gmres(a, b, oracle.poly_gmres(a, v0, 4), tol=1e-10, m=64, maxit=5000)
+    for s in (8, 7):
+        x, info = sol.solve(T(b), tol=1e-10 if prec == ppg.PPG_F64 else 1e-8, restart=64, maxit=5000, precision=prec,
+                            sstep=s, sstep_shift=1.0)
+        xg = x.cpu().numpy()
+        assert info.status == ppg.PPG_OK, (s, info.stats)
+        assert np.linalg.norm(xg - ref.x) <= (1e-8 if prec == ppg.PPG_F64 else 1e-6) * np.linalg.norm(ref.x)
+    sol.close()
+
+
 def test_sstep_zero_rhs_exact_start_and_maxit():
     a = w.c1_matrix()
     sol = solver_for(a)
