@@ -234,6 +234,8 @@ def main():
     ap.add_argument("--harness-iters", type=int, default=20)
     ap.add_argument("--spmv-format", default="auto", choices=["auto", "csr", "sell", "staged"],
                     help="sparse format of the SpMV kernels (ppg_spmv_format)")
+    ap.add_argument("--sstep", type=int, default=0,
+                    help="s-step blocks of this many Newton vectors in the timed solve (float32: standard form)")
     ap.add_argument("--systems", type=int, default=0,
                     help="c4: solve only the first N systems of the batch (0: all 256), without the one-by-one "
                          "comparison when N > 0 (a small case for profiling)")
@@ -279,7 +281,8 @@ def main():
         s.close()
         return
 
-    def step(deg=args.degree, precision=prec, bvec=b, f32_form=ppg.PPG_F32_FLEXIBLE, sstep=0):
+    def step(deg=args.degree, precision=prec, bvec=b,
+             f32_form=ppg.PPG_F32_STANDARD if args.sstep else ppg.PPG_F32_FLEXIBLE, sstep=args.sstep):
         used, _ = s.build_poly(deg, ppg.PPG_BASIS_ROOTS, v0=v0)
         x, info = s.solve(bvec, tol=1e-8, restart=50, maxit=20000, precision=precision, f32_form=f32_form,
                           sstep=sstep, sstep_shift=1.0)
@@ -404,8 +407,10 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload_name(args.N, a.nnz), "degree": args.degree, "basis": "roots (Leja)",
                    "restart": 50,
-                   "precision": ("f32 inner (flexible form, restart projection), f64 refinement"
+                   "precision": ("f32 inner (standard form, s-step blocks), f64 refinement" if prec == ppg.PPG_F32
+                                 and args.sstep else "f32 inner (flexible form, restart projection), f64 refinement"
                                  if prec == ppg.PPG_F32 else "f64"),
+                   "sstep": args.sstep,
                    "l2": "working set of a step larger than L2 (matrix blocks 88 MB float32 + 117 MB "
                          "float64, basis up to 428 MB float32), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
