@@ -55,13 +55,13 @@ def _T(a, dt=torch.float64):
     return torch.as_tensor(np.asarray(a), dtype=dt, device=DEV)
 
 
-def _gpu_solve(config, degree, precision):
+def _gpu_solve(config, degree, precision, **kw):
     a = _matrix(config)
     b = w.rhs(a.n)
     s = ppg.Solver(_T(a.rowptr, torch.int32), _T(a.colidx, torch.int32), _T(a.vals))
     used, _ = s.build_poly(degree, ppg.PPG_BASIS_ROOTS, v0=_T(w.v0(a.n)))
     assert used == degree
-    x, info = s.solve(_T(b), tol=1e-8, restart=50, maxit=5000, precision=precision)
+    x, info = s.solve(_T(b), tol=1e-8, restart=50, maxit=5000, precision=precision, **kw)
     xs = x.cpu().numpy()
     s.close()
     relres = np.linalg.norm(b - oracle.spmv(a, xs)) / np.linalg.norm(b)
@@ -97,3 +97,30 @@ def test_c2_float32_refined_matches_oracle(oracle_runs, degree):
 
 def test_c3_degree25_float32_refined_matches_oracle(oracle_runs):
     _check("c3", 25, ppg.PPG_F32, oracle_runs[("c3", 25)].result())
+
+
+def test_c2_degree10_sstep_float64_matches_oracle(oracle_runs):
+    """s-step blocks of 5 (Section VII's combination) in float64: in exact arithmetic GMRES's iterates,
+    so the standard oracle's solution and iteration count (within 5%) hold."""
+    ref = oracle_runs[("c2", 10)].result()
+    xs, info, relres = _gpu_solve("c2", 10, ppg.PPG_F64, sstep=5, sstep_shift=1.0)
+    err = np.linalg.norm(xs - ref["x"]) / np.linalg.norm(ref["x"])
+    msg = f"s-step float64: {info.stats['iterations']} iterations (oracle {ref['iters']}), relres {relres:.3e}, err {err:.3e}"
+    assert info.status == ppg.PPG_OK and relres <= 1e-8 and err <= 1e-6, msg
+    assert abs(info.stats["iterations"] - ref["iters"]) <= 0.05 * ref["iters"], msg
+    assert info.stats["dots"] < 0.3 * 3 * ref["iters"], msg  # 3 reductions per block of 5, not 3 per iteration
+    print(msg)
+
+
+def test_c2_degree10_sstep_float32_matches_oracle(oracle_runs):
+    """s-step blocks of 4 in float32 with float64 refinement (standard form): the oracle's solution, and
+    the iteration count of the library's standard-form float32 solve without blocks, within one."""
+    ref = oracle_runs[("c2", 10)].result()
+    xs, info, relres = _gpu_solve("c2", 10, ppg.PPG_F32, sstep=4, sstep_shift=1.0)
+    _, info_std, _ = _gpu_solve("c2", 10, ppg.PPG_F32, f32_form=ppg.PPG_F32_STANDARD)
+    err = np.linalg.norm(xs - ref["x"]) / np.linalg.norm(ref["x"])
+    msg = (f"s-step float32: {info.stats['iterations']} iterations (standard form {info_std.stats['iterations']}, "
+           f"oracle {ref['iters']}), relres {relres:.3e}, err {err:.3e}")
+    assert info.status == ppg.PPG_OK and relres <= 1e-8 and err <= 1e-6, msg
+    assert abs(info.stats["iterations"] - info_std.stats["iterations"]) <= 1, msg
+    print(msg)
