@@ -60,16 +60,19 @@ def test_round_counter_wait_runs_out_and_the_context_recovers():
     s.close()
 
 
-def test_host_progress_wait_runs_out_and_the_context_recovers():
+@pytest.mark.parametrize("sstep", [0, 4])
+def test_host_progress_wait_runs_out_and_the_context_recovers(sstep):
+    """Iterations (sstep 0) or s-step blocks of 4 (the host queues two blocks ahead): the host's wait for
+    the device's progress runs out after 1 us, and the next solve on the same context succeeds."""
     a = w.c2_matrix(96)  # 884,736 rows: an iteration takes far longer than the host needs to queue two
     b = w.rhs(a.n)
     s = _solver(a)
     s.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=_T(w.v0(a.n)))
     with pytest.raises(ppg.PPGError) as e:
-        s.solve(_T(b), tol=1e-8, restart=50, maxit=500, precision=ppg.PPG_F32, wait_limit_us=1)
+        s.solve(_T(b), tol=1e-8, restart=50, maxit=500, precision=ppg.PPG_F32, wait_limit_us=1, sstep=sstep)
     assert e.value.status == ppg.PPG_ERR_TIMEOUT
     assert "wait for the device's progress ran out" in str(e.value)
-    x, info = s.solve(_T(b), tol=1e-8, restart=50, maxit=500, precision=ppg.PPG_F32)
+    x, info = s.solve(_T(b), tol=1e-8, restart=50, maxit=500, precision=ppg.PPG_F32, sstep=sstep)
     assert info.status == ppg.PPG_OK and _relres(a, b, x.cpu().numpy()) <= 1e-8
     s.close()
 
