@@ -61,3 +61,25 @@ def test_missing_library_fails_loudly(tmp_path):
     mod._lib = None
     with pytest.raises(ImportError):
         mod.load_library(str(tmp_path / "libppg.so"))
+
+
+@pytest.mark.parametrize("name", ["ppg_opts", "ppg_stats", "ppg_batch_system"])
+def test_struct_layouts_match_the_header(name, tmp_path):
+    """The binding's ctypes mirrors of the header's structs have the C compiler's size and field
+    offsets (a host program built with gcc against include/ppg.h prints them)."""
+    cls = getattr(ppg, name)
+    fields = [f for f, _ in cls._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "ppg.h"', "int main(void) {",
+             f'    printf("%zu\\n", sizeof({name}));']
+    lines += [f'    printf("%zu\\n", offsetof({name}, {f}));' for f in fields]
+    lines += ["    return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    import ctypes
+
+    assert out[0] == ctypes.sizeof(cls), (name, out[0], ctypes.sizeof(cls))
+    for f, off in zip(fields, out[1:]):
+        assert getattr(cls, f).offset == off, (name, f, off, getattr(cls, f).offset)
