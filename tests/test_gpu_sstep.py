@@ -181,3 +181,29 @@ def test_sstep_rejects_bad_arguments():
         sol.solve(b, tol=1e-8, restart=20, sstep=4)
     assert e.value.status == ppg.PPG_ERR_INVALID_ARG
     sol.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5])
+def test_sstep_tiny_systems(n):
+    """Degenerate sizes: the Krylov space has at most n dimensions, so a block of 4 Newton vectors is
+    rank-deficient from n = 1 on (the block ends in a lucky breakdown); blocks larger than the restart
+    length (restart 2 with blocks of 4) shrink to it.  Every solve reaches the dense solution."""
+    rng = np.random.default_rng(n)
+    dense = rng.uniform(-1, 1, (n, n)) + np.diag(np.full(n, n + 2.0))
+    rp = np.arange(0, n * n + 1, n, dtype=np.int32)
+    ci = np.tile(np.arange(n, dtype=np.int32), n)
+    a = w.CSR(n, rp, ci, dense.reshape(-1), f"dense{n}")
+    b = w.uniform(3, n)
+    xd = np.linalg.solve(dense, b)
+    sol = solver_for(a)
+    for poly in (False, True):
+        if poly:
+            sol.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=T(w.uniform(4, n)))
+        for prec in (ppg.PPG_F64, ppg.PPG_F32):
+            for restart in (2, 10):
+                x, info = sol.solve(T(b), tol=1e-10, restart=restart, maxit=200, precision=prec, sstep=4,
+                                    sstep_shift=1.0)
+                assert info.status == ppg.PPG_OK, (poly, prec, restart, info.stats)
+                np.testing.assert_allclose(x.cpu().numpy(), xd, rtol=1e-8, atol=1e-12)
+    sol.close()
+
