@@ -6,10 +6,13 @@ Workload: 3D convection-diffusion, 7-point upwind stencil on a 128^3 grid
 Peclet 50, b uniform in [-1, 1] (SplitMix64 seed 1), x0 = 0, GMRES(50), relative
 residual 1e-8.  One step = build the minimum-residual polynomial (roots form,
 v0 from seed 2) + solve, inputs resident in HBM.  The headline is the float32
-p(A)/Arnoldi solve with float64 iterative refinement; the float64 solve and the
-other degrees are reported under "variants".
+p(A)/Arnoldi solve with float64 iterative refinement, its basis built in s-step
+blocks of 4 Newton vectors (Section VII's combination of the polynomial with an
+s-step method: the same GMRES iterates, three global reductions per block); the
+solve without blocks (--sstep 0), the float64 solve and the other degrees are
+reported under "variants".
 
-  python bench.py [--gpus N --steps K --warmup W] [--degree D] [--precision f32|f64]
+  python bench.py [--gpus N --steps K --warmup W] [--degree D] [--precision f32|f64] [--sstep S]
   python bench.py --impl reference ...   # the CPU oracle: one full solve per step, same metric
 """
 from __future__ import annotations
@@ -234,8 +237,9 @@ def main():
     ap.add_argument("--harness-iters", type=int, default=20)
     ap.add_argument("--spmv-format", default="auto", choices=["auto", "csr", "sell", "staged"],
                     help="sparse format of the SpMV kernels (ppg_spmv_format)")
-    ap.add_argument("--sstep", type=int, default=0,
-                    help="s-step blocks of this many Newton vectors in the timed solve (float32: standard form)")
+    ap.add_argument("--sstep", type=int, default=4,
+                    help="s-step blocks of this many Newton vectors in the timed solve (Section VII's combination; "
+                         "0: one basis vector per orthogonalisation)")
     ap.add_argument("--systems", type=int, default=0,
                     help="c4: solve only the first N systems of the batch (0: all 256), without the one-by-one "
                          "comparison when N > 0 (a small case for profiling)")
@@ -281,8 +285,7 @@ def main():
         s.close()
         return
 
-    def step(deg=args.degree, precision=prec, bvec=b,
-             f32_form=ppg.PPG_F32_STANDARD if args.sstep else ppg.PPG_F32_FLEXIBLE, sstep=args.sstep):
+    def step(deg=args.degree, precision=prec, bvec=b, f32_form=ppg.PPG_F32_FLEXIBLE, sstep=args.sstep):
         used, _ = s.build_poly(deg, ppg.PPG_BASIS_ROOTS, v0=v0)
         x, info = s.solve(bvec, tol=1e-8, restart=50, maxit=20000, precision=precision, f32_form=f32_form,
                           sstep=sstep, sstep_shift=1.0)
@@ -329,18 +332,25 @@ def main():
     # every SpMV-chain and Gram-Schmidt launch on the library's stream, with algorithmic bytes
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
+    # the timed configuration's solve (its SpMV chain is the dominant kernel; with s-step blocks its
+    # "Gram-Schmidt" class holds the block passes, their reductions and finalisation, and the cycle ends)
     s.build_poly(args.degree, ppg.PPG_BASIS_ROOTS, v0=v0)
-    _, pinfo = s.solve(b, tol=1e-8, restart=50, maxit=20000, precision=prec, profile=1)
+    _, pinfo = s.solve(b, tol=1e-8, restart=50, maxit=20000, precision=prec, profile=1, sstep=args.sstep or 4,
+                       sstep_shift=1.0)
     ps = pinfo.stats
     spmv_gbs = ps["spmv_bytes"] / (ps["spmv_ms"] * 1e-3) / 1e9
-    gs_gbs = ps["gs_bytes"] / (ps["gs_ms"] * 1e-3) / 1e9
-    # the s-step solve's block passes (blocks of 4 Newton vectors; Section VII's combination), profiled
-    # the same way: the three block passes, their reductions and finalisation, and Z R^-1 per block
-    s.build_poly(args.degree, ppg.PPG_BASIS_ROOTS, v0=v0)
-    _, sinfo = s.solve(b, tol=1e-8, restart=50, maxit=20000, precision=prec, profile=1, sstep=4, sstep_shift=1.0,
-                       f32_form=ppg.PPG_F32_STANDARD)
-    sps = sinfo.stats
+    sps = ps
     sstep_gbs = sps["gs_bytes"] / (sps["gs_ms"] * 1e-3) / 1e9
+    if not args.sstep:  # the timed configuration has no blocks: its own solve for the chain
+        s.build_poly(args.degree, ppg.PPG_BASIS_ROOTS, v0=v0)
+        _, pinfo = s.solve(b, tol=1e-8, restart=50, maxit=20000, precision=prec, profile=1)
+        ps = pinfo.stats
+        spmv_gbs = ps["spmv_bytes"] / (ps["spmv_ms"] * 1e-3) / 1e9
+    # the two-pass classical Gram-Schmidt kernel of a solve without blocks
+    s.build_poly(args.degree, ppg.PPG_BASIS_ROOTS, v0=v0)
+    _, oinfo = s.solve(b, tol=1e-8, restart=50, maxit=20000, precision=prec, profile=1)
+    ops = oinfo.stats
+    gs_gbs = ops["gs_bytes"] / (ops["gs_ms"] * 1e-3) / 1e9
     # plain SpMV y = A x of the benchmark matrix, one event pair per launch
     dtype_t = torch.float32 if prec == ppg.PPG_F32 else torch.float64
     sv = 4 if prec == ppg.PPG_F32 else 8
@@ -366,9 +376,12 @@ def main():
     if not args.no_variants:
         forms = (("f64", ppg.PPG_F64, ppg.PPG_F32_FLEXIBLE), ("f32", ppg.PPG_F32, ppg.PPG_F32_FLEXIBLE),
                  ("f32_standard", ppg.PPG_F32, ppg.PPG_F32_STANDARD))
-        # s-step blocks (Section VII's combination; standard float32 form, Newton shift 1) at the headline degree
+        # without blocks at every degree; s-step blocks (Section VII's combination, Newton shift 1) at the
+        # headline degree
         runs = [(deg, pname, pv, form, 0) for deg in (1, 10, 25, 40) for pname, pv, form in forms]
-        runs += [(args.degree, f"f32_sstep{k}", ppg.PPG_F32, ppg.PPG_F32_STANDARD, k) for k in (4, 5, 8)]
+        runs += [(args.degree, f"f32_sstep{k}", ppg.PPG_F32, ppg.PPG_F32_FLEXIBLE, k) for k in (2, 4, 5, 8)]
+        runs += [(args.degree, "f32_standard_sstep4", ppg.PPG_F32, ppg.PPG_F32_STANDARD, 4)]
+        runs += [(deg, "f32_sstep4", ppg.PPG_F32, ppg.PPG_F32_FLEXIBLE, 4) for deg in (25, 40)]
         runs += [(args.degree, "f64_sstep5", ppg.PPG_F64, ppg.PPG_F32_FLEXIBLE, 5)]
         for deg, pname, pv, form, sst in runs:
             step(deg, pv, f32_form=form, sstep=sst)
@@ -407,9 +420,11 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload_name(args.N, a.nnz), "degree": args.degree, "basis": "roots (Leja)",
                    "restart": 50,
-                   "precision": ("f32 inner (standard form, s-step blocks), f64 refinement" if prec == ppg.PPG_F32
-                                 and args.sstep else "f32 inner (flexible form, restart projection), f64 refinement"
-                                 if prec == ppg.PPG_F32 else "f64"),
+                   "precision": ("f32 inner (flexible form, restart projection), f64 refinement" if prec == ppg.PPG_F32
+                                 else "f64"),
+                   "orthogonalisation": (f"s-step blocks of {args.sstep} Newton vectors (shift 1): block CGS2 + "
+                                         f"Cholesky QR, 3 global reductions per block" if args.sstep
+                                         else "two-pass classical Gram-Schmidt per basis vector"),
                    "sstep": args.sstep,
                    "l2": "working set of a step larger than L2 (matrix blocks 88 MB float32 + 117 MB "
                          "float64, basis up to 428 MB float32), no flush",
@@ -426,12 +441,13 @@ def main():
                      "traffic_note": traffic_info,
                      "timed_segments": ps["spmv_segments"], "ms_total": round(ps["spmv_ms"], 3),
                      "bytes_total": ps["spmv_bytes"]},
-        "roofline_ortho": {"bound": "hbm", "kernel": "k_gs (two-pass classical Gram-Schmidt)",
+        "roofline_ortho": {"bound": "hbm", "kernel": "k_gs (two-pass classical Gram-Schmidt, solve without blocks)",
                            "achieved": round(gs_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gs_gbs / hbm, 3),
-                           "timed_segments": ps["gs_segments"], "ms_total": round(ps["gs_ms"], 3),
-                           "bytes_total": ps["gs_bytes"]},
-        "roofline_sstep": {"bound": "hbm", "kernel": "k_bgs_dot, k_bgs_gram, k_bgs_finish, k_btri (s-step blocks of "
-                                                     "4 Newton vectors: block CGS2, Cholesky QR, Hessenberg recovery)",
+                           "timed_segments": ops["gs_segments"], "ms_total": round(ops["gs_ms"], 3),
+                           "bytes_total": ops["gs_bytes"]},
+        "roofline_sstep": {"bound": "hbm", "kernel": f"k_bgs_dot, k_bgs_finish, k_bgs_tri (s-step blocks of "
+                                                     f"{args.sstep or 4} Newton vectors: block CGS2, Cholesky QR, "
+                                                     f"Hessenberg recovery; cycle ends included)",
                            "achieved": round(sstep_gbs, 1), "peak": hbm, "unit": "GB/s",
                            "frac": round(sstep_gbs / hbm, 3), "timed_segments": sps["gs_segments"],
                            "ms_total": round(sps["gs_ms"], 3), "bytes_total": sps["gs_bytes"],

@@ -710,14 +710,16 @@ struct Exec {
     // iteration) and w = A z.  When the product form ends with a real root, the last update
     // z = y + t P rides on the SpMV's gather as in poly_then_A, and the SpMV's second output writes
     // that z (the same fused value the gather used) to zdst.
-    ppg_status poly_then_A_flex(VecRef src, const double *sig, VecRef zdst, VecRef w, char *const tmp[4], int check)
+    ppg_status poly_then_A_flex(VecRef src, const double *sig, VecRef zdst, VecRef w, char *const tmp[4], int check,
+                                double shift = 0.0)
     {
         chain_begin();
-        PPG_TRY(poly_then_A_flex_links(src, sig, zdst, w, tmp, check));
+        PPG_TRY(poly_then_A_flex_links(src, sig, zdst, w, tmp, check, shift));
         return chain_end();
     }
+    // (shift: w = A z - shift * (scale * src), on the last SpMV's epilogue, for the s-step Newton basis)
     ppg_status poly_then_A_flex_links(VecRef src, const double *sig, VecRef zdst, VecRef w, char *const tmp[4],
-                                      int check)
+                                      int check, double shift)
     {
         char *t3[3] = {tmp[1], tmp[2], tmp[3]};
         const int k = c->degree + 1;
@@ -746,6 +748,10 @@ struct Exec {
             PPG_TRY(axpy(cpy, check));
             e.x = zdst;
         }
+        if (shift != 0.0) {
+            e.u0 = src;
+            e.b0 = sscaled(-shift, sig);
+        }
         return spmv(e, check);
     }
 
@@ -764,6 +770,7 @@ struct Iter {
     const Layout *L;
     int maxcols;  // restart + 1: bound on the columns a cycle-end combination uses
     bool flex = false;  // flexible float32 form: z_j = p(A) v_j kept in L->zbasis, x += Z y
+    bool sstep = false; // s-step blocks: the flexible form keeps P (Z = P M) and transforms y first
 
     // U: the basis the pass streams (null: the Krylov basis V); w: its vector input (null: vec[0])
     ppg_status gs(int op, int from_k, void *out, int out_follow, int kcols, const void *U = nullptr,
@@ -836,9 +843,15 @@ struct Iter {
         c->prof_j = k;
         char *tmp[4] = {L->vec[1], L->vec[2], L->vec[3], L->vec[4]};
         prof_open(c, x->s, 0);
-        for (int i = 0; i < sb; ++i)  // columns follow the device's j (= k): j + i -> j + i + 1
-            PPG_TRY(x->poly_then_A(vcol(L->basis, c->ld, i), i == 0 ? c->st->sigma : nullptr,
-                                   vcol(L->basis, c->ld, i + 1), tmp, kSkipIfDone, theta));
+        for (int i = 0; i < sb; ++i) {  // columns follow the device's j (= k): j + i -> j + i + 1
+            if (flex)  // the flexible form keeps P_i = p(A) u_i in column j + i of Z
+                PPG_TRY(x->poly_then_A_flex(vcol(L->basis, c->ld, i), i == 0 ? c->st->sigma : nullptr,
+                                            vcol(L->zbasis, c->ld, i), vcol(L->basis, c->ld, i + 1), tmp,
+                                            kSkipIfDone, theta));
+            else
+                PPG_TRY(x->poly_then_A(vcol(L->basis, c->ld, i), i == 0 ? c->st->sigma : nullptr,
+                                       vcol(L->basis, c->ld, i + 1), tmp, kSkipIfDone, theta));
+        }
         prof_close(c, x->s);
         prof_open(c, x->s, 1);
         BgsArgs a{};
@@ -852,6 +865,7 @@ struct Iter {
         a.partials = c->d_bgs_partials;
         a.pld = c->bgs_pld;
         a.nblk = bgs_max_blocks(c->num_sms);
+        a.flex = flex ? 1 : 0;
         const double col = (double)x->A->n * (x->prec == kF64 ? 8.0 : 4.0);
         for (int op : {kBgsDot, kBgsUpdDot, kBgsUpdTri}) {
             a.op = op;
@@ -948,6 +962,10 @@ struct Iter {
         x->c->prof_j = -2;
         if (flex) {
             prof_open(x->c, x->s, 1);
+            if (sstep) {
+                x->c->launches++;
+                PPG_CK(launch_sstep_flex_y(x->c->st, x->c->d_sstep, 0, x->s));
+            }
             PPG_TRY(combine_x(xsol, 0));
             prof_close(x->c, x->s);
             return PPG_OK;
@@ -980,6 +998,10 @@ struct Iter {
         PPG_CK(launch_residual(c->A, x->prec, b, xsol, L->vec[7], c->st, L->partials, x->s, 1));
         prof_open(c, x->s, 1);
         PPG_TRY(gs(kGsProj, 1, nullptr, 0, maxcols, L->basis, L->vec[7]));
+        if (sstep) {
+            c->launches++;
+            PPG_CK(launch_sstep_flex_y(c->st, c->d_sstep, 1, x->s));
+        }
         PPG_TRY(combine_x(xsol, 1));
         prof_close(c, x->s);
         return PPG_OK;
@@ -1310,10 +1332,10 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
         if (!std::isfinite(theta)) return fail(PPG_ERR_INVALID_ARG, "the s-step shift must be finite");
     }
     // the flexible form keeps z_j = p(A) v_j; with no polynomial (or a scalar one) z_j is v_j itself
-    // (with ILU(0) on the left the standard form runs: its operator is M^{-1} A throughout; s-step
-    // solves use the standard form: their block's vectors are not the preconditioned basis)
+    // (with ILU(0) on the left the standard form runs: its operator is M^{-1} A throughout).  s-step
+    // solves keep the chains' p(A) u_i instead and combine them through M (Z = P M)
     const bool flex = prec == PPG_F32 && form == PPG_F32_FLEXIBLE && c->has_poly &&
-                      !(c->basis == PPG_BASIS_POWER && c->degree == 0) && !c->ilu_on && sstep == 0;
+                      !(c->basis == PPG_BASIS_POWER && c->degree == 0) && !c->ilu_on;
     // limits of the software waits for this solve (the context keeps the defaults otherwise)
     c->waits = WaitCfg{};
     if (opts && opts->wait_limit_us > 0 && opts->wait_limit_us < 1000000)
@@ -1342,6 +1364,7 @@ ppg_status solve_impl(ppg_ctx *c, const double *b, double *x, double tol, int re
     Exec ex{c, &c->A, prec, c->stream};
     Iter it{&ex, &L, ncols};
     it.flex = flex;
+    it.sstep = sstep > 0;
     it.use_graph = !opts || opts->use_graph != 0;
     c->prof = opts && opts->profile;
     c->prof_open = false;

@@ -209,6 +209,9 @@ struct SStep {
     double w0[kSMax];               // ||z_i||^2 before the projections
     double red[kSMax * kSColsMax + kSMax * (kSMax + 1) / 2];  // the last pass's reduced sums
     double tinv[kSMax * kSMax];     // R^{-1} (column-major, upper), for the triangular pass
+    // flexible float32 form: the preconditioned basis is Z = P M, P the chains' p(A) u_i (stored where
+    // the flexible form keeps Z), M upper triangular, column j at M[j][0 .. j]
+    double M[kSColsMax][kSColsMax];
     int tri_cols;                   // columns the triangular pass turns into Z R^{-1} (0: none)
     int tri_base;                   // the first of them
     unsigned int ticket[4];
@@ -226,6 +229,7 @@ struct BgsArgs {
     int pld;
     int nblk;
     long long ntiles;
+    int flex;          // 1: flexible float32 form (the finalisation extends M)
 };
 // One pass over the block (nblk CTAs); for kBgsDot and kBgsUpdDot the reduction of its sums follows
 // and, after kBgsUpdDot, the block's finalisation: Cholesky, Hessenberg columns, Givens rotations and
@@ -233,6 +237,10 @@ struct BgsArgs {
 // when the finalisation left no columns to form).
 cudaError_t launch_bgs(int prec, BgsArgs a, Cycle *st, SStep *ss, int num_sms, cudaStream_t s);
 int bgs_max_blocks(int num_sms);
+// Flexible s-step form, before x += Z y: y <- M y over the cycle's k columns (Z = P M), so that the
+// combination of the stored p(A) u_i with y gives x's correction.  Returns at once when k = 0 or
+// (skip_if_stop) the solve has stopped, like the combination.
+cudaError_t launch_sstep_flex_y(Cycle *st, SStep *ss, int skip_if_stop, cudaStream_t s);
 
 // ---- ILU(0) on the left (Section VI)
 // One level of the row-by-row ILU(0) factorisation (rows: the level's rows): lu holds A's values on

@@ -376,6 +376,23 @@ __global__ void __launch_bounds__(kBT) k_bgs_tri(BgsArgs a, Cycle *st, SStep *ss
     }
 }
 
+// Flexible form, before the combination x += Z y: y <- M y (Z = P M, P the stored chain vectors).
+__global__ void __launch_bounds__(kThreads) k_sstep_flex_y(Cycle *st, SStep *ss, int skip_if_stop)
+{
+    __shared__ double sy[kSColsMax];
+    pdl_wait();
+    pdl_trigger();
+    const int k = st->k;
+    if (k == 0 || k > kSColsMax || (skip_if_stop && st->stop)) return;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) sy[r] = st->y[r];
+    __syncthreads();
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+        double v = 0.0;
+        for (int j = r; j < k; ++j) v = fma(ss->M[j][r], sy[j], v);
+        st->y[r] = v;
+    }
+}
+
 // index of (i, j), i <= j < sb, in the packed upper triangle the Gram pass writes
 __host__ __device__ constexpr int tri_index(int i, int j, int sb) { return i * sb - i * (i - 1) / 2 + (j - i); }
 
@@ -478,6 +495,28 @@ __device__ void cta_finish_block(const BgsArgs &a, Cycle *st, SStep *ss, const d
         }
     }
     __syncthreads();
+    // flexible form: the block's preconditioned columns Z_in = (P_blk - Z_old S_a) S_b^{-1} (the change of
+    // basis that gives H), with Z = P M: M[:, k + j] = (e_{k+j} - M[:, 0..k-1] S_a[:, j]
+    // - M[:, k..k+j-1] S_b[0..j-1, j]) / S_b[j][j], column by column, rows in parallel (zero below j)
+    if (a.flex && !s_bad) {
+        for (int j = 0; j < sbp; ++j) {
+            const int col = k + j;
+            for (int r = tid; r < kSColsMax; r += nt) {
+                double v = 0.0;
+                if (r <= col) {
+                    v = r == col ? 1.0 : 0.0;
+                    const double *Sj = S + j * ns;
+#pragma unroll 8
+                    for (int c = r; c < k; ++c) v -= ss->M[c][r] * Sj[c];  // M[c][r] = 0 for r > c
+                    for (int q = 0; q < j; ++q)
+                        if (r <= k + q) v -= ss->M[k + q][r] * Sj[k + q];
+                    v = j == 0 ? v : v * s_rl[j - 1];
+                }
+                ss->M[col][r] = v;
+            }
+            __syncthreads();
+        }
+    }
     // the columns as built, then the cycle's earlier rotations 0 .. k-1 (one thread per column); the
     // serial part below works on shared-memory copies of the rotations, g and the columns (a dependent
     // access to the device state costs an L2 round trip) and the results are written back in parallel
@@ -565,6 +604,9 @@ __device__ void cta_finish_block(const BgsArgs &a, Cycle *st, SStep *ss, const d
             if (brk) {
                 st->breakdown = 1;
                 st->n_breakdowns += 1;
+                // the column after the last one formed holds no basis vector (its subdiagonal entry is
+                // zero): scale 0, as the single-vector breakdown leaves it, for the restart projection
+                st->sigma[k + 1 + nq] = 0.0;
             }
             st->j = jend;
             if (kdone > 0) {
@@ -766,6 +808,11 @@ cudaError_t launch_bgs_t(BgsArgs a, Cycle *st, SStep *ss, int num_sms, cudaStrea
 }  // namespace
 
 int bgs_max_blocks(int num_sms) { return 3 * num_sms; }
+
+cudaError_t launch_sstep_flex_y(Cycle *st, SStep *ss, int skip_if_stop, cudaStream_t s)
+{
+    return launch_pdl(k_sstep_flex_y, dim3(1), dim3(kSColsMax), 0, s, st, ss, skip_if_stop);
+}
 
 cudaError_t launch_bgs(int prec, BgsArgs a, Cycle *st, SStep *ss, int num_sms, cudaStream_t s)
 {

@@ -112,15 +112,20 @@ def test_c2_degree10_sstep_float64_matches_oracle(oracle_runs):
     print(msg)
 
 
-def test_c2_degree10_sstep_float32_matches_oracle(oracle_runs):
-    """s-step blocks of 4 in float32 with float64 refinement (standard form): the oracle's solution, and
-    the iteration count of the library's standard-form float32 solve without blocks, within one."""
+@pytest.mark.parametrize("form", [ppg.PPG_F32_FLEXIBLE, ppg.PPG_F32_STANDARD])
+def test_c2_degree10_sstep_float32_matches_oracle(oracle_runs, form):
+    """s-step blocks of 4 in float32 with float64 refinement: the oracle's solution, and the iteration
+    count of the library's float32 solve without blocks in the same form, within one; the flexible form
+    (Z = P M from the chains' p(A) u_i) also holds the oracle's count to max(5%, 1)."""
     ref = oracle_runs[("c2", 10)].result()
-    xs, info, relres = _gpu_solve("c2", 10, ppg.PPG_F32, sstep=4, sstep_shift=1.0)
-    _, info_std, _ = _gpu_solve("c2", 10, ppg.PPG_F32, f32_form=ppg.PPG_F32_STANDARD)
+    xs, info, relres = _gpu_solve("c2", 10, ppg.PPG_F32, sstep=4, sstep_shift=1.0, f32_form=form)
+    _, info_nb, _ = _gpu_solve("c2", 10, ppg.PPG_F32, f32_form=form)
     err = np.linalg.norm(xs - ref["x"]) / np.linalg.norm(ref["x"])
-    msg = (f"s-step float32: {info.stats['iterations']} iterations (standard form {info_std.stats['iterations']}, "
-           f"oracle {ref['iters']}), relres {relres:.3e}, err {err:.3e}")
+    it, it_nb = info.stats["iterations"], info_nb.stats["iterations"]
+    msg = (f"s-step float32 (form {form}): {it} iterations (without blocks {it_nb}, oracle {ref['iters']}), "
+           f"relres {relres:.3e}, err {err:.3e}")
     assert info.status == ppg.PPG_OK and relres <= 1e-8 and err <= 1e-6, msg
-    assert abs(info.stats["iterations"] - info_std.stats["iterations"]) <= 1, msg
+    assert abs(it - it_nb) <= 1, msg
+    if form == ppg.PPG_F32_FLEXIBLE:
+        assert abs(it - ref["iters"]) <= max(0.05 * ref["iters"], 1), msg
     print(msg)
