@@ -106,7 +106,9 @@ typedef struct {
                           together by block classical Gram-Schmidt twice and Cholesky QR, three global
                           reductions per block; the block's Hessenberg columns follow from the change of
                           basis, so the iterates are GMRES's in exact arithmetic.  Requires restart <= 64 and no
-                          ILU(0); the float32 solve runs in the standard form.  A block whose Newton vector
+                          ILU(0).  float32 solves take f32_form: the flexible form keeps each chain's p(A) u_i and
+                          the block's preconditioned columns as their combination Z = P M (M from the same change
+                          of basis), so x += Z y as without blocks.  A block whose Newton vector
                           is numerically dependent (Cholesky pivot below 1e-14 (float64) or 1e-6 (float32)
                           of its squared norm) ends the cycle with a lucky breakdown.  The first s-step solve of a
                           context allocates the blocks' device state and per-CTA sums (about 13 KB + 12.2 KB per SM
