@@ -18,6 +18,9 @@
 // a fixed order by a second kernel whose last CTA finishes the pass, so results are deterministic.
 // A Cholesky pivot below tau ||z_j||^2 means z_{j+1} lies in the span already built: the block
 // then ends with j + 1 columns, the last one with a zero subdiagonal entry (a lucky breakdown).
+// Flexible float32 form: each chain keeps P_i = p(A) u_i (u_0 = q_k, u_i = z_i); the block's
+// preconditioned columns (P_blk - Z_old S_a) S_b^{-1} satisfy A Z = [Q, Q_new] H exactly as built, and
+// are kept as Z = P M with M extended by the finalisation (y <- M y before x += Z y).
 #include <cuda_runtime.h>
 
 #include "ppg_cycle.cuh"
