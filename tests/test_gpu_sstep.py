@@ -4,8 +4,9 @@ against the oracle's s-step solver and the library's standard solve.
 Blocks of s Newton vectors (A p(A) - theta I)^i q_k are orthogonalised together (block classical
 Gram-Schmidt twice, Cholesky QR); in exact arithmetic the iterates are GMRES's.  Tolerances: the
 float64 solve follows the oracle's iteration count within max(1, 5%) and its solution within 1e-6
-(relative), like the standard solve's parity tests; the float32 solve (standard form, float64
-refinement) reaches the true relative residual asked for.
+(relative), like the standard solve's parity tests; the float32 solve (float64 refinement; the
+flexible form by default, Z = P M from the chains' p(A) u_i, and the standard form) reaches the true
+relative residual asked for and the oracle's solution.
 """
 import numpy as np
 import pytest
@@ -89,16 +90,19 @@ def test_sstep_f64_follows_the_standard_solve(s):
     sol.close()
 
 
+@pytest.mark.parametrize("form", [ppg.PPG_F32_FLEXIBLE, ppg.PPG_F32_STANDARD])
 @pytest.mark.parametrize("s", [4, 8])
-def test_sstep_f32_reaches_the_oracles_solution(s):
-    """Float32 blocks with float64 refinement (standard form) reach the float64 oracle's solution."""
+def test_sstep_f32_reaches_the_oracles_solution(s, form):
+    """Float32 blocks with float64 refinement, in the flexible form (Z = P M) and the standard form,
+    reach the float64 oracle's solution."""
     a = w.convdiff(17, 3, 20.0)
     b = w.rhs(a.n)
     v0 = w.v0(a.n)
     sol = solver_for(a)
     sol.build_poly(10, ppg.PPG_BASIS_ROOTS, v0=T(v0))
     ref = oracle.gmres(a, b, oracle.poly_gmres(a, v0, 10), tol=1e-8, m=50, maxit=5000)
-    x, info = sol.solve(T(b), tol=1e-8, restart=50, maxit=5000, precision=ppg.PPG_F32, sstep=s, sstep_shift=1.0)
+    x, info = sol.solve(T(b), tol=1e-8, restart=50, maxit=5000, precision=ppg.PPG_F32, sstep=s, sstep_shift=1.0,
+                        f32_form=form)
     xg = x.cpu().numpy()
     assert info.status == ppg.PPG_OK, info.stats
     assert relres(a, b, xg) <= 1e-8
