@@ -111,7 +111,7 @@ typedef struct {
                           of basis), so x += Z y as without blocks.  A block whose Newton vector
                           is numerically dependent (Cholesky pivot below 1e-14 (float64) or 1e-6 (float32)
                           of its squared norm) ends the cycle with a lucky breakdown.  The first s-step solve of a
-                          context allocates the blocks' device state and per-CTA sums (about 45 KB + 12.2 KB per SM
+                          context allocates the blocks' device state and per-CTA sums (about 45 KB + 13 KB per SM
                           of the GPU), outside the workspace */
     double sstep_shift; /* the Newton shift theta (sstep > 0): a point inside the spectrum of A p(A); a
                           minimum-residual polynomial clusters that spectrum around 1 */

@@ -1294,7 +1294,8 @@ ppg_status ensure_sstep(ppg_ctx *c)
     if (c->d_sstep) return PPG_OK;
     const int nblk = bgs_max_blocks(c->num_sms);
     const int pld = (nblk + 1) & ~1;
-    const size_t slots = (size_t)(kSMax * kSColsMax + kSMax) * (size_t)pld;
+    // one slot per (sum, CTA): at most (k + 1) s inner products plus s (s + 1) / 2 Gram entries per pass
+    const size_t slots = (size_t)(kSMax * kSColsMax + kSMax * (kSMax + 1) / 2) * (size_t)pld;
     if (cudaMalloc(&c->d_bgs_partials, slots * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         c->d_bgs_partials = nullptr;
