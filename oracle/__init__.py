@@ -77,7 +77,7 @@ def _load():
         _lib.orc_gmres_lu.argtypes = [i64, p, p, p, p, ci, ci, p, p, p, d, p, p, d, ci, ci, p, p, ci]
         _lib.orc_gmres_lu.restype = ci
         # s-step GMRES with the polynomial (Newton basis, block CGS2, Cholesky QR)
-        _lib.orc_sstep_gmres.argtypes = [i64, p, p, p, ci, ci, p, p, p, d, p, p, d, ci, ci, ci, d, p, p, ci]
+        _lib.orc_sstep_gmres.argtypes = [i64, p, p, p, ci, ci, p, p, p, d, p, p, d, ci, ci, ci, d, p, p, ci, p]
         _lib.orc_sstep_gmres.restype = ci
     return _lib
 
@@ -312,12 +312,12 @@ def gmres(a, b, p: Poly = IDENTITY, tol=1e-8, m=50, maxit=10000, x0=None, lu=Non
                        float(stats[6]), hist[:it].copy())
 
 
-def sstep_gmres(a, b, p: Poly = IDENTITY, s=5, theta=0.0, tol=1e-8, m=50, maxit=10000, x0=None):
+def sstep_gmres(a, b, p: Poly = IDENTITY, s=5, theta=0.0, tol=1e-8, m=50, maxit=10000, x0=None, want_h=False):
     """s-step GMRES(m) with right preconditioning A p(A) u = b: per block, s Newton vectors
     (B - theta I) z / ||.|| from the last basis vector (B = A p(A)), block classical Gram-Schmidt twice
     against the basis, Cholesky QR within the block, and the block's Hessenberg columns recovered from
     the change of basis.  The same iterates as gmres() in exact arithmetic.  Returns (SolveResult,
-    number of breakdowns)."""
+    number of breakdowns), and with want_h the first cycle's Hessenberg matrix ((m+1) x m, as built)."""
     lib = _load()
     n, rp, ci, va = _csr(a)
     b = _f64(b)
@@ -325,10 +325,14 @@ def sstep_gmres(a, b, p: Poly = IDENTITY, s=5, theta=0.0, tol=1e-8, m=50, maxit=
     stats = np.zeros(8)
     hist = np.zeros(maxit)
     keep = p._keep()  # noqa: F841
+    h = np.zeros((int(m), int(m) + 1)) if want_h else None  # column-major (m+1) x m, as rows of a (m, m+1) array
     st = lib.orc_sstep_gmres(n, _ptr(rp), _ptr(ci), _ptr(va), *p.args(), _ptr(b), _ptr(x), float(tol), int(m),
-                             int(maxit), int(s), float(theta), _ptr(stats), _ptr(hist), int(maxit))
+                             int(maxit), int(s), float(theta), _ptr(stats), _ptr(hist), int(maxit), _ptr(h))
     if st == -2:
         raise MemoryError("oracle allocation failed")
     it = int(stats[0])
-    return SolveResult(x, bool(stats[4]), it, int(stats[1]), int(stats[2]), int(stats[3]), float(stats[5]),
-                       float(stats[6]), hist[:it].copy()), int(stats[7])
+    res = SolveResult(x, bool(stats[4]), it, int(stats[1]), int(stats[2]), int(stats[3]), float(stats[5]),
+                      float(stats[6]), hist[:it].copy())
+    if want_h:
+        return res, int(stats[7]), h.T.copy()
+    return res, int(stats[7])

@@ -791,10 +791,12 @@ int orc_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const double *va,
  * rotations one by one, as in orc_gmres.  A Newton vector of norm 0 or a Cholesky pivot that is not
  * positive shortens the block to the vectors before it; an empty block is a breakdown (the cycle ends).
  * stats as orc_gmres, with stats[3] = global reductions: one per Newton norm, two block inner products
- * and one Gram matrix per block, one per true residual. */
+ * and one Gram matrix per block, one per true residual.  h_first (optional, (m+1) x m column-major)
+ * receives the first cycle's Hessenberg matrix as built (before the rotations), its other entries zero. */
 int orc_sstep_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const double *va, int kind, int deg,
                     const double *coef, const double *Hp, const double *yp, double betap, const double *b, double *x,
-                    double tol, int m, int maxit, int s, double theta, double *stats, double *hist, int hist_cap)
+                    double tol, int m, int maxit, int s, double theta, double *stats, double *hist, int hist_cap,
+                    double *h_first)
 {
     csr_t A = {n, rp, ci, va, NULL};
     poly_t p = {kind, deg, coef, Hp, yp, betap};
@@ -977,6 +979,10 @@ int orc_sstep_gmres(int64_t n, const int32_t *rp, const int32_t *ci, const doubl
             }
             if (!stop) k += sb;
         }
+        if (h_first && cycles == 1) /* the first cycle's columns 0 .. k-1 as built (rows 0 .. j+1 of column j) */
+            for (int j = 0; j < m; ++j)
+                for (int i = 0; i <= m; ++i)
+                    h_first[i + (int64_t)j * ldh] = (j < k && i <= j + 1) ? Hraw[i + (int64_t)j * ldh] : 0.0;
         /* y = R^{-1} g over the k columns, x += p(A) V y */
         for (int i = k - 1; i >= 0; --i) {
             double v = g[i];

@@ -572,3 +572,42 @@ def test_sstep_zero_rhs_and_maxit():
     assert not r.converged and r.iters == 7
     ref = oracle.gmres(a, w.rhs(a.n), oracle.IDENTITY, tol=1e-8, m=50, maxit=7)
     np.testing.assert_allclose(r.hist, ref.hist, rtol=1e-8)
+
+
+def _dense_arnoldi_reorth(M, v, k):
+    """k Arnoldi steps with the dense operator M from v, classical Gram-Schmidt applied twice (numpy)."""
+    n = len(v)
+    V = np.zeros((n, k + 1))
+    H = np.zeros((k + 1, k))
+    V[:, 0] = v / np.linalg.norm(v)
+    for j in range(k):
+        w_ = M @ V[:, j]
+        for _ in range(2):
+            h = V[:, : j + 1].T @ w_
+            w_ = w_ - V[:, : j + 1] @ h
+            H[: j + 1, j] += h
+        H[j + 1, j] = np.linalg.norm(w_)
+        V[:, j + 1] = w_ / H[j + 1, j]
+    return H
+
+
+@pytest.mark.parametrize("s,theta", [(1, 1.0), (3, 1.0), (4, 0.5), (7, 1.0)])
+def test_sstep_hessenberg_equals_arnoldis(s, theta):
+    """The first cycle's Hessenberg matrix recovered block by block from the change of basis equals the
+    one Arnoldi builds from b with the explicit dense operator A p(A) and reorthogonalisation (both
+    bases are orthonormal with positive subdiagonal entries, so unique), for blocks that do and do not
+    divide the 9 columns; and the oracle's own MGS Arnoldi's, whose orthogonality loss grows about tenfold
+    per column here (1e-9 by the ninth).  Blocks of 1 and 3 agree with the dense reference to 1e-13;
+    larger blocks to about 1e-10, the precision Cholesky QR of a Newton block keeps (kappa(Z)^2 u)."""
+    a = w.convdiff(10, 3, 20.0)
+    b = w.rhs(a.n)
+    p = oracle.poly_gmres(a, w.v0(a.n), 5)
+    M = np.column_stack([oracle.spmv(a, oracle.poly_apply(a, p, e)) for e in np.eye(a.n)])
+    k = 9
+    _, _, H_s = oracle.sstep_gmres(a, b, p, s=s, theta=theta, tol=1e-15, m=k, maxit=k, want_h=True)
+    H_d = _dense_arnoldi_reorth(M, b, k)
+    _, H_a, _, steps = oracle.arnoldi(a, p, b, k)
+    assert steps == k and H_s.shape == H_d.shape == H_a.shape == (k + 1, k)
+    scale = np.abs(H_d).max()
+    np.testing.assert_allclose(H_s, H_d, rtol=0, atol=(1e-12 if s <= 3 else 1e-9) * scale)
+    np.testing.assert_allclose(H_s, H_a, rtol=0, atol=1e-8 * scale)
